@@ -1,0 +1,34 @@
+"""FP64 CPU oracle for the Neural Shadow Mapping hot path.
+
+TEST INFRASTRUCTURE.  This package is the plain, slow, obviously correct
+statement of what the GPU path computes; it exists to check that path.  Only
+the test-suite, the smoke check of the package entry file and the CPU-baseline
+leg of the benchmark may import it.  The product library never imports,
+links or executes anything here, and nothing here imports the product.
+
+Contents
+  gather   -- texel lookup and hard depth test (binary32-exact definition),
+              the four input features (Sec. 3.1, 3.2, Fig. 2), the blocker
+              search and the penumbra-width model (Sec. 3.6, suppl. Sec. 4).
+  network  -- the compact encoder/decoder (Sec. 3.5), its adjoint, the
+              Eq. 2 loss (L1 part) and an Adam step.
+
+Pinning status (what checks each function against something other than
+itself; the tests under tests/test_oracle_*.py):
+  project_fp32 / lookup_and_test -- brute-force shadow rays on tiny scenes,
+      the sphere-over-plane shadow conic, hand-built projections with known
+      texel indices, the FP64 index (differences only at texel boundaries).
+  features -- closed forms on hand-built pixels; invariants on rendered frames.
+  blocker_search -- brute force over the whole map on tiny inputs, the
+      no-occluder and k = 0 special cases.
+  penumbra_width -- the r_e = 0 and r_s = 0 closed forms (similar triangles).
+  conv2d / avgpool2 / upsample2 -- direct summation loops, torch FP64
+      library routines, adjoint dot-product identities.
+  forward / backward -- composition of the pinned operators; backward against
+      central finite differences; parameter and MAC counts against the
+      paper's printed table values.  With random weights the network output
+      has no printed worked example: parity with respect to trained weights
+      is unpinned beyond the operator level.
+  loss_l1 / adam_update / train_step -- closed forms on small vectors and
+      finite differences of the loss.
+"""

@@ -1,0 +1,327 @@
+"""Oracle: the compact encoder/decoder, its adjoint, the loss and Adam (FP64).
+
+TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).
+
+Architecture (Sec. 3.5): each level has one 3x3 convolution and one 1x1
+convolution; average pooling (2x2, stride 2) on the way down; bilinear x2
+upsampling on the way up; decoder skips merged by an algebraic sum; no skip
+connection at level 0.  Readings where the paper is silent: ReLU after every
+convolution except the output head, which is a 1x1 convolution 16 -> 1
+followed by a sigmoid; zero "same" padding; biases present; bilinear x2 with
+half-pixel centres (align_corners = False) and edge clamping.
+
+Per-level channel plan (w_l = 16 * 2^l): encoder 3x3 w_{l-1} -> w_l (4 input
+features at level 0), encoder 1x1 w_l -> w_l; decoder 3x3 w_l -> w_l,
+decoder 1x1 w_l -> w_{l-1} (16 -> 16 at level 0); the bottleneck level L-1
+has 3x3 w_{L-2} -> w_{L-1} and 1x1 w_{L-1} -> w_{L-2}.  This plan gives
+exactly the parameter and per-pixel MAC counts the paper prints for the 3-
+and 5-level nets (suppl. Tab. 3 and Tab. 5): 39,248 / 8,528 and
+653,648 / 16,208, and 7.15 / 8.05 / 8.05 / 8.05 / 2.68 GMAC per level at
+1024 x 2048.
+
+Tensors are channel-first (C, H, W) float64.  Weight layout: a flat vector,
+for each layer in `layer_table` order its OIHW weights then its bias.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+# ------------------------------------------------------------------ topology
+
+
+def layer_table(levels: int = 3, base: int = 16, in_ch: int = 4):
+    """[(name, c_in, c_out, k)] in canonical order: encoder levels 0..L-2
+    (3x3, 1x1), bottleneck (3x3, 1x1), decoder levels L-2..0 (3x3, 1x1), head."""
+    w = [base * (2 ** l) for l in range(levels)]
+    t = []
+    for l in range(levels - 1):
+        cin = in_ch if l == 0 else w[l - 1]
+        t.append((f"enc{l}_3x3", cin, w[l], 3))
+        t.append((f"enc{l}_1x1", w[l], w[l], 1))
+    b = levels - 1
+    t.append((f"bott_3x3", w[b - 1], w[b], 3))
+    t.append((f"bott_1x1", w[b], w[b - 1], 1))
+    for l in range(levels - 2, -1, -1):
+        cout = w[l - 1] if l > 0 else w[0]
+        t.append((f"dec{l}_3x3", w[l], w[l], 3))
+        t.append((f"dec{l}_1x1", w[l], cout, 1))
+    t.append(("head", w[0], 1, 1))
+    return t
+
+
+def param_count(levels: int = 3, with_bias: bool = False) -> int:
+    n = 0
+    for (_, ci, co, k) in layer_table(levels):
+        n += ci * co * k * k + (co if with_bias else 0)
+    return n
+
+
+def macs_per_pixel_by_level(levels: int = 3):
+    """MACs per full-resolution pixel, per level (level l runs at 1/4^l pixels)."""
+    out = [0.0] * levels
+    for (name, ci, co, k) in layer_table(levels):
+        if name == "head":
+            lvl = 0
+        elif name.startswith("bott"):
+            lvl = levels - 1
+        else:
+            lvl = int(name[3])
+        out[lvl] += ci * co * k * k / (4.0 ** lvl)
+    return out
+
+
+def unpack(theta: np.ndarray, levels: int = 3):
+    """Flat canonical vector -> {name: (W (O,I,k,k), b (O,))}."""
+    theta = np.asarray(theta, np.float64)
+    out = {}
+    off = 0
+    for (name, ci, co, k) in layer_table(levels):
+        n = co * ci * k * k
+        W = theta[off:off + n].reshape(co, ci, k, k)
+        off += n
+        b = theta[off:off + co]
+        off += co
+        out[name] = (W, b)
+    if off != theta.size:
+        raise ValueError(f"weight vector has {theta.size} entries, expected {off}")
+    return out
+
+
+def pack(params, levels: int = 3) -> np.ndarray:
+    parts = []
+    for (name, ci, co, k) in layer_table(levels):
+        W, b = params[name]
+        parts.append(np.asarray(W, np.float64).reshape(-1))
+        parts.append(np.asarray(b, np.float64).reshape(-1))
+    return np.concatenate(parts)
+
+
+# ------------------------------------------------------------------ operators
+
+
+def conv2d(x: np.ndarray, W: np.ndarray, b: np.ndarray) -> np.ndarray:
+    """Zero-padded 'same' cross-correlation: y[o,y,x] = b[o] +
+    sum_{c,u,v} W[o,c,u,v] x[c, y+u-p, x+v-p], p = (k-1)/2.  The channel sum
+    of each tap is one tensordot; taps are summed in (u, v) order."""
+    co, ci, k, _ = W.shape
+    p = (k - 1) // 2
+    C, H, Wd = x.shape
+    assert C == ci
+    xp = np.pad(x, ((0, 0), (p, p), (p, p)))
+    y = np.broadcast_to(b[:, None, None], (co, H, Wd)).astype(np.float64).copy()
+    for u in range(k):
+        for v in range(k):
+            y += np.tensordot(W[:, :, u, v], xp[:, u:u + H, v:v + Wd], axes=(1, 0))
+    return y
+
+
+def conv2d_adjoint(gy: np.ndarray, x: np.ndarray, W: np.ndarray):
+    """Adjoint of conv2d: (dx, dW, db) for output cotangent gy."""
+    co, ci, k, _ = W.shape
+    p = (k - 1) // 2
+    C, H, Wd = x.shape
+    xp = np.pad(x, ((0, 0), (p, p), (p, p)))
+    dxp = np.zeros_like(xp)
+    dW = np.zeros_like(W)
+    for u in range(k):
+        for v in range(k):
+            dxp[:, u:u + H, v:v + Wd] += np.tensordot(W[:, :, u, v], gy, axes=(0, 0))
+            dW[:, :, u, v] = np.tensordot(gy, xp[:, u:u + H, v:v + Wd], axes=([1, 2], [1, 2]))
+    dx = dxp[:, p:p + H, p:p + Wd] if p else dxp
+    db = gy.sum(axis=(1, 2))
+    return dx, dW, db
+
+
+def relu(x):
+    return np.maximum(x, 0.0)
+
+
+def avgpool2(x: np.ndarray) -> np.ndarray:
+    """2x2 average pooling, stride 2 (H, W even)."""
+    C, H, W = x.shape
+    return x.reshape(C, H // 2, 2, W // 2, 2).mean(axis=(2, 4))
+
+
+def avgpool2_adjoint(gy: np.ndarray) -> np.ndarray:
+    return 0.25 * np.repeat(np.repeat(gy, 2, axis=1), 2, axis=2)
+
+
+def _bilinear_taps(n: int):
+    """Output index o of a x2 upsample samples the input at o/2 - 1/4
+    (half-pixel centres).  Returns (i0, i1, w0, w1) with clamped indices."""
+    o = np.arange(2 * n)
+    src = (o + 0.5) / 2.0 - 0.5
+    i0 = np.floor(src).astype(np.int64)
+    w1 = src - i0
+    w0 = 1.0 - w1
+    i1 = i0 + 1
+    return np.clip(i0, 0, n - 1), np.clip(i1, 0, n - 1), w0, w1
+
+
+def upsample2(x: np.ndarray) -> np.ndarray:
+    """Bilinear x2 upsampling, align_corners = False, edge clamp."""
+    C, H, W = x.shape
+    y0, y1, wy0, wy1 = _bilinear_taps(H)
+    x0, x1, wx0, wx1 = _bilinear_taps(W)
+    rows = x[:, y0, :] * wy0[None, :, None] + x[:, y1, :] * wy1[None, :, None]
+    return rows[:, :, x0] * wx0[None, None, :] + rows[:, :, x1] * wx1[None, None, :]
+
+
+def upsample2_adjoint(gy: np.ndarray) -> np.ndarray:
+    C, H2, W2 = gy.shape
+    H, W = H2 // 2, W2 // 2
+    y0, y1, wy0, wy1 = _bilinear_taps(H)
+    x0, x1, wx0, wx1 = _bilinear_taps(W)
+    g_rows = np.zeros((C, H2, W))
+    np.add.at(g_rows, (slice(None), slice(None), x0), gy * wx0[None, None, :])
+    np.add.at(g_rows, (slice(None), slice(None), x1), gy * wx1[None, None, :])
+    gx = np.zeros((C, H, W))
+    np.add.at(gx, (slice(None), y0, slice(None)), g_rows * wy0[None, :, None])
+    np.add.at(gx, (slice(None), y1, slice(None)), g_rows * wy1[None, :, None])
+    return gx
+
+
+def sigmoid(x):
+    return 1.0 / (1.0 + np.exp(-x))
+
+
+# ------------------------------------------------------------------ network
+
+
+def forward(feat: np.ndarray, theta: np.ndarray, levels: int = 3, keep: bool = False):
+    """Visibility (H, W) from features (4, H, W); H, W multiples of 2^(levels-1).
+    With keep=True also returns the dict of every intermediate (for the adjoint)."""
+    P = unpack(theta, levels)
+    t = {}
+    h = np.asarray(feat, np.float64)
+    skips = {}
+    for l in range(levels - 1):
+        t[f"enc{l}_in"] = h
+        a = conv2d(h, *P[f"enc{l}_3x3"])
+        t[f"enc{l}_a3"] = a
+        h3 = relu(a)
+        t[f"enc{l}_h3"] = h3
+        a1 = conv2d(h3, *P[f"enc{l}_1x1"])
+        t[f"enc{l}_a1"] = a1
+        h1 = relu(a1)
+        t[f"enc{l}_h1"] = h1
+        if l >= 1:
+            skips[l] = h1
+        h = avgpool2(h1)
+    t["bott_in"] = h
+    a = conv2d(h, *P["bott_3x3"])
+    t["bott_a3"] = a
+    h3 = relu(a)
+    t["bott_h3"] = h3
+    a1 = conv2d(h3, *P["bott_1x1"])
+    t["bott_a1"] = a1
+    h = relu(a1)
+    t["bott_out"] = h
+    for l in range(levels - 2, -1, -1):
+        u = upsample2(h)
+        x = u + skips[l] if l >= 1 else u
+        t[f"dec{l}_in"] = x
+        a = conv2d(x, *P[f"dec{l}_3x3"])
+        t[f"dec{l}_a3"] = a
+        h3 = relu(a)
+        t[f"dec{l}_h3"] = h3
+        a1 = conv2d(h3, *P[f"dec{l}_1x1"])
+        t[f"dec{l}_a1"] = a1
+        h = relu(a1)
+        t[f"dec{l}_out"] = h
+    logit = conv2d(h, *P["head"])[0]
+    t["logit"] = logit
+    vis = sigmoid(logit)
+    t["vis"] = vis
+    return (vis, t) if keep else vis
+
+
+def backward(gvis: np.ndarray, theta: np.ndarray, t: dict, levels: int = 3):
+    """Adjoint of `forward`: returns (dtheta flat, dfeat) for cotangent gvis (H, W)."""
+    P = unpack(theta, levels)
+    G = {}
+    vis = t["vis"]
+    glogit = (gvis * vis * (1.0 - vis))[None]
+    gh, dW, db = conv2d_adjoint(glogit, t["dec0_out"], P["head"][0])
+    G["head"] = (dW, db)
+    gskip = {}
+    for l in range(0, levels - 1):
+        ga1 = gh * (t[f"dec{l}_a1"] > 0)
+        gh3, dW, db = conv2d_adjoint(ga1, t[f"dec{l}_h3"], P[f"dec{l}_1x1"][0])
+        G[f"dec{l}_1x1"] = (dW, db)
+        ga3 = gh3 * (t[f"dec{l}_a3"] > 0)
+        gx, dW, db = conv2d_adjoint(ga3, t[f"dec{l}_in"], P[f"dec{l}_3x3"][0])
+        G[f"dec{l}_3x3"] = (dW, db)
+        if l >= 1:
+            gskip[l] = gx
+        gh = upsample2_adjoint(gx)
+    ga1 = gh * (t["bott_a1"] > 0)
+    gh3, dW, db = conv2d_adjoint(ga1, t["bott_h3"], P["bott_1x1"][0])
+    G["bott_1x1"] = (dW, db)
+    ga3 = gh3 * (t["bott_a3"] > 0)
+    gx, dW, db = conv2d_adjoint(ga3, t["bott_in"], P["bott_3x3"][0])
+    G["bott_3x3"] = (dW, db)
+    gh = gx
+    for l in range(levels - 2, -1, -1):
+        gh1 = avgpool2_adjoint(gh)
+        if l >= 1:
+            gh1 = gh1 + gskip[l]
+        ga1 = gh1 * (t[f"enc{l}_a1"] > 0)
+        gh3, dW, db = conv2d_adjoint(ga1, t[f"enc{l}_h3"], P[f"enc{l}_1x1"][0])
+        G[f"enc{l}_1x1"] = (dW, db)
+        ga3 = gh3 * (t[f"enc{l}_a3"] > 0)
+        gx, dW, db = conv2d_adjoint(ga3, t[f"enc{l}_in"], P[f"enc{l}_3x3"][0])
+        G[f"enc{l}_3x3"] = (dW, db)
+        gh = gx
+    return pack(G, levels), gh
+
+
+# ------------------------------------------------------------------ loss (Eq. 2)
+
+
+def loss_l1(x0: np.ndarray, target: np.ndarray, xs, alpha: float = 0.9):
+    """Eq. 2 with the per-pixel term L(y, y~) = alpha |y - y~| (the VGG-19 term
+    is not evaluated: its ImageNet weights are unavailable), averaged over
+    pixels:  alpha mean|x0 - x~| + sum_i alpha mean|x0 - x_i|.
+    Gradient flows through x0 only; d|u|/du at u = 0 is taken as 0.
+    Returns (loss, dloss/dx0)."""
+    n = x0.size
+    loss = alpha * np.abs(x0 - target).sum() / n
+    g = alpha * np.sign(x0 - target) / n
+    for xi in xs:
+        loss += alpha * np.abs(x0 - xi).sum() / n
+        g = g + alpha * np.sign(x0 - xi) / n
+    return float(loss), g
+
+
+def adam_update(theta, grad, m, v, step, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
+    """One Adam step (Kingma & Ba 2015) with bias correction; step >= 1.
+    Returns (theta, m, v)."""
+    m = beta1 * m + (1.0 - beta1) * grad
+    v = beta2 * v + (1.0 - beta2) * grad * grad
+    mh = m / (1.0 - beta1 ** step)
+    vh = v / (1.0 - beta2 ** step)
+    theta = theta - lr * mh / (np.sqrt(vh) + eps)
+    return theta, m, v
+
+
+def train_step(batch_feats, targets, theta, m, v, step, lr=1e-3, alpha=0.9, levels=3):
+    """One temporal-window training step (Sec. 3.3, Eq. 2).
+
+    batch_feats: list over batch items of lists over window instances of
+    features (4, H, W); instance 0 carries the target and the gradient, the
+    others are evaluated without gradient.  The per-item losses are averaged
+    over the batch.  Returns (theta, m, v, loss, grad)."""
+    B = len(batch_feats)
+    grad = np.zeros_like(np.asarray(theta, np.float64))
+    total = 0.0
+    for b in range(B):
+        insts = batch_feats[b]
+        x0, t = forward(insts[0], theta, levels, keep=True)
+        xs = [forward(f, theta, levels) for f in insts[1:]]
+        loss, g = loss_l1(x0, targets[b], xs, alpha)
+        total += loss / B
+        dth, _ = backward(g / B, theta, t, levels)
+        grad += dth
+    theta2, m2, v2 = adam_update(theta, grad, m, v, step, lr)
+    return theta2, m2, v2, total, grad

@@ -1,0 +1,235 @@
+"""Pins for the oracle's network operators, architecture counts, adjoint,
+Eq. 2 loss and Adam step."""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import network as N
+
+GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_network_counts.json")))
+
+
+def _conv_direct(x, W, b):
+    """Seven nested loops: y[o,i,j] = b[o] + sum_c sum_u sum_v W[o,c,u,v] x[c, i+u-p, j+v-p]."""
+    co, ci, k, _ = W.shape
+    p = (k - 1) // 2
+    C, H, Wd = x.shape
+    y = np.zeros((co, H, Wd))
+    for o in range(co):
+        for i in range(H):
+            for j in range(Wd):
+                s = b[o]
+                for c in range(ci):
+                    for u in range(k):
+                        for v in range(k):
+                            ii, jj = i + u - p, j + v - p
+                            if 0 <= ii < H and 0 <= jj < Wd:
+                                s += W[o, c, u, v] * x[c, ii, jj]
+                y[o, i, j] = s
+    return y
+
+
+@pytest.mark.parametrize("k", [1, 3])
+def test_conv_matches_direct_summation(k):
+    rng = np.random.default_rng(1)
+    x = rng.standard_normal((3, 5, 7))
+    W = rng.standard_normal((4, 3, k, k))
+    b = rng.standard_normal(4)
+    np.testing.assert_allclose(N.conv2d(x, W, b), _conv_direct(x, W, b), rtol=1e-13, atol=1e-13)
+
+
+def test_conv_matches_asymmetric_kernel_orientation():
+    """A single off-centre tap shifts the image: W[0,0,0,2] = 1 reads x[i-1, j+1]."""
+    x = np.arange(20.0).reshape(1, 4, 5)
+    W = np.zeros((1, 1, 3, 3))
+    W[0, 0, 0, 2] = 1.0
+    y = N.conv2d(x, W, np.zeros(1))
+    assert y[0, 2, 1] == x[0, 1, 2]
+    assert y[0, 0, 1] == 0.0 and y[0, 2, 4] == 0.0  # zero padding
+
+
+def test_ops_match_torch_fp64():
+    torch = pytest.importorskip("torch")
+    F = torch.nn.functional
+    rng = np.random.default_rng(2)
+    x = rng.standard_normal((6, 8, 12))
+    W = rng.standard_normal((5, 6, 3, 3))
+    b = rng.standard_normal(5)
+    ref = F.conv2d(torch.from_numpy(x)[None], torch.from_numpy(W), torch.from_numpy(b), padding=1)[0].numpy()
+    np.testing.assert_allclose(N.conv2d(x, W, b), ref, rtol=1e-12, atol=1e-12)
+    ref = F.avg_pool2d(torch.from_numpy(x)[None], 2)[0].numpy()
+    np.testing.assert_allclose(N.avgpool2(x), ref, rtol=1e-14, atol=1e-14)
+    ref = F.interpolate(torch.from_numpy(x)[None], scale_factor=2, mode="bilinear", align_corners=False)[0].numpy()
+    np.testing.assert_allclose(N.upsample2(x), ref, rtol=1e-13, atol=1e-13)
+
+
+def test_upsample_closed_form():
+    x = np.array([[[0.0, 4.0], [8.0, 12.0]]])
+    y = N.upsample2(x)
+    # row 0 sits at source 0 (clamped), column 1 at source 0.25
+    assert y[0, 0, 0] == 0.0
+    assert y[0, 0, 1] == pytest.approx(1.0)
+    # row 1, column 1 sit at source (0.25, 0.25): 0.75 (0.75*0 + 0.25*4) + 0.25 (0.75*8 + 0.25*12)
+    assert y[0, 1, 1] == pytest.approx(3.0)
+    assert y[0, 3, 3] == 12.0
+
+
+@pytest.mark.parametrize("name", ["conv3", "conv1", "pool", "up"])
+def test_adjoint_dot_product_identity(name):
+    """<A x, y> = <x, A^T y> for every linear operator in the network."""
+    rng = np.random.default_rng(3)
+    x = rng.standard_normal((4, 6, 10))
+    if name.startswith("conv"):
+        k = 3 if name == "conv3" else 1
+        W = rng.standard_normal((5, 4, k, k))
+        Ax = N.conv2d(x, W, np.zeros(5))
+        y = rng.standard_normal(Ax.shape)
+        ATy, dW, db = N.conv2d_adjoint(y, x, W)
+        # and the weight adjoint: <A_W x, y> is linear in W
+        assert np.sum(Ax * y) == pytest.approx(np.sum(W * dW), rel=1e-12)
+    elif name == "pool":
+        Ax = N.avgpool2(x)
+        y = rng.standard_normal(Ax.shape)
+        ATy = N.avgpool2_adjoint(y)
+    else:
+        Ax = N.upsample2(x)
+        y = rng.standard_normal(Ax.shape)
+        ATy = N.upsample2_adjoint(y)
+    assert np.sum(Ax * y) == pytest.approx(np.sum(x * ATy), rel=1e-12)
+
+
+def test_architecture_counts_match_paper():
+    t3 = N.layer_table(3)
+    assert [n for (n, *_r) in t3] == ["enc0_3x3", "enc0_1x1", "enc1_3x3", "enc1_1x1", "bott_3x3",
+                                     "bott_1x1", "dec1_3x3", "dec1_1x1", "dec0_3x3", "dec0_1x1", "head"]
+    nc = GOLD["network_cost"]
+    for lv in ("3", "5"):
+        L = int(lv)
+        assert sum(N.macs_per_pixel_by_level(L)) == nc[lv]["macs_per_pixel"]
+        # printed to the last shown digit (653,648 is printed as 653.7K)
+        assert abs(N.param_count(L) / 1000.0 - nc[lv]["params_thousands"]) <= (0.005 if L == 3 else 0.06)
+    per = GOLD["params_per_level_5lvl_thousands"]["values"]
+    gm = GOLD["gmac_per_level_5lvl_1024x2048"]
+    npx = gm["height"] * gm["width"]
+    macs = N.macs_per_pixel_by_level(5)
+    for lvl in range(5):
+        assert round(macs[lvl] * npx / 1e9, 2) == pytest.approx(gm["values"][lvl])
+        params = macs[lvl] * 4 ** lvl
+        assert round(params / 1000.0, 2) == pytest.approx(per[lvl], abs=0.051)
+    # 5-level FP32 size ~ 2.5 MB (Sec. 3.5)
+    assert round(N.param_count(5) * 4 / 2 ** 20, 1) == GOLD["fp32_size_mb"]["value"]
+
+
+def _rand_theta(levels, seed=0, scale=1.0):
+    rng = np.random.default_rng(seed)
+    parts = []
+    for (_, ci, co, k) in N.layer_table(levels):
+        parts.append(rng.standard_normal(co * ci * k * k) * scale * math.sqrt(2.0 / (ci * k * k)))
+        parts.append(rng.standard_normal(co) * 0.1)
+    return np.concatenate(parts)
+
+
+def test_forward_range_and_shapes():
+    rng = np.random.default_rng(4)
+    x = rng.standard_normal((4, 16, 24))
+    th = _rand_theta(3)
+    v, t = N.forward(x, th, keep=True)
+    assert v.shape == (16, 24)
+    assert ((v > 0) & (v < 1)).all()
+    assert t["bott_in"].shape == (32, 4, 6)
+    assert t["dec1_in"].shape == (32, 8, 12)
+    # the skip is the level-1 encoder output, merged by a sum
+    np.testing.assert_allclose(t["dec1_in"], N.upsample2(t["bott_out"]) + t["enc1_h1"])
+    # level 0 has no skip
+    np.testing.assert_allclose(t["dec0_in"], N.upsample2(t["dec1_out"]))
+
+
+def test_backward_matches_central_finite_differences():
+    """dL/dtheta against central differences (h = 1e-3, FP64) on a 32x32 crop,
+    for the scalar L = <g, vis>; coordinates whose stencil crosses a ReLU kink
+    are excluded by checking that the forward pattern does not change."""
+    rng = np.random.default_rng(5)
+    x = rng.standard_normal((4, 32, 32))
+    th = _rand_theta(3, seed=6)
+    g = rng.standard_normal((32, 32))
+    v, t = N.forward(x, th, keep=True)
+    grad, gfeat = N.backward(g, th, t)
+    h = 1e-3
+    idx = rng.choice(th.size, 60, replace=False)
+    offs = np.cumsum([0] + [co * ci * k * k + co for (_, ci, co, k) in N.layer_table(3)])
+    idx = np.concatenate([idx, offs[:-1], offs[1:] - 1])  # first weight and last bias of every layer
+
+    def pattern(tt):
+        return np.concatenate([(tt[k] > 0).ravel() for k in tt if k.endswith(("_a3", "_a1"))])
+
+    checked = 0
+    for i in idx:
+        tp = th.copy(); tp[i] += h
+        tm = th.copy(); tm[i] -= h
+        vp, ttp = N.forward(x, tp, keep=True)
+        vm, ttm = N.forward(x, tm, keep=True)
+        if not (np.array_equal(pattern(ttp), pattern(t)) and np.array_equal(pattern(ttm), pattern(t))):
+            continue
+        fd = (np.sum(g * vp) - np.sum(g * vm)) / (2 * h)
+        assert fd == pytest.approx(grad[i], rel=1e-6, abs=1e-9), i
+        checked += 1
+    assert checked >= 40
+    # input gradient, a few coordinates
+    for (c, yy, xx) in [(0, 3, 4), (1, 16, 16), (2, 31, 0), (3, 10, 29)]:
+        xp = x.copy(); xp[c, yy, xx] += h
+        xm = x.copy(); xm[c, yy, xx] -= h
+        fd = (np.sum(g * N.forward(xp, th)) - np.sum(g * N.forward(xm, th))) / (2 * h)
+        assert fd == pytest.approx(gfeat[c, yy, xx], rel=1e-5, abs=1e-9)
+
+
+def test_loss_eq2_closed_form_and_gradient():
+    x0 = np.array([[0.2, 0.5], [0.9, 0.4]])
+    tgt = np.array([[0.0, 0.5], [1.0, 1.0]])
+    x1 = np.array([[0.3, 0.5], [0.9, 0.1]])
+    x2 = np.array([[0.1, 0.6], [0.8, 0.4]])
+    loss, g = N.loss_l1(x0, tgt, [x1, x2], alpha=0.9)
+    expect = 0.9 * (0.2 + 0 + 0.1 + 0.6) / 4 + 0.9 * (0.1 + 0 + 0 + 0.3) / 4 + 0.9 * (0.1 + 0.1 + 0.1 + 0) / 4
+    assert loss == pytest.approx(expect, rel=1e-14)
+    np.testing.assert_allclose(g, 0.9 / 4 * np.array([[1 - 1 + 1, 0 + 0 - 1], [-1 + 0 + 1, -1 + 1 + 0]]))
+    assert GOLD["loss"]["alpha"] == 0.9
+
+
+def test_adam_closed_form_first_steps():
+    th = np.array([1.0, -2.0, 0.0])
+    g = np.array([0.5, -0.1, 0.0])
+    m = np.zeros(3); v = np.zeros(3)
+    th1, m1, v1 = N.adam_update(th, g, m, v, 1, lr=0.01)
+    # step 1: m_hat = g, v_hat = g^2 -> update = lr * sign(g) (up to eps)
+    np.testing.assert_allclose(th1, th - 0.01 * np.array([1.0, -1.0, 0.0]), atol=1e-9)
+    th2, m2, v2 = N.adam_update(th1, g, m1, v1, 2, lr=0.01)
+    np.testing.assert_allclose(th2, th1 - 0.01 * np.array([1.0, -1.0, 0.0]), atol=1e-9)
+    np.testing.assert_allclose(m2, 0.19 * g)
+
+
+def test_train_step_gradient_is_loss_gradient():
+    """The batch gradient equals central differences of the Eq. 2 loss
+    (with the perturbed outputs x_i held fixed, as the stop-gradient says)."""
+    rng = np.random.default_rng(8)
+    B, T, H, W = 2, 3, 8, 8
+    feats = [[rng.standard_normal((4, H, W)) for _ in range(T)] for _ in range(B)]
+    tgts = [rng.uniform(0, 1, (H, W)) for _ in range(B)]
+    th = _rand_theta(3, seed=9)
+    _, _, _, loss, grad = N.train_step(feats, tgts, th, np.zeros_like(th), np.zeros_like(th), 1)
+    xs = [[N.forward(f, th) for f in feats[b][1:]] for b in range(B)]
+
+    def L(tt):
+        tot = 0.0
+        for b in range(B):
+            tot += N.loss_l1(N.forward(feats[b][0], tt), tgts[b], xs[b])[0] / B
+        return tot
+
+    assert loss == pytest.approx(L(th), rel=1e-12)
+    h = 1e-6
+    for i in rng.choice(th.size, 12, replace=False):
+        tp = th.copy(); tp[i] += h
+        tm = th.copy(); tm[i] -= h
+        fd = (L(tp) - L(tm)) / (2 * h)
+        assert fd == pytest.approx(grad[i], rel=1e-4, abs=1e-9)
