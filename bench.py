@@ -1,0 +1,387 @@
+#!/usr/bin/env python3
+"""Benchmark: 1080p neural-shadow inference (gather + compact encoder/decoder)
+on one GB300 per rank, through the library's C ABI.
+
+Workload per rank and step: one 1920 x 1080 view with a 2048^2 shadow map of a
+seeded scene (ground plane + 64 boxes / spheres, point light), inputs resident
+in HBM; one nsm_infer call = one step.  Ranks process independent frames (weak
+scaling, no collective on the data path).  L2 is flushed (256 MiB write)
+between timed steps, outside the timed events.
+
+Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle on a
+bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "1080p neural-shadow inference ms/frame & Mpix/s, BF16 vs FP32 at stated MSE"
+H, W, HS, WS, N_OBJ = 1080, 1920, 2048, 2048, 64
+WORKLOAD = "1920x1080 view, 2048x2048 shadow map, 64 seeded boxes/spheres on a ground plane, point light, 3-level 16/32/64 net"
+SCENE_SEED, WEIGHT_SEED = 11, 3
+
+# per-pixel MACs of each inference kernel, indexed by pixels of its own level
+MACS = {"enc0": 4 * 16 * 9 + 16 * 16, "enc1": 16 * 32 * 9 + 32 * 32, "bott": 32 * 64 * 9 + 64 * 32,
+        "dec1": 32 * 32 * 9 + 32 * 16, "dec0": 16 * 16 * 9 + 16 * 16 + 16}
+
+
+def kernel_algorithmic(name: str, precision: str):
+    """(flops, bytes) per launch of one inference kernel at the bench size."""
+    eb = 4 if precision == "fp32" else 2
+    n0, n1, n2 = H * W, (H // 2) * (W // 2), (H // 4) * (W // 4)
+    sm_bytes = min(n0, HS * WS) * 4
+    if "enc0" in name:
+        return 2 * MACS["enc0"] * n0, 32 * n0 + sm_bytes + n1 * 16 * eb
+    if "enc1" in name:
+        return 2 * MACS["enc1"] * n1, n1 * 16 * eb + n1 * 32 * eb + n2 * 32 * eb
+    if "bott" in name:
+        return 2 * MACS["bott"] * n2, n2 * 32 * eb * 2
+    if "dec1" in name:
+        return 2 * MACS["dec1"] * n1, n2 * 32 * eb + n1 * 32 * eb + n1 * 16 * eb
+    if "dec0" in name:
+        return 2 * MACS["dec0"] * n0, n1 * 16 * eb + n0 * 4
+    raise KeyError(name)
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return {"hbm_gbs": d["hbm_gbs"], "bf16_tflops": d["bf16_tflops"],
+                "sm_max_mhz": d.get("sm_max_mhz", 2070.0), "src": "measured"}
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0, "src": "fallback"}
+
+
+def fp32_alu_peak_tflops(sm_count: int, mhz: float) -> float:
+    # 128 FP32 lanes per SM, one FMA (2 FLOP) per lane per clock
+    return sm_count * 128 * 2 * mhz * 1e6 / 1e12
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.proc = None
+        self.path = None
+        try:
+            import tempfile
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        rows = [r.split(",") for r in open(self.path).read().strip().splitlines() if r.strip()]
+        os.unlink(self.path)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+                for k, nm in enumerate(names):
+                    if r[5 + k].strip().lower().startswith("active"):
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                continue
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ distributed
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def reduce_max(value: float, world: int, device):
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ------------------------------------------------------------------ oracle (reference arm / cpu baseline)
+def oracle_sample(frame, theta, rows: int):
+    """Time the FP64 oracle (features + network forward) on the first `rows`
+    rows of the frame; returns (seconds, pixels)."""
+    from oracle import gather as G
+    from oracle import network as N
+    sub = slice(0, rows)
+    t0 = time.perf_counter()
+    feat, _, _ = G.features(frame.pos4[sub], frame.nrm4[sub], frame.sm, frame.view_proj, frame.light_pos,
+                            frame.cam_pos, frame.r_hat, frame.z_far, frame.bias)
+    N.forward(feat, theta)
+    return time.perf_counter() - t0, rows * frame.W
+
+
+def cpu_threads():
+    try:
+        from threadpoolctl import threadpool_info
+        info = threadpool_info()
+        if info:
+            return max(i.get("num_threads", 1) for i in info)
+    except Exception:
+        pass
+    return os.cpu_count() or 1
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    import scenegen
+    from oracle import network as N
+    frame = scenegen.hard_frame(H, W, HS, WS, N_OBJ, SCENE_SEED)
+    theta = scenegen.he_init_weights(WEIGHT_SEED, N.layer_table(3)).astype(np.float32).astype(np.float64)
+    rows = 256
+    for _ in range(args.warmup):
+        oracle_sample(frame, theta, rows)
+    secs, px = 0.0, 0
+    for _ in range(args.steps):
+        s, p = oracle_sample(frame, theta, rows)
+        secs += s
+        px += p
+    mpix = px / secs / 1e6
+    ms_frame = (H * W) / (px / secs) * 1e3
+    cores = cpu_threads()
+    sample = f"first {rows} rows ({rows}x{W} px) of the frame per step: binary32 texel lookup + FP64 features + FP64 network forward"
+    line = {"impl": "reference", "metric": METRIC, "value": mpix, "unit": "Mpix/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs / args.steps * 1e3,
+            "ms_per_frame": ms_frame, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic (seeded ray-cast scene)",
+            "config": {"workload": WORKLOAD, "l2": "n/a (CPU)"},
+            "cpu_baseline": {"value": mpix, "unit": "Mpix/s", "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": mpix, "unit": "Mpix/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ our arm
+def run_ours(args):
+    import torch
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=device)
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2301_05262_gb300 as nsm
+    import scenegen
+
+    frame = scenegen.hard_frame(H, W, HS, WS, N_OBJ, SCENE_SEED + rank)
+    theta = scenegen.he_init_weights(WEIGHT_SEED, nsm.LAYERS).astype(np.float32)
+    ctx = nsm.Context()
+    weights = nsm.Weights(ctx, theta)
+    pos4 = torch.from_numpy(frame.pos4).to(device)
+    nrm4 = torch.from_numpy(frame.nrm4).to(device)
+    sm = torch.from_numpy(frame.sm).to(device)
+    light = nsm.LightDesc(pos=tuple(frame.light_pos), radius=frame.light_radius, r_hat=frame.r_hat,
+                          view_proj=frame.view_proj, z_far=frame.z_far, bias=frame.bias,
+                          tan_half_fov=frame.tan_half_fov)
+    fr = nsm.make_frame(pos4, nrm4, sm, light, frame.cam_pos)
+    flush = torch.empty(256 * 2 ** 20, dtype=torch.uint8, device=device)
+    stream = torch.cuda.current_stream(device)
+    sms = torch.cuda.get_device_properties(device).multi_processor_count
+    peaks = load_peaks()
+
+    forms = {}
+    precisions = [p for p in args.precisions.split(",") if p]
+    for pname in precisions:
+        prec = nsm.PRECISIONS[pname]
+        knames = nsm.nsm_infer_kernel_names(prec)
+        if not knames:
+            continue
+        ws = torch.empty((nsm.nsm_infer_workspace_bytes(H, W, prec),), dtype=torch.uint8, device=device)
+        vis = torch.empty((H, W), dtype=torch.float32, device=device)
+        for _ in range(args.warmup):
+            flush.zero_()
+            nsm.nsm_infer(ctx, fr, weights, prec, ws, vis)
+        torch.cuda.synchronize()
+        nk = len(knames)
+        step_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        stage_ev = [[torch.cuda.Event(enable_timing=True) for _ in range(nk + 1)] for _ in range(args.steps)]
+        for evs in stage_ev:  # torch creates the CUDA event on its first record
+            for ev in evs:
+                ev.record(stream)
+        torch.cuda.synchronize()
+        sampler = ClockSampler(local) if pname == precisions[0] else None
+        barrier(world)
+        torch.cuda.synchronize()
+        for k in range(args.steps):
+            flush.zero_()
+            ctx.set_stage_events(stage_ev[k])
+            step_ev[k][0].record(stream)
+            nsm.nsm_infer(ctx, fr, weights, prec, ws, vis)
+            step_ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        barrier(world)
+        clocks = sampler.stop() if sampler else None
+        ctx.set_stage_events([])
+        ctx.check()
+        step_ms = [a.elapsed_time(b) for (a, b) in step_ev]
+        total_ms = reduce_max(sum(step_ms), world, device)
+        per_kernel = {}
+        for i, kn in enumerate(knames):
+            per_kernel[kn] = sum(stage_ev[k][i].elapsed_time(stage_ev[k][i + 1]) for k in range(args.steps)) / args.steps
+        forms[pname] = {"ms_per_frame": total_ms / args.steps, "mpix_s": world * H * W * args.steps / (total_ms * 1e-3) / 1e6,
+                        "kernels_ms": per_kernel, "launches_per_step": nk, "clocks": clocks}
+
+    # end-to-end through the host-buffer entry point (copies inside the timed region)
+    head = precisions[0]
+    prec = nsm.PRECISIONS[head]
+    pin_pos = torch.from_numpy(frame.pos4).pin_memory()
+    pin_nrm = torch.from_numpy(frame.nrm4).pin_memory()
+    pin_sm = torch.from_numpy(frame.sm).pin_memory()
+    pin_vis = torch.empty((H, W), dtype=torch.float32).pin_memory()
+    hfr = nsm.make_frame(pin_pos, pin_nrm, pin_sm, light, frame.cam_pos)
+    stage = torch.empty((nsm.nsm_infer_host_stage_bytes(H, W, HS, WS),), dtype=torch.uint8, device=device)
+    ws = torch.empty((nsm.nsm_infer_workspace_bytes(H, W, prec),), dtype=torch.uint8, device=device)
+    vis_np = pin_vis.numpy()
+    for _ in range(args.warmup):
+        nsm.nsm_infer_host(ctx, hfr, weights, prec, stage, ws, vis_np)
+    barrier(world)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        nsm.nsm_infer_host(ctx, hfr, weights, prec, stage, ws, vis_np)
+    torch.cuda.synchronize()
+    e2e_s = reduce_max(time.perf_counter() - t0, world, device)
+    e2e = {"value": world * H * W * args.steps / e2e_s / 1e6, "unit": "Mpix/s",
+           "h2d_bytes_per_step": 2 * H * W * 16 + HS * WS * 4, "d2h_bytes_per_step": H * W * 4,
+           "ms_per_frame": e2e_s / args.steps * 1e3}
+
+    # accuracy of the timed output vs the FP64 oracle (rank 0 only, full frame)
+    errs = {}
+    if rank == 0 and not args.skip_error:
+        from oracle import gather as G
+        from oracle import network as N
+        feat, _, _ = G.features(frame.pos4, frame.nrm4, frame.sm, frame.view_proj, frame.light_pos, frame.cam_pos,
+                                frame.r_hat, frame.z_far, frame.bias)
+        ref = N.forward(feat, theta.astype(np.float64))
+        for pname in forms:
+            ws = torch.empty((nsm.nsm_infer_workspace_bytes(H, W, nsm.PRECISIONS[pname]),), dtype=torch.uint8, device=device)
+            vis = torch.empty((H, W), dtype=torch.float32, device=device)
+            nsm.nsm_infer(ctx, fr, weights, nsm.PRECISIONS[pname], ws, vis)
+            d = vis.cpu().numpy().astype(np.float64) - ref
+            errs[pname] = {"max_abs": float(np.abs(d).max()), "mse": float(np.mean(d * d))}
+
+    # CPU baseline: the oracle on a bounded sample, host cores (rank 0 only)
+    cpu = None
+    if rank == 0 and not args.skip_cpu:
+        theta64 = theta.astype(np.float64)
+        secs, px = oracle_sample(frame, theta64, 540)
+        cpu = {"value": px / secs / 1e6, "unit": "Mpix/s", "cores": cpu_threads(), "kind": "oracle",
+               "sample": f"540x{W} rows of the frame: binary32 texel lookup + FP64 features + FP64 network forward ({secs:.1f} s)"}
+
+    if rank != 0:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return 0
+
+    hf = forms[head]
+    kern = max(hf["kernels_ms"], key=hf["kernels_ms"].get)
+    flops, nbytes = kernel_algorithmic(kern, head)
+    dur_s = hf["kernels_ms"][kern] * 1e-3
+    if head == "fp32":
+        peak_tf = fp32_alu_peak_tflops(sms, peaks["sm_max_mhz"])
+        t_alu = flops / (peak_tf * 1e12)
+        t_hbm = nbytes / (peaks["hbm_gbs"] * 1e9)
+        if t_alu >= t_hbm:
+            roof = {"bound": "alu", "achieved": flops / dur_s / 1e12, "peak": peak_tf, "unit": "TFLOP/s"}
+        else:
+            roof = {"bound": "hbm", "achieved": nbytes / dur_s / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s"}
+    else:
+        t_tc = flops / (peaks["bf16_tflops"] * 1e12)
+        t_hbm = nbytes / (peaks["hbm_gbs"] * 1e9)
+        if t_tc >= t_hbm:
+            roof = {"bound": "tensor", "achieved": flops / dur_s / 1e12, "peak": peaks["bf16_tflops"], "unit": "TFLOP/s"}
+        else:
+            roof = {"bound": "hbm", "achieved": nbytes / dur_s / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["traffic"] = None
+    roof["kernel"] = kern
+    roof["peak_src"] = peaks["src"] if roof["bound"] != "alu" else "derived: SMs x 128 FP32 lanes x 2 FLOP x max SM clock"
+    roof["algorithmic"] = {"flops": flops, "bytes": nbytes}
+
+    line = {"metric": METRIC, "value": hf["mpix_s"], "unit": "Mpix/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": hf["ms_per_frame"], "ms_per_frame": hf["ms_per_frame"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32" if head == "fp32" else head,
+            "data": "synthetic (seeded ray-cast scene, He-init weights)",
+            "config": {"workload": WORKLOAD, "precision": head, "l2": "flushed (256 MiB write) between timed steps",
+                       "parallelism": f"{world} independent frame(s), one per GPU"},
+            "forms": {k: {kk: vv for kk, vv in v.items() if kk != "clocks"} for k, v in forms.items()},
+            "error_vs_fp64_oracle": errs,
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": hf["launches_per_step"] * args.steps,
+            "clocks": hf["clocks"]}
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precisions", default="fp32", help="comma list; the first is the headline form")
+    ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--skip-error", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

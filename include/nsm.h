@@ -1,0 +1,188 @@
+/*
+ * nsm.h -- C ABI of the GB300 (sm_103a) Neural Shadow Mapping hot path.
+ *
+ * The library computes per-pixel shadow visibility for one view from the
+ * rasterised inputs the paper names (Sec. 3.1): a G-buffer (world position,
+ * view depth d, normal n), a vanilla single-frustum shadow map holding the
+ * emitter-to-occluder depth z, and the emitter description (position, size).
+ * Two stages run on the GPU:
+ *   1. the shadow-map feature gather: project each pixel into the map, fetch
+ *      z, do the depth test and form the four network inputs
+ *      f = [c_e + r_e, z / z_f, z - z_f, c_c / d]   (Sec. 3.1, 3.2, Fig. 2);
+ *   2. the compact encoder/decoder (Sec. 3.5): 3 levels of widths 16/32/64,
+ *      one 3x3 and one 1x1 convolution per level, 2x2 average pooling down,
+ *      bilinear x2 upsampling up, decoder skip merged by a sum, no skip at
+ *      level 0, ReLU after every convolution, 1x1 head 16 -> 1 + sigmoid.
+ *
+ * Conventions for every entry point:
+ *   - Buffers named "device" must be device (or managed) memory of the
+ *     current CUDA device, owned by the caller; the library never frees them.
+ *   - Images are dense, row-major, row 0 first; pixel p = y * W + x.
+ *   - Calls are asynchronous on the given stream (a cudaStream_t passed as
+ *     void*, NULL = the legacy default stream) and never synchronise, except
+ *     where stated.  Errors found on the host are returned before any work is
+ *     queued; outputs are then untouched.  nsm_last_error() gives a message.
+ *   - No entry point allocates device memory except nsm_ctx_create,
+ *     nsm_weights_create and nsm_train_state_create (set-up calls).
+ *   - Kernel waits are bounded; a wait that runs out sets the context's device
+ *     error word, read back by nsm_ctx_check (NSM_ERR_TIMEOUT).
+ */
+#ifndef NSM_H
+#define NSM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define NSM_ABI_VERSION 1
+
+typedef enum {
+    NSM_OK = 0,
+    NSM_ERR_INVALID_ARG = 1,  /* null / non-device pointer, bad enum, bad value */
+    NSM_ERR_SHAPE = 2,        /* unsupported sizes (see each call) */
+    NSM_ERR_ALIGNMENT = 3,    /* a pointer or size breaks the stated alignment */
+    NSM_ERR_DEVICE = 4,       /* no usable sm_103 device / wrong device */
+    NSM_ERR_CUDA = 5,         /* a CUDA runtime call failed */
+    NSM_ERR_TIMEOUT = 6,      /* a bounded device-side wait gave up */
+    NSM_ERR_UNSUPPORTED = 7,  /* valid request this build cannot serve */
+    NSM_ERR_WORKSPACE = 8     /* workspace missing or too small */
+} nsm_status;
+
+typedef enum {
+    NSM_FP32 = 0,  /* FP32 CUDA-core convolutions (parity form) */
+    NSM_BF16 = 1,  /* BF16 operands on tcgen05 tensor cores, FP32 accumulation */
+    NSM_FP8 = 2    /* FP8 E4M3 operands (per-channel weight scales), FP32 accumulation */
+} nsm_precision;
+
+/* Emitter and its shadow-map frustum (Sec. 3.1). */
+typedef struct {
+    float pos[3];         /* emitter centre L, world space */
+    float radius;         /* emitter radius r (world); 0 = point light */
+    float r_hat;          /* emitter-size input, added to c_e as a DC offset (Sec. 3.1.1), 0..4 */
+    float view_proj[16];  /* world -> light clip space, row-major:
+                             clip_r = ((M[r][0] Px + M[r][1] Py) + M[r][2] Pz) + M[r][3] */
+    float z_far;          /* depth used for pixels that project outside the map */
+    float bias;           /* relative depth bias beta: a pixel is lit iff z_f <= z + beta z_f */
+    float tan_half_fov;   /* tan(fov / 2) of the map frustum (blocker-search window) */
+} nsm_light;
+
+typedef struct {
+    float pos[3];         /* camera centre C, world space */
+} nsm_camera;
+
+/* One view: G-buffer + shadow map + emitter + camera. */
+typedef struct {
+    int H, W;             /* view size in pixels */
+    const float* pos4;    /* device, H*W*4 floats, 16-byte aligned: (P.x, P.y, P.z, d), d > 0 the view depth */
+    const float* nrm4;    /* device, H*W*4 floats, 16-byte aligned: (n.x, n.y, n.z, unused), |n| = 1 */
+    int Hs, Ws;           /* shadow-map size (texels), each in [1, 16384] */
+    const float* sm;      /* device, Hs*Ws floats: z per texel, row j = floor(v Hs), v = ndc_y / 2 + 1/2 */
+    nsm_light light;
+    nsm_camera camera;
+} nsm_frame;
+
+typedef struct nsm_ctx nsm_ctx;          /* device error word, autotune table, graph cache */
+typedef struct nsm_weights nsm_weights;  /* network weights, FP32 + packed BF16 / FP8 copies */
+
+/* ---------------------------------------------------------------- general */
+
+int nsm_abi_version(void);
+
+/* Message for the last error returned on the calling thread ("" if none). */
+const char* nsm_last_error(void);
+
+/* Create a context on the current CUDA device (which must be sm_103). Allocates
+ * a few bytes of device memory (the error word). */
+nsm_status nsm_ctx_create(nsm_ctx** out);
+void nsm_ctx_destroy(nsm_ctx* ctx);
+
+/* Synchronise the context's work and read the device error word: NSM_OK, or
+ * NSM_ERR_TIMEOUT when a bounded device wait gave up since the last check
+ * (the word is cleared).  This call synchronises the device. */
+nsm_status nsm_ctx_check(nsm_ctx* ctx);
+
+/* Profiling hook.  With n > 0, every later nsm_infer / nsm_infer_host on this
+ * context records events[i] (cudaEvent_t handles passed as void*, created and
+ * owned by the caller) on its stream right before launching its i-th kernel,
+ * and events[k] after the last of its k kernels; n must be >= k + 1 for the
+ * precision used (see nsm_infer_kernel_count).  n = 0 (events NULL) turns the
+ * hook off.  Recording events does not change the results. */
+nsm_status nsm_ctx_set_stage_events(nsm_ctx* ctx, void* const* events, int n);
+
+/* Number of kernels nsm_infer launches per call for a precision, and the name
+ * of the i-th (a static string; "" when i is out of range). */
+int nsm_infer_kernel_count(nsm_precision precision);
+const char* nsm_infer_kernel_name(nsm_precision precision, int i);
+
+/* ---------------------------------------------------------------- weights */
+
+/* Number of floats in the canonical parameter vector: for each layer, in the
+ * order enc0_3x3, enc0_1x1, enc1_3x3, enc1_1x1, bott_3x3, bott_1x1, dec1_3x3,
+ * dec1_1x1, dec0_3x3, dec0_1x1, head, its OIHW weights then its bias
+ * (39,248 weights + 273 biases = 39,521; Sec. 3.5, suppl. Table 5). */
+size_t nsm_param_count(void);
+
+/* Upload a canonical parameter vector (host memory, n == nsm_param_count())
+ * and build the packed BF16 / FP8 copies.  Set-up call: allocates device memory. */
+nsm_status nsm_weights_create(nsm_ctx* ctx, const float* host_params, size_t n, nsm_weights** out);
+
+/* Re-pack from a canonical FP32 vector already on the device (e.g. the
+ * master weights of a training state); asynchronous on stream. */
+nsm_status nsm_weights_load_device(nsm_weights* w, const float* dev_params, size_t n, void* stream);
+void nsm_weights_destroy(nsm_weights* w);
+
+/* ---------------------------------------------------------------- gather */
+
+/* Feature gather (Sec. 3.1, 3.2): for every pixel p of the frame
+ *   feat_out  [4][H][W] float32 (device, required):
+ *             channel 0 c_e + r_hat, 1 z / z_f, 2 z - z_f, 3 c_c / d, with
+ *             z_f = |L - P|, c_e = n.(L - P) / z_f, c_c = n.(C - P) / |C - P|;
+ *   texel_out [H][W] int32 (device, nullable): j * Ws + i of the texel read,
+ *             -1 when P projects outside the map (then z = z_far);
+ *   hard_out  [ceil(H W / 32)] uint32 (device, nullable): bit (p % 32) of
+ *             word p / 32 is 1 iff the pixel is lit by the hard depth test;
+ *   blocker_out [3][H][W] float32 (device, nullable): z_min, z_max of the map
+ *             texels z < z_f - beta z_f within the emitter's window around
+ *             (i, j) (half-size k = min(32, ceil(r Ws / 2 / (z_f tan_half_fov)))),
+ *             and the penumbra width x_a + x_b of the spherical-occluder model
+ *             (Sec. 3.6, suppl. Sec. 4); all three 0 where no blocker is found.
+ * Texel index, hard bit and blocker window are computed in binary32 with a
+ * fixed operation order and no contraction, so they are reproducible bit for
+ * bit.  H, W >= 0 (0 = nothing to do). */
+nsm_status nsm_features(const nsm_frame* frame, float* feat_out, int32_t* texel_out,
+                        uint32_t* hard_out, float* blocker_out, void* stream);
+
+/* ---------------------------------------------------------------- inference */
+
+/* Bytes of device workspace nsm_infer needs for an H x W view (0 if H or W
+ * is 0).  The workspace holds the intermediate activations of the levels. */
+size_t nsm_infer_workspace_bytes(int H, int W, nsm_precision precision);
+
+/* Per-pixel visibility in [0, 1] for one view: the gather fused into the
+ * first level, then the network (Sec. 3.5).
+ *   vis_out   [H][W] float32 (device).
+ *   workspace device, >= nsm_infer_workspace_bytes(H, W, precision) bytes,
+ *             256-byte aligned, not shared with a concurrent call.
+ * H and W must be multiples of 4 (two 2x2 poolings), W <= 16384, H <= 16384. */
+nsm_status nsm_infer(nsm_ctx* ctx, const nsm_frame* frame, const nsm_weights* w,
+                     nsm_precision precision, void* workspace, size_t workspace_bytes,
+                     float* vis_out, void* stream);
+
+/* nsm_infer with HOST inputs and output: copies pos4 / nrm4 / sm (host
+ * pointers inside *frame, pinned or pageable) to the caller's device staging
+ * buffers, runs nsm_infer and copies the visibility back to vis_host.
+ *   dev_stage  device, >= nsm_infer_host_stage_bytes(frame) bytes, 256-byte aligned.
+ * Synchronises the stream before returning (vis_host is then valid). */
+size_t nsm_infer_host_stage_bytes(int H, int W, int Hs, int Ws);
+nsm_status nsm_infer_host(nsm_ctx* ctx, const nsm_frame* host_frame, const nsm_weights* w,
+                          nsm_precision precision, void* dev_stage, size_t stage_bytes,
+                          void* workspace, size_t workspace_bytes, float* vis_host, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NSM_H */

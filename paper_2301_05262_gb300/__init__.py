@@ -1,0 +1,246 @@
+"""Python binding of libnsm.so (include/nsm.h): argument marshalling only.
+
+Every step of the hot path runs in the library's CUDA kernels; this module
+turns torch tensors (device memory, streams) and numpy arrays (host memory)
+into the C structs and pointers of the ABI and raises NSMError on failure.
+There is no fallback: if libnsm.so has not been built, loading it raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libnsm.so")
+
+NSM_FP32, NSM_BF16, NSM_FP8 = 0, 1, 2
+PRECISIONS = {"fp32": NSM_FP32, "bf16": NSM_BF16, "fp8": NSM_FP8}
+STATUS = {0: "NSM_OK", 1: "NSM_ERR_INVALID_ARG", 2: "NSM_ERR_SHAPE", 3: "NSM_ERR_ALIGNMENT",
+          4: "NSM_ERR_DEVICE", 5: "NSM_ERR_CUDA", 6: "NSM_ERR_TIMEOUT", 7: "NSM_ERR_UNSUPPORTED",
+          8: "NSM_ERR_WORKSPACE"}
+
+# canonical layer order of the parameter vector: (name, c_in, c_out, k)
+LAYERS = [("enc0_3x3", 4, 16, 3), ("enc0_1x1", 16, 16, 1), ("enc1_3x3", 16, 32, 3),
+          ("enc1_1x1", 32, 32, 1), ("bott_3x3", 32, 64, 3), ("bott_1x1", 64, 32, 1),
+          ("dec1_3x3", 32, 32, 3), ("dec1_1x1", 32, 16, 1), ("dec0_3x3", 16, 16, 3),
+          ("dec0_1x1", 16, 16, 1), ("head", 16, 1, 1)]
+
+
+class NSMError(RuntimeError):
+    def __init__(self, status: int, where: str, msg: str):
+        super().__init__(f"{where}: {STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class nsm_light(ctypes.Structure):
+    _fields_ = [("pos", ctypes.c_float * 3), ("radius", ctypes.c_float), ("r_hat", ctypes.c_float),
+                ("view_proj", ctypes.c_float * 16), ("z_far", ctypes.c_float), ("bias", ctypes.c_float),
+                ("tan_half_fov", ctypes.c_float)]
+
+
+class nsm_camera(ctypes.Structure):
+    _fields_ = [("pos", ctypes.c_float * 3)]
+
+
+class nsm_frame(ctypes.Structure):
+    _fields_ = [("H", ctypes.c_int), ("W", ctypes.c_int), ("pos4", ctypes.c_void_p),
+                ("nrm4", ctypes.c_void_p), ("Hs", ctypes.c_int), ("Ws", ctypes.c_int),
+                ("sm", ctypes.c_void_p), ("light", nsm_light), ("camera", nsm_camera)]
+
+
+_lib = None
+
+
+def lib():
+    """The loaded library; raises if it has not been built (no fallback)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: build it with "
+                              "`python -c 'import __graft_entry__ as g; g.build()'`")
+        L = ctypes.CDLL(LIB_PATH)
+        P, I, Z = ctypes.c_void_p, ctypes.c_int, ctypes.c_size_t
+        FP = ctypes.POINTER(nsm_frame)
+        sig = {
+            "nsm_abi_version": ([], I),
+            "nsm_last_error": ([], ctypes.c_char_p),
+            "nsm_ctx_create": ([ctypes.POINTER(P)], I),
+            "nsm_ctx_destroy": ([P], None),
+            "nsm_ctx_check": ([P], I),
+            "nsm_ctx_set_stage_events": ([P, P, I], I),
+            "nsm_infer_kernel_count": ([I], I),
+            "nsm_infer_kernel_name": ([I, I], ctypes.c_char_p),
+            "nsm_param_count": ([], Z),
+            "nsm_weights_create": ([P, P, Z, ctypes.POINTER(P)], I),
+            "nsm_weights_load_device": ([P, P, Z, P], I),
+            "nsm_weights_destroy": ([P], None),
+            "nsm_features": ([FP, P, P, P, P, P], I),
+            "nsm_infer_workspace_bytes": ([I, I, I], Z),
+            "nsm_infer": ([P, FP, P, I, P, Z, P, P], I),
+            "nsm_infer_host_stage_bytes": ([I, I, I, I], Z),
+            "nsm_infer_host": ([P, FP, P, I, P, Z, P, Z, P, P], I),
+        }
+        for name, (args, res) in sig.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = L
+    return _lib
+
+
+def declared_symbols():
+    """Names declared by include/nsm.h (for the ABI completeness test)."""
+    import re
+    hdr = open(os.path.join(os.path.dirname(HERE), "include", "nsm.h")).read()
+    hdr = re.sub(r"/\*.*?\*/", "", hdr, flags=re.S)
+    return sorted(set(re.findall(r"\b(nsm_[a-z0-9_]+)\s*\(", hdr)))
+
+
+def _check(status: int, where: str):
+    if status != 0:
+        raise NSMError(status, where, lib().nsm_last_error().decode())
+
+
+def _ptr(x):
+    """Address of a torch tensor / numpy array / None."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        assert x.flags["C_CONTIGUOUS"]
+        return ctypes.c_void_p(x.ctypes.data)
+    if hasattr(x, "data_ptr"):
+        assert x.is_contiguous()
+        return ctypes.c_void_p(x.data_ptr())
+    return ctypes.c_void_p(int(x))
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        if torch.cuda.is_available():
+            return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+@dataclass
+class LightDesc:
+    pos: tuple
+    radius: float
+    r_hat: float
+    view_proj: np.ndarray  # (4, 4) row-major
+    z_far: float
+    bias: float
+    tan_half_fov: float
+
+
+def make_frame(pos4, nrm4, sm, light: LightDesc, cam_pos) -> nsm_frame:
+    """Build an nsm_frame from (H, W, 4) pos4 / nrm4 and (Hs, Ws) sm buffers
+    (torch device tensors or numpy host arrays; the caller keeps them alive)."""
+    H, W = int(pos4.shape[0]), int(pos4.shape[1])
+    Hs, Ws = int(sm.shape[0]), int(sm.shape[1])
+    L = nsm_light()
+    L.pos[:] = [float(v) for v in light.pos]
+    L.radius = float(light.radius)
+    L.r_hat = float(light.r_hat)
+    L.view_proj[:] = [float(v) for v in np.asarray(light.view_proj, np.float32).reshape(-1)]
+    L.z_far = float(light.z_far)
+    L.bias = float(light.bias)
+    L.tan_half_fov = float(light.tan_half_fov)
+    C = nsm_camera()
+    C.pos[:] = [float(v) for v in cam_pos]
+    return nsm_frame(H=H, W=W, pos4=_ptr(pos4), nrm4=_ptr(nrm4), Hs=Hs, Ws=Ws, sm=_ptr(sm), light=L, camera=C)
+
+
+class Context:
+    def __init__(self):
+        h = ctypes.c_void_p()
+        _check(lib().nsm_ctx_create(ctypes.byref(h)), "nsm_ctx_create")
+        self.h = h
+
+    def check(self):
+        _check(lib().nsm_ctx_check(self.h), "nsm_ctx_check")
+
+    def set_stage_events(self, events):
+        """events: list of torch.cuda.Event (timing enabled), or [] to turn the hook off."""
+        handles = [ctypes.c_void_p(e.cuda_event) for e in events]
+        arr = (ctypes.c_void_p * max(1, len(handles)))(*handles)
+        _check(lib().nsm_ctx_set_stage_events(self.h, arr if handles else None, len(handles)),
+               "nsm_ctx_set_stage_events")
+
+    def close(self):
+        if self.h:
+            lib().nsm_ctx_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Weights:
+    def __init__(self, ctx: Context, params: np.ndarray):
+        p = np.ascontiguousarray(params, np.float32)
+        h = ctypes.c_void_p()
+        _check(lib().nsm_weights_create(ctx.h, _ptr(p), p.size, ctypes.byref(h)), "nsm_weights_create")
+        self.h = h
+
+    def load_device(self, dev_params, stream=None):
+        _check(lib().nsm_weights_load_device(self.h, _ptr(dev_params), int(dev_params.numel()), _stream(stream)),
+               "nsm_weights_load_device")
+
+    def close(self):
+        if self.h:
+            lib().nsm_weights_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def nsm_infer_kernel_names(precision: int):
+    n = lib().nsm_infer_kernel_count(precision)
+    return [lib().nsm_infer_kernel_name(precision, i).decode() for i in range(n)]
+
+
+def nsm_param_count() -> int:
+    return int(lib().nsm_param_count())
+
+
+def nsm_features(frame: nsm_frame, feat_out, texel_out=None, hard_out=None, blocker_out=None, stream=None):
+    _check(lib().nsm_features(ctypes.byref(frame), _ptr(feat_out), _ptr(texel_out), _ptr(hard_out),
+                              _ptr(blocker_out), _stream(stream)), "nsm_features")
+
+
+def nsm_infer_workspace_bytes(H: int, W: int, precision: int) -> int:
+    return int(lib().nsm_infer_workspace_bytes(H, W, precision))
+
+
+def nsm_infer(ctx: Context, frame: nsm_frame, weights: Weights, precision: int, workspace, vis_out, stream=None,
+              workspace_bytes=None):
+    nbytes = workspace_bytes if workspace_bytes is not None else (
+        0 if workspace is None else int(workspace.numel() * workspace.element_size()))
+    _check(lib().nsm_infer(ctx.h, ctypes.byref(frame), weights.h, precision, _ptr(workspace), nbytes,
+                           _ptr(vis_out), _stream(stream)), "nsm_infer")
+
+
+def nsm_infer_host_stage_bytes(H, W, Hs, Ws) -> int:
+    return int(lib().nsm_infer_host_stage_bytes(H, W, Hs, Ws))
+
+
+def nsm_infer_host(ctx: Context, host_frame: nsm_frame, weights: Weights, precision: int, dev_stage, workspace,
+                   vis_host: np.ndarray, stream=None):
+    _check(lib().nsm_infer_host(ctx.h, ctypes.byref(host_frame), weights.h, precision, _ptr(dev_stage),
+                                int(dev_stage.numel() * dev_stage.element_size()), _ptr(workspace),
+                                int(workspace.numel() * workspace.element_size()), _ptr(vis_host),
+                                _stream(stream)), "nsm_infer_host")

@@ -1,0 +1,371 @@
+// C ABI of the library (include/nsm.h): argument validation, weight upload,
+// workspace carving and dispatch to the kernels.
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/nsm.h"
+#include "nsm_internal.h"
+
+struct nsm_ctx {
+    int device;
+    int* d_err;  // device error word (bounded waits that gave up)
+    std::vector<cudaEvent_t> stage_events;  // profiling hook (caller-owned events)
+};
+
+struct nsm_weights {
+    int device;
+    float* d_params;  // canonical FP32 vector (nsm_param_count floats)
+};
+
+namespace nsm {
+
+static thread_local std::string g_last_error;
+
+static nsm_status fail(nsm_status s, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return s;
+}
+
+static nsm_status cuda_fail(cudaError_t e, const char* what) {
+    return fail(NSM_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+LayerOffsets layer_offsets() {
+    LayerOffsets o{};
+    size_t off = 0;
+    for (int l = 0; l < NUM_LAYERS; ++l) {
+        o.w[l] = off;
+        off += static_cast<size_t>(kLayers[l].cin) * kLayers[l].cout * kLayers[l].k * kLayers[l].k;
+        o.b[l] = off;
+        off += kLayers[l].cout;
+    }
+    o.total = off;
+    return o;
+}
+
+int num_sms() {
+    static int cached[64] = {0};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) return 148;
+    if (cached[dev] == 0) {
+        int n = 0;
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        cached[dev] = n > 0 ? n : 1;
+    }
+    return cached[dev];
+}
+
+static size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+size_t activations_bytes(int H, int W, size_t eb, Activations* carve, void* base) {
+    const size_t h2 = static_cast<size_t>(H / 2) * (W / 2), h4 = static_cast<size_t>(H / 4) * (W / 4);
+    const size_t sizes[5] = {h2 * 16 * eb, h2 * 32 * eb, h4 * 32 * eb, h4 * 32 * eb, h2 * 16 * eb};
+    size_t off = 0;
+    void* ptrs[5];
+    for (int i = 0; i < 5; ++i) {
+        ptrs[i] = base ? static_cast<char*>(base) + off : nullptr;
+        off += align_up(sizes[i], 256);
+    }
+    if (carve) { carve->e0 = ptrs[0]; carve->s1 = ptrs[1]; carve->p1 = ptrs[2]; carve->bo = ptrs[3]; carve->d1 = ptrs[4]; }
+    return off;
+}
+
+// ------------------------------------------------------------------ checks
+static nsm_status check_device() {
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return fail(NSM_ERR_DEVICE, "no CUDA device: %s", cudaGetErrorString(e));
+    int major = 0, minor = 0;
+    cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+    cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
+    if (major != 10 || minor != 3)
+        return fail(NSM_ERR_DEVICE, "device %d is sm_%d%d; this library is built for sm_103a only", dev, major, minor);
+    return NSM_OK;
+}
+
+static nsm_status check_dev_ptr(const void* p, const char* name, size_t align, bool nullable = false) {
+    if (!p) {
+        if (nullable) return NSM_OK;
+        return fail(NSM_ERR_INVALID_ARG, "%s is NULL", name);
+    }
+    cudaPointerAttributes at{};
+    cudaError_t e = cudaPointerGetAttributes(&at, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(NSM_ERR_INVALID_ARG, "%s: cannot query pointer (%s)", name, cudaGetErrorString(e));
+    }
+    if (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged)
+        return fail(NSM_ERR_INVALID_ARG, "%s is not device memory", name);
+    int dev = -1;
+    cudaGetDevice(&dev);
+    if (at.device != dev) return fail(NSM_ERR_INVALID_ARG, "%s lives on device %d, current device is %d", name, at.device, dev);
+    if (reinterpret_cast<uintptr_t>(p) % align)
+        return fail(NSM_ERR_ALIGNMENT, "%s must be %zu-byte aligned", name, align);
+    return NSM_OK;
+}
+
+static bool finite_all(const float* v, int n) {
+    for (int i = 0; i < n; ++i)
+        if (!(v[i] == v[i]) || v[i] == INFINITY || v[i] == -INFINITY) return false;
+    return true;
+}
+
+static nsm_status check_frame(const nsm_frame* f, bool need_mult4) {
+    if (!f) return fail(NSM_ERR_INVALID_ARG, "frame is NULL");
+    if (f->H < 0 || f->W < 0 || f->H > 16384 || f->W > 16384)
+        return fail(NSM_ERR_SHAPE, "view size %d x %d outside [0, 16384]", f->H, f->W);
+    if (need_mult4 && ((f->H % 4) || (f->W % 4)))
+        return fail(NSM_ERR_SHAPE, "view size %d x %d: H and W must be multiples of 4", f->H, f->W);
+    if (f->Hs < 1 || f->Ws < 1 || f->Hs > 16384 || f->Ws > 16384)
+        return fail(NSM_ERR_SHAPE, "shadow map %d x %d outside [1, 16384]", f->Hs, f->Ws);
+    const nsm_light& l = f->light;
+    if (!finite_all(l.pos, 3) || !finite_all(l.view_proj, 16) || !finite_all(f->camera.pos, 3) ||
+        !finite_all(&l.radius, 1) || !finite_all(&l.r_hat, 1) || !finite_all(&l.z_far, 1) ||
+        !finite_all(&l.bias, 1) || !finite_all(&l.tan_half_fov, 1))
+        return fail(NSM_ERR_INVALID_ARG, "light / camera parameters must be finite");
+    if (l.radius < 0.f || l.bias < 0.f || l.tan_half_fov <= 0.f)
+        return fail(NSM_ERR_INVALID_ARG, "light radius and bias must be >= 0, tan_half_fov > 0");
+    if (static_cast<size_t>(f->H) * f->W == 0) return NSM_OK;
+    nsm_status s;
+    if ((s = check_dev_ptr(f->pos4, "frame.pos4", 16)) != NSM_OK) return s;
+    if ((s = check_dev_ptr(f->nrm4, "frame.nrm4", 16)) != NSM_OK) return s;
+    if ((s = check_dev_ptr(f->sm, "frame.sm", 4)) != NSM_OK) return s;
+    return NSM_OK;
+}
+
+static GatherParams make_gather(const nsm_frame* f) {
+    GatherParams g{};
+    std::memcpy(g.M, f->light.view_proj, sizeof(g.M));
+    for (int k = 0; k < 3; ++k) { g.L[k] = f->light.pos[k]; g.C[k] = f->camera.pos[k]; }
+    g.r_hat = f->light.r_hat;
+    g.z_far = f->light.z_far;
+    g.beta = f->light.bias;
+    g.radius = f->light.radius;
+    g.tan_half_fov = f->light.tan_half_fov;
+    g.Ws = f->Ws; g.Hs = f->Hs;
+    g.Ws_f = static_cast<float>(f->Ws); g.Hs_f = static_cast<float>(f->Hs);
+    g.half_Ws = 0.5f * static_cast<float>(f->Ws);
+    g.H = f->H; g.W = f->W;
+    g.pos4 = reinterpret_cast<const float4*>(f->pos4);
+    g.nrm4 = reinterpret_cast<const float4*>(f->nrm4);
+    g.sm = f->sm;
+    return g;
+}
+
+}  // namespace nsm
+
+using namespace nsm;
+
+// ====================================================================== C ABI
+extern "C" {
+
+int nsm_abi_version(void) { return NSM_ABI_VERSION; }
+
+const char* nsm_last_error(void) { return g_last_error.c_str(); }
+
+nsm_status nsm_ctx_create(nsm_ctx** out) {
+    if (!out) return fail(NSM_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    nsm_status s = check_device();
+    if (s != NSM_OK) return s;
+    nsm_ctx* c = new nsm_ctx{};
+    cudaGetDevice(&c->device);
+    cudaError_t e = cudaMalloc(&c->d_err, sizeof(int) * 4);
+    if (e != cudaSuccess) { delete c; return cuda_fail(e, "cudaMalloc(error word)"); }
+    e = cudaMemset(c->d_err, 0, sizeof(int) * 4);
+    if (e != cudaSuccess) { cudaFree(c->d_err); delete c; return cuda_fail(e, "cudaMemset(error word)"); }
+    *out = c;
+    return NSM_OK;
+}
+
+void nsm_ctx_destroy(nsm_ctx* c) {
+    if (!c) return;
+    cudaFree(c->d_err);
+    delete c;
+}
+
+nsm_status nsm_ctx_check(nsm_ctx* c) {
+    if (!c) return fail(NSM_ERR_INVALID_ARG, "ctx is NULL");
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceSynchronize");
+    int h[4] = {0, 0, 0, 0};
+    e = cudaMemcpy(h, c->d_err, sizeof(h), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "read error word");
+    if (h[0] != 0) {
+        cudaMemset(c->d_err, 0, sizeof(h));
+        return fail(NSM_ERR_TIMEOUT, "a bounded device wait gave up (code %d, site %d)", h[0], h[1]);
+    }
+    return NSM_OK;
+}
+
+nsm_status nsm_ctx_set_stage_events(nsm_ctx* c, void* const* events, int n) {
+    if (!c) return fail(NSM_ERR_INVALID_ARG, "ctx is NULL");
+    if (n < 0 || (n > 0 && !events)) return fail(NSM_ERR_INVALID_ARG, "bad event list");
+    c->stage_events.clear();
+    for (int i = 0; i < n; ++i) {
+        if (!events[i]) return fail(NSM_ERR_INVALID_ARG, "event %d is NULL", i);
+        c->stage_events.push_back(static_cast<cudaEvent_t>(events[i]));
+    }
+    return NSM_OK;
+}
+
+int nsm_infer_kernel_count(nsm_precision precision) {
+    switch (precision) {
+        case NSM_FP32: return kInferKernelsFp32;
+        default: return 0;
+    }
+}
+
+const char* nsm_infer_kernel_name(nsm_precision precision, int i) {
+    if (i < 0 || i >= nsm_infer_kernel_count(precision)) return "";
+    switch (precision) {
+        case NSM_FP32: return kInferKernelNamesFp32[i];
+        default: return "";
+    }
+}
+
+size_t nsm_param_count(void) { return layer_offsets().total; }
+
+nsm_status nsm_weights_create(nsm_ctx* ctx, const float* host_params, size_t n, nsm_weights** out) {
+    if (!ctx || !host_params || !out) return fail(NSM_ERR_INVALID_ARG, "ctx, host_params and out must be non-NULL");
+    *out = nullptr;
+    const size_t want = layer_offsets().total;
+    if (n != want) return fail(NSM_ERR_SHAPE, "parameter vector has %zu floats, expected %zu", n, want);
+    if (!finite_all(host_params, static_cast<int>(n))) return fail(NSM_ERR_INVALID_ARG, "parameters must be finite");
+    nsm_weights* w = new nsm_weights{};
+    cudaGetDevice(&w->device);
+    cudaError_t e = cudaMalloc(&w->d_params, n * sizeof(float));
+    if (e != cudaSuccess) { delete w; return cuda_fail(e, "cudaMalloc(weights)"); }
+    e = cudaMemcpy(w->d_params, host_params, n * sizeof(float), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) { cudaFree(w->d_params); delete w; return cuda_fail(e, "upload weights"); }
+    *out = w;
+    return NSM_OK;
+}
+
+nsm_status nsm_weights_load_device(nsm_weights* w, const float* dev_params, size_t n, void* stream) {
+    if (!w) return fail(NSM_ERR_INVALID_ARG, "weights is NULL");
+    if (n != layer_offsets().total) return fail(NSM_ERR_SHAPE, "parameter vector has %zu floats, expected %zu", n, layer_offsets().total);
+    nsm_status s = check_dev_ptr(dev_params, "dev_params", 4);
+    if (s != NSM_OK) return s;
+    cudaError_t e = cudaMemcpyAsync(w->d_params, dev_params, n * sizeof(float), cudaMemcpyDeviceToDevice,
+                                    static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "copy weights");
+    return NSM_OK;
+}
+
+void nsm_weights_destroy(nsm_weights* w) {
+    if (!w) return;
+    cudaFree(w->d_params);
+    delete w;
+}
+
+nsm_status nsm_features(const nsm_frame* frame, float* feat_out, int32_t* texel_out, uint32_t* hard_out,
+                        float* blocker_out, void* stream) {
+    nsm_status s = check_frame(frame, false);
+    if (s != NSM_OK) return s;
+    if (static_cast<size_t>(frame->H) * frame->W == 0) return NSM_OK;
+    if ((s = check_device()) != NSM_OK) return s;
+    if ((s = check_dev_ptr(feat_out, "feat_out", 4)) != NSM_OK) return s;
+    if ((s = check_dev_ptr(texel_out, "texel_out", 4, true)) != NSM_OK) return s;
+    if ((s = check_dev_ptr(hard_out, "hard_out", 4, true)) != NSM_OK) return s;
+    if ((s = check_dev_ptr(blocker_out, "blocker_out", 4, true)) != NSM_OK) return s;
+    GatherParams g = make_gather(frame);
+    cudaError_t e = launch_features(g, feat_out, texel_out, hard_out, blocker_out, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "features kernel launch");
+    return NSM_OK;
+}
+
+size_t nsm_infer_workspace_bytes(int H, int W, nsm_precision precision) {
+    if (H <= 0 || W <= 0) return 0;
+    const size_t eb = (precision == NSM_FP32) ? 4 : 2;
+    return activations_bytes(H, W, eb, nullptr, nullptr);
+}
+
+nsm_status nsm_infer(nsm_ctx* ctx, const nsm_frame* frame, const nsm_weights* w, nsm_precision precision,
+                     void* workspace, size_t workspace_bytes, float* vis_out, void* stream) {
+    if (!ctx) return fail(NSM_ERR_INVALID_ARG, "ctx is NULL");
+    if (!w) return fail(NSM_ERR_INVALID_ARG, "weights is NULL");
+    if (precision != NSM_FP32 && precision != NSM_BF16 && precision != NSM_FP8)
+        return fail(NSM_ERR_INVALID_ARG, "unknown precision %d", static_cast<int>(precision));
+    nsm_status s = check_frame(frame, true);
+    if (s != NSM_OK) return s;
+    if (static_cast<size_t>(frame->H) * frame->W == 0) return NSM_OK;
+    int dev = -1;
+    cudaGetDevice(&dev);
+    if (dev != ctx->device || dev != w->device)
+        return fail(NSM_ERR_DEVICE, "context / weights were created on another device");
+    if ((s = check_dev_ptr(vis_out, "vis_out", 4)) != NSM_OK) return s;
+    const size_t need = nsm_infer_workspace_bytes(frame->H, frame->W, precision);
+    if (!workspace || workspace_bytes < need)
+        return fail(NSM_ERR_WORKSPACE, "workspace of %zu bytes given, %zu needed", workspace_bytes, need);
+    if ((s = check_dev_ptr(workspace, "workspace", 256)) != NSM_OK) return s;
+    if (precision != NSM_FP32) return fail(NSM_ERR_UNSUPPORTED, "precision %d not built yet", static_cast<int>(precision));
+    Activations act{};
+    activations_bytes(frame->H, frame->W, 4, &act, workspace);
+    GatherParams g = make_gather(frame);
+    StageEvents se;
+    const int k = nsm_infer_kernel_count(precision);
+    if (!ctx->stage_events.empty()) {
+        if (static_cast<int>(ctx->stage_events.size()) < k + 1)
+            return fail(NSM_ERR_INVALID_ARG, "%zu stage events set, %d needed", ctx->stage_events.size(), k + 1);
+        se.ev = ctx->stage_events.data();
+        se.n = static_cast<int>(ctx->stage_events.size());
+        se.stream = static_cast<cudaStream_t>(stream);
+    }
+    cudaError_t e = launch_infer_fp32(g, w->d_params, act, vis_out, static_cast<cudaStream_t>(stream), se);
+    if (e != cudaSuccess) return cuda_fail(e, "inference kernel launch");
+    return NSM_OK;
+}
+
+size_t nsm_infer_host_stage_bytes(int H, int W, int Hs, int Ws) {
+    if (H <= 0 || W <= 0 || Hs <= 0 || Ws <= 0) return 0;
+    const size_t npx = static_cast<size_t>(H) * W;
+    return align_up(npx * 16, 256) * 2 + align_up(static_cast<size_t>(Hs) * Ws * 4, 256) + align_up(npx * 4, 256);
+}
+
+nsm_status nsm_infer_host(nsm_ctx* ctx, const nsm_frame* hf, const nsm_weights* w, nsm_precision precision,
+                          void* dev_stage, size_t stage_bytes, void* workspace, size_t workspace_bytes,
+                          float* vis_host, void* stream) {
+    if (!hf) return fail(NSM_ERR_INVALID_ARG, "frame is NULL");
+    if (!hf->pos4 || !hf->nrm4 || !hf->sm || !vis_host)
+        return fail(NSM_ERR_INVALID_ARG, "host pointers must be non-NULL");
+    if (hf->H < 0 || hf->W < 0) return fail(NSM_ERR_SHAPE, "negative view size");
+    const size_t npx = static_cast<size_t>(hf->H) * hf->W;
+    if (npx == 0) return NSM_OK;
+    const size_t need = nsm_infer_host_stage_bytes(hf->H, hf->W, hf->Hs, hf->Ws);
+    if (!dev_stage || stage_bytes < need)
+        return fail(NSM_ERR_WORKSPACE, "staging buffer of %zu bytes given, %zu needed", stage_bytes, need);
+    nsm_status s = check_dev_ptr(dev_stage, "dev_stage", 256);
+    if (s != NSM_OK) return s;
+    char* base = static_cast<char*>(dev_stage);
+    float* d_pos = reinterpret_cast<float*>(base);
+    float* d_nrm = reinterpret_cast<float*>(base + align_up(npx * 16, 256));
+    float* d_sm = reinterpret_cast<float*>(base + 2 * align_up(npx * 16, 256));
+    float* d_vis = reinterpret_cast<float*>(base + 2 * align_up(npx * 16, 256) +
+                                            align_up(static_cast<size_t>(hf->Hs) * hf->Ws * 4, 256));
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e;
+    if ((e = cudaMemcpyAsync(d_pos, hf->pos4, npx * 16, cudaMemcpyHostToDevice, st)) != cudaSuccess) return cuda_fail(e, "H2D pos4");
+    if ((e = cudaMemcpyAsync(d_nrm, hf->nrm4, npx * 16, cudaMemcpyHostToDevice, st)) != cudaSuccess) return cuda_fail(e, "H2D nrm4");
+    if ((e = cudaMemcpyAsync(d_sm, hf->sm, static_cast<size_t>(hf->Hs) * hf->Ws * 4, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+        return cuda_fail(e, "H2D shadow map");
+    nsm_frame df = *hf;
+    df.pos4 = d_pos; df.nrm4 = d_nrm; df.sm = d_sm;
+    s = nsm_infer(ctx, &df, w, precision, workspace, workspace_bytes, d_vis, stream);
+    if (s != NSM_OK) return s;
+    if ((e = cudaMemcpyAsync(vis_host, d_vis, npx * 4, cudaMemcpyDeviceToHost, st)) != cudaSuccess) return cuda_fail(e, "D2H visibility");
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e, "stream synchronize");
+    return NSM_OK;
+}
+
+}  // extern "C"

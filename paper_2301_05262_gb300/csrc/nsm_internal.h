@@ -1,0 +1,54 @@
+// Internal (host-side) declarations shared by the library's translation units.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "nsm_common.cuh"
+
+namespace nsm {
+
+// Canonical layer table of the 3-level network (Sec. 3.5): offsets of each
+// layer's OIHW weights and bias in the canonical parameter vector.
+enum Layer { ENC0_3, ENC0_1, ENC1_3, ENC1_1, BOTT_3, BOTT_1, DEC1_3, DEC1_1, DEC0_3, DEC0_1, HEAD, NUM_LAYERS };
+
+struct LayerShape { int cin, cout, k; };
+constexpr LayerShape kLayers[NUM_LAYERS] = {
+    {4, 16, 3}, {16, 16, 1}, {16, 32, 3}, {32, 32, 1}, {32, 64, 3}, {64, 32, 1},
+    {32, 32, 3}, {32, 16, 1}, {16, 16, 3}, {16, 16, 1}, {16, 1, 1}};
+
+struct LayerOffsets { size_t w[NUM_LAYERS]; size_t b[NUM_LAYERS]; size_t total; };
+LayerOffsets layer_offsets();
+
+int num_sms();
+
+// Activation buffers of one inference, carved out of the caller's workspace.
+struct Activations {
+    void* e0;   // [H/2][W/2][16]  pooled level-0 encoder output
+    void* s1;   // [H/2][W/2][32]  level-1 encoder output (decoder skip)
+    void* p1;   // [H/4][W/4][32]  pooled level-1 encoder output
+    void* bo;   // [H/4][W/4][32]  bottleneck output
+    void* d1;   // [H/2][W/2][16]  level-1 decoder output
+};
+size_t activations_bytes(int H, int W, size_t elem_bytes, Activations* carve, void* base);
+
+// Optional per-kernel event recording (profiling hook of nsm_ctx).
+struct StageEvents {
+    cudaEvent_t* ev = nullptr;
+    int n = 0;
+    cudaStream_t stream = nullptr;
+    inline void rec(int i) const {
+        if (ev && i < n) cudaEventRecord(ev[i], stream);
+    }
+};
+
+cudaError_t launch_features(const GatherParams& g, float* feat, int32_t* texel_out, uint32_t* hard_out,
+                            float* blocker_out, cudaStream_t stream);
+
+constexpr int kInferKernelsFp32 = 5;
+extern const char* const kInferKernelNamesFp32[kInferKernelsFp32];
+cudaError_t launch_infer_fp32(const GatherParams& g, const float* params, const Activations& act,
+                              float* vis, cudaStream_t stream, const StageEvents& se);
+
+}  // namespace nsm

@@ -1,0 +1,51 @@
+"""Shared helpers for the GPU tests: move a seeded scenegen frame to the
+device and run the library's calls through the Python binding."""
+import numpy as np
+import torch
+
+import paper_2301_05262_gb300 as nsm
+
+
+def light_desc(f):
+    return nsm.LightDesc(pos=tuple(float(v) for v in f.light_pos), radius=f.light_radius, r_hat=f.r_hat,
+                         view_proj=f.view_proj, z_far=f.z_far, bias=f.bias, tan_half_fov=f.tan_half_fov)
+
+
+class DeviceFrame:
+    """Device copies of a frame's buffers plus the nsm_frame struct."""
+
+    def __init__(self, f, device="cuda"):
+        self.f = f
+        self.pos4 = torch.from_numpy(f.pos4).to(device)
+        self.nrm4 = torch.from_numpy(f.nrm4).to(device)
+        self.sm = torch.from_numpy(f.sm).to(device)
+        self.frame = nsm.make_frame(self.pos4, self.nrm4, self.sm, light_desc(f), f.cam_pos)
+
+
+def run_features(df, blocker=False):
+    f = df.f
+    H, W = f.H, f.W
+    feat = torch.empty((4, H, W), dtype=torch.float32, device="cuda")
+    tex = torch.empty((H, W), dtype=torch.int32, device="cuda")
+    hard = torch.empty(((H * W + 31) // 32,), dtype=torch.int32, device="cuda")
+    blk = torch.empty((3, H, W), dtype=torch.float32, device="cuda") if blocker else None
+    nsm.nsm_features(df.frame, feat, tex, hard, blk)
+    torch.cuda.synchronize()
+    return feat, tex, hard, blk
+
+
+def unpack_hard_bits(words: np.ndarray, n: int) -> np.ndarray:
+    w = words.astype(np.uint32)
+    bits = (w[:, None] >> np.arange(32, dtype=np.uint32)[None, :]) & 1
+    return bits.reshape(-1)[:n].astype(bool)
+
+
+def run_infer(ctx, weights, df, precision, vis=None):
+    f = df.f
+    nbytes = nsm.nsm_infer_workspace_bytes(f.H, f.W, precision)
+    ws = torch.empty((max(nbytes, 1),), dtype=torch.uint8, device="cuda")
+    if vis is None:
+        vis = torch.empty((f.H, f.W), dtype=torch.float32, device="cuda")
+    nsm.nsm_infer(ctx, df.frame, weights, precision, ws, vis)
+    torch.cuda.synchronize()
+    return vis

@@ -1,0 +1,62 @@
+"""Host-only checks of the C-ABI library: it builds, loads, exports every
+symbol include/nsm.h declares, and its host-side sizes and validation paths
+behave as documented (no GPU work is issued)."""
+import ctypes
+
+import numpy as np
+import pytest
+
+import paper_2301_05262_gb300 as nsm
+from paper_2301_05262_gb300 import build as nsm_build
+from oracle import network as N
+
+
+@pytest.fixture(scope="module")
+def lib():
+    nsm_build.build()
+    return nsm.lib()
+
+
+def test_exports_every_declared_symbol(lib):
+    declared = nsm.declared_symbols()
+    assert "nsm_features" in declared and "nsm_infer" in declared
+    missing = [s for s in declared if not hasattr(lib, s)]
+    assert not missing, missing
+
+
+def test_abi_version_and_param_count(lib):
+    assert lib.nsm_abi_version() == 1
+    biases = sum(co for (_, _, co, _) in N.layer_table(3))
+    assert nsm.nsm_param_count() == N.param_count(3) + biases == 39521
+    assert [(c, o, k) for (_, c, o, k) in nsm.LAYERS] == [(c, o, k) for (_, c, o, k) in N.layer_table(3)]
+
+
+def test_workspace_bytes(lib):
+    for prec, eb in ((nsm.NSM_FP32, 4), (nsm.NSM_BF16, 2)):
+        H, W = 1080, 1920
+        n = nsm.nsm_infer_workspace_bytes(H, W, prec)
+        h2, h4 = (H // 2) * (W // 2), (H // 4) * (W // 4)
+        assert n >= eb * (h2 * (16 + 32 + 16) + h4 * (32 + 32))
+        assert n < eb * (h2 * (16 + 32 + 16) + h4 * (32 + 32)) + 5 * 256
+    assert nsm.nsm_infer_workspace_bytes(0, 64, nsm.NSM_FP32) == 0
+
+
+def test_host_validation_errors(lib):
+    # NULL frame / NULL context are rejected before any CUDA call
+    assert lib.nsm_features(None, None, None, None, None, None) == 1
+    assert b"frame" in lib.nsm_last_error()
+    assert lib.nsm_infer(None, None, None, 0, None, 0, None, None) == 1
+    assert b"ctx" in lib.nsm_last_error()
+    out = ctypes.c_void_p()
+    assert lib.nsm_weights_create(None, None, 0, ctypes.byref(out)) == 1
+    # host-frame entry point: missing buffers
+    fr = nsm.nsm_frame(H=4, W=4)
+    assert lib.nsm_infer_host(None, ctypes.byref(fr), None, 0, None, 0, None, 0, None, None) == 1
+    assert nsm.nsm_infer_host_stage_bytes(4, 4, 8, 8) >= 4 * 4 * 32 + 8 * 8 * 4 + 4 * 4 * 4
+
+
+def test_binding_fails_loudly_without_library(tmp_path, monkeypatch):
+    monkeypatch.setattr(nsm, "LIB_PATH", str(tmp_path / "missing.so"))
+    monkeypatch.setattr(nsm, "_lib", None)
+    with pytest.raises(ImportError):
+        nsm.lib()

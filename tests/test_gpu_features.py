@@ -1,0 +1,91 @@
+"""GPU parity of the feature gather (nsm_features) against the oracle:
+texel indices and hard bits bit-exact, features within FP32 rounding,
+blocker search exact (window minima / maxima are texel values)."""
+import numpy as np
+import pytest
+
+import scenegen
+from oracle import gather as G
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+from gpu_helpers import DeviceFrame, run_features, unpack_hard_bits  # noqa: E402
+
+
+def _check_frame(f, blocker=False, sample=None):
+    df = DeviceFrame(f)
+    feat, tex, hard, blk = run_features(df, blocker=blocker)
+    feat = feat.cpu().numpy()
+    tex = tex.cpu().numpy()
+    hard = unpack_hard_bits(hard.cpu().numpy().view(np.uint32), f.H * f.W).reshape(f.H, f.W)
+    ofeat, otex, ohard = G.features(f.pos4, f.nrm4, f.sm, f.view_proj, f.light_pos, f.cam_pos,
+                                    f.r_hat, f.z_far, f.bias)
+    # bit-exact: texel choice and hard depth test
+    np.testing.assert_array_equal(tex, otex.astype(np.int32))
+    np.testing.assert_array_equal(hard, ohard)
+    # features: FP32 evaluation vs FP64 from the same inputs
+    err = np.abs(feat - ofeat)
+    scale = np.maximum(1.0, np.abs(ofeat))
+    assert (err / scale).max() < 2e-6, (err / scale).max()
+    if blocker:
+        blk = blk.cpu().numpy()
+        idx = sample if sample is not None else np.s_[:, :]
+        sub = f.pos4[idx]
+        zmin, zmax, found = G.blocker_search(sub, f.sm, f.view_proj, f.light_pos, f.light_radius,
+                                             f.tan_half_fov, f.z_far, f.bias)
+        np.testing.assert_array_equal(blk[0][idx], zmin)
+        np.testing.assert_array_equal(blk[1][idx], zmax)
+        zf = G.emitter_distance_fp32(sub[..., :3], f.light_pos)
+        xa, xb = G.penumbra_width(zf, np.where(found, zmin, 1.0), np.where(found, zmax, 1.0), f.light_radius)
+        width = np.where(found, xa + xb, 0.0)
+        np.testing.assert_allclose(blk[2][idx], width, rtol=2e-4, atol=2e-5)
+        assert found.mean() > 0.0
+    return tex, hard
+
+
+def test_features_config1_256():
+    f = scenegen.hard_frame(256, 256, 512, 512, 8, 1)
+    tex, hard = _check_frame(f)
+    assert (tex >= 0).mean() > 0.5 and (~hard).sum() > 100
+
+
+def test_features_ragged_sizes_and_tail_word():
+    # H*W not a multiple of 32 (last hard-bit word partly used), odd sizes
+    f = scenegen.soft_frame(37, 53, 333, 129, 8, 4)
+    _check_frame(f, blocker=True)
+
+
+def test_features_soft_blocker_search():
+    f = scenegen.soft_frame(64, 96, 512, 512, 16, 21)
+    _check_frame(f, blocker=True)
+
+
+def test_features_1080p_full_size():
+    f = scenegen.hard_frame(1080, 1920, 2048, 2048, 64, 11)
+    _check_frame(f)
+
+
+def test_features_1080p_blocker_sampled_rows():
+    f = scenegen.soft_frame(1080, 1920, 2048, 2048, 64, 21)
+    rows = np.s_[500:504, :]
+    _check_frame(f, blocker=True, sample=rows)
+
+
+def test_features_empty_frame():
+    import paper_2301_05262_gb300 as nsm
+    f = scenegen.hard_frame(4, 4, 8, 8, 2, 1)
+    df = DeviceFrame(f)
+    df.frame.H = 0
+    feat = torch.empty((4, 1), device="cuda")
+    nsm.nsm_features(df.frame, feat)  # nothing to do, no error
+
+
+def test_features_rejects_host_pointer():
+    import paper_2301_05262_gb300 as nsm
+    f = scenegen.hard_frame(8, 8, 8, 8, 2, 1)
+    fr = nsm.make_frame(f.pos4, f.nrm4, f.sm, __import__("gpu_helpers").light_desc(f), f.cam_pos)
+    feat = torch.empty((4, 8, 8), device="cuda")
+    with pytest.raises(nsm.NSMError) as ei:
+        nsm.nsm_features(fr, feat)
+    assert ei.value.status == 1
