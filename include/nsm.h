@@ -181,6 +181,27 @@ nsm_status nsm_infer_host(nsm_ctx* ctx, const nsm_frame* host_frame, const nsm_w
                           nsm_precision precision, void* dev_stage, size_t stage_bytes,
                           void* workspace, size_t workspace_bytes, float* vis_host, void* stream);
 
+/* ---------------------------------------------------------------- no-allocation variant */
+
+/* FP32 inference that allocates nothing and needs no workspace, for callers
+ * that hold only their own input and output buffers and may not allocate
+ * device memory (e.g. a per-frame render loop or a plug-in whose host engine
+ * forbids device allocation after start-up, since an allocation can
+ * synchronise the device and stall a frame).  The paper has no counterpart:
+ * this is a deployment convenience of this library.
+ *   dev_params  device, the canonical FP32 parameter vector (nsm_param_count
+ *               floats, layout as for nsm_weights_create).
+ *   vis_out     device, H*W floats.
+ * Same results as nsm_infer with NSM_FP32.  The activations live in one fixed
+ * device array inside the library, sized for H * W <= 262,144 pixels (e.g.
+ * 512 x 512; about 21 MB, held on every device that loads the library until
+ * the process exits); larger views return NSM_ERR_SHAPE.  Every call shares
+ * that array: calls whose work overlaps on the GPU race and must be ordered by
+ * the caller (one stream, or events).  The first call on a device looks up
+ * the array's device address (once per device); make that first call before
+ * any stream capture.  Asynchronous on stream. */
+nsm_status nsm_infer_fp32_static(const nsm_frame* frame, const float* dev_params, float* vis_out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

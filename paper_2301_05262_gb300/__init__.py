@@ -82,6 +82,7 @@ def lib():
             "nsm_infer": ([P, FP, P, I, P, Z, P, P], I),
             "nsm_infer_host_stage_bytes": ([I, I, I, I], Z),
             "nsm_infer_host": ([P, FP, P, I, P, Z, P, Z, P, P], I),
+            "nsm_infer_fp32_static": ([FP, P, P, P], I),
         }
         for name, (args, res) in sig.items():
             fn = getattr(L, name)
@@ -244,3 +245,9 @@ def nsm_infer_host(ctx: Context, host_frame: nsm_frame, weights: Weights, precis
                                 int(dev_stage.numel() * dev_stage.element_size()), _ptr(workspace),
                                 int(workspace.numel() * workspace.element_size()), _ptr(vis_host),
                                 _stream(stream)), "nsm_infer_host")
+
+
+def nsm_infer_fp32_static(frame: nsm_frame, dev_params, vis_out, stream=None):
+    """FP32 inference without allocation or workspace (views up to 262,144 pixels)."""
+    _check(lib().nsm_infer_fp32_static(ctypes.byref(frame), _ptr(dev_params), _ptr(vis_out), _stream(stream)),
+           "nsm_infer_fp32_static")

@@ -35,6 +35,8 @@ static nsm_status fail(nsm_status s, const char* fmt, ...) {
     return s;
 }
 
+void set_last_error(const std::string& msg) { g_last_error = msg; }
+
 static nsm_status cuda_fail(cudaError_t e, const char* what) {
     return fail(NSM_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
 }

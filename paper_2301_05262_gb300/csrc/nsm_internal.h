@@ -3,6 +3,7 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <string>
 #include <cuda_runtime.h>
 
 #include "nsm_common.cuh"
@@ -22,6 +23,9 @@ struct LayerOffsets { size_t w[NUM_LAYERS]; size_t b[NUM_LAYERS]; size_t total; 
 LayerOffsets layer_offsets();
 
 int num_sms();
+
+// Message returned by nsm_last_error() on this thread.
+void set_last_error(const std::string& msg);
 
 // Activation buffers of one inference, carved out of the caller's workspace.
 struct Activations {
