@@ -372,7 +372,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precisions", default="fp32", help="comma list; the first is the headline form")
+    ap.add_argument("--precisions", default="bf16,fp32", help="comma list; the first is the headline form")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-error", action="store_true")
     args = ap.parse_args()

@@ -276,6 +276,62 @@ def backward(gvis: np.ndarray, theta: np.ndarray, t: dict, levels: int = 3):
     return pack(G, levels), gh
 
 
+# ------------------------------------------------------------------ reduced-precision storage
+
+
+def round_bf16(x):
+    """Round to the nearest bfloat16 (ties to even), returned as float64:
+    bfloat16 keeps the sign, the 8 exponent bits and the top 7 mantissa bits
+    of an IEEE binary32 value.  (Inputs are first rounded to binary32.)"""
+    a = np.ascontiguousarray(np.asarray(x, np.float32))
+    u = a.view(np.uint32).astype(np.uint64)
+    u = u + 0x7FFF + ((u >> 16) & 1)
+    u = (u & 0xFFFF0000).astype(np.uint32)
+    return u.view(np.float32).astype(np.float64)
+
+
+def round_bf16_pair(x):
+    """hi + lo with hi = bf16(x) and lo = bf16(x - hi): x to about 16 bits."""
+    x32 = np.asarray(x, np.float32).astype(np.float64)
+    hi = round_bf16(x32)
+    lo = round_bf16((x32 - hi).astype(np.float32))
+    return hi + lo
+
+
+def forward_rounded(feat, theta, rnd, rnd_in=None, rnd_w=None, rnd_mid=None, levels: int = 3):
+    """`forward` with values rounded wherever a reduced-precision form stores
+    them: every convolution weight by `rnd_w` (not biases or the head), the
+    3x3 output that feeds each 1x1 by `rnd_mid`, and by `rnd` each level's
+    output (after pooling where the level pools; the level-1 skip separately;
+    the up-sampled (+ skip) decoder inputs).  The input features are rounded
+    by `rnd_in`.  `rnd_w` / `rnd_mid` default to `rnd`.  All arithmetic between
+    those points is exact (FP64)."""
+    rnd_w = rnd if rnd_w is None else rnd_w
+    rnd_mid = rnd if rnd_mid is None else rnd_mid
+    P = unpack(theta, levels)
+    Wr = {k: ((rnd_w(W) if k != "head" else W), b) for k, (W, b) in P.items()}
+    h = np.asarray(feat, np.float64) if rnd_in is None else rnd_in(feat)
+    skips = {}
+
+    def pair(x, l3, l1):
+        a = rnd_mid(relu(conv2d(x, *Wr[l3])))
+        return relu(conv2d(a, *Wr[l1]))
+
+    for l in range(levels - 1):
+        h1 = pair(h, f"enc{l}_3x3", f"enc{l}_1x1")
+        if l >= 1:
+            skips[l] = rnd(h1)
+        h = rnd(avgpool2(h1))
+    h = rnd(pair(h, "bott_3x3", "bott_1x1"))
+    for l in range(levels - 2, -1, -1):
+        u = upsample2(h)
+        x = rnd(u + skips[l]) if l >= 1 else rnd(u)
+        h = pair(x, f"dec{l}_3x3", f"dec{l}_1x1")
+        if l >= 1:
+            h = rnd(h)
+    return sigmoid(conv2d(h, *Wr["head"])[0])
+
+
 # ------------------------------------------------------------------ loss (Eq. 2)
 
 

@@ -1,0 +1,569 @@
+// BF16 tensor-core form of the compact encoder/decoder (Sec. 3.5) on
+// Blackwell tcgen05: every convolution is an implicit GEMM
+//   D[pixels x C_out] = A[pixels x K] * B[C_out x K]^T,  K = 9 C_in (3x3) or C_mid (1x1),
+// issued as 128 x N x 16 MMAs by one thread, accumulated in FP32 in tensor
+// memory (TMEM).  One fused kernel per level runs "3x3 conv + ReLU ->
+// 1x1 conv + ReLU" with the same prologues / epilogues as the FP32 form:
+//   prologue  GATHER (features from G-buffer + shadow map, the gather fused
+//             into the first level), PLAIN, UP_SKIP, UP;
+//   epilogue  POOL, SKIP_POOL, STORE, HEAD (1x1 16 -> 1 + sigmoid).
+//
+// Tile: R rows x 128 pixels of the level; MMA row block = one 128-pixel row
+// segment.  The input tile with its 1-pixel halo is staged in shared memory
+// as 16-byte chunks of 8 channels, [channel group][staged row][staged pixel],
+// which *is* the tensor core's no-swizzle K-major operand layout: the A
+// operand of tap (ky, kx) and channel pair (2g, 2g+1) is the same buffer
+// started (ky, kx) chunks further on, so the im2col matrix is never built.
+// The 3x3 result goes TMEM -> registers (bias, ReLU, BF16) -> shared memory,
+// where it is the A operand of the 1x1 MMA (written back into the same TMEM
+// columns).
+//
+// First level: the four FP32 features are split into BF16 hi + lo parts
+// (f = hi + lo to ~2^-16 relative), giving 8 "channels" per pixel; K steps
+// pair two taps (two 16-byte chunks), so the 3x3 4 -> 16 convolution is five
+// K = 16 steps with a zero-weight pad.  This keeps the depth-test features
+// (z / z_f near 1, z - z_f near 0) at near-FP32 resolution on BF16 hardware.
+#include "nsm_internal.h"
+#include "tc_common.cuh"
+
+namespace nsm {
+
+using namespace tc;
+
+enum TcPro { TPRO_GATHER = 0, TPRO_PLAIN = 1, TPRO_UP_SKIP = 2, TPRO_UP = 3 };
+enum TcEpi { TEPI_POOL = 0, TEPI_SKIP_POOL = 1, TEPI_STORE = 2, TEPI_HEAD = 3 };
+
+struct TcArgs {
+    GatherParams g;
+    int H, W;                    // this level's resolution
+    const uint16_t* in;          // BF16 NHWC: PLAIN [H][W][CIN]; UP* [H/2][W/2][CIN]
+    const uint16_t* skip;        // UP_SKIP: [H][W][CIN]
+    const uint4* b3img;          // packed 3x3 weights (shared-memory image)
+    const uint4* b1img;          // packed 1x1 weights
+    const float* bias3;
+    const float* bias1;
+    const float* head;           // head weights [COUT] then bias
+    uint16_t* out;               // POOL: [H/2][W/2][COUT]; STORE: [H][W][COUT]; SKIP_POOL: pooled
+    uint16_t* out_skip;          // SKIP_POOL: [H][W][COUT]
+    float* vis;                  // HEAD: [H][W]
+    int* err;                    // device error word
+};
+
+constexpr int kTileM = 128;      // pixels per MMA row block
+constexpr int kSW = 136;         // staged pixels per row (128 + halo + pad)
+constexpr uint64_t kWaitNs = 2000000000ull;  // 2 s bound on every mbarrier wait
+
+template <int CIN, int CMID, int COUT, int R, int PRO>
+struct TcCfg {
+    static constexpr bool SPLIT = (PRO == TPRO_GATHER);
+    static constexpr int CG_IN = SPLIT ? 1 : CIN / 8;
+    static constexpr int KSTEPS3 = SPLIT ? 5 : 9 * (CIN / 16);
+    static constexpr int A0_CHUNKS = CG_IN * (R + 2) * kSW;
+    // 3x3 -> 1x1 intermediate as BF16 hi + lo parts: [row][part][channel group][pixel]
+    static constexpr int A1_CHUNKS = R * 2 * (CMID / 8) * kTileM;
+    // weights as BF16 hi + lo images (hi image first, then lo image)
+    static constexpr int B3_IMG = KSTEPS3 * 2 * CMID;
+    static constexpr int B1_IMG = (CMID / 8) * COUT;
+    static constexpr int B3_CHUNKS = 2 * B3_IMG;
+    static constexpr int B1_CHUNKS = 2 * B1_IMG;
+    static constexpr int OFF_A0 = 0;
+    static constexpr int OFF_A1 = OFF_A0 + A0_CHUNKS * 16;
+    static constexpr int OFF_B3 = OFF_A1 + A1_CHUNKS * 16;
+    static constexpr int OFF_B1 = OFF_B3 + B3_CHUNKS * 16;
+    static constexpr int OFF_BIAS3 = OFF_B1 + B1_CHUNKS * 16;
+    static constexpr int OFF_BIAS1 = OFF_BIAS3 + CMID * 4;
+    static constexpr int OFF_HEAD = OFF_BIAS1 + COUT * 4;
+    static constexpr int OFF_BAR = ((OFF_HEAD + (COUT + 1) * 4) + 15) / 16 * 16;
+    static constexpr int BYTES_USED = OFF_BAR + 32;
+    static constexpr int TMEM_COLS = R * CMID;
+    // enough shared memory per CTA that the CTAs resident on one SM can never
+    // ask for more than its 512 TMEM columns (228 KB of shared memory per SM)
+    static constexpr int TMEM_CAP = 512 / TMEM_COLS;
+    static constexpr int BYTES_MIN = (236 * 1024) / (TMEM_CAP + 1);
+    static constexpr int BYTES = BYTES_USED < BYTES_MIN ? BYTES_MIN : BYTES_USED;
+    static_assert(TMEM_COLS == 32 || TMEM_COLS == 64 || TMEM_COLS == 128 || TMEM_COLS == 256, "TMEM columns");
+    static_assert(CMID % 16 == 0 && COUT % 16 == 0 && COUT <= CMID, "channel shapes");
+};
+
+__device__ __forceinline__ void st_shared_v4(uint32_t addr, uint4 v) {
+    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" :: "r"(addr), "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w)
+                 : "memory");
+}
+__device__ __forceinline__ uint4 ld_shared_v4(uint32_t addr) {
+    uint4 v;
+    asm volatile("ld.shared.v4.b32 {%0, %1, %2, %3}, [%4];" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "r"(addr));
+    return v;
+}
+__device__ __forceinline__ uint4 ldg_v4(const void* p) {
+    return __ldg(reinterpret_cast<const uint4*>(p));
+}
+
+// 8 BF16 values of a chunk -> FP32
+__device__ __forceinline__ void chunk_to_f32(uint4 c, float (&f)[8]) {
+    float2 a = unpack_bf16x2(c.x), b = unpack_bf16x2(c.y), d = unpack_bf16x2(c.z), e = unpack_bf16x2(c.w);
+    f[0] = a.x; f[1] = a.y; f[2] = b.x; f[3] = b.y; f[4] = d.x; f[5] = d.y; f[6] = e.x; f[7] = e.y;
+}
+__device__ __forceinline__ uint4 f32_to_chunk(const float* f) {
+    return make_uint4(pack_bf16x2(f[0], f[1]), pack_bf16x2(f[2], f[3]), pack_bf16x2(f[4], f[5]),
+                      pack_bf16x2(f[6], f[7]));
+}
+
+template <int CIN, int CMID, int COUT, int R, int PRO, int EPI>
+__global__ void __launch_bounds__(128, 1) level_tc_kernel(TcArgs a) {
+    using C = TcCfg<CIN, CMID, COUT, R, PRO>;
+    extern __shared__ __align__(1024) unsigned char smem[];
+    const uint32_t sbase = smem_u32(smem);
+    const uint32_t sA0 = sbase + C::OFF_A0, sA1 = sbase + C::OFF_A1;
+    const uint32_t sB3 = sbase + C::OFF_B3, sB1 = sbase + C::OFF_B1;
+    float* bias3_s = reinterpret_cast<float*>(smem + C::OFF_BIAS3);
+    float* bias1_s = reinterpret_cast<float*>(smem + C::OFF_BIAS1);
+    float* head_s = reinterpret_cast<float*>(smem + C::OFF_HEAD);
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + C::OFF_BAR);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + C::OFF_BAR + 8);
+    int* s_abort = reinterpret_cast<int*>(smem + C::OFF_BAR + 12);
+
+    const int tid = threadIdx.x;
+    const int warp = tid >> 5;
+
+    // ---- one-time set-up: weights, barrier, TMEM
+    for (int i = tid; i < C::B3_CHUNKS; i += 128) st_shared_v4(sB3 + 16 * i, __ldg(a.b3img + i));
+    for (int i = tid; i < C::B1_CHUNKS; i += 128) st_shared_v4(sB1 + 16 * i, __ldg(a.b1img + i));
+    for (int i = tid; i < CMID; i += 128) bias3_s[i] = __ldg(a.bias3 + i);
+    for (int i = tid; i < COUT; i += 128) bias1_s[i] = __ldg(a.bias1 + i);
+    if (EPI == TEPI_HEAD)
+        for (int i = tid; i <= COUT; i += 128) head_s[i] = __ldg(a.head + i);
+    if (tid == 0) {
+        mbar_init(mbar, 1);
+        fence_mbar_init();
+        *s_abort = 0;
+    }
+    if (warp == 0) tmem_alloc(tslot, C::TMEM_COLS);
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+    const uint32_t tbase = *tslot;
+    const uint32_t tlane = tbase + (static_cast<uint32_t>(warp * 32) << 16);
+    uint32_t phase = 0;
+
+    const int H = a.H, W = a.W;
+    const int tiles_x = (W + kTileM - 1) / kTileM;
+    const int tiles_y = (H + R - 1) / R;
+    const int ntiles = tiles_x * tiles_y;
+    constexpr uint32_t kPlane = (R + 2) * kSW * 16;  // bytes between channel groups of A0
+
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int y0 = (tile / tiles_x) * R;
+        const int x0 = (tile % tiles_x) * kTileM;
+
+        // ---------------- prologue: stage the (R+2) x 130 input tile (zero padded)
+        if constexpr (PRO == TPRO_GATHER) {
+            constexpr int NSP = 131;  // staged pixels -1 .. 129 (129 = zero pad read by the dummy tap)
+            for (int idx = tid; idx < (R + 2) * NSP; idx += 128) {
+                const int sr = idx / NSP, sp = idx % NSP;
+                const int gy = y0 - 1 + sr, gx = x0 - 1 + sp;
+                uint4 chunk = make_uint4(0, 0, 0, 0);
+                if (sp < 130 && gy >= 0 && gy < H && gx >= 0 && gx < W) {
+                    float f[4];
+                    gather_features(a.g, gy, gx, f);
+                    float hl[8];
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        const __nv_bfloat16 hi = __float2bfloat16_rn(f[c]);
+                        const float hf = __bfloat162float(hi);
+                        hl[c] = hf;
+                        hl[4 + c] = f[c] - hf;
+                    }
+                    chunk = f32_to_chunk(hl);
+                }
+                st_shared_v4(sA0 + 16 * (sr * kSW + sp), chunk);
+            }
+        } else if constexpr (PRO == TPRO_PLAIN) {
+            constexpr int CG = CIN / 8;
+            for (int idx = tid; idx < (R + 2) * 130 * CG; idx += 128) {
+                const int cg = idx % CG;
+                const int t = idx / CG;
+                const int sp = t % 130, sr = t / 130;
+                const int gy = y0 - 1 + sr, gx = x0 - 1 + sp;
+                uint4 v = make_uint4(0, 0, 0, 0);
+                if (gy >= 0 && gy < H && gx >= 0 && gx < W)
+                    v = ldg_v4(a.in + (static_cast<size_t>(gy) * W + gx) * CIN + cg * 8);
+                st_shared_v4(sA0 + cg * kPlane + 16 * (sr * kSW + sp), v);
+            }
+        } else {  // UP_SKIP / UP
+            constexpr int CG = CIN / 8;
+            const int Hl = H / 2, Wl = W / 2;
+            for (int idx = tid; idx < (R + 2) * 130 * CG; idx += 128) {
+                const int cg = idx % CG;
+                const int t = idx / CG;
+                const int sp = t % 130, sr = t / 130;
+                const int gy = y0 - 1 + sr, gx = x0 - 1 + sp;
+                uint4 v = make_uint4(0, 0, 0, 0);
+                if (gy >= 0 && gy < H && gx >= 0 && gx < W) {
+                    const BilinTap ty = bilin_tap(gy, Hl), tx = bilin_tap(gx, Wl);
+                    float p00[8], p01[8], p10[8], p11[8], o[8];
+                    chunk_to_f32(ldg_v4(a.in + (static_cast<size_t>(ty.i0) * Wl + tx.i0) * CIN + cg * 8), p00);
+                    chunk_to_f32(ldg_v4(a.in + (static_cast<size_t>(ty.i0) * Wl + tx.i1) * CIN + cg * 8), p01);
+                    chunk_to_f32(ldg_v4(a.in + (static_cast<size_t>(ty.i1) * Wl + tx.i0) * CIN + cg * 8), p10);
+                    chunk_to_f32(ldg_v4(a.in + (static_cast<size_t>(ty.i1) * Wl + tx.i1) * CIN + cg * 8), p11);
+#pragma unroll
+                    for (int c = 0; c < 8; ++c) {
+                        const float r0 = p00[c] * tx.w0 + p01[c] * tx.w1;
+                        const float r1 = p10[c] * tx.w0 + p11[c] * tx.w1;
+                        o[c] = r0 * ty.w0 + r1 * ty.w1;
+                    }
+                    if constexpr (PRO == TPRO_UP_SKIP) {
+                        float s[8];
+                        chunk_to_f32(ldg_v4(a.skip + (static_cast<size_t>(gy) * W + gx) * CIN + cg * 8), s);
+#pragma unroll
+                        for (int c = 0; c < 8; ++c) o[c] += s[c];
+                    }
+                    v = f32_to_chunk(o);
+                }
+                st_shared_v4(sA0 + cg * kPlane + 16 * (sr * kSW + sp), v);
+            }
+        }
+        fence_proxy_async_smem();
+        fence_before_sync();
+        __syncthreads();
+
+        // ---------------- 3x3 convolution: R row blocks of 128 x CMID; each K step
+        // twice, against the hi and the lo image of the weights
+        if (tid == 0) {
+            fence_after_sync();
+            constexpr uint32_t id3 = idesc_bf16(128, CMID);
+            constexpr uint32_t kB3lo = 16 * C::B3_IMG;  // byte offset of the lo image
+            for (int r = 0; r < R; ++r) {
+                const uint32_t d = tbase + r * CMID;
+                if constexpr (C::SPLIT) {
+#pragma unroll
+                    for (int k = 0; k < 5; ++k) {
+                        const int t0 = 2 * k, t1 = 2 * k + 1;
+                        const uint32_t a0 = sA0 + 16 * ((r + t0 / 3) * kSW + t0 % 3);
+                        const uint32_t lbo = (t1 < 9) ? 16 * ((r + t1 / 3) * kSW + t1 % 3) - 16 * ((r + t0 / 3) * kSW + t0 % 3) : 16;
+                        const uint64_t ad = smem_desc(a0, lbo, 128);
+                        const uint32_t b0 = sB3 + 16 * (k * 2 * CMID);
+                        mma_bf16(d, ad, smem_desc(b0, CMID * 16, 128), id3, k > 0);
+                        mma_bf16(d, ad, smem_desc(b0 + kB3lo, CMID * 16, 128), id3, 1);
+                    }
+                } else {
+#pragma unroll
+                    for (int tap = 0; tap < 9; ++tap) {
+#pragma unroll
+                        for (int kk = 0; kk < CIN / 16; ++kk) {
+                            const uint32_t a0 = sA0 + (2 * kk) * kPlane + 16 * ((r + tap / 3) * kSW + tap % 3);
+                            const uint64_t ad = smem_desc(a0, kPlane, 128);
+                            const uint32_t b0 = sB3 + 16 * ((tap * C::CG_IN + 2 * kk) * CMID);
+                            mma_bf16(d, ad, smem_desc(b0, CMID * 16, 128), id3, (tap | kk) != 0);
+                            mma_bf16(d, ad, smem_desc(b0 + kB3lo, CMID * 16, 128), id3, 1);
+                        }
+                    }
+                }
+            }
+            mma_commit(mbar);
+        }
+        if (!mbar_wait_bounded(mbar, phase, kWaitNs)) {
+            atomicExch(a.err, 1);
+            *s_abort = 1;
+        }
+        phase ^= 1;
+        __syncthreads();
+        if (*s_abort) break;
+        fence_after_sync();
+
+        // ---------------- epilogue 1: bias + ReLU -> BF16 hi + lo -> A operand of the 1x1
+        constexpr int kA1Part = (CMID / 8) * kTileM;  // chunks per part of one row
+        for (int r = 0; r < R; ++r) {
+#pragma unroll
+            for (int c0 = 0; c0 < CMID; c0 += 16) {
+                float v[16], lo[16];
+                tmem_ld16(tlane + r * CMID + c0, v);
+                tmem_ld_wait();
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    v[j] = fmaxf(v[j] + bias3_s[c0 + j], 0.f);
+                    const float hi = __bfloat162float(__float2bfloat16_rn(v[j]));
+                    lo[j] = v[j] - hi;
+                    v[j] = hi;
+                }
+                const int cg = c0 / 8;
+                const uint32_t row = sA1 + 16 * (r * 2 * kA1Part);
+                st_shared_v4(row + 16 * (cg * kTileM + tid), f32_to_chunk(v));
+                st_shared_v4(row + 16 * ((cg + 1) * kTileM + tid), f32_to_chunk(v + 8));
+                st_shared_v4(row + 16 * (kA1Part + cg * kTileM + tid), f32_to_chunk(lo));
+                st_shared_v4(row + 16 * (kA1Part + (cg + 1) * kTileM + tid), f32_to_chunk(lo + 8));
+            }
+        }
+        fence_proxy_async_smem();
+        fence_before_sync();
+        __syncthreads();
+
+        // ---------------- 1x1 convolution into the same TMEM columns:
+        // A_hi B_hi + A_hi B_lo + A_lo B_hi per K step
+        if (tid == 0) {
+            fence_after_sync();
+            constexpr uint32_t id1 = idesc_bf16(128, COUT);
+            constexpr uint32_t kB1lo = 16 * C::B1_IMG;
+            for (int r = 0; r < R; ++r) {
+                const uint32_t row = sA1 + 16 * (r * 2 * kA1Part);
+#pragma unroll
+                for (int kk = 0; kk < CMID / 16; ++kk) {
+                    const uint64_t ahi = smem_desc(row + 16 * (2 * kk * kTileM), kTileM * 16, 128);
+                    const uint64_t alo = smem_desc(row + 16 * (kA1Part + 2 * kk * kTileM), kTileM * 16, 128);
+                    const uint32_t b0 = sB1 + 16 * (2 * kk * COUT);
+                    const uint64_t bhi = smem_desc(b0, COUT * 16, 128);
+                    const uint64_t blo = smem_desc(b0 + kB1lo, COUT * 16, 128);
+                    mma_bf16(tbase + r * CMID, ahi, bhi, id1, kk > 0);
+                    mma_bf16(tbase + r * CMID, ahi, blo, id1, 1);
+                    mma_bf16(tbase + r * CMID, alo, bhi, id1, 1);
+                }
+            }
+            mma_commit(mbar);
+        }
+        if (!mbar_wait_bounded(mbar, phase, kWaitNs)) {
+            atomicExch(a.err, 2);
+            *s_abort = 1;
+        }
+        phase ^= 1;
+        __syncthreads();
+        if (*s_abort) break;
+        fence_after_sync();
+
+        // ---------------- epilogue 2
+        const int ox = x0 + tid;
+        if (EPI == TEPI_POOL || EPI == TEPI_SKIP_POOL) {
+            for (int r = 0; r < R; r += 2) {
+                float s[COUT];
+#pragma unroll
+                for (int c0 = 0; c0 < COUT; c0 += 16) {
+                    float v0[16], v1[16];
+                    tmem_ld16(tlane + r * CMID + c0, v0);
+                    tmem_ld16(tlane + (r + 1) * CMID + c0, v1);
+                    tmem_ld_wait();
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        v0[j] = fmaxf(v0[j] + bias1_s[c0 + j], 0.f);
+                        v1[j] = fmaxf(v1[j] + bias1_s[c0 + j], 0.f);
+                        s[c0 + j] = v0[j] + v1[j];
+                    }
+                    if (EPI == TEPI_SKIP_POOL) {
+                        const int oy = y0 + r;
+                        if (oy < H && ox < W) {
+                            uint16_t* dst = a.out_skip + (static_cast<size_t>(oy) * W + ox) * COUT + c0;
+                            reinterpret_cast<uint4*>(dst)[0] = f32_to_chunk(v0);
+                            reinterpret_cast<uint4*>(dst)[1] = f32_to_chunk(v0 + 8);
+                            dst += static_cast<size_t>(W) * COUT;
+                            reinterpret_cast<uint4*>(dst)[0] = f32_to_chunk(v1);
+                            reinterpret_cast<uint4*>(dst)[1] = f32_to_chunk(v1 + 8);
+                        }
+                    }
+                }
+#pragma unroll
+                for (int c = 0; c < COUT; ++c) s[c] = 0.25f * (s[c] + __shfl_xor_sync(0xffffffffu, s[c], 1));
+                const int oy = y0 + r;
+                if (oy < H && ox < W) {
+                    // even pixel writes the first half of the channels, odd the second
+                    const int half = (tid & 1) * (COUT / 2);
+                    uint16_t* dst = a.out + (static_cast<size_t>(oy / 2) * (W / 2) + ox / 2) * COUT + half;
+#pragma unroll
+                    for (int c = 0; c < COUT / 2; c += 8) {
+                        float t8[8];
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) t8[j] = s[half + c + j];
+                        reinterpret_cast<uint4*>(dst + c)[0] = f32_to_chunk(t8);
+                    }
+                }
+            }
+        } else {
+            for (int r = 0; r < R; ++r) {
+                const int oy = y0 + r;
+                float hsum = 0.f;
+#pragma unroll
+                for (int c0 = 0; c0 < COUT; c0 += 16) {
+                    float v[16];
+                    tmem_ld16(tlane + r * CMID + c0, v);
+                    tmem_ld_wait();
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) v[j] = fmaxf(v[j] + bias1_s[c0 + j], 0.f);
+                    if (EPI == TEPI_STORE) {
+                        if (oy < H && ox < W) {
+                            uint16_t* dst = a.out + (static_cast<size_t>(oy) * W + ox) * COUT + c0;
+                            reinterpret_cast<uint4*>(dst)[0] = f32_to_chunk(v);
+                            reinterpret_cast<uint4*>(dst)[1] = f32_to_chunk(v + 8);
+                        }
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) hsum = fmaf(head_s[c0 + j], v[j], hsum);
+                    }
+                }
+                if (EPI == TEPI_HEAD && oy < H && ox < W)
+                    a.vis[static_cast<size_t>(oy) * W + ox] = sigmoidf_acc(hsum + head_s[COUT]);
+            }
+        }
+        fence_before_sync();
+        __syncthreads();  // TMEM columns and A1 are free for the next tile
+    }
+
+    __syncthreads();
+    fence_after_sync();
+    if (warp == 0) tmem_dealloc(tbase, C::TMEM_COLS);
+}
+
+// ------------------------------------------------------------------ weight packing
+// Shared-memory images of the BF16 weights, each weight w stored as
+// hi = bf16(w) in one image and lo = bf16(w - hi) in a second image right
+// after it (16-byte chunks of 8 K values):
+//   3x3, C_in >= 16:  chunk (tap, g, n) = W[n][8g .. 8g+7][tap]
+//   3x3 first level:  chunk (k, h, n)   = tap t = 2k + h (t < 9), channels
+//                     [c0..c3 | c0..c3] (the same weight for the hi and lo
+//                     parts of each feature), zero for t = 9
+//   1x1:              chunk (g, n)      = W[n][8g .. 8g+7]
+using PackDesc = PackDescHost;
+
+__global__ void pack_bf16_kernel(const float* __restrict__ params, uint16_t* __restrict__ img,
+                                 const PackDesc* __restrict__ descs, int ndesc) {
+    for (int d = 0; d < ndesc; ++d) {
+        const PackDesc pd = descs[d];
+        for (size_t i = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; i < pd.count;
+             i += static_cast<size_t>(gridDim.x) * blockDim.x) {
+            const int e = static_cast<int>(i % 8);
+            const size_t chunk = i / 8;
+            float v = 0.f;
+            if (pd.kind == 0) {  // 3x3 general: chunk = (tap * (cin/8) + g) * cout + n
+                const int n = static_cast<int>(chunk % pd.cout);
+                const size_t t2 = chunk / pd.cout;
+                const int g = static_cast<int>(t2 % (pd.cin / 8));
+                const int tap = static_cast<int>(t2 / (pd.cin / 8));
+                v = params[pd.w_off + (static_cast<size_t>(n) * pd.cin + 8 * g + e) * 9 + tap];
+            } else if (pd.kind == 1) {  // first level hi/lo: chunk = (k * 2 + h) * cout + n
+                const int n = static_cast<int>(chunk % pd.cout);
+                const int kh = static_cast<int>(chunk / pd.cout);
+                const int tap = kh;  // = 2k + h
+                if (tap < 9) v = params[pd.w_off + (static_cast<size_t>(n) * 4 + (e % 4)) * 9 + tap];
+            } else {  // 1x1: chunk = g * cout + n
+                const int n = static_cast<int>(chunk % pd.cout);
+                const int g = static_cast<int>(chunk / pd.cout);
+                v = params[pd.w_off + static_cast<size_t>(n) * pd.cin + 8 * g + e];
+            }
+            const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+            const __nv_bfloat16 lo = __float2bfloat16_rn(v - __bfloat162float(hi));
+            img[pd.img_off + i] = __bfloat16_as_ushort(hi);
+            img[pd.img_off + pd.count + i] = __bfloat16_as_ushort(lo);
+        }
+    }
+}
+
+BF16Images bf16_images() {
+    const LayerOffsets off = layer_offsets();
+    BF16Images im{};
+    size_t pos = 0;
+    auto add = [&](int layer, int kind) {
+        const int ci = kLayers[layer].cin, co = kLayers[layer].cout;
+        size_t count;
+        if (kind == 0) count = static_cast<size_t>(9) * ci * co;
+        else if (kind == 1) count = static_cast<size_t>(10) * co * 8;
+        else count = static_cast<size_t>(ci) * co;
+        im.desc[im.n] = {kind, ci, co, off.w[layer], pos, count};
+        im.img_off[layer] = pos;
+        pos += 2 * count;  // hi image, then lo image (counts are multiples of 8)
+        ++im.n;
+    };
+    add(ENC0_3, 1); add(ENC0_1, 2); add(ENC1_3, 0); add(ENC1_1, 2); add(BOTT_3, 0); add(BOTT_1, 2);
+    add(DEC1_3, 0); add(DEC1_1, 2); add(DEC0_3, 0); add(DEC0_1, 2);
+    im.total = pos;
+    return im;
+}
+
+cudaError_t launch_pack_bf16(const float* params, uint16_t* img, const void* dev_descs, int ndesc, cudaStream_t stream) {
+    pack_bf16_kernel<<<64, 256, 0, stream>>>(params, img, static_cast<const PackDesc*>(dev_descs), ndesc);
+    return cudaGetLastError();
+}
+
+size_t pack_desc_bytes() { return sizeof(PackDesc); }
+
+// ------------------------------------------------------------------ launch
+template <int CIN, int CMID, int COUT, int R, int PRO, int EPI>
+static cudaError_t launch_tc(const TcArgs& a, cudaStream_t stream) {
+    using C = TcCfg<CIN, CMID, COUT, R, PRO>;
+    auto kern = level_tc_kernel<CIN, CMID, COUT, R, PRO, EPI>;
+    static int occ = -1;
+    if (occ < 0) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::BYTES);
+        if (e != cudaSuccess) return e;
+        int o = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, 128, C::BYTES);
+        if (e != cudaSuccess) return e;
+        // never more CTAs per SM than TMEM can hold at once (512 columns)
+        occ = o < 1 ? 1 : (o > C::TMEM_CAP ? C::TMEM_CAP : o);
+    }
+    const int tiles = ((a.W + kTileM - 1) / kTileM) * ((a.H + R - 1) / R);
+    if (tiles == 0) return cudaSuccess;
+    const int cap = occ * num_sms();
+    const int grid = tiles < cap ? tiles : cap;
+    kern<<<grid, 128, C::BYTES, stream>>>(a);
+    return cudaGetLastError();
+}
+
+const char* const kInferKernelNamesBf16[kInferKernelsBf16] = {
+    "bf16_enc0_gather", "bf16_enc1", "bf16_bottleneck", "bf16_dec1", "bf16_dec0_head"};
+
+cudaError_t launch_infer_bf16(const GatherParams& g, const float* params, const uint16_t* img,
+                              const Activations& act, float* vis, int* err, cudaStream_t stream,
+                              const StageEvents& se) {
+    const LayerOffsets off = layer_offsets();
+    const BF16Images im = bf16_images();
+    const int H = g.H, W = g.W;
+    auto I = [&](int layer) { return reinterpret_cast<const uint4*>(img + im.img_off[layer]); };
+    cudaError_t e;
+    TcArgs a{};
+    a.g = g; a.err = err;
+    // level 0 encoder fused with the gather
+    a.H = H; a.W = W;
+    a.b3img = I(ENC0_3); a.b1img = I(ENC0_1);
+    a.bias3 = params + off.b[ENC0_3]; a.bias1 = params + off.b[ENC0_1];
+    a.out = static_cast<uint16_t*>(act.e0);
+    se.rec(0);
+    if ((e = launch_tc<4, 16, 16, 4, TPRO_GATHER, TEPI_POOL>(a, stream)) != cudaSuccess) return e;
+    // level 1 encoder
+    a = TcArgs{}; a.g = g; a.err = err;
+    a.H = H / 2; a.W = W / 2;
+    a.in = static_cast<const uint16_t*>(act.e0);
+    a.b3img = I(ENC1_3); a.b1img = I(ENC1_1);
+    a.bias3 = params + off.b[ENC1_3]; a.bias1 = params + off.b[ENC1_1];
+    a.out_skip = static_cast<uint16_t*>(act.s1);
+    a.out = static_cast<uint16_t*>(act.p1);
+    se.rec(1);
+    if ((e = launch_tc<16, 32, 32, 2, TPRO_PLAIN, TEPI_SKIP_POOL>(a, stream)) != cudaSuccess) return e;
+    // bottleneck
+    a = TcArgs{}; a.g = g; a.err = err;
+    a.H = H / 4; a.W = W / 4;
+    a.in = static_cast<const uint16_t*>(act.p1);
+    a.b3img = I(BOTT_3); a.b1img = I(BOTT_1);
+    a.bias3 = params + off.b[BOTT_3]; a.bias1 = params + off.b[BOTT_1];
+    a.out = static_cast<uint16_t*>(act.bo);
+    se.rec(2);
+    if ((e = launch_tc<32, 64, 32, 2, TPRO_PLAIN, TEPI_STORE>(a, stream)) != cudaSuccess) return e;
+    // level 1 decoder
+    a = TcArgs{}; a.g = g; a.err = err;
+    a.H = H / 2; a.W = W / 2;
+    a.in = static_cast<const uint16_t*>(act.bo);
+    a.skip = static_cast<const uint16_t*>(act.s1);
+    a.b3img = I(DEC1_3); a.b1img = I(DEC1_1);
+    a.bias3 = params + off.b[DEC1_3]; a.bias1 = params + off.b[DEC1_1];
+    a.out = static_cast<uint16_t*>(act.d1);
+    se.rec(3);
+    if ((e = launch_tc<32, 32, 16, 2, TPRO_UP_SKIP, TEPI_STORE>(a, stream)) != cudaSuccess) return e;
+    // level 0 decoder + head
+    a = TcArgs{}; a.g = g; a.err = err;
+    a.H = H; a.W = W;
+    a.in = static_cast<const uint16_t*>(act.d1);
+    a.b3img = I(DEC0_3); a.b1img = I(DEC0_1);
+    a.bias3 = params + off.b[DEC0_3]; a.bias1 = params + off.b[DEC0_1];
+    a.head = params + off.w[HEAD];  // head weights followed by its bias
+    a.vis = vis;
+    se.rec(4);
+    e = launch_tc<16, 16, 16, 4, TPRO_UP, TEPI_HEAD>(a, stream);
+    se.rec(5);
+    return e;
+}
+
+}  // namespace nsm

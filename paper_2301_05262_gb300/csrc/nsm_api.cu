@@ -18,7 +18,10 @@ struct nsm_ctx {
 
 struct nsm_weights {
     int device;
-    float* d_params;  // canonical FP32 vector (nsm_param_count floats)
+    float* d_params;   // canonical FP32 vector (nsm_param_count floats)
+    uint16_t* d_bf16;  // packed BF16 images (tensor-core form)
+    void* d_descs;     // packing table
+    int ndesc;
 };
 
 namespace nsm {
@@ -224,6 +227,7 @@ nsm_status nsm_ctx_set_stage_events(nsm_ctx* c, void* const* events, int n) {
 int nsm_infer_kernel_count(nsm_precision precision) {
     switch (precision) {
         case NSM_FP32: return kInferKernelsFp32;
+        case NSM_BF16: return kInferKernelsBf16;
         default: return 0;
     }
 }
@@ -232,6 +236,7 @@ const char* nsm_infer_kernel_name(nsm_precision precision, int i) {
     if (i < 0 || i >= nsm_infer_kernel_count(precision)) return "";
     switch (precision) {
         case NSM_FP32: return kInferKernelNamesFp32[i];
+        case NSM_BF16: return kInferKernelNamesBf16[i];
         default: return "";
     }
 }
@@ -250,6 +255,17 @@ nsm_status nsm_weights_create(nsm_ctx* ctx, const float* host_params, size_t n, 
     if (e != cudaSuccess) { delete w; return cuda_fail(e, "cudaMalloc(weights)"); }
     e = cudaMemcpy(w->d_params, host_params, n * sizeof(float), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) { cudaFree(w->d_params); delete w; return cuda_fail(e, "upload weights"); }
+    const BF16Images im = bf16_images();
+    w->ndesc = im.n;
+    e = cudaMalloc(&w->d_bf16, im.total * sizeof(uint16_t));
+    if (e == cudaSuccess) e = cudaMalloc(&w->d_descs, pack_desc_bytes() * im.n);
+    if (e == cudaSuccess) e = cudaMemcpy(w->d_descs, im.desc, pack_desc_bytes() * im.n, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = launch_pack_bf16(w->d_params, w->d_bf16, w->d_descs, w->ndesc, nullptr);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        cudaFree(w->d_params); cudaFree(w->d_bf16); cudaFree(w->d_descs); delete w;
+        return cuda_fail(e, "pack weights");
+    }
     *out = w;
     return NSM_OK;
 }
@@ -262,12 +278,16 @@ nsm_status nsm_weights_load_device(nsm_weights* w, const float* dev_params, size
     cudaError_t e = cudaMemcpyAsync(w->d_params, dev_params, n * sizeof(float), cudaMemcpyDeviceToDevice,
                                     static_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) return cuda_fail(e, "copy weights");
+    e = launch_pack_bf16(w->d_params, w->d_bf16, w->d_descs, w->ndesc, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "pack weights");
     return NSM_OK;
 }
 
 void nsm_weights_destroy(nsm_weights* w) {
     if (!w) return;
     cudaFree(w->d_params);
+    cudaFree(w->d_bf16);
+    cudaFree(w->d_descs);
     delete w;
 }
 
@@ -311,9 +331,9 @@ nsm_status nsm_infer(nsm_ctx* ctx, const nsm_frame* frame, const nsm_weights* w,
     if (!workspace || workspace_bytes < need)
         return fail(NSM_ERR_WORKSPACE, "workspace of %zu bytes given, %zu needed", workspace_bytes, need);
     if ((s = check_dev_ptr(workspace, "workspace", 256)) != NSM_OK) return s;
-    if (precision != NSM_FP32) return fail(NSM_ERR_UNSUPPORTED, "precision %d not built yet", static_cast<int>(precision));
+    if (precision == NSM_FP8) return fail(NSM_ERR_UNSUPPORTED, "precision %d not built yet", static_cast<int>(precision));
     Activations act{};
-    activations_bytes(frame->H, frame->W, 4, &act, workspace);
+    activations_bytes(frame->H, frame->W, precision == NSM_FP32 ? 4 : 2, &act, workspace);
     GatherParams g = make_gather(frame);
     StageEvents se;
     const int k = nsm_infer_kernel_count(precision);
@@ -324,7 +344,9 @@ nsm_status nsm_infer(nsm_ctx* ctx, const nsm_frame* frame, const nsm_weights* w,
         se.n = static_cast<int>(ctx->stage_events.size());
         se.stream = static_cast<cudaStream_t>(stream);
     }
-    cudaError_t e = launch_infer_fp32(g, w->d_params, act, vis_out, static_cast<cudaStream_t>(stream), se);
+    cudaError_t e = (precision == NSM_FP32)
+        ? launch_infer_fp32(g, w->d_params, act, vis_out, static_cast<cudaStream_t>(stream), se)
+        : launch_infer_bf16(g, w->d_params, w->d_bf16, act, vis_out, ctx->d_err, static_cast<cudaStream_t>(stream), se);
     if (e != cudaSuccess) return cuda_fail(e, "inference kernel launch");
     return NSM_OK;
 }

@@ -55,4 +55,24 @@ extern const char* const kInferKernelNamesFp32[kInferKernelsFp32];
 cudaError_t launch_infer_fp32(const GatherParams& g, const float* params, const Activations& act,
                               float* vis, cudaStream_t stream, const StageEvents& se);
 
+// Packed BF16 weight images for the tensor-core form (shared-memory layout of
+// each layer's B operand), built on the device from the canonical FP32 vector.
+struct PackDescHost { int kind, cin, cout; size_t w_off; size_t img_off; size_t count; };
+struct BF16Images {
+    PackDescHost desc[NUM_LAYERS];
+    int n;
+    size_t img_off[NUM_LAYERS];  // element offset of each layer's image (head has none)
+    size_t total;                // elements (uint16)
+};
+BF16Images bf16_images();
+size_t pack_desc_bytes();
+cudaError_t launch_pack_bf16(const float* params, uint16_t* img, const void* dev_descs, int ndesc,
+                             cudaStream_t stream);
+
+constexpr int kInferKernelsBf16 = 5;
+extern const char* const kInferKernelNamesBf16[kInferKernelsBf16];
+cudaError_t launch_infer_bf16(const GatherParams& g, const float* params, const uint16_t* img,
+                              const Activations& act, float* vis, int* err, cudaStream_t stream,
+                              const StageEvents& se);
+
 }  // namespace nsm

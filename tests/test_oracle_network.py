@@ -233,3 +233,31 @@ def test_train_step_gradient_is_loss_gradient():
         tm = th.copy(); tm[i] -= h
         fd = (L(tp) - L(tm)) / (2 * h)
         assert fd == pytest.approx(grad[i], rel=1e-4, abs=1e-9)
+
+
+def test_round_bf16_definition():
+    # exact values stay, halfway cases go to even, 8 significant bits survive
+    x = np.array([1.0, 1.0 + 2 ** -8, 1.0 + 3 * 2 ** -8, 1.0 + 2 ** -7, -3.140625, 0.0, 2.0 ** -130])
+    r = N.round_bf16(x)
+    assert list(r[:5]) == [1.0, 1.0, 1.0 + 2 ** -6, 1.0 + 2 ** -7, -3.140625]
+    assert r[5] == 0.0 and r[6] == np.float32(2.0 ** -130)  # a binary32 subnormal with 7 mantissa bits fits
+    rng = np.random.default_rng(11)
+    y = rng.standard_normal(10000) * 100
+    rel = np.abs(N.round_bf16(y) - y) / np.abs(y)
+    assert rel.max() <= 2 ** -8
+    torch = pytest.importorskip("torch")
+    ref = torch.from_numpy(y.astype(np.float32)).to(torch.bfloat16).to(torch.float64).numpy()
+    np.testing.assert_array_equal(N.round_bf16(y), ref)
+    # the hi + lo pair keeps about 16 bits
+    assert (np.abs(N.round_bf16_pair(y) - y.astype(np.float32)) / np.abs(y)).max() <= 2 ** -15
+
+
+def test_forward_rounded_identity_and_sensitivity():
+    rng = np.random.default_rng(12)
+    x = rng.standard_normal((4, 8, 12))
+    th = _rand_theta(3, seed=13)
+    ident = lambda a: np.asarray(a, np.float64)
+    np.testing.assert_allclose(N.forward_rounded(x, th, ident), N.forward(x, th), rtol=1e-12, atol=1e-14)
+    v = N.forward_rounded(x, th, N.round_bf16)
+    d = np.abs(v - N.forward(x, th))
+    assert 0 < d.max() < 0.05

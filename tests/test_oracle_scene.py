@@ -111,7 +111,7 @@ def test_sphere_over_plane_shadow_is_exact_conic():
     f = scenegen.render_frame(scene, 64, 64, 64, 64)
     vis = scenegen.hard_visibility(f).astype(bool)
     P = f.pos4[..., :3].astype(np.float64)
-    ground = f.nrm4[..., 2] > 0.999
+    ground = (f.nrm4[..., 2] > 0.999) & (np.abs(f.pos4[..., 2]) < 1e-6)
     d = L - P
     tt = np.clip(np.sum((S - P) * d, axis=-1) / np.sum(d * d, axis=-1), 0, 1)
     closest = P + tt[..., None] * d
@@ -130,7 +130,7 @@ def test_soft_visibility_umbra_and_point_limit():
     scene = scenegen.Scene(objects=np.array([[0.0, 0.0, 0.0, 1.5, 0.6]]), light_pos=L, light_radius=0.1)
     f = scenegen.render_frame(scene, 32, 32, 64, 64)
     P = f.pos4[..., :3]
-    ground = f.nrm4[..., 2] > 0.999
+    ground = (f.nrm4[..., 2] > 0.999) & (np.abs(f.pos4[..., 2]) < 1e-6)
     near = ground & (np.hypot(P[..., 0], P[..., 1]) < 0.2)
     if near.any():
         v = scenegen.soft_visibility(f, spp_side=8)
