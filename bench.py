@@ -272,6 +272,10 @@ def run_ours(args):
 
     # end-to-end through the host-buffer entry point (copies inside the timed region)
     head = precisions[0]
+    if args.skip_e2e:
+        print(json.dumps({"forms": {k: {kk: vv for kk, vv in v.items() if kk != "clocks"} for k, v in forms.items()}}),
+              flush=True)
+        return 0
     prec = nsm.PRECISIONS[head]
     pin_pos = torch.from_numpy(frame.pos4).pin_memory()
     pin_nrm = torch.from_numpy(frame.nrm4).pin_memory()
@@ -375,7 +379,13 @@ def main():
     ap.add_argument("--precisions", default="bf16,fp32", help="comma list; the first is the headline form")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-error", action="store_true")
+    ap.add_argument("--skip-e2e", action="store_true")
+    ap.add_argument("--size", default=None, help="WxH view size (profiling runs); default 1920x1080")
     args = ap.parse_args()
+    if args.size:
+        global H, W, WORKLOAD
+        W, H = (int(v) for v in args.size.lower().split("x"))
+        WORKLOAD = WORKLOAD.replace("1920x1080", f"{W}x{H}")
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":

@@ -181,6 +181,67 @@ nsm_status nsm_infer_host(nsm_ctx* ctx, const nsm_frame* host_frame, const nsm_w
                           nsm_precision precision, void* dev_stage, size_t stage_bytes,
                           void* workspace, size_t workspace_bytes, float* vis_host, void* stream);
 
+/* ---------------------------------------------------------------- backward / training */
+
+/* Bytes of device workspace nsm_backward needs for an H x W view. */
+size_t nsm_backward_workspace_bytes(int H, int W);
+
+/* Adjoint of the FP32 inference (the hand-written backward of the gather +
+ * network, Sec. 3.5): for the visibility cotangent grad_vis ([H][W] float32,
+ * device) it ADDS dL/dtheta to grad_params (device, nsm_param_count floats,
+ * canonical layout) and, when grad_feat is non-NULL, writes dL/dfeatures
+ * ([H][W][4] float32, pixel-major, device).  vis_out (nullable, [H][W]) receives
+ * the forward visibility computed on the way.  The forward keeps only the
+ * level checkpoints; each level's internals are recomputed during the backward.
+ * No gradient flows to the G-buffer or shadow map (the nearest-texel lookup is
+ * piecewise constant).  dev_params: device FP32 canonical vector.
+ * H and W multiples of 4.  Asynchronous on stream. */
+nsm_status nsm_backward(nsm_ctx* ctx, const nsm_frame* frame, const float* dev_params, const float* grad_vis,
+                        float* grad_params, float* grad_feat, float* vis_out, void* workspace,
+                        size_t workspace_bytes, void* stream);
+
+/* One training batch of the temporal-window loss (Sec. 3.3, Eq. 2). */
+typedef struct {
+    int B, T;                   /* items; window instances per item (T >= 1), instance 0 carries
+                                   the target and the gradient, instances 1..T-1 are the perturbed
+                                   inputs whose outputs enter the loss detached */
+    int H, W;                   /* crop size, multiples of 4 */
+    int Hs, Ws;                 /* shadow-map size (all instances) */
+    const float* pos4;          /* device [T][B][H][W][4], as nsm_frame.pos4 */
+    const float* nrm4;          /* device [T][B][H][W][4] */
+    const float* sm;            /* device [T][B][Hs][Ws] */
+    const nsm_light* lights;    /* host [T][B] */
+    const nsm_camera* cameras;  /* host [T][B] */
+    const float* target;        /* device [B][H][W], ray-traced visibility of instance 0 */
+} nsm_batch;
+
+typedef struct {
+    float lr;       /* Adam step size */
+    float alpha;    /* weight of the L1 term of L(y, y~), Eq. 2 (0.9 in the paper) */
+    float beta1, beta2, eps;  /* Adam moments (0.9, 0.999, 1e-8) */
+} nsm_train_cfg;
+
+typedef struct nsm_train_state nsm_train_state;  /* FP32 master weights, Adam moments, workspace */
+
+/* Set-up call (allocates): the master weights start from host_params
+ * (nsm_param_count floats); batches up to max_B x max_T instances of H x W. */
+nsm_status nsm_train_state_create(nsm_ctx* ctx, const float* host_params, size_t n, int max_B, int max_T, int H,
+                                  int W, nsm_train_state** out);
+void nsm_train_state_destroy(nsm_train_state* st);
+
+/* One step: features of all B*T instances, forward with level checkpoints,
+ * loss L = alpha mean|x0 - x~| + sum_i alpha mean|x0 - x_i| (per item, averaged
+ * over items; the VGG-19 term of Eq. 2 is not evaluated), backward through x0
+ * with recomputation, Adam update of the master weights.  loss_out (device,
+ * nullable) receives the batch loss.  Asynchronous on stream. */
+nsm_status nsm_train_step(nsm_ctx* ctx, nsm_train_state* st, const nsm_batch* batch, const nsm_train_cfg* cfg,
+                          float* loss_out, void* stream);
+
+/* Copy a state vector (n = nsm_param_count floats) to device memory dev_out:
+ * what = 0 master weights, 1 gradient of the last step, 2 Adam first moment,
+ * 3 Adam second moment.  Asynchronous on stream. */
+nsm_status nsm_train_state_read(nsm_train_state* st, int what, float* dev_out, size_t n, void* stream);
+
 /* ---------------------------------------------------------------- no-allocation variant */
 
 /* FP32 inference that allocates nothing and needs no workspace, for callers

@@ -251,3 +251,136 @@ def nsm_infer_fp32_static(frame: nsm_frame, dev_params, vis_out, stream=None):
     """FP32 inference without allocation or workspace (views up to 262,144 pixels)."""
     _check(lib().nsm_infer_fp32_static(ctypes.byref(frame), _ptr(dev_params), _ptr(vis_out), _stream(stream)),
            "nsm_infer_fp32_static")
+
+
+# ---------------------------------------------------------------- backward / training
+class nsm_batch(ctypes.Structure):
+    _fields_ = [("B", ctypes.c_int), ("T", ctypes.c_int), ("H", ctypes.c_int), ("W", ctypes.c_int),
+                ("Hs", ctypes.c_int), ("Ws", ctypes.c_int), ("pos4", ctypes.c_void_p), ("nrm4", ctypes.c_void_p),
+                ("sm", ctypes.c_void_p), ("lights", ctypes.POINTER(nsm_light)),
+                ("cameras", ctypes.POINTER(nsm_camera)), ("target", ctypes.c_void_p)]
+
+
+class nsm_train_cfg(ctypes.Structure):
+    _fields_ = [("lr", ctypes.c_float), ("alpha", ctypes.c_float), ("beta1", ctypes.c_float),
+                ("beta2", ctypes.c_float), ("eps", ctypes.c_float)]
+
+
+def _train_sigs():
+    L = lib()
+    if getattr(L, "_train_sigs", False):
+        return L
+    P, I, Z = ctypes.c_void_p, ctypes.c_int, ctypes.c_size_t
+    sig = {
+        "nsm_backward_workspace_bytes": ([I, I], Z),
+        "nsm_backward": ([P, ctypes.POINTER(nsm_frame), P, P, P, P, P, P, Z, P], I),
+        "nsm_train_state_create": ([P, P, Z, I, I, I, I, ctypes.POINTER(P)], I),
+        "nsm_train_state_destroy": ([P], None),
+        "nsm_train_step": ([P, P, ctypes.POINTER(nsm_batch), ctypes.POINTER(nsm_train_cfg), P, P], I),
+        "nsm_train_state_read": ([P, I, P, Z, P], I),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(L, name)
+        fn.argtypes = args
+        fn.restype = res
+    L._train_sigs = True
+    return L
+
+
+def nsm_backward_workspace_bytes(H: int, W: int) -> int:
+    return int(_train_sigs().nsm_backward_workspace_bytes(H, W))
+
+
+def nsm_backward(ctx: Context, frame: nsm_frame, dev_params, grad_vis, grad_params, workspace, grad_feat=None,
+                 vis_out=None, stream=None):
+    L = _train_sigs()
+    _check(L.nsm_backward(ctx.h, ctypes.byref(frame), _ptr(dev_params), _ptr(grad_vis), _ptr(grad_params),
+                          _ptr(grad_feat), _ptr(vis_out), _ptr(workspace),
+                          int(workspace.numel() * workspace.element_size()), _stream(stream)), "nsm_backward")
+
+
+class TrainState:
+    """FP32 master weights + Adam state for nsm_train_step."""
+
+    def __init__(self, ctx: Context, params: np.ndarray, max_B: int, max_T: int, H: int, W: int):
+        L = _train_sigs()
+        p = np.ascontiguousarray(params, np.float32)
+        h = ctypes.c_void_p()
+        _check(L.nsm_train_state_create(ctx.h, _ptr(p), p.size, max_B, max_T, H, W, ctypes.byref(h)),
+               "nsm_train_state_create")
+        self.h, self.ctx, self.n = h, ctx, p.size
+
+    def step(self, batch: nsm_batch, lr=1e-3, alpha=0.9, beta1=0.9, beta2=0.999, eps=1e-8, loss_out=None,
+             stream=None):
+        cfg = nsm_train_cfg(lr=lr, alpha=alpha, beta1=beta1, beta2=beta2, eps=eps)
+        _check(_train_sigs().nsm_train_step(self.ctx.h, self.h, ctypes.byref(batch), ctypes.byref(cfg),
+                                            _ptr(loss_out), _stream(stream)), "nsm_train_step")
+
+    def read(self, what: int, out, stream=None):
+        _check(_train_sigs().nsm_train_state_read(self.h, what, _ptr(out), self.n, _stream(stream)),
+               "nsm_train_state_read")
+
+    def close(self):
+        if self.h:
+            _train_sigs().nsm_train_state_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def make_batch(pos4, nrm4, sm, lights, cams, target, B, T):
+    """nsm_batch from device tensors pos4/nrm4 [T,B,H,W,4], sm [T,B,Hs,Ws],
+    target [B,H,W] and T*B LightDesc / camera positions (instance order t*B+b)."""
+    H, W = int(pos4.shape[2]), int(pos4.shape[3])
+    Hs, Ws = int(sm.shape[2]), int(sm.shape[3])
+    LA = (nsm_light * (T * B))()
+    CA = (nsm_camera * (T * B))()
+    for i, (ld, cp) in enumerate(zip(lights, cams)):
+        fr = make_frame(np.zeros((1, 1, 4), np.float32), np.zeros((1, 1, 4), np.float32),
+                        np.zeros((1, 1), np.float32), ld, cp)
+        LA[i] = fr.light
+        CA[i] = fr.camera
+    bt = nsm_batch(B=B, T=T, H=H, W=W, Hs=Hs, Ws=Ws, pos4=_ptr(pos4), nrm4=_ptr(nrm4), sm=_ptr(sm),
+                   lights=ctypes.cast(LA, ctypes.POINTER(nsm_light)),
+                   cameras=ctypes.cast(CA, ctypes.POINTER(nsm_camera)), target=_ptr(target))
+    bt._keep = (LA, CA)
+    return bt
+
+
+def autograd_function():
+    """torch.autograd.Function whose forward is nsm_infer (FP32) and whose
+    backward is the library's hand-written adjoint (nsm_backward).
+    Usage: vis = F.apply(params, ctx, frame) with params a device FP32 tensor
+    of nsm_param_count() floats; the frame's buffers must stay alive."""
+    import torch
+
+    class NSMFunction(torch.autograd.Function):
+        @staticmethod
+        def forward(fctx, params, ctx, frame):
+            H, W = frame.H, frame.W
+            vis = torch.empty((H, W), dtype=torch.float32, device=params.device)
+            ws = torch.empty((nsm_backward_workspace_bytes(H, W),), dtype=torch.uint8, device=params.device)
+            gp = torch.zeros_like(params)
+            g0 = torch.zeros((H, W), dtype=torch.float32, device=params.device)
+            # the adjoint call also returns the forward visibility; with a zero
+            # cotangent it leaves the gradient untouched
+            nsm_backward(ctx, frame, params.contiguous(), g0, gp, ws, vis_out=vis)
+            fctx.save_for_backward(params)
+            fctx.nsm = (ctx, frame)
+            return vis
+
+        @staticmethod
+        def backward(fctx, grad_vis):
+            (params,) = fctx.saved_tensors
+            ctx, frame = fctx.nsm
+            ws = torch.empty((nsm_backward_workspace_bytes(frame.H, frame.W),), dtype=torch.uint8,
+                             device=params.device)
+            gp = torch.zeros_like(params)
+            nsm_backward(ctx, frame, params.contiguous(), grad_vis.contiguous().float(), gp, ws)
+            return gp, None, None
+
+    return NSMFunction

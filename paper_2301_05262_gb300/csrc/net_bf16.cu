@@ -109,7 +109,7 @@ __device__ __forceinline__ uint4 f32_to_chunk(const float* f) {
 }
 
 template <int CIN, int CMID, int COUT, int R, int PRO, int EPI>
-__global__ void __launch_bounds__(128, 1) level_tc_kernel(TcArgs a) {
+__global__ void __launch_bounds__(128, 3) level_tc_kernel(TcArgs a) {
     using C = TcCfg<CIN, CMID, COUT, R, PRO>;
     extern __shared__ __align__(1024) unsigned char smem[];
     const uint32_t sbase = smem_u32(smem);
@@ -157,28 +157,58 @@ __global__ void __launch_bounds__(128, 1) level_tc_kernel(TcArgs a) {
 
         // ---------------- prologue: stage the (R+2) x 130 input tile (zero padded)
         if constexpr (PRO == TPRO_GATHER) {
-            constexpr int NSP = 131;  // staged pixels -1 .. 129 (129 = zero pad read by the dummy tap)
-            for (int idx = tid; idx < (R + 2) * NSP; idx += 128) {
+            // staged pixels -1 .. 129 of each row (129 = zero pad read by the dummy tap);
+            // each thread gathers NPT of them in three batched phases so that its
+            // G-buffer loads, then its shadow-map loads, are all in flight together
+            constexpr int NSP = 131;
+            constexpr int ITEMS = (R + 2) * NSP;
+            constexpr int NPT = (ITEMS + 127) / 128;
+            float4 P[NPT], Nv[NPT];
+            int tex[NPT];
+            bool ok[NPT];
+#pragma unroll
+            for (int k = 0; k < NPT; ++k) {
+                const int idx = tid + 128 * k;
                 const int sr = idx / NSP, sp = idx % NSP;
                 const int gy = y0 - 1 + sr, gx = x0 - 1 + sp;
-                uint4 chunk = make_uint4(0, 0, 0, 0);
-                if (sp < 130 && gy >= 0 && gy < H && gx >= 0 && gx < W) {
-                    float f[4];
-                    gather_features(a.g, gy, gx, f);
-                    float hl[8];
-#pragma unroll
-                    for (int c = 0; c < 4; ++c) {
-                        const __nv_bfloat16 hi = __float2bfloat16_rn(f[c]);
-                        const float hf = __bfloat162float(hi);
-                        hl[c] = hf;
-                        hl[4 + c] = f[c] - hf;
-                    }
-                    chunk = f32_to_chunk(hl);
+                ok[k] = idx < ITEMS && sp < 130 && gy >= 0 && gy < H && gx >= 0 && gx < W;
+                if (ok[k]) {
+                    const size_t p = static_cast<size_t>(gy) * W + gx;
+                    P[k] = __ldg(a.g.pos4 + p);
+                    Nv[k] = __ldg(a.g.nrm4 + p);
                 }
-                st_shared_v4(sA0 + 16 * (sr * kSW + sp), chunk);
+            }
+            float z[NPT];
+#pragma unroll
+            for (int k = 0; k < NPT; ++k) {
+                tex[k] = ok[k] ? texel_index(a.g, P[k].x, P[k].y, P[k].z) : -1;
+                z[k] = a.g.z_far;
+                if (tex[k] >= 0) z[k] = __ldg(a.g.sm + tex[k]);
+            }
+#pragma unroll
+            for (int k = 0; k < NPT; ++k) {
+                const int idx = tid + 128 * k;
+                if (idx < ITEMS) {
+                    const int sr = idx / NSP, sp = idx % NSP;
+                    uint4 chunk = make_uint4(0, 0, 0, 0);
+                    if (ok[k]) {
+                        float f[4];
+                        pixel_features(a.g, P[k], Nv[k], z[k], f);
+                        float hl[8];
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) {
+                            const float hf = __bfloat162float(__float2bfloat16_rn(f[c]));
+                            hl[c] = hf;
+                            hl[4 + c] = f[c] - hf;
+                        }
+                        chunk = f32_to_chunk(hl);
+                    }
+                    st_shared_v4(sA0 + 16 * (sr * kSW + sp), chunk);
+                }
             }
         } else if constexpr (PRO == TPRO_PLAIN) {
             constexpr int CG = CIN / 8;
+#pragma unroll 4
             for (int idx = tid; idx < (R + 2) * 130 * CG; idx += 128) {
                 const int cg = idx % CG;
                 const int t = idx / CG;
@@ -192,6 +222,7 @@ __global__ void __launch_bounds__(128, 1) level_tc_kernel(TcArgs a) {
         } else {  // UP_SKIP / UP
             constexpr int CG = CIN / 8;
             const int Hl = H / 2, Wl = W / 2;
+#pragma unroll 2
             for (int idx = tid; idx < (R + 2) * 130 * CG; idx += 128) {
                 const int cg = idx % CG;
                 const int t = idx / CG;
@@ -489,11 +520,18 @@ static cudaError_t launch_tc(const TcArgs& a, cudaStream_t stream) {
     if (occ < 0) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::BYTES);
         if (e != cudaSuccess) return e;
-        int o = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, 128, C::BYTES);
+        // resident CTAs per SM from the kernel's own resources: registers,
+        // shared memory (228 KB per SM, 1 KB reserved per CTA) and TMEM columns
+        cudaFuncAttributes fa{};
+        e = cudaFuncGetAttributes(&fa, kern);
         if (e != cudaSuccess) return e;
-        // never more CTAs per SM than TMEM can hold at once (512 columns)
-        occ = o < 1 ? 1 : (o > C::TMEM_CAP ? C::TMEM_CAP : o);
+        const int regs = ((fa.numRegs + 7) / 8) * 8 * 128;
+        const int by_regs = regs > 0 ? 65536 / regs : 16;
+        const int by_smem = (228 * 1024) / (C::BYTES + 1024);
+        int o = by_regs < by_smem ? by_regs : by_smem;
+        if (o > C::TMEM_CAP) o = C::TMEM_CAP;
+        if (o > 16) o = 16;
+        occ = o < 1 ? 1 : o;
     }
     const int tiles = ((a.W + kTileM - 1) / kTileM) * ((a.H + R - 1) / R);
     if (tiles == 0) return cudaSuccess;

@@ -28,7 +28,7 @@ namespace nsm {
 
 static thread_local std::string g_last_error;
 
-static nsm_status fail(nsm_status s, const char* fmt, ...) {
+nsm_status fail(nsm_status s, const char* fmt, ...) {
     char buf[512];
     va_list ap;
     va_start(ap, fmt);
@@ -40,7 +40,7 @@ static nsm_status fail(nsm_status s, const char* fmt, ...) {
 
 void set_last_error(const std::string& msg) { g_last_error = msg; }
 
-static nsm_status cuda_fail(cudaError_t e, const char* what) {
+nsm_status cuda_fail(cudaError_t e, const char* what) {
     return fail(NSM_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
@@ -70,7 +70,7 @@ int num_sms() {
     return cached[dev];
 }
 
-static size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 size_t activations_bytes(int H, int W, size_t eb, Activations* carve, void* base) {
     const size_t h2 = static_cast<size_t>(H / 2) * (W / 2), h4 = static_cast<size_t>(H / 4) * (W / 4);
@@ -86,7 +86,7 @@ size_t activations_bytes(int H, int W, size_t eb, Activations* carve, void* base
 }
 
 // ------------------------------------------------------------------ checks
-static nsm_status check_device() {
+nsm_status check_device() {
     int dev = -1;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return fail(NSM_ERR_DEVICE, "no CUDA device: %s", cudaGetErrorString(e));
@@ -98,7 +98,7 @@ static nsm_status check_device() {
     return NSM_OK;
 }
 
-static nsm_status check_dev_ptr(const void* p, const char* name, size_t align, bool nullable = false) {
+nsm_status check_dev_ptr(const void* p, const char* name, size_t align, bool nullable) {
     if (!p) {
         if (nullable) return NSM_OK;
         return fail(NSM_ERR_INVALID_ARG, "%s is NULL", name);
@@ -119,13 +119,13 @@ static nsm_status check_dev_ptr(const void* p, const char* name, size_t align, b
     return NSM_OK;
 }
 
-static bool finite_all(const float* v, int n) {
+bool finite_all(const float* v, int n) {
     for (int i = 0; i < n; ++i)
         if (!(v[i] == v[i]) || v[i] == INFINITY || v[i] == -INFINITY) return false;
     return true;
 }
 
-static nsm_status check_frame(const nsm_frame* f, bool need_mult4) {
+nsm_status check_frame(const nsm_frame* f, bool need_mult4) {
     if (!f) return fail(NSM_ERR_INVALID_ARG, "frame is NULL");
     if (f->H < 0 || f->W < 0 || f->H > 16384 || f->W > 16384)
         return fail(NSM_ERR_SHAPE, "view size %d x %d outside [0, 16384]", f->H, f->W);
@@ -148,7 +148,7 @@ static nsm_status check_frame(const nsm_frame* f, bool need_mult4) {
     return NSM_OK;
 }
 
-static GatherParams make_gather(const nsm_frame* f) {
+GatherParams make_gather(const nsm_frame* f) {
     GatherParams g{};
     std::memcpy(g.M, f->light.view_proj, sizeof(g.M));
     for (int k = 0; k < 3; ++k) { g.L[k] = f->light.pos[k]; g.C[k] = f->camera.pos[k]; }

@@ -68,6 +68,20 @@ __device__ __forceinline__ bool depth_test(const GatherParams& g, float zf, floa
     return zf <= __fadd_rn(z, __fmul_rn(g.beta, zf));
 }
 
+// The four features from the pixel's G-buffer entry and the fetched depth z.
+__device__ __forceinline__ void pixel_features(const GatherParams& g, float4 P, float4 N, float z, float f[4]) {
+    const float zf = emitter_distance(g, P.x, P.y, P.z);
+    const float lx = g.L[0] - P.x, ly = g.L[1] - P.y, lz = g.L[2] - P.z;
+    const float ce = (N.x * lx + N.y * ly + N.z * lz) / zf;
+    const float cxv = g.C[0] - P.x, cyv = g.C[1] - P.y, czv = g.C[2] - P.z;
+    const float cl = sqrtf(cxv * cxv + cyv * cyv + czv * czv);
+    const float cc = (N.x * cxv + N.y * cyv + N.z * czv) / cl;
+    f[0] = ce + g.r_hat;
+    f[1] = z / zf;
+    f[2] = z - zf;
+    f[3] = cc / P.w;
+}
+
 struct PixelGather {
     float f[4];  // c_e + r_hat, z / z_f, z - z_f, c_c / d
     float zf;    // binary32 z_f
@@ -84,15 +98,7 @@ __device__ __forceinline__ PixelGather gather_pixel(const GatherParams& g, float
     o.zf = emitter_distance(g, P.x, P.y, P.z);
     o.lit = depth_test(g, o.zf, o.z);
     // features (ordinary FP32 arithmetic; not part of the bit-exact contract)
-    const float lx = g.L[0] - P.x, ly = g.L[1] - P.y, lz = g.L[2] - P.z;
-    const float ce = (N.x * lx + N.y * ly + N.z * lz) / o.zf;
-    const float cxv = g.C[0] - P.x, cyv = g.C[1] - P.y, czv = g.C[2] - P.z;
-    const float cl = sqrtf(cxv * cxv + cyv * cyv + czv * czv);
-    const float cc = (N.x * cxv + N.y * cyv + N.z * czv) / cl;
-    o.f[0] = ce + g.r_hat;
-    o.f[1] = o.z / o.zf;
-    o.f[2] = o.z - o.zf;
-    o.f[3] = cc / P.w;
+    pixel_features(g, P, N, o.z, o.f);
     return o;
 }
 

@@ -27,6 +27,19 @@ int num_sms();
 // Message returned by nsm_last_error() on this thread.
 void set_last_error(const std::string& msg);
 
+}  // namespace nsm
+#include "../../include/nsm.h"
+namespace nsm {
+// Host-side validation helpers of the C ABI (nsm_api.cu).
+nsm_status fail(nsm_status s, const char* fmt, ...);
+nsm_status cuda_fail(cudaError_t e, const char* what);
+nsm_status check_device();
+nsm_status check_dev_ptr(const void* p, const char* name, size_t align, bool nullable = false);
+bool finite_all(const float* v, int n);
+nsm_status check_frame(const nsm_frame* f, bool need_mult4);
+GatherParams make_gather(const nsm_frame* f);
+size_t align_up(size_t v, size_t a);
+
 // Activation buffers of one inference, carved out of the caller's workspace.
 struct Activations {
     void* e0;   // [H/2][W/2][16]  pooled level-0 encoder output

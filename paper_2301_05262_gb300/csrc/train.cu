@@ -1,0 +1,626 @@
+// Training path: forward with level checkpoints, hand-written adjoint
+// (backward) with per-level recomputation, the Eq. 2 loss and Adam
+// (Sec. 3.3, Eq. 2; network of Sec. 3.5).
+//
+// All tensors here are FP32 NHWC batches [N][H][W][C].  The forward keeps
+// only the level boundaries (features, pooled level-0 output, level-1 skip,
+// pooled level-1 output, bottleneck output, level-1 decoder output); the
+// backward recomputes each level's 3x3 / 1x1 pre-activations from its
+// checkpoint right before back-propagating through it, so at most one
+// level's internals are alive at a time.
+//
+// Kernels (CUDA cores, FP32):
+//   conv_fwd   y = conv(x~) (+ b) (masked by m > 0), x~ = x, relu(x) or x (m_in > 0);
+//              also the data gradient, as a convolution with the transposed,
+//              flipped weights;
+//   conv_wgrad dW += sum_p g~(p) x~(p + tap), db += sum_p g~(p), partial sums per
+//              CTA in shared memory, one atomicAdd per weight per CTA;
+//   pooling, bilinear x2 and their adjoints, head, loss, Adam.
+#include <vector>
+
+#include "nsm_internal.h"
+#include "train_internal.h"
+
+namespace nsm {
+namespace tr {
+
+constexpr int TH = 8, TW = 16, NT = TH * TW;  // pixel tile of the conv kernels, one pixel per thread
+
+// ------------------------------------------------------------------ convolution
+// y[n,p,o] = b[o] + sum_{c,tap} Wc[o][c][tap] * xin(n, p + off(tap), c), zero padded,
+// xin = relu(x) if relu_in, x * (xm > 0) if xm, else x;  y *= (ym > 0) if ym.
+// Weights come as canonical OIHW (transpose_flip = 0) or as the weights of the
+// layer whose data gradient this is (transpose_flip = 1): Wc[o][c][tap] =
+// W[c][o][8 - tap].
+template <int CIN, int COUT, int K>
+__global__ void __launch_bounds__(NT) conv_fwd_kernel(const float* __restrict__ x, const float* __restrict__ xm,
+                                                      int relu_in, int N, int H, int W,
+                                                      const float* __restrict__ w, int transpose_flip,
+                                                      const float* __restrict__ b, const float* __restrict__ ym,
+                                                      float* __restrict__ y) {
+    constexpr int P = K / 2;
+    constexpr int RH = TH + 2 * P, RW = TW + 2 * P, PLANE = RH * RW;
+    extern __shared__ float sm[];
+    float* xs = sm;                       // [CIN][RH][RW]
+    float* ws = xs + CIN * PLANE;         // [tap][ci][co]
+    const int tid = threadIdx.x;
+    for (int i = tid; i < K * K * CIN * COUT; i += NT) {
+        const int co = i % COUT, ci = (i / COUT) % CIN, tap = i / (COUT * CIN);
+        ws[i] = transpose_flip ? __ldg(w + (static_cast<size_t>(ci) * COUT + co) * K * K + (K * K - 1 - tap))
+                               : __ldg(w + (static_cast<size_t>(co) * CIN + ci) * K * K + tap);
+    }
+    const int tx = (W + TW - 1) / TW, ty = (H + TH - 1) / TH;
+    const long long ntiles = static_cast<long long>(N) * tx * ty;
+    for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int n = static_cast<int>(t / (tx * ty));
+        const int r = static_cast<int>(t % (tx * ty));
+        const int y0 = (r / tx) * TH, x0 = (r % tx) * TW;
+        __syncthreads();
+        for (int i = tid; i < PLANE * CIN; i += NT) {
+            const int c = i % CIN, q = i / CIN;
+            const int gy = y0 - P + q / RW, gx = x0 - P + q % RW;
+            float v = 0.f;
+            if (gy >= 0 && gy < H && gx >= 0 && gx < W) {
+                const size_t idx = ((static_cast<size_t>(n) * H + gy) * W + gx) * CIN + c;
+                v = __ldg(x + idx);
+                if (relu_in) v = fmaxf(v, 0.f);
+                if (xm && !(__ldg(xm + idx) > 0.f)) v = 0.f;
+            }
+            xs[c * PLANE + q] = v;
+        }
+        __syncthreads();
+        const int ly = tid / TW, lx = tid % TW;
+        const int oy = y0 + ly, ox = x0 + lx;
+        float acc[COUT];
+#pragma unroll
+        for (int o = 0; o < COUT; ++o) acc[o] = b ? __ldg(b + o) : 0.f;
+#pragma unroll
+        for (int tap = 0; tap < K * K; ++tap) {
+            const float* xin = xs + (ly + tap / K) * RW + (lx + tap % K);
+            const float* wt = ws + tap * CIN * COUT;
+#pragma unroll 4
+            for (int c = 0; c < CIN; ++c) {
+                const float xv = xin[c * PLANE];
+#pragma unroll
+                for (int o = 0; o < COUT; ++o) acc[o] = fmaf(xv, wt[c * COUT + o], acc[o]);
+            }
+        }
+        if (oy < H && ox < W) {
+            const size_t base = ((static_cast<size_t>(n) * H + oy) * W + ox) * COUT;
+#pragma unroll
+            for (int o = 0; o < COUT; ++o) {
+                float v = acc[o];
+                if (ym && !(__ldg(ym + base + o) > 0.f)) v = 0.f;
+                y[base + o] = v;
+            }
+        }
+    }
+}
+
+// dW[o][c][tap] += sum_p g~[p][o] xin[p + off(tap)][c];  db[o] += sum_p g~[p][o]
+// g~ = g * (gm > 0) if gm.  Each CTA keeps the partial sums of all weights in
+// shared memory over the tiles it visits, then adds them to dW / db once.
+template <int CIN, int COUT, int K>
+__global__ void __launch_bounds__(NT) conv_wgrad_kernel(const float* __restrict__ x, int relu_in,
+                                                        const float* __restrict__ g, const float* __restrict__ gm,
+                                                        int N, int H, int W, float* __restrict__ dW,
+                                                        float* __restrict__ db) {
+    constexpr int P = K / 2;
+    constexpr int RH = TH + 2 * P, RW = TW + 2 * P, PLANE = RH * RW;
+    constexpr int NW = COUT * CIN * K * K;
+    extern __shared__ float sm[];
+    float* xs = sm;                 // [CIN][RH][RW]
+    float* gs = xs + CIN * PLANE;   // [COUT][TH*TW]
+    float* acc = gs + COUT * NT;    // [NW + COUT]
+    const int tid = threadIdx.x;
+    for (int i = tid; i < NW + COUT; i += NT) acc[i] = 0.f;
+    const int tx = (W + TW - 1) / TW, ty = (H + TH - 1) / TH;
+    const long long ntiles = static_cast<long long>(N) * tx * ty;
+    for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int n = static_cast<int>(t / (tx * ty));
+        const int r = static_cast<int>(t % (tx * ty));
+        const int y0 = (r / tx) * TH, x0 = (r % tx) * TW;
+        __syncthreads();
+        for (int i = tid; i < PLANE * CIN; i += NT) {
+            const int c = i % CIN, q = i / CIN;
+            const int gy = y0 - P + q / RW, gx = x0 - P + q % RW;
+            float v = 0.f;
+            if (gy >= 0 && gy < H && gx >= 0 && gx < W) {
+                v = __ldg(x + ((static_cast<size_t>(n) * H + gy) * W + gx) * CIN + c);
+                if (relu_in) v = fmaxf(v, 0.f);
+            }
+            xs[c * PLANE + q] = v;
+        }
+        for (int i = tid; i < NT * COUT; i += NT) {
+            const int o = i % COUT, q = i / COUT;
+            const int gy = y0 + q / TW, gx = x0 + q % TW;
+            float v = 0.f;
+            if (gy < H && gx < W) {
+                const size_t idx = ((static_cast<size_t>(n) * H + gy) * W + gx) * COUT + o;
+                v = __ldg(g + idx);
+                if (gm && !(__ldg(gm + idx) > 0.f)) v = 0.f;
+            }
+            gs[o * NT + q] = v;
+        }
+        __syncthreads();
+        for (int e = tid; e < NW; e += NT) {
+            const int tap = e % (K * K);
+            const int c = (e / (K * K)) % CIN;
+            const int o = e / (K * K * CIN);
+            const float* xp = xs + c * PLANE + (tap / K) * RW + (tap % K);
+            const float* gp = gs + o * NT;
+            float s = 0.f;
+#pragma unroll 4
+            for (int q = 0; q < NT; ++q) s = fmaf(gp[q], xp[(q / TW) * RW + (q % TW)], s);
+            acc[e] += s;
+        }
+        for (int o = tid; o < COUT; o += NT) {
+            float s = 0.f;
+            for (int q = 0; q < NT; ++q) s += gs[o * NT + q];
+            acc[NW + o] += s;
+        }
+    }
+    __syncthreads();
+    for (int e = tid; e < NW; e += NT) atomicAdd(dW + e, acc[e]);
+    if (db)
+        for (int o = tid; o < COUT; o += NT) atomicAdd(db + o, acc[NW + o]);
+}
+
+template <int CIN, int COUT, int K>
+cudaError_t conv_fwd(const float* x, const float* xm, int relu_in, int N, int H, int W, const float* w, int tf,
+                     const float* b, const float* ym, float* y, cudaStream_t st) {
+    constexpr int P = K / 2;
+    const size_t smem = sizeof(float) * (CIN * (TH + 2 * P) * (TW + 2 * P) + K * K * CIN * COUT);
+    auto kern = conv_fwd_kernel<CIN, COUT, K>;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    const long long tiles = static_cast<long long>(N) * ((W + TW - 1) / TW) * ((H + TH - 1) / TH);
+    if (tiles == 0) return cudaSuccess;
+    const long long cap = static_cast<long long>(num_sms()) * 4;
+    kern<<<static_cast<int>(tiles < cap ? tiles : cap), NT, smem, st>>>(x, xm, relu_in, N, H, W, w, tf, b, ym, y);
+    return cudaGetLastError();
+}
+
+template <int CIN, int COUT, int K>
+cudaError_t conv_wgrad(const float* x, int relu_in, const float* g, const float* gm, int N, int H, int W, float* dW,
+                       float* db, cudaStream_t st) {
+    constexpr int P = K / 2;
+    const size_t smem = sizeof(float) * (CIN * (TH + 2 * P) * (TW + 2 * P) + COUT * NT + COUT * CIN * K * K + COUT);
+    auto kern = conv_wgrad_kernel<CIN, COUT, K>;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    const long long tiles = static_cast<long long>(N) * ((W + TW - 1) / TW) * ((H + TH - 1) / TH);
+    if (tiles == 0) return cudaSuccess;
+    const long long cap = static_cast<long long>(num_sms()) * 2;
+    kern<<<static_cast<int>(tiles < cap ? tiles : cap), NT, smem, st>>>(x, relu_in, g, gm, N, H, W, dW, db);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ pooling / upsampling
+// y[n,Y,X,c] = 1/4 sum of relu?(x) over the 2x2 block; H, W of x even
+__global__ void pool_fwd_kernel(const float* __restrict__ x, int relu_in, int N, int H, int W, int C,
+                                float* __restrict__ y) {
+    const int Ho = H / 2, Wo = W / 2;
+    const size_t total = static_cast<size_t>(N) * Ho * Wo * C;
+    for (size_t i = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; i < total;
+         i += static_cast<size_t>(gridDim.x) * blockDim.x) {
+        const int c = static_cast<int>(i % C);
+        size_t q = i / C;
+        const int X = static_cast<int>(q % Wo); q /= Wo;
+        const int Y = static_cast<int>(q % Ho);
+        const int n = static_cast<int>(q / Ho);
+        float s = 0.f;
+        for (int dy = 0; dy < 2; ++dy)
+            for (int dx = 0; dx < 2; ++dx) {
+                float v = x[((static_cast<size_t>(n) * H + 2 * Y + dy) * W + 2 * X + dx) * C + c];
+                if (relu_in) v = fmaxf(v, 0.f);
+                s += v;
+            }
+        y[i] = 0.25f * s;
+    }
+}
+
+// gx[n,y,x,c] (+)= 1/4 gy[n,y/2,x/2,c]
+__global__ void pool_adj_kernel(const float* __restrict__ gy, int N, int H, int W, int C, int accumulate,
+                                float* __restrict__ gx) {
+    const size_t total = static_cast<size_t>(N) * H * W * C;
+    for (size_t i = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; i < total;
+         i += static_cast<size_t>(gridDim.x) * blockDim.x) {
+        const int c = static_cast<int>(i % C);
+        size_t q = i / C;
+        const int x = static_cast<int>(q % W); q /= W;
+        const int y = static_cast<int>(q % H);
+        const int n = static_cast<int>(q / H);
+        const float v = 0.25f * gy[((static_cast<size_t>(n) * (H / 2) + y / 2) * (W / 2) + x / 2) * C + c];
+        gx[i] = accumulate ? gx[i] + v : v;
+    }
+}
+
+// y[n,y,x,c] = bilinear x2 of lo (H/2 x W/2) (+ skip[n,y,x,c])
+__global__ void up_fwd_kernel(const float* __restrict__ lo, const float* __restrict__ skip, int N, int H, int W, int C,
+                              float* __restrict__ y) {
+    const int Hl = H / 2, Wl = W / 2;
+    const size_t total = static_cast<size_t>(N) * H * W * C;
+    for (size_t i = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; i < total;
+         i += static_cast<size_t>(gridDim.x) * blockDim.x) {
+        const int c = static_cast<int>(i % C);
+        size_t q = i / C;
+        const int x = static_cast<int>(q % W); q /= W;
+        const int yy = static_cast<int>(q % H);
+        const int n = static_cast<int>(q / H);
+        const BilinTap ty = bilin_tap(yy, Hl), tx = bilin_tap(x, Wl);
+        auto L = [&](int a, int b2) { return lo[((static_cast<size_t>(n) * Hl + a) * Wl + b2) * C + c]; };
+        const float r0 = L(ty.i0, tx.i0) * tx.w0 + L(ty.i0, tx.i1) * tx.w1;
+        const float r1 = L(ty.i1, tx.i0) * tx.w0 + L(ty.i1, tx.i1) * tx.w1;
+        float v = r0 * ty.w0 + r1 * ty.w1;
+        if (skip) v += skip[i];
+        y[i] = v;
+    }
+}
+
+// Adjoint of the bilinear x2 upsampling in gather form: each coarse pixel
+// sums the fine-grid cotangents of the (at most 4 x 4) fine pixels whose taps
+// reach it, with those taps' weights.
+__global__ void up_adj_kernel(const float* __restrict__ g, int N, int H, int W, int C, float* __restrict__ glo) {
+    const int Hl = H / 2, Wl = W / 2;
+    const size_t total = static_cast<size_t>(N) * Hl * Wl * C;
+    for (size_t i = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; i < total;
+         i += static_cast<size_t>(gridDim.x) * blockDim.x) {
+        const int c = static_cast<int>(i % C);
+        size_t q = i / C;
+        const int X = static_cast<int>(q % Wl); q /= Wl;
+        const int Y = static_cast<int>(q % Hl);
+        const int n = static_cast<int>(q / Hl);
+        float s = 0.f;
+        for (int yy = 2 * Y - 2; yy <= 2 * Y + 3; ++yy) {
+            if (yy < 0 || yy >= H) continue;
+            const BilinTap ty = bilin_tap(yy, Hl);
+            const float wy = (ty.i0 == Y ? ty.w0 : 0.f) + (ty.i1 == Y ? ty.w1 : 0.f);
+            if (wy == 0.f) continue;
+            for (int xx = 2 * X - 2; xx <= 2 * X + 3; ++xx) {
+                if (xx < 0 || xx >= W) continue;
+                const BilinTap tx = bilin_tap(xx, Wl);
+                const float wx = (tx.i0 == X ? tx.w0 : 0.f) + (tx.i1 == X ? tx.w1 : 0.f);
+                if (wx == 0.f) continue;
+                s += wy * wx * g[((static_cast<size_t>(n) * H + yy) * W + xx) * C + c];
+            }
+        }
+        glo[i] = s;
+    }
+}
+
+__global__ void relu_copy_kernel(const float* __restrict__ x, size_t n, float* __restrict__ y) {
+    for (size_t i = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; i < n;
+         i += static_cast<size_t>(gridDim.x) * blockDim.x)
+        y[i] = fmaxf(x[i], 0.f);
+}
+
+__global__ void add_kernel(float* __restrict__ y, const float* __restrict__ x, size_t n) {
+    for (size_t i = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; i < n;
+         i += static_cast<size_t>(gridDim.x) * blockDim.x)
+        y[i] += x[i];
+}
+
+// ------------------------------------------------------------------ head, loss
+// vis = sigmoid(bh + sum_c wh[c] relu(a1[c])), C = 16
+__global__ void head_fwd_kernel(const float* __restrict__ a1, const float* __restrict__ wh, size_t npx,
+                                float* __restrict__ vis) {
+    for (size_t p = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; p < npx;
+         p += static_cast<size_t>(gridDim.x) * blockDim.x) {
+        float l = __ldg(wh + 16);
+#pragma unroll
+        for (int c = 0; c < 16; ++c) l = fmaf(__ldg(wh + c), fmaxf(a1[p * 16 + c], 0.f), l);
+        vis[p] = sigmoidf_acc(l);
+    }
+}
+
+// g_logit = g_vis vis (1 - vis); g_a1[c] = wh[c] g_logit (a1[c] > 0);
+// dwh[c] += sum g_logit relu(a1[c]); dbh += sum g_logit
+__global__ void head_bwd_kernel(const float* __restrict__ a1, const float* __restrict__ vis,
+                                const float* __restrict__ gvis, const float* __restrict__ wh, size_t npx,
+                                float* __restrict__ ga1, float* __restrict__ dwh) {
+    __shared__ float red[17][8];
+    float part[17];
+#pragma unroll
+    for (int c = 0; c < 17; ++c) part[c] = 0.f;
+    for (size_t p = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; p < npx;
+         p += static_cast<size_t>(gridDim.x) * blockDim.x) {
+        const float v = vis[p];
+        const float gl = gvis[p] * v * (1.f - v);
+#pragma unroll
+        for (int c = 0; c < 16; ++c) {
+            const float a = a1[p * 16 + c];
+            ga1[p * 16 + c] = (a > 0.f) ? __ldg(wh + c) * gl : 0.f;
+            part[c] = fmaf(gl, fmaxf(a, 0.f), part[c]);
+        }
+        part[16] += gl;
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int c = 0; c < 17; ++c) {
+        float s = part[c];
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) red[c][warp] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x < 17) {
+        float s = 0.f;
+        for (int w = 0; w < static_cast<int>(blockDim.x / 32); ++w) s += red[threadIdx.x][w];
+        atomicAdd(dwh + threadIdx.x, s);
+    }
+}
+
+// Eq. 2 with the L1 term: per item b, alpha mean|x0 - target| + sum_i alpha mean|x0 - x_i|
+// (x_i detached), averaged over the B items.  vis is [T][B][npx] (instance 0
+// first).  Writes g_vis for x0 ([B][npx]) and adds the loss to *loss.
+__global__ void loss_l1_kernel(const float* __restrict__ vis, const float* __restrict__ target, int B, int T,
+                               size_t npx, float alpha, float* __restrict__ gvis, float* __restrict__ loss) {
+    __shared__ float red[8];
+    const float scale = alpha / (static_cast<float>(npx) * B);
+    float part = 0.f;
+    const size_t total = static_cast<size_t>(B) * npx;
+    for (size_t i = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; i < total;
+         i += static_cast<size_t>(gridDim.x) * blockDim.x) {
+        const float x0 = vis[i];
+        float d = x0 - target[i];
+        float g = (d > 0.f) ? 1.f : ((d < 0.f) ? -1.f : 0.f);
+        float l = fabsf(d);
+        for (int t = 1; t < T; ++t) {
+            const float xi = vis[static_cast<size_t>(t) * total + i];
+            d = x0 - xi;
+            g += (d > 0.f) ? 1.f : ((d < 0.f) ? -1.f : 0.f);
+            l += fabsf(d);
+        }
+        gvis[i] = scale * g;
+        part += l;
+    }
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = part;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float s = 0.f;
+        for (int w = 0; w < static_cast<int>(blockDim.x / 32); ++w) s += red[w];
+        atomicAdd(loss, s * scale);
+    }
+}
+
+// Adam (Kingma & Ba 2015) with bias correction; step >= 1
+__global__ void adam_kernel(float* __restrict__ theta, const float* __restrict__ grad, float* __restrict__ m,
+                            float* __restrict__ v, size_t n, float lr, float b1, float b2, float eps, float c1,
+                            float c2) {
+    for (size_t i = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; i < n;
+         i += static_cast<size_t>(gridDim.x) * blockDim.x) {
+        const float g = grad[i];
+        const float mi = b1 * m[i] + (1.f - b1) * g;
+        const float vi = b2 * v[i] + (1.f - b2) * g * g;
+        m[i] = mi;
+        v[i] = vi;
+        theta[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    }
+}
+
+// Features of a batch of views, NHWC [N][H][W][4]; one GatherParams per view.
+__global__ void features_batch_kernel(const GatherParams* __restrict__ gp, int N, int H, int W,
+                                      float* __restrict__ feat) {
+    const size_t npx = static_cast<size_t>(H) * W;
+    const size_t total = npx * N;
+    for (size_t i = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; i < total;
+         i += static_cast<size_t>(gridDim.x) * blockDim.x) {
+        const int n = static_cast<int>(i / npx);
+        const size_t p = i % npx;
+        const GatherParams& g = gp[n];
+        const float4 P = __ldg(g.pos4 + p);
+        const float4 Nn = __ldg(g.nrm4 + p);
+        PixelGather o = gather_pixel(g, P, Nn);
+        reinterpret_cast<float4*>(feat)[i] = make_float4(o.f[0], o.f[1], o.f[2], o.f[3]);
+    }
+}
+
+static int ew_grid(size_t n) {
+    const size_t b = (n + 255) / 256;
+    const size_t cap = static_cast<size_t>(num_sms()) * 8;
+    return static_cast<int>(b < 1 ? 1 : (b < cap ? b : cap));
+}
+
+// ------------------------------------------------------------------ network driver
+struct Level {  // offsets into the canonical vector
+    const float *w3, *b3, *w1, *b1;
+    float *dw3, *db3, *dw1, *db1;
+};
+
+static Level level(const float* th, float* gr, int l3, int l1) {
+    const LayerOffsets o = layer_offsets();
+    return {th + o.w[l3], th + o.b[l3], th + o.w[l1], th + o.b[l1],
+            gr ? gr + o.w[l3] : nullptr, gr ? gr + o.b[l3] : nullptr,
+            gr ? gr + o.w[l1] : nullptr, gr ? gr + o.b[l1] : nullptr};
+}
+
+#define NSM_TRY(x) do { cudaError_t _e = (x); if (_e != cudaSuccess) return _e; } while (0)
+
+size_t workspace_floats(int N, int Nb, int H, int W) {
+    const size_t p0 = static_cast<size_t>(H) * W, p1 = p0 / 4, p2 = p0 / 16;
+    size_t f = 0;
+    f += N * p0 * 4;            // feat
+    f += N * p1 * 16;           // e0
+    f += N * p1 * 32;           // s1
+    f += N * p2 * 32;           // p1
+    f += N * p2 * 32;           // bo
+    f += N * p1 * 16;           // d1
+    f += N * p0;                // vis
+    f += Nb * p0;               // g_vis
+    // per-level scratch (largest level: level 0): x_in, a3, a1, g_a1, g_a3, g_x, g_low, g_skip
+    f += Nb * p0 * 16 * 6 + Nb * p1 * 32 * 2;
+    f += Nb * p0 * 16;          // conv scratch (level-0 1x1 input gradient)
+    return f + 64;
+}
+
+Buffers carve(float* base, int N, int Nb, int H, int W) {
+    const size_t p0 = static_cast<size_t>(H) * W, p1 = p0 / 4, p2 = p0 / 16;
+    Buffers b{};
+    float* q = base;
+    auto take = [&](size_t n) { float* r = q; q += (n + 63) / 64 * 64; return r; };
+    b.feat = take(N * p0 * 4);
+    b.e0 = take(N * p1 * 16);
+    b.s1 = take(N * p1 * 32);
+    b.p1 = take(N * p2 * 32);
+    b.bo = take(N * p2 * 32);
+    b.d1 = take(N * p1 * 16);
+    b.vis = take(N * p0);
+    b.gvis = take(Nb * p0);
+    b.xin = take(Nb * p0 * 16);
+    b.a3 = take(Nb * p0 * 16);
+    b.a1 = take(Nb * p0 * 16);
+    b.ga1 = take(Nb * p0 * 16);
+    b.ga3 = take(Nb * p0 * 16);
+    b.gx = take(Nb * p0 * 16);
+    b.glo = take(Nb * p1 * 32);
+    b.gskip = take(Nb * p1 * 32);
+    b.gtmp = take(Nb * p0 * 16);
+    return b;
+}
+
+// Forward of N views (features already in b.feat) keeping the level
+// checkpoints; uses xin / a3 / a1 of the scratch, sized for Nb views, in
+// chunks of Nb views.
+cudaError_t forward(const float* th, const Buffers& b, int N, int Nb, int H, int W, cudaStream_t st) {
+    const size_t p0 = static_cast<size_t>(H) * W, p1 = p0 / 4, p2 = p0 / 16;
+    const int H1 = H / 2, W1 = W / 2, H2 = H / 4, W2 = W / 4;
+    const LayerOffsets o = layer_offsets();
+    for (int n0 = 0; n0 < N; n0 += Nb) {
+        const int n = (N - n0) < Nb ? (N - n0) : Nb;
+        const float* feat = b.feat + n0 * p0 * 4;
+        float* e0 = b.e0 + n0 * p1 * 16;
+        float* s1 = b.s1 + n0 * p1 * 32;
+        float* pp1 = b.p1 + n0 * p2 * 32;
+        float* bo = b.bo + n0 * p2 * 32;
+        float* d1 = b.d1 + n0 * p1 * 16;
+        float* vis = b.vis + n0 * p0;
+        Level L;
+        // level 0 encoder
+        L = level(th, nullptr, ENC0_3, ENC0_1);
+        NSM_TRY((conv_fwd<4, 16, 3>(feat, nullptr, 0, n, H, W, L.w3, 0, L.b3, nullptr, b.a3, st)));
+        NSM_TRY((conv_fwd<16, 16, 1>(b.a3, nullptr, 1, n, H, W, L.w1, 0, L.b1, nullptr, b.a1, st)));
+        pool_fwd_kernel<<<ew_grid(n * p1 * 16), 256, 0, st>>>(b.a1, 1, n, H, W, 16, e0);
+        // level 1 encoder
+        L = level(th, nullptr, ENC1_3, ENC1_1);
+        NSM_TRY((conv_fwd<16, 32, 3>(e0, nullptr, 0, n, H1, W1, L.w3, 0, L.b3, nullptr, b.a3, st)));
+        NSM_TRY((conv_fwd<32, 32, 1>(b.a3, nullptr, 1, n, H1, W1, L.w1, 0, L.b1, nullptr, b.a1, st)));
+        pool_fwd_kernel<<<ew_grid(n * p2 * 32), 256, 0, st>>>(b.a1, 1, n, H1, W1, 32, pp1);
+        // the decoder skip is relu(a1) of level 1
+        relu_copy_kernel<<<ew_grid(n * p1 * 32), 256, 0, st>>>(b.a1, n * p1 * 32, s1);
+        // bottleneck
+        L = level(th, nullptr, BOTT_3, BOTT_1);
+        NSM_TRY((conv_fwd<32, 64, 3>(pp1, nullptr, 0, n, H2, W2, L.w3, 0, L.b3, nullptr, b.a3, st)));
+        NSM_TRY((conv_fwd<64, 32, 1>(b.a3, nullptr, 1, n, H2, W2, L.w1, 0, L.b1, nullptr, b.a1, st)));
+        relu_copy_kernel<<<ew_grid(n * p2 * 32), 256, 0, st>>>(b.a1, n * p2 * 32, bo);
+        // level 1 decoder
+        L = level(th, nullptr, DEC1_3, DEC1_1);
+        up_fwd_kernel<<<ew_grid(n * p1 * 32), 256, 0, st>>>(bo, s1, n, H1, W1, 32, b.xin);
+        NSM_TRY((conv_fwd<32, 32, 3>(b.xin, nullptr, 0, n, H1, W1, L.w3, 0, L.b3, nullptr, b.a3, st)));
+        NSM_TRY((conv_fwd<32, 16, 1>(b.a3, nullptr, 1, n, H1, W1, L.w1, 0, L.b1, nullptr, b.a1, st)));
+        relu_copy_kernel<<<ew_grid(n * p1 * 16), 256, 0, st>>>(b.a1, n * p1 * 16, d1);
+        // level 0 decoder + head
+        L = level(th, nullptr, DEC0_3, DEC0_1);
+        up_fwd_kernel<<<ew_grid(n * p0 * 16), 256, 0, st>>>(d1, nullptr, n, H, W, 16, b.xin);
+        NSM_TRY((conv_fwd<16, 16, 3>(b.xin, nullptr, 0, n, H, W, L.w3, 0, L.b3, nullptr, b.a3, st)));
+        NSM_TRY((conv_fwd<16, 16, 1>(b.a3, nullptr, 1, n, H, W, L.w1, 0, L.b1, nullptr, b.a1, st)));
+        head_fwd_kernel<<<ew_grid(n * p0), 256, 0, st>>>(b.a1, th + o.w[HEAD], n * p0, vis);
+        NSM_TRY(cudaGetLastError());
+    }
+    return cudaSuccess;
+}
+
+// Backward of the first Nb views (cotangent b.gvis) into grad (canonical
+// layout, accumulated), recomputing each level from its checkpoint.
+// With gfeat != nullptr also the feature gradient [Nb][H][W][4].
+cudaError_t backward(const float* th, float* grad, const Buffers& b, int Nb, int H, int W, float* gfeat,
+                     cudaStream_t st) {
+    const size_t p0 = static_cast<size_t>(H) * W, p1 = p0 / 4, p2 = p0 / 16;
+    const int H1 = H / 2, W1 = W / 2, H2 = H / 4, W2 = W / 4;
+    const LayerOffsets o = layer_offsets();
+    const int n = Nb;
+    Level L;
+    // ---- level 0 decoder + head: recompute x = up(d1), a3, a1
+    L = level(th, grad, DEC0_3, DEC0_1);
+    up_fwd_kernel<<<ew_grid(n * p0 * 16), 256, 0, st>>>(b.d1, nullptr, n, H, W, 16, b.xin);
+    NSM_TRY((conv_fwd<16, 16, 3>(b.xin, nullptr, 0, n, H, W, L.w3, 0, L.b3, nullptr, b.a3, st)));
+    NSM_TRY((conv_fwd<16, 16, 1>(b.a3, nullptr, 1, n, H, W, L.w1, 0, L.b1, nullptr, b.a1, st)));
+    head_bwd_kernel<<<ew_grid(n * p0), 256, 0, st>>>(b.a1, b.vis, b.gvis, th + o.w[HEAD], n * p0, b.ga1,
+                                                     grad + o.w[HEAD]);
+    NSM_TRY((conv_wgrad<16, 16, 1>(b.a3, 1, b.ga1, nullptr, n, H, W, L.dw1, L.db1, st)));
+    NSM_TRY((conv_fwd<16, 16, 1>(b.ga1, nullptr, 0, n, H, W, L.w1, 1, nullptr, b.a3, b.ga3, st)));
+    NSM_TRY((conv_wgrad<16, 16, 3>(b.xin, 0, b.ga3, nullptr, n, H, W, L.dw3, L.db3, st)));
+    NSM_TRY((conv_fwd<16, 16, 3>(b.ga3, nullptr, 0, n, H, W, L.w3, 1, nullptr, nullptr, b.gx, st)));
+    up_adj_kernel<<<ew_grid(n * p1 * 16), 256, 0, st>>>(b.gx, n, H, W, 16, b.glo);  // g d1 [n][H1][W1][16]
+    // ---- level 1 decoder: recompute x = up(bo) + s1, a3, a1
+    L = level(th, grad, DEC1_3, DEC1_1);
+    up_fwd_kernel<<<ew_grid(n * p1 * 32), 256, 0, st>>>(b.bo, b.s1, n, H1, W1, 32, b.xin);
+    NSM_TRY((conv_fwd<32, 32, 3>(b.xin, nullptr, 0, n, H1, W1, L.w3, 0, L.b3, nullptr, b.a3, st)));
+    NSM_TRY((conv_fwd<32, 16, 1>(b.a3, nullptr, 1, n, H1, W1, L.w1, 0, L.b1, nullptr, b.a1, st)));
+    // g_a1 = g_d1 (a1 > 0)
+    NSM_TRY((conv_wgrad<32, 16, 1>(b.a3, 1, b.glo, b.a1, n, H1, W1, L.dw1, L.db1, st)));
+    NSM_TRY((conv_fwd<16, 32, 1>(b.glo, b.a1, 0, n, H1, W1, L.w1, 1, nullptr, b.a3, b.ga3, st)));
+    NSM_TRY((conv_wgrad<32, 32, 3>(b.xin, 0, b.ga3, nullptr, n, H1, W1, L.dw3, L.db3, st)));
+    NSM_TRY((conv_fwd<32, 32, 3>(b.ga3, nullptr, 0, n, H1, W1, L.w3, 1, nullptr, nullptr, b.gskip, st)));  // g x1
+    up_adj_kernel<<<ew_grid(n * p2 * 32), 256, 0, st>>>(b.gskip, n, H1, W1, 32, b.glo);  // g bo [n][H2][W2][32]
+    // ---- bottleneck: recompute a3 = conv3(p1), a1
+    L = level(th, grad, BOTT_3, BOTT_1);
+    NSM_TRY((conv_fwd<32, 64, 3>(b.p1, nullptr, 0, n, H2, W2, L.w3, 0, L.b3, nullptr, b.a3, st)));
+    NSM_TRY((conv_fwd<64, 32, 1>(b.a3, nullptr, 1, n, H2, W2, L.w1, 0, L.b1, nullptr, b.a1, st)));
+    NSM_TRY((conv_wgrad<64, 32, 1>(b.a3, 1, b.glo, b.a1, n, H2, W2, L.dw1, L.db1, st)));
+    NSM_TRY((conv_fwd<32, 64, 1>(b.glo, b.a1, 0, n, H2, W2, L.w1, 1, nullptr, b.a3, b.ga3, st)));
+    NSM_TRY((conv_wgrad<32, 64, 3>(b.p1, 0, b.ga3, nullptr, n, H2, W2, L.dw3, L.db3, st)));
+    NSM_TRY((conv_fwd<64, 32, 3>(b.ga3, nullptr, 0, n, H2, W2, L.w3, 1, nullptr, nullptr, b.gx, st)));  // g p1
+    // ---- level 1 encoder: g_h1 = pool_adj(g p1) + g s1 ; recompute a3 = conv3(e0), a1
+    L = level(th, grad, ENC1_3, ENC1_1);
+    pool_adj_kernel<<<ew_grid(n * p1 * 32), 256, 0, st>>>(b.gx, n, H1, W1, 32, 0, b.glo);
+    add_kernel<<<ew_grid(n * p1 * 32), 256, 0, st>>>(b.glo, b.gskip, n * p1 * 32);
+    NSM_TRY((conv_fwd<16, 32, 3>(b.e0, nullptr, 0, n, H1, W1, L.w3, 0, L.b3, nullptr, b.a3, st)));
+    NSM_TRY((conv_fwd<32, 32, 1>(b.a3, nullptr, 1, n, H1, W1, L.w1, 0, L.b1, nullptr, b.a1, st)));
+    NSM_TRY((conv_wgrad<32, 32, 1>(b.a3, 1, b.glo, b.a1, n, H1, W1, L.dw1, L.db1, st)));
+    NSM_TRY((conv_fwd<32, 32, 1>(b.glo, b.a1, 0, n, H1, W1, L.w1, 1, nullptr, b.a3, b.ga3, st)));
+    NSM_TRY((conv_wgrad<16, 32, 3>(b.e0, 0, b.ga3, nullptr, n, H1, W1, L.dw3, L.db3, st)));
+    NSM_TRY((conv_fwd<32, 16, 3>(b.ga3, nullptr, 0, n, H1, W1, L.w3, 1, nullptr, nullptr, b.gx, st)));  // g e0
+    // ---- level 0 encoder: g_h1 = pool_adj(g e0); recompute a3 = conv3(feat), a1
+    L = level(th, grad, ENC0_3, ENC0_1);
+    pool_adj_kernel<<<ew_grid(n * p0 * 16), 256, 0, st>>>(b.gx, n, H, W, 16, 0, b.gtmp);
+    NSM_TRY((conv_fwd<4, 16, 3>(b.feat, nullptr, 0, n, H, W, L.w3, 0, L.b3, nullptr, b.a3, st)));
+    NSM_TRY((conv_fwd<16, 16, 1>(b.a3, nullptr, 1, n, H, W, L.w1, 0, L.b1, nullptr, b.a1, st)));
+    NSM_TRY((conv_wgrad<16, 16, 1>(b.a3, 1, b.gtmp, b.a1, n, H, W, L.dw1, L.db1, st)));
+    NSM_TRY((conv_fwd<16, 16, 1>(b.gtmp, b.a1, 0, n, H, W, L.w1, 1, nullptr, b.a3, b.ga3, st)));
+    NSM_TRY((conv_wgrad<4, 16, 3>(b.feat, 0, b.ga3, nullptr, n, H, W, L.dw3, L.db3, st)));
+    if (gfeat) NSM_TRY((conv_fwd<16, 4, 3>(b.ga3, nullptr, 0, n, H, W, L.w3, 1, nullptr, nullptr, gfeat, st)));
+    return cudaGetLastError();
+}
+
+cudaError_t features_batch(const GatherParams* dev_params, int N, int H, int W, float* feat, cudaStream_t st) {
+    const size_t total = static_cast<size_t>(N) * H * W;
+    if (total == 0) return cudaSuccess;
+    features_batch_kernel<<<ew_grid(total), 256, 0, st>>>(dev_params, N, H, W, feat);
+    return cudaGetLastError();
+}
+
+cudaError_t loss_l1(const float* vis, const float* target, int B, int T, size_t npx, float alpha, float* gvis,
+                    float* loss, cudaStream_t st) {
+    loss_l1_kernel<<<ew_grid(static_cast<size_t>(B) * npx), 256, 0, st>>>(vis, target, B, T, npx, alpha, gvis, loss);
+    return cudaGetLastError();
+}
+
+cudaError_t adam(float* theta, const float* grad, float* m, float* v, size_t n, float lr, float b1, float b2,
+                 float eps, int step, cudaStream_t st) {
+    const float c1 = 1.f - powf(b1, static_cast<float>(step));
+    const float c2 = 1.f - powf(b2, static_cast<float>(step));
+    adam_kernel<<<ew_grid(n), 256, 0, st>>>(theta, grad, m, v, n, lr, b1, b2, eps, c1, c2);
+    return cudaGetLastError();
+}
+
+}  // namespace tr
+}  // namespace nsm

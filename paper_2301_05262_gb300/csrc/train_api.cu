@@ -1,0 +1,176 @@
+// C ABI of the backward and training entry points (include/nsm.h).
+#include <vector>
+
+#include "nsm_internal.h"
+#include "train_internal.h"
+
+struct nsm_train_state {
+    int device;
+    int max_B, max_T, H, W;
+    size_t n;            // parameters
+    float* theta;        // FP32 master weights
+    float* m;            // Adam first moment
+    float* v;            // Adam second moment
+    float* grad;         // gradient of the last step
+    float* loss;         // device scalar
+    nsm::GatherParams* gp;  // per-instance gather parameters (device)
+    float* work;         // FP32 workspace
+    int step;
+};
+
+namespace nsm {
+
+static size_t backward_floats(int H, int W) { return tr::workspace_floats(1, 1, H, W); }
+
+}  // namespace nsm
+
+using namespace nsm;
+
+extern "C" {
+
+size_t nsm_backward_workspace_bytes(int H, int W) {
+    if (H <= 0 || W <= 0) return 0;
+    return align_up(sizeof(GatherParams), 256) + backward_floats(H, W) * sizeof(float);
+}
+
+nsm_status nsm_backward(nsm_ctx* ctx, const nsm_frame* frame, const float* dev_params, const float* grad_vis,
+                        float* grad_params, float* grad_feat, float* vis_out, void* workspace,
+                        size_t workspace_bytes, void* stream) {
+    if (!ctx) return fail(NSM_ERR_INVALID_ARG, "ctx is NULL");
+    nsm_status s = check_frame(frame, true);
+    if (s != NSM_OK) return s;
+    const int H = frame->H, W = frame->W;
+    if (static_cast<size_t>(H) * W == 0) return NSM_OK;
+    if ((s = check_dev_ptr(dev_params, "dev_params", 4)) != NSM_OK) return s;
+    if ((s = check_dev_ptr(grad_vis, "grad_vis", 4)) != NSM_OK) return s;
+    if ((s = check_dev_ptr(grad_params, "grad_params", 4)) != NSM_OK) return s;
+    if ((s = check_dev_ptr(grad_feat, "grad_feat", 4, true)) != NSM_OK) return s;
+    if ((s = check_dev_ptr(vis_out, "vis_out", 4, true)) != NSM_OK) return s;
+    const size_t need = nsm_backward_workspace_bytes(H, W);
+    if (!workspace || workspace_bytes < need)
+        return fail(NSM_ERR_WORKSPACE, "workspace of %zu bytes given, %zu needed", workspace_bytes, need);
+    if ((s = check_dev_ptr(workspace, "workspace", 256)) != NSM_OK) return s;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    GatherParams g = make_gather(frame);
+    GatherParams* dgp = static_cast<GatherParams*>(workspace);
+    float* base = reinterpret_cast<float*>(static_cast<char*>(workspace) + align_up(sizeof(GatherParams), 256));
+    cudaError_t e = cudaMemcpyAsync(dgp, &g, sizeof(g), cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(e, "upload gather parameters");
+    tr::Buffers b = tr::carve(base, 1, 1, H, W);
+    if ((e = tr::features_batch(dgp, 1, H, W, b.feat, st)) != cudaSuccess) return cuda_fail(e, "features");
+    if ((e = tr::forward(dev_params, b, 1, 1, H, W, st)) != cudaSuccess) return cuda_fail(e, "forward");
+    const size_t npx = static_cast<size_t>(H) * W;
+    if ((e = cudaMemcpyAsync(b.gvis, grad_vis, npx * 4, cudaMemcpyDeviceToDevice, st)) != cudaSuccess)
+        return cuda_fail(e, "copy cotangent");
+    if (vis_out && (e = cudaMemcpyAsync(vis_out, b.vis, npx * 4, cudaMemcpyDeviceToDevice, st)) != cudaSuccess)
+        return cuda_fail(e, "copy visibility");
+    if ((e = tr::backward(dev_params, grad_params, b, 1, H, W, grad_feat, st)) != cudaSuccess)
+        return cuda_fail(e, "backward");
+    return NSM_OK;
+}
+
+nsm_status nsm_train_state_create(nsm_ctx* ctx, const float* host_params, size_t n, int max_B, int max_T, int H,
+                                  int W, nsm_train_state** out) {
+    if (!ctx || !host_params || !out) return fail(NSM_ERR_INVALID_ARG, "ctx, host_params and out must be non-NULL");
+    *out = nullptr;
+    if (n != nsm_param_count()) return fail(NSM_ERR_SHAPE, "parameter vector has %zu floats, expected %zu", n, nsm_param_count());
+    if (max_B < 1 || max_T < 1 || H < 4 || W < 4 || (H % 4) || (W % 4) || H > 4096 || W > 4096)
+        return fail(NSM_ERR_SHAPE, "batch %d x %d of %d x %d crops not supported", max_B, max_T, H, W);
+    if (!finite_all(host_params, static_cast<int>(n))) return fail(NSM_ERR_INVALID_ARG, "parameters must be finite");
+    nsm_train_state* s = new nsm_train_state{};
+    cudaGetDevice(&s->device);
+    s->max_B = max_B; s->max_T = max_T; s->H = H; s->W = W; s->n = n;
+    const int N = max_B * max_T;
+    cudaError_t e = cudaSuccess;
+    auto alloc = [&](void** p, size_t bytes) { if (e == cudaSuccess) e = cudaMalloc(p, bytes); };
+    alloc(reinterpret_cast<void**>(&s->theta), n * 4);
+    alloc(reinterpret_cast<void**>(&s->m), n * 4);
+    alloc(reinterpret_cast<void**>(&s->v), n * 4);
+    alloc(reinterpret_cast<void**>(&s->grad), n * 4);
+    alloc(reinterpret_cast<void**>(&s->loss), 256);
+    alloc(reinterpret_cast<void**>(&s->gp), sizeof(GatherParams) * N);
+    alloc(reinterpret_cast<void**>(&s->work), tr::workspace_floats(N, max_B, H, W) * 4);
+    if (e == cudaSuccess) e = cudaMemcpy(s->theta, host_params, n * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(s->m, 0, n * 4);
+    if (e == cudaSuccess) e = cudaMemset(s->v, 0, n * 4);
+    if (e == cudaSuccess) e = cudaMemset(s->grad, 0, n * 4);
+    if (e != cudaSuccess) {
+        nsm_train_state_destroy(s);
+        return cuda_fail(e, "train state allocation");
+    }
+    *out = s;
+    return NSM_OK;
+}
+
+void nsm_train_state_destroy(nsm_train_state* s) {
+    if (!s) return;
+    cudaFree(s->theta); cudaFree(s->m); cudaFree(s->v); cudaFree(s->grad);
+    cudaFree(s->loss); cudaFree(s->gp); cudaFree(s->work);
+    delete s;
+}
+
+nsm_status nsm_train_step(nsm_ctx* ctx, nsm_train_state* s, const nsm_batch* bt, const nsm_train_cfg* cfg,
+                          float* loss_out, void* stream) {
+    if (!ctx || !s || !bt || !cfg) return fail(NSM_ERR_INVALID_ARG, "ctx, state, batch and cfg must be non-NULL");
+    if (bt->B < 1 || bt->T < 1 || bt->B > s->max_B || bt->T > s->max_T || bt->H != s->H || bt->W != s->W)
+        return fail(NSM_ERR_SHAPE, "batch %d x %d of %d x %d does not fit the state (%d x %d of %d x %d)", bt->B,
+                    bt->T, bt->H, bt->W, s->max_B, s->max_T, s->H, s->W);
+    if (bt->Hs < 1 || bt->Ws < 1 || bt->Hs > 16384 || bt->Ws > 16384) return fail(NSM_ERR_SHAPE, "bad shadow-map size");
+    if (!bt->lights || !bt->cameras) return fail(NSM_ERR_INVALID_ARG, "lights / cameras are NULL");
+    if (!(cfg->lr > 0.f) || !(cfg->alpha >= 0.f) || !(cfg->beta1 >= 0.f && cfg->beta1 < 1.f) ||
+        !(cfg->beta2 >= 0.f && cfg->beta2 < 1.f) || !(cfg->eps > 0.f))
+        return fail(NSM_ERR_INVALID_ARG, "bad training configuration");
+    nsm_status st;
+    if ((st = check_dev_ptr(bt->pos4, "batch.pos4", 16)) != NSM_OK) return st;
+    if ((st = check_dev_ptr(bt->nrm4, "batch.nrm4", 16)) != NSM_OK) return st;
+    if ((st = check_dev_ptr(bt->sm, "batch.sm", 4)) != NSM_OK) return st;
+    if ((st = check_dev_ptr(bt->target, "batch.target", 4)) != NSM_OK) return st;
+    if ((st = check_dev_ptr(loss_out, "loss_out", 4, true)) != NSM_OK) return st;
+    const int N = bt->B * bt->T, H = bt->H, W = bt->W;
+    const size_t npx = static_cast<size_t>(H) * W;
+    std::vector<GatherParams> gps(N);
+    for (int i = 0; i < N; ++i) {
+        nsm_frame f{};
+        f.H = H; f.W = W; f.Hs = bt->Hs; f.Ws = bt->Ws;
+        f.pos4 = bt->pos4 + static_cast<size_t>(i) * npx * 4;
+        f.nrm4 = bt->nrm4 + static_cast<size_t>(i) * npx * 4;
+        f.sm = bt->sm + static_cast<size_t>(i) * bt->Hs * bt->Ws;
+        f.light = bt->lights[i];
+        f.camera = bt->cameras[i];
+        if (!finite_all(f.light.view_proj, 16) || !finite_all(f.light.pos, 3) || !finite_all(f.camera.pos, 3))
+            return fail(NSM_ERR_INVALID_ARG, "instance %d: light / camera must be finite", i);
+        gps[i] = make_gather(&f);
+    }
+    cudaStream_t cs = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaMemcpyAsync(s->gp, gps.data(), sizeof(GatherParams) * N, cudaMemcpyHostToDevice, cs);
+    if (e != cudaSuccess) return cuda_fail(e, "upload gather parameters");
+    tr::Buffers b = tr::carve(s->work, N, bt->B, H, W);
+    if ((e = tr::features_batch(s->gp, N, H, W, b.feat, cs)) != cudaSuccess) return cuda_fail(e, "features");
+    if ((e = tr::forward(s->theta, b, N, bt->B, H, W, cs)) != cudaSuccess) return cuda_fail(e, "forward");
+    if ((e = cudaMemsetAsync(s->loss, 0, sizeof(float), cs)) != cudaSuccess) return cuda_fail(e, "loss reset");
+    if ((e = tr::loss_l1(b.vis, bt->target, bt->B, bt->T, npx, cfg->alpha, b.gvis, s->loss, cs)) != cudaSuccess)
+        return cuda_fail(e, "loss");
+    if ((e = cudaMemsetAsync(s->grad, 0, s->n * 4, cs)) != cudaSuccess) return cuda_fail(e, "grad reset");
+    if ((e = tr::backward(s->theta, s->grad, b, bt->B, H, W, nullptr, cs)) != cudaSuccess) return cuda_fail(e, "backward");
+    s->step += 1;
+    if ((e = tr::adam(s->theta, s->grad, s->m, s->v, s->n, cfg->lr, cfg->beta1, cfg->beta2, cfg->eps, s->step, cs)) !=
+        cudaSuccess)
+        return cuda_fail(e, "adam");
+    if (loss_out && (e = cudaMemcpyAsync(loss_out, s->loss, sizeof(float), cudaMemcpyDeviceToDevice, cs)) != cudaSuccess)
+        return cuda_fail(e, "copy loss");
+    return NSM_OK;
+}
+
+nsm_status nsm_train_state_read(nsm_train_state* s, int what, float* dev_out, size_t n, void* stream) {
+    if (!s) return fail(NSM_ERR_INVALID_ARG, "state is NULL");
+    if (n != s->n) return fail(NSM_ERR_SHAPE, "%zu floats requested, the state holds %zu", n, s->n);
+    nsm_status st = check_dev_ptr(dev_out, "dev_out", 4);
+    if (st != NSM_OK) return st;
+    const float* src = what == 0 ? s->theta : what == 1 ? s->grad : what == 2 ? s->m : what == 3 ? s->v : nullptr;
+    if (!src) return fail(NSM_ERR_INVALID_ARG, "unknown state vector %d", what);
+    cudaError_t e = cudaMemcpyAsync(dev_out, src, n * 4, cudaMemcpyDeviceToDevice, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "copy state");
+    return NSM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,33 @@
+// Internal declarations of the training path (train.cu).
+#pragma once
+
+#include <cstddef>
+#include <cuda_runtime.h>
+
+#include "nsm_common.cuh"
+
+namespace nsm {
+namespace tr {
+
+// FP32 NHWC buffers of one training / backward call, carved from one block:
+// checkpoints for N views (features, level outputs, visibility) and the
+// per-level recomputation scratch for the Nb views that are back-propagated.
+struct Buffers {
+    float *feat, *e0, *s1, *p1, *bo, *d1, *vis;
+    float *gvis;
+    float *xin, *a3, *a1, *ga1, *ga3, *gx, *glo, *gskip, *gtmp;
+};
+
+size_t workspace_floats(int N, int Nb, int H, int W);
+Buffers carve(float* base, int N, int Nb, int H, int W);
+cudaError_t features_batch(const GatherParams* dev_params, int N, int H, int W, float* feat, cudaStream_t st);
+cudaError_t forward(const float* theta, const Buffers& b, int N, int Nb, int H, int W, cudaStream_t st);
+cudaError_t backward(const float* theta, float* grad, const Buffers& b, int Nb, int H, int W, float* gfeat,
+                     cudaStream_t st);
+cudaError_t loss_l1(const float* vis, const float* target, int B, int T, size_t npx, float alpha, float* gvis,
+                    float* loss, cudaStream_t st);
+cudaError_t adam(float* theta, const float* grad, float* m, float* v, size_t n, float lr, float b1, float b2,
+                 float eps, int step, cudaStream_t st);
+
+}  // namespace tr
+}  // namespace nsm

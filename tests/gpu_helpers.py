@@ -49,3 +49,32 @@ def run_infer(ctx, weights, df, precision, vis=None):
     nsm.nsm_infer(ctx, df.frame, weights, precision, ws, vis)
     torch.cuda.synchronize()
     return vis
+
+
+def train_batch_frames(B, T, H, W, S, seed, n_obj=8, spp_side=8):
+    """Frames [t][b] of a temporal-window batch (instance 0 = the seeded soft
+    scene, instances 1..T-1 = its perturbations) and the MC targets [b]."""
+    import scenegen
+    rng = scenegen.SplitMix64(seed ^ 0xBA7C4)
+    frames = [[None] * B for _ in range(T)]
+    targets = []
+    for b in range(B):
+        base = scenegen.random_scene(seed * 100 + b, n_obj, soft=True)
+        frames[0][b] = scenegen.render_frame(base, H, W, S, S)
+        for t in range(1, T):
+            frames[t][b] = scenegen.render_frame(scenegen.perturbed(base, rng), H, W, S, S)
+        targets.append(scenegen.soft_visibility(frames[0][b], spp_side=spp_side))
+    return frames, np.stack(targets).astype(np.float32)
+
+
+def device_batch(frames, targets):
+    T, B = len(frames), len(frames[0])
+    pos = torch.from_numpy(np.stack([[frames[t][b].pos4 for b in range(B)] for t in range(T)])).cuda()
+    nrm = torch.from_numpy(np.stack([[frames[t][b].nrm4 for b in range(B)] for t in range(T)])).cuda()
+    sm = torch.from_numpy(np.stack([[frames[t][b].sm for b in range(B)] for t in range(T)])).cuda()
+    tgt = torch.from_numpy(targets).cuda()
+    lights = [light_desc(frames[t][b]) for t in range(T) for b in range(B)]
+    cams = [frames[t][b].cam_pos for t in range(T) for b in range(B)]
+    bt = nsm.make_batch(pos, nrm, sm, lights, cams, tgt, B, T)
+    bt._tensors = (pos, nrm, sm, tgt)
+    return bt

@@ -1,0 +1,183 @@
+"""GPU checks of the hand-written backward (nsm_backward), the training step
+(nsm_train_step, Eq. 2 with Adam) and the torch.autograd.Function wrapper,
+against the FP64 oracle's adjoint and central finite differences."""
+import math
+
+import numpy as np
+import pytest
+
+import scenegen
+from oracle import gather as G
+from oracle import network as N
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+import paper_2301_05262_gb300 as nsm  # noqa: E402
+from gpu_helpers import DeviceFrame, device_batch, train_batch_frames  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = nsm.Context()
+    yield c
+    c.check()
+    c.close()
+
+
+def _theta(seed):
+    """He-normal weights and small random biases (non-zero, so every bias
+    gradient path is exercised)."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for (_, ci, co, k) in N.layer_table(3):
+        parts.append(rng.standard_normal(co * ci * k * k) * math.sqrt(2.0 / (ci * k * k)))
+        parts.append(rng.standard_normal(co) * 0.05)
+    return np.concatenate(parts).astype(np.float32)
+
+
+def _layer_slices():
+    out, off = [], 0
+    for (name, ci, co, k) in N.layer_table(3):
+        nw = ci * co * k * k
+        out.append((name + ".w", slice(off, off + nw)))
+        out.append((name + ".b", slice(off + nw, off + nw + co)))
+        off += nw + co
+    return out
+
+
+def _gpu_backward(ctx, f, theta, gvis):
+    df = DeviceFrame(f)
+    params = torch.from_numpy(theta).cuda()
+    gv = torch.from_numpy(gvis.astype(np.float32)).cuda()
+    gp = torch.zeros_like(params)
+    gf = torch.empty((f.H, f.W, 4), device="cuda")
+    vis = torch.empty((f.H, f.W), device="cuda")
+    ws = torch.empty((nsm.nsm_backward_workspace_bytes(f.H, f.W),), dtype=torch.uint8, device="cuda")
+    nsm.nsm_backward(ctx, df.frame, params, gv, gp, ws, grad_feat=gf, vis_out=vis)
+    torch.cuda.synchronize()
+    return gp.cpu().numpy().astype(np.float64), gf.cpu().numpy().astype(np.float64), vis.cpu().numpy()
+
+
+@pytest.mark.parametrize("size", [(32, 32), (36, 68)])
+def test_backward_matches_oracle_adjoint(ctx, size):
+    H, W = size
+    f = scenegen.soft_frame(H, W, 128, 128, 8, 31)
+    theta = _theta(1)
+    gvis = np.random.default_rng(2).standard_normal((H, W))
+    gp, gf, vis = _gpu_backward(ctx, f, theta, gvis)
+    feat, _, _ = G.features(f.pos4, f.nrm4, f.sm, f.view_proj, f.light_pos, f.cam_pos, f.r_hat, f.z_far, f.bias)
+    ref_vis, t = N.forward(feat, theta.astype(np.float64), keep=True)
+    ref_g, ref_gf = N.backward(gvis, theta.astype(np.float64), t)
+    assert np.abs(vis - ref_vis).max() < 1e-4
+    for name, sl in _layer_slices():
+        a, b = gp[sl], ref_g[sl]
+        scale = max(np.abs(b).max(), 1e-12)
+        assert np.abs(a - b).max() <= 2e-4 * scale, (name, np.abs(a - b).max(), scale)
+    scale = np.abs(ref_gf).max()
+    assert np.abs(gf - ref_gf.transpose(1, 2, 0)).max() <= 2e-4 * scale
+
+
+def test_backward_central_finite_differences(ctx):
+    """GPU gradient against central differences (h = 1e-3) of the FP64 oracle
+    forward on a 32 x 32 crop; coordinates whose stencil flips a ReLU are skipped."""
+    H = W = 32
+    f = scenegen.soft_frame(H, W, 128, 128, 8, 33)
+    theta = _theta(3)
+    gvis = np.random.default_rng(4).standard_normal((H, W))
+    gp, _, _ = _gpu_backward(ctx, f, theta, gvis)
+    feat, _, _ = G.features(f.pos4, f.nrm4, f.sm, f.view_proj, f.light_pos, f.cam_pos, f.r_hat, f.z_far, f.bias)
+    th = theta.astype(np.float64)
+    _, t0 = N.forward(feat, th, keep=True)
+
+    def pattern(tt):
+        return np.concatenate([(tt[k] > 0).ravel() for k in tt if k.endswith(("_a3", "_a1"))])
+
+    p0 = pattern(t0)
+    rng = np.random.default_rng(5)
+    idx = list(rng.choice(th.size, 50, replace=False))
+    idx += [sl.start for _, sl in _layer_slices()]
+    h = 1e-3
+    checked = 0
+    for i in idx:
+        tp = th.copy(); tp[i] += h
+        tm = th.copy(); tm[i] -= h
+        vp, ttp = N.forward(feat, tp, keep=True)
+        vm, ttm = N.forward(feat, tm, keep=True)
+        if not (np.array_equal(pattern(ttp), p0) and np.array_equal(pattern(ttm), p0)):
+            continue
+        fd = (np.sum(gvis * vp) - np.sum(gvis * vm)) / (2 * h)
+        assert abs(gp[i] - fd) <= 1e-3 * abs(fd) + 1e-5, (i, gp[i], fd)
+        checked += 1
+    assert checked >= 40
+
+
+def test_autograd_function_matches_oracle(ctx):
+    H = W = 32
+    f = scenegen.hard_frame(H, W, 128, 128, 8, 35)
+    theta = _theta(6)
+    df = DeviceFrame(f)
+    F = nsm.autograd_function()
+    params = torch.from_numpy(theta).cuda().requires_grad_(True)
+    vis = F.apply(params, ctx, df.frame)
+    g = torch.from_numpy(np.random.default_rng(7).standard_normal((H, W)).astype(np.float32)).cuda()
+    (vis * g).sum().backward()
+    feat, _, _ = G.features(f.pos4, f.nrm4, f.sm, f.view_proj, f.light_pos, f.cam_pos, f.r_hat, f.z_far, f.bias)
+    ref_vis, t = N.forward(feat, theta.astype(np.float64), keep=True)
+    ref_g, _ = N.backward(g.cpu().numpy().astype(np.float64), theta.astype(np.float64), t)
+    assert np.abs(vis.detach().cpu().numpy() - ref_vis).max() < 1e-4
+    got = params.grad.cpu().numpy()
+    assert np.abs(got - ref_g).max() <= 2e-4 * np.abs(ref_g).max()
+
+
+def test_train_step_matches_oracle(ctx):
+    """One temporal-window step (B = 2 items, T = 3 instances, 32 x 32 crops):
+    loss, gradient and Adam-updated weights against the oracle's train_step."""
+    B, T, H, W, S = 2, 3, 32, 32, 128
+    frames, targets = train_batch_frames(B, T, H, W, S, seed=41)
+    theta = _theta(8)
+    st = nsm.TrainState(ctx, theta, B, T, H, W)
+    bt = device_batch(frames, targets)
+    loss = torch.zeros(1, device="cuda")
+    lr = 1e-3
+    st.step(bt, lr=lr, alpha=0.9, loss_out=loss)
+    out = {k: torch.empty(theta.size, device="cuda") for k in (0, 1)}
+    for k, v in out.items():
+        st.read(k, v)
+    torch.cuda.synchronize()
+    feats = []
+    for b in range(B):
+        insts = []
+        for t in range(T):
+            fr = frames[t][b]
+            ft, _, _ = G.features(fr.pos4, fr.nrm4, fr.sm, fr.view_proj, fr.light_pos, fr.cam_pos, fr.r_hat,
+                                  fr.z_far, fr.bias)
+            insts.append(ft)
+        feats.append(insts)
+    th64 = theta.astype(np.float64)
+    th2, _, _, ref_loss, ref_grad = N.train_step(feats, [targets[b].astype(np.float64) for b in range(B)], th64,
+                                                 np.zeros_like(th64), np.zeros_like(th64), 1, lr=lr, alpha=0.9)
+    assert float(loss.item()) == pytest.approx(ref_loss, rel=1e-4)
+    grad = out[1].cpu().numpy().astype(np.float64)
+    for name, sl in _layer_slices():
+        scale = max(np.abs(ref_grad[sl]).max(), 1e-12)
+        assert np.abs(grad[sl] - ref_grad[sl]).max() <= 2e-3 * scale, name
+    # Adam's first step moves every weight by about lr * sign(g); compare where the gradient is clearly non-zero
+    new = out[0].cpu().numpy().astype(np.float64)
+    big = np.abs(ref_grad) > 1e-3 * np.abs(ref_grad).max()
+    np.testing.assert_allclose((new - th64)[big], (th2 - th64)[big], rtol=1e-3, atol=1e-7)
+
+
+def test_training_reduces_the_loss(ctx):
+    B, T, H, W, S = 4, 3, 64, 64, 256
+    frames, targets = train_batch_frames(B, T, H, W, S, seed=43)
+    theta = scenegen.he_init_weights(9, N.layer_table(3)).astype(np.float32)
+    st = nsm.TrainState(ctx, theta, B, T, H, W)
+    bt = device_batch(frames, targets)
+    loss = torch.zeros(1, device="cuda")
+    losses = []
+    for _ in range(60):
+        st.step(bt, lr=3e-3, loss_out=loss)
+        losses.append(float(loss.item()))
+    assert all(np.isfinite(losses))
+    assert min(losses[-10:]) < 0.7 * losses[0], (losses[0], losses[-10:])
