@@ -181,6 +181,43 @@ nsm_status nsm_infer_host(nsm_ctx* ctx, const nsm_frame* host_frame, const nsm_w
                           nsm_precision precision, void* dev_stage, size_t stage_bytes,
                           void* workspace, size_t workspace_bytes, float* vis_host, void* stream);
 
+/* ---------------------------------------------------------------- batched serving */
+
+/* One view of a batch: its inputs (as for nsm_infer) and its output. */
+typedef struct {
+    nsm_frame frame;   /* H, W multiples of 4; device buffers */
+    float* vis_out;    /* device [H][W] visibility */
+} nsm_view;
+
+/* Workspace bytes of nsm_infer_batched / nsm_autotune for these views (0 if invalid). */
+size_t nsm_infer_batched_workspace_bytes(int n, const nsm_view* views);
+
+/* BF16 tensor-core inference of n (1..32) independent views of any sizes
+ * (different resolutions, shadow maps, emitters and cameras) in one pass of
+ * five persistent kernel launches, one per network stage, whose CTAs share
+ * one list of tiles of all views.  With nsm_ctx_set_graph(ctx, 1) the five
+ * launches are captured once into a CUDA graph per batch plan (the views'
+ * sizes and the tile plan) and replayed by a single graph launch while the
+ * plan repeats (new buffers and emitters only update the graph's kernel
+ * arguments).  The tile heights and CTAs per SM of every stage come from the
+ * context's plan (nsm_autotune).  workspace: device, 256-byte aligned,
+ * >= nsm_infer_batched_workspace_bytes.  Asynchronous on stream. */
+nsm_status nsm_infer_batched(nsm_ctx* ctx, int n, const nsm_view* views, const nsm_weights* w, void* workspace,
+                             size_t workspace_bytes, void* stream);
+nsm_status nsm_ctx_set_graph(nsm_ctx* ctx, int enable);
+/* Graph launches of the currently cached plan since it was captured. */
+int nsm_ctx_graph_replays(nsm_ctx* ctx);
+
+/* Autotuner: time every tile height and every CTAs-per-SM choice of each of
+ * the five tensor-core stages on this batch (reps timed launches each, after
+ * one warm-up) and keep the fastest per stage in the context's plan, used by
+ * nsm_infer (BF16) and nsm_infer_batched from then on.  Synchronises. */
+nsm_status nsm_autotune(nsm_ctx* ctx, int n, const nsm_view* views, const nsm_weights* w, void* workspace,
+                        size_t workspace_bytes, int reps, void* stream);
+/* The plan per stage (5 entries each, nullable): tile rows, CTAs per SM
+ * (0 = as many as fit), and the tuned time in ms (0 before tuning). */
+nsm_status nsm_autotune_report(nsm_ctx* ctx, int* rows_out, int* ctas_out, float* ms_out);
+
 /* ---------------------------------------------------------------- backward / training */
 
 /* Bytes of device workspace nsm_backward needs for an H x W view. */

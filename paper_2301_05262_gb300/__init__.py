@@ -384,3 +384,70 @@ def autograd_function():
             return gp, None, None
 
     return NSMFunction
+
+
+# ---------------------------------------------------------------- batched serving, graphs, autotuner
+class nsm_view(ctypes.Structure):
+    _fields_ = [("frame", nsm_frame), ("vis_out", ctypes.c_void_p)]
+
+
+def _batch_sigs():
+    L = lib()
+    if getattr(L, "_batch_sigs", False):
+        return L
+    P, I, Z = ctypes.c_void_p, ctypes.c_int, ctypes.c_size_t
+    VP = ctypes.POINTER(nsm_view)
+    sig = {
+        "nsm_infer_batched_workspace_bytes": ([I, VP], Z),
+        "nsm_infer_batched": ([P, I, VP, P, P, Z, P], I),
+        "nsm_ctx_set_graph": ([P, I], I),
+        "nsm_ctx_graph_replays": ([P], I),
+        "nsm_autotune": ([P, I, VP, P, P, Z, I, P], I),
+        "nsm_autotune_report": ([P, P, P, P], I),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(L, name)
+        fn.argtypes = args
+        fn.restype = res
+    L._batch_sigs = True
+    return L
+
+
+def make_views(frames, vis_outs):
+    arr = (nsm_view * len(frames))()
+    for i, (fr, vo) in enumerate(zip(frames, vis_outs)):
+        arr[i].frame = fr
+        arr[i].vis_out = _ptr(vo)
+    return arr
+
+
+def nsm_infer_batched_workspace_bytes(views) -> int:
+    return int(_batch_sigs().nsm_infer_batched_workspace_bytes(len(views), views))
+
+
+def nsm_infer_batched(ctx: Context, views, weights: Weights, workspace, stream=None):
+    _check(_batch_sigs().nsm_infer_batched(ctx.h, len(views), views, weights.h, _ptr(workspace),
+                                           int(workspace.numel() * workspace.element_size()), _stream(stream)),
+           "nsm_infer_batched")
+
+
+def nsm_ctx_set_graph(ctx: Context, enable: bool):
+    _check(_batch_sigs().nsm_ctx_set_graph(ctx.h, 1 if enable else 0), "nsm_ctx_set_graph")
+
+
+def nsm_ctx_graph_replays(ctx: Context) -> int:
+    return int(_batch_sigs().nsm_ctx_graph_replays(ctx.h))
+
+
+def nsm_autotune(ctx: Context, views, weights: Weights, workspace, reps=3, stream=None):
+    _check(_batch_sigs().nsm_autotune(ctx.h, len(views), views, weights.h, _ptr(workspace),
+                                      int(workspace.numel() * workspace.element_size()), reps, _stream(stream)),
+           "nsm_autotune")
+
+
+def nsm_autotune_report(ctx: Context):
+    rows = (ctypes.c_int * 5)()
+    ctas = (ctypes.c_int * 5)()
+    ms = (ctypes.c_float * 5)()
+    _check(_batch_sigs().nsm_autotune_report(ctx.h, rows, ctas, ms), "nsm_autotune_report")
+    return list(rows), list(ctas), list(ms)

@@ -1,0 +1,36 @@
+// Definitions of the opaque handles of the C ABI (shared by the API files).
+#pragma once
+
+#include <vector>
+
+#include "nsm_internal.h"
+#include "tc_stage.h"
+
+// Context: device error word, profiling hook, tensor-core tile plan (set by
+// the autotuner) and the cached CUDA graph of the batched launch.
+struct nsm_ctx {
+    int device;
+    int* d_err;                              // device error word (bounded waits that gave up)
+    std::vector<cudaEvent_t> stage_events;   // profiling hook (caller-owned events)
+    int tc_variant[nsm::kTcStages];          // tile variant per stage
+    int tc_ctas[nsm::kTcStages];             // CTAs per SM per stage (0 = as many as fit)
+    float tc_ms[nsm::kTcStages];             // autotuned stage times (ms), 0 if not tuned
+    // CUDA graph of nsm_infer_batched, keyed by the batch plan
+    int use_graph;
+    std::vector<long long> graph_key;
+    cudaGraph_t graph;
+    cudaGraphExec_t graph_exec;
+    cudaGraphNode_t graph_nodes[nsm::kTcStages];
+    cudaKernelNodeParams graph_params[nsm::kTcStages];
+    int graph_launches;                      // replays of the cached graph (for tests)
+};
+
+struct nsm_weights {
+    int device;
+    float* d_params;   // canonical FP32 vector (nsm_param_count floats)
+    uint16_t* d_bf16;  // packed BF16 images (tensor-core form)
+    void* d_descs;     // packing table
+    int ndesc;
+};
+
+void ctx_release_graph(nsm_ctx* c);

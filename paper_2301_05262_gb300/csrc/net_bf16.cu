@@ -2,53 +2,45 @@
 // Blackwell tcgen05: every convolution is an implicit GEMM
 //   D[pixels x C_out] = A[pixels x K] * B[C_out x K]^T,  K = 9 C_in (3x3) or C_mid (1x1),
 // issued as 128 x N x 16 MMAs by one thread, accumulated in FP32 in tensor
-// memory (TMEM).  One fused kernel per level runs "3x3 conv + ReLU ->
-// 1x1 conv + ReLU" with the same prologues / epilogues as the FP32 form:
-//   prologue  GATHER (features from G-buffer + shadow map, the gather fused
+// memory (TMEM).  One fused kernel per level ("stage") runs
+// "3x3 conv + ReLU -> 1x1 conv + ReLU" with one of these prologues / epilogues:
+//   prologue  GATHER (features from G-buffer + shadow map: the gather fused
 //             into the first level), PLAIN, UP_SKIP, UP;
 //   epilogue  POOL, SKIP_POOL, STORE, HEAD (1x1 16 -> 1 + sigmoid).
+//
+// Each launch is persistent and serves a job table of up to kMaxViews views
+// of any sizes (one view for nsm_infer, many for nsm_infer_batched): the
+// CTAs walk one global list of tiles, each tile belonging to one view.
 //
 // Tile: R rows x 128 pixels of the level; MMA row block = one 128-pixel row
 // segment.  The input tile with its 1-pixel halo is staged in shared memory
 // as 16-byte chunks of 8 channels, [channel group][staged row][staged pixel],
-// which *is* the tensor core's no-swizzle K-major operand layout: the A
-// operand of tap (ky, kx) and channel pair (2g, 2g+1) is the same buffer
-// started (ky, kx) chunks further on, so the im2col matrix is never built.
-// The 3x3 result goes TMEM -> registers (bias, ReLU, BF16) -> shared memory,
-// where it is the A operand of the 1x1 MMA (written back into the same TMEM
-// columns).
+// which is the tensor core's no-swizzle K-major operand layout: the A operand
+// of tap (ky, kx) and channel pair (2g, 2g+1) is the same buffer started
+// (ky, kx) chunks further on, so the im2col matrix is never built.  The 3x3
+// result goes TMEM -> registers (bias, ReLU) -> shared memory as BF16 hi + lo
+// parts, the A operand of the 1x1 MMA (written into the same TMEM columns).
+// Weights are BF16 hi + lo images: each K step runs against both, and the
+// 1x1 adds A_hi B_hi + A_hi B_lo + A_lo B_hi, so weight and intermediate
+// rounding leave no trace beyond ~2^-16; only the level outputs are BF16.
 //
 // First level: the four FP32 features are split into BF16 hi + lo parts
-// (f = hi + lo to ~2^-16 relative), giving 8 "channels" per pixel; K steps
-// pair two taps (two 16-byte chunks), so the 3x3 4 -> 16 convolution is five
-// K = 16 steps with a zero-weight pad.  This keeps the depth-test features
-// (z / z_f near 1, z - z_f near 0) at near-FP32 resolution on BF16 hardware.
+// (f = hi + lo to ~2^-16 relative), 8 "channels" per pixel; K steps pair two
+// taps (two 16-byte chunks), so the 3x3 4 -> 16 convolution is five K = 16
+// steps with a zero-weight pad.  This keeps the depth-test features
+// (z / z_f near 1, z - z_f near 0) at near-FP32 resolution.
+//
+// 256 threads (8 warps) per CTA: all stage the input; warp w reads TMEM lane
+// quarter w % 4 and the two warpgroups split the epilogue rows.
 #include "nsm_internal.h"
 #include "tc_common.cuh"
+#include "tc_stage.h"
 
 namespace nsm {
 
 using namespace tc;
 
-enum TcPro { TPRO_GATHER = 0, TPRO_PLAIN = 1, TPRO_UP_SKIP = 2, TPRO_UP = 3 };
-enum TcEpi { TEPI_POOL = 0, TEPI_SKIP_POOL = 1, TEPI_STORE = 2, TEPI_HEAD = 3 };
-
-struct TcArgs {
-    GatherParams g;
-    int H, W;                    // this level's resolution
-    const uint16_t* in;          // BF16 NHWC: PLAIN [H][W][CIN]; UP* [H/2][W/2][CIN]
-    const uint16_t* skip;        // UP_SKIP: [H][W][CIN]
-    const uint4* b3img;          // packed 3x3 weights (shared-memory image)
-    const uint4* b1img;          // packed 1x1 weights
-    const float* bias3;
-    const float* bias1;
-    const float* head;           // head weights [COUT] then bias
-    uint16_t* out;               // POOL: [H/2][W/2][COUT]; STORE: [H][W][COUT]; SKIP_POOL: pooled
-    uint16_t* out_skip;          // SKIP_POOL: [H][W][COUT]
-    float* vis;                  // HEAD: [H][W]
-    int* err;                    // device error word
-};
-
+constexpr int kNT = 256;         // threads per CTA
 constexpr int kTileM = 128;      // pixels per MMA row block
 constexpr int kSW = 136;         // staged pixels per row (128 + halo + pad)
 constexpr uint64_t kWaitNs = 2000000000ull;  // 2 s bound on every mbarrier wait
@@ -75,7 +67,8 @@ struct TcCfg {
     static constexpr int OFF_HEAD = OFF_BIAS1 + COUT * 4;
     static constexpr int OFF_BAR = ((OFF_HEAD + (COUT + 1) * 4) + 15) / 16 * 16;
     static constexpr int BYTES_USED = OFF_BAR + 32;
-    static constexpr int TMEM_COLS = R * CMID;
+    static constexpr int TMEM_COLS_RAW = R * CMID;
+    static constexpr int TMEM_COLS = TMEM_COLS_RAW < 32 ? 32 : TMEM_COLS_RAW;
     // enough shared memory per CTA that the CTAs resident on one SM can never
     // ask for more than its 512 TMEM columns (228 KB of shared memory per SM)
     static constexpr int TMEM_CAP = 512 / TMEM_COLS;
@@ -83,16 +76,12 @@ struct TcCfg {
     static constexpr int BYTES = BYTES_USED < BYTES_MIN ? BYTES_MIN : BYTES_USED;
     static_assert(TMEM_COLS == 32 || TMEM_COLS == 64 || TMEM_COLS == 128 || TMEM_COLS == 256, "TMEM columns");
     static_assert(CMID % 16 == 0 && COUT % 16 == 0 && COUT <= CMID, "channel shapes");
+    static_assert(BYTES_USED <= 227 * 1024, "shared memory");
 };
 
 __device__ __forceinline__ void st_shared_v4(uint32_t addr, uint4 v) {
     asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" :: "r"(addr), "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w)
                  : "memory");
-}
-__device__ __forceinline__ uint4 ld_shared_v4(uint32_t addr) {
-    uint4 v;
-    asm volatile("ld.shared.v4.b32 {%0, %1, %2, %3}, [%4];" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "r"(addr));
-    return v;
 }
 __device__ __forceinline__ uint4 ldg_v4(const void* p) {
     return __ldg(reinterpret_cast<const uint4*>(p));
@@ -109,7 +98,7 @@ __device__ __forceinline__ uint4 f32_to_chunk(const float* f) {
 }
 
 template <int CIN, int CMID, int COUT, int R, int PRO, int EPI>
-__global__ void __launch_bounds__(128, 3) level_tc_kernel(TcArgs a) {
+__global__ void __launch_bounds__(kNT, 2) level_tc_kernel(const __grid_constant__ TcBatch a) {
     using C = TcCfg<CIN, CMID, COUT, R, PRO>;
     extern __shared__ __align__(1024) unsigned char smem[];
     const uint32_t sbase = smem_u32(smem);
@@ -124,14 +113,16 @@ __global__ void __launch_bounds__(128, 3) level_tc_kernel(TcArgs a) {
 
     const int tid = threadIdx.x;
     const int warp = tid >> 5;
+    const int wg = warp >> 2;          // warpgroup: splits the epilogue rows
+    const int m = tid & 127;           // pixel of the row block = TMEM lane
 
     // ---- one-time set-up: weights, barrier, TMEM
-    for (int i = tid; i < C::B3_CHUNKS; i += 128) st_shared_v4(sB3 + 16 * i, __ldg(a.b3img + i));
-    for (int i = tid; i < C::B1_CHUNKS; i += 128) st_shared_v4(sB1 + 16 * i, __ldg(a.b1img + i));
-    for (int i = tid; i < CMID; i += 128) bias3_s[i] = __ldg(a.bias3 + i);
-    for (int i = tid; i < COUT; i += 128) bias1_s[i] = __ldg(a.bias1 + i);
+    for (int i = tid; i < C::B3_CHUNKS; i += kNT) st_shared_v4(sB3 + 16 * i, __ldg(a.b3img + i));
+    for (int i = tid; i < C::B1_CHUNKS; i += kNT) st_shared_v4(sB1 + 16 * i, __ldg(a.b1img + i));
+    for (int i = tid; i < CMID; i += kNT) bias3_s[i] = __ldg(a.bias3 + i);
+    for (int i = tid; i < COUT; i += kNT) bias1_s[i] = __ldg(a.bias1 + i);
     if (EPI == TEPI_HEAD)
-        for (int i = tid; i <= COUT; i += 128) head_s[i] = __ldg(a.head + i);
+        for (int i = tid; i <= COUT; i += kNT) head_s[i] = __ldg(a.head + i);
     if (tid == 0) {
         mbar_init(mbar, 1);
         fence_mbar_init();
@@ -142,18 +133,20 @@ __global__ void __launch_bounds__(128, 3) level_tc_kernel(TcArgs a) {
     __syncthreads();
     fence_after_sync();
     const uint32_t tbase = *tslot;
-    const uint32_t tlane = tbase + (static_cast<uint32_t>(warp * 32) << 16);
+    const uint32_t tlane = tbase + (static_cast<uint32_t>((warp & 3) * 32) << 16);
     uint32_t phase = 0;
 
-    const int H = a.H, W = a.W;
-    const int tiles_x = (W + kTileM - 1) / kTileM;
-    const int tiles_y = (H + R - 1) / R;
-    const int ntiles = tiles_x * tiles_y;
     constexpr uint32_t kPlane = (R + 2) * kSW * 16;  // bytes between channel groups of A0
+    const int ntiles = a.tile_start[a.nviews];
+    int v = 0;
 
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const int y0 = (tile / tiles_x) * R;
-        const int x0 = (tile % tiles_x) * kTileM;
+        while (tile >= a.tile_start[v + 1]) ++v;
+        const TcJob& job = a.job[v];
+        const int H = job.H, W = job.W;
+        const int local = tile - a.tile_start[v];
+        const int y0 = (local / job.tiles_x) * R;
+        const int x0 = (local % job.tiles_x) * kTileM;
 
         // ---------------- prologue: stage the (R+2) x 130 input tile (zero padded)
         if constexpr (PRO == TPRO_GATHER) {
@@ -162,38 +155,38 @@ __global__ void __launch_bounds__(128, 3) level_tc_kernel(TcArgs a) {
             // G-buffer loads, then its shadow-map loads, are all in flight together
             constexpr int NSP = 131;
             constexpr int ITEMS = (R + 2) * NSP;
-            constexpr int NPT = (ITEMS + 127) / 128;
+            constexpr int NPT = (ITEMS + kNT - 1) / kNT;
+            const GatherParams& g = job.g;
             float4 P[NPT], Nv[NPT];
-            int tex[NPT];
             bool ok[NPT];
 #pragma unroll
             for (int k = 0; k < NPT; ++k) {
-                const int idx = tid + 128 * k;
+                const int idx = tid + kNT * k;
                 const int sr = idx / NSP, sp = idx % NSP;
                 const int gy = y0 - 1 + sr, gx = x0 - 1 + sp;
                 ok[k] = idx < ITEMS && sp < 130 && gy >= 0 && gy < H && gx >= 0 && gx < W;
                 if (ok[k]) {
                     const size_t p = static_cast<size_t>(gy) * W + gx;
-                    P[k] = __ldg(a.g.pos4 + p);
-                    Nv[k] = __ldg(a.g.nrm4 + p);
+                    P[k] = __ldg(g.pos4 + p);
+                    Nv[k] = __ldg(g.nrm4 + p);
                 }
             }
             float z[NPT];
 #pragma unroll
             for (int k = 0; k < NPT; ++k) {
-                tex[k] = ok[k] ? texel_index(a.g, P[k].x, P[k].y, P[k].z) : -1;
-                z[k] = a.g.z_far;
-                if (tex[k] >= 0) z[k] = __ldg(a.g.sm + tex[k]);
+                const int tx = ok[k] ? texel_index(g, P[k].x, P[k].y, P[k].z) : -1;
+                z[k] = g.z_far;
+                if (tx >= 0) z[k] = __ldg(g.sm + tx);
             }
 #pragma unroll
             for (int k = 0; k < NPT; ++k) {
-                const int idx = tid + 128 * k;
+                const int idx = tid + kNT * k;
                 if (idx < ITEMS) {
                     const int sr = idx / NSP, sp = idx % NSP;
                     uint4 chunk = make_uint4(0, 0, 0, 0);
                     if (ok[k]) {
                         float f[4];
-                        pixel_features(a.g, P[k], Nv[k], z[k], f);
+                        pixel_features(g, P[k], Nv[k], z[k], f);
                         float hl[8];
 #pragma unroll
                         for (int c = 0; c < 4; ++c) {
@@ -209,33 +202,33 @@ __global__ void __launch_bounds__(128, 3) level_tc_kernel(TcArgs a) {
         } else if constexpr (PRO == TPRO_PLAIN) {
             constexpr int CG = CIN / 8;
 #pragma unroll 4
-            for (int idx = tid; idx < (R + 2) * 130 * CG; idx += 128) {
+            for (int idx = tid; idx < (R + 2) * 130 * CG; idx += kNT) {
                 const int cg = idx % CG;
                 const int t = idx / CG;
                 const int sp = t % 130, sr = t / 130;
                 const int gy = y0 - 1 + sr, gx = x0 - 1 + sp;
-                uint4 v = make_uint4(0, 0, 0, 0);
+                uint4 val = make_uint4(0, 0, 0, 0);
                 if (gy >= 0 && gy < H && gx >= 0 && gx < W)
-                    v = ldg_v4(a.in + (static_cast<size_t>(gy) * W + gx) * CIN + cg * 8);
-                st_shared_v4(sA0 + cg * kPlane + 16 * (sr * kSW + sp), v);
+                    val = ldg_v4(job.in + (static_cast<size_t>(gy) * W + gx) * CIN + cg * 8);
+                st_shared_v4(sA0 + cg * kPlane + 16 * (sr * kSW + sp), val);
             }
         } else {  // UP_SKIP / UP
             constexpr int CG = CIN / 8;
             const int Hl = H / 2, Wl = W / 2;
 #pragma unroll 2
-            for (int idx = tid; idx < (R + 2) * 130 * CG; idx += 128) {
+            for (int idx = tid; idx < (R + 2) * 130 * CG; idx += kNT) {
                 const int cg = idx % CG;
                 const int t = idx / CG;
                 const int sp = t % 130, sr = t / 130;
                 const int gy = y0 - 1 + sr, gx = x0 - 1 + sp;
-                uint4 v = make_uint4(0, 0, 0, 0);
+                uint4 val = make_uint4(0, 0, 0, 0);
                 if (gy >= 0 && gy < H && gx >= 0 && gx < W) {
                     const BilinTap ty = bilin_tap(gy, Hl), tx = bilin_tap(gx, Wl);
                     float p00[8], p01[8], p10[8], p11[8], o[8];
-                    chunk_to_f32(ldg_v4(a.in + (static_cast<size_t>(ty.i0) * Wl + tx.i0) * CIN + cg * 8), p00);
-                    chunk_to_f32(ldg_v4(a.in + (static_cast<size_t>(ty.i0) * Wl + tx.i1) * CIN + cg * 8), p01);
-                    chunk_to_f32(ldg_v4(a.in + (static_cast<size_t>(ty.i1) * Wl + tx.i0) * CIN + cg * 8), p10);
-                    chunk_to_f32(ldg_v4(a.in + (static_cast<size_t>(ty.i1) * Wl + tx.i1) * CIN + cg * 8), p11);
+                    chunk_to_f32(ldg_v4(job.in + (static_cast<size_t>(ty.i0) * Wl + tx.i0) * CIN + cg * 8), p00);
+                    chunk_to_f32(ldg_v4(job.in + (static_cast<size_t>(ty.i0) * Wl + tx.i1) * CIN + cg * 8), p01);
+                    chunk_to_f32(ldg_v4(job.in + (static_cast<size_t>(ty.i1) * Wl + tx.i0) * CIN + cg * 8), p10);
+                    chunk_to_f32(ldg_v4(job.in + (static_cast<size_t>(ty.i1) * Wl + tx.i1) * CIN + cg * 8), p11);
 #pragma unroll
                     for (int c = 0; c < 8; ++c) {
                         const float r0 = p00[c] * tx.w0 + p01[c] * tx.w1;
@@ -244,13 +237,13 @@ __global__ void __launch_bounds__(128, 3) level_tc_kernel(TcArgs a) {
                     }
                     if constexpr (PRO == TPRO_UP_SKIP) {
                         float s[8];
-                        chunk_to_f32(ldg_v4(a.skip + (static_cast<size_t>(gy) * W + gx) * CIN + cg * 8), s);
+                        chunk_to_f32(ldg_v4(job.skip + (static_cast<size_t>(gy) * W + gx) * CIN + cg * 8), s);
 #pragma unroll
                         for (int c = 0; c < 8; ++c) o[c] += s[c];
                     }
-                    v = f32_to_chunk(o);
+                    val = f32_to_chunk(o);
                 }
-                st_shared_v4(sA0 + cg * kPlane + 16 * (sr * kSW + sp), v);
+                st_shared_v4(sA0 + cg * kPlane + 16 * (sr * kSW + sp), val);
             }
         }
         fence_proxy_async_smem();
@@ -303,25 +296,25 @@ __global__ void __launch_bounds__(128, 3) level_tc_kernel(TcArgs a) {
 
         // ---------------- epilogue 1: bias + ReLU -> BF16 hi + lo -> A operand of the 1x1
         constexpr int kA1Part = (CMID / 8) * kTileM;  // chunks per part of one row
-        for (int r = 0; r < R; ++r) {
+        for (int r = wg; r < R; r += 2) {
 #pragma unroll
             for (int c0 = 0; c0 < CMID; c0 += 16) {
-                float v[16], lo[16];
-                tmem_ld16(tlane + r * CMID + c0, v);
+                float val[16], lo[16];
+                tmem_ld16(tlane + r * CMID + c0, val);
                 tmem_ld_wait();
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
-                    v[j] = fmaxf(v[j] + bias3_s[c0 + j], 0.f);
-                    const float hi = __bfloat162float(__float2bfloat16_rn(v[j]));
-                    lo[j] = v[j] - hi;
-                    v[j] = hi;
+                    val[j] = fmaxf(val[j] + bias3_s[c0 + j], 0.f);
+                    const float hi = __bfloat162float(__float2bfloat16_rn(val[j]));
+                    lo[j] = val[j] - hi;
+                    val[j] = hi;
                 }
                 const int cg = c0 / 8;
                 const uint32_t row = sA1 + 16 * (r * 2 * kA1Part);
-                st_shared_v4(row + 16 * (cg * kTileM + tid), f32_to_chunk(v));
-                st_shared_v4(row + 16 * ((cg + 1) * kTileM + tid), f32_to_chunk(v + 8));
-                st_shared_v4(row + 16 * (kA1Part + cg * kTileM + tid), f32_to_chunk(lo));
-                st_shared_v4(row + 16 * (kA1Part + (cg + 1) * kTileM + tid), f32_to_chunk(lo + 8));
+                st_shared_v4(row + 16 * (cg * kTileM + m), f32_to_chunk(val));
+                st_shared_v4(row + 16 * ((cg + 1) * kTileM + m), f32_to_chunk(val + 8));
+                st_shared_v4(row + 16 * (kA1Part + cg * kTileM + m), f32_to_chunk(lo));
+                st_shared_v4(row + 16 * (kA1Part + (cg + 1) * kTileM + m), f32_to_chunk(lo + 8));
             }
         }
         fence_proxy_async_smem();
@@ -360,9 +353,9 @@ __global__ void __launch_bounds__(128, 3) level_tc_kernel(TcArgs a) {
         fence_after_sync();
 
         // ---------------- epilogue 2
-        const int ox = x0 + tid;
-        if (EPI == TEPI_POOL || EPI == TEPI_SKIP_POOL) {
-            for (int r = 0; r < R; r += 2) {
+        const int ox = x0 + m;
+        if constexpr (EPI == TEPI_POOL || EPI == TEPI_SKIP_POOL) {
+            for (int r = 2 * wg; r < R; r += 4) {  // row pairs (r, r + 1), alternating warpgroups
                 float s[COUT];
 #pragma unroll
                 for (int c0 = 0; c0 < COUT; c0 += 16) {
@@ -376,10 +369,10 @@ __global__ void __launch_bounds__(128, 3) level_tc_kernel(TcArgs a) {
                         v1[j] = fmaxf(v1[j] + bias1_s[c0 + j], 0.f);
                         s[c0 + j] = v0[j] + v1[j];
                     }
-                    if (EPI == TEPI_SKIP_POOL) {
+                    if constexpr (EPI == TEPI_SKIP_POOL) {
                         const int oy = y0 + r;
                         if (oy < H && ox < W) {
-                            uint16_t* dst = a.out_skip + (static_cast<size_t>(oy) * W + ox) * COUT + c0;
+                            uint16_t* dst = job.out_skip + (static_cast<size_t>(oy) * W + ox) * COUT + c0;
                             reinterpret_cast<uint4*>(dst)[0] = f32_to_chunk(v0);
                             reinterpret_cast<uint4*>(dst)[1] = f32_to_chunk(v0 + 8);
                             dst += static_cast<size_t>(W) * COUT;
@@ -393,8 +386,8 @@ __global__ void __launch_bounds__(128, 3) level_tc_kernel(TcArgs a) {
                 const int oy = y0 + r;
                 if (oy < H && ox < W) {
                     // even pixel writes the first half of the channels, odd the second
-                    const int half = (tid & 1) * (COUT / 2);
-                    uint16_t* dst = a.out + (static_cast<size_t>(oy / 2) * (W / 2) + ox / 2) * COUT + half;
+                    const int half = (m & 1) * (COUT / 2);
+                    uint16_t* dst = job.out + (static_cast<size_t>(oy / 2) * (W / 2) + ox / 2) * COUT + half;
 #pragma unroll
                     for (int c = 0; c < COUT / 2; c += 8) {
                         float t8[8];
@@ -405,33 +398,33 @@ __global__ void __launch_bounds__(128, 3) level_tc_kernel(TcArgs a) {
                 }
             }
         } else {
-            for (int r = 0; r < R; ++r) {
+            for (int r = wg; r < R; r += 2) {
                 const int oy = y0 + r;
                 float hsum = 0.f;
 #pragma unroll
                 for (int c0 = 0; c0 < COUT; c0 += 16) {
-                    float v[16];
-                    tmem_ld16(tlane + r * CMID + c0, v);
+                    float val[16];
+                    tmem_ld16(tlane + r * CMID + c0, val);
                     tmem_ld_wait();
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) v[j] = fmaxf(v[j] + bias1_s[c0 + j], 0.f);
-                    if (EPI == TEPI_STORE) {
+                    for (int j = 0; j < 16; ++j) val[j] = fmaxf(val[j] + bias1_s[c0 + j], 0.f);
+                    if constexpr (EPI == TEPI_STORE) {
                         if (oy < H && ox < W) {
-                            uint16_t* dst = a.out + (static_cast<size_t>(oy) * W + ox) * COUT + c0;
-                            reinterpret_cast<uint4*>(dst)[0] = f32_to_chunk(v);
-                            reinterpret_cast<uint4*>(dst)[1] = f32_to_chunk(v + 8);
+                            uint16_t* dst = job.out + (static_cast<size_t>(oy) * W + ox) * COUT + c0;
+                            reinterpret_cast<uint4*>(dst)[0] = f32_to_chunk(val);
+                            reinterpret_cast<uint4*>(dst)[1] = f32_to_chunk(val + 8);
                         }
                     } else {
 #pragma unroll
-                        for (int j = 0; j < 16; ++j) hsum = fmaf(head_s[c0 + j], v[j], hsum);
+                        for (int j = 0; j < 16; ++j) hsum = fmaf(head_s[c0 + j], val[j], hsum);
                     }
                 }
                 if (EPI == TEPI_HEAD && oy < H && ox < W)
-                    a.vis[static_cast<size_t>(oy) * W + ox] = sigmoidf_acc(hsum + head_s[COUT]);
+                    job.vis[static_cast<size_t>(oy) * W + ox] = sigmoidf_acc(hsum + head_s[COUT]);
             }
         }
         fence_before_sync();
-        __syncthreads();  // TMEM columns and A1 are free for the next tile
+        __syncthreads();  // TMEM columns, A0 and A1 are free for the next tile
     }
 
     __syncthreads();
@@ -439,81 +432,9 @@ __global__ void __launch_bounds__(128, 3) level_tc_kernel(TcArgs a) {
     if (warp == 0) tmem_dealloc(tbase, C::TMEM_COLS);
 }
 
-// ------------------------------------------------------------------ weight packing
-// Shared-memory images of the BF16 weights, each weight w stored as
-// hi = bf16(w) in one image and lo = bf16(w - hi) in a second image right
-// after it (16-byte chunks of 8 K values):
-//   3x3, C_in >= 16:  chunk (tap, g, n) = W[n][8g .. 8g+7][tap]
-//   3x3 first level:  chunk (k, h, n)   = tap t = 2k + h (t < 9), channels
-//                     [c0..c3 | c0..c3] (the same weight for the hi and lo
-//                     parts of each feature), zero for t = 9
-//   1x1:              chunk (g, n)      = W[n][8g .. 8g+7]
-using PackDesc = PackDescHost;
-
-__global__ void pack_bf16_kernel(const float* __restrict__ params, uint16_t* __restrict__ img,
-                                 const PackDesc* __restrict__ descs, int ndesc) {
-    for (int d = 0; d < ndesc; ++d) {
-        const PackDesc pd = descs[d];
-        for (size_t i = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; i < pd.count;
-             i += static_cast<size_t>(gridDim.x) * blockDim.x) {
-            const int e = static_cast<int>(i % 8);
-            const size_t chunk = i / 8;
-            float v = 0.f;
-            if (pd.kind == 0) {  // 3x3 general: chunk = (tap * (cin/8) + g) * cout + n
-                const int n = static_cast<int>(chunk % pd.cout);
-                const size_t t2 = chunk / pd.cout;
-                const int g = static_cast<int>(t2 % (pd.cin / 8));
-                const int tap = static_cast<int>(t2 / (pd.cin / 8));
-                v = params[pd.w_off + (static_cast<size_t>(n) * pd.cin + 8 * g + e) * 9 + tap];
-            } else if (pd.kind == 1) {  // first level hi/lo: chunk = (k * 2 + h) * cout + n
-                const int n = static_cast<int>(chunk % pd.cout);
-                const int kh = static_cast<int>(chunk / pd.cout);
-                const int tap = kh;  // = 2k + h
-                if (tap < 9) v = params[pd.w_off + (static_cast<size_t>(n) * 4 + (e % 4)) * 9 + tap];
-            } else {  // 1x1: chunk = g * cout + n
-                const int n = static_cast<int>(chunk % pd.cout);
-                const int g = static_cast<int>(chunk / pd.cout);
-                v = params[pd.w_off + static_cast<size_t>(n) * pd.cin + 8 * g + e];
-            }
-            const __nv_bfloat16 hi = __float2bfloat16_rn(v);
-            const __nv_bfloat16 lo = __float2bfloat16_rn(v - __bfloat162float(hi));
-            img[pd.img_off + i] = __bfloat16_as_ushort(hi);
-            img[pd.img_off + pd.count + i] = __bfloat16_as_ushort(lo);
-        }
-    }
-}
-
-BF16Images bf16_images() {
-    const LayerOffsets off = layer_offsets();
-    BF16Images im{};
-    size_t pos = 0;
-    auto add = [&](int layer, int kind) {
-        const int ci = kLayers[layer].cin, co = kLayers[layer].cout;
-        size_t count;
-        if (kind == 0) count = static_cast<size_t>(9) * ci * co;
-        else if (kind == 1) count = static_cast<size_t>(10) * co * 8;
-        else count = static_cast<size_t>(ci) * co;
-        im.desc[im.n] = {kind, ci, co, off.w[layer], pos, count};
-        im.img_off[layer] = pos;
-        pos += 2 * count;  // hi image, then lo image (counts are multiples of 8)
-        ++im.n;
-    };
-    add(ENC0_3, 1); add(ENC0_1, 2); add(ENC1_3, 0); add(ENC1_1, 2); add(BOTT_3, 0); add(BOTT_1, 2);
-    add(DEC1_3, 0); add(DEC1_1, 2); add(DEC0_3, 0); add(DEC0_1, 2);
-    im.total = pos;
-    return im;
-}
-
-cudaError_t launch_pack_bf16(const float* params, uint16_t* img, const void* dev_descs, int ndesc, cudaStream_t stream) {
-    pack_bf16_kernel<<<64, 256, 0, stream>>>(params, img, static_cast<const PackDesc*>(dev_descs), ndesc);
-    return cudaGetLastError();
-}
-
-size_t pack_desc_bytes() { return sizeof(PackDesc); }
-
-// ------------------------------------------------------------------ launch
+// ------------------------------------------------------------------ variants and launch
 template <int CIN, int CMID, int COUT, int R, int PRO, int EPI>
-static cudaError_t launch_tc(const TcArgs& a, cudaStream_t stream) {
+static cudaError_t launch_variant(const TcBatch& a, int ctas_per_sm, cudaStream_t stream) {
     using C = TcCfg<CIN, CMID, COUT, R, PRO>;
     auto kern = level_tc_kernel<CIN, CMID, COUT, R, PRO, EPI>;
     static int occ = -1;
@@ -525,83 +446,152 @@ static cudaError_t launch_tc(const TcArgs& a, cudaStream_t stream) {
         cudaFuncAttributes fa{};
         e = cudaFuncGetAttributes(&fa, kern);
         if (e != cudaSuccess) return e;
-        const int regs = ((fa.numRegs + 7) / 8) * 8 * 128;
-        const int by_regs = regs > 0 ? 65536 / regs : 16;
+        const int regs = ((fa.numRegs + 7) / 8) * 8 * kNT;
+        const int by_regs = regs > 0 ? 65536 / regs : 8;
         const int by_smem = (228 * 1024) / (C::BYTES + 1024);
         int o = by_regs < by_smem ? by_regs : by_smem;
         if (o > C::TMEM_CAP) o = C::TMEM_CAP;
-        if (o > 16) o = 16;
+        if (o > 8) o = 8;
         occ = o < 1 ? 1 : o;
     }
-    const int tiles = ((a.W + kTileM - 1) / kTileM) * ((a.H + R - 1) / R);
+    const int tiles = a.tile_start[a.nviews];
     if (tiles == 0) return cudaSuccess;
-    const int cap = occ * num_sms();
+    const int per_sm = (ctas_per_sm <= 0 || ctas_per_sm > occ) ? occ : ctas_per_sm;
+    const int cap = per_sm * num_sms();
     const int grid = tiles < cap ? tiles : cap;
-    kern<<<grid, 128, C::BYTES, stream>>>(a);
+    kern<<<grid, kNT, C::BYTES, stream>>>(a);
     return cudaGetLastError();
+}
+
+template <int CIN, int CMID, int COUT, int R, int PRO, int EPI>
+static const void* kernel_of() {
+    return reinterpret_cast<const void*>(level_tc_kernel<CIN, CMID, COUT, R, PRO, EPI>);
+}
+
+template <int CIN, int CMID, int COUT, int R, int PRO, int EPI>
+static int occupancy_of() {
+    using C = TcCfg<CIN, CMID, COUT, R, PRO>;
+    cudaFuncAttributes fa{};
+    if (cudaFuncGetAttributes(&fa, level_tc_kernel<CIN, CMID, COUT, R, PRO, EPI>) != cudaSuccess) return 1;
+    const int regs = ((fa.numRegs + 7) / 8) * 8 * kNT;
+    const int by_regs = regs > 0 ? 65536 / regs : 8;
+    const int by_smem = (228 * 1024) / (C::BYTES + 1024);
+    int o = by_regs < by_smem ? by_regs : by_smem;
+    if (o > C::TMEM_CAP) o = C::TMEM_CAP;
+    if (o > 8) o = 8;
+    return o < 1 ? 1 : o;
+}
+
+// Variant tables: the tile height R of every stage (the autotuner's search space).
+using LaunchFn = cudaError_t (*)(const TcBatch&, int, cudaStream_t);
+struct Variant { int R; LaunchFn fn; const void* (*func)(); int (*occ)(); };
+#define NSM_VARIANT(R_, ...) {R_, launch_variant<__VA_ARGS__>, kernel_of<__VA_ARGS__>, occupancy_of<__VA_ARGS__>}
+
+static const Variant kVarEnc0[] = {
+    NSM_VARIANT(2, 4, 16, 16, 2, TPRO_GATHER, TEPI_POOL),
+    NSM_VARIANT(4, 4, 16, 16, 4, TPRO_GATHER, TEPI_POOL),
+    NSM_VARIANT(8, 4, 16, 16, 8, TPRO_GATHER, TEPI_POOL)};
+static const Variant kVarEnc1[] = {
+    NSM_VARIANT(2, 16, 32, 32, 2, TPRO_PLAIN, TEPI_SKIP_POOL),
+    NSM_VARIANT(4, 16, 32, 32, 4, TPRO_PLAIN, TEPI_SKIP_POOL)};
+static const Variant kVarBott[] = {
+    NSM_VARIANT(1, 32, 64, 32, 1, TPRO_PLAIN, TEPI_STORE),
+    NSM_VARIANT(2, 32, 64, 32, 2, TPRO_PLAIN, TEPI_STORE)};
+static const Variant kVarDec1[] = {
+    NSM_VARIANT(2, 32, 32, 16, 2, TPRO_UP_SKIP, TEPI_STORE),
+    NSM_VARIANT(4, 32, 32, 16, 4, TPRO_UP_SKIP, TEPI_STORE)};
+static const Variant kVarDec0[] = {
+    NSM_VARIANT(2, 16, 16, 16, 2, TPRO_UP, TEPI_HEAD),
+    NSM_VARIANT(4, 16, 16, 16, 4, TPRO_UP, TEPI_HEAD),
+    NSM_VARIANT(8, 16, 16, 16, 8, TPRO_UP, TEPI_HEAD)};
+
+struct StageTable { const Variant* v; int n; };
+static const StageTable kStages[kTcStages] = {
+    {kVarEnc0, 3}, {kVarEnc1, 2}, {kVarBott, 2}, {kVarDec1, 2}, {kVarDec0, 3}};
+
+int tc_stage_variants(int stage) { return (stage >= 0 && stage < kTcStages) ? kStages[stage].n : 0; }
+int tc_stage_rows(int stage, int variant) { return kStages[stage].v[variant].R; }
+const void* tc_stage_kernel(int stage, int variant) { return kStages[stage].v[variant].func(); }
+int tc_stage_occupancy(int stage, int variant) { return kStages[stage].v[variant].occ(); }
+
+int tc_default_variant(int stage) {
+    // R = 4 for the full-resolution stages, the smaller tiles for the others
+    static const int def[kTcStages] = {1, 1, 1, 0, 1};
+    return def[stage];
+}
+
+// Fill the tile table of a stage for the given tile height.
+static void fill_tiles(TcBatch& b, int rows) {
+    b.tile_start[0] = 0;
+    for (int i = 0; i < b.nviews; ++i) {
+        TcJob& j = b.job[i];
+        j.tiles_x = (j.W + kTileM - 1) / kTileM;
+        const int ty = (j.H + rows - 1) / rows;
+        b.tile_start[i + 1] = b.tile_start[i] + j.tiles_x * ty;
+    }
+}
+
+cudaError_t tc_launch_stage(int stage, int variant, TcBatch& b, int ctas_per_sm, cudaStream_t stream) {
+    if (stage < 0 || stage >= kTcStages || variant < 0 || variant >= kStages[stage].n) return cudaErrorInvalidValue;
+    const Variant& v = kStages[stage].v[variant];
+    fill_tiles(b, v.R);
+    return v.fn(b, ctas_per_sm, stream);
 }
 
 const char* const kInferKernelNamesBf16[kInferKernelsBf16] = {
     "bf16_enc0_gather", "bf16_enc1", "bf16_bottleneck", "bf16_dec1", "bf16_dec0_head"};
 
-cudaError_t launch_infer_bf16(const GatherParams& g, const float* params, const uint16_t* img,
-                              const Activations& act, float* vis, int* err, cudaStream_t stream,
-                              const StageEvents& se) {
+// Jobs of the five stages for a list of views (one Activations per view).
+void tc_make_batches(const GatherParams* g, const Activations* act, float* const* vis, int n, const float* params,
+                     const uint16_t* img, int* err, TcBatch* out) {
     const LayerOffsets off = layer_offsets();
     const BF16Images im = bf16_images();
-    const int H = g.H, W = g.W;
     auto I = [&](int layer) { return reinterpret_cast<const uint4*>(img + im.img_off[layer]); };
-    cudaError_t e;
-    TcArgs a{};
-    a.g = g; a.err = err;
-    // level 0 encoder fused with the gather
-    a.H = H; a.W = W;
-    a.b3img = I(ENC0_3); a.b1img = I(ENC0_1);
-    a.bias3 = params + off.b[ENC0_3]; a.bias1 = params + off.b[ENC0_1];
-    a.out = static_cast<uint16_t*>(act.e0);
-    se.rec(0);
-    if ((e = launch_tc<4, 16, 16, 4, TPRO_GATHER, TEPI_POOL>(a, stream)) != cudaSuccess) return e;
-    // level 1 encoder
-    a = TcArgs{}; a.g = g; a.err = err;
-    a.H = H / 2; a.W = W / 2;
-    a.in = static_cast<const uint16_t*>(act.e0);
-    a.b3img = I(ENC1_3); a.b1img = I(ENC1_1);
-    a.bias3 = params + off.b[ENC1_3]; a.bias1 = params + off.b[ENC1_1];
-    a.out_skip = static_cast<uint16_t*>(act.s1);
-    a.out = static_cast<uint16_t*>(act.p1);
-    se.rec(1);
-    if ((e = launch_tc<16, 32, 32, 2, TPRO_PLAIN, TEPI_SKIP_POOL>(a, stream)) != cudaSuccess) return e;
-    // bottleneck
-    a = TcArgs{}; a.g = g; a.err = err;
-    a.H = H / 4; a.W = W / 4;
-    a.in = static_cast<const uint16_t*>(act.p1);
-    a.b3img = I(BOTT_3); a.b1img = I(BOTT_1);
-    a.bias3 = params + off.b[BOTT_3]; a.bias1 = params + off.b[BOTT_1];
-    a.out = static_cast<uint16_t*>(act.bo);
-    se.rec(2);
-    if ((e = launch_tc<32, 64, 32, 2, TPRO_PLAIN, TEPI_STORE>(a, stream)) != cudaSuccess) return e;
-    // level 1 decoder
-    a = TcArgs{}; a.g = g; a.err = err;
-    a.H = H / 2; a.W = W / 2;
-    a.in = static_cast<const uint16_t*>(act.bo);
-    a.skip = static_cast<const uint16_t*>(act.s1);
-    a.b3img = I(DEC1_3); a.b1img = I(DEC1_1);
-    a.bias3 = params + off.b[DEC1_3]; a.bias1 = params + off.b[DEC1_1];
-    a.out = static_cast<uint16_t*>(act.d1);
-    se.rec(3);
-    if ((e = launch_tc<32, 32, 16, 2, TPRO_UP_SKIP, TEPI_STORE>(a, stream)) != cudaSuccess) return e;
-    // level 0 decoder + head
-    a = TcArgs{}; a.g = g; a.err = err;
-    a.H = H; a.W = W;
-    a.in = static_cast<const uint16_t*>(act.d1);
-    a.b3img = I(DEC0_3); a.b1img = I(DEC0_1);
-    a.bias3 = params + off.b[DEC0_3]; a.bias1 = params + off.b[DEC0_1];
-    a.head = params + off.w[HEAD];  // head weights followed by its bias
-    a.vis = vis;
-    se.rec(4);
-    e = launch_tc<16, 16, 16, 4, TPRO_UP, TEPI_HEAD>(a, stream);
-    se.rec(5);
-    return e;
+    const int l3[kTcStages] = {ENC0_3, ENC1_3, BOTT_3, DEC1_3, DEC0_3};
+    const int l1[kTcStages] = {ENC0_1, ENC1_1, BOTT_1, DEC1_1, DEC0_1};
+    for (int s = 0; s < kTcStages; ++s) {
+        TcBatch& b = out[s];
+        b = TcBatch{};
+        b.nviews = n;
+        b.b3img = I(l3[s]);
+        b.b1img = I(l1[s]);
+        b.bias3 = params + off.b[l3[s]];
+        b.bias1 = params + off.b[l1[s]];
+        b.head = params + off.w[HEAD];  // head weights followed by its bias
+        b.err = err;
+        for (int i = 0; i < n; ++i) {
+            TcJob& j = b.job[i];
+            j.g = g[i];
+            const int H = g[i].H, W = g[i].W;
+            const Activations& A = act[i];
+            switch (s) {
+                case 0: j.H = H; j.W = W; j.out = static_cast<uint16_t*>(A.e0); break;
+                case 1: j.H = H / 2; j.W = W / 2; j.in = static_cast<const uint16_t*>(A.e0);
+                        j.out_skip = static_cast<uint16_t*>(A.s1); j.out = static_cast<uint16_t*>(A.p1); break;
+                case 2: j.H = H / 4; j.W = W / 4; j.in = static_cast<const uint16_t*>(A.p1);
+                        j.out = static_cast<uint16_t*>(A.bo); break;
+                case 3: j.H = H / 2; j.W = W / 2; j.in = static_cast<const uint16_t*>(A.bo);
+                        j.skip = static_cast<const uint16_t*>(A.s1); j.out = static_cast<uint16_t*>(A.d1); break;
+                default: j.H = H; j.W = W; j.in = static_cast<const uint16_t*>(A.d1); j.vis = vis[i]; break;
+            }
+        }
+    }
+}
+
+cudaError_t launch_infer_bf16(const GatherParams& g, const float* params, const uint16_t* img,
+                              const Activations& act, float* vis, int* err, cudaStream_t stream,
+                              const StageEvents& se, const int* variant, const int* ctas) {
+    TcBatch b[kTcStages];
+    float* vp[1] = {vis};
+    tc_make_batches(&g, &act, vp, 1, params, img, err, b);
+    for (int s = 0; s < kTcStages; ++s) {
+        se.rec(s);
+        cudaError_t e = tc_launch_stage(s, variant ? variant[s] : tc_default_variant(s), b[s],
+                                        ctas ? ctas[s] : 0, stream);
+        if (e != cudaSuccess) return e;
+    }
+    se.rec(kTcStages);
+    return cudaSuccess;
 }
 
 }  // namespace nsm

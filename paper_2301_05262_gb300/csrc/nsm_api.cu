@@ -10,19 +10,9 @@
 #include "../../include/nsm.h"
 #include "nsm_internal.h"
 
-struct nsm_ctx {
-    int device;
-    int* d_err;  // device error word (bounded waits that gave up)
-    std::vector<cudaEvent_t> stage_events;  // profiling hook (caller-owned events)
-};
+#include "ctx_internal.h"
 
-struct nsm_weights {
-    int device;
-    float* d_params;   // canonical FP32 vector (nsm_param_count floats)
-    uint16_t* d_bf16;  // packed BF16 images (tensor-core form)
-    void* d_descs;     // packing table
-    int ndesc;
-};
+
 
 namespace nsm {
 
@@ -185,6 +175,7 @@ nsm_status nsm_ctx_create(nsm_ctx** out) {
     if (s != NSM_OK) return s;
     nsm_ctx* c = new nsm_ctx{};
     cudaGetDevice(&c->device);
+    for (int st = 0; st < kTcStages; ++st) { c->tc_variant[st] = tc_default_variant(st); c->tc_ctas[st] = 0; }
     cudaError_t e = cudaMalloc(&c->d_err, sizeof(int) * 4);
     if (e != cudaSuccess) { delete c; return cuda_fail(e, "cudaMalloc(error word)"); }
     e = cudaMemset(c->d_err, 0, sizeof(int) * 4);
@@ -195,6 +186,7 @@ nsm_status nsm_ctx_create(nsm_ctx** out) {
 
 void nsm_ctx_destroy(nsm_ctx* c) {
     if (!c) return;
+    ctx_release_graph(c);
     cudaFree(c->d_err);
     delete c;
 }
@@ -346,7 +338,8 @@ nsm_status nsm_infer(nsm_ctx* ctx, const nsm_frame* frame, const nsm_weights* w,
     }
     cudaError_t e = (precision == NSM_FP32)
         ? launch_infer_fp32(g, w->d_params, act, vis_out, static_cast<cudaStream_t>(stream), se)
-        : launch_infer_bf16(g, w->d_params, w->d_bf16, act, vis_out, ctx->d_err, static_cast<cudaStream_t>(stream), se);
+        : launch_infer_bf16(g, w->d_params, w->d_bf16, act, vis_out, ctx->d_err, static_cast<cudaStream_t>(stream), se,
+                            ctx->tc_variant, ctx->tc_ctas);
     if (e != cudaSuccess) return cuda_fail(e, "inference kernel launch");
     return NSM_OK;
 }

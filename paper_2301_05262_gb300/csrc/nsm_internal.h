@@ -86,6 +86,6 @@ constexpr int kInferKernelsBf16 = 5;
 extern const char* const kInferKernelNamesBf16[kInferKernelsBf16];
 cudaError_t launch_infer_bf16(const GatherParams& g, const float* params, const uint16_t* img,
                               const Activations& act, float* vis, int* err, cudaStream_t stream,
-                              const StageEvents& se);
+                              const StageEvents& se, const int* variant, const int* ctas);
 
 }  // namespace nsm

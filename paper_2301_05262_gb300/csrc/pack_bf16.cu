@@ -1,0 +1,81 @@
+// Packing of the network weights into the tensor-core operand images
+// (shared-memory layout of each layer's B operand, BF16 hi + lo parts).
+#include <cuda_bf16.h>
+
+#include "nsm_internal.h"
+
+namespace nsm {
+
+// ------------------------------------------------------------------ weight packing
+// Shared-memory images of the BF16 weights, each weight w stored as
+// hi = bf16(w) in one image and lo = bf16(w - hi) in a second image right
+// after it (16-byte chunks of 8 K values):
+//   3x3, C_in >= 16:  chunk (tap, g, n) = W[n][8g .. 8g+7][tap]
+//   3x3 first level:  chunk (k, h, n)   = tap t = 2k + h (t < 9), channels
+//                     [c0..c3 | c0..c3] (the same weight for the hi and lo
+//                     parts of each feature), zero for t = 9
+//   1x1:              chunk (g, n)      = W[n][8g .. 8g+7]
+using PackDesc = PackDescHost;
+
+__global__ void pack_bf16_kernel(const float* __restrict__ params, uint16_t* __restrict__ img,
+                                 const PackDesc* __restrict__ descs, int ndesc) {
+    for (int d = 0; d < ndesc; ++d) {
+        const PackDesc pd = descs[d];
+        for (size_t i = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; i < pd.count;
+             i += static_cast<size_t>(gridDim.x) * blockDim.x) {
+            const int e = static_cast<int>(i % 8);
+            const size_t chunk = i / 8;
+            float v = 0.f;
+            if (pd.kind == 0) {  // 3x3 general: chunk = (tap * (cin/8) + g) * cout + n
+                const int n = static_cast<int>(chunk % pd.cout);
+                const size_t t2 = chunk / pd.cout;
+                const int g = static_cast<int>(t2 % (pd.cin / 8));
+                const int tap = static_cast<int>(t2 / (pd.cin / 8));
+                v = params[pd.w_off + (static_cast<size_t>(n) * pd.cin + 8 * g + e) * 9 + tap];
+            } else if (pd.kind == 1) {  // first level hi/lo: chunk = (k * 2 + h) * cout + n
+                const int n = static_cast<int>(chunk % pd.cout);
+                const int kh = static_cast<int>(chunk / pd.cout);
+                const int tap = kh;  // = 2k + h
+                if (tap < 9) v = params[pd.w_off + (static_cast<size_t>(n) * 4 + (e % 4)) * 9 + tap];
+            } else {  // 1x1: chunk = g * cout + n
+                const int n = static_cast<int>(chunk % pd.cout);
+                const int g = static_cast<int>(chunk / pd.cout);
+                v = params[pd.w_off + static_cast<size_t>(n) * pd.cin + 8 * g + e];
+            }
+            const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+            const __nv_bfloat16 lo = __float2bfloat16_rn(v - __bfloat162float(hi));
+            img[pd.img_off + i] = __bfloat16_as_ushort(hi);
+            img[pd.img_off + pd.count + i] = __bfloat16_as_ushort(lo);
+        }
+    }
+}
+
+BF16Images bf16_images() {
+    const LayerOffsets off = layer_offsets();
+    BF16Images im{};
+    size_t pos = 0;
+    auto add = [&](int layer, int kind) {
+        const int ci = kLayers[layer].cin, co = kLayers[layer].cout;
+        size_t count;
+        if (kind == 0) count = static_cast<size_t>(9) * ci * co;
+        else if (kind == 1) count = static_cast<size_t>(10) * co * 8;
+        else count = static_cast<size_t>(ci) * co;
+        im.desc[im.n] = {kind, ci, co, off.w[layer], pos, count};
+        im.img_off[layer] = pos;
+        pos += 2 * count;  // hi image, then lo image (counts are multiples of 8)
+        ++im.n;
+    };
+    add(ENC0_3, 1); add(ENC0_1, 2); add(ENC1_3, 0); add(ENC1_1, 2); add(BOTT_3, 0); add(BOTT_1, 2);
+    add(DEC1_3, 0); add(DEC1_1, 2); add(DEC0_3, 0); add(DEC0_1, 2);
+    im.total = pos;
+    return im;
+}
+
+cudaError_t launch_pack_bf16(const float* params, uint16_t* img, const void* dev_descs, int ndesc, cudaStream_t stream) {
+    pack_bf16_kernel<<<64, 256, 0, stream>>>(params, img, static_cast<const PackDesc*>(dev_descs), ndesc);
+    return cudaGetLastError();
+}
+
+size_t pack_desc_bytes() { return sizeof(PackDesc); }
+
+}  // namespace nsm

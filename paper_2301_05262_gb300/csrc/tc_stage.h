@@ -1,0 +1,54 @@
+// Job tables of the tensor-core level kernels (net_bf16.cu): one launch per
+// stage serves up to kMaxViews views of any size.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "nsm_common.cuh"
+
+namespace nsm {
+
+constexpr int kMaxViews = 32;
+constexpr int kTcStages = 5;  // enc0 (+ gather), enc1, bottleneck, dec1, dec0 (+ head)
+
+enum TcPro { TPRO_GATHER = 0, TPRO_PLAIN = 1, TPRO_UP_SKIP = 2, TPRO_UP = 3 };
+enum TcEpi { TEPI_POOL = 0, TEPI_SKIP_POOL = 1, TEPI_STORE = 2, TEPI_HEAD = 3 };
+
+// One view's work in one stage.
+struct TcJob {
+    GatherParams g;             // GATHER prologue: the view's G-buffer, map, emitter, camera
+    int H, W;                   // the stage's resolution for this view
+    int tiles_x;                // tiles per row (filled at launch)
+    const uint16_t* in;         // BF16 NHWC: PLAIN [H][W][CIN]; UP* [H/2][W/2][CIN]
+    const uint16_t* skip;       // UP_SKIP: [H][W][CIN]
+    uint16_t* out;              // POOL / SKIP_POOL: [H/2][W/2][COUT] (pooled); STORE: [H][W][COUT]
+    uint16_t* out_skip;         // SKIP_POOL: [H][W][COUT]
+    float* vis;                 // HEAD: [H][W]
+};
+
+// Kernel parameter of a stage launch (passed by value, __grid_constant__).
+struct TcBatch {
+    int nviews;
+    int tile_start[kMaxViews + 1];  // prefix sums of the views' tile counts
+    TcJob job[kMaxViews];
+    const uint4* b3img;         // packed 3x3 weights (shared-memory image, hi then lo)
+    const uint4* b1img;         // packed 1x1 weights
+    const float* bias3;
+    const float* bias1;
+    const float* head;          // head weights [16] then its bias
+    int* err;                   // device error word
+};
+
+struct Activations;
+
+int tc_stage_variants(int stage);
+int tc_stage_rows(int stage, int variant);
+int tc_default_variant(int stage);
+const void* tc_stage_kernel(int stage, int variant);
+int tc_stage_occupancy(int stage, int variant);
+void tc_make_batches(const GatherParams* g, const Activations* act, float* const* vis, int n, const float* params,
+                     const uint16_t* img, int* err, TcBatch* out);
+cudaError_t tc_launch_stage(int stage, int variant, TcBatch& b, int ctas_per_sm, cudaStream_t stream);
+
+}  // namespace nsm
