@@ -230,6 +230,16 @@ def run_ours(args):
 
     forms = {}
     precisions = [p for p in args.precisions.split(",") if p]
+    plan = None
+    if "bf16" in precisions and not args.no_autotune:
+        # the library's autotuner picks every stage's tile height and CTAs per SM on this frame
+        vtmp = torch.empty((H, W), dtype=torch.float32, device=device)
+        views = nsm.make_views([fr], [vtmp])
+        ws_t = torch.empty((nsm.nsm_infer_batched_workspace_bytes(views),), dtype=torch.uint8, device=device)
+        nsm.nsm_autotune(ctx, views, weights, ws_t, reps=5)
+        rows, ctas, ms = nsm.nsm_autotune_report(ctx)
+        plan = {"tile_rows": rows, "ctas_per_sm": ctas, "tuned_stage_ms": [round(x, 5) for x in ms]}
+        del ws_t, vtmp
     for pname in precisions:
         prec = nsm.PRECISIONS[pname]
         knames = nsm.nsm_infer_kernel_names(prec)
@@ -357,7 +367,7 @@ def run_ours(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32" if head == "fp32" else head,
             "data": "synthetic (seeded ray-cast scene, He-init weights)",
             "config": {"workload": WORKLOAD, "precision": head, "l2": "flushed (256 MiB write) between timed steps",
-                       "parallelism": f"{world} independent frame(s), one per GPU"},
+                       "parallelism": f"{world} independent frame(s), one per GPU", "autotuned_plan": plan},
             "forms": {k: {kk: vv for kk, vv in v.items() if kk != "clocks"} for k, v in forms.items()},
             "error_vs_fp64_oracle": errs,
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
@@ -380,6 +390,7 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-error", action="store_true")
     ap.add_argument("--skip-e2e", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--size", default=None, help="WxH view size (profiling runs); default 1920x1080")
     args = ap.parse_args()
     if args.size:

@@ -20,9 +20,12 @@
 // (ky, kx) chunks further on, so the im2col matrix is never built.  The 3x3
 // result goes TMEM -> registers (bias, ReLU) -> shared memory as BF16 hi + lo
 // parts, the A operand of the 1x1 MMA (written into the same TMEM columns).
-// Weights are BF16 hi + lo images: each K step runs against both, and the
-// 1x1 adds A_hi B_hi + A_hi B_lo + A_lo B_hi, so weight and intermediate
-// rounding leave no trace beyond ~2^-16; only the level outputs are BF16.
+// Weights are BF16 hi + lo parts stacked along N: one MMA of width 2 C per K
+// step yields x W_hi and x W_lo side by side in TMEM, summed in the
+// epilogue; the 1x1 runs (A_hi + A_lo) [W_hi; W_lo] as two MMAs.  Weight and
+// intermediate rounding so leave no trace beyond ~2^-16 and only the level
+// outputs are BF16.  (A 128 x N x 16 MMA costs about the same issue time for
+// any N <= 64 on this part, so widening N is nearly free, unlike extra MMAs.)
 //
 // First level: the four FP32 features are split into BF16 hi + lo parts
 // (f = hi + lo to ~2^-16 relative), 8 "channels" per pixel; K steps pair two
@@ -30,8 +33,25 @@
 // steps with a zero-weight pad.  This keeps the depth-test features
 // (z / z_f near 1, z - z_f near 0) at near-FP32 resolution.
 //
-// 256 threads (8 warps) per CTA: all stage the input; warp w reads TMEM lane
-// quarter w % 4 and the two warpgroups split the epilogue rows.
+// Warp-specialised pipeline, 13 warps per CTA:
+//   warps 4-11 producers: PLAIN copies tile i straight into input buffer i % 2
+//              with cp.async; GATHER / UP* prefetch tile i + 1's raw inputs
+//              (G-buffer, or the coarser level) into raw buffer (i + 1) % 2
+//              with cp.async while they compute tile i from raw buffer i % 2
+//              (texel lookups, features / bilinear x2 (+ skip)) into input
+//              buffer i % 2
+//   warp 12    MMA issuer (one thread) and TMEM owner: the 3x3 of tile i into
+//              accumulator buffer i % 2, then its 1x1 into the same columns
+//   warps 0-3  epilogue: TMEM lane quarter = warp; 3x3 result -> 1x1 operand,
+//              1x1 result -> outputs
+// mbarriers (every wait is bounded and gives up when another role aborted):
+//   gfull[b]  producers' cp.async -> producers: raw buffer b landed (256 arrivals)
+//   rfree[b]  producers -> producers: raw buffer b consumed (256 arrivals)
+//   full[b]   producers -> MMA: input buffer b staged (256 arrivals)
+//   mma3[b]   MMA -> epilogue: 3x3 of buffer b done; -> producers: buffer b free
+//   a1full    epilogue -> MMA: 1x1 operand written (128 arrivals)
+//   mma1      MMA -> epilogue: 1x1 done (and its operand free)
+//   tfree[b]  epilogue -> MMA: accumulator buffer b read out (128 arrivals)
 #include "nsm_internal.h"
 #include "tc_common.cuh"
 #include "tc_stage.h"
@@ -40,42 +60,52 @@ namespace nsm {
 
 using namespace tc;
 
-constexpr int kNT = 256;         // threads per CTA
+constexpr int kNP = 256;         // producer threads (warps 4-11)
+constexpr int kNT = 128 + kNP + 32;  // threads per CTA: 4 epilogue warps, 8 producer warps, 1 MMA warp
+constexpr int kMmaWarp = (128 + kNP) / 32;
 constexpr int kTileM = 128;      // pixels per MMA row block
 constexpr int kSW = 136;         // staged pixels per row (128 + halo + pad)
+constexpr int kNCC = 66;         // coarse-level columns behind one tile
 constexpr uint64_t kWaitNs = 2000000000ull;  // 2 s bound on every mbarrier wait
 
 template <int CIN, int CMID, int COUT, int R, int PRO>
 struct TcCfg {
     static constexpr bool SPLIT = (PRO == TPRO_GATHER);
+    static constexpr bool UP = (PRO == TPRO_UP || PRO == TPRO_UP_SKIP);
     static constexpr int CG_IN = SPLIT ? 1 : CIN / 8;
     static constexpr int KSTEPS3 = SPLIT ? 5 : 9 * (CIN / 16);
-    static constexpr int A0_CHUNKS = CG_IN * (R + 2) * kSW;
+    static constexpr int A0_CHUNKS = CG_IN * (R + 2) * kSW;     // one input buffer
     // 3x3 -> 1x1 intermediate as BF16 hi + lo parts: [row][part][channel group][pixel]
     static constexpr int A1_CHUNKS = R * 2 * (CMID / 8) * kTileM;
-    // weights as BF16 hi + lo images (hi image first, then lo image)
-    static constexpr int B3_IMG = KSTEPS3 * 2 * CMID;
-    static constexpr int B1_IMG = (CMID / 8) * COUT;
-    static constexpr int B3_CHUNKS = 2 * B3_IMG;
-    static constexpr int B1_CHUNKS = 2 * B1_IMG;
-    static constexpr int OFF_A0 = 0;
-    static constexpr int OFF_A1 = OFF_A0 + A0_CHUNKS * 16;
-    static constexpr int OFF_B3 = OFF_A1 + A1_CHUNKS * 16;
+    // raw prefetch buffer (two): the staged G-buffer (pos, nrm) or the coarse rows
+    static constexpr int NCR = R / 2 + 2;
+    static constexpr int RAW_BYTES = SPLIT ? (R + 2) * 130 * 32 : (UP ? NCR * kNCC * CIN * 2 : 0);
+    // weights as BF16 hi + lo parts stacked along the output rows (2 C rows per K block)
+    static constexpr int N3 = 2 * CMID, N1 = 2 * COUT;             // MMA widths
+    static constexpr int B3_CHUNKS = KSTEPS3 * 2 * N3;
+    static constexpr int B1_CHUNKS = (CMID / 8) * N1;
+    static constexpr int OFF_A0 = 0;                                // two input buffers
+    static constexpr int OFF_A1 = OFF_A0 + 2 * A0_CHUNKS * 16;
+    static constexpr int OFF_RAW = OFF_A1 + A1_CHUNKS * 16;         // two raw buffers
+    static constexpr int OFF_B3 = OFF_RAW + 2 * RAW_BYTES;
     static constexpr int OFF_B1 = OFF_B3 + B3_CHUNKS * 16;
     static constexpr int OFF_BIAS3 = OFF_B1 + B1_CHUNKS * 16;
     static constexpr int OFF_BIAS1 = OFF_BIAS3 + CMID * 4;
     static constexpr int OFF_HEAD = OFF_BIAS1 + COUT * 4;
     static constexpr int OFF_BAR = ((OFF_HEAD + (COUT + 1) * 4) + 15) / 16 * 16;
-    static constexpr int BYTES_USED = OFF_BAR + 32;
-    static constexpr int TMEM_COLS_RAW = R * CMID;
+    static constexpr int BYTES_USED = OFF_BAR + 128;
+    static constexpr int TMEM_BUF = R * N3;                         // columns of one accumulator buffer
+    static constexpr int TMEM_COLS_RAW = 2 * TMEM_BUF;
     static constexpr int TMEM_COLS = TMEM_COLS_RAW < 32 ? 32 : TMEM_COLS_RAW;
     // enough shared memory per CTA that the CTAs resident on one SM can never
     // ask for more than its 512 TMEM columns (228 KB of shared memory per SM)
     static constexpr int TMEM_CAP = 512 / TMEM_COLS;
     static constexpr int BYTES_MIN = (236 * 1024) / (TMEM_CAP + 1);
     static constexpr int BYTES = BYTES_USED < BYTES_MIN ? BYTES_MIN : BYTES_USED;
-    static_assert(TMEM_COLS == 32 || TMEM_COLS == 64 || TMEM_COLS == 128 || TMEM_COLS == 256, "TMEM columns");
+    static_assert(TMEM_COLS == 32 || TMEM_COLS == 64 || TMEM_COLS == 128 || TMEM_COLS == 256 || TMEM_COLS == 512,
+                  "TMEM columns");
     static_assert(CMID % 16 == 0 && COUT % 16 == 0 && COUT <= CMID, "channel shapes");
+    static_assert(!UP || (R % 2 == 0), "up-sampling stages need an even tile height");
     static_assert(BYTES_USED <= 227 * 1024, "shared memory");
 };
 
@@ -83,8 +113,42 @@ __device__ __forceinline__ void st_shared_v4(uint32_t addr, uint4 v) {
     asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" :: "r"(addr), "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w)
                  : "memory");
 }
-__device__ __forceinline__ uint4 ldg_v4(const void* p) {
-    return __ldg(reinterpret_cast<const uint4*>(p));
+__device__ __forceinline__ uint4 ld_shared_v4(uint32_t addr) {
+    uint4 v;
+    asm volatile("ld.shared.v4.b32 {%0, %1, %2, %3}, [%4];" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "r"(addr)
+                 : "memory");
+    return v;
+}
+__device__ __forceinline__ float4 ld_shared_f4(uint32_t addr) {
+    const uint4 u = ld_shared_v4(addr);
+    return make_float4(__uint_as_float(u.x), __uint_as_float(u.y), __uint_as_float(u.z), __uint_as_float(u.w));
+}
+// 16-byte asynchronous copy global -> shared; src_bytes = 0 writes zeros
+__device__ __forceinline__ void cp_async16(uint32_t saddr, const void* src, uint32_t src_bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" :: "r"(saddr), "l"(src), "r"(src_bytes) : "memory");
+}
+// arrive on mbar once every cp.async this thread issued so far has landed
+__device__ __forceinline__ void cp_async_arrive(uint64_t* mbar) {
+    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" :: "r"(smem_u32(mbar)) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* mbar) {
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" :: "r"(smem_u32(mbar))
+                 : "memory");
+}
+// Bounded wait that also gives up when another role of the CTA has aborted.
+__device__ __forceinline__ bool wait_phase(uint64_t* mbar, uint32_t parity, const volatile int* abort_flag) {
+    if (mbar_try_wait(mbar, parity)) return true;
+    uint64_t t0;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+    for (uint32_t it = 0; it < (1u << 30); ++it) {
+        __nanosleep(64);
+        if (mbar_try_wait(mbar, parity)) return true;
+        if (*abort_flag) return false;
+        uint64_t t;
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+        if (t - t0 > kWaitNs) return false;
+    }
+    return false;
 }
 
 // 8 BF16 values of a chunk -> FP32
@@ -97,26 +161,182 @@ __device__ __forceinline__ uint4 f32_to_chunk(const float* f) {
                       pack_bf16x2(f[6], f[7]));
 }
 
+// ------------------------------------------------------------------ producer pieces
+// (pt = producer thread 0..kNP-1; staged rows y0-1 .. y0+R, pixels x0-1 .. x0+128)
+
+// PLAIN (and the skip part of UP_SKIP): NHWC BF16 tile straight into the input
+// buffer, zeros outside the image
+template <int CIN, int R>
+__device__ __forceinline__ void copy_tile(const uint16_t* src, int H, int W, int y0, int x0, uint32_t a0, int pt) {
+    constexpr int CG = CIN / 8;
+    constexpr uint32_t kPlane = (R + 2) * kSW * 16;
+    // each thread owns (pixel column, channel group) items and walks the staged rows
+    for (int ci = pt; ci < 130 * CG; ci += kNP) {
+        const int cg = ci % CG, sp = ci / CG;
+        const int gx = x0 - 1 + sp;
+        const bool okx = gx >= 0 && gx < W;
+        const uint32_t dst = a0 + cg * kPlane + 16 * sp;
+#pragma unroll
+        for (int sr = 0; sr < R + 2; ++sr) {
+            const int gy = y0 - 1 + sr;
+            const bool ok = okx && gy >= 0 && gy < H;
+            const uint16_t* s = ok ? src + (static_cast<size_t>(gy) * W + gx) * CIN + cg * 8 : src;
+            cp_async16(dst + 16 * (sr * kSW), s, ok ? 16u : 0u);
+        }
+    }
+}
+
+// GATHER raw: pos4 / nrm4 of the staged pixels in bounds, 32 bytes per pixel
+template <int R>
+__device__ __forceinline__ void prefetch_gbuffer(const TcJob& job, int y0, int x0, uint32_t raw, int pt) {
+    const int H = job.H, W = job.W;
+    for (int idx = pt; idx < (R + 2) * 130 * 2; idx += kNP) {
+        const int part = idx & 1, q = idx >> 1;
+        const int sr = q / 130, sp = q % 130;
+        const int gy = y0 - 1 + sr, gx = x0 - 1 + sp;
+        if (gy >= 0 && gy < H && gx >= 0 && gx < W)
+            cp_async16(raw + 16 * idx, (part ? job.g.nrm4 : job.g.pos4) + static_cast<size_t>(gy) * W + gx, 16);
+    }
+}
+
+// UP raw: the coarse rows y0/2-1 .. y0/2+R/2 and columns x0/2-1 .. x0/2+64 in bounds
+template <int CIN, int R>
+__device__ __forceinline__ void prefetch_coarse(const TcJob& job, int y0, int x0, uint32_t raw, int pt) {
+    constexpr int CG = CIN / 8, NCR = R / 2 + 2;
+    const int Hl = job.H / 2, Wl = job.W / 2;
+    const int cy0 = y0 / 2 - 1, cx0 = x0 / 2 - 1;
+    for (int idx = pt; idx < NCR * kNCC * CG; idx += kNP) {
+        const int cg = idx % CG, q = idx / CG;
+        const int gy = cy0 + q / kNCC, gx = cx0 + q % kNCC;
+        if (gy >= 0 && gy < Hl && gx >= 0 && gx < Wl)
+            cp_async16(raw + 16 * idx, job.in + (static_cast<size_t>(gy) * Wl + gx) * CIN + cg * 8, 16);
+    }
+}
+
+// GATHER compute: features of the staged pixels from the raw G-buffer, the
+// shadow-map texel fetched per pixel (all of a thread's fetches in flight
+// together), BF16 hi + lo chunks into the input buffer
+template <int R>
+__device__ __forceinline__ void compute_gather(const TcJob& job, int y0, int x0, uint32_t raw, uint32_t a0, int pt) {
+    constexpr int NSP = 131;  // staged pixel 130 is the zero pad read by the dummy tap
+    constexpr int ITEMS = (R + 2) * NSP;
+    constexpr int NPT = (ITEMS + kNP - 1) / kNP;
+    const GatherParams g = job.g;  // one copy per tile: the view index is only known at run time
+    const int H = job.H, W = job.W;
+    float4 P[NPT], Nv[NPT];
+    float z[NPT];
+    bool ok[NPT];
+#pragma unroll
+    for (int k = 0; k < NPT; ++k) {
+        const int idx = pt + kNP * k;
+        const int sr = idx / NSP, sp = idx % NSP;
+        const int gy = y0 - 1 + sr, gx = x0 - 1 + sp;
+        ok[k] = idx < ITEMS && sp < 130 && gy >= 0 && gy < H && gx >= 0 && gx < W;
+        z[k] = g.z_far;
+        if (ok[k]) {
+            const uint32_t q = static_cast<uint32_t>(sr * 130 + sp);
+            P[k] = ld_shared_f4(raw + 32 * q);
+            Nv[k] = ld_shared_f4(raw + 32 * q + 16);
+            const int tx = texel_index(g, P[k].x, P[k].y, P[k].z);
+            if (tx >= 0) z[k] = __ldg(g.sm + tx);
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < NPT; ++k) {
+        const int idx = pt + kNP * k;
+        if (idx < ITEMS) {
+            const int sr = idx / NSP, sp = idx % NSP;
+            uint4 chunk = make_uint4(0, 0, 0, 0);
+            if (ok[k]) {
+                float f[4];
+                pixel_features(g, P[k], Nv[k], z[k], f);
+                float hl[8];
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    const float hf = __bfloat162float(__float2bfloat16_rn(f[c]));
+                    hl[c] = hf;
+                    hl[4 + c] = f[c] - hf;
+                }
+                chunk = f32_to_chunk(hl);
+            }
+            st_shared_v4(a0 + 16 * (sr * kSW + sp), chunk);
+        }
+    }
+}
+
+// UP / UP_SKIP compute: bilinear x2 of the raw coarse rows (+ the skip
+// already copied into the input buffer) -> BF16 chunks of the input buffer
+template <int CIN, int R, bool SKIP>
+__device__ __forceinline__ void compute_up(const TcJob& job, int y0, int x0, uint32_t raw, uint32_t a0, int pt) {
+    constexpr int CG = CIN / 8;
+    constexpr uint32_t kPlane = (R + 2) * kSW * 16;
+    const int H = job.H, W = job.W, Hl = H / 2, Wl = W / 2;
+    const int cy0 = y0 / 2 - 1, cx0 = x0 / 2 - 1;
+    // each thread owns (pixel column, channel group) items and walks the staged rows
+    for (int ci = pt; ci < 130 * CG; ci += kNP) {
+        const int cg = ci % CG, sp = ci / CG;
+        const int gx = x0 - 1 + sp;
+        const bool okx = gx >= 0 && gx < W;
+        const BilinTap tx = bilin_tap(okx ? gx : 0, Wl);
+        const uint32_t c0 = raw + 16 * ((tx.i0 - cx0) * CG + cg);  // coarse column i0, row cy0
+        const uint32_t c1 = raw + 16 * ((tx.i1 - cx0) * CG + cg);
+        const uint32_t dst = a0 + cg * kPlane + 16 * sp;
+#pragma unroll 2
+        for (int sr = 0; sr < R + 2; ++sr) {
+            const int gy = y0 - 1 + sr;
+            uint4 val = make_uint4(0, 0, 0, 0);
+            if (okx && gy >= 0 && gy < H) {
+                const BilinTap ty = bilin_tap(gy, Hl);
+                const uint32_t r0 = 16 * ((ty.i0 - cy0) * kNCC * CG), r1 = 16 * ((ty.i1 - cy0) * kNCC * CG);
+                float p00[8], p01[8], p10[8], p11[8], o[8];
+                chunk_to_f32(ld_shared_v4(c0 + r0), p00);
+                chunk_to_f32(ld_shared_v4(c1 + r0), p01);
+                chunk_to_f32(ld_shared_v4(c0 + r1), p10);
+                chunk_to_f32(ld_shared_v4(c1 + r1), p11);
+#pragma unroll
+                for (int c = 0; c < 8; ++c) {
+                    const float q0 = p00[c] * tx.w0 + p01[c] * tx.w1;
+                    const float q1 = p10[c] * tx.w0 + p11[c] * tx.w1;
+                    o[c] = q0 * ty.w0 + q1 * ty.w1;
+                }
+                if constexpr (SKIP) {
+                    float sk[8];
+                    chunk_to_f32(ld_shared_v4(dst + 16 * (sr * kSW)), sk);
+#pragma unroll
+                    for (int c = 0; c < 8; ++c) o[c] += sk[c];
+                }
+                val = f32_to_chunk(o);
+            }
+            st_shared_v4(dst + 16 * (sr * kSW), val);
+        }
+    }
+}
+
 template <int CIN, int CMID, int COUT, int R, int PRO, int EPI>
-__global__ void __launch_bounds__(kNT, 2) level_tc_kernel(const __grid_constant__ TcBatch a) {
+__global__ void __launch_bounds__(kNT, 1) level_tc_kernel(const __grid_constant__ TcBatch a) {
     using C = TcCfg<CIN, CMID, COUT, R, PRO>;
     extern __shared__ __align__(1024) unsigned char smem[];
     const uint32_t sbase = smem_u32(smem);
-    const uint32_t sA0 = sbase + C::OFF_A0, sA1 = sbase + C::OFF_A1;
+    const uint32_t sA0 = sbase + C::OFF_A0, sA1 = sbase + C::OFF_A1, sRAW = sbase + C::OFF_RAW;
     const uint32_t sB3 = sbase + C::OFF_B3, sB1 = sbase + C::OFF_B1;
     float* bias3_s = reinterpret_cast<float*>(smem + C::OFF_BIAS3);
     float* bias1_s = reinterpret_cast<float*>(smem + C::OFF_BIAS1);
     float* head_s = reinterpret_cast<float*>(smem + C::OFF_HEAD);
-    uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + C::OFF_BAR);
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + C::OFF_BAR + 8);
-    int* s_abort = reinterpret_cast<int*>(smem + C::OFF_BAR + 12);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + C::OFF_BAR);
+    uint64_t* full = bar;          // [2]
+    uint64_t* mma3 = bar + 2;      // [2]
+    uint64_t* tfree = bar + 4;     // [2]
+    uint64_t* a1full = bar + 6;
+    uint64_t* mma1 = bar + 7;
+    uint64_t* gfull = bar + 8;     // [2]
+    uint64_t* rfree = bar + 10;    // [2]
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + C::OFF_BAR + 96);
+    volatile int* s_abort = reinterpret_cast<volatile int*>(smem + C::OFF_BAR + 100);
 
     const int tid = threadIdx.x;
     const int warp = tid >> 5;
-    const int wg = warp >> 2;          // warpgroup: splits the epilogue rows
-    const int m = tid & 127;           // pixel of the row block = TMEM lane
 
-    // ---- one-time set-up: weights, barrier, TMEM
+    // ---- one-time set-up: weights, barriers, TMEM
     for (int i = tid; i < C::B3_CHUNKS; i += kNT) st_shared_v4(sB3 + 16 * i, __ldg(a.b3img + i));
     for (int i = tid; i < C::B1_CHUNKS; i += kNT) st_shared_v4(sB1 + 16 * i, __ldg(a.b1img + i));
     for (int i = tid; i < CMID; i += kNT) bias3_s[i] = __ldg(a.bias3 + i);
@@ -124,312 +344,302 @@ __global__ void __launch_bounds__(kNT, 2) level_tc_kernel(const __grid_constant_
     if (EPI == TEPI_HEAD)
         for (int i = tid; i <= COUT; i += kNT) head_s[i] = __ldg(a.head + i);
     if (tid == 0) {
-        mbar_init(mbar, 1);
+        for (int k = 0; k < 2; ++k) {
+            mbar_init(full + k, kNP);
+            mbar_init(mma3 + k, 1);
+            mbar_init(tfree + k, 128);
+            mbar_init(gfull + k, kNP);
+            mbar_init(rfree + k, kNP);
+        }
+        mbar_init(a1full, 128);
+        mbar_init(mma1, 1);
         fence_mbar_init();
         *s_abort = 0;
     }
-    if (warp == 0) tmem_alloc(tslot, C::TMEM_COLS);
+    if (warp == kMmaWarp) tmem_alloc(tslot, C::TMEM_COLS);
+    fence_proxy_async_smem();  // the weights are read by the tensor core
     fence_before_sync();
     __syncthreads();
     fence_after_sync();
     const uint32_t tbase = *tslot;
-    const uint32_t tlane = tbase + (static_cast<uint32_t>((warp & 3) * 32) << 16);
-    uint32_t phase = 0;
-
-    constexpr uint32_t kPlane = (R + 2) * kSW * 16;  // bytes between channel groups of A0
     const int ntiles = a.tile_start[a.nviews];
-    int v = 0;
 
-    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        while (tile >= a.tile_start[v + 1]) ++v;
-        const TcJob& job = a.job[v];
-        const int H = job.H, W = job.W;
-        const int local = tile - a.tile_start[v];
-        const int y0 = (local / job.tiles_x) * R;
-        const int x0 = (local % job.tiles_x) * kTileM;
-
-        // ---------------- prologue: stage the (R+2) x 130 input tile (zero padded)
-        if constexpr (PRO == TPRO_GATHER) {
-            // staged pixels -1 .. 129 of each row (129 = zero pad read by the dummy tap);
-            // each thread gathers NPT of them in three batched phases so that its
-            // G-buffer loads, then its shadow-map loads, are all in flight together
-            constexpr int NSP = 131;
-            constexpr int ITEMS = (R + 2) * NSP;
-            constexpr int NPT = (ITEMS + kNT - 1) / kNT;
-            const GatherParams& g = job.g;
-            float4 P[NPT], Nv[NPT];
-            bool ok[NPT];
-#pragma unroll
-            for (int k = 0; k < NPT; ++k) {
-                const int idx = tid + kNT * k;
-                const int sr = idx / NSP, sp = idx % NSP;
-                const int gy = y0 - 1 + sr, gx = x0 - 1 + sp;
-                ok[k] = idx < ITEMS && sp < 130 && gy >= 0 && gy < H && gx >= 0 && gx < W;
-                if (ok[k]) {
-                    const size_t p = static_cast<size_t>(gy) * W + gx;
-                    P[k] = __ldg(g.pos4 + p);
-                    Nv[k] = __ldg(g.nrm4 + p);
-                }
-            }
-            float z[NPT];
-#pragma unroll
-            for (int k = 0; k < NPT; ++k) {
-                const int tx = ok[k] ? texel_index(g, P[k].x, P[k].y, P[k].z) : -1;
-                z[k] = g.z_far;
-                if (tx >= 0) z[k] = __ldg(g.sm + tx);
-            }
-#pragma unroll
-            for (int k = 0; k < NPT; ++k) {
-                const int idx = tid + kNT * k;
-                if (idx < ITEMS) {
-                    const int sr = idx / NSP, sp = idx % NSP;
-                    uint4 chunk = make_uint4(0, 0, 0, 0);
-                    if (ok[k]) {
-                        float f[4];
-                        pixel_features(g, P[k], Nv[k], z[k], f);
-                        float hl[8];
-#pragma unroll
-                        for (int c = 0; c < 4; ++c) {
-                            const float hf = __bfloat162float(__float2bfloat16_rn(f[c]));
-                            hl[c] = hf;
-                            hl[4 + c] = f[c] - hf;
-                        }
-                        chunk = f32_to_chunk(hl);
-                    }
-                    st_shared_v4(sA0 + 16 * (sr * kSW + sp), chunk);
-                }
-            }
-        } else if constexpr (PRO == TPRO_PLAIN) {
-            constexpr int CG = CIN / 8;
-#pragma unroll 4
-            for (int idx = tid; idx < (R + 2) * 130 * CG; idx += kNT) {
-                const int cg = idx % CG;
-                const int t = idx / CG;
-                const int sp = t % 130, sr = t / 130;
-                const int gy = y0 - 1 + sr, gx = x0 - 1 + sp;
-                uint4 val = make_uint4(0, 0, 0, 0);
-                if (gy >= 0 && gy < H && gx >= 0 && gx < W)
-                    val = ldg_v4(job.in + (static_cast<size_t>(gy) * W + gx) * CIN + cg * 8);
-                st_shared_v4(sA0 + cg * kPlane + 16 * (sr * kSW + sp), val);
-            }
-        } else {  // UP_SKIP / UP
-            constexpr int CG = CIN / 8;
-            const int Hl = H / 2, Wl = W / 2;
-#pragma unroll 2
-            for (int idx = tid; idx < (R + 2) * 130 * CG; idx += kNT) {
-                const int cg = idx % CG;
-                const int t = idx / CG;
-                const int sp = t % 130, sr = t / 130;
-                const int gy = y0 - 1 + sr, gx = x0 - 1 + sp;
-                uint4 val = make_uint4(0, 0, 0, 0);
-                if (gy >= 0 && gy < H && gx >= 0 && gx < W) {
-                    const BilinTap ty = bilin_tap(gy, Hl), tx = bilin_tap(gx, Wl);
-                    float p00[8], p01[8], p10[8], p11[8], o[8];
-                    chunk_to_f32(ldg_v4(job.in + (static_cast<size_t>(ty.i0) * Wl + tx.i0) * CIN + cg * 8), p00);
-                    chunk_to_f32(ldg_v4(job.in + (static_cast<size_t>(ty.i0) * Wl + tx.i1) * CIN + cg * 8), p01);
-                    chunk_to_f32(ldg_v4(job.in + (static_cast<size_t>(ty.i1) * Wl + tx.i0) * CIN + cg * 8), p10);
-                    chunk_to_f32(ldg_v4(job.in + (static_cast<size_t>(ty.i1) * Wl + tx.i1) * CIN + cg * 8), p11);
-#pragma unroll
-                    for (int c = 0; c < 8; ++c) {
-                        const float r0 = p00[c] * tx.w0 + p01[c] * tx.w1;
-                        const float r1 = p10[c] * tx.w0 + p11[c] * tx.w1;
-                        o[c] = r0 * ty.w0 + r1 * ty.w1;
-                    }
-                    if constexpr (PRO == TPRO_UP_SKIP) {
-                        float s[8];
-                        chunk_to_f32(ldg_v4(job.skip + (static_cast<size_t>(gy) * W + gx) * CIN + cg * 8), s);
-#pragma unroll
-                        for (int c = 0; c < 8; ++c) o[c] += s[c];
-                    }
-                    val = f32_to_chunk(o);
-                }
-                st_shared_v4(sA0 + cg * kPlane + 16 * (sr * kSW + sp), val);
+    if (warp >= 4 && warp < kMmaWarp) {
+        // ================= producers
+        const int pt = tid - 128;
+        auto locate = [&](int tile, int& v, int& y0, int& x0) -> const TcJob& {
+            while (tile >= a.tile_start[v + 1]) ++v;
+            const TcJob& job = a.job[v];
+            const int local = tile - a.tile_start[v];
+            y0 = (local / job.tiles_x) * R;
+            x0 = (local % job.tiles_x) * kTileM;
+            return job;
+        };
+        int v = 0, vn = 0, it = 0;
+        if constexpr (PRO != TPRO_PLAIN) {
+            // prefetch the first tile's raw inputs (and skip) into buffer 0
+            if (blockIdx.x < ntiles) {
+                int y0, x0;
+                const TcJob& job = locate(blockIdx.x, vn, y0, x0);
+                if constexpr (PRO == TPRO_GATHER) prefetch_gbuffer<R>(job, y0, x0, sRAW, pt);
+                else prefetch_coarse<CIN, R>(job, y0, x0, sRAW, pt);
+                if constexpr (PRO == TPRO_UP_SKIP) copy_tile<CIN, R>(job.skip, job.H, job.W, y0, x0, sA0, pt);
+                cp_async_arrive(gfull + 0);
             }
         }
-        fence_proxy_async_smem();
-        fence_before_sync();
-        __syncthreads();
-
-        // ---------------- 3x3 convolution: R row blocks of 128 x CMID; each K step
-        // twice, against the hi and the lo image of the weights
-        if (tid == 0) {
-            fence_after_sync();
-            constexpr uint32_t id3 = idesc_bf16(128, CMID);
-            constexpr uint32_t kB3lo = 16 * C::B3_IMG;  // byte offset of the lo image
-            for (int r = 0; r < R; ++r) {
-                const uint32_t d = tbase + r * CMID;
-                if constexpr (C::SPLIT) {
-#pragma unroll
-                    for (int k = 0; k < 5; ++k) {
-                        const int t0 = 2 * k, t1 = 2 * k + 1;
-                        const uint32_t a0 = sA0 + 16 * ((r + t0 / 3) * kSW + t0 % 3);
-                        const uint32_t lbo = (t1 < 9) ? 16 * ((r + t1 / 3) * kSW + t1 % 3) - 16 * ((r + t0 / 3) * kSW + t0 % 3) : 16;
-                        const uint64_t ad = smem_desc(a0, lbo, 128);
-                        const uint32_t b0 = sB3 + 16 * (k * 2 * CMID);
-                        mma_bf16(d, ad, smem_desc(b0, CMID * 16, 128), id3, k > 0);
-                        mma_bf16(d, ad, smem_desc(b0 + kB3lo, CMID * 16, 128), id3, 1);
+        bool failed = false;
+        for (int tile = blockIdx.x; tile < ntiles && !failed; tile += gridDim.x, ++it) {
+            const int b = it & 1;
+            const uint32_t A0 = sA0 + b * (C::A0_CHUNKS * 16);
+            int y0, x0;
+            const TcJob& job = locate(tile, v, y0, x0);
+            if constexpr (PRO == TPRO_PLAIN) {
+                if (it >= 2 && !wait_phase(mma3 + b, ((it >> 1) - 1) & 1, s_abort)) { failed = true; break; }
+                copy_tile<CIN, R>(job.in, job.H, job.W, y0, x0, A0, pt);
+                cp_async_arrive(full + b);
+            } else {
+                // prefetch tile it + 1 into the other raw buffer (and its skip into the other input buffer)
+                const int next = tile + gridDim.x;
+                if (next < ntiles) {
+                    const int nb = b ^ 1;
+                    const int un = (it + 1) >> 1;  // use index of buffer nb for tile it + 1
+                    if (un >= 1 && !wait_phase(rfree + nb, (un - 1) & 1, s_abort)) { failed = true; break; }
+                    if (PRO == TPRO_UP_SKIP && un >= 1 && !wait_phase(mma3 + nb, (un - 1) & 1, s_abort)) {
+                        failed = true;
+                        break;
                     }
-                } else {
-#pragma unroll
-                    for (int tap = 0; tap < 9; ++tap) {
-#pragma unroll
-                        for (int kk = 0; kk < CIN / 16; ++kk) {
-                            const uint32_t a0 = sA0 + (2 * kk) * kPlane + 16 * ((r + tap / 3) * kSW + tap % 3);
-                            const uint64_t ad = smem_desc(a0, kPlane, 128);
-                            const uint32_t b0 = sB3 + 16 * ((tap * C::CG_IN + 2 * kk) * CMID);
-                            mma_bf16(d, ad, smem_desc(b0, CMID * 16, 128), id3, (tap | kk) != 0);
-                            mma_bf16(d, ad, smem_desc(b0 + kB3lo, CMID * 16, 128), id3, 1);
-                        }
-                    }
+                    int ny0, nx0;
+                    const TcJob& nj = locate(next, vn, ny0, nx0);
+                    const uint32_t nraw = sRAW + nb * C::RAW_BYTES;
+                    if constexpr (PRO == TPRO_GATHER) prefetch_gbuffer<R>(nj, ny0, nx0, nraw, pt);
+                    else prefetch_coarse<CIN, R>(nj, ny0, nx0, nraw, pt);
+                    if constexpr (PRO == TPRO_UP_SKIP)
+                        copy_tile<CIN, R>(nj.skip, nj.H, nj.W, ny0, nx0, sA0 + nb * (C::A0_CHUNKS * 16), pt);
+                    cp_async_arrive(gfull + nb);
                 }
+                // this tile's raw inputs
+                if (!wait_phase(gfull + b, (it >> 1) & 1, s_abort)) { failed = true; break; }
+                if (PRO != TPRO_UP_SKIP && it >= 2 && !wait_phase(mma3 + b, ((it >> 1) - 1) & 1, s_abort)) {
+                    failed = true;
+                    break;
+                }
+                const uint32_t raw = sRAW + b * C::RAW_BYTES;
+                if constexpr (PRO == TPRO_GATHER) compute_gather<R>(job, y0, x0, raw, A0, pt);
+                else compute_up<CIN, R, PRO == TPRO_UP_SKIP>(job, y0, x0, raw, A0, pt);
+                fence_proxy_async_smem();
+                mbar_arrive(full + b);
+                mbar_arrive(rfree + b);
             }
-            mma_commit(mbar);
         }
-        if (!mbar_wait_bounded(mbar, phase, kWaitNs)) {
-            atomicExch(a.err, 1);
+        if (failed) {
+            atomicExch(a.err, 3);
             *s_abort = 1;
         }
-        phase ^= 1;
-        __syncthreads();
-        if (*s_abort) break;
-        fence_after_sync();
-
-        // ---------------- epilogue 1: bias + ReLU -> BF16 hi + lo -> A operand of the 1x1
-        constexpr int kA1Part = (CMID / 8) * kTileM;  // chunks per part of one row
-        for (int r = wg; r < R; r += 2) {
-#pragma unroll
-            for (int c0 = 0; c0 < CMID; c0 += 16) {
-                float val[16], lo[16];
-                tmem_ld16(tlane + r * CMID + c0, val);
-                tmem_ld_wait();
-#pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    val[j] = fmaxf(val[j] + bias3_s[c0 + j], 0.f);
-                    const float hi = __bfloat162float(__float2bfloat16_rn(val[j]));
-                    lo[j] = val[j] - hi;
-                    val[j] = hi;
+    } else if (warp == kMmaWarp) {
+        // ================= MMA issuer
+        if ((tid & 31) == 0) {
+            constexpr uint32_t id3 = idesc_bf16(128, C::N3);
+            constexpr uint32_t id1 = idesc_bf16(128, C::N1);
+            constexpr uint32_t kPlane = (R + 2) * kSW * 16;
+            constexpr int kA1Part = (CMID / 8) * kTileM;
+            int it = 0;
+            for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
+                const int b = it & 1;
+                if (!wait_phase(full + b, (it >> 1) & 1, s_abort) ||
+                    (it >= 2 && !wait_phase(tfree + b, ((it >> 1) - 1) & 1, s_abort))) {
+                    atomicExch(a.err, 4);
+                    *s_abort = 1;
+                    break;
                 }
-                const int cg = c0 / 8;
-                const uint32_t row = sA1 + 16 * (r * 2 * kA1Part);
-                st_shared_v4(row + 16 * (cg * kTileM + m), f32_to_chunk(val));
-                st_shared_v4(row + 16 * ((cg + 1) * kTileM + m), f32_to_chunk(val + 8));
-                st_shared_v4(row + 16 * (kA1Part + cg * kTileM + m), f32_to_chunk(lo));
-                st_shared_v4(row + 16 * (kA1Part + (cg + 1) * kTileM + m), f32_to_chunk(lo + 8));
-            }
-        }
-        fence_proxy_async_smem();
-        fence_before_sync();
-        __syncthreads();
-
-        // ---------------- 1x1 convolution into the same TMEM columns:
-        // A_hi B_hi + A_hi B_lo + A_lo B_hi per K step
-        if (tid == 0) {
-            fence_after_sync();
-            constexpr uint32_t id1 = idesc_bf16(128, COUT);
-            constexpr uint32_t kB1lo = 16 * C::B1_IMG;
-            for (int r = 0; r < R; ++r) {
-                const uint32_t row = sA1 + 16 * (r * 2 * kA1Part);
+                fence_proxy_async_smem();  // cp.async / st.shared data -> tensor core
+                fence_after_sync();
+                const uint32_t A0 = sA0 + b * (C::A0_CHUNKS * 16);
+                const uint32_t D = tbase + b * C::TMEM_BUF;
+                // 3x3: one MMA of width 2 CMID per K step (hi and lo weights stacked)
+                for (int r = 0; r < R; ++r) {
+                    const uint32_t d = D + r * C::N3;
+                    if constexpr (C::SPLIT) {
 #pragma unroll
-                for (int kk = 0; kk < CMID / 16; ++kk) {
-                    const uint64_t ahi = smem_desc(row + 16 * (2 * kk * kTileM), kTileM * 16, 128);
-                    const uint64_t alo = smem_desc(row + 16 * (kA1Part + 2 * kk * kTileM), kTileM * 16, 128);
-                    const uint32_t b0 = sB1 + 16 * (2 * kk * COUT);
-                    const uint64_t bhi = smem_desc(b0, COUT * 16, 128);
-                    const uint64_t blo = smem_desc(b0 + kB1lo, COUT * 16, 128);
-                    mma_bf16(tbase + r * CMID, ahi, bhi, id1, kk > 0);
-                    mma_bf16(tbase + r * CMID, ahi, blo, id1, 1);
-                    mma_bf16(tbase + r * CMID, alo, bhi, id1, 1);
-                }
-            }
-            mma_commit(mbar);
-        }
-        if (!mbar_wait_bounded(mbar, phase, kWaitNs)) {
-            atomicExch(a.err, 2);
-            *s_abort = 1;
-        }
-        phase ^= 1;
-        __syncthreads();
-        if (*s_abort) break;
-        fence_after_sync();
-
-        // ---------------- epilogue 2
-        const int ox = x0 + m;
-        if constexpr (EPI == TEPI_POOL || EPI == TEPI_SKIP_POOL) {
-            for (int r = 2 * wg; r < R; r += 4) {  // row pairs (r, r + 1), alternating warpgroups
-                float s[COUT];
-#pragma unroll
-                for (int c0 = 0; c0 < COUT; c0 += 16) {
-                    float v0[16], v1[16];
-                    tmem_ld16(tlane + r * CMID + c0, v0);
-                    tmem_ld16(tlane + (r + 1) * CMID + c0, v1);
-                    tmem_ld_wait();
-#pragma unroll
-                    for (int j = 0; j < 16; ++j) {
-                        v0[j] = fmaxf(v0[j] + bias1_s[c0 + j], 0.f);
-                        v1[j] = fmaxf(v1[j] + bias1_s[c0 + j], 0.f);
-                        s[c0 + j] = v0[j] + v1[j];
-                    }
-                    if constexpr (EPI == TEPI_SKIP_POOL) {
-                        const int oy = y0 + r;
-                        if (oy < H && ox < W) {
-                            uint16_t* dst = job.out_skip + (static_cast<size_t>(oy) * W + ox) * COUT + c0;
-                            reinterpret_cast<uint4*>(dst)[0] = f32_to_chunk(v0);
-                            reinterpret_cast<uint4*>(dst)[1] = f32_to_chunk(v0 + 8);
-                            dst += static_cast<size_t>(W) * COUT;
-                            reinterpret_cast<uint4*>(dst)[0] = f32_to_chunk(v1);
-                            reinterpret_cast<uint4*>(dst)[1] = f32_to_chunk(v1 + 8);
-                        }
-                    }
-                }
-#pragma unroll
-                for (int c = 0; c < COUT; ++c) s[c] = 0.25f * (s[c] + __shfl_xor_sync(0xffffffffu, s[c], 1));
-                const int oy = y0 + r;
-                if (oy < H && ox < W) {
-                    // even pixel writes the first half of the channels, odd the second
-                    const int half = (m & 1) * (COUT / 2);
-                    uint16_t* dst = job.out + (static_cast<size_t>(oy / 2) * (W / 2) + ox / 2) * COUT + half;
-#pragma unroll
-                    for (int c = 0; c < COUT / 2; c += 8) {
-                        float t8[8];
-#pragma unroll
-                        for (int j = 0; j < 8; ++j) t8[j] = s[half + c + j];
-                        reinterpret_cast<uint4*>(dst + c)[0] = f32_to_chunk(t8);
-                    }
-                }
-            }
-        } else {
-            for (int r = wg; r < R; r += 2) {
-                const int oy = y0 + r;
-                float hsum = 0.f;
-#pragma unroll
-                for (int c0 = 0; c0 < COUT; c0 += 16) {
-                    float val[16];
-                    tmem_ld16(tlane + r * CMID + c0, val);
-                    tmem_ld_wait();
-#pragma unroll
-                    for (int j = 0; j < 16; ++j) val[j] = fmaxf(val[j] + bias1_s[c0 + j], 0.f);
-                    if constexpr (EPI == TEPI_STORE) {
-                        if (oy < H && ox < W) {
-                            uint16_t* dst = job.out + (static_cast<size_t>(oy) * W + ox) * COUT + c0;
-                            reinterpret_cast<uint4*>(dst)[0] = f32_to_chunk(val);
-                            reinterpret_cast<uint4*>(dst)[1] = f32_to_chunk(val + 8);
+                        for (int k = 0; k < 5; ++k) {
+                            const int t0 = 2 * k, t1 = 2 * k + 1;
+                            const uint32_t a0 = A0 + 16 * ((r + t0 / 3) * kSW + t0 % 3);
+                            const uint32_t lbo = (t1 < 9) ? 16 * ((r + t1 / 3) * kSW + t1 % 3) - 16 * ((r + t0 / 3) * kSW + t0 % 3) : 16;
+                            mma_bf16(d, smem_desc(a0, lbo, 128), smem_desc(sB3 + 16 * (k * 2 * C::N3), C::N3 * 16, 128),
+                                     id3, k > 0);
                         }
                     } else {
 #pragma unroll
-                        for (int j = 0; j < 16; ++j) hsum = fmaf(head_s[c0 + j], val[j], hsum);
+                        for (int tap = 0; tap < 9; ++tap) {
+#pragma unroll
+                            for (int kk = 0; kk < CIN / 16; ++kk) {
+                                const uint32_t a0 = A0 + (2 * kk) * kPlane + 16 * ((r + tap / 3) * kSW + tap % 3);
+                                const uint32_t b0 = sB3 + 16 * ((tap * C::CG_IN + 2 * kk) * C::N3);
+                                mma_bf16(d, smem_desc(a0, kPlane, 128), smem_desc(b0, C::N3 * 16, 128), id3,
+                                         (tap | kk) != 0);
+                            }
+                        }
                     }
                 }
-                if (EPI == TEPI_HEAD && oy < H && ox < W)
-                    job.vis[static_cast<size_t>(oy) * W + ox] = sigmoidf_acc(hsum + head_s[COUT]);
+                mma_commit(mma3 + b);
+                // 1x1 once the epilogue has written its operand: (A_hi + A_lo) [B_hi; B_lo]
+                if (!wait_phase(a1full, it & 1, s_abort)) {
+                    atomicExch(a.err, 5);
+                    *s_abort = 1;
+                    break;
+                }
+                fence_after_sync();
+                for (int r = 0; r < R; ++r) {
+                    const uint32_t row = sA1 + 16 * (r * 2 * kA1Part);
+#pragma unroll
+                    for (int kk = 0; kk < CMID / 16; ++kk) {
+                        const uint64_t ahi = smem_desc(row + 16 * (2 * kk * kTileM), kTileM * 16, 128);
+                        const uint64_t alo = smem_desc(row + 16 * (kA1Part + 2 * kk * kTileM), kTileM * 16, 128);
+                        const uint64_t bd = smem_desc(sB1 + 16 * (2 * kk * C::N1), C::N1 * 16, 128);
+                        mma_bf16(D + r * C::N3, ahi, bd, id1, kk > 0);
+                        mma_bf16(D + r * C::N3, alo, bd, id1, 1);
+                    }
+                }
+                mma_commit(mma1);
             }
         }
-        fence_before_sync();
-        __syncthreads();  // TMEM columns, A0 and A1 are free for the next tile
+        __syncwarp();
+    } else {
+        // ================= epilogue (warps 0-3; warp = TMEM lane quarter)
+        const int m = tid;  // pixel of the row block = TMEM lane
+        const uint32_t tlane = tbase + (static_cast<uint32_t>(warp * 32) << 16);
+        constexpr int kA1Part = (CMID / 8) * kTileM;
+        int v = 0, it = 0;
+        for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
+            const int b = it & 1;
+            while (tile >= a.tile_start[v + 1]) ++v;
+            const TcJob& job = a.job[v];
+            const int H = job.H, W = job.W;
+            const int local = tile - a.tile_start[v];
+            const int y0 = (local / job.tiles_x) * R;
+            const int x0 = (local % job.tiles_x) * kTileM;
+            const uint32_t Dl = tlane + b * C::TMEM_BUF;
+            if (!wait_phase(mma3 + b, (it >> 1) & 1, s_abort)) {
+                atomicExch(a.err, 1);
+                *s_abort = 1;
+                break;
+            }
+            fence_after_sync();
+            // ---- 3x3 result: bias + ReLU -> BF16 hi + lo -> operand of the 1x1
+            for (int r = 0; r < R; ++r) {
+#pragma unroll
+                for (int c0 = 0; c0 < CMID; c0 += 16) {
+                    float val[16], lo[16];
+                    tmem_ld16(Dl + r * C::N3 + c0, val);         // x W_hi
+                    tmem_ld16(Dl + r * C::N3 + CMID + c0, lo);   // x W_lo
+                    tmem_ld_wait();
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        val[j] = fmaxf(val[j] + lo[j] + bias3_s[c0 + j], 0.f);
+                        const float hi = __bfloat162float(__float2bfloat16_rn(val[j]));
+                        lo[j] = val[j] - hi;
+                        val[j] = hi;
+                    }
+                    const int cg = c0 / 8;
+                    const uint32_t row = sA1 + 16 * (r * 2 * kA1Part);
+                    st_shared_v4(row + 16 * (cg * kTileM + m), f32_to_chunk(val));
+                    st_shared_v4(row + 16 * ((cg + 1) * kTileM + m), f32_to_chunk(val + 8));
+                    st_shared_v4(row + 16 * (kA1Part + cg * kTileM + m), f32_to_chunk(lo));
+                    st_shared_v4(row + 16 * (kA1Part + (cg + 1) * kTileM + m), f32_to_chunk(lo + 8));
+                }
+            }
+            fence_proxy_async_smem();
+            fence_before_sync();
+            mbar_arrive(a1full);
+            if (!wait_phase(mma1, it & 1, s_abort)) {
+                atomicExch(a.err, 2);
+                *s_abort = 1;
+                break;
+            }
+            fence_after_sync();
+            // ---- 1x1 result -> outputs
+            const int ox = x0 + m;
+            if constexpr (EPI == TEPI_POOL || EPI == TEPI_SKIP_POOL) {
+                for (int r = 0; r < R; r += 2) {
+                    float s[COUT];
+#pragma unroll
+                    for (int c0 = 0; c0 < COUT; c0 += 16) {
+                        float v0[16], v1[16], w0[16], w1[16];
+                        tmem_ld16(Dl + r * C::N3 + c0, v0);
+                        tmem_ld16(Dl + r * C::N3 + COUT + c0, w0);
+                        tmem_ld16(Dl + (r + 1) * C::N3 + c0, v1);
+                        tmem_ld16(Dl + (r + 1) * C::N3 + COUT + c0, w1);
+                        tmem_ld_wait();
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) {
+                            v0[j] = fmaxf(v0[j] + w0[j] + bias1_s[c0 + j], 0.f);
+                            v1[j] = fmaxf(v1[j] + w1[j] + bias1_s[c0 + j], 0.f);
+                            s[c0 + j] = v0[j] + v1[j];
+                        }
+                        if constexpr (EPI == TEPI_SKIP_POOL) {
+                            const int oy = y0 + r;
+                            if (oy < H && ox < W) {
+                                uint16_t* dst = job.out_skip + (static_cast<size_t>(oy) * W + ox) * COUT + c0;
+                                reinterpret_cast<uint4*>(dst)[0] = f32_to_chunk(v0);
+                                reinterpret_cast<uint4*>(dst)[1] = f32_to_chunk(v0 + 8);
+                                dst += static_cast<size_t>(W) * COUT;
+                                reinterpret_cast<uint4*>(dst)[0] = f32_to_chunk(v1);
+                                reinterpret_cast<uint4*>(dst)[1] = f32_to_chunk(v1 + 8);
+                            }
+                        }
+                    }
+#pragma unroll
+                    for (int c = 0; c < COUT; ++c) s[c] = 0.25f * (s[c] + __shfl_xor_sync(0xffffffffu, s[c], 1));
+                    const int oy = y0 + r;
+                    if (oy < H && ox < W) {
+                        // even pixel writes the first half of the channels, odd the second
+                        const int half = (m & 1) * (COUT / 2);
+                        uint16_t* dst = job.out + (static_cast<size_t>(oy / 2) * (W / 2) + ox / 2) * COUT + half;
+#pragma unroll
+                        for (int c = 0; c < COUT / 2; c += 8) {
+                            float t8[8];
+#pragma unroll
+                            for (int j = 0; j < 8; ++j) t8[j] = s[half + c + j];
+                            reinterpret_cast<uint4*>(dst + c)[0] = f32_to_chunk(t8);
+                        }
+                    }
+                }
+            } else {
+                for (int r = 0; r < R; ++r) {
+                    const int oy = y0 + r;
+                    float hsum = 0.f;
+#pragma unroll
+                    for (int c0 = 0; c0 < COUT; c0 += 16) {
+                        float val[16], lo[16];
+                        tmem_ld16(Dl + r * C::N3 + c0, val);
+                        tmem_ld16(Dl + r * C::N3 + COUT + c0, lo);
+                        tmem_ld_wait();
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) val[j] = fmaxf(val[j] + lo[j] + bias1_s[c0 + j], 0.f);
+                        if constexpr (EPI == TEPI_STORE) {
+                            if (oy < H && ox < W) {
+                                uint16_t* dst = job.out + (static_cast<size_t>(oy) * W + ox) * COUT + c0;
+                                reinterpret_cast<uint4*>(dst)[0] = f32_to_chunk(val);
+                                reinterpret_cast<uint4*>(dst)[1] = f32_to_chunk(val + 8);
+                            }
+                        } else {
+#pragma unroll
+                            for (int j = 0; j < 16; ++j) hsum = fmaf(head_s[c0 + j], val[j], hsum);
+                        }
+                    }
+                    if (EPI == TEPI_HEAD && oy < H && ox < W)
+                        job.vis[static_cast<size_t>(oy) * W + ox] = sigmoidf_acc(hsum + head_s[COUT]);
+                }
+            }
+            fence_before_sync();
+            mbar_arrive(tfree + b);
+        }
     }
 
+    // wait for every cp.async of this thread before the CTA ends
+    asm volatile("cp.async.wait_all;" ::: "memory");
     __syncthreads();
     fence_after_sync();
-    if (warp == 0) tmem_dealloc(tbase, C::TMEM_COLS);
+    if (warp == kMmaWarp) tmem_dealloc(tbase, C::TMEM_COLS);
 }
 
 // ------------------------------------------------------------------ variants and launch
@@ -498,8 +708,7 @@ static const Variant kVarBott[] = {
     NSM_VARIANT(1, 32, 64, 32, 1, TPRO_PLAIN, TEPI_STORE),
     NSM_VARIANT(2, 32, 64, 32, 2, TPRO_PLAIN, TEPI_STORE)};
 static const Variant kVarDec1[] = {
-    NSM_VARIANT(2, 32, 32, 16, 2, TPRO_UP_SKIP, TEPI_STORE),
-    NSM_VARIANT(4, 32, 32, 16, 4, TPRO_UP_SKIP, TEPI_STORE)};
+    NSM_VARIANT(2, 32, 32, 16, 2, TPRO_UP_SKIP, TEPI_STORE)};
 static const Variant kVarDec0[] = {
     NSM_VARIANT(2, 16, 16, 16, 2, TPRO_UP, TEPI_HEAD),
     NSM_VARIANT(4, 16, 16, 16, 4, TPRO_UP, TEPI_HEAD),
@@ -507,7 +716,7 @@ static const Variant kVarDec0[] = {
 
 struct StageTable { const Variant* v; int n; };
 static const StageTable kStages[kTcStages] = {
-    {kVarEnc0, 3}, {kVarEnc1, 2}, {kVarBott, 2}, {kVarDec1, 2}, {kVarDec0, 3}};
+    {kVarEnc0, 3}, {kVarEnc1, 2}, {kVarBott, 2}, {kVarDec1, 1}, {kVarDec0, 3}};
 
 int tc_stage_variants(int stage) { return (stage >= 0 && stage < kTcStages) ? kStages[stage].n : 0; }
 int tc_stage_rows(int stage, int variant) { return kStages[stage].v[variant].R; }

@@ -8,8 +8,9 @@ namespace nsm {
 
 // ------------------------------------------------------------------ weight packing
 // Shared-memory images of the BF16 weights, each weight w stored as
-// hi = bf16(w) in one image and lo = bf16(w - hi) in a second image right
-// after it (16-byte chunks of 8 K values):
+// hi = bf16(w) and lo = bf16(w - hi), stacked along the output rows of every
+// K block (rows 0 .. c_out-1 hi, rows c_out .. 2 c_out-1 lo), so one MMA of
+// width 2 c_out multiplies by both (16-byte chunks of 8 K values):
 //   3x3, C_in >= 16:  chunk (tap, g, n) = W[n][8g .. 8g+7][tap]
 //   3x3 first level:  chunk (k, h, n)   = tap t = 2k + h (t < 9), channels
 //                     [c0..c3 | c0..c3] (the same weight for the hi and lo
@@ -44,8 +45,12 @@ __global__ void pack_bf16_kernel(const float* __restrict__ params, uint16_t* __r
             }
             const __nv_bfloat16 hi = __float2bfloat16_rn(v);
             const __nv_bfloat16 lo = __float2bfloat16_rn(v - __bfloat162float(hi));
-            img[pd.img_off + i] = __bfloat16_as_ushort(hi);
-            img[pd.img_off + pd.count + i] = __bfloat16_as_ushort(lo);
+            // hi and lo weights stacked along the output rows of each K block:
+            // rows [0, cout) hold the hi parts, rows [cout, 2 cout) the lo parts
+            const size_t blk = chunk / pd.cout, n = chunk % pd.cout;
+            const size_t base = blk * 2 * pd.cout;
+            img[pd.img_off + (base + n) * 8 + e] = __bfloat16_as_ushort(hi);
+            img[pd.img_off + (base + pd.cout + n) * 8 + e] = __bfloat16_as_ushort(lo);
         }
     }
 }
@@ -62,7 +67,7 @@ BF16Images bf16_images() {
         else count = static_cast<size_t>(ci) * co;
         im.desc[im.n] = {kind, ci, co, off.w[layer], pos, count};
         im.img_off[layer] = pos;
-        pos += 2 * count;  // hi image, then lo image (counts are multiples of 8)
+        pos += 2 * count;  // hi and lo parts (counts are multiples of 8)
         ++im.n;
     };
     add(ENC0_3, 1); add(ENC0_1, 2); add(ENC1_3, 0); add(ENC1_1, 2); add(BOTT_3, 0); add(BOTT_1, 2);
