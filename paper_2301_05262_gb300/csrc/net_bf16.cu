@@ -82,7 +82,10 @@ struct TcCfg {
     static constexpr int RAW_BYTES = SPLIT ? (R + 2) * 130 * 32 : (UP ? NCR * kNCC * CIN * 2 : 0);
     // weights as BF16 hi + lo parts stacked along the output rows (2 C rows per K block)
     static constexpr int N3 = 2 * CMID, N1 = 2 * COUT;             // MMA widths
-    static constexpr int B3_CHUNKS = KSTEPS3 * 2 * N3;
+    // row-stacked 3x3: the kernel rows ky = 0, 1, 2 stacked along N as well, so
+    // one MMA over staged input row j accumulates into output rows j, j-1, j-2
+    static constexpr bool STACK = 3 * N3 <= 256;
+    static constexpr int B3_CHUNKS = STACK ? (SPLIT ? 12 * N3 : 9 * CG_IN * N3) : KSTEPS3 * 2 * N3;
     static constexpr int B1_CHUNKS = (CMID / 8) * N1;
     static constexpr int OFF_A0 = 0;                                // two input buffers
     static constexpr int OFF_A1 = OFF_A0 + 2 * A0_CHUNKS * 16;
@@ -92,7 +95,9 @@ struct TcCfg {
     static constexpr int OFF_BIAS3 = OFF_B1 + B1_CHUNKS * 16;
     static constexpr int OFF_BIAS1 = OFF_BIAS3 + CMID * 4;
     static constexpr int OFF_HEAD = OFF_BIAS1 + COUT * 4;
-    static constexpr int OFF_BAR = ((OFF_HEAD + (COUT + 1) * 4) + 15) / 16 * 16;
+    static constexpr int OFF_ZERO = ((OFF_HEAD + (COUT + 1) * 4) + 127) / 128 * 128;  // zero A operand
+    static constexpr int ZERO_BYTES = STACK ? kTileM * 16 + 128 : 0;
+    static constexpr int OFF_BAR = OFF_ZERO + ZERO_BYTES;
     static constexpr int BYTES_USED = OFF_BAR + 128;
     static constexpr int TMEM_BUF = R * N3;                         // columns of one accumulator buffer
     static constexpr int TMEM_COLS_RAW = 2 * TMEM_BUF;
@@ -106,6 +111,7 @@ struct TcCfg {
                   "TMEM columns");
     static_assert(CMID % 16 == 0 && COUT % 16 == 0 && COUT <= CMID, "channel shapes");
     static_assert(!UP || (R % 2 == 0), "up-sampling stages need an even tile height");
+    static_assert(!STACK || R * N3 <= 256, "row-stacked accumulators are cleared by one MMA");
     static_assert(BYTES_USED <= 227 * 1024, "shared memory");
 };
 
@@ -265,50 +271,79 @@ __device__ __forceinline__ void compute_gather(const TcJob& job, int y0, int x0,
 }
 
 // UP / UP_SKIP compute: bilinear x2 of the raw coarse rows (+ the skip
-// already copied into the input buffer) -> BF16 chunks of the input buffer
+// already copied into the input buffer) -> BF16 chunks of the input buffer.
+// Separable: a coarse row is interpolated horizontally once and kept while the
+// staged rows that need it are produced (two coarse rows live at a time).
+// Column sp, channel group cg, staged rows [sr0, sr1).
 template <int CIN, int R, bool SKIP>
-__device__ __forceinline__ void compute_up(const TcJob& job, int y0, int x0, uint32_t raw, uint32_t a0, int pt) {
+__device__ __forceinline__ void up_column(const TcJob& job, int y0, int x0, uint32_t raw, uint32_t a0, int sp, int cg,
+                                          int sr0, int sr1) {
     constexpr int CG = CIN / 8;
     constexpr uint32_t kPlane = (R + 2) * kSW * 16;
     const int H = job.H, W = job.W, Hl = H / 2, Wl = W / 2;
     const int cy0 = y0 / 2 - 1, cx0 = x0 / 2 - 1;
-    // each thread owns (pixel column, channel group) items and walks the staged rows
-    for (int ci = pt; ci < 130 * CG; ci += kNP) {
-        const int cg = ci % CG, sp = ci / CG;
-        const int gx = x0 - 1 + sp;
-        const bool okx = gx >= 0 && gx < W;
-        const BilinTap tx = bilin_tap(okx ? gx : 0, Wl);
-        const uint32_t c0 = raw + 16 * ((tx.i0 - cx0) * CG + cg);  // coarse column i0, row cy0
-        const uint32_t c1 = raw + 16 * ((tx.i1 - cx0) * CG + cg);
-        const uint32_t dst = a0 + cg * kPlane + 16 * sp;
-#pragma unroll 2
-        for (int sr = 0; sr < R + 2; ++sr) {
-            const int gy = y0 - 1 + sr;
-            uint4 val = make_uint4(0, 0, 0, 0);
-            if (okx && gy >= 0 && gy < H) {
-                const BilinTap ty = bilin_tap(gy, Hl);
-                const uint32_t r0 = 16 * ((ty.i0 - cy0) * kNCC * CG), r1 = 16 * ((ty.i1 - cy0) * kNCC * CG);
-                float p00[8], p01[8], p10[8], p11[8], o[8];
-                chunk_to_f32(ld_shared_v4(c0 + r0), p00);
-                chunk_to_f32(ld_shared_v4(c1 + r0), p01);
-                chunk_to_f32(ld_shared_v4(c0 + r1), p10);
-                chunk_to_f32(ld_shared_v4(c1 + r1), p11);
+    const int gx = x0 - 1 + sp;
+    const bool okx = gx >= 0 && gx < W;
+    const BilinTap tx = bilin_tap(okx ? gx : 0, Wl);
+    const uint32_t c0 = raw + 16 * ((tx.i0 - cx0) * CG + cg);  // coarse column i0, row cy0
+    const uint32_t c1 = raw + 16 * ((tx.i1 - cx0) * CG + cg);
+    const uint32_t dst = a0 + cg * kPlane + 16 * sp;
+    // horizontal interpolation of coarse row ci
+    auto hrow = [&](int ci, float (&h)[8]) {
+        const uint32_t ro = 16 * ((ci - cy0) * kNCC * CG);
+        float p0[8], p1[8];
+        chunk_to_f32(ld_shared_v4(c0 + ro), p0);
+        chunk_to_f32(ld_shared_v4(c1 + ro), p1);
 #pragma unroll
-                for (int c = 0; c < 8; ++c) {
-                    const float q0 = p00[c] * tx.w0 + p01[c] * tx.w1;
-                    const float q1 = p10[c] * tx.w0 + p11[c] * tx.w1;
-                    o[c] = q0 * ty.w0 + q1 * ty.w1;
-                }
-                if constexpr (SKIP) {
-                    float sk[8];
-                    chunk_to_f32(ld_shared_v4(dst + 16 * (sr * kSW)), sk);
+        for (int c = 0; c < 8; ++c) h[c] = p0[c] * tx.w0 + p1[c] * tx.w1;
+    };
+    int ia = -4, ib = -4;  // coarse rows held in ha, hb
+    float ha[8], hb[8];
+    for (int sr = sr0; sr < sr1; ++sr) {
+        const int gy = y0 - 1 + sr;
+        uint4 val = make_uint4(0, 0, 0, 0);
+        if (okx && gy >= 0 && gy < H) {
+            const BilinTap ty = bilin_tap(gy, Hl);
+            if (ty.i0 != ia) {
+                if (ty.i0 == ib) {
 #pragma unroll
-                    for (int c = 0; c < 8; ++c) o[c] += sk[c];
+                    for (int c = 0; c < 8; ++c) ha[c] = hb[c];
+                } else {
+                    hrow(ty.i0, ha);
                 }
-                val = f32_to_chunk(o);
+                ia = ty.i0;
+                ib = ia;
             }
-            st_shared_v4(dst + 16 * (sr * kSW), val);
+            if (ty.i1 != ia && ty.i1 != ib) {
+                hrow(ty.i1, hb);
+                ib = ty.i1;
+            }
+            const bool same = ty.i1 == ia;
+            float o[8];
+#pragma unroll
+            for (int c = 0; c < 8; ++c) o[c] = ha[c] * ty.w0 + (same ? ha[c] : hb[c]) * ty.w1;
+            if constexpr (SKIP) {
+                float sk[8];
+                chunk_to_f32(ld_shared_v4(dst + 16 * (sr * kSW)), sk);
+#pragma unroll
+                for (int c = 0; c < 8; ++c) o[c] += sk[c];
+            }
+            val = f32_to_chunk(o);
         }
+        st_shared_v4(dst + 16 * (sr * kSW), val);
+    }
+}
+
+// The 128 interior columns x channel groups walk all staged rows (one item per
+// producer thread per pass); the two halo columns are split into single rows.
+template <int CIN, int R, bool SKIP>
+__device__ __forceinline__ void compute_up(const TcJob& job, int y0, int x0, uint32_t raw, uint32_t a0, int pt) {
+    constexpr int CG = CIN / 8;
+    constexpr int MAIN = kTileM * CG, HALO = 2 * CG * (R + 2);
+    for (int i = pt; i < MAIN; i += kNP) up_column<CIN, R, SKIP>(job, y0, x0, raw, a0, 1 + i / CG, i % CG, 0, R + 2);
+    for (int i = pt; i < HALO; i += kNP) {
+        const int sr = i % (R + 2), q = i / (R + 2);
+        up_column<CIN, R, SKIP>(job, y0, x0, raw, a0, (q / CG) ? 129 : 0, q % CG, sr, sr + 1);
     }
 }
 
@@ -343,6 +378,7 @@ __global__ void __launch_bounds__(kNT, 1) level_tc_kernel(const __grid_constant_
     for (int i = tid; i < COUT; i += kNT) bias1_s[i] = __ldg(a.bias1 + i);
     if (EPI == TEPI_HEAD)
         for (int i = tid; i <= COUT; i += kNT) head_s[i] = __ldg(a.head + i);
+    for (int i = tid; i < C::ZERO_BYTES / 16; i += kNT) st_shared_v4(sbase + C::OFF_ZERO + 16 * i, make_uint4(0, 0, 0, 0));
     if (tid == 0) {
         for (int k = 0; k < 2; ++k) {
             mbar_init(full + k, kNP);
@@ -455,6 +491,37 @@ __global__ void __launch_bounds__(kNT, 1) level_tc_kernel(const __grid_constant_
                 fence_after_sync();
                 const uint32_t A0 = sA0 + b * (C::A0_CHUNKS * 16);
                 const uint32_t D = tbase + b * C::TMEM_BUF;
+                if constexpr (C::STACK) {
+                    // clear the R x N3 accumulator columns (zero A operand), then
+                    // one MMA per (staged row j, K step) of width (#ky) x N3:
+                    // output row r accumulates at column (R - 1 - r) N3, kernel
+                    // row ky of input row j at (R - 1 - j + ky) N3
+                    mma_bf16(D, smem_desc(sbase + C::OFF_ZERO, 16, 128), smem_desc(sB3, 16, 128),
+                             idesc_bf16(128, R * C::N3), 0);
+                    constexpr uint32_t kBL = 3 * C::N3 * 16;  // B: next K chunk
+                    const uint64_t bdesc = smem_desc(sB3, kBL, 128);
+#pragma unroll
+                    for (int j = 0; j < R + 2; ++j) {
+                        const int ka = j - (R - 1) > 0 ? j - (R - 1) : 0, kb = j < 2 ? j : 2;
+                        const uint32_t id = idesc_bf16(128, (kb - ka + 1) * C::N3);
+                        const uint32_t d = D + (R - 1 - j + ka) * C::N3;
+                        if constexpr (C::SPLIT) {
+                            // K = staged pixels m + 2p, m + 2p + 1 (4 features hi | lo each)
+                            const uint64_t adesc = smem_desc(A0 + 16 * (j * kSW), 16, 128);
+#pragma unroll
+                            for (int p2 = 0; p2 < 2; ++p2)
+                                mma_bf16(d, adesc + 2 * p2, bdesc + ((2 * p2 * 3 + ka) * C::N3), id, 1);
+                        } else {
+                            const uint64_t adesc = smem_desc(A0 + 16 * (j * kSW), kPlane, 128);
+#pragma unroll
+                            for (int kx = 0; kx < 3; ++kx)
+#pragma unroll
+                                for (int kk = 0; kk < CIN / 16; ++kk)
+                                    mma_bf16(d, adesc + (2 * kk * kPlane / 16 + kx),
+                                             bdesc + (((kx * C::CG_IN + 2 * kk) * 3 + ka) * C::N3), id, 1);
+                        }
+                    }
+                } else {
                 // 3x3: one MMA of width 2 CMID per K step (hi and lo weights stacked)
                 for (int r = 0; r < R; ++r) {
                     const uint32_t d = D + r * C::N3;
@@ -479,6 +546,7 @@ __global__ void __launch_bounds__(kNT, 1) level_tc_kernel(const __grid_constant_
                             }
                         }
                     }
+                }
                 }
                 mma_commit(mma3 + b);
                 // 1x1 once the epilogue has written its operand: (A_hi + A_lo) [B_hi; B_lo]
@@ -529,8 +597,9 @@ __global__ void __launch_bounds__(kNT, 1) level_tc_kernel(const __grid_constant_
 #pragma unroll
                 for (int c0 = 0; c0 < CMID; c0 += 16) {
                     float val[16], lo[16];
-                    tmem_ld16(Dl + r * C::N3 + c0, val);         // x W_hi
-                    tmem_ld16(Dl + r * C::N3 + CMID + c0, lo);   // x W_lo
+                    const uint32_t col = (C::STACK ? R - 1 - r : r) * C::N3;
+                    tmem_ld16(Dl + col + c0, val);         // x W_hi
+                    tmem_ld16(Dl + col + CMID + c0, lo);   // x W_lo
                     tmem_ld_wait();
 #pragma unroll
                     for (int j = 0; j < 16; ++j) {

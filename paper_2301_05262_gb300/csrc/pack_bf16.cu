@@ -16,6 +16,11 @@ namespace nsm {
 //                     [c0..c3 | c0..c3] (the same weight for the hi and lo
 //                     parts of each feature), zero for t = 9
 //   1x1:              chunk (g, n)      = W[n][8g .. 8g+7]
+// Row-stacked 3x3 forms (the three kernel rows ky stacked along the output
+// rows as well, so one MMA over an input row feeds three output rows):
+//   3x3, C_in >= 16:  chunk (kx, g, ky, n) = W[n][8g .. 8g+7][ky][kx]
+//   3x3 first level:  chunk (p, h, ky, n)  = column kx = 2p + h (zero for
+//                     kx = 3), channels [c0..c3 | c0..c3] as above
 using PackDesc = PackDescHost;
 
 __global__ void pack_bf16_kernel(const float* __restrict__ params, uint16_t* __restrict__ img,
@@ -38,6 +43,20 @@ __global__ void pack_bf16_kernel(const float* __restrict__ params, uint16_t* __r
                 const int kh = static_cast<int>(chunk / pd.cout);
                 const int tap = kh;  // = 2k + h
                 if (tap < 9) v = params[pd.w_off + (static_cast<size_t>(n) * 4 + (e % 4)) * 9 + tap];
+            } else if (pd.kind == 3) {  // stacked 3x3: chunk = ((kx * (cin/8) + g) * 3 + ky) * cout + n
+                const int n = static_cast<int>(chunk % pd.cout);
+                const size_t t2 = chunk / pd.cout;
+                const int ky = static_cast<int>(t2 % 3);
+                const size_t t3 = t2 / 3;
+                const int g = static_cast<int>(t3 % (pd.cin / 8));
+                const int kx = static_cast<int>(t3 / (pd.cin / 8));
+                v = params[pd.w_off + (static_cast<size_t>(n) * pd.cin + 8 * g + e) * 9 + ky * 3 + kx];
+            } else if (pd.kind == 4) {  // stacked first level: chunk = ((p * 2 + h) * 3 + ky) * cout + n
+                const int n = static_cast<int>(chunk % pd.cout);
+                const size_t t2 = chunk / pd.cout;
+                const int ky = static_cast<int>(t2 % 3);
+                const int kx = static_cast<int>(t2 / 3);  // = 2p + h
+                if (kx < 3) v = params[pd.w_off + (static_cast<size_t>(n) * 4 + (e % 4)) * 9 + ky * 3 + kx];
             } else {  // 1x1: chunk = g * cout + n
                 const int n = static_cast<int>(chunk % pd.cout);
                 const int g = static_cast<int>(chunk / pd.cout);
@@ -62,16 +81,21 @@ BF16Images bf16_images() {
     auto add = [&](int layer, int kind) {
         const int ci = kLayers[layer].cin, co = kLayers[layer].cout;
         size_t count;
-        if (kind == 0) count = static_cast<size_t>(9) * ci * co;
+        if (kind == 0 || kind == 3) count = static_cast<size_t>(9) * ci * co;
         else if (kind == 1) count = static_cast<size_t>(10) * co * 8;
+        else if (kind == 4) count = static_cast<size_t>(12) * co * 8;
         else count = static_cast<size_t>(ci) * co;
         im.desc[im.n] = {kind, ci, co, off.w[layer], pos, count};
         im.img_off[layer] = pos;
         pos += 2 * count;  // hi and lo parts (counts are multiples of 8)
         ++im.n;
     };
-    add(ENC0_3, 1); add(ENC0_1, 2); add(ENC1_3, 0); add(ENC1_1, 2); add(BOTT_3, 0); add(BOTT_1, 2);
-    add(DEC1_3, 0); add(DEC1_1, 2); add(DEC0_3, 0); add(DEC0_1, 2);
+    // a 3x3 layer is row-stacked when its three stacked kernel rows (3 x 2 c_out
+    // MMA rows) fit one MMA of width <= 256
+    auto k3 = [&](int layer) { return 3 * 2 * kLayers[layer].cout <= 256 ? 3 : 0; };
+    add(ENC0_3, 3 * 2 * kLayers[ENC0_3].cout <= 256 ? 4 : 1); add(ENC0_1, 2);
+    add(ENC1_3, k3(ENC1_3)); add(ENC1_1, 2); add(BOTT_3, k3(BOTT_3)); add(BOTT_1, 2);
+    add(DEC1_3, k3(DEC1_3)); add(DEC1_1, 2); add(DEC0_3, k3(DEC0_3)); add(DEC0_1, 2);
     im.total = pos;
     return im;
 }
