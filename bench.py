@@ -238,7 +238,9 @@ def run_ours(args):
         ws_t = torch.empty((nsm.nsm_infer_batched_workspace_bytes(views),), dtype=torch.uint8, device=device)
         nsm.nsm_autotune(ctx, views, weights, ws_t, reps=5)
         rows, ctas, ms = nsm.nsm_autotune_report(ctx)
-        plan = {"tile_rows": rows, "ctas_per_sm": ctas, "tuned_stage_ms": [round(x, 5) for x in ms]}
+        ew, pw = nsm.nsm_autotune_report_warps(ctx)
+        plan = {"tile_rows": rows, "ctas_per_sm": ctas, "epilogue_warps": ew, "producer_warps": pw,
+                "tuned_stage_ms": [round(x, 5) for x in ms]}
         del ws_t, vtmp
     for pname in precisions:
         prec = nsm.PRECISIONS[pname]

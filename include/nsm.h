@@ -158,7 +158,8 @@ nsm_status nsm_features(const nsm_frame* frame, float* feat_out, int32_t* texel_
 /* ---------------------------------------------------------------- inference */
 
 /* Bytes of device workspace nsm_infer needs for an H x W view (0 if H or W
- * is 0).  The workspace holds the intermediate activations of the levels. */
+ * is 0).  The workspace holds the intermediate activations of the levels,
+ * 4 bytes per channel (FP32, or a BF16 hi + lo pair in the BF16 form). */
 size_t nsm_infer_workspace_bytes(int H, int W, nsm_precision precision);
 
 /* Per-pixel visibility in [0, 1] for one view: the gather fused into the
@@ -217,6 +218,9 @@ nsm_status nsm_autotune(nsm_ctx* ctx, int n, const nsm_view* views, const nsm_we
 /* The plan per stage (5 entries each, nullable): tile rows, CTAs per SM
  * (0 = as many as fit), and the tuned time in ms (0 before tuning). */
 nsm_status nsm_autotune_report(nsm_ctx* ctx, int* rows_out, int* ctas_out, float* ms_out);
+/* The warp roles of the plan per stage (5 entries each, nullable): epilogue
+ * warps (4 or 8: TMEM readers) and producer warps (input staging). */
+nsm_status nsm_autotune_report_warps(nsm_ctx* ctx, int* epilogue_warps_out, int* producer_warps_out);
 
 /* ---------------------------------------------------------------- backward / training */
 

@@ -404,6 +404,7 @@ def _batch_sigs():
         "nsm_ctx_graph_replays": ([P], I),
         "nsm_autotune": ([P, I, VP, P, P, Z, I, P], I),
         "nsm_autotune_report": ([P, P, P, P], I),
+        "nsm_autotune_report_warps": ([P, P, P], I),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -451,3 +452,11 @@ def nsm_autotune_report(ctx: Context):
     ms = (ctypes.c_float * 5)()
     _check(_batch_sigs().nsm_autotune_report(ctx.h, rows, ctas, ms), "nsm_autotune_report")
     return list(rows), list(ctas), list(ms)
+
+
+def nsm_autotune_report_warps(ctx: Context):
+    """(epilogue warps, producer warps) of every stage of the context's plan."""
+    ew = (ctypes.c_int * 5)()
+    pw = (ctypes.c_int * 5)()
+    _check(_batch_sigs().nsm_autotune_report_warps(ctx.h, ew, pw), "nsm_autotune_report_warps")
+    return list(ew), list(pw)

@@ -30,7 +30,7 @@ static void carve_views(int n, const nsm_view* views, void* ws, std::vector<Acti
     size_t off = 0;
     for (int i = 0; i < n; ++i) {
         const nsm_frame& f = views[i].frame;
-        off += activations_bytes(f.H, f.W, 2, &act[i], static_cast<char*>(ws) + off);
+        off += activations_bytes(f.H, f.W, 4, &act[i], static_cast<char*>(ws) + off);
         gp[i] = make_gather(&f);
         vis[i] = views[i].vis_out;
     }
@@ -69,7 +69,7 @@ size_t nsm_infer_batched_workspace_bytes(int n, const nsm_view* views) {
     size_t t = 0;
     for (int i = 0; i < n; ++i) {
         if (views[i].frame.H <= 0 || views[i].frame.W <= 0) return 0;
-        t += activations_bytes(views[i].frame.H, views[i].frame.W, 2, nullptr, nullptr);
+        t += activations_bytes(views[i].frame.H, views[i].frame.W, 4, nullptr, nullptr);
     }
     return t;
 }
@@ -234,6 +234,17 @@ nsm_status nsm_autotune_report(nsm_ctx* c, int* rows_out, int* ctas_out, float* 
         if (rows_out) rows_out[k] = tc_stage_rows(k, c->tc_variant[k]);
         if (ctas_out) ctas_out[k] = c->tc_ctas[k];
         if (ms_out) ms_out[k] = c->tc_ms[k];
+    }
+    return NSM_OK;
+}
+
+nsm_status nsm_autotune_report_warps(nsm_ctx* c, int* epilogue_warps_out, int* producer_warps_out) {
+    if (!c) return fail(NSM_ERR_INVALID_ARG, "ctx is NULL");
+    for (int k = 0; k < kTcStages; ++k) {
+        int pw = 0;
+        const int ew = tc_stage_warps(k, c->tc_variant[k], &pw);
+        if (epilogue_warps_out) epilogue_warps_out[k] = ew;
+        if (producer_warps_out) producer_warps_out[k] = pw;
     }
     return NSM_OK;
 }

@@ -12,46 +12,57 @@
 // of any sizes (one view for nsm_infer, many for nsm_infer_batched): the
 // CTAs walk one global list of tiles, each tile belonging to one view.
 //
+// Compensated BF16: every value the tensor cores read is a pair of BF16
+// numbers, v = hi + lo with hi = bf16(v), lo = bf16(v - hi) (about 16
+// significant bits): the weights (hi and lo stacked along N, so one MMA
+// yields x W_hi and x W_lo side by side in TMEM, summed in the epilogue), the
+// features, the 3x3 -> 1x1 intermediate and every activation stored between
+// stages ([pixel][part][C] in global memory, 4 bytes per channel like FP32).
+// The products are BF16 x BF16 with FP32 accumulation; what rounding remains
+// is ~2^-16 relative per stored value instead of BF16's 2^-9, which a deep
+// chain of unnormalised convolutions otherwise amplifies well past 1e-2 in
+// the visibility.
+//
 // Tile: R rows x 128 pixels of the level; MMA row block = one 128-pixel row
 // segment.  The input tile with its 1-pixel halo is staged in shared memory
-// as 16-byte chunks of 8 channels, [channel group][staged row][staged pixel],
-// which is the tensor core's no-swizzle K-major operand layout: the A operand
-// of tap (ky, kx) and channel pair (2g, 2g+1) is the same buffer started
-// (ky, kx) chunks further on, so the im2col matrix is never built.  The 3x3
-// result goes TMEM -> registers (bias, ReLU) -> shared memory as BF16 hi + lo
-// parts, the A operand of the 1x1 MMA (written into the same TMEM columns).
-// Weights are BF16 hi + lo parts stacked along N: one MMA of width 2 C per K
-// step yields x W_hi and x W_lo side by side in TMEM, summed in the
-// epilogue; the 1x1 runs (A_hi + A_lo) [W_hi; W_lo] as two MMAs.  Weight and
-// intermediate rounding so leave no trace beyond ~2^-16 and only the level
-// outputs are BF16.  (A 128 x N x 16 MMA costs about the same issue time for
-// any N <= 64 on this part, so widening N is nearly free, unlike extra MMAs.)
+// as 16-byte chunks of 8 channels, [plane][staged row][staged pixel], which
+// is the tensor core's no-swizzle K-major operand layout: the A operand of
+// tap (ky, kx) and a channel pair is the same buffer started (ky, kx) chunks
+// further on, so the im2col matrix is never built.  A plane is one channel
+// group of one part (hi or lo); both parts are multiplied by the same weight
+// chunk.  Large inputs are staged in K slices (KS > 1: an input buffer holds
+// the hi and lo planes of 8 C_in / KS channels), each slice one pipeline
+// step.  Row-stacked 3x3 (when 3 x 2 C_mid <= 256): the kernel rows ky are
+// stacked along N too, so one MMA over staged input row j accumulates into
+// output rows j, j-1, j-2 (accumulators in descending column order, cleared
+// by one MMA with a zero A operand).  The 3x3 result goes TMEM -> registers
+// (bias, ReLU) -> shared memory as hi + lo parts, the A operand of the 1x1
+// MMAs (written into the same TMEM columns).
 //
-// First level: the four FP32 features are split into BF16 hi + lo parts
-// (f = hi + lo to ~2^-16 relative), 8 "channels" per pixel; K steps pair two
-// taps (two 16-byte chunks), so the 3x3 4 -> 16 convolution is five K = 16
-// steps with a zero-weight pad.  This keeps the depth-test features
-// (z / z_f near 1, z - z_f near 0) at near-FP32 resolution.
+// First level: the four FP32 features are split into hi + lo parts, 8
+// "channels" per pixel; K steps pair two taps (two 16-byte chunks).
 //
-// Warp-specialised pipeline, 13 warps per CTA:
-//   warps 4-11 producers: PLAIN copies tile i straight into input buffer i % 2
-//              with cp.async; GATHER / UP* prefetch tile i + 1's raw inputs
-//              (G-buffer, or the coarser level) into raw buffer (i + 1) % 2
-//              with cp.async while they compute tile i from raw buffer i % 2
-//              (texel lookups, features / bilinear x2 (+ skip)) into input
-//              buffer i % 2
-//   warp 12    MMA issuer (one thread) and TMEM owner: the 3x3 of tile i into
-//              accumulator buffer i % 2, then its 1x1 into the same columns
-//   warps 0-3  epilogue: TMEM lane quarter = warp; 3x3 result -> 1x1 operand,
-//              1x1 result -> outputs
+// Warp-specialised pipeline (NEW epilogue warps, NPW producer warps, one MMA
+// warp; the autotuner picks the split):
+//   producers  PLAIN copies step i (a tile's K slice) straight into input
+//              buffer i % 2 with cp.async; GATHER / UP* prefetch tile t + 1's
+//              raw inputs (G-buffer, or the coarser level) into raw buffer
+//              (t + 1) % 2 with cp.async while they compute tile t from raw
+//              buffer t % 2 (texel lookups, features / bilinear x2 + skip)
+//   MMA warp   one thread issues the 3x3 of tile t, slice by slice, into
+//              accumulator buffer t % 2, then its 1x1 into the same columns;
+//              it also owns the TMEM allocation
+//   epilogue   TMEM lane quarter = warp % 4, tile rows r = warp / 4 (mod
+//              NEW / 4); 3x3 result -> 1x1 operand, 1x1 result -> outputs
 // mbarriers (every wait is bounded and gives up when another role aborted):
-//   gfull[b]  producers' cp.async -> producers: raw buffer b landed (256 arrivals)
-//   rfree[b]  producers -> producers: raw buffer b consumed (256 arrivals)
-//   full[b]   producers -> MMA: input buffer b staged (256 arrivals)
-//   mma3[b]   MMA -> epilogue: 3x3 of buffer b done; -> producers: buffer b free
-//   a1full    epilogue -> MMA: 1x1 operand written (128 arrivals)
+//   gfull[b]  producers' cp.async -> producers: raw buffer b landed
+//   rfree[b]  producers -> producers: raw buffer b consumed
+//   full[b]   producers -> MMA: input buffer b staged
+//   mma3[b]   MMA -> producers: input buffer b consumed
+//   accf[t]   MMA -> epilogue: 3x3 accumulators of buffer t complete
+//   a1full    epilogue -> MMA: 1x1 operand written
 //   mma1      MMA -> epilogue: 1x1 done (and its operand free)
-//   tfree[b]  epilogue -> MMA: accumulator buffer b read out (128 arrivals)
+//   tfree[t]  epilogue -> MMA: accumulator buffer t read out
 #include "nsm_internal.h"
 #include "tc_common.cuh"
 #include "tc_stage.h"
@@ -60,26 +71,30 @@ namespace nsm {
 
 using namespace tc;
 
-constexpr int kNP = 256;         // producer threads (warps 4-11)
-constexpr int kNT = 128 + kNP + 32;  // threads per CTA: 4 epilogue warps, 8 producer warps, 1 MMA warp
-constexpr int kMmaWarp = (128 + kNP) / 32;
+// Warp roles of a CTA (NEW epilogue warps, NPW producer warps, one MMA warp):
+// warps [0, NEW) epilogue (warp w reads TMEM lane quarter w % 4 and the tile
+// rows r = w / 4 (mod NEW / 4)), [NEW, NEW + NPW) producers, NEW + NPW MMA.
 constexpr int kTileM = 128;      // pixels per MMA row block
 constexpr int kSW = 136;         // staged pixels per row (128 + halo + pad)
 constexpr int kNCC = 66;         // coarse-level columns behind one tile
 constexpr uint64_t kWaitNs = 2000000000ull;  // 2 s bound on every mbarrier wait
 
-template <int CIN, int CMID, int COUT, int R, int PRO>
+template <int CIN, int CMID, int COUT, int R, int PRO, int KS>
 struct TcCfg {
     static constexpr bool SPLIT = (PRO == TPRO_GATHER);
     static constexpr bool UP = (PRO == TPRO_UP || PRO == TPRO_UP_SKIP);
-    static constexpr int CG_IN = SPLIT ? 1 : CIN / 8;
+    static constexpr int CG_IN = SPLIT ? 1 : CIN / 8;           // channel groups of each part of the input
+    // K slices: an input buffer holds the hi and lo planes of CGS channel
+    // groups, [part][group of the slice] (the first level: one plane)
+    static constexpr int CGS = SPLIT ? 1 : CG_IN / KS;
+    static constexpr int PLN = SPLIT ? 1 : 2 * CGS;
     static constexpr int KSTEPS3 = SPLIT ? 5 : 9 * (CIN / 16);
-    static constexpr int A0_CHUNKS = CG_IN * (R + 2) * kSW;     // one input buffer
+    static constexpr int A0_CHUNKS = PLN * (R + 2) * kSW;        // one input buffer
     // 3x3 -> 1x1 intermediate as BF16 hi + lo parts: [row][part][channel group][pixel]
     static constexpr int A1_CHUNKS = R * 2 * (CMID / 8) * kTileM;
-    // raw prefetch buffer (two): the staged G-buffer (pos, nrm) or the coarse rows
+    // raw prefetch buffer (two): the staged G-buffer (pos, nrm) or the coarse rows (hi + lo)
     static constexpr int NCR = R / 2 + 2;
-    static constexpr int RAW_BYTES = SPLIT ? (R + 2) * 130 * 32 : (UP ? NCR * kNCC * CIN * 2 : 0);
+    static constexpr int RAW_BYTES = SPLIT ? (R + 2) * 130 * 32 : (UP ? NCR * kNCC * 2 * CG_IN * 16 : 0);
     // weights as BF16 hi + lo parts stacked along the output rows (2 C rows per K block)
     static constexpr int N3 = 2 * CMID, N1 = 2 * COUT;             // MMA widths
     // row-stacked 3x3: the kernel rows ky = 0, 1, 2 stacked along N as well, so
@@ -112,6 +127,7 @@ struct TcCfg {
     static_assert(CMID % 16 == 0 && COUT % 16 == 0 && COUT <= CMID, "channel shapes");
     static_assert(!UP || (R % 2 == 0), "up-sampling stages need an even tile height");
     static_assert(!STACK || R * N3 <= 256, "row-stacked accumulators are cleared by one MMA");
+    static_assert(SPLIT ? KS == 1 : (CG_IN % KS == 0 && CGS % 2 == 0), "a K slice holds whole 16-channel K steps");
     static_assert(BYTES_USED <= 227 * 1024, "shared memory");
 };
 
@@ -168,35 +184,39 @@ __device__ __forceinline__ uint4 f32_to_chunk(const float* f) {
 }
 
 // ------------------------------------------------------------------ producer pieces
-// (pt = producer thread 0..kNP-1; staged rows y0-1 .. y0+R, pixels x0-1 .. x0+128)
+// (pt = producer thread 0..NP-1 of NP; staged rows y0-1 .. y0+R, pixels x0-1 .. x0+128)
+// Activations in global memory: [pixel][part][C] BF16, part 0 = hi, 1 = lo, so
+// chunk part * CG + g of a pixel holds channels 8g .. 8g+7 of that part.
 
-// PLAIN (and the skip part of UP_SKIP): NHWC BF16 tile straight into the input
-// buffer, zeros outside the image
-template <int CIN, int R>
-__device__ __forceinline__ void copy_tile(const uint16_t* src, int H, int W, int y0, int x0, uint32_t a0, int pt) {
-    constexpr int CG = CIN / 8;
+// PLAIN: K slice s of an NHWC tile straight into the input buffer, zeros
+// outside the image (planes [part][group of the slice])
+template <int NP, int CIN, int R, int KS>
+__device__ __forceinline__ void copy_slice(const uint16_t* src, int H, int W, int y0, int x0, uint32_t a0, int s,
+                                           int pt) {
+    constexpr int CG = CIN / 8, CGS = CG / KS, PLN = 2 * CGS;
     constexpr uint32_t kPlane = (R + 2) * kSW * 16;
-    // each thread owns (pixel column, channel group) items and walks the staged rows
-    for (int ci = pt; ci < 130 * CG; ci += kNP) {
-        const int cg = ci % CG, sp = ci / CG;
+    // each thread owns (pixel column, plane) items and walks the staged rows
+    for (int ci = pt; ci < 130 * PLN; ci += NP) {
+        const int pl = ci % PLN, sp = ci / PLN;
+        const int chunk = (pl / CGS) * CG + s * CGS + pl % CGS;
         const int gx = x0 - 1 + sp;
         const bool okx = gx >= 0 && gx < W;
-        const uint32_t dst = a0 + cg * kPlane + 16 * sp;
+        const uint32_t dst = a0 + pl * kPlane + 16 * sp;
 #pragma unroll
         for (int sr = 0; sr < R + 2; ++sr) {
             const int gy = y0 - 1 + sr;
             const bool ok = okx && gy >= 0 && gy < H;
-            const uint16_t* s = ok ? src + (static_cast<size_t>(gy) * W + gx) * CIN + cg * 8 : src;
-            cp_async16(dst + 16 * (sr * kSW), s, ok ? 16u : 0u);
+            const uint16_t* p = ok ? src + ((static_cast<size_t>(gy) * W + gx) * 2 * CG + chunk) * 8 : src;
+            cp_async16(dst + 16 * (sr * kSW), p, ok ? 16u : 0u);
         }
     }
 }
 
 // GATHER raw: pos4 / nrm4 of the staged pixels in bounds, 32 bytes per pixel
-template <int R>
+template <int NP, int R>
 __device__ __forceinline__ void prefetch_gbuffer(const TcJob& job, int y0, int x0, uint32_t raw, int pt) {
     const int H = job.H, W = job.W;
-    for (int idx = pt; idx < (R + 2) * 130 * 2; idx += kNP) {
+    for (int idx = pt; idx < (R + 2) * 130 * 2; idx += NP) {
         const int part = idx & 1, q = idx >> 1;
         const int sr = q / 130, sp = q % 130;
         const int gy = y0 - 1 + sr, gx = x0 - 1 + sp;
@@ -205,28 +225,29 @@ __device__ __forceinline__ void prefetch_gbuffer(const TcJob& job, int y0, int x
     }
 }
 
-// UP raw: the coarse rows y0/2-1 .. y0/2+R/2 and columns x0/2-1 .. x0/2+64 in bounds
-template <int CIN, int R>
+// UP raw: the coarse rows y0/2-1 .. y0/2+R/2 and columns x0/2-1 .. x0/2+64 in
+// bounds, FP32, CIN / 4 chunks of each coarse pixel
+template <int NP, int CIN, int R>
 __device__ __forceinline__ void prefetch_coarse(const TcJob& job, int y0, int x0, uint32_t raw, int pt) {
-    constexpr int CG = CIN / 8, NCR = R / 2 + 2;
+    constexpr int C2 = CIN / 4, NCR = R / 2 + 2;
     const int Hl = job.H / 2, Wl = job.W / 2;
     const int cy0 = y0 / 2 - 1, cx0 = x0 / 2 - 1;
-    for (int idx = pt; idx < NCR * kNCC * CG; idx += kNP) {
-        const int cg = idx % CG, q = idx / CG;
+    for (int idx = pt; idx < NCR * kNCC * C2; idx += NP) {
+        const int ch = idx % C2, q = idx / C2;
         const int gy = cy0 + q / kNCC, gx = cx0 + q % kNCC;
         if (gy >= 0 && gy < Hl && gx >= 0 && gx < Wl)
-            cp_async16(raw + 16 * idx, job.in + (static_cast<size_t>(gy) * Wl + gx) * CIN + cg * 8, 16);
+            cp_async16(raw + 16 * idx, job.in_f + (static_cast<size_t>(gy) * Wl + gx) * CIN + 4 * ch, 16);
     }
 }
 
 // GATHER compute: features of the staged pixels from the raw G-buffer, the
 // shadow-map texel fetched per pixel (all of a thread's fetches in flight
 // together), BF16 hi + lo chunks into the input buffer
-template <int R>
+template <int NP, int R>
 __device__ __forceinline__ void compute_gather(const TcJob& job, int y0, int x0, uint32_t raw, uint32_t a0, int pt) {
     constexpr int NSP = 131;  // staged pixel 130 is the zero pad read by the dummy tap
     constexpr int ITEMS = (R + 2) * NSP;
-    constexpr int NPT = (ITEMS + kNP - 1) / kNP;
+    constexpr int NPT = (ITEMS + NP - 1) / NP;
     const GatherParams g = job.g;  // one copy per tile: the view index is only known at run time
     const int H = job.H, W = job.W;
     float4 P[NPT], Nv[NPT];
@@ -234,7 +255,7 @@ __device__ __forceinline__ void compute_gather(const TcJob& job, int y0, int x0,
     bool ok[NPT];
 #pragma unroll
     for (int k = 0; k < NPT; ++k) {
-        const int idx = pt + kNP * k;
+        const int idx = pt + NP * k;
         const int sr = idx / NSP, sp = idx % NSP;
         const int gy = y0 - 1 + sr, gx = x0 - 1 + sp;
         ok[k] = idx < ITEMS && sp < 130 && gy >= 0 && gy < H && gx >= 0 && gx < W;
@@ -249,7 +270,7 @@ __device__ __forceinline__ void compute_gather(const TcJob& job, int y0, int x0,
     }
 #pragma unroll
     for (int k = 0; k < NPT; ++k) {
-        const int idx = pt + kNP * k;
+        const int idx = pt + NP * k;
         if (idx < ITEMS) {
             const int sr = idx / NSP, sp = idx % NSP;
             uint4 chunk = make_uint4(0, 0, 0, 0);
@@ -270,38 +291,77 @@ __device__ __forceinline__ void compute_gather(const TcJob& job, int y0, int x0,
     }
 }
 
-// UP / UP_SKIP compute: bilinear x2 of the raw coarse rows (+ the skip
-// already copied into the input buffer) -> BF16 chunks of the input buffer.
-// Separable: a coarse row is interpolated horizontally once and kept while the
-// staged rows that need it are produced (two coarse rows live at a time).
-// Column sp, channel group cg, staged rows [sr0, sr1).
-template <int CIN, int R, bool SKIP>
-__device__ __forceinline__ void up_column(const TcJob& job, int y0, int x0, uint32_t raw, uint32_t a0, int sp, int cg,
-                                          int sr0, int sr1) {
-    constexpr int CG = CIN / 8;
+// BF16 hi + lo chunks of 8 FP32 values: hi = bf16(v), lo = bf16(v - hi)
+__device__ __forceinline__ void split_chunks(const float* f, uint4& hi, uint4& lo) {
+    float h[8], l[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        h[c] = __bfloat162float(__float2bfloat16_rn(f[c]));
+        l[c] = f[c] - h[c];
+    }
+    hi = f32_to_chunk(h);
+    lo = f32_to_chunk(l);
+}
+// FP32 value of a hi + lo chunk pair
+__device__ __forceinline__ void pair_to_f32(uint4 hi, uint4 lo, float (&f)[8]) {
+    float l[8];
+    chunk_to_f32(hi, f);
+    chunk_to_f32(lo, l);
+#pragma unroll
+    for (int c = 0; c < 8; ++c) f[c] += l[c];
+}
+
+// UP / UP_SKIP compute: bilinear x2 of the raw FP32 coarse rows (+ the FP32
+// skip, read from global memory) -> BF16 hi + lo planes of the input buffer.  Separable:
+// a coarse row is interpolated horizontally once and kept while the staged
+// rows that need it are produced (two coarse rows live at a time).
+// Column sp, channel group cgl of K slice s, staged rows [sr0, sr0 + NROWS).
+template <int CIN, int R, int KS, bool SKIP, int NROWS>
+__device__ __forceinline__ void up_column(const TcJob& job, int y0, int x0, uint32_t raw, uint32_t a0, int s, int sp,
+                                          int cgl, int sr0) {
+    constexpr int CG = CIN / 8, CGS = CG / KS, C4 = CIN / 4;
     constexpr uint32_t kPlane = (R + 2) * kSW * 16;
     const int H = job.H, W = job.W, Hl = H / 2, Wl = W / 2;
     const int cy0 = y0 / 2 - 1, cx0 = x0 / 2 - 1;
+    const int cg = s * CGS + cgl;
     const int gx = x0 - 1 + sp;
     const bool okx = gx >= 0 && gx < W;
     const BilinTap tx = bilin_tap(okx ? gx : 0, Wl);
-    const uint32_t c0 = raw + 16 * ((tx.i0 - cx0) * CG + cg);  // coarse column i0, row cy0
-    const uint32_t c1 = raw + 16 * ((tx.i1 - cx0) * CG + cg);
-    const uint32_t dst = a0 + cg * kPlane + 16 * sp;
+    const uint32_t c0 = raw + 16 * ((tx.i0 - cx0) * C4 + 2 * cg);  // coarse column i0, row cy0
+    const uint32_t c1 = raw + 16 * ((tx.i1 - cx0) * C4 + 2 * cg);
+    const uint32_t dst = a0 + cgl * kPlane + 16 * sp;          // hi plane; lo plane CGS planes on
+    // the skip chunks of all rows first (global loads in flight together)
+    float4 ska[NROWS], skb[NROWS];
+    if constexpr (SKIP) {
+#pragma unroll
+        for (int k = 0; k < NROWS; ++k) {
+            const int gy = y0 - 1 + sr0 + k;
+            ska[k] = skb[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (okx && gy >= 0 && gy < H) {
+                const float4* p = reinterpret_cast<const float4*>(job.skip + (static_cast<size_t>(gy) * W + gx) * CIN) +
+                                  2 * cg;
+                ska[k] = __ldg(p);
+                skb[k] = __ldg(p + 1);
+            }
+        }
+    }
     // horizontal interpolation of coarse row ci
     auto hrow = [&](int ci, float (&h)[8]) {
-        const uint32_t ro = 16 * ((ci - cy0) * kNCC * CG);
-        float p0[8], p1[8];
-        chunk_to_f32(ld_shared_v4(c0 + ro), p0);
-        chunk_to_f32(ld_shared_v4(c1 + ro), p1);
+        const uint32_t ro = 16 * ((ci - cy0) * kNCC * C4);
+        const float4 a0 = ld_shared_f4(c0 + ro), a1 = ld_shared_f4(c0 + ro + 16);
+        const float4 b0 = ld_shared_f4(c1 + ro), b1 = ld_shared_f4(c1 + ro + 16);
+        const float p0[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+        const float p1[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
 #pragma unroll
         for (int c = 0; c < 8; ++c) h[c] = p0[c] * tx.w0 + p1[c] * tx.w1;
     };
     int ia = -4, ib = -4;  // coarse rows held in ha, hb
     float ha[8], hb[8];
-    for (int sr = sr0; sr < sr1; ++sr) {
+#pragma unroll
+    for (int k = 0; k < NROWS; ++k) {
+        const int sr = sr0 + k;
         const int gy = y0 - 1 + sr;
-        uint4 val = make_uint4(0, 0, 0, 0);
+        uint4 vh = make_uint4(0, 0, 0, 0), vl = vh;
         if (okx && gy >= 0 && gy < H) {
             const BilinTap ty = bilin_tap(gy, Hl);
             if (ty.i0 != ia) {
@@ -323,33 +383,38 @@ __device__ __forceinline__ void up_column(const TcJob& job, int y0, int x0, uint
 #pragma unroll
             for (int c = 0; c < 8; ++c) o[c] = ha[c] * ty.w0 + (same ? ha[c] : hb[c]) * ty.w1;
             if constexpr (SKIP) {
-                float sk[8];
-                chunk_to_f32(ld_shared_v4(dst + 16 * (sr * kSW)), sk);
+                const float sk[8] = {ska[k].x, ska[k].y, ska[k].z, ska[k].w, skb[k].x, skb[k].y, skb[k].z, skb[k].w};
 #pragma unroll
                 for (int c = 0; c < 8; ++c) o[c] += sk[c];
             }
-            val = f32_to_chunk(o);
+            split_chunks(o, vh, vl);
         }
-        st_shared_v4(dst + 16 * (sr * kSW), val);
+        st_shared_v4(dst + 16 * (sr * kSW), vh);
+        st_shared_v4(dst + CGS * kPlane + 16 * (sr * kSW), vl);
     }
 }
 
-// The 128 interior columns x channel groups walk all staged rows (one item per
-// producer thread per pass); the two halo columns are split into single rows.
-template <int CIN, int R, bool SKIP>
-__device__ __forceinline__ void compute_up(const TcJob& job, int y0, int x0, uint32_t raw, uint32_t a0, int pt) {
-    constexpr int CG = CIN / 8;
-    constexpr int MAIN = kTileM * CG, HALO = 2 * CG * (R + 2);
-    for (int i = pt; i < MAIN; i += kNP) up_column<CIN, R, SKIP>(job, y0, x0, raw, a0, 1 + i / CG, i % CG, 0, R + 2);
-    for (int i = pt; i < HALO; i += kNP) {
+// K slice s: the 128 interior columns x channel groups walk all staged rows
+// (one item per producer thread per pass); the two halo columns are split
+// into single rows.
+template <int NP, int CIN, int R, int KS, bool SKIP>
+__device__ __forceinline__ void compute_up(const TcJob& job, int y0, int x0, uint32_t raw, uint32_t a0, int s,
+                                           int pt) {
+    constexpr int CGS = CIN / 8 / KS;
+    constexpr int MAIN = kTileM * CGS, HALO = 2 * CGS * (R + 2);
+    for (int i = pt; i < MAIN; i += NP)
+        up_column<CIN, R, KS, SKIP, R + 2>(job, y0, x0, raw, a0, s, 1 + i / CGS, i % CGS, 0);
+    for (int i = pt; i < HALO; i += NP) {
         const int sr = i % (R + 2), q = i / (R + 2);
-        up_column<CIN, R, SKIP>(job, y0, x0, raw, a0, (q / CG) ? 129 : 0, q % CG, sr, sr + 1);
+        up_column<CIN, R, KS, SKIP, 1>(job, y0, x0, raw, a0, s, (q / CGS) ? 129 : 0, q % CGS, sr);
     }
 }
 
-template <int CIN, int CMID, int COUT, int R, int PRO, int EPI>
-__global__ void __launch_bounds__(kNT, 1) level_tc_kernel(const __grid_constant__ TcBatch a) {
-    using C = TcCfg<CIN, CMID, COUT, R, PRO>;
+template <int CIN, int CMID, int COUT, int R, int PRO, int EPI, int NEW, int NPW, int KS>
+__global__ void __launch_bounds__(32 * (NEW + NPW + 1), 1) level_tc_kernel(const __grid_constant__ TcBatch a) {
+    using C = TcCfg<CIN, CMID, COUT, R, PRO, KS>;
+    constexpr int NP = 32 * NPW, NT = 32 * (NEW + NPW + 1), MW = NEW + NPW, NE = 32 * NEW;
+    static_assert(NEW == 4 || NEW == 8, "epilogue warps cover the four TMEM lane quarters");
     extern __shared__ __align__(1024) unsigned char smem[];
     const uint32_t sbase = smem_u32(smem);
     const uint32_t sA0 = sbase + C::OFF_A0, sA1 = sbase + C::OFF_A1, sRAW = sbase + C::OFF_RAW;
@@ -358,41 +423,43 @@ __global__ void __launch_bounds__(kNT, 1) level_tc_kernel(const __grid_constant_
     float* bias1_s = reinterpret_cast<float*>(smem + C::OFF_BIAS1);
     float* head_s = reinterpret_cast<float*>(smem + C::OFF_HEAD);
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem + C::OFF_BAR);
-    uint64_t* full = bar;          // [2]
-    uint64_t* mma3 = bar + 2;      // [2]
-    uint64_t* tfree = bar + 4;     // [2]
+    uint64_t* full = bar;          // [2] per input buffer
+    uint64_t* mma3 = bar + 2;      // [2] per input buffer
+    uint64_t* tfree = bar + 4;     // [2] per accumulator buffer
     uint64_t* a1full = bar + 6;
     uint64_t* mma1 = bar + 7;
-    uint64_t* gfull = bar + 8;     // [2]
-    uint64_t* rfree = bar + 10;    // [2]
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + C::OFF_BAR + 96);
-    volatile int* s_abort = reinterpret_cast<volatile int*>(smem + C::OFF_BAR + 100);
+    uint64_t* gfull = bar + 8;     // [2] per raw buffer
+    uint64_t* rfree = bar + 10;    // [2] per raw buffer
+    uint64_t* accf = bar + 12;     // [2] per accumulator buffer
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + C::OFF_BAR + 112);
+    volatile int* s_abort = reinterpret_cast<volatile int*>(smem + C::OFF_BAR + 116);
 
     const int tid = threadIdx.x;
     const int warp = tid >> 5;
 
     // ---- one-time set-up: weights, barriers, TMEM
-    for (int i = tid; i < C::B3_CHUNKS; i += kNT) st_shared_v4(sB3 + 16 * i, __ldg(a.b3img + i));
-    for (int i = tid; i < C::B1_CHUNKS; i += kNT) st_shared_v4(sB1 + 16 * i, __ldg(a.b1img + i));
-    for (int i = tid; i < CMID; i += kNT) bias3_s[i] = __ldg(a.bias3 + i);
-    for (int i = tid; i < COUT; i += kNT) bias1_s[i] = __ldg(a.bias1 + i);
+    for (int i = tid; i < C::B3_CHUNKS; i += NT) st_shared_v4(sB3 + 16 * i, __ldg(a.b3img + i));
+    for (int i = tid; i < C::B1_CHUNKS; i += NT) st_shared_v4(sB1 + 16 * i, __ldg(a.b1img + i));
+    for (int i = tid; i < CMID; i += NT) bias3_s[i] = __ldg(a.bias3 + i);
+    for (int i = tid; i < COUT; i += NT) bias1_s[i] = __ldg(a.bias1 + i);
     if (EPI == TEPI_HEAD)
-        for (int i = tid; i <= COUT; i += kNT) head_s[i] = __ldg(a.head + i);
-    for (int i = tid; i < C::ZERO_BYTES / 16; i += kNT) st_shared_v4(sbase + C::OFF_ZERO + 16 * i, make_uint4(0, 0, 0, 0));
+        for (int i = tid; i <= COUT; i += NT) head_s[i] = __ldg(a.head + i);
+    for (int i = tid; i < C::ZERO_BYTES / 16; i += NT) st_shared_v4(sbase + C::OFF_ZERO + 16 * i, make_uint4(0, 0, 0, 0));
     if (tid == 0) {
         for (int k = 0; k < 2; ++k) {
-            mbar_init(full + k, kNP);
+            mbar_init(full + k, NP);
             mbar_init(mma3 + k, 1);
-            mbar_init(tfree + k, 128);
-            mbar_init(gfull + k, kNP);
-            mbar_init(rfree + k, kNP);
+            mbar_init(tfree + k, NE);
+            mbar_init(gfull + k, NP);
+            mbar_init(rfree + k, NP);
+            mbar_init(accf + k, 1);
         }
-        mbar_init(a1full, 128);
+        mbar_init(a1full, NE);
         mbar_init(mma1, 1);
         fence_mbar_init();
         *s_abort = 0;
     }
-    if (warp == kMmaWarp) tmem_alloc(tslot, C::TMEM_COLS);
+    if (warp == MW) tmem_alloc(tslot, C::TMEM_COLS);
     fence_proxy_async_smem();  // the weights are read by the tensor core
     fence_before_sync();
     __syncthreads();
@@ -400,9 +467,9 @@ __global__ void __launch_bounds__(kNT, 1) level_tc_kernel(const __grid_constant_
     const uint32_t tbase = *tslot;
     const int ntiles = a.tile_start[a.nviews];
 
-    if (warp >= 4 && warp < kMmaWarp) {
-        // ================= producers
-        const int pt = tid - 128;
+    if (warp >= NEW && warp < MW) {
+        // ================= producers: step st = (tile it, K slice s) fills input buffer st % 2
+        const int pt = tid - NE;
         auto locate = [&](int tile, int& v, int& y0, int& x0) -> const TcJob& {
             while (tile >= a.tile_start[v + 1]) ++v;
             const TcJob& job = a.job[v];
@@ -413,65 +480,62 @@ __global__ void __launch_bounds__(kNT, 1) level_tc_kernel(const __grid_constant_
         };
         int v = 0, vn = 0, it = 0;
         if constexpr (PRO != TPRO_PLAIN) {
-            // prefetch the first tile's raw inputs (and skip) into buffer 0
+            // prefetch the first tile's raw inputs into raw buffer 0
             if (blockIdx.x < ntiles) {
                 int y0, x0;
                 const TcJob& job = locate(blockIdx.x, vn, y0, x0);
-                if constexpr (PRO == TPRO_GATHER) prefetch_gbuffer<R>(job, y0, x0, sRAW, pt);
-                else prefetch_coarse<CIN, R>(job, y0, x0, sRAW, pt);
-                if constexpr (PRO == TPRO_UP_SKIP) copy_tile<CIN, R>(job.skip, job.H, job.W, y0, x0, sA0, pt);
+                if constexpr (PRO == TPRO_GATHER) prefetch_gbuffer<NP, R>(job, y0, x0, sRAW, pt);
+                else prefetch_coarse<NP, CIN, R>(job, y0, x0, sRAW, pt);
                 cp_async_arrive(gfull + 0);
             }
         }
         bool failed = false;
         for (int tile = blockIdx.x; tile < ntiles && !failed; tile += gridDim.x, ++it) {
-            const int b = it & 1;
-            const uint32_t A0 = sA0 + b * (C::A0_CHUNKS * 16);
             int y0, x0;
             const TcJob& job = locate(tile, v, y0, x0);
-            if constexpr (PRO == TPRO_PLAIN) {
-                if (it >= 2 && !wait_phase(mma3 + b, ((it >> 1) - 1) & 1, s_abort)) { failed = true; break; }
-                copy_tile<CIN, R>(job.in, job.H, job.W, y0, x0, A0, pt);
-                cp_async_arrive(full + b);
-            } else {
-                // prefetch tile it + 1 into the other raw buffer (and its skip into the other input buffer)
+            const int rb = it & 1;
+            if constexpr (PRO != TPRO_PLAIN) {
+                // prefetch tile it + 1 into the other raw buffer
                 const int next = tile + gridDim.x;
                 if (next < ntiles) {
-                    const int nb = b ^ 1;
-                    const int un = (it + 1) >> 1;  // use index of buffer nb for tile it + 1
+                    const int nb = rb ^ 1;
+                    const int un = (it + 1) >> 1;  // use index of raw buffer nb for tile it + 1
                     if (un >= 1 && !wait_phase(rfree + nb, (un - 1) & 1, s_abort)) { failed = true; break; }
-                    if (PRO == TPRO_UP_SKIP && un >= 1 && !wait_phase(mma3 + nb, (un - 1) & 1, s_abort)) {
-                        failed = true;
-                        break;
-                    }
                     int ny0, nx0;
                     const TcJob& nj = locate(next, vn, ny0, nx0);
                     const uint32_t nraw = sRAW + nb * C::RAW_BYTES;
-                    if constexpr (PRO == TPRO_GATHER) prefetch_gbuffer<R>(nj, ny0, nx0, nraw, pt);
-                    else prefetch_coarse<CIN, R>(nj, ny0, nx0, nraw, pt);
-                    if constexpr (PRO == TPRO_UP_SKIP)
-                        copy_tile<CIN, R>(nj.skip, nj.H, nj.W, ny0, nx0, sA0 + nb * (C::A0_CHUNKS * 16), pt);
+                    if constexpr (PRO == TPRO_GATHER) prefetch_gbuffer<NP, R>(nj, ny0, nx0, nraw, pt);
+                    else prefetch_coarse<NP, CIN, R>(nj, ny0, nx0, nraw, pt);
                     cp_async_arrive(gfull + nb);
                 }
                 // this tile's raw inputs
-                if (!wait_phase(gfull + b, (it >> 1) & 1, s_abort)) { failed = true; break; }
-                if (PRO != TPRO_UP_SKIP && it >= 2 && !wait_phase(mma3 + b, ((it >> 1) - 1) & 1, s_abort)) {
-                    failed = true;
-                    break;
-                }
-                const uint32_t raw = sRAW + b * C::RAW_BYTES;
-                if constexpr (PRO == TPRO_GATHER) compute_gather<R>(job, y0, x0, raw, A0, pt);
-                else compute_up<CIN, R, PRO == TPRO_UP_SKIP>(job, y0, x0, raw, A0, pt);
-                fence_proxy_async_smem();
-                mbar_arrive(full + b);
-                mbar_arrive(rfree + b);
+                if (!wait_phase(gfull + rb, (it >> 1) & 1, s_abort)) { failed = true; break; }
             }
+            const uint32_t raw = sRAW + rb * C::RAW_BYTES;
+#pragma unroll 1
+            for (int s = 0; s < KS; ++s) {
+                const int st = it * KS + s, b = st & 1;
+                const uint32_t A0 = sA0 + b * (C::A0_CHUNKS * 16);
+                // input buffer b is free once the MMAs of step st - 2 are done
+                if (st >= 2 && !wait_phase(mma3 + b, ((st >> 1) - 1) & 1, s_abort)) { failed = true; break; }
+                if constexpr (PRO == TPRO_PLAIN) {
+                    copy_slice<NP, CIN, R, KS>(job.in, job.H, job.W, y0, x0, A0, s, pt);
+                    cp_async_arrive(full + b);
+                } else {
+                    if constexpr (PRO == TPRO_GATHER) compute_gather<NP, R>(job, y0, x0, raw, A0, pt);
+                    else compute_up<NP, CIN, R, KS, PRO == TPRO_UP_SKIP>(job, y0, x0, raw, A0, s, pt);
+                    fence_proxy_async_smem();
+                    mbar_arrive(full + b);
+                }
+            }
+            if (failed) break;
+            if constexpr (PRO != TPRO_PLAIN) mbar_arrive(rfree + rb);
         }
         if (failed) {
             atomicExch(a.err, 3);
             *s_abort = 1;
         }
-    } else if (warp == kMmaWarp) {
+    } else if (warp == MW) {
         // ================= MMA issuer
         if ((tid & 31) == 0) {
             constexpr uint32_t id3 = idesc_bf16(128, C::N3);
@@ -479,80 +543,83 @@ __global__ void __launch_bounds__(kNT, 1) level_tc_kernel(const __grid_constant_
             constexpr uint32_t kPlane = (R + 2) * kSW * 16;
             constexpr int kA1Part = (CMID / 8) * kTileM;
             int it = 0;
+            bool failed = false;
             for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
-                const int b = it & 1;
-                if (!wait_phase(full + b, (it >> 1) & 1, s_abort) ||
-                    (it >= 2 && !wait_phase(tfree + b, ((it >> 1) - 1) & 1, s_abort))) {
-                    atomicExch(a.err, 4);
-                    *s_abort = 1;
-                    break;
-                }
-                fence_proxy_async_smem();  // cp.async / st.shared data -> tensor core
-                fence_after_sync();
-                const uint32_t A0 = sA0 + b * (C::A0_CHUNKS * 16);
-                const uint32_t D = tbase + b * C::TMEM_BUF;
-                if constexpr (C::STACK) {
-                    // clear the R x N3 accumulator columns (zero A operand), then
-                    // one MMA per (staged row j, K step) of width (#ky) x N3:
-                    // output row r accumulates at column (R - 1 - r) N3, kernel
-                    // row ky of input row j at (R - 1 - j + ky) N3
-                    mma_bf16(D, smem_desc(sbase + C::OFF_ZERO, 16, 128), smem_desc(sB3, 16, 128),
-                             idesc_bf16(128, R * C::N3), 0);
-                    constexpr uint32_t kBL = 3 * C::N3 * 16;  // B: next K chunk
-                    const uint64_t bdesc = smem_desc(sB3, kBL, 128);
-#pragma unroll
-                    for (int j = 0; j < R + 2; ++j) {
-                        const int ka = j - (R - 1) > 0 ? j - (R - 1) : 0, kb = j < 2 ? j : 2;
-                        const uint32_t id = idesc_bf16(128, (kb - ka + 1) * C::N3);
-                        const uint32_t d = D + (R - 1 - j + ka) * C::N3;
-                        if constexpr (C::SPLIT) {
-                            // K = staged pixels m + 2p, m + 2p + 1 (4 features hi | lo each)
-                            const uint64_t adesc = smem_desc(A0 + 16 * (j * kSW), 16, 128);
-#pragma unroll
-                            for (int p2 = 0; p2 < 2; ++p2)
-                                mma_bf16(d, adesc + 2 * p2, bdesc + ((2 * p2 * 3 + ka) * C::N3), id, 1);
-                        } else {
-                            const uint64_t adesc = smem_desc(A0 + 16 * (j * kSW), kPlane, 128);
-#pragma unroll
-                            for (int kx = 0; kx < 3; ++kx)
-#pragma unroll
-                                for (int kk = 0; kk < CIN / 16; ++kk)
-                                    mma_bf16(d, adesc + (2 * kk * kPlane / 16 + kx),
-                                             bdesc + (((kx * C::CG_IN + 2 * kk) * 3 + ka) * C::N3), id, 1);
-                        }
+                const int tb = it & 1;
+                const uint32_t D = tbase + tb * C::TMEM_BUF;
+#pragma unroll 1
+                for (int s = 0; s < KS; ++s) {
+                    const int st = it * KS + s, b = st & 1;
+                    if (!wait_phase(full + b, (st >> 1) & 1, s_abort) ||
+                        (s == 0 && it >= 2 && !wait_phase(tfree + tb, ((it >> 1) - 1) & 1, s_abort))) {
+                        failed = true;
+                        break;
                     }
-                } else {
-                // 3x3: one MMA of width 2 CMID per K step (hi and lo weights stacked)
-                for (int r = 0; r < R; ++r) {
-                    const uint32_t d = D + r * C::N3;
-                    if constexpr (C::SPLIT) {
+                    fence_proxy_async_smem();  // cp.async / st.shared data -> tensor core
+                    fence_after_sync();
+                    const uint32_t A0 = sA0 + b * (C::A0_CHUNKS * 16);
+                    if constexpr (C::STACK) {
+                        // clear the R x N3 accumulator columns (zero A operand), then
+                        // one MMA per (staged row j, K step) of width (#ky) x N3:
+                        // output row r accumulates at column (R - 1 - r) N3, kernel
+                        // row ky of input row j at (R - 1 - j + ky) N3
+                        if (s == 0)
+                            mma_bf16(D, smem_desc(sbase + C::OFF_ZERO, 16, 128), smem_desc(sB3, 16, 128),
+                                     idesc_bf16(128, R * C::N3), 0);
+                        constexpr uint32_t kBL = 3 * C::N3 * 16;  // B: next K chunk
+                        const uint64_t bdesc = smem_desc(sB3, kBL, 128);
 #pragma unroll
-                        for (int k = 0; k < 5; ++k) {
-                            const int t0 = 2 * k, t1 = 2 * k + 1;
-                            const uint32_t a0 = A0 + 16 * ((r + t0 / 3) * kSW + t0 % 3);
-                            const uint32_t lbo = (t1 < 9) ? 16 * ((r + t1 / 3) * kSW + t1 % 3) - 16 * ((r + t0 / 3) * kSW + t0 % 3) : 16;
-                            mma_bf16(d, smem_desc(a0, lbo, 128), smem_desc(sB3 + 16 * (k * 2 * C::N3), C::N3 * 16, 128),
-                                     id3, k > 0);
+                        for (int j = 0; j < R + 2; ++j) {
+                            const int ka = j - (R - 1) > 0 ? j - (R - 1) : 0, kb = j < 2 ? j : 2;
+                            const uint32_t id = idesc_bf16(128, (kb - ka + 1) * C::N3);
+                            const uint32_t d = D + (R - 1 - j + ka) * C::N3;
+                            if constexpr (C::SPLIT) {
+                                // K = staged pixels m + 2p, m + 2p + 1 (4 features hi | lo each)
+                                const uint64_t adesc = smem_desc(A0 + 16 * (j * kSW), 16, 128);
+#pragma unroll
+                                for (int p2 = 0; p2 < 2; ++p2)
+                                    mma_bf16(d, adesc + 2 * p2, bdesc + ((2 * p2 * 3 + ka) * C::N3), id, 1);
+                            } else {
+                                // K step = planes (2q, 2q + 1) of one part; both parts use the same weights
+                                const uint64_t adesc = smem_desc(A0 + 16 * (j * kSW), kPlane, 128);
+#pragma unroll
+                                for (int kx = 0; kx < 3; ++kx)
+#pragma unroll
+                                    for (int q = 0; q < C::CGS / 2; ++q)
+#pragma unroll
+                                        for (int part = 0; part < 2; ++part)
+                                            mma_bf16(d, adesc + ((part * C::CGS + 2 * q) * kPlane / 16 + kx),
+                                                     bdesc + (((kx * C::CG_IN + s * C::CGS + 2 * q) * 3 + ka) * C::N3),
+                                                     id, 1);
+                            }
                         }
                     } else {
+                        // 3x3: one MMA of width 2 CMID per (row, tap, K step, part)
+                        for (int r = 0; r < R; ++r) {
+                            const uint32_t d = D + r * C::N3;
 #pragma unroll
-                        for (int tap = 0; tap < 9; ++tap) {
+                            for (int tap = 0; tap < 9; ++tap) {
 #pragma unroll
-                            for (int kk = 0; kk < CIN / 16; ++kk) {
-                                const uint32_t a0 = A0 + (2 * kk) * kPlane + 16 * ((r + tap / 3) * kSW + tap % 3);
-                                const uint32_t b0 = sB3 + 16 * ((tap * C::CG_IN + 2 * kk) * C::N3);
-                                mma_bf16(d, smem_desc(a0, kPlane, 128), smem_desc(b0, C::N3 * 16, 128), id3,
-                                         (tap | kk) != 0);
+                                for (int q = 0; q < C::CGS / 2; ++q) {
+#pragma unroll
+                                    for (int part = 0; part < 2; ++part) {
+                                        const uint32_t a0 = A0 + (part * C::CGS + 2 * q) * kPlane +
+                                                            16 * ((r + tap / 3) * kSW + tap % 3);
+                                        const uint32_t b0 = sB3 + 16 * ((tap * C::CG_IN + s * C::CGS + 2 * q) * C::N3);
+                                        mma_bf16(d, smem_desc(a0, kPlane, 128), smem_desc(b0, C::N3 * 16, 128), id3,
+                                                 (s | tap | q | part) != 0);
+                                    }
+                                }
                             }
                         }
                     }
+                    mma_commit(mma3 + b);  // input buffer b consumed
                 }
-                }
-                mma_commit(mma3 + b);
+                if (failed) break;
+                mma_commit(accf + tb);     // 3x3 accumulators of this tile complete
                 // 1x1 once the epilogue has written its operand: (A_hi + A_lo) [B_hi; B_lo]
                 if (!wait_phase(a1full, it & 1, s_abort)) {
-                    atomicExch(a.err, 5);
-                    *s_abort = 1;
+                    failed = true;
                     break;
                 }
                 fence_after_sync();
@@ -569,31 +636,37 @@ __global__ void __launch_bounds__(kNT, 1) level_tc_kernel(const __grid_constant_
                 }
                 mma_commit(mma1);
             }
+            if (failed) {
+                atomicExch(a.err, 4);
+                *s_abort = 1;
+            }
         }
         __syncwarp();
     } else {
-        // ================= epilogue (warps 0-3; warp = TMEM lane quarter)
-        const int m = tid;  // pixel of the row block = TMEM lane
-        const uint32_t tlane = tbase + (static_cast<uint32_t>(warp * 32) << 16);
+        // ================= epilogue (warps 0 .. NEW-1; TMEM lane quarter = warp % 4)
+        constexpr int G = NEW / 4;
+        const int m = (warp & 3) * 32 + (tid & 31);  // pixel of the row block = TMEM lane
+        const int rg = G == 1 ? 0 : warp >> 2;         // row group of this warp
+        const uint32_t tlane = tbase + (static_cast<uint32_t>((warp & 3) * 32) << 16);
         constexpr int kA1Part = (CMID / 8) * kTileM;
         int v = 0, it = 0;
         for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
-            const int b = it & 1;
+            const int tb = it & 1;
             while (tile >= a.tile_start[v + 1]) ++v;
             const TcJob& job = a.job[v];
             const int H = job.H, W = job.W;
             const int local = tile - a.tile_start[v];
             const int y0 = (local / job.tiles_x) * R;
             const int x0 = (local % job.tiles_x) * kTileM;
-            const uint32_t Dl = tlane + b * C::TMEM_BUF;
-            if (!wait_phase(mma3 + b, (it >> 1) & 1, s_abort)) {
+            const uint32_t Dl = tlane + tb * C::TMEM_BUF;
+            if (!wait_phase(accf + tb, (it >> 1) & 1, s_abort)) {
                 atomicExch(a.err, 1);
                 *s_abort = 1;
                 break;
             }
             fence_after_sync();
             // ---- 3x3 result: bias + ReLU -> BF16 hi + lo -> operand of the 1x1
-            for (int r = 0; r < R; ++r) {
+            for (int r = rg; r < R; r += G) {
 #pragma unroll
                 for (int c0 = 0; c0 < CMID; c0 += 16) {
                     float val[16], lo[16];
@@ -625,10 +698,10 @@ __global__ void __launch_bounds__(kNT, 1) level_tc_kernel(const __grid_constant_
                 break;
             }
             fence_after_sync();
-            // ---- 1x1 result -> outputs
+            // ---- 1x1 result -> outputs (pooled: BF16 hi + lo [pixel][part][COUT]; else FP32)
             const int ox = x0 + m;
             if constexpr (EPI == TEPI_POOL || EPI == TEPI_SKIP_POOL) {
-                for (int r = 0; r < R; r += 2) {
+                for (int r = 2 * rg; r < R; r += 2 * G) {
                     float s[COUT];
 #pragma unroll
                     for (int c0 = 0; c0 < COUT; c0 += 16) {
@@ -647,12 +720,14 @@ __global__ void __launch_bounds__(kNT, 1) level_tc_kernel(const __grid_constant_
                         if constexpr (EPI == TEPI_SKIP_POOL) {
                             const int oy = y0 + r;
                             if (oy < H && ox < W) {
-                                uint16_t* dst = job.out_skip + (static_cast<size_t>(oy) * W + ox) * COUT + c0;
-                                reinterpret_cast<uint4*>(dst)[0] = f32_to_chunk(v0);
-                                reinterpret_cast<uint4*>(dst)[1] = f32_to_chunk(v0 + 8);
-                                dst += static_cast<size_t>(W) * COUT;
-                                reinterpret_cast<uint4*>(dst)[0] = f32_to_chunk(v1);
-                                reinterpret_cast<uint4*>(dst)[1] = f32_to_chunk(v1 + 8);
+                                float4* dst = reinterpret_cast<float4*>(job.out_skip +
+                                                                        (static_cast<size_t>(oy) * W + ox) * COUT + c0);
+                                float4* dst1 = dst + static_cast<size_t>(W) * (COUT / 4);
+#pragma unroll
+                                for (int q = 0; q < 4; ++q) {
+                                    dst[q] = make_float4(v0[4 * q], v0[4 * q + 1], v0[4 * q + 2], v0[4 * q + 3]);
+                                    dst1[q] = make_float4(v1[4 * q], v1[4 * q + 1], v1[4 * q + 2], v1[4 * q + 3]);
+                                }
                             }
                         }
                     }
@@ -660,20 +735,20 @@ __global__ void __launch_bounds__(kNT, 1) level_tc_kernel(const __grid_constant_
                     for (int c = 0; c < COUT; ++c) s[c] = 0.25f * (s[c] + __shfl_xor_sync(0xffffffffu, s[c], 1));
                     const int oy = y0 + r;
                     if (oy < H && ox < W) {
-                        // even pixel writes the first half of the channels, odd the second
-                        const int half = (m & 1) * (COUT / 2);
-                        uint16_t* dst = job.out + (static_cast<size_t>(oy / 2) * (W / 2) + ox / 2) * COUT + half;
+                        // even pixel writes the hi part, odd pixel the lo part
+                        const int part = m & 1;
+                        uint4* dst = reinterpret_cast<uint4*>(job.out + (static_cast<size_t>(oy / 2) * (W / 2) + ox / 2) *
+                                                                            2 * COUT) + part * (COUT / 8);
 #pragma unroll
-                        for (int c = 0; c < COUT / 2; c += 8) {
-                            float t8[8];
-#pragma unroll
-                            for (int j = 0; j < 8; ++j) t8[j] = s[half + c + j];
-                            reinterpret_cast<uint4*>(dst + c)[0] = f32_to_chunk(t8);
+                        for (int c = 0; c < COUT; c += 8) {
+                            uint4 h, l;
+                            split_chunks(s + c, h, l);
+                            dst[c / 8] = part ? l : h;
                         }
                     }
                 }
             } else {
-                for (int r = 0; r < R; ++r) {
+                for (int r = rg; r < R; r += G) {
                     const int oy = y0 + r;
                     float hsum = 0.f;
 #pragma unroll
@@ -686,9 +761,11 @@ __global__ void __launch_bounds__(kNT, 1) level_tc_kernel(const __grid_constant_
                         for (int j = 0; j < 16; ++j) val[j] = fmaxf(val[j] + lo[j] + bias1_s[c0 + j], 0.f);
                         if constexpr (EPI == TEPI_STORE) {
                             if (oy < H && ox < W) {
-                                uint16_t* dst = job.out + (static_cast<size_t>(oy) * W + ox) * COUT + c0;
-                                reinterpret_cast<uint4*>(dst)[0] = f32_to_chunk(val);
-                                reinterpret_cast<uint4*>(dst)[1] = f32_to_chunk(val + 8);
+                                float4* dst = reinterpret_cast<float4*>(job.out_f +
+                                                                        (static_cast<size_t>(oy) * W + ox) * COUT + c0);
+#pragma unroll
+                                for (int q = 0; q < 4; ++q)
+                                    dst[q] = make_float4(val[4 * q], val[4 * q + 1], val[4 * q + 2], val[4 * q + 3]);
                             }
                         } else {
 #pragma unroll
@@ -700,7 +777,7 @@ __global__ void __launch_bounds__(kNT, 1) level_tc_kernel(const __grid_constant_
                 }
             }
             fence_before_sync();
-            mbar_arrive(tfree + b);
+            mbar_arrive(tfree + tb);
         }
     }
 
@@ -708,14 +785,14 @@ __global__ void __launch_bounds__(kNT, 1) level_tc_kernel(const __grid_constant_
     asm volatile("cp.async.wait_all;" ::: "memory");
     __syncthreads();
     fence_after_sync();
-    if (warp == kMmaWarp) tmem_dealloc(tbase, C::TMEM_COLS);
+    if (warp == MW) tmem_dealloc(tbase, C::TMEM_COLS);
 }
 
 // ------------------------------------------------------------------ variants and launch
-template <int CIN, int CMID, int COUT, int R, int PRO, int EPI>
+template <int CIN, int CMID, int COUT, int R, int PRO, int EPI, int NEW, int NPW, int KS>
 static cudaError_t launch_variant(const TcBatch& a, int ctas_per_sm, cudaStream_t stream) {
-    using C = TcCfg<CIN, CMID, COUT, R, PRO>;
-    auto kern = level_tc_kernel<CIN, CMID, COUT, R, PRO, EPI>;
+    using C = TcCfg<CIN, CMID, COUT, R, PRO, KS>;
+    auto kern = level_tc_kernel<CIN, CMID, COUT, R, PRO, EPI, NEW, NPW, KS>;
     static int occ = -1;
     if (occ < 0) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::BYTES);
@@ -725,7 +802,7 @@ static cudaError_t launch_variant(const TcBatch& a, int ctas_per_sm, cudaStream_
         cudaFuncAttributes fa{};
         e = cudaFuncGetAttributes(&fa, kern);
         if (e != cudaSuccess) return e;
-        const int regs = ((fa.numRegs + 7) / 8) * 8 * kNT;
+        const int regs = ((fa.numRegs + 7) / 8) * 8 * (32 * (NEW + NPW + 1));
         const int by_regs = regs > 0 ? 65536 / regs : 8;
         const int by_smem = (228 * 1024) / (C::BYTES + 1024);
         int o = by_regs < by_smem ? by_regs : by_smem;
@@ -738,21 +815,21 @@ static cudaError_t launch_variant(const TcBatch& a, int ctas_per_sm, cudaStream_
     const int per_sm = (ctas_per_sm <= 0 || ctas_per_sm > occ) ? occ : ctas_per_sm;
     const int cap = per_sm * num_sms();
     const int grid = tiles < cap ? tiles : cap;
-    kern<<<grid, kNT, C::BYTES, stream>>>(a);
+    kern<<<grid, 32 * (NEW + NPW + 1), C::BYTES, stream>>>(a);
     return cudaGetLastError();
 }
 
-template <int CIN, int CMID, int COUT, int R, int PRO, int EPI>
+template <int CIN, int CMID, int COUT, int R, int PRO, int EPI, int NEW, int NPW, int KS>
 static const void* kernel_of() {
-    return reinterpret_cast<const void*>(level_tc_kernel<CIN, CMID, COUT, R, PRO, EPI>);
+    return reinterpret_cast<const void*>(level_tc_kernel<CIN, CMID, COUT, R, PRO, EPI, NEW, NPW, KS>);
 }
 
-template <int CIN, int CMID, int COUT, int R, int PRO, int EPI>
+template <int CIN, int CMID, int COUT, int R, int PRO, int EPI, int NEW, int NPW, int KS>
 static int occupancy_of() {
-    using C = TcCfg<CIN, CMID, COUT, R, PRO>;
+    using C = TcCfg<CIN, CMID, COUT, R, PRO, KS>;
     cudaFuncAttributes fa{};
-    if (cudaFuncGetAttributes(&fa, level_tc_kernel<CIN, CMID, COUT, R, PRO, EPI>) != cudaSuccess) return 1;
-    const int regs = ((fa.numRegs + 7) / 8) * 8 * kNT;
+    if (cudaFuncGetAttributes(&fa, level_tc_kernel<CIN, CMID, COUT, R, PRO, EPI, NEW, NPW, KS>) != cudaSuccess) return 1;
+    const int regs = ((fa.numRegs + 7) / 8) * 8 * (32 * (NEW + NPW + 1));
     const int by_regs = regs > 0 ? 65536 / regs : 8;
     const int by_smem = (228 * 1024) / (C::BYTES + 1024);
     int o = by_regs < by_smem ? by_regs : by_smem;
@@ -761,40 +838,57 @@ static int occupancy_of() {
     return o < 1 ? 1 : o;
 }
 
-// Variant tables: the tile height R of every stage (the autotuner's search space).
+// Variant tables: tile height R and warp roles of every stage (the
+// autotuner's search space).
 using LaunchFn = cudaError_t (*)(const TcBatch&, int, cudaStream_t);
-struct Variant { int R; LaunchFn fn; const void* (*func)(); int (*occ)(); };
-#define NSM_VARIANT(R_, ...) {R_, launch_variant<__VA_ARGS__>, kernel_of<__VA_ARGS__>, occupancy_of<__VA_ARGS__>}
+struct Variant { int R, ew, pw, ks; LaunchFn fn; const void* (*func)(); int (*occ)(); };
+#define NSM_VARIANT(R_, EW_, PW_, KS_, CIN_, CMID_, COUT_, PRO_, EPI_)                                   \
+    {R_, EW_, PW_, KS_, launch_variant<CIN_, CMID_, COUT_, R_, PRO_, EPI_, EW_, PW_, KS_>,                \
+     kernel_of<CIN_, CMID_, COUT_, R_, PRO_, EPI_, EW_, PW_, KS_>,                                        \
+     occupancy_of<CIN_, CMID_, COUT_, R_, PRO_, EPI_, EW_, PW_, KS_>}
 
+// (rows, epilogue warps, producer warps, K slices, C_in, C_mid, C_out, prologue, epilogue)
 static const Variant kVarEnc0[] = {
-    NSM_VARIANT(2, 4, 16, 16, 2, TPRO_GATHER, TEPI_POOL),
-    NSM_VARIANT(4, 4, 16, 16, 4, TPRO_GATHER, TEPI_POOL),
-    NSM_VARIANT(8, 4, 16, 16, 8, TPRO_GATHER, TEPI_POOL)};
+    NSM_VARIANT(4, 4, 8, 1, 4, 16, 16, TPRO_GATHER, TEPI_POOL),
+    NSM_VARIANT(4, 8, 8, 1, 4, 16, 16, TPRO_GATHER, TEPI_POOL),
+    NSM_VARIANT(8, 4, 8, 1, 4, 16, 16, TPRO_GATHER, TEPI_POOL),
+    NSM_VARIANT(8, 4, 16, 1, 4, 16, 16, TPRO_GATHER, TEPI_POOL),
+    NSM_VARIANT(8, 8, 12, 1, 4, 16, 16, TPRO_GATHER, TEPI_POOL)};
 static const Variant kVarEnc1[] = {
-    NSM_VARIANT(2, 16, 32, 32, 2, TPRO_PLAIN, TEPI_SKIP_POOL),
-    NSM_VARIANT(4, 16, 32, 32, 4, TPRO_PLAIN, TEPI_SKIP_POOL)};
+    NSM_VARIANT(2, 4, 8, 1, 16, 32, 32, TPRO_PLAIN, TEPI_SKIP_POOL),
+    NSM_VARIANT(2, 8, 8, 1, 16, 32, 32, TPRO_PLAIN, TEPI_SKIP_POOL),
+    NSM_VARIANT(4, 4, 8, 1, 16, 32, 32, TPRO_PLAIN, TEPI_SKIP_POOL),
+    NSM_VARIANT(4, 8, 8, 1, 16, 32, 32, TPRO_PLAIN, TEPI_SKIP_POOL)};
 static const Variant kVarBott[] = {
-    NSM_VARIANT(1, 32, 64, 32, 1, TPRO_PLAIN, TEPI_STORE),
-    NSM_VARIANT(2, 32, 64, 32, 2, TPRO_PLAIN, TEPI_STORE)};
+    NSM_VARIANT(1, 4, 8, 1, 32, 64, 32, TPRO_PLAIN, TEPI_STORE),
+    NSM_VARIANT(2, 4, 8, 2, 32, 64, 32, TPRO_PLAIN, TEPI_STORE),
+    NSM_VARIANT(2, 8, 8, 2, 32, 64, 32, TPRO_PLAIN, TEPI_STORE)};
 static const Variant kVarDec1[] = {
-    NSM_VARIANT(2, 32, 32, 16, 2, TPRO_UP_SKIP, TEPI_STORE)};
+    NSM_VARIANT(2, 4, 8, 2, 32, 32, 16, TPRO_UP_SKIP, TEPI_STORE),
+    NSM_VARIANT(2, 8, 8, 2, 32, 32, 16, TPRO_UP_SKIP, TEPI_STORE)};
 static const Variant kVarDec0[] = {
-    NSM_VARIANT(2, 16, 16, 16, 2, TPRO_UP, TEPI_HEAD),
-    NSM_VARIANT(4, 16, 16, 16, 4, TPRO_UP, TEPI_HEAD),
-    NSM_VARIANT(8, 16, 16, 16, 8, TPRO_UP, TEPI_HEAD)};
+    NSM_VARIANT(4, 4, 8, 1, 16, 16, 16, TPRO_UP, TEPI_HEAD),
+    NSM_VARIANT(4, 8, 8, 1, 16, 16, 16, TPRO_UP, TEPI_HEAD),
+    NSM_VARIANT(4, 8, 12, 1, 16, 16, 16, TPRO_UP, TEPI_HEAD)};
 
 struct StageTable { const Variant* v; int n; };
+#define NSM_STAGE(t) {t, static_cast<int>(sizeof(t) / sizeof(t[0]))}
 static const StageTable kStages[kTcStages] = {
-    {kVarEnc0, 3}, {kVarEnc1, 2}, {kVarBott, 2}, {kVarDec1, 1}, {kVarDec0, 3}};
+    NSM_STAGE(kVarEnc0), NSM_STAGE(kVarEnc1), NSM_STAGE(kVarBott), NSM_STAGE(kVarDec1), NSM_STAGE(kVarDec0)};
 
 int tc_stage_variants(int stage) { return (stage >= 0 && stage < kTcStages) ? kStages[stage].n : 0; }
 int tc_stage_rows(int stage, int variant) { return kStages[stage].v[variant].R; }
 const void* tc_stage_kernel(int stage, int variant) { return kStages[stage].v[variant].func(); }
 int tc_stage_occupancy(int stage, int variant) { return kStages[stage].v[variant].occ(); }
 
+int tc_stage_warps(int stage, int variant, int* producer_warps) {
+    if (producer_warps) *producer_warps = kStages[stage].v[variant].pw;
+    return kStages[stage].v[variant].ew;
+}
+
 int tc_default_variant(int stage) {
-    // R = 4 for the full-resolution stages, the smaller tiles for the others
-    static const int def[kTcStages] = {1, 1, 1, 0, 1};
+    // the fastest plan of the 1080p autotuning runs
+    static const int def[kTcStages] = {3, 2, 1, 0, 1};
     return def[stage];
 }
 
@@ -845,12 +939,12 @@ void tc_make_batches(const GatherParams* g, const Activations* act, float* const
             switch (s) {
                 case 0: j.H = H; j.W = W; j.out = static_cast<uint16_t*>(A.e0); break;
                 case 1: j.H = H / 2; j.W = W / 2; j.in = static_cast<const uint16_t*>(A.e0);
-                        j.out_skip = static_cast<uint16_t*>(A.s1); j.out = static_cast<uint16_t*>(A.p1); break;
+                        j.out_skip = static_cast<float*>(A.s1); j.out = static_cast<uint16_t*>(A.p1); break;
                 case 2: j.H = H / 4; j.W = W / 4; j.in = static_cast<const uint16_t*>(A.p1);
-                        j.out = static_cast<uint16_t*>(A.bo); break;
-                case 3: j.H = H / 2; j.W = W / 2; j.in = static_cast<const uint16_t*>(A.bo);
-                        j.skip = static_cast<const uint16_t*>(A.s1); j.out = static_cast<uint16_t*>(A.d1); break;
-                default: j.H = H; j.W = W; j.in = static_cast<const uint16_t*>(A.d1); j.vis = vis[i]; break;
+                        j.out_f = static_cast<float*>(A.bo); break;
+                case 3: j.H = H / 2; j.W = W / 2; j.in_f = static_cast<const float*>(A.bo);
+                        j.skip = static_cast<const float*>(A.s1); j.out_f = static_cast<float*>(A.d1); break;
+                default: j.H = H; j.W = W; j.in_f = static_cast<const float*>(A.d1); j.vis = vis[i]; break;
             }
         }
     }

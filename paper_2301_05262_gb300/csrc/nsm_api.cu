@@ -301,8 +301,8 @@ nsm_status nsm_features(const nsm_frame* frame, float* feat_out, int32_t* texel_
 
 size_t nsm_infer_workspace_bytes(int H, int W, nsm_precision precision) {
     if (H <= 0 || W <= 0) return 0;
-    const size_t eb = (precision == NSM_FP32) ? 4 : 2;
-    return activations_bytes(H, W, eb, nullptr, nullptr);
+    (void)precision;  // FP32 activations, or BF16 hi + lo pairs: 4 bytes per channel either way
+    return activations_bytes(H, W, 4, nullptr, nullptr);
 }
 
 nsm_status nsm_infer(nsm_ctx* ctx, const nsm_frame* frame, const nsm_weights* w, nsm_precision precision,
@@ -325,7 +325,7 @@ nsm_status nsm_infer(nsm_ctx* ctx, const nsm_frame* frame, const nsm_weights* w,
     if ((s = check_dev_ptr(workspace, "workspace", 256)) != NSM_OK) return s;
     if (precision == NSM_FP8) return fail(NSM_ERR_UNSUPPORTED, "precision %d not built yet", static_cast<int>(precision));
     Activations act{};
-    activations_bytes(frame->H, frame->W, precision == NSM_FP32 ? 4 : 2, &act, workspace);
+    activations_bytes(frame->H, frame->W, 4, &act, workspace);
     GatherParams g = make_gather(frame);
     StageEvents se;
     const int k = nsm_infer_kernel_count(precision);

@@ -42,6 +42,7 @@ size_t align_up(size_t v, size_t a);
 
 // Activation buffers of one inference, carved out of the caller's workspace.
 struct Activations {
+    // FP32 [..][C], or BF16 hi + lo pairs [..][2][C]: 4 bytes per channel
     void* e0;   // [H/2][W/2][16]  pooled level-0 encoder output
     void* s1;   // [H/2][W/2][32]  level-1 encoder output (decoder skip)
     void* p1;   // [H/4][W/4][32]  pooled level-1 encoder output

@@ -20,10 +20,15 @@ struct TcJob {
     GatherParams g;             // GATHER prologue: the view's G-buffer, map, emitter, camera
     int H, W;                   // the stage's resolution for this view
     int tiles_x;                // tiles per row (filled at launch)
-    const uint16_t* in;         // BF16 NHWC: PLAIN [H][W][CIN]; UP* [H/2][W/2][CIN]
-    const uint16_t* skip;       // UP_SKIP: [H][W][CIN]
-    uint16_t* out;              // POOL / SKIP_POOL: [H/2][W/2][COUT] (pooled); STORE: [H][W][COUT]
-    uint16_t* out_skip;         // SKIP_POOL: [H][W][COUT]
+    // activations read by the tensor cores straight from memory (PLAIN inputs)
+    // are BF16 hi + lo pairs, [pixel][part][C] (part 0 = hi, 1 = lo); those
+    // the up-sampling producers read are FP32 [pixel][C] (same 4 bytes per channel)
+    const uint16_t* in;         // PLAIN: [H][W][2][CIN]
+    const float* in_f;          // UP*: [H/2][W/2][CIN]
+    const float* skip;          // UP_SKIP: [H][W][CIN]
+    uint16_t* out;              // POOL / SKIP_POOL: pooled [H/2][W/2][2][COUT]
+    float* out_f;               // STORE: [H][W][COUT]
+    float* out_skip;            // SKIP_POOL: [H][W][COUT]
     float* vis;                 // HEAD: [H][W]
 };
 
@@ -44,6 +49,7 @@ struct Activations;
 
 int tc_stage_variants(int stage);
 int tc_stage_rows(int stage, int variant);
+int tc_stage_warps(int stage, int variant, int* producer_warps);  // epilogue warps
 int tc_default_variant(int stage);
 const void* tc_stage_kernel(int stage, int variant);
 int tc_stage_occupancy(int stage, int variant);

@@ -32,7 +32,8 @@ def test_abi_version_and_param_count(lib):
 
 
 def test_workspace_bytes(lib):
-    for prec, eb in ((nsm.NSM_FP32, 4), (nsm.NSM_BF16, 2)):
+    # FP32 activations, or BF16 hi + lo pairs: 4 bytes per channel in both forms
+    for prec, eb in ((nsm.NSM_FP32, 4), (nsm.NSM_BF16, 4)):
         H, W = 1080, 1920
         n = nsm.nsm_infer_workspace_bytes(H, W, prec)
         h2, h4 = (H // 2) * (W // 2), (H // 4) * (W // 4)

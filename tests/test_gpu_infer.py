@@ -2,14 +2,11 @@
 oracle on the same seeded inputs.
 
 FP32 form: max-abs <= 1e-4 on visibility against the FP64 forward.
-BF16 form: (a) against the oracle forward with the BF16 storage points
-rounded the same way (level outputs to BF16; weights, the 3x3 -> 1x1
-intermediate and the features as BF16 hi + lo pairs): MSE <= 1e-6 and
-max-abs <= 5e-2 -- what is left is FP32 accumulation order, which makes a
-few activations per receptive field round to the neighbouring BF16 value;
-(b) against the exact FP64 forward: MSE <= 1e-4, and max-abs <= 1e-2 on the
-256^2 frames (test_infer_bf16_vs_fp64); with random He-init weights the
-largest errors over a full 1080p frame reach a few 1e-2 (reported by bench.py)."""
+BF16 form (compensated: every stored value a BF16 hi + lo pair): (a) against
+the oracle forward rounded the same way at every storage point (features,
+weights, the 3x3 -> 1x1 intermediate, every level output): MSE <= 1e-8 and
+max-abs <= 1e-3 -- what is left is FP32 accumulation order; (b) against the
+exact FP64 forward: MSE <= 1e-4 and max-abs <= 1e-2."""
 import numpy as np
 import pytest
 
@@ -57,13 +54,12 @@ def _check(ctx, f, theta, precision):
     if precision == nsm.NSM_FP32:
         assert err.max() <= 1e-4, err.max()
     else:
-        qref = N.forward_rounded(feat, th64, N.round_bf16, rnd_in=N.round_bf16_pair,
-                                 rnd_w=N.round_bf16_pair, rnd_mid=N.round_bf16_pair)
+        qref = N.forward_rounded(feat, th64, N.round_bf16_pair, rnd_in=N.round_bf16_pair)
         qerr = np.abs(vis - qref)
-        # the kernel follows the rounding model: 10x below its error vs FP64
-        assert float(np.mean(qerr ** 2)) <= 1e-6, float(np.mean(qerr ** 2))
-        assert qerr.max() <= 5e-2, qerr.max()
+        assert float(np.mean(qerr ** 2)) <= 1e-8, float(np.mean(qerr ** 2))
+        assert qerr.max() <= 1e-3, qerr.max()
         assert float(np.mean(err ** 2)) <= 1e-4
+        assert err.max() <= 1e-2, err.max()
     return vis, err
 
 
