@@ -888,7 +888,7 @@ int tc_stage_warps(int stage, int variant, int* producer_warps) {
 
 int tc_default_variant(int stage) {
     // the fastest plan of the 1080p autotuning runs
-    static const int def[kTcStages] = {3, 2, 1, 0, 1};
+    static const int def[kTcStages] = {3, 2, 2, 0, 1};
     return def[stage];
 }
 
