@@ -141,6 +141,14 @@ def barrier(world: int):
         dist.barrier()
 
 
+def job_throughput(local_seconds: float, units_per_rank: float, world: int, device):
+    """Whole-job rate of a weak-scaling run: every rank processes the same
+    number of units; the job time is the slowest rank's (max over ranks).
+    Returns (job seconds, units of all ranks / job seconds)."""
+    job_s = reduce_max(local_seconds, world, device)
+    return job_s, world * units_per_rank / job_s
+
+
 # ------------------------------------------------------------------ oracle (reference arm / cpu baseline)
 def oracle_sample(frame, theta, rows: int):
     """Time the FP64 oracle (features + network forward) on the first `rows`
@@ -275,11 +283,12 @@ def run_ours(args):
         ctx.set_stage_events([])
         ctx.check()
         step_ms = [a.elapsed_time(b) for (a, b) in step_ev]
-        total_ms = reduce_max(sum(step_ms), world, device)
+        job_s, rate = job_throughput(sum(step_ms) * 1e-3, H * W * args.steps, world, device)
+        total_ms = job_s * 1e3
         per_kernel = {}
         for i, kn in enumerate(knames):
             per_kernel[kn] = sum(stage_ev[k][i].elapsed_time(stage_ev[k][i + 1]) for k in range(args.steps)) / args.steps
-        forms[pname] = {"ms_per_frame": total_ms / args.steps, "mpix_s": world * H * W * args.steps / (total_ms * 1e-3) / 1e6,
+        forms[pname] = {"ms_per_frame": total_ms / args.steps, "mpix_s": rate / 1e6,
                         "kernels_ms": per_kernel, "launches_per_step": nk, "clocks": clocks}
 
     # end-to-end through the host-buffer entry point (copies inside the timed region)
@@ -305,8 +314,8 @@ def run_ours(args):
     for _ in range(args.steps):
         nsm.nsm_infer_host(ctx, hfr, weights, prec, stage, ws, vis_np)
     torch.cuda.synchronize()
-    e2e_s = reduce_max(time.perf_counter() - t0, world, device)
-    e2e = {"value": world * H * W * args.steps / e2e_s / 1e6, "unit": "Mpix/s",
+    e2e_s, e2e_rate = job_throughput(time.perf_counter() - t0, H * W * args.steps, world, device)
+    e2e = {"value": e2e_rate / 1e6, "unit": "Mpix/s",
            "h2d_bytes_per_step": 2 * H * W * 16 + HS * WS * 4, "d2h_bytes_per_step": H * W * 4,
            "ms_per_frame": e2e_s / args.steps * 1e3}
 
