@@ -158,12 +158,7 @@ nsm_status nsm_infer_batched(nsm_ctx* c, int n, const nsm_view* views, const nsm
         for (int k = 0; k < kTcStages; ++k) {
             // the tile tables are a pure function of the plan; refill them for the job copy
             TcBatch& bk = b[k];
-            bk.tile_start[0] = 0;
-            const int R = tc_stage_rows(k, c->tc_variant[k]);
-            for (int i = 0; i < n; ++i) {
-                bk.job[i].tiles_x = (bk.job[i].W + 127) / 128;
-                bk.tile_start[i + 1] = bk.tile_start[i] + bk.job[i].tiles_x * ((bk.job[i].H + R - 1) / R);
-            }
+            tc_fill_tiles(bk, tc_stage_rows(k, c->tc_variant[k]));
             cudaKernelNodeParams p = c->graph_params[k];
             void* args[1] = {&bk};
             p.kernelParams = args;

@@ -90,11 +90,18 @@ struct TcCfg {
     static constexpr int PLN = SPLIT ? 1 : 2 * CGS;
     static constexpr int KSTEPS3 = SPLIT ? 5 : 9 * (CIN / 16);
     static constexpr int A0_CHUNKS = PLN * (R + 2) * kSW;        // one input buffer
+    // KS == 1: the two input buffers form one ring of 2 (R + 2) staged rows per
+    // plane, so a tile that continues the previous one down its column reuses
+    // the two overlapping rows and stages only R new ones; KS > 1: two buffers
+    // of R + 2 rows, one K slice each
+    static constexpr bool RING = (KS == 1);
+    static constexpr int NRW = RING ? 2 * (R + 2) : R + 2;      // staged rows per plane
+    static constexpr uint32_t PLANE = NRW * kSW * 16;            // bytes per plane
     // 3x3 -> 1x1 intermediate as BF16 hi + lo parts: [row][part][channel group][pixel]
     static constexpr int A1_CHUNKS = R * 2 * (CMID / 8) * kTileM;
     // raw prefetch buffer (two): the staged G-buffer (pos, nrm) or the coarse rows (hi + lo)
     static constexpr int NCR = R / 2 + 2;
-    static constexpr int RAW_BYTES = SPLIT ? (R + 2) * 130 * 32 : (UP ? NCR * kNCC * 2 * CG_IN * 16 : 0);
+    static constexpr int RAW_BYTES = SPLIT ? (R + 2) * 130 * 32 : (UP ? NCR * kNCC * (CIN / 4 + 1) * 16 : 0);
     // weights as BF16 hi + lo parts stacked along the output rows (2 C rows per K block)
     static constexpr int N3 = 2 * CMID, N1 = 2 * COUT;             // MMA widths
     // row-stacked 3x3: the kernel rows ky = 0, 1, 2 stacked along N as well, so
@@ -184,17 +191,24 @@ __device__ __forceinline__ uint4 f32_to_chunk(const float* f) {
 }
 
 // ------------------------------------------------------------------ producer pieces
-// (pt = producer thread 0..NP-1 of NP; staged rows y0-1 .. y0+R, pixels x0-1 .. x0+128)
+// (pt = producer thread 0..NP-1 of NP; staged rows y0-1 .. y0+R, pixels x0-1 .. x0+128;
+// staged row sr of a tile lives in row slot (base + sr) mod NRW of every plane,
+// and a producer call writes the staged rows [first, R + 2))
+template <int NRW>
+__device__ __forceinline__ int row_slot(int base, int sr) {
+    const int q = base + sr;
+    return q >= NRW ? q - NRW : q;
+}
 // Activations in global memory: [pixel][part][C] BF16, part 0 = hi, 1 = lo, so
 // chunk part * CG + g of a pixel holds channels 8g .. 8g+7 of that part.
 
 // PLAIN: K slice s of an NHWC tile straight into the input buffer, zeros
 // outside the image (planes [part][group of the slice])
-template <int NP, int CIN, int R, int KS>
+template <int NP, int CIN, int R, int KS, int NRW>
 __device__ __forceinline__ void copy_slice(const uint16_t* src, int H, int W, int y0, int x0, uint32_t a0, int s,
-                                           int pt) {
+                                           int base, int first, int pt) {
     constexpr int CG = CIN / 8, CGS = CG / KS, PLN = 2 * CGS;
-    constexpr uint32_t kPlane = (R + 2) * kSW * 16;
+    constexpr uint32_t kPlane = NRW * kSW * 16;
     // each thread owns (pixel column, plane) items and walks the staged rows
     for (int ci = pt; ci < 130 * PLN; ci += NP) {
         const int pl = ci % PLN, sp = ci / PLN;
@@ -202,31 +216,33 @@ __device__ __forceinline__ void copy_slice(const uint16_t* src, int H, int W, in
         const int gx = x0 - 1 + sp;
         const bool okx = gx >= 0 && gx < W;
         const uint32_t dst = a0 + pl * kPlane + 16 * sp;
-#pragma unroll
-        for (int sr = 0; sr < R + 2; ++sr) {
+#pragma unroll 2
+        for (int sr = first; sr < R + 2; ++sr) {
             const int gy = y0 - 1 + sr;
             const bool ok = okx && gy >= 0 && gy < H;
             const uint16_t* p = ok ? src + ((static_cast<size_t>(gy) * W + gx) * 2 * CG + chunk) * 8 : src;
-            cp_async16(dst + 16 * (sr * kSW), p, ok ? 16u : 0u);
+            cp_async16(dst + 16 * (row_slot<NRW>(base, sr) * kSW), p, ok ? 16u : 0u);
         }
     }
 }
 
-// GATHER raw: pos4 / nrm4 of the staged pixels in bounds, 32 bytes per pixel
+// GATHER raw: pos4 / nrm4 of the staged pixels in bounds, [part][staged row][pixel]
 template <int NP, int R>
-__device__ __forceinline__ void prefetch_gbuffer(const TcJob& job, int y0, int x0, uint32_t raw, int pt) {
+__device__ __forceinline__ void prefetch_gbuffer(const TcJob& job, int y0, int x0, uint32_t raw, int first, int pt) {
     const int H = job.H, W = job.W;
-    for (int idx = pt; idx < (R + 2) * 130 * 2; idx += NP) {
+    for (int idx = pt; idx < (R + 2 - first) * 130 * 2; idx += NP) {
         const int part = idx & 1, q = idx >> 1;
-        const int sr = q / 130, sp = q % 130;
+        const int sr = first + q / 130, sp = q % 130;
         const int gy = y0 - 1 + sr, gx = x0 - 1 + sp;
         if (gy >= 0 && gy < H && gx >= 0 && gx < W)
-            cp_async16(raw + 16 * idx, (part ? job.g.nrm4 : job.g.pos4) + static_cast<size_t>(gy) * W + gx, 16);
+            cp_async16(raw + 16 * (part * (R + 2) * 130 + sr * 130 + sp),
+                       (part ? job.g.nrm4 : job.g.pos4) + static_cast<size_t>(gy) * W + gx, 16);
     }
 }
 
 // UP raw: the coarse rows y0/2-1 .. y0/2+R/2 and columns x0/2-1 .. x0/2+64 in
-// bounds, FP32, CIN / 4 chunks of each coarse pixel
+// bounds, FP32, CIN / 4 chunks of each coarse pixel, pixels CIN / 4 + 1 chunks
+// apart (the pad chunk spreads neighbouring pixels over the banks)
 template <int NP, int CIN, int R>
 __device__ __forceinline__ void prefetch_coarse(const TcJob& job, int y0, int x0, uint32_t raw, int pt) {
     constexpr int C2 = CIN / 4, NCR = R / 2 + 2;
@@ -236,18 +252,19 @@ __device__ __forceinline__ void prefetch_coarse(const TcJob& job, int y0, int x0
         const int ch = idx % C2, q = idx / C2;
         const int gy = cy0 + q / kNCC, gx = cx0 + q % kNCC;
         if (gy >= 0 && gy < Hl && gx >= 0 && gx < Wl)
-            cp_async16(raw + 16 * idx, job.in_f + (static_cast<size_t>(gy) * Wl + gx) * CIN + 4 * ch, 16);
+            cp_async16(raw + 16 * (q * (C2 + 1) + ch), job.in_f + (static_cast<size_t>(gy) * Wl + gx) * CIN + 4 * ch, 16);
     }
 }
 
 // GATHER compute: features of the staged pixels from the raw G-buffer, the
 // shadow-map texel fetched per pixel (all of a thread's fetches in flight
 // together), BF16 hi + lo chunks into the input buffer
-template <int NP, int R>
-__device__ __forceinline__ void compute_gather(const TcJob& job, int y0, int x0, uint32_t raw, uint32_t a0, int pt) {
+template <int NP, int R, int NRW>
+__device__ __forceinline__ void compute_gather(const TcJob& job, int y0, int x0, uint32_t raw, uint32_t a0, int base,
+                                               int first, int pt) {
     constexpr int NSP = 131;  // staged pixel 130 is the zero pad read by the dummy tap
-    constexpr int ITEMS = (R + 2) * NSP;
-    constexpr int NPT = (ITEMS + NP - 1) / NP;
+    constexpr int NPT = ((R + 2) * NSP + NP - 1) / NP;
+    const int ITEMS = (R + 2 - first) * NSP;
     const GatherParams g = job.g;  // one copy per tile: the view index is only known at run time
     const int H = job.H, W = job.W;
     float4 P[NPT], Nv[NPT];
@@ -256,14 +273,14 @@ __device__ __forceinline__ void compute_gather(const TcJob& job, int y0, int x0,
 #pragma unroll
     for (int k = 0; k < NPT; ++k) {
         const int idx = pt + NP * k;
-        const int sr = idx / NSP, sp = idx % NSP;
+        const int sr = first + idx / NSP, sp = idx % NSP;
         const int gy = y0 - 1 + sr, gx = x0 - 1 + sp;
         ok[k] = idx < ITEMS && sp < 130 && gy >= 0 && gy < H && gx >= 0 && gx < W;
         z[k] = g.z_far;
         if (ok[k]) {
             const uint32_t q = static_cast<uint32_t>(sr * 130 + sp);
-            P[k] = ld_shared_f4(raw + 32 * q);
-            Nv[k] = ld_shared_f4(raw + 32 * q + 16);
+            P[k] = ld_shared_f4(raw + 16 * q);
+            Nv[k] = ld_shared_f4(raw + 16 * ((R + 2) * 130 + q));
             const int tx = texel_index(g, P[k].x, P[k].y, P[k].z);
             if (tx >= 0) z[k] = __ldg(g.sm + tx);
         }
@@ -272,7 +289,7 @@ __device__ __forceinline__ void compute_gather(const TcJob& job, int y0, int x0,
     for (int k = 0; k < NPT; ++k) {
         const int idx = pt + NP * k;
         if (idx < ITEMS) {
-            const int sr = idx / NSP, sp = idx % NSP;
+            const int sr = first + idx / NSP, sp = idx % NSP;
             uint4 chunk = make_uint4(0, 0, 0, 0);
             if (ok[k]) {
                 float f[4];
@@ -286,7 +303,7 @@ __device__ __forceinline__ void compute_gather(const TcJob& job, int y0, int x0,
                 }
                 chunk = f32_to_chunk(hl);
             }
-            st_shared_v4(a0 + 16 * (sr * kSW + sp), chunk);
+            st_shared_v4(a0 + 16 * (row_slot<NRW>(base, sr) * kSW + sp), chunk);
         }
     }
 }
@@ -316,19 +333,19 @@ __device__ __forceinline__ void pair_to_f32(uint4 hi, uint4 lo, float (&f)[8]) {
 // a coarse row is interpolated horizontally once and kept while the staged
 // rows that need it are produced (two coarse rows live at a time).
 // Column sp, channel group cgl of K slice s, staged rows [sr0, sr0 + NROWS).
-template <int CIN, int R, int KS, bool SKIP, int NROWS>
+template <int CIN, int R, int KS, bool SKIP, int NROWS, int NRW>
 __device__ __forceinline__ void up_column(const TcJob& job, int y0, int x0, uint32_t raw, uint32_t a0, int s, int sp,
-                                          int cgl, int sr0) {
+                                          int cgl, int sr0, int base) {
     constexpr int CG = CIN / 8, CGS = CG / KS, C4 = CIN / 4;
-    constexpr uint32_t kPlane = (R + 2) * kSW * 16;
+    constexpr uint32_t kPlane = NRW * kSW * 16;
     const int H = job.H, W = job.W, Hl = H / 2, Wl = W / 2;
     const int cy0 = y0 / 2 - 1, cx0 = x0 / 2 - 1;
     const int cg = s * CGS + cgl;
     const int gx = x0 - 1 + sp;
     const bool okx = gx >= 0 && gx < W;
     const BilinTap tx = bilin_tap(okx ? gx : 0, Wl);
-    const uint32_t c0 = raw + 16 * ((tx.i0 - cx0) * C4 + 2 * cg);  // coarse column i0, row cy0
-    const uint32_t c1 = raw + 16 * ((tx.i1 - cx0) * C4 + 2 * cg);
+    const uint32_t c0 = raw + 16 * ((tx.i0 - cx0) * (C4 + 1) + 2 * cg);  // coarse column i0, row cy0
+    const uint32_t c1 = raw + 16 * ((tx.i1 - cx0) * (C4 + 1) + 2 * cg);
     const uint32_t dst = a0 + cgl * kPlane + 16 * sp;          // hi plane; lo plane CGS planes on
     // the skip chunks of all rows first (global loads in flight together)
     float4 ska[NROWS], skb[NROWS];
@@ -347,7 +364,7 @@ __device__ __forceinline__ void up_column(const TcJob& job, int y0, int x0, uint
     }
     // horizontal interpolation of coarse row ci
     auto hrow = [&](int ci, float (&h)[8]) {
-        const uint32_t ro = 16 * ((ci - cy0) * kNCC * C4);
+        const uint32_t ro = 16 * ((ci - cy0) * kNCC * (C4 + 1));
         const float4 a0 = ld_shared_f4(c0 + ro), a1 = ld_shared_f4(c0 + ro + 16);
         const float4 b0 = ld_shared_f4(c1 + ro), b1 = ld_shared_f4(c1 + ro + 16);
         const float p0[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
@@ -389,24 +406,31 @@ __device__ __forceinline__ void up_column(const TcJob& job, int y0, int x0, uint
             }
             split_chunks(o, vh, vl);
         }
-        st_shared_v4(dst + 16 * (sr * kSW), vh);
-        st_shared_v4(dst + CGS * kPlane + 16 * (sr * kSW), vl);
+        const uint32_t ro = 16 * (row_slot<NRW>(base, sr) * kSW);
+        st_shared_v4(dst + ro, vh);
+        st_shared_v4(dst + CGS * kPlane + ro, vl);
     }
 }
 
 // K slice s: the 128 interior columns x channel groups walk all staged rows
 // (one item per producer thread per pass); the two halo columns are split
 // into single rows.
-template <int NP, int CIN, int R, int KS, bool SKIP>
+template <int NP, int CIN, int R, int KS, bool SKIP, int NRW>
 __device__ __forceinline__ void compute_up(const TcJob& job, int y0, int x0, uint32_t raw, uint32_t a0, int s,
-                                           int pt) {
+                                           int base, int first, int pt) {
     constexpr int CGS = CIN / 8 / KS;
-    constexpr int MAIN = kTileM * CGS, HALO = 2 * CGS * (R + 2);
-    for (int i = pt; i < MAIN; i += NP)
-        up_column<CIN, R, KS, SKIP, R + 2>(job, y0, x0, raw, a0, s, 1 + i / CGS, i % CGS, 0);
-    for (int i = pt; i < HALO; i += NP) {
-        const int sr = i % (R + 2), q = i / (R + 2);
-        up_column<CIN, R, KS, SKIP, 1>(job, y0, x0, raw, a0, s, (q / CGS) ? 129 : 0, q % CGS, sr);
+    constexpr int MAIN = kTileM * CGS;
+    const int nrows = R + 2 - first;
+    // channel-group-major items: a warp writes 32 consecutive chunks of one plane
+    for (int i = pt; i < MAIN; i += NP) {
+        if (first == 0)
+            up_column<CIN, R, KS, SKIP, R + 2, NRW>(job, y0, x0, raw, a0, s, 1 + i % kTileM, i / kTileM, 0, base);
+        else
+            up_column<CIN, R, KS, SKIP, R, NRW>(job, y0, x0, raw, a0, s, 1 + i % kTileM, i / kTileM, 2, base);
+    }
+    for (int i = pt; i < 2 * CGS * nrows; i += NP) {
+        const int sr = first + i % nrows, q = i / nrows;
+        up_column<CIN, R, KS, SKIP, 1, NRW>(job, y0, x0, raw, a0, s, (q / CGS) ? 129 : 0, q % CGS, sr, base);
     }
 }
 
@@ -465,46 +489,70 @@ __global__ void __launch_bounds__(32 * (NEW + NPW + 1), 1) level_tc_kernel(const
     __syncthreads();
     fence_after_sync();
     const uint32_t tbase = *tslot;
-    const int ntiles = a.tile_start[a.nviews];
+    // this CTA's tiles: a contiguous range of the tile list, which runs
+    // column-major within each view (vertical strips of 128-pixel columns)
+    const long long ntl = a.tile_start[a.nviews];
+    const int t_lo = static_cast<int>(ntl * blockIdx.x / gridDim.x);
+    const int t_hi = static_cast<int>(ntl * (blockIdx.x + 1) / gridDim.x);
+    // view, origin and continuation (the tile right below the CTA's previous one)
+    auto locate = [&](int tile, int& v, int& y0, int& x0, bool& cont) -> const TcJob& {
+        while (tile >= a.tile_start[v + 1]) ++v;
+        const TcJob& job = a.job[v];
+        const int local = tile - a.tile_start[v];
+        const int ys = local % job.tiles_y;
+        y0 = ys * R;
+        x0 = (local / job.tiles_y) * kTileM;
+        cont = C::RING && tile > t_lo && ys > 0;
+        return job;
+    };
+    // ring slots (KS == 1): staged row 0 of a tile sits in slot `base`; the
+    // counter `ring` is the slot after the last staged row produced so far
+    auto ring_next = [&](bool cont, int& ring, int& base, int& first) {
+        if constexpr (C::RING) {
+            first = cont ? 2 : 0;
+            base = cont ? (ring >= 2 ? ring - 2 : ring - 2 + C::NRW) : ring;
+            ring = base + R + 2;
+            if (ring >= C::NRW) ring -= C::NRW;
+        } else {
+            first = 0;
+            base = 0;
+        }
+    };
 
     if (warp >= NEW && warp < MW) {
         // ================= producers: step st = (tile it, K slice s) fills input buffer st % 2
         const int pt = tid - NE;
-        auto locate = [&](int tile, int& v, int& y0, int& x0) -> const TcJob& {
-            while (tile >= a.tile_start[v + 1]) ++v;
-            const TcJob& job = a.job[v];
-            const int local = tile - a.tile_start[v];
-            y0 = (local / job.tiles_x) * R;
-            x0 = (local % job.tiles_x) * kTileM;
-            return job;
-        };
-        int v = 0, vn = 0, it = 0;
+        int v = 0, vn = 0, it = 0, ring = 0;
         if constexpr (PRO != TPRO_PLAIN) {
             // prefetch the first tile's raw inputs into raw buffer 0
-            if (blockIdx.x < ntiles) {
+            if (t_lo < t_hi) {
                 int y0, x0;
-                const TcJob& job = locate(blockIdx.x, vn, y0, x0);
-                if constexpr (PRO == TPRO_GATHER) prefetch_gbuffer<NP, R>(job, y0, x0, sRAW, pt);
+                bool cont;
+                const TcJob& job = locate(t_lo, vn, y0, x0, cont);
+                if constexpr (PRO == TPRO_GATHER) prefetch_gbuffer<NP, R>(job, y0, x0, sRAW, 0, pt);
                 else prefetch_coarse<NP, CIN, R>(job, y0, x0, sRAW, pt);
                 cp_async_arrive(gfull + 0);
             }
         }
         bool failed = false;
-        for (int tile = blockIdx.x; tile < ntiles && !failed; tile += gridDim.x, ++it) {
-            int y0, x0;
-            const TcJob& job = locate(tile, v, y0, x0);
+        for (int tile = t_lo; tile < t_hi && !failed; ++tile, ++it) {
+            int y0, x0, base, first;
+            bool cont;
+            const TcJob& job = locate(tile, v, y0, x0, cont);
+            ring_next(cont, ring, base, first);
             const int rb = it & 1;
             if constexpr (PRO != TPRO_PLAIN) {
                 // prefetch tile it + 1 into the other raw buffer
-                const int next = tile + gridDim.x;
-                if (next < ntiles) {
+                const int next = tile + 1;
+                if (next < t_hi) {
                     const int nb = rb ^ 1;
                     const int un = (it + 1) >> 1;  // use index of raw buffer nb for tile it + 1
                     if (un >= 1 && !wait_phase(rfree + nb, (un - 1) & 1, s_abort)) { failed = true; break; }
                     int ny0, nx0;
-                    const TcJob& nj = locate(next, vn, ny0, nx0);
+                    bool ncont;
+                    const TcJob& nj = locate(next, vn, ny0, nx0, ncont);
                     const uint32_t nraw = sRAW + nb * C::RAW_BYTES;
-                    if constexpr (PRO == TPRO_GATHER) prefetch_gbuffer<NP, R>(nj, ny0, nx0, nraw, pt);
+                    if constexpr (PRO == TPRO_GATHER) prefetch_gbuffer<NP, R>(nj, ny0, nx0, nraw, ncont ? 2 : 0, pt);
                     else prefetch_coarse<NP, CIN, R>(nj, ny0, nx0, nraw, pt);
                     cp_async_arrive(gfull + nb);
                 }
@@ -515,15 +563,18 @@ __global__ void __launch_bounds__(32 * (NEW + NPW + 1), 1) level_tc_kernel(const
 #pragma unroll 1
             for (int s = 0; s < KS; ++s) {
                 const int st = it * KS + s, b = st & 1;
-                const uint32_t A0 = sA0 + b * (C::A0_CHUNKS * 16);
-                // input buffer b is free once the MMAs of step st - 2 are done
+                const uint32_t A0 = C::RING ? sA0 : sA0 + b * (C::A0_CHUNKS * 16);
+                // the rows written now are free once the MMAs of step st - 2 are done
                 if (st >= 2 && !wait_phase(mma3 + b, ((st >> 1) - 1) & 1, s_abort)) { failed = true; break; }
                 if constexpr (PRO == TPRO_PLAIN) {
-                    copy_slice<NP, CIN, R, KS>(job.in, job.H, job.W, y0, x0, A0, s, pt);
+                    copy_slice<NP, CIN, R, KS, C::NRW>(job.in, job.H, job.W, y0, x0, A0, s, base, first, pt);
                     cp_async_arrive(full + b);
                 } else {
-                    if constexpr (PRO == TPRO_GATHER) compute_gather<NP, R>(job, y0, x0, raw, A0, pt);
-                    else compute_up<NP, CIN, R, KS, PRO == TPRO_UP_SKIP>(job, y0, x0, raw, A0, s, pt);
+                    if constexpr (PRO == TPRO_GATHER)
+                        compute_gather<NP, R, C::NRW>(job, y0, x0, raw, A0, base, first, pt);
+                    else
+                        compute_up<NP, CIN, R, KS, PRO == TPRO_UP_SKIP, C::NRW>(job, y0, x0, raw, A0, s, base, first,
+                                                                                pt);
                     fence_proxy_async_smem();
                     mbar_arrive(full + b);
                 }
@@ -540,11 +591,15 @@ __global__ void __launch_bounds__(32 * (NEW + NPW + 1), 1) level_tc_kernel(const
         if ((tid & 31) == 0) {
             constexpr uint32_t id3 = idesc_bf16(128, C::N3);
             constexpr uint32_t id1 = idesc_bf16(128, C::N1);
-            constexpr uint32_t kPlane = (R + 2) * kSW * 16;
+            constexpr uint32_t kPlane = C::PLANE;
             constexpr int kA1Part = (CMID / 8) * kTileM;
-            int it = 0;
+            int it = 0, v = 0, ring = 0;
             bool failed = false;
-            for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
+            for (int tile = t_lo; tile < t_hi; ++tile, ++it) {
+                int y0, x0, rbase, first;
+                bool cont;
+                locate(tile, v, y0, x0, cont);
+                ring_next(cont, ring, rbase, first);
                 const int tb = it & 1;
                 const uint32_t D = tbase + tb * C::TMEM_BUF;
 #pragma unroll 1
@@ -557,7 +612,7 @@ __global__ void __launch_bounds__(32 * (NEW + NPW + 1), 1) level_tc_kernel(const
                     }
                     fence_proxy_async_smem();  // cp.async / st.shared data -> tensor core
                     fence_after_sync();
-                    const uint32_t A0 = sA0 + b * (C::A0_CHUNKS * 16);
+                    const uint32_t A0 = C::RING ? sA0 : sA0 + b * (C::A0_CHUNKS * 16);
                     if constexpr (C::STACK) {
                         // clear the R x N3 accumulator columns (zero A operand), then
                         // one MMA per (staged row j, K step) of width (#ky) x N3:
@@ -575,13 +630,13 @@ __global__ void __launch_bounds__(32 * (NEW + NPW + 1), 1) level_tc_kernel(const
                             const uint32_t d = D + (R - 1 - j + ka) * C::N3;
                             if constexpr (C::SPLIT) {
                                 // K = staged pixels m + 2p, m + 2p + 1 (4 features hi | lo each)
-                                const uint64_t adesc = smem_desc(A0 + 16 * (j * kSW), 16, 128);
+                                const uint64_t adesc = smem_desc(A0 + 16 * (row_slot<C::NRW>(rbase, j) * kSW), 16, 128);
 #pragma unroll
                                 for (int p2 = 0; p2 < 2; ++p2)
                                     mma_bf16(d, adesc + 2 * p2, bdesc + ((2 * p2 * 3 + ka) * C::N3), id, 1);
                             } else {
                                 // K step = planes (2q, 2q + 1) of one part; both parts use the same weights
-                                const uint64_t adesc = smem_desc(A0 + 16 * (j * kSW), kPlane, 128);
+                                const uint64_t adesc = smem_desc(A0 + 16 * (row_slot<C::NRW>(rbase, j) * kSW), kPlane, 128);
 #pragma unroll
                                 for (int kx = 0; kx < 3; ++kx)
 #pragma unroll
@@ -604,7 +659,7 @@ __global__ void __launch_bounds__(32 * (NEW + NPW + 1), 1) level_tc_kernel(const
 #pragma unroll
                                     for (int part = 0; part < 2; ++part) {
                                         const uint32_t a0 = A0 + (part * C::CGS + 2 * q) * kPlane +
-                                                            16 * ((r + tap / 3) * kSW + tap % 3);
+                                                            16 * (row_slot<C::NRW>(rbase, r + tap / 3) * kSW + tap % 3);
                                         const uint32_t b0 = sB3 + 16 * ((tap * C::CG_IN + s * C::CGS + 2 * q) * C::N3);
                                         mma_bf16(d, smem_desc(a0, kPlane, 128), smem_desc(b0, C::N3 * 16, 128), id3,
                                                  (s | tap | q | part) != 0);
@@ -650,14 +705,12 @@ __global__ void __launch_bounds__(32 * (NEW + NPW + 1), 1) level_tc_kernel(const
         const uint32_t tlane = tbase + (static_cast<uint32_t>((warp & 3) * 32) << 16);
         constexpr int kA1Part = (CMID / 8) * kTileM;
         int v = 0, it = 0;
-        for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
+        for (int tile = t_lo; tile < t_hi; ++tile, ++it) {
             const int tb = it & 1;
-            while (tile >= a.tile_start[v + 1]) ++v;
-            const TcJob& job = a.job[v];
+            int y0, x0;
+            bool cont;
+            const TcJob& job = locate(tile, v, y0, x0, cont);
             const int H = job.H, W = job.W;
-            const int local = tile - a.tile_start[v];
-            const int y0 = (local / job.tiles_x) * R;
-            const int x0 = (local % job.tiles_x) * kTileM;
             const uint32_t Dl = tlane + tb * C::TMEM_BUF;
             if (!wait_phase(accf + tb, (it >> 1) & 1, s_abort)) {
                 atomicExch(a.err, 1);
@@ -893,20 +946,20 @@ int tc_default_variant(int stage) {
 }
 
 // Fill the tile table of a stage for the given tile height.
-static void fill_tiles(TcBatch& b, int rows) {
+void tc_fill_tiles(TcBatch& b, int rows) {
     b.tile_start[0] = 0;
     for (int i = 0; i < b.nviews; ++i) {
         TcJob& j = b.job[i];
         j.tiles_x = (j.W + kTileM - 1) / kTileM;
-        const int ty = (j.H + rows - 1) / rows;
-        b.tile_start[i + 1] = b.tile_start[i] + j.tiles_x * ty;
+        j.tiles_y = (j.H + rows - 1) / rows;
+        b.tile_start[i + 1] = b.tile_start[i] + j.tiles_x * j.tiles_y;
     }
 }
 
 cudaError_t tc_launch_stage(int stage, int variant, TcBatch& b, int ctas_per_sm, cudaStream_t stream) {
     if (stage < 0 || stage >= kTcStages || variant < 0 || variant >= kStages[stage].n) return cudaErrorInvalidValue;
     const Variant& v = kStages[stage].v[variant];
-    fill_tiles(b, v.R);
+    tc_fill_tiles(b, v.R);
     return v.fn(b, ctas_per_sm, stream);
 }
 

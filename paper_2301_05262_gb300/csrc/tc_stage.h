@@ -19,7 +19,7 @@ enum TcEpi { TEPI_POOL = 0, TEPI_SKIP_POOL = 1, TEPI_STORE = 2, TEPI_HEAD = 3 };
 struct TcJob {
     GatherParams g;             // GATHER prologue: the view's G-buffer, map, emitter, camera
     int H, W;                   // the stage's resolution for this view
-    int tiles_x;                // tiles per row (filled at launch)
+    int tiles_x, tiles_y;       // tiles per row / column (filled at launch); tiles run column-major
     // activations read by the tensor cores straight from memory (PLAIN inputs)
     // are BF16 hi + lo pairs, [pixel][part][C] (part 0 = hi, 1 = lo); those
     // the up-sampling producers read are FP32 [pixel][C] (same 4 bytes per channel)
@@ -56,5 +56,6 @@ int tc_stage_occupancy(int stage, int variant);
 void tc_make_batches(const GatherParams* g, const Activations* act, float* const* vis, int n, const float* params,
                      const uint16_t* img, int* err, TcBatch* out);
 cudaError_t tc_launch_stage(int stage, int variant, TcBatch& b, int ctas_per_sm, cudaStream_t stream);
+void tc_fill_tiles(TcBatch& b, int rows);  // tile counts of every view for tile height rows
 
 }  // namespace nsm
