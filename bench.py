@@ -84,7 +84,7 @@ class ClockSampler:
             os.close(fd)
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=self.fh, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
@@ -206,6 +206,173 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------ our arm
+# ------------------------------------------------------------------ side measurements (one GPU)
+def _events(torch, n):
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(n)]
+    for e in ev:  # torch creates the CUDA event on its first record
+        e.record()
+    torch.cuda.synchronize()
+    return ev
+
+
+def extra_features(nsm, scenegen, torch, device, peaks, reps):
+    """A1-A4 alone (nsm_features with the blocker search) on the 1080p soft frame."""
+    f = scenegen.soft_frame(H, W, HS, WS, N_OBJ, SCENE_SEED + 10)
+    light = nsm.LightDesc(pos=tuple(f.light_pos), radius=f.light_radius, r_hat=f.r_hat, view_proj=f.view_proj,
+                          z_far=f.z_far, bias=f.bias, tan_half_fov=f.tan_half_fov)
+    pos4, nrm4, sm = (torch.from_numpy(x).to(device) for x in (f.pos4, f.nrm4, f.sm))
+    fr = nsm.make_frame(pos4, nrm4, sm, light, f.cam_pos)
+    feat = torch.empty((4, H, W), dtype=torch.float32, device=device)
+    blk = torch.empty((3, H, W), dtype=torch.float32, device=device)
+    hard = torch.empty(((H * W + 31) // 32,), dtype=torch.int32, device=device)
+    flush = torch.empty(256 * 2 ** 20, dtype=torch.uint8, device=device)
+    out = {}
+    for name, b in (("gather", None), ("gather_blocker", blk)):
+        for _ in range(3):
+            nsm.nsm_features(fr, feat, None, hard, b)
+        ev = _events(torch, 2 * reps)
+        for k in range(reps):
+            flush.zero_()
+            ev[2 * k].record()
+            nsm.nsm_features(fr, feat, None, hard, b)
+            ev[2 * k + 1].record()
+        torch.cuda.synchronize()
+        ms = sum(ev[2 * k].elapsed_time(ev[2 * k + 1]) for k in range(reps)) / reps
+        # algorithmic bytes: G-buffer 32 B/px + one 4 B texel/px + features 16 B/px + hard bits 1/8 B/px
+        # (+ blocker 12 B/px written; window texels are L2 / L1 traffic)
+        nbytes = H * W * (32 + 4 + 16 + 0.125 + (12 if b is not None else 0))
+        gbs = nbytes / (ms * 1e-3) / 1e9
+        out[name] = {"ms": ms, "mpix_s": H * W / (ms * 1e-3) / 1e6, "algorithmic_bytes": nbytes,
+                     "achieved_gbs": gbs, "frac_of_measured_hbm": gbs / peaks["hbm_gbs"]}
+    out["workload"] = "1920x1080 soft frame (spherical emitter), 2048^2 map; blocker window half-size <= 32 texels"
+    return out
+
+
+def extra_serving(nsm, scenegen, torch, device, theta, reps):
+    """32 views of uneven size in one batched, graph-replayed pass (BF16)."""
+    res = [(540, 960), (720, 1280), (1080, 1920), (1440, 2560), (2160, 3840)]
+    sms = [1024, 2048, 4096]
+    rng = scenegen.SplitMix64(51)
+    ctx = nsm.Context()
+    w = nsm.Weights(ctx, theta)
+    frames, outs, keep = [], [], []
+    cache = {}
+    for i in range(32):
+        h = rng.next_u64()
+        (hh, ww), s = res[h % 5], sms[(h >> 8) % 3]
+        soft = bool(i & 1)
+        key = (hh, s, soft)
+        if key not in cache:  # one rendered scene per (size, map, light kind) class
+            f = (scenegen.soft_frame if soft else scenegen.hard_frame)(hh, ww, s, s, N_OBJ, 500 + len(cache))
+            light = nsm.LightDesc(pos=tuple(f.light_pos), radius=f.light_radius, r_hat=f.r_hat,
+                                  view_proj=f.view_proj, z_far=f.z_far, bias=f.bias, tan_half_fov=f.tan_half_fov)
+            t = tuple(torch.from_numpy(x).to(device) for x in (f.pos4, f.nrm4, f.sm))
+            cache[key] = (nsm.make_frame(t[0], t[1], t[2], light, f.cam_pos), t)
+        fr, t = cache[key]
+        keep.append(t)
+        frames.append(fr)
+        outs.append(torch.empty((hh, ww), dtype=torch.float32, device=device))
+    views = nsm.make_views(frames, outs)
+    ws = torch.empty((nsm.nsm_infer_batched_workspace_bytes(views),), dtype=torch.uint8, device=device)
+    nsm.nsm_autotune(ctx, views, w, ws, reps=3)
+    nsm.nsm_ctx_set_graph(ctx, True)
+    for _ in range(3):
+        nsm.nsm_infer_batched(ctx, views, w, ws)
+    ev = _events(torch, 2 * reps)
+    for k in range(reps):
+        ev[2 * k].record()
+        nsm.nsm_infer_batched(ctx, views, w, ws)
+        ev[2 * k + 1].record()
+    torch.cuda.synchronize()
+    ctx.check()
+    lat = sorted(ev[2 * k].elapsed_time(ev[2 * k + 1]) for k in range(reps))
+    mpix = sum(o.numel() for o in outs) / 1e6
+    ms = statistics.mean(lat)
+    return {"views": 32, "mpix_per_batch": mpix, "ms_per_batch": ms, "mpix_s": mpix / (ms * 1e-3),
+            "batch_latency_ms_p50": lat[len(lat) // 2], "batch_latency_ms_p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
+            "per_view_latency": "every view of a batch completes with the batch's last kernel: per-view latency = batch latency",
+            "graph_replays": nsm.nsm_ctx_graph_replays(ctx), "reps": reps,
+            "workload": "32 views, sizes from {540p,720p,1080p,1440p,2160p} x maps {1024^2,2048^2,4096^2} by a seeded hash (seed 51), odd views soft"}
+
+
+def extra_train(nsm, scenegen, torch, device, theta, reps):
+    """One nsm_train_step on B=16 x T=3 soft 256^2 instances (hand-written backward, Adam)."""
+    B, T, S = 16, 3, 256
+    rng = scenegen.SplitMix64(4242)
+    frames = [[None] * B for _ in range(T)]
+    targets = []
+    for b in range(B):
+        base = scenegen.random_scene(4000 + b, 8, soft=True)
+        frames[0][b] = scenegen.render_frame(base, S, S, 512, 512)
+        for t in range(1, T):
+            frames[t][b] = scenegen.render_frame(scenegen.perturbed(base, rng), S, S, 512, 512)
+        targets.append(scenegen.soft_visibility(frames[0][b], spp_side=8))
+    st = lambda key: torch.from_numpy(np.stack([[getattr(frames[t][b], key) for b in range(B)] for t in range(T)])).to(device)
+    pos, nrm, sm = st("pos4"), st("nrm4"), st("sm")
+    tgt = torch.from_numpy(np.stack(targets).astype(np.float32)).to(device)
+    lights, cams = [], []
+    for t in range(T):
+        for b in range(B):
+            f = frames[t][b]
+            lights.append(nsm.LightDesc(pos=tuple(f.light_pos), radius=f.light_radius, r_hat=f.r_hat,
+                                        view_proj=f.view_proj, z_far=f.z_far, bias=f.bias, tan_half_fov=f.tan_half_fov))
+            cams.append(f.cam_pos)
+    batch = nsm.make_batch(pos, nrm, sm, lights, cams, tgt, B, T)
+    ctx = nsm.Context()
+    state = nsm.TrainState(ctx, theta, B, T, S, S)
+    loss = torch.zeros((1,), dtype=torch.float32, device=device)
+    for _ in range(3):
+        state.step(batch, loss_out=loss)
+    ev = _events(torch, 2 * reps)
+    for k in range(reps):
+        ev[2 * k].record()
+        state.step(batch, loss_out=loss)
+        ev[2 * k + 1].record()
+    torch.cuda.synchronize()
+    ctx.check()
+    ms = sum(ev[2 * k].elapsed_time(ev[2 * k + 1]) for k in range(reps)) / reps
+    return {"ms_per_step": ms, "instances_per_s": B * T / (ms * 1e-3), "loss_last": float(loss.item()),
+            "workload": "B=16 x T=3 soft 256^2 instances (seeded scenes + 2 perturbations each), 64-sample MC targets",
+            "precision": "FP32 CUDA cores (forward checkpoints per level, recomputation in the backward, Adam)"}
+
+
+def extra_soft_frame(nsm, scenegen, torch, device, theta, weights, ctx, reps, with_error):
+    """The 1080p soft-shadow frame in both forms, with the error against the FP64 oracle."""
+    f = scenegen.soft_frame(H, W, HS, WS, N_OBJ, SCENE_SEED + 10)
+    light = nsm.LightDesc(pos=tuple(f.light_pos), radius=f.light_radius, r_hat=f.r_hat, view_proj=f.view_proj,
+                          z_far=f.z_far, bias=f.bias, tan_half_fov=f.tan_half_fov)
+    t = tuple(torch.from_numpy(x).to(device) for x in (f.pos4, f.nrm4, f.sm))
+    fr = nsm.make_frame(t[0], t[1], t[2], light, f.cam_pos)
+    flush = torch.empty(256 * 2 ** 20, dtype=torch.uint8, device=device)
+    out = {"workload": f"1920x1080 soft frame, emitter radius {f.light_radius:.3f}, 2048^2 map"}
+    vis = {}
+    for pname in ("bf16", "fp32"):
+        prec = nsm.PRECISIONS[pname]
+        ws = torch.empty((nsm.nsm_infer_workspace_bytes(H, W, prec),), dtype=torch.uint8, device=device)
+        v = torch.empty((H, W), dtype=torch.float32, device=device)
+        for _ in range(3):
+            nsm.nsm_infer(ctx, fr, weights, prec, ws, v)
+        ev = _events(torch, 2 * reps)
+        for k in range(reps):
+            flush.zero_()
+            ev[2 * k].record()
+            nsm.nsm_infer(ctx, fr, weights, prec, ws, v)
+            ev[2 * k + 1].record()
+        torch.cuda.synchronize()
+        ms = sum(ev[2 * k].elapsed_time(ev[2 * k + 1]) for k in range(reps)) / reps
+        out[pname] = {"ms_per_frame": ms, "mpix_s": H * W / (ms * 1e-3) / 1e6}
+        vis[pname] = v.cpu().numpy().astype(np.float64)
+    if with_error:
+        from oracle import gather as G
+        from oracle import network as N
+        feat, _, _ = G.features(f.pos4, f.nrm4, f.sm, f.view_proj, f.light_pos, f.cam_pos, f.r_hat, f.z_far, f.bias)
+        ref = N.forward(feat, theta.astype(np.float64))
+        for pname in ("bf16", "fp32"):
+            e = np.abs(vis[pname] - ref)
+            out[pname]["error_vs_fp64_oracle"] = {"max_abs": float(e.max()), "mse": float(np.mean(e ** 2))}
+    return out
+
+
 def run_ours(args):
     import torch
     world, rank, local = dist_env()
@@ -342,6 +509,22 @@ def run_ours(args):
         cpu = {"value": px / secs / 1e6, "unit": "Mpix/s", "cores": cpu_threads(), "kind": "oracle",
                "sample": f"540x{W} rows of the frame: binary32 texel lookup + FP64 features + FP64 network forward ({secs:.1f} s)"}
 
+    # side measurements of the other hot-path rows (one GPU only): A1-A4 alone, the
+    # 1080p soft frame with its error, batched serving, one training step
+    extras = None
+    if world == 1 and not args.skip_extras:
+        extras = {}
+        for name, fn in (("features", lambda: extra_features(nsm, scenegen, torch, device, peaks, 10)),
+                         ("soft_1080p", lambda: extra_soft_frame(nsm, scenegen, torch, device, theta, weights, ctx, 10,
+                                                                 not args.skip_error)),
+                         ("serving_32_views", lambda: extra_serving(nsm, scenegen, torch, device, theta, 20)),
+                         ("train_step", lambda: extra_train(nsm, scenegen, torch, device, theta, 10))):
+            try:
+                extras[name] = fn()
+            except Exception as exc:  # reported, never hidden
+                extras[name] = {"error": f"{type(exc).__name__}: {exc}"}
+            torch.cuda.empty_cache()
+
     if rank != 0:
         if world > 1:
             import torch.distributed as dist
@@ -383,7 +566,7 @@ def run_ours(args):
             "error_vs_fp64_oracle": errs,
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": hf["launches_per_step"] * args.steps,
-            "clocks": hf["clocks"]}
+            "clocks": hf["clocks"], "extras": extras}
     print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
@@ -394,7 +577,7 @@ def run_ours(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=2000, help="timed steps (2000 BF16 frames take about 1 s, long enough for clock samples)")
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precisions", default="bf16,fp32", help="comma list; the first is the headline form")
@@ -402,6 +585,8 @@ def main():
     ap.add_argument("--skip-error", action="store_true")
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--skip-extras", action="store_true", help="skip the side measurements (features, soft frame, "
+                    "batched serving, training step)")
     ap.add_argument("--size", default=None, help="WxH view size (profiling runs); default 1920x1080")
     args = ap.parse_args()
     if args.size:
