@@ -38,8 +38,11 @@ MACS = {"enc0": 4 * 16 * 9 + 16 * 16, "enc1": 16 * 32 * 9 + 32 * 32, "bott": 32 
 
 
 def kernel_algorithmic(name: str, precision: str):
-    """(flops, bytes) per launch of one inference kernel at the bench size."""
-    eb = 4 if precision == "fp32" else 2
+    """(flops, bytes) per launch of one inference kernel at the bench size:
+    algorithmic MACs x 2 and the bytes of its inputs and outputs (activations
+    4 B/channel in the FP32 form and the compensated BF16 form -- FP32 or a
+    BF16 hi + lo pair -- and 1 B/channel in the FP8 form)."""
+    eb = {"fp32": 4, "bf16": 4, "fp8": 1}[precision]
     n0, n1, n2 = H * W, (H // 2) * (W // 2), (H // 4) * (W // 4)
     sm_bytes = min(n0, HS * WS) * 4
     if "enc0" in name:
@@ -580,7 +583,7 @@ def main():
     ap.add_argument("--steps", type=int, default=2000, help="timed steps (2000 BF16 frames take about 1 s, long enough for clock samples)")
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precisions", default="bf16,fp32", help="comma list; the first is the headline form")
+    ap.add_argument("--precisions", default="bf16,fp32,fp8", help="comma list; the first is the headline form")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-error", action="store_true")
     ap.add_argument("--skip-e2e", action="store_true")

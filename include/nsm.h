@@ -163,7 +163,15 @@ nsm_status nsm_features(const nsm_frame* frame, float* feat_out, int32_t* texel_
 size_t nsm_infer_workspace_bytes(int H, int W, nsm_precision precision);
 
 /* Per-pixel visibility in [0, 1] for one view: the gather fused into the
- * first level, then the network (Sec. 3.5).
+ * first level, then the network (Sec. 3.5).  Forms:
+ *   NSM_FP32  CUDA cores, FP32 throughout.
+ *   NSM_BF16  tcgen05 tensor cores, every operand a BF16 hi + lo pair (weights,
+ *             features, activations), FP32 accumulation: ~2^-16 relative
+ *             storage error.
+ *   NSM_FP8   tcgen05 tensor cores, E4M3 operands: weights with one scale per
+ *             output channel, activations and features with unit scale
+ *             (saturating at +-448), FP32 accumulation.
+ * The texel index and the depth test are FP32 (bit-exact) in every form.
  *   vis_out   [H][W] float32 (device).
  *   workspace device, >= nsm_infer_workspace_bytes(H, W, precision) bytes,
  *             256-byte aligned, not shared with a concurrent call.

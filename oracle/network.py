@@ -298,6 +298,53 @@ def round_bf16_pair(x):
     return hi + lo
 
 
+def e4m3_values():
+    """All finite non-negative values of the FP8 E4M3 format (1 sign bit, 4
+    exponent bits with bias 7, 3 mantissa bits; exponent field 0 encodes the
+    subnormals m/8 * 2^-6; the all-ones exponent with mantissa 7 is NaN, so
+    the largest finite value is 1.75 * 2^8 = 448; there are no infinities),
+    enumerated from the bit fields: 127 values, ascending."""
+    vals = []
+    for e in range(16):
+        for m in range(8):
+            if e == 15 and m == 7:
+                continue
+            vals.append((m / 8.0) * 2.0 ** -6 if e == 0 else (1.0 + m / 8.0) * 2.0 ** (e - 7))
+    return np.array(sorted(vals))
+
+
+_E4M3 = None
+
+
+def round_e4m3(x):
+    """Round to the nearest E4M3 value, ties to the even mantissa, saturating
+    at +-448 (the conversion an FP8 tensor-core form applies to values it
+    stores).  Inputs are first rounded to binary32; returned as float64."""
+    global _E4M3
+    if _E4M3 is None:
+        _E4M3 = e4m3_values()
+    v = _E4M3
+    a = np.abs(np.asarray(x, np.float32).astype(np.float64))
+    a = np.minimum(a, v[-1])
+    hi = np.clip(np.searchsorted(v, a, side="left"), 1, v.size - 1)
+    lo_v, hi_v = v[hi - 1], v[hi]
+    dl, dh = a - lo_v, hi_v - a
+    # ties: the neighbour whose mantissa field is even (index parity follows the
+    # mantissa field, since each binade holds 8 consecutive codes)
+    pick_hi = (dh < dl) | ((dh == dl) & (hi % 2 == 0))
+    q = np.where(a == hi_v, hi_v, np.where(pick_hi, hi_v, lo_v))
+    return np.sign(np.asarray(x, np.float64)) * q
+
+
+def round_e4m3_per_out_channel(W):
+    """E4M3 weights with one scale per output channel (axis 0): s_o =
+    max|W[o]| / 448 (1 for an all-zero channel), W ~ e4m3(W / s_o) * s_o."""
+    W = np.asarray(W, np.float64)
+    s = np.abs(W).reshape(W.shape[0], -1).max(axis=1) / 448.0
+    s = np.where(s > 0, s, 1.0).reshape((-1,) + (1,) * (W.ndim - 1))
+    return round_e4m3(W / s) * s
+
+
 def forward_rounded(feat, theta, rnd, rnd_in=None, rnd_w=None, rnd_mid=None, levels: int = 3):
     """`forward` with values rounded wherever a reduced-precision form stores
     them: every convolution weight by `rnd_w` (not biases or the head), the

@@ -31,6 +31,8 @@ struct nsm_weights {
     uint16_t* d_bf16;  // packed BF16 images (tensor-core form)
     void* d_descs;     // packing table
     int ndesc;
+    uint8_t* d_fp8;        // E4M3 images (FP8 form)
+    float* d_fp8_scales;   // their per-output-channel scales
 };
 
 void ctx_release_graph(nsm_ctx* c);

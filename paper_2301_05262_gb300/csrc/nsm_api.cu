@@ -220,6 +220,7 @@ int nsm_infer_kernel_count(nsm_precision precision) {
     switch (precision) {
         case NSM_FP32: return kInferKernelsFp32;
         case NSM_BF16: return kInferKernelsBf16;
+        case NSM_FP8: return kInferKernelsFp8;
         default: return 0;
     }
 }
@@ -229,6 +230,7 @@ const char* nsm_infer_kernel_name(nsm_precision precision, int i) {
     switch (precision) {
         case NSM_FP32: return kInferKernelNamesFp32[i];
         case NSM_BF16: return kInferKernelNamesBf16[i];
+        case NSM_FP8: return kInferKernelNamesFp8[i];
         default: return "";
     }
 }
@@ -253,9 +255,14 @@ nsm_status nsm_weights_create(nsm_ctx* ctx, const float* host_params, size_t n, 
     if (e == cudaSuccess) e = cudaMalloc(&w->d_descs, pack_desc_bytes() * im.n);
     if (e == cudaSuccess) e = cudaMemcpy(w->d_descs, im.desc, pack_desc_bytes() * im.n, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = launch_pack_bf16(w->d_params, w->d_bf16, w->d_descs, w->ndesc, nullptr);
+    const F8Images f8 = fp8_images();
+    if (e == cudaSuccess) e = cudaMalloc(&w->d_fp8, f8.img_bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&w->d_fp8_scales, f8.scales * sizeof(float));
+    if (e == cudaSuccess) e = launch_pack_fp8(w->d_params, w->d_fp8, w->d_fp8_scales, nullptr);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
-        cudaFree(w->d_params); cudaFree(w->d_bf16); cudaFree(w->d_descs); delete w;
+        cudaFree(w->d_params); cudaFree(w->d_bf16); cudaFree(w->d_descs); cudaFree(w->d_fp8);
+        cudaFree(w->d_fp8_scales); delete w;
         return cuda_fail(e, "pack weights");
     }
     *out = w;
@@ -271,6 +278,7 @@ nsm_status nsm_weights_load_device(nsm_weights* w, const float* dev_params, size
                                     static_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) return cuda_fail(e, "copy weights");
     e = launch_pack_bf16(w->d_params, w->d_bf16, w->d_descs, w->ndesc, static_cast<cudaStream_t>(stream));
+    if (e == cudaSuccess) e = launch_pack_fp8(w->d_params, w->d_fp8, w->d_fp8_scales, static_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) return cuda_fail(e, "pack weights");
     return NSM_OK;
 }
@@ -280,6 +288,8 @@ void nsm_weights_destroy(nsm_weights* w) {
     cudaFree(w->d_params);
     cudaFree(w->d_bf16);
     cudaFree(w->d_descs);
+    cudaFree(w->d_fp8);
+    cudaFree(w->d_fp8_scales);
     delete w;
 }
 
@@ -323,7 +333,6 @@ nsm_status nsm_infer(nsm_ctx* ctx, const nsm_frame* frame, const nsm_weights* w,
     if (!workspace || workspace_bytes < need)
         return fail(NSM_ERR_WORKSPACE, "workspace of %zu bytes given, %zu needed", workspace_bytes, need);
     if ((s = check_dev_ptr(workspace, "workspace", 256)) != NSM_OK) return s;
-    if (precision == NSM_FP8) return fail(NSM_ERR_UNSUPPORTED, "precision %d not built yet", static_cast<int>(precision));
     Activations act{};
     activations_bytes(frame->H, frame->W, 4, &act, workspace);
     GatherParams g = make_gather(frame);
@@ -336,10 +345,15 @@ nsm_status nsm_infer(nsm_ctx* ctx, const nsm_frame* frame, const nsm_weights* w,
         se.n = static_cast<int>(ctx->stage_events.size());
         se.stream = static_cast<cudaStream_t>(stream);
     }
-    cudaError_t e = (precision == NSM_FP32)
-        ? launch_infer_fp32(g, w->d_params, act, vis_out, static_cast<cudaStream_t>(stream), se)
-        : launch_infer_bf16(g, w->d_params, w->d_bf16, act, vis_out, ctx->d_err, static_cast<cudaStream_t>(stream), se,
-                            ctx->tc_variant, ctx->tc_ctas);
+    cudaError_t e;
+    if (precision == NSM_FP32)
+        e = launch_infer_fp32(g, w->d_params, act, vis_out, static_cast<cudaStream_t>(stream), se);
+    else if (precision == NSM_BF16)
+        e = launch_infer_bf16(g, w->d_params, w->d_bf16, act, vis_out, ctx->d_err, static_cast<cudaStream_t>(stream), se,
+                              ctx->tc_variant, ctx->tc_ctas);
+    else
+        e = launch_infer_fp8(g, w->d_params, w->d_fp8, w->d_fp8_scales, act, vis_out, ctx->d_err,
+                             static_cast<cudaStream_t>(stream), se);
     if (e != cudaSuccess) return cuda_fail(e, "inference kernel launch");
     return NSM_OK;
 }

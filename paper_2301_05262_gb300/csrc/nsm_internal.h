@@ -83,6 +83,22 @@ size_t pack_desc_bytes();
 cudaError_t launch_pack_bf16(const float* params, uint16_t* img, const void* dev_descs, int ndesc,
                              cudaStream_t stream);
 
+// E4M3 weight images + per-output-channel scales of the FP8 form (pack_fp8.cu).
+struct F8Images {
+    size_t img_off[NUM_LAYERS];    // byte offset of each layer's image (head has none)
+    size_t scale_off[NUM_LAYERS];  // offset of each layer's scales (one per output channel)
+    size_t img_bytes;
+    size_t scales;
+};
+F8Images fp8_images();
+cudaError_t launch_pack_fp8(const float* params, uint8_t* img, float* scales, cudaStream_t stream);
+
+constexpr int kInferKernelsFp8 = 5;
+extern const char* const kInferKernelNamesFp8[kInferKernelsFp8];
+cudaError_t launch_infer_fp8(const GatherParams& g, const float* params, const uint8_t* img, const float* scales,
+                             const Activations& act, float* vis, int* err, cudaStream_t stream,
+                             const StageEvents& se);
+
 constexpr int kInferKernelsBf16 = 5;
 extern const char* const kInferKernelNamesBf16[kInferKernelsBf16];
 cudaError_t launch_infer_bf16(const GatherParams& g, const float* params, const uint16_t* img,

@@ -29,6 +29,11 @@ struct TcJob {
     uint16_t* out;              // POOL / SKIP_POOL: pooled [H/2][W/2][2][COUT]
     float* out_f;               // STORE: [H][W][COUT]
     float* out_skip;            // SKIP_POOL: [H][W][COUT]
+    // FP8 form: every activation E4M3 [pixel][C], 1 byte per channel
+    const uint8_t* in8;         // PLAIN: [H][W][CIN]; UP*: [H/2][W/2][CIN]
+    const uint8_t* skip8;       // UP_SKIP: [H][W][CIN]
+    uint8_t* out8;              // POOL / SKIP_POOL: pooled [H/2][W/2][COUT]; STORE: [H][W][COUT]
+    uint8_t* out_skip8;         // SKIP_POOL: [H][W][COUT]
     float* vis;                 // HEAD: [H][W]
 };
 
@@ -42,6 +47,8 @@ struct TcBatch {
     const float* bias3;
     const float* bias1;
     const float* head;          // head weights [16] then its bias
+    const float* scale3;        // FP8 form: per-output-channel weight scales of the 3x3
+    const float* scale1;        // and of the 1x1
     int* err;                   // device error word
 };
 

@@ -123,3 +123,36 @@ def test_infer_host_entry_point_matches_device_call(ctx, precision):
     out = np.empty((f.H, f.W), np.float32)
     nsm.nsm_infer_host(ctx, hf, w, precision, stage, ws, out)
     np.testing.assert_array_equal(out, dev)
+
+
+def _fp8_model(feat, theta):
+    """The oracle forward rounded as the FP8 form stores values: E4M3 features,
+    3x3 -> 1x1 intermediates and level outputs (unit scale), E4M3 weights with
+    one scale per output channel."""
+    return N.forward_rounded(feat, theta.astype(np.float64), N.round_e4m3, rnd_in=N.round_e4m3,
+                             rnd_w=N.round_e4m3_per_out_channel, rnd_mid=N.round_e4m3)
+
+
+@pytest.mark.parametrize("case", ["hard256", "soft256", "ragged"])
+def test_infer_fp8_follows_its_rounding_model(ctx, case):
+    """FP8 form against the oracle with the same E4M3 storage points: what is
+    left is FP32 accumulation order, which can move a stored value to the
+    neighbouring E4M3 value (1/16 relative steps), so the bound is on the MSE
+    with a looser max.  Against FP64 this form misses the 1e-2 / 1e-4 bar
+    with He-init weights (~0.15 max-abs, ~4e-4 MSE; reported by bench.py);
+    the test only checks it stays in that regime."""
+    f = {"hard256": lambda: scenegen.hard_frame(256, 256, 512, 512, 8, 1),
+         "soft256": lambda: scenegen.soft_frame(256, 256, 512, 512, 8, 21),
+         "ragged": lambda: scenegen.soft_frame(68, 132, 300, 200, 8, 5)}[case]()
+    theta = _theta(3)
+    vis = _run(ctx, f, theta, nsm.NSM_FP8)
+    feat = _features(f)
+    q = _fp8_model(feat, theta)
+    ref = N.forward(feat, theta.astype(np.float64))
+    qerr = np.abs(vis - q)
+    err = np.abs(vis - ref)
+    print(f"fp8 {case}: vs model max {qerr.max():.3e} mse {np.mean(qerr ** 2):.3e}; "
+          f"vs fp64 max {err.max():.3e} mse {np.mean(err ** 2):.3e}")
+    assert float(np.mean(qerr ** 2)) <= 1e-6, float(np.mean(qerr ** 2))
+    assert qerr.max() <= 0.1, qerr.max()
+    assert float(np.mean(err ** 2)) <= 5e-3

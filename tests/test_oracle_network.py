@@ -261,3 +261,56 @@ def test_forward_rounded_identity_and_sensitivity():
     v = N.forward_rounded(x, th, N.round_bf16)
     d = np.abs(v - N.forward(x, th))
     assert 0 < d.max() < 0.05
+
+
+# ------------------------------------------------------------------ E4M3 (FP8 form)
+def _e4m3_decode(byte):
+    """Value of an E4M3 byte from its bit fields (OCP 8-bit floating point,
+    E4M3: bias 7, no infinities, S.1111.111 is NaN)."""
+    s, e, m = (byte >> 7) & 1, (byte >> 3) & 0xF, byte & 7
+    if e == 15 and m == 7:
+        return float("nan")
+    v = (m / 8.0) * 2.0 ** -6 if e == 0 else (1 + m / 8.0) * 2.0 ** (e - 7)
+    return -v if s else v
+
+
+def test_e4m3_value_set_matches_the_bit_fields():
+    v = N.e4m3_values()
+    assert v.size == 127 and v[0] == 0.0 and v[-1] == 448.0
+    dec = sorted({_e4m3_decode(b) for b in range(128) if b != 0x7F})
+    np.testing.assert_array_equal(v, np.array(dec))
+    # a few codes of the format's table
+    assert _e4m3_decode(0x38) == 1.0 and _e4m3_decode(0x7E) == 448.0 and _e4m3_decode(0x01) == 2.0 ** -9
+    assert _e4m3_decode(0x08) == 2.0 ** -6 and _e4m3_decode(0xB8) == -1.0
+
+
+def test_round_e4m3_is_nearest_with_ties_to_even_and_saturates():
+    v = N.e4m3_values()
+    full = np.concatenate([-v[::-1], v[1:]])
+    rng = np.random.default_rng(8)
+    x = np.concatenate([rng.normal(0, 10, 4000), rng.uniform(-2 ** -5, 2 ** -5, 2000), [500.0, -1e6, 448.0]])
+    x = x.astype(np.float32).astype(np.float64)
+    q = N.round_e4m3(x)
+    xs = np.clip(x, -448.0, 448.0)
+    # brute force: q is one of the nearest representable values
+    d = np.abs(xs[:, None] - full[None, :])
+    assert np.all(np.abs(xs - q) <= d.min(axis=1))
+    # exact midpoints go to the even mantissa field
+    for lo_i in range(1, v.size - 1):
+        mid = 0.5 * (v[lo_i] + v[lo_i + 1])
+        even = v[lo_i] if lo_i % 2 == 0 else v[lo_i + 1]
+        if np.float32(mid) == mid:
+            assert N.round_e4m3(np.array([mid]))[0] == even
+    assert N.round_e4m3(np.array([1e9]))[0] == 448.0
+
+
+def test_round_e4m3_per_out_channel_keeps_each_row_maximum():
+    rng = np.random.default_rng(9)
+    W = rng.normal(0, 0.3, (8, 5, 3, 3))
+    Q = N.round_e4m3_per_out_channel(W)
+    for o in range(8):
+        i = np.argmax(np.abs(W[o]))
+        assert abs(Q[o].flat[i] - W[o].flat[i]) <= 1e-12 * abs(W[o].flat[i])
+        s = np.abs(W[o]).max() / 448.0
+        big = np.abs(W[o]) >= 2 ** -6 * s  # normal range: relative error <= 2^-4
+        assert np.all(np.abs(Q[o] - W[o])[big] <= 2 ** -4 * np.abs(W[o])[big] + 1e-15)
