@@ -67,9 +67,22 @@ def test_features_1080p_full_size():
 
 
 def test_features_1080p_blocker_sampled_rows():
+    # full 16-row tile bands of the blocker kernel (staged windows), top and bottom edges
     f = scenegen.soft_frame(1080, 1920, 2048, 2048, 64, 21)
-    rows = np.s_[500:504, :]
-    _check_frame(f, blocker=True, sample=rows)
+    for rows in (np.s_[496:512, :], np.s_[1064:1080, :], np.s_[0:2, :]):
+        _check_frame(f, blocker=True, sample=rows)
+
+
+def test_features_hard_blocker_point_light_windows():
+    # point light: k = 0, one-texel windows (the direct-scan branch)
+    f = scenegen.hard_frame(128, 160, 256, 256, 8, 3)
+    _check_frame(f, blocker=True)
+
+
+def test_features_blocker_wide_texel_spacing():
+    # few pixels over a large map: tile boxes exceed the staging capacity (global-memory scan)
+    f = scenegen.soft_frame(48, 64, 2048, 2048, 16, 22)
+    _check_frame(f, blocker=True)
 
 
 def test_features_empty_frame():
