@@ -116,7 +116,7 @@ struct TcCfg {
     static constexpr int OFF_ZERO = ((OFF_HEAD + (COUT + 1) * 4) + 127) / 128 * 128;  // zero A operand
     static constexpr int ZERO_BYTES = STACK ? kTileM * 16 + 128 : 0;
     static constexpr int OFF_BAR = OFF_ZERO + ZERO_BYTES;
-    static constexpr int BYTES_USED = OFF_BAR + 128;
+    static constexpr int BYTES_USED = OFF_BAR + 144;
     static constexpr int TMEM_BUF = R * N3;                         // columns of one accumulator buffer
     static constexpr int TMEM_COLS_RAW = 2 * TMEM_BUF;
     static constexpr int TMEM_COLS = TMEM_COLS_RAW < 32 ? 32 : TMEM_COLS_RAW;
@@ -373,6 +373,33 @@ __device__ __forceinline__ void compute_up(const TcJob& job, int y0, int x0, uin
     }
 }
 
+// Coalesced FP32 row output of the epilogue: each lane (pixel) puts its C values
+// into a per-warp shared-memory staging area ([pixel][16-byte chunk], chunks
+// XOR-swizzled by the pixel so a warp's writes and reads spread over the
+// banks), then the warp writes its 32 pixels' contiguous 32 * C * 4 bytes with
+// 16-byte stores (512 contiguous bytes per instruction).
+template <int C>
+__device__ __forceinline__ void stage_put(uint32_t stg, int lane, int c0, const float* v16) {
+    constexpr int Q = C / 4;  // chunks per pixel
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int q = c0 / 4 + j;
+        st_shared_v4(stg + 16 * (lane * Q + (q ^ (lane & (Q - 1)))),
+                     make_uint4(__float_as_uint(v16[4 * j]), __float_as_uint(v16[4 * j + 1]),
+                                __float_as_uint(v16[4 * j + 2]), __float_as_uint(v16[4 * j + 3])));
+    }
+}
+template <int C>
+__device__ __forceinline__ void stage_flush(uint32_t stg, int lane, float* gdst, int npix) {
+    constexpr int Q = C / 4;
+    uint4* g = reinterpret_cast<uint4*>(gdst);
+#pragma unroll
+    for (int t = 0; t < Q; ++t) {
+        const int j = lane + 32 * t, px = j / Q, q = j % Q;
+        if (px < npix) g[j] = ld_shared_v4(stg + 16 * (px * Q + (q ^ (px & (Q - 1)))));
+    }
+}
+
 template <int CIN, int CMID, int COUT, int R, int PRO, int EPI, int NEW, int NPW, int KS>
 __global__ void __launch_bounds__(32 * (NEW + NPW + 1), 1) level_tc_kernel(const __grid_constant__ TcBatch a) {
     using C = TcCfg<CIN, CMID, COUT, R, PRO, KS>;
@@ -394,8 +421,9 @@ __global__ void __launch_bounds__(32 * (NEW + NPW + 1), 1) level_tc_kernel(const
     uint64_t* gfull = bar + 8;     // [2] per raw buffer
     uint64_t* rfree = bar + 10;    // [2] per raw buffer
     uint64_t* accf = bar + 12;     // [2] per accumulator buffer
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + C::OFF_BAR + 112);
-    volatile int* s_abort = reinterpret_cast<volatile int*>(smem + C::OFF_BAR + 116);
+    uint64_t* sfree = bar + 14;    // epilogue -> epilogue: output staging (in the 1x1 operand) done
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + C::OFF_BAR + 128);
+    volatile int* s_abort = reinterpret_cast<volatile int*>(smem + C::OFF_BAR + 132);
 
     const int tid = threadIdx.x;
     const int warp = tid >> 5;
@@ -419,6 +447,7 @@ __global__ void __launch_bounds__(32 * (NEW + NPW + 1), 1) level_tc_kernel(const
         }
         mbar_init(a1full, NE);
         mbar_init(mma1, 1);
+        mbar_init(sfree, NE);
         fence_mbar_init();
         *s_abort = 0;
     }
@@ -643,6 +672,13 @@ __global__ void __launch_bounds__(32 * (NEW + NPW + 1), 1) level_tc_kernel(const
         const int rg = G == 1 ? 0 : warp >> 2;         // row group of this warp
         const uint32_t tlane = tbase + (static_cast<uint32_t>((warp & 3) * 32) << 16);
         constexpr int kA1Part = (CMID / 8) * kTileM;
+        // FP32 rows go out through a per-warp staging area in the 1x1 operand
+        // buffer (free between the 1x1 MMAs and the next tile's 3x3 result) when
+        // it has room for every epilogue warp
+        constexpr int kStg = 32 * COUT * 4;                              // one row of a warp
+        constexpr int kRows = EPI == TEPI_SKIP_POOL ? 2 : 1;            // rows staged at once
+        constexpr bool kStage = (EPI == TEPI_STORE || EPI == TEPI_SKIP_POOL) &&
+                                NEW * kRows * kStg <= C::A1_CHUNKS * 16;
         int v = 0, it = 0;
         for (int tile = t_lo; tile < t_hi; ++tile, ++it) {
             const int tb = it & 1;
@@ -657,6 +693,14 @@ __global__ void __launch_bounds__(32 * (NEW + NPW + 1), 1) level_tc_kernel(const
                 break;
             }
             fence_after_sync();
+            if constexpr (kStage) {
+                // every epilogue warp has flushed the previous tile's staged rows
+                if (it >= 1 && !wait_phase(sfree, (it - 1) & 1, s_abort)) {
+                    atomicExch(a.err, 6);
+                    *s_abort = 1;
+                    break;
+                }
+            }
             // ---- 3x3 result: bias + ReLU -> BF16 hi + lo -> operand of the 1x1
             for (int r = rg; r < R; r += G) {
 #pragma unroll
@@ -692,6 +736,10 @@ __global__ void __launch_bounds__(32 * (NEW + NPW + 1), 1) level_tc_kernel(const
             fence_after_sync();
             // ---- 1x1 result -> outputs (pooled: BF16 hi + lo [pixel][part][COUT]; else FP32)
             const int ox = x0 + m;
+            const int lane = tid & 31;
+            const uint32_t stg = sA1 + warp * (kRows * kStg);
+            const int px0 = x0 + 32 * (warp & 3);
+            const int npix = min(32, W - px0);
             if constexpr (EPI == TEPI_POOL || EPI == TEPI_SKIP_POOL) {
                 for (int r = 2 * rg; r < R; r += 2 * G) {
                     float s[COUT];
@@ -711,7 +759,10 @@ __global__ void __launch_bounds__(32 * (NEW + NPW + 1), 1) level_tc_kernel(const
                         }
                         if constexpr (EPI == TEPI_SKIP_POOL) {
                             const int oy = y0 + r;
-                            if (oy < H && ox < W) {
+                            if constexpr (kStage) {
+                                stage_put<COUT>(stg, lane, c0, v0);
+                                stage_put<COUT>(stg + kStg, lane, c0, v1);
+                            } else if (oy < H && ox < W) {
                                 float4* dst = reinterpret_cast<float4*>(job.out_skip +
                                                                         (static_cast<size_t>(oy) * W + ox) * COUT + c0);
                                 float4* dst1 = dst + static_cast<size_t>(W) * (COUT / 4);
@@ -722,6 +773,16 @@ __global__ void __launch_bounds__(32 * (NEW + NPW + 1), 1) level_tc_kernel(const
                                 }
                             }
                         }
+                    }
+                    if constexpr (EPI == TEPI_SKIP_POOL && kStage) {
+                        __syncwarp();
+                        const int oy = y0 + r;
+                        if (oy < H && npix > 0) {
+                            float* g0 = job.out_skip + (static_cast<size_t>(oy) * W + px0) * COUT;
+                            stage_flush<COUT>(stg, lane, g0, npix);
+                            stage_flush<COUT>(stg + kStg, lane, g0 + static_cast<size_t>(W) * COUT, npix);
+                        }
+                        __syncwarp();
                     }
 #pragma unroll
                     for (int c = 0; c < COUT; ++c) s[c] = 0.25f * (s[c] + __shfl_xor_sync(0xffffffffu, s[c], 1));
@@ -752,7 +813,9 @@ __global__ void __launch_bounds__(32 * (NEW + NPW + 1), 1) level_tc_kernel(const
 #pragma unroll
                         for (int j = 0; j < 16; ++j) val[j] = fmaxf(val[j] + lo[j] + bias1_s[c0 + j], 0.f);
                         if constexpr (EPI == TEPI_STORE) {
-                            if (oy < H && ox < W) {
+                            if constexpr (kStage) {
+                                stage_put<COUT>(stg, lane, c0, val);
+                            } else if (oy < H && ox < W) {
                                 float4* dst = reinterpret_cast<float4*>(job.out_f +
                                                                         (static_cast<size_t>(oy) * W + ox) * COUT + c0);
 #pragma unroll
@@ -766,8 +829,16 @@ __global__ void __launch_bounds__(32 * (NEW + NPW + 1), 1) level_tc_kernel(const
                     }
                     if (EPI == TEPI_HEAD && oy < H && ox < W)
                         job.vis[static_cast<size_t>(oy) * W + ox] = sigmoidf_acc(hsum + head_s[COUT]);
+                    if constexpr (EPI == TEPI_STORE && kStage) {
+                        __syncwarp();
+                        if (oy < H && npix > 0)
+                            stage_flush<COUT>(stg, lane, job.out_f + (static_cast<size_t>(oy) * W + px0) * COUT, npix);
+                        __syncwarp();
+                    }
                 }
             }
+            // the next tile's 3x3 result goes where the rows were staged
+            if constexpr (kStage) mbar_arrive(sfree);
             fence_before_sync();
             mbar_arrive(tfree + tb);
         }
