@@ -376,6 +376,55 @@ def extra_soft_frame(nsm, scenegen, torch, device, theta, weights, ctx, reps, wi
     return out
 
 
+def oracle_band(frame, theta64, y0: int, y1: int, margin: int = 32):
+    """FP64 oracle visibility of rows [y0, y1) (y0, y1 multiples of 4), computed
+    on the rows [y0 - margin, y1 + margin) clipped to the frame: the network's
+    receptive field is about 20 level-0 pixels, so rows at least `margin` away
+    from a band edge equal the full-frame forward."""
+    from oracle import gather as G
+    from oracle import network as N
+    a, b = max(0, y0 - margin), min(frame.H, y1 + margin)
+    sub = slice(a, b)
+    feat, _, _ = G.features(frame.pos4[sub], frame.nrm4[sub], frame.sm, frame.view_proj, frame.light_pos,
+                            frame.cam_pos, frame.r_hat, frame.z_far, frame.bias)
+    return N.forward(feat, theta64)[y0 - a:y1 - a]
+
+
+def extra_sequence(nsm, scenegen, torch, device, theta, weights, ctx, with_error):
+    """The soft temporal sequence (8 frames: the emitter orbits 2 degrees per
+    frame, 4 objects move 0.01 per frame) at 1080p, BF16 and FP8 forms: per-frame
+    time and error against the FP64 oracle on a band of rows."""
+    frames = scenegen.temporal_sequence(H, W, HS, WS, N_OBJ, SCENE_SEED + 10)
+    y0, y1 = 520, 560
+    out = {"workload": "8-frame soft sequence, 1920x1080, 2048^2 map; errors on rows 520-559 of every frame "
+                       "(oracle on rows 488-591: the receptive field is ~20 pixels)", "frames": []}
+    theta64 = theta.astype(np.float64)
+    for f in frames:
+        light = nsm.LightDesc(pos=tuple(f.light_pos), radius=f.light_radius, r_hat=f.r_hat, view_proj=f.view_proj,
+                              z_far=f.z_far, bias=f.bias, tan_half_fov=f.tan_half_fov)
+        t = tuple(torch.from_numpy(x).to(device) for x in (f.pos4, f.nrm4, f.sm))
+        fr = nsm.make_frame(t[0], t[1], t[2], light, f.cam_pos)
+        ref = oracle_band(f, theta64, y0, y1) if with_error else None
+        rec = {}
+        for pname in ("bf16", "fp8"):
+            prec = nsm.PRECISIONS[pname]
+            ws = torch.empty((nsm.nsm_infer_workspace_bytes(H, W, prec),), dtype=torch.uint8, device=device)
+            v = torch.empty((H, W), dtype=torch.float32, device=device)
+            nsm.nsm_infer(ctx, fr, weights, prec, ws, v)
+            ev = _events(torch, 2)
+            ev[0].record()
+            nsm.nsm_infer(ctx, fr, weights, prec, ws, v)
+            ev[1].record()
+            torch.cuda.synchronize()
+            r = {"ms": ev[0].elapsed_time(ev[1])}
+            if ref is not None:
+                e = np.abs(v[y0:y1].cpu().numpy().astype(np.float64) - ref)
+                r.update({"max_abs": float(e.max()), "mse": float(np.mean(e ** 2))})
+            rec[pname] = r
+        out["frames"].append(rec)
+    return out
+
+
 def run_ours(args):
     import torch
     world, rank, local = dist_env()
@@ -520,6 +569,8 @@ def run_ours(args):
         for name, fn in (("features", lambda: extra_features(nsm, scenegen, torch, device, peaks, 10)),
                          ("soft_1080p", lambda: extra_soft_frame(nsm, scenegen, torch, device, theta, weights, ctx, 10,
                                                                  not args.skip_error)),
+                         ("soft_sequence_1080p", lambda: extra_sequence(nsm, scenegen, torch, device, theta, weights,
+                                                                         ctx, not args.skip_error)),
                          ("serving_32_views", lambda: extra_serving(nsm, scenegen, torch, device, theta, 20)),
                          ("train_step", lambda: extra_train(nsm, scenegen, torch, device, theta, 10))):
             try:

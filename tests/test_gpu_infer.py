@@ -156,3 +156,20 @@ def test_infer_fp8_follows_its_rounding_model(ctx, case):
     assert float(np.mean(qerr ** 2)) <= 1e-6, float(np.mean(qerr ** 2))
     assert qerr.max() <= 0.1, qerr.max()
     assert float(np.mean(err ** 2)) <= 5e-3
+
+
+def test_infer_soft_temporal_sequence_per_frame(ctx):
+    """The soft temporal sequence (emitter orbiting 2 degrees / frame, 4 objects
+    moving 0.01 / frame), 8 frames at 256^2: every frame's BF16 output within
+    1e-2 max-abs / 1e-4 MSE of the FP64 forward, the FP8 output on its rounding
+    model."""
+    theta = _theta(3)
+    for f in scenegen.temporal_sequence(256, 256, 512, 512, 12, 21):
+        feat = _features(f)
+        ref = N.forward(feat, theta.astype(np.float64))
+        vb = _run(ctx, f, theta, nsm.NSM_BF16)
+        e = np.abs(vb - ref)
+        assert e.max() <= 1e-2 and float(np.mean(e ** 2)) <= 1e-4, (e.max(), float(np.mean(e ** 2)))
+        v8 = _run(ctx, f, theta, nsm.NSM_FP8)
+        assert float(np.mean((v8 - _fp8_model(feat, theta)) ** 2)) <= 1e-6
+

@@ -314,3 +314,21 @@ def test_round_e4m3_per_out_channel_keeps_each_row_maximum():
         s = np.abs(W[o]).max() / 448.0
         big = np.abs(W[o]) >= 2 ** -6 * s  # normal range: relative error <= 2^-4
         assert np.all(np.abs(Q[o] - W[o])[big] <= 2 ** -4 * np.abs(W[o])[big] + 1e-15)
+
+
+def test_band_forward_equals_the_full_frame():
+    """bench.py measures errors on a band of rows with the oracle run on the
+    band plus a 32-row margin: the receptive field of the 3-level net is about
+    20 pixels, so the band rows equal the full-frame forward exactly."""
+    import os
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import bench
+    import scenegen
+    from oracle import gather as G
+    f = scenegen.soft_frame(192, 160, 256, 256, 10, 23)
+    th = scenegen.he_init_weights(4, N.layer_table(3)).astype(np.float64)
+    feat, _, _ = G.features(f.pos4, f.nrm4, f.sm, f.view_proj, f.light_pos, f.cam_pos, f.r_hat, f.z_far, f.bias)
+    full = N.forward(feat, th)
+    for y0, y1 in ((0, 40), (76, 100), (148, 192)):
+        np.testing.assert_array_equal(bench.oracle_band(f, th, y0, y1), full[y0:y1])
