@@ -58,6 +58,26 @@ def kernel_algorithmic(name: str, precision: str):
     raise KeyError(name)
 
 
+def measured_traffic(kernel: str):
+    """DRAM bytes per launch of a stage kernel from the committed ncu summary,
+    if it was captured from the current kernel sources (else None)."""
+    import hashlib
+    src = os.path.join(ROOT, "paper_2301_05262_gb300", "csrc")
+    h = hashlib.sha256()
+    for f in ("net_bf16.cu", "tc_pipeline.cuh", "tc_common.cuh", "tc_stage.h"):
+        with open(os.path.join(src, f), "rb") as fh:
+            h.update(fh.read())
+    digest = h.hexdigest()[:16]
+    path = os.path.join(ROOT, "profiles", "roofline_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    for line in open(path):
+        parts = line.split()
+        if len(parts) == 3 and not line.startswith("#") and parts[0] == kernel and parts[1] == digest:
+            return int(parts[2])
+    return None
+
+
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -605,7 +625,7 @@ def run_ours(args):
         else:
             roof = {"bound": "hbm", "achieved": nbytes / dur_s / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s"}
     roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["traffic"] = None
+    roof["traffic"] = measured_traffic(kern)
     roof["kernel"] = kern
     roof["peak_src"] = peaks["src"] if roof["bound"] != "alu" else "derived: SMs x 128 FP32 lanes x 2 FLOP x max SM clock"
     roof["algorithmic"] = {"flops": flops, "bytes": nbytes}
