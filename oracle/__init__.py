@@ -31,4 +31,9 @@ itself; the tests under tests/test_oracle_*.py):
       is unpinned beyond the operator level.
   loss_l1 / adam_update / train_step -- closed forms on small vectors and
       finite differences of the loss.
+  space_to_depth / s2d_output / forward_s2d (Sec. 3.5, the space-to-depth
+      topology) -- the index map by brute force, the detail placement and
+      channel-0 bilinear by explicit loops, the whole network against a
+      direct-summation loop implementation on 8 x 8 inputs, and the head-bias
+      closed form.
 """

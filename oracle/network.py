@@ -379,6 +379,80 @@ def forward_rounded(feat, theta, rnd, rnd_in=None, rnd_w=None, rnd_mid=None, lev
     return sigmoid(conv2d(h, *Wr["head"])[0])
 
 
+# ------------------------------------------------------------------ space-to-depth topology (Sec. 3.5)
+# The paper's final first-layer optimisation: the level-0 convolutions are
+# removed; a 2x2 square of full-resolution pixels is flattened into channels,
+# so the 4 input features become 16 channels at half resolution and feed the
+# second level directly; on the decoder side 4 output channels are rearranged
+# into the 2x2 square, the first one bilinearly upscaled to full resolution
+# and the other three added to it as the details.
+# Readings (the text fixes neither): input channel order 4 * (2 a + b) + c for
+# feature c of the pixel at offset (a, b) = (row, column) in the square; the
+# three detail channels go to offsets (0, 1), (1, 0), (1, 1) (none to (0, 0));
+# the sigmoid is applied to the recombined sum; the decoder's 1x1 output
+# (16 channels) feeds a 1x1 head with 4 outputs.
+
+
+def layer_table_s2d(levels: int = 3, base: int = 16):
+    """The level-0 layers of `layer_table` removed and the head widened to 4
+    outputs: the level-1 encoder takes the 16 space-to-depth channels."""
+    t = [(n, ci, co, k) for (n, ci, co, k) in layer_table(levels, base) if not n.startswith(("enc0", "dec0"))]
+    return [(n, ci, 4 if n == "head" else co, k) for (n, ci, co, k) in t]
+
+
+def unpack_s2d(theta: np.ndarray, levels: int = 3):
+    theta = np.asarray(theta, np.float64)
+    out, off = {}, 0
+    for (name, ci, co, k) in layer_table_s2d(levels):
+        n = co * ci * k * k
+        out[name] = (theta[off:off + n].reshape(co, ci, k, k), theta[off + n:off + n + co])
+        off += n + co
+    if off != theta.size:
+        raise ValueError(f"weight vector has {theta.size} entries, expected {off}")
+    return out
+
+
+def space_to_depth(x: np.ndarray) -> np.ndarray:
+    """(C, H, W) -> (4C, H/2, W/2): out[4 * (2a + b) + c, i, j] = x[c, 2i + a, 2j + b]."""
+    C, H, W = x.shape
+    y = np.empty((4 * C, H // 2, W // 2), x.dtype)
+    for a in range(2):
+        for b in range(2):
+            y[C * (2 * a + b):C * (2 * a + b + 1)] = x[:, a::2, b::2]
+    return y
+
+
+def s2d_output(o: np.ndarray) -> np.ndarray:
+    """(4, H/2, W/2) head outputs -> (H, W) pre-sigmoid values: the bilinear x2
+    of channel 0 plus channels 1, 2, 3 at square offsets (0, 1), (1, 0), (1, 1)."""
+    up = upsample2(o[0:1])[0]
+    up[0::2, 1::2] += o[1]
+    up[1::2, 0::2] += o[2]
+    up[1::2, 1::2] += o[3]
+    return up
+
+
+def forward_s2d(feat: np.ndarray, theta: np.ndarray, levels: int = 3):
+    """Visibility of the space-to-depth network: the levels 1 .. L-1 of
+    `forward` on space_to_depth(features), then the 4-channel head and the
+    2x2 recombination (Sec. 3.5)."""
+    P = unpack_s2d(theta, levels)
+    h = space_to_depth(np.asarray(feat, np.float64))
+    skips = {}
+
+    def pair(x, l3, l1):
+        return relu(conv2d(relu(conv2d(x, *P[l3])), *P[l1]))
+
+    for l in range(1, levels - 1):
+        h1 = pair(h, f"enc{l}_3x3", f"enc{l}_1x1")
+        skips[l] = h1
+        h = avgpool2(h1)
+    h = pair(h, "bott_3x3", "bott_1x1")
+    for l in range(levels - 2, 0, -1):
+        h = pair(upsample2(h) + skips[l], f"dec{l}_3x3", f"dec{l}_1x1")
+    return sigmoid(s2d_output(conv2d(h, *P["head"])))
+
+
 # ------------------------------------------------------------------ loss (Eq. 2)
 
 

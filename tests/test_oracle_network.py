@@ -332,3 +332,113 @@ def test_band_forward_equals_the_full_frame():
     full = N.forward(feat, th)
     for y0, y1 in ((0, 40), (76, 100), (148, 192)):
         np.testing.assert_array_equal(bench.oracle_band(f, th, y0, y1), full[y0:y1])
+
+
+# ------------------------------------------------------------------ space-to-depth topology
+def _naive_conv(x, W, b):
+    co, ci, k, _ = W.shape
+    p = (k - 1) // 2
+    C, H, Wd = x.shape
+    y = np.zeros((co, H, Wd))
+    for o in range(co):
+        for i in range(H):
+            for j in range(Wd):
+                acc = b[o]
+                for c in range(ci):
+                    for u in range(k):
+                        for v in range(k):
+                            ii, jj = i + u - p, j + v - p
+                            if 0 <= ii < H and 0 <= jj < Wd:
+                                acc += W[o, c, u, v] * x[c, ii, jj]
+                y[o, i, j] = acc
+    return y
+
+
+def _naive_up(x):
+    # bilinear x2, half-pixel centres, edge clamp: source coordinate o / 2 - 1/4
+    C, H, W = x.shape
+    y = np.zeros((C, 2 * H, 2 * W))
+    for c in range(C):
+        for i in range(2 * H):
+            for j in range(2 * W):
+                sy, sx = i / 2 - 0.25, j / 2 - 0.25
+                y0, x0 = int(np.floor(sy)), int(np.floor(sx))
+                fy, fx = sy - y0, sx - x0
+                cl = lambda v, n: min(max(v, 0), n - 1)
+                a = x[c, cl(y0, H), cl(x0, W)] * (1 - fx) + x[c, cl(y0, H), cl(x0 + 1, W)] * fx
+                b = x[c, cl(y0 + 1, H), cl(x0, W)] * (1 - fx) + x[c, cl(y0 + 1, H), cl(x0 + 1, W)] * fx
+                y[c, i, j] = a * (1 - fy) + b * fy
+    return y
+
+
+def test_space_to_depth_index_map_and_inverse():
+    rng = np.random.default_rng(31)
+    x = rng.normal(size=(4, 6, 8))
+    y = N.space_to_depth(x)
+    assert y.shape == (16, 3, 4)
+    for c in range(4):
+        for i in range(6):
+            for j in range(8):
+                assert y[4 * (2 * (i % 2) + (j % 2)) + c, i // 2, j // 2] == x[c, i, j]
+
+
+def test_s2d_output_places_details_and_upsamples_channel0():
+    rng = np.random.default_rng(32)
+    o = rng.normal(size=(4, 3, 5))
+    z = o.copy()
+    z[0] = 0
+    d = N.s2d_output(z)
+    assert np.all(d[0::2, 0::2] == 0)
+    np.testing.assert_array_equal(d[0::2, 1::2], o[1])
+    np.testing.assert_array_equal(d[1::2, 0::2], o[2])
+    np.testing.assert_array_equal(d[1::2, 1::2], o[3])
+    z = np.zeros_like(o)
+    z[0] = o[0]
+    np.testing.assert_allclose(N.s2d_output(z), _naive_up(o[0:1])[0], rtol=0, atol=1e-14)
+
+
+def test_forward_s2d_matches_direct_summation_network():
+    """forward_s2d against a network written out with direct-summation
+    convolutions, explicit bilinear weights and loops (8 x 8 input)."""
+    rng = np.random.default_rng(33)
+    t = N.layer_table_s2d(3)
+    n = sum(ci * co * k * k + co for (_, ci, co, k) in t)
+    theta = rng.normal(0, 0.2, n)
+    feat = rng.normal(0, 1, (4, 8, 8))
+    P = N.unpack_s2d(theta)
+    relu = lambda v: np.maximum(v, 0)
+    x = np.zeros((16, 4, 4))
+    for a in range(2):
+        for b in range(2):
+            for c in range(4):
+                x[4 * (2 * a + b) + c] = feat[c, a::2, b::2]
+    s1 = relu(_naive_conv(relu(_naive_conv(x, *P["enc1_3x3"])), *P["enc1_1x1"]))
+    p1 = 0.25 * (s1[:, 0::2, 0::2] + s1[:, 0::2, 1::2] + s1[:, 1::2, 0::2] + s1[:, 1::2, 1::2])
+    bo = relu(_naive_conv(relu(_naive_conv(p1, *P["bott_3x3"])), *P["bott_1x1"]))
+    d1 = relu(_naive_conv(relu(_naive_conv(_naive_up(bo) + s1, *P["dec1_3x3"])), *P["dec1_1x1"]))
+    o = _naive_conv(d1, *P["head"])
+    pre = _naive_up(o[0:1])[0]
+    for i in range(8):
+        for j in range(8):
+            a, b = i % 2, j % 2
+            if (a, b) != (0, 0):
+                pre[i, j] += o[2 * a + b, i // 2, j // 2]
+    ref = 1 / (1 + np.exp(-pre))
+    np.testing.assert_allclose(N.forward_s2d(feat, theta), ref, rtol=0, atol=1e-12)
+
+
+def test_forward_s2d_head_bias_closed_form():
+    """Zero weights everywhere but the head biases: every output is the
+    sigmoid of b0 plus the detail bias of its square offset."""
+    t = N.layer_table_s2d(3)
+    n = sum(ci * co * k * k + co for (_, ci, co, k) in t)
+    theta = np.zeros(n)
+    bias = np.array([0.3, -0.7, 1.1, 0.2])
+    theta[-4:] = bias
+    v = N.forward_s2d(np.ones((4, 12, 16)), theta)
+    sig = lambda z: 1 / (1 + np.exp(-z))
+    np.testing.assert_allclose(v[0::2, 0::2], sig(bias[0]), atol=1e-15)
+    np.testing.assert_allclose(v[0::2, 1::2], sig(bias[0] + bias[1]), atol=1e-15)
+    np.testing.assert_allclose(v[1::2, 0::2], sig(bias[0] + bias[2]), atol=1e-15)
+    np.testing.assert_allclose(v[1::2, 1::2], sig(bias[0] + bias[3]), atol=1e-15)
+    assert sum(ci * co * k * k for (_, ci, co, k) in t) == 35904  # 39,248 - level 0 - old head + 16x4 head
