@@ -410,6 +410,46 @@ def oracle_band(frame, theta64, y0: int, y1: int, margin: int = 32):
     return N.forward(feat, theta64)[y0 - a:y1 - a]
 
 
+def extra_s2d(nsm, scenegen, torch, device, ctx, reps, with_error):
+    """The space-to-depth topology (Sec. 3.5: level-0 convolutions removed) on the
+    1080p soft frame, BF16 form, seeded He-init weights of that topology; error
+    against the FP64 oracle on a band of rows."""
+    from oracle import network as N
+    f = scenegen.soft_frame(H, W, HS, WS, N_OBJ, SCENE_SEED + 10)
+    theta = scenegen.he_init_weights(WEIGHT_SEED, N.layer_table_s2d(3)).astype(np.float32)
+    w = nsm.Weights(ctx, theta, nsm.NSM_TOPO_S2D)
+    light = nsm.LightDesc(pos=tuple(f.light_pos), radius=f.light_radius, r_hat=f.r_hat, view_proj=f.view_proj,
+                          z_far=f.z_far, bias=f.bias, tan_half_fov=f.tan_half_fov)
+    t = tuple(torch.from_numpy(x).to(device) for x in (f.pos4, f.nrm4, f.sm))
+    fr = nsm.make_frame(t[0], t[1], t[2], light, f.cam_pos)
+    prec = nsm.NSM_BF16
+    ws = torch.empty((nsm.nsm_infer_workspace_bytes(H, W, prec),), dtype=torch.uint8, device=device)
+    v = torch.empty((H, W), dtype=torch.float32, device=device)
+    flush = torch.empty(256 * 2 ** 20, dtype=torch.uint8, device=device)
+    for _ in range(3):
+        nsm.nsm_infer(ctx, fr, w, prec, ws, v)
+    ev = _events(torch, 2 * reps)
+    for k in range(reps):
+        flush.zero_()
+        ev[2 * k].record()
+        nsm.nsm_infer(ctx, fr, w, prec, ws, v)
+        ev[2 * k + 1].record()
+    torch.cuda.synchronize()
+    ms = sum(ev[2 * k].elapsed_time(ev[2 * k + 1]) for k in range(reps)) / reps
+    out = {"workload": "1920x1080 soft frame, 2048^2 map, space-to-depth topology (36,116 parameters)",
+           "bf16": {"ms_per_frame": ms, "mpix_s": H * W / (ms * 1e-3) / 1e6}}
+    if with_error:
+        from oracle import gather as G
+        y0, y1, m = 520, 560, 32
+        sub = slice(y0 - m, y1 + m)
+        feat, _, _ = G.features(f.pos4[sub], f.nrm4[sub], f.sm, f.view_proj, f.light_pos, f.cam_pos, f.r_hat,
+                                f.z_far, f.bias)
+        ref = N.forward_s2d(feat, theta.astype(np.float64))[m:m + (y1 - y0)]
+        e = np.abs(v[y0:y1].cpu().numpy().astype(np.float64) - ref)
+        out["bf16"]["error_vs_fp64_oracle_rows_520_559"] = {"max_abs": float(e.max()), "mse": float(np.mean(e ** 2))}
+    return out
+
+
 def extra_sequence(nsm, scenegen, torch, device, theta, weights, ctx, with_error):
     """The soft temporal sequence (8 frames: the emitter orbits 2 degrees per
     frame, 4 objects move 0.01 per frame) at 1080p, BF16 and FP8 forms: per-frame
@@ -591,6 +631,8 @@ def run_ours(args):
                                                                  not args.skip_error)),
                          ("soft_sequence_1080p", lambda: extra_sequence(nsm, scenegen, torch, device, theta, weights,
                                                                          ctx, not args.skip_error)),
+                         ("space_to_depth_1080p", lambda: extra_s2d(nsm, scenegen, torch, device, ctx, 10,
+                                                                    not args.skip_error)),
                          ("serving_32_views", lambda: extra_serving(nsm, scenegen, torch, device, theta, 20)),
                          ("train_step", lambda: extra_train(nsm, scenegen, torch, device, theta, 10))):
             try:

@@ -129,6 +129,24 @@ size_t nsm_param_count(void);
  * and build the packed BF16 / FP8 copies.  Set-up call: allocates device memory. */
 nsm_status nsm_weights_create(nsm_ctx* ctx, const float* host_params, size_t n, nsm_weights** out);
 
+/* Network topologies.  NSM_TOPO_LEVELS3: the 3-level encoder/decoder above.
+ * NSM_TOPO_S2D: the paper's first-layer optimisation (Sec. 3.5): the level-0
+ * convolutions removed, each 2x2 square of pixels flattened into 16 input
+ * channels (channel 4 (2a + b) + c = feature c of square offset (a, b)) that
+ * feed the level-1 encoder, and a 1x1 head 16 -> 4 whose channel 0 is upscaled
+ * bilinearly to full resolution and whose channels 1, 2, 3 are added at square
+ * offsets (0, 1), (1, 0), (1, 1) before the sigmoid.  Parameter order:
+ * enc1_3x3, enc1_1x1, bott_3x3, bott_1x1, dec1_3x3, dec1_1x1, head (16 -> 4),
+ * each OIHW weights then bias (35,904 weights + 212 biases = 36,116). */
+typedef enum { NSM_TOPO_LEVELS3 = 0, NSM_TOPO_S2D = 1 } nsm_topology;
+size_t nsm_param_count_topology(nsm_topology topology);  /* 0 for an unknown topology */
+/* nsm_weights_create for a topology (nsm_weights_create = NSM_TOPO_LEVELS3).
+ * Weights of NSM_TOPO_S2D run in nsm_infer / nsm_infer_host with NSM_BF16
+ * only (other precisions, the batched calls, the autotuner and training
+ * return NSM_ERR_UNSUPPORTED for them). */
+nsm_status nsm_weights_create_topology(nsm_ctx* ctx, nsm_topology topology, const float* host_params, size_t n,
+                                       nsm_weights** out);
+
 /* Re-pack from a canonical FP32 vector already on the device (e.g. the
  * master weights of a training state); asynchronous on stream. */
 nsm_status nsm_weights_load_device(nsm_weights* w, const float* dev_params, size_t n, void* stream);

@@ -17,6 +17,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libnsm.so")
 
 NSM_FP32, NSM_BF16, NSM_FP8 = 0, 1, 2
+NSM_TOPO_LEVELS3, NSM_TOPO_S2D = 0, 1
 PRECISIONS = {"fp32": NSM_FP32, "bf16": NSM_BF16, "fp8": NSM_FP8}
 STATUS = {0: "NSM_OK", 1: "NSM_ERR_INVALID_ARG", 2: "NSM_ERR_SHAPE", 3: "NSM_ERR_ALIGNMENT",
           4: "NSM_ERR_DEVICE", 5: "NSM_ERR_CUDA", 6: "NSM_ERR_TIMEOUT", 7: "NSM_ERR_UNSUPPORTED",
@@ -75,6 +76,8 @@ def lib():
             "nsm_infer_kernel_name": ([I, I], ctypes.c_char_p),
             "nsm_param_count": ([], Z),
             "nsm_weights_create": ([P, P, Z, ctypes.POINTER(P)], I),
+            "nsm_param_count_topology": ([I], Z),
+            "nsm_weights_create_topology": ([P, I, P, Z, ctypes.POINTER(P)], I),
             "nsm_weights_load_device": ([P, P, Z, P], I),
             "nsm_weights_destroy": ([P], None),
             "nsm_features": ([FP, P, P, P, P, P], I),
@@ -187,11 +190,15 @@ class Context:
 
 
 class Weights:
-    def __init__(self, ctx: Context, params: np.ndarray):
+    """Network weights on the device; topology NSM_TOPO_LEVELS3 (default) or NSM_TOPO_S2D."""
+
+    def __init__(self, ctx: Context, params: np.ndarray, topology: int = 0):
         p = np.ascontiguousarray(params, np.float32)
         h = ctypes.c_void_p()
-        _check(lib().nsm_weights_create(ctx.h, _ptr(p), p.size, ctypes.byref(h)), "nsm_weights_create")
+        _check(lib().nsm_weights_create_topology(ctx.h, topology, _ptr(p), p.size, ctypes.byref(h)),
+               "nsm_weights_create_topology")
         self.h = h
+        self.topology = topology
 
     def load_device(self, dev_params, stream=None):
         _check(lib().nsm_weights_load_device(self.h, _ptr(dev_params), int(dev_params.numel()), _stream(stream)),
@@ -460,3 +467,7 @@ def nsm_autotune_report_warps(ctx: Context):
     pw = (ctypes.c_int * 5)()
     _check(_batch_sigs().nsm_autotune_report_warps(ctx.h, ew, pw), "nsm_autotune_report_warps")
     return list(ew), list(pw)
+
+
+def nsm_param_count_topology(topology: int) -> int:
+    return int(lib().nsm_param_count_topology(topology))

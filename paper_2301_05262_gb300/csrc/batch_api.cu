@@ -86,6 +86,7 @@ int nsm_ctx_graph_replays(nsm_ctx* c) { return c ? c->graph_launches : 0; }
 nsm_status nsm_infer_batched(nsm_ctx* c, int n, const nsm_view* views, const nsm_weights* w, void* workspace,
                              size_t workspace_bytes, void* stream) {
     if (!c || !w) return fail(NSM_ERR_INVALID_ARG, "ctx and weights must be non-NULL");
+    if (w->topology != NSM_TOPO_LEVELS3) return fail(NSM_ERR_UNSUPPORTED, "batched calls take 3-level weights");
     nsm_status s = check_views(n, views);
     if (s != NSM_OK) return s;
     const size_t need = nsm_infer_batched_workspace_bytes(n, views);
@@ -175,6 +176,7 @@ nsm_status nsm_infer_batched(nsm_ctx* c, int n, const nsm_view* views, const nsm
 nsm_status nsm_autotune(nsm_ctx* c, int n, const nsm_view* views, const nsm_weights* w, void* workspace,
                         size_t workspace_bytes, int reps, void* stream) {
     if (!c || !w) return fail(NSM_ERR_INVALID_ARG, "ctx and weights must be non-NULL");
+    if (w->topology != NSM_TOPO_LEVELS3) return fail(NSM_ERR_UNSUPPORTED, "batched calls take 3-level weights");
     nsm_status s = check_views(n, views);
     if (s != NSM_OK) return s;
     const size_t need = nsm_infer_batched_workspace_bytes(n, views);

@@ -27,6 +27,7 @@ struct nsm_ctx {
 
 struct nsm_weights {
     int device;
+    int topology;      // nsm_topology
     float* d_params;   // canonical FP32 vector (nsm_param_count floats)
     uint16_t* d_bf16;  // packed BF16 images (tensor-core form)
     void* d_descs;     // packing table

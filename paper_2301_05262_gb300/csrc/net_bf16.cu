@@ -113,7 +113,7 @@ struct TcCfg {
     static constexpr int OFF_BIAS3 = OFF_B1 + B1_CHUNKS * 16;
     static constexpr int OFF_BIAS1 = OFF_BIAS3 + CMID * 4;
     static constexpr int OFF_HEAD = OFF_BIAS1 + COUT * 4;
-    static constexpr int OFF_ZERO = ((OFF_HEAD + (COUT + 1) * 4) + 127) / 128 * 128;  // zero A operand
+    static constexpr int OFF_ZERO = ((OFF_HEAD + 4 * (COUT + 1) * 4) + 127) / 128 * 128;  // zero A operand
     static constexpr int ZERO_BYTES = STACK ? kTileM * 16 + 128 : 0;
     static constexpr int OFF_BAR = OFF_ZERO + ZERO_BYTES;
     static constexpr int BYTES_USED = OFF_BAR + 144;
@@ -433,8 +433,8 @@ __global__ void __launch_bounds__(32 * (NEW + NPW + 1), 1) level_tc_kernel(const
     for (int i = tid; i < C::B1_CHUNKS; i += NT) st_shared_v4(sB1 + 16 * i, __ldg(a.b1img + i));
     for (int i = tid; i < CMID; i += NT) bias3_s[i] = __ldg(a.bias3 + i);
     for (int i = tid; i < COUT; i += NT) bias1_s[i] = __ldg(a.bias1 + i);
-    if (EPI == TEPI_HEAD)
-        for (int i = tid; i <= COUT; i += NT) head_s[i] = __ldg(a.head + i);
+    if (EPI == TEPI_HEAD || EPI == TEPI_HEAD4)
+        for (int i = tid; i < (EPI == TEPI_HEAD4 ? 4 : 1) * (COUT + 1); i += NT) head_s[i] = __ldg(a.head + i);
     for (int i = tid; i < C::ZERO_BYTES / 16; i += NT) st_shared_v4(sbase + C::OFF_ZERO + 16 * i, make_uint4(0, 0, 0, 0));
     if (tid == 0) {
         for (int k = 0; k < 2; ++k) {
@@ -804,6 +804,7 @@ __global__ void __launch_bounds__(32 * (NEW + NPW + 1), 1) level_tc_kernel(const
                 for (int r = rg; r < R; r += G) {
                     const int oy = y0 + r;
                     float hsum = 0.f;
+                    float h4[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
                     for (int c0 = 0; c0 < COUT; c0 += 16) {
                         float val[16], lo[16];
@@ -822,6 +823,11 @@ __global__ void __launch_bounds__(32 * (NEW + NPW + 1), 1) level_tc_kernel(const
                                 for (int q = 0; q < 4; ++q)
                                     dst[q] = make_float4(val[4 * q], val[4 * q + 1], val[4 * q + 2], val[4 * q + 3]);
                             }
+                        } else if constexpr (EPI == TEPI_HEAD4) {
+#pragma unroll
+                            for (int k = 0; k < 4; ++k)
+#pragma unroll
+                                for (int j = 0; j < 16; ++j) h4[k] = fmaf(head_s[k * COUT + c0 + j], val[j], h4[k]);
                         } else {
 #pragma unroll
                             for (int j = 0; j < 16; ++j) hsum = fmaf(head_s[c0 + j], val[j], hsum);
@@ -829,6 +835,10 @@ __global__ void __launch_bounds__(32 * (NEW + NPW + 1), 1) level_tc_kernel(const
                     }
                     if (EPI == TEPI_HEAD && oy < H && ox < W)
                         job.vis[static_cast<size_t>(oy) * W + ox] = sigmoidf_acc(hsum + head_s[COUT]);
+                    if (EPI == TEPI_HEAD4 && oy < H && ox < W)
+                        reinterpret_cast<float4*>(job.out_f)[static_cast<size_t>(oy) * W + ox] =
+                            make_float4(h4[0] + head_s[4 * COUT], h4[1] + head_s[4 * COUT + 1],
+                                        h4[2] + head_s[4 * COUT + 2], h4[3] + head_s[4 * COUT + 3]);
                     if constexpr (EPI == TEPI_STORE && kStage) {
                         __syncwarp();
                         if (oy < H && npix > 0)
@@ -934,6 +944,9 @@ static const Variant kVarDec0[] = {
     NSM_VARIANT(4, 8, 8, 1, 16, 16, 16, TPRO_UP, TEPI_HEAD),
     NSM_VARIANT(4, 8, 12, 1, 16, 16, 16, TPRO_UP, TEPI_HEAD)};
 
+static const Variant kVarDec1Head4[] = {
+    NSM_VARIANT(2, 4, 8, 2, 32, 32, 16, TPRO_UP_SKIP, TEPI_HEAD4)};
+
 struct StageTable { const Variant* v; int n; };
 #define NSM_STAGE(t) {t, static_cast<int>(sizeof(t) / sizeof(t[0]))}
 static const StageTable kStages[kTcStages] = {
@@ -1027,6 +1040,57 @@ cudaError_t launch_infer_bf16(const GatherParams& g, const float* params, const 
     }
     se.rec(kTcStages);
     return cudaSuccess;
+}
+
+const char* const kInferKernelNamesS2d[kInferKernelsS2d] = {
+    "s2d_gather_flatten", "s2d_bf16_enc1", "s2d_bf16_bottleneck", "s2d_bf16_dec1_head4", "s2d_recombine"};
+
+// Space-to-depth topology (Sec. 3.5), BF16 form: the gather writes the 2x2
+// flattened features (16 channels, BF16 hi + lo) where the 3-level net keeps
+// its pooled level-0 output, so the level-1 encoder and the bottleneck run
+// unchanged; dec1 ends in the 4-channel head; a last kernel recombines.
+cudaError_t launch_infer_s2d_bf16(const GatherParams& g, const float* params, const uint16_t* img,
+                                  const Activations& A, float* vis, int* err, cudaStream_t stream,
+                                  const StageEvents& se) {
+    const LayerOffsets off = layer_offsets_s2d();
+    const BF16Images im = bf16_images(true);
+    auto I = [&](int layer) { return reinterpret_cast<const uint4*>(img + im.img_off[layer]); };
+    const int H = g.H, W = g.W;
+    se.rec(0);
+    cudaError_t e = launch_s2d_features(g, static_cast<uint16_t*>(A.e0), stream);
+    if (e != cudaSuccess) return e;
+    const int l3[3] = {ENC1_3, BOTT_3, DEC1_3}, l1[3] = {ENC1_1, BOTT_1, DEC1_1};
+    for (int s = 0; s < 3; ++s) {
+        TcBatch b{};
+        b.nviews = 1;
+        b.b3img = I(l3[s]);
+        b.b1img = I(l1[s]);
+        b.bias3 = params + off.b[l3[s]];
+        b.bias1 = params + off.b[l1[s]];
+        b.head = params + off.w[HEAD];  // [4][16] weights followed by the 4 biases
+        b.err = err;
+        TcJob& j = b.job[0];
+        j.g = g;
+        se.rec(1 + s);
+        if (s == 0) {
+            j.H = H / 2; j.W = W / 2; j.in = static_cast<const uint16_t*>(A.e0);
+            j.out_skip = static_cast<float*>(A.s1); j.out = static_cast<uint16_t*>(A.p1);
+            e = tc_launch_stage(1, tc_default_variant(1), b, 0, stream);
+        } else if (s == 1) {
+            j.H = H / 4; j.W = W / 4; j.in = static_cast<const uint16_t*>(A.p1); j.out_f = static_cast<float*>(A.bo);
+            e = tc_launch_stage(2, tc_default_variant(2), b, 0, stream);
+        } else {
+            j.H = H / 2; j.W = W / 2; j.in_f = static_cast<const float*>(A.bo);
+            j.skip = static_cast<const float*>(A.s1); j.out_f = static_cast<float*>(A.d1);
+            tc_fill_tiles(b, kVarDec1Head4[0].R);
+            e = kVarDec1Head4[0].fn(b, 0, stream);
+        }
+        if (e != cudaSuccess) return e;
+    }
+    se.rec(4);
+    e = launch_s2d_output(static_cast<const float*>(A.d1), H, W, vis, stream);
+    se.rec(5);
+    return e;
 }
 
 }  // namespace nsm

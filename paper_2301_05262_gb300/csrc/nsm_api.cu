@@ -47,6 +47,24 @@ LayerOffsets layer_offsets() {
     return o;
 }
 
+LayerOffsets layer_offsets_s2d() {
+    LayerOffsets o{};
+    size_t off = 0;
+    for (int l = 0; l < NUM_LAYERS; ++l) {
+        if (l == ENC0_3 || l == ENC0_1 || l == DEC0_3 || l == DEC0_1) {
+            o.w[l] = o.b[l] = SIZE_MAX;
+            continue;
+        }
+        const int cout = l == HEAD ? kS2dHeadOut : kLayers[l].cout;
+        o.w[l] = off;
+        off += static_cast<size_t>(kLayers[l].cin) * cout * kLayers[l].k * kLayers[l].k;
+        o.b[l] = off;
+        off += cout;
+    }
+    o.total = off;
+    return o;
+}
+
 int num_sms() {
     static int cached[64] = {0};
     int dev = 0;
@@ -237,28 +255,43 @@ const char* nsm_infer_kernel_name(nsm_precision precision, int i) {
 
 size_t nsm_param_count(void) { return layer_offsets().total; }
 
+size_t nsm_param_count_topology(nsm_topology t) {
+    return t == NSM_TOPO_LEVELS3 ? layer_offsets().total : (t == NSM_TOPO_S2D ? layer_offsets_s2d().total : 0);
+}
+
 nsm_status nsm_weights_create(nsm_ctx* ctx, const float* host_params, size_t n, nsm_weights** out) {
+    return nsm_weights_create_topology(ctx, NSM_TOPO_LEVELS3, host_params, n, out);
+}
+
+nsm_status nsm_weights_create_topology(nsm_ctx* ctx, nsm_topology topology, const float* host_params, size_t n,
+                                       nsm_weights** out) {
     if (!ctx || !host_params || !out) return fail(NSM_ERR_INVALID_ARG, "ctx, host_params and out must be non-NULL");
     *out = nullptr;
-    const size_t want = layer_offsets().total;
+    if (topology != NSM_TOPO_LEVELS3 && topology != NSM_TOPO_S2D)
+        return fail(NSM_ERR_INVALID_ARG, "unknown topology %d", static_cast<int>(topology));
+    const bool s2d = topology == NSM_TOPO_S2D;
+    const size_t want = nsm_param_count_topology(topology);
     if (n != want) return fail(NSM_ERR_SHAPE, "parameter vector has %zu floats, expected %zu", n, want);
     if (!finite_all(host_params, static_cast<int>(n))) return fail(NSM_ERR_INVALID_ARG, "parameters must be finite");
     nsm_weights* w = new nsm_weights{};
+    w->topology = topology;
     cudaGetDevice(&w->device);
     cudaError_t e = cudaMalloc(&w->d_params, n * sizeof(float));
     if (e != cudaSuccess) { delete w; return cuda_fail(e, "cudaMalloc(weights)"); }
     e = cudaMemcpy(w->d_params, host_params, n * sizeof(float), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) { cudaFree(w->d_params); delete w; return cuda_fail(e, "upload weights"); }
-    const BF16Images im = bf16_images();
+    const BF16Images im = bf16_images(s2d);
     w->ndesc = im.n;
     e = cudaMalloc(&w->d_bf16, im.total * sizeof(uint16_t));
     if (e == cudaSuccess) e = cudaMalloc(&w->d_descs, pack_desc_bytes() * im.n);
     if (e == cudaSuccess) e = cudaMemcpy(w->d_descs, im.desc, pack_desc_bytes() * im.n, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = launch_pack_bf16(w->d_params, w->d_bf16, w->d_descs, w->ndesc, nullptr);
     const F8Images f8 = fp8_images();
-    if (e == cudaSuccess) e = cudaMalloc(&w->d_fp8, f8.img_bytes);
-    if (e == cudaSuccess) e = cudaMalloc(&w->d_fp8_scales, f8.scales * sizeof(float));
-    if (e == cudaSuccess) e = launch_pack_fp8(w->d_params, w->d_fp8, w->d_fp8_scales, nullptr);
+    if (!s2d) {
+        if (e == cudaSuccess) e = cudaMalloc(&w->d_fp8, f8.img_bytes);
+        if (e == cudaSuccess) e = cudaMalloc(&w->d_fp8_scales, f8.scales * sizeof(float));
+        if (e == cudaSuccess) e = launch_pack_fp8(w->d_params, w->d_fp8, w->d_fp8_scales, nullptr);
+    }
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
         cudaFree(w->d_params); cudaFree(w->d_bf16); cudaFree(w->d_descs); cudaFree(w->d_fp8);
@@ -271,14 +304,16 @@ nsm_status nsm_weights_create(nsm_ctx* ctx, const float* host_params, size_t n, 
 
 nsm_status nsm_weights_load_device(nsm_weights* w, const float* dev_params, size_t n, void* stream) {
     if (!w) return fail(NSM_ERR_INVALID_ARG, "weights is NULL");
-    if (n != layer_offsets().total) return fail(NSM_ERR_SHAPE, "parameter vector has %zu floats, expected %zu", n, layer_offsets().total);
+    const size_t want = nsm_param_count_topology(static_cast<nsm_topology>(w->topology));
+    if (n != want) return fail(NSM_ERR_SHAPE, "parameter vector has %zu floats, expected %zu", n, want);
     nsm_status s = check_dev_ptr(dev_params, "dev_params", 4);
     if (s != NSM_OK) return s;
     cudaError_t e = cudaMemcpyAsync(w->d_params, dev_params, n * sizeof(float), cudaMemcpyDeviceToDevice,
                                     static_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) return cuda_fail(e, "copy weights");
     e = launch_pack_bf16(w->d_params, w->d_bf16, w->d_descs, w->ndesc, static_cast<cudaStream_t>(stream));
-    if (e == cudaSuccess) e = launch_pack_fp8(w->d_params, w->d_fp8, w->d_fp8_scales, static_cast<cudaStream_t>(stream));
+    if (e == cudaSuccess && w->topology == NSM_TOPO_LEVELS3)
+        e = launch_pack_fp8(w->d_params, w->d_fp8, w->d_fp8_scales, static_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) return cuda_fail(e, "pack weights");
     return NSM_OK;
 }
@@ -346,7 +381,12 @@ nsm_status nsm_infer(nsm_ctx* ctx, const nsm_frame* frame, const nsm_weights* w,
         se.stream = static_cast<cudaStream_t>(stream);
     }
     cudaError_t e;
-    if (precision == NSM_FP32)
+    if (w->topology == NSM_TOPO_S2D) {
+        if (precision != NSM_BF16)
+            return fail(NSM_ERR_UNSUPPORTED, "space-to-depth weights run in the BF16 form only");
+        e = launch_infer_s2d_bf16(g, w->d_params, w->d_bf16, act, vis_out, ctx->d_err,
+                                  static_cast<cudaStream_t>(stream), se);
+    } else if (precision == NSM_FP32)
         e = launch_infer_fp32(g, w->d_params, act, vis_out, static_cast<cudaStream_t>(stream), se);
     else if (precision == NSM_BF16)
         e = launch_infer_bf16(g, w->d_params, w->d_bf16, act, vis_out, ctx->d_err, static_cast<cudaStream_t>(stream), se,

@@ -21,6 +21,10 @@ constexpr LayerShape kLayers[NUM_LAYERS] = {
 
 struct LayerOffsets { size_t w[NUM_LAYERS]; size_t b[NUM_LAYERS]; size_t total; };
 LayerOffsets layer_offsets();
+// Space-to-depth topology (Sec. 3.5): the level-0 layers removed (offsets
+// SIZE_MAX) and the head 16 -> 4 (stored at index HEAD).
+LayerOffsets layer_offsets_s2d();
+constexpr int kS2dHeadOut = 4;
 
 int num_sms();
 
@@ -78,7 +82,7 @@ struct BF16Images {
     size_t img_off[NUM_LAYERS];  // element offset of each layer's image (head has none)
     size_t total;                // elements (uint16)
 };
-BF16Images bf16_images();
+BF16Images bf16_images(bool s2d = false);
 size_t pack_desc_bytes();
 cudaError_t launch_pack_bf16(const float* params, uint16_t* img, const void* dev_descs, int ndesc,
                              cudaStream_t stream);
@@ -98,6 +102,16 @@ extern const char* const kInferKernelNamesFp8[kInferKernelsFp8];
 cudaError_t launch_infer_fp8(const GatherParams& g, const float* params, const uint8_t* img, const float* scales,
                              const Activations& act, float* vis, int* err, cudaStream_t stream,
                              const StageEvents& se);
+
+// Space-to-depth topology, BF16 form: gather + 2x2 flattening, enc1, bottleneck,
+// dec1 with the 4-channel head, 2x2 recombination (5 launches).
+constexpr int kInferKernelsS2d = 5;
+extern const char* const kInferKernelNamesS2d[kInferKernelsS2d];
+cudaError_t launch_s2d_features(const GatherParams& g, uint16_t* out, cudaStream_t stream);
+cudaError_t launch_s2d_output(const float* o4, int H, int W, float* vis, cudaStream_t stream);
+cudaError_t launch_infer_s2d_bf16(const GatherParams& g, const float* params, const uint16_t* img,
+                                  const Activations& act, float* vis, int* err, cudaStream_t stream,
+                                  const StageEvents& se);
 
 constexpr int kInferKernelsBf16 = 5;
 extern const char* const kInferKernelNamesBf16[kInferKernelsBf16];

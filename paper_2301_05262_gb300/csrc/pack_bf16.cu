@@ -74,8 +74,8 @@ __global__ void pack_bf16_kernel(const float* __restrict__ params, uint16_t* __r
     }
 }
 
-BF16Images bf16_images() {
-    const LayerOffsets off = layer_offsets();
+BF16Images bf16_images(bool s2d) {
+    const LayerOffsets off = s2d ? layer_offsets_s2d() : layer_offsets();
     BF16Images im{};
     size_t pos = 0;
     auto add = [&](int layer, int kind) {
@@ -93,9 +93,10 @@ BF16Images bf16_images() {
     // a 3x3 layer is row-stacked when its three stacked kernel rows (3 x 2 c_out
     // MMA rows) fit one MMA of width <= 256
     auto k3 = [&](int layer) { return 3 * 2 * kLayers[layer].cout <= 256 ? 3 : 0; };
-    add(ENC0_3, 3 * 2 * kLayers[ENC0_3].cout <= 256 ? 4 : 1); add(ENC0_1, 2);
+    if (!s2d) { add(ENC0_3, 3 * 2 * kLayers[ENC0_3].cout <= 256 ? 4 : 1); add(ENC0_1, 2); }
     add(ENC1_3, k3(ENC1_3)); add(ENC1_1, 2); add(BOTT_3, k3(BOTT_3)); add(BOTT_1, 2);
-    add(DEC1_3, k3(DEC1_3)); add(DEC1_1, 2); add(DEC0_3, k3(DEC0_3)); add(DEC0_1, 2);
+    add(DEC1_3, k3(DEC1_3)); add(DEC1_1, 2);
+    if (!s2d) { add(DEC0_3, k3(DEC0_3)); add(DEC0_1, 2); }
     im.total = pos;
     return im;
 }

@@ -13,7 +13,7 @@ constexpr int kMaxViews = 32;
 constexpr int kTcStages = 5;  // enc0 (+ gather), enc1, bottleneck, dec1, dec0 (+ head)
 
 enum TcPro { TPRO_GATHER = 0, TPRO_PLAIN = 1, TPRO_UP_SKIP = 2, TPRO_UP = 3 };
-enum TcEpi { TEPI_POOL = 0, TEPI_SKIP_POOL = 1, TEPI_STORE = 2, TEPI_HEAD = 3 };
+enum TcEpi { TEPI_POOL = 0, TEPI_SKIP_POOL = 1, TEPI_STORE = 2, TEPI_HEAD = 3, TEPI_HEAD4 = 4 };
 
 // One view's work in one stage.
 struct TcJob {
@@ -34,7 +34,7 @@ struct TcJob {
     const uint8_t* skip8;       // UP_SKIP: [H][W][CIN]
     uint8_t* out8;              // POOL / SKIP_POOL: pooled [H/2][W/2][COUT]; STORE: [H][W][COUT]
     uint8_t* out_skip8;         // SKIP_POOL: [H][W][COUT]
-    float* vis;                 // HEAD: [H][W]
+    float* vis;                 // HEAD: [H][W]; HEAD4 writes out_f [H][W][4]
 };
 
 // Kernel parameter of a stage launch (passed by value, __grid_constant__).
@@ -46,7 +46,7 @@ struct TcBatch {
     const uint4* b1img;         // packed 1x1 weights
     const float* bias3;
     const float* bias1;
-    const float* head;          // head weights [16] then its bias
+    const float* head;          // HEAD: weights [16] then bias; HEAD4: weights [4][16] then biases [4]
     const float* scale3;        // FP8 form: per-output-channel weight scales of the 3x3
     const float* scale1;        // and of the 1x1
     int* err;                   // device error word
