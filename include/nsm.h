@@ -309,6 +309,42 @@ nsm_status nsm_train_step(nsm_ctx* ctx, nsm_train_state* st, const nsm_batch* ba
  * 3 Adam second moment.  Asynchronous on stream. */
 nsm_status nsm_train_state_read(nsm_train_state* st, int what, float* dev_out, size_t n, void* stream);
 
+/* ---------------------------------------------------------------- scene generation (GPU ray casting) */
+
+/* Training data as the method uses it (Sec. 3.1: a G-buffer and shadow-map
+ * pass, ray-traced hard / soft shadow targets), produced on the GPU by ray
+ * casting an analytic scene: the ground plane z = 0 (normal +z) plus up to 256
+ * objects, each 5 floats (type, cx, cy, cz, s): type 0 = sphere of radius s,
+ * type 1 = axis-aligned box of half-extent s (host array).  Nearest hit wins;
+ * an exact tie goes to the lower object index and the plane is tested last.
+ * FP32 arithmetic.  Asynchronous on stream; outputs on the device. */
+
+/* cam (host, 14 floats): eye C[3], forward[3], right[3], up[3] (orthonormal),
+ * tan(fovy / 2), aspect W / H.  Ray through pixel (x, y) centre, row 0 at the
+ * top.  pos4 [H][W] float4 = (P, view depth (P - C).forward), nrm4 [H][W]
+ * float4 = (n, 0), mask [H][W] uint8 = 1 where the ray hits (pos4 = nrm4 = 0
+ * elsewhere). */
+nsm_status nsm_gen_gbuffer(int H, int W, const float* cam, int n_obj, const float* objects, float* pos4,
+                           float* nrm4, uint8_t* mask, void* stream);
+
+/* lcam (host, 13 floats): emitter centre L[3], forward[3], right[3], up[3],
+ * tan(fov / 2).  depth [Hs][Ws]: distance from L to the nearest hit along the
+ * ray through texel (i, j)'s centre (ndc 2 (i + 1/2) / Ws - 1, 2 (j + 1/2) /
+ * Hs - 1, row 0 at ndc_y = -1), z_far where nothing is hit before z_far. */
+nsm_status nsm_gen_shadowmap(int Hs, int Ws, const float* lcam, float z_far, int n_obj, const float* objects,
+                             float* depth, void* stream);
+
+/* Monte-Carlo visibility of a spherical emitter (centre light_pos (host, 3
+ * floats), radius) seen as its silhouette disk perpendicular to L - P:
+ * spp_side^2 stratified jittered samples per pixel (SplitMix64 jitter keyed by
+ * seed, pixel and sample), concentric disk map, shadow rays from P + eps n;
+ * vis [H][W] float = unoccluded fraction, 1 where mask is 0.  radius 0 gives
+ * the hard (point-light) visibility.  pos4 / nrm4 / mask as written by
+ * nsm_gen_gbuffer. */
+nsm_status nsm_gen_visibility(int H, int W, const float* pos4, const float* nrm4, const uint8_t* mask,
+                              const float* light_pos, float radius, int spp_side, uint64_t seed, float eps,
+                              int n_obj, const float* objects, float* vis, void* stream);
+
 /* ---------------------------------------------------------------- no-allocation variant */
 
 /* FP32 inference that allocates nothing and needs no workspace, for callers

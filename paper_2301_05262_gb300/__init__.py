@@ -471,3 +471,49 @@ def nsm_autotune_report_warps(ctx: Context):
 
 def nsm_param_count_topology(topology: int) -> int:
     return int(lib().nsm_param_count_topology(topology))
+
+
+# ------------------------------------------------------------------ scene generation (GPU ray casting)
+_GEN = None
+
+
+def _gen_sigs():
+    global _GEN
+    if _GEN is None:
+        L = lib()
+        P, I, F = ctypes.c_void_p, ctypes.c_int, ctypes.c_float
+        for name, args in {
+            "nsm_gen_gbuffer": [I, I, P, I, P, P, P, P, P],
+            "nsm_gen_shadowmap": [I, I, P, F, I, P, P, P],
+            "nsm_gen_visibility": [I, I, P, P, P, P, F, I, ctypes.c_uint64, F, I, P, P, P],
+        }.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = I
+        _GEN = L
+    return _GEN
+
+
+def _host_f32(a):
+    return np.ascontiguousarray(np.asarray(a, np.float32).reshape(-1))
+
+
+def gen_gbuffer(H, W, cam, objects, pos4, nrm4, mask, stream=None):
+    """cam: 14 floats (eye, forward, right, up, tan(fovy/2), aspect); objects: (n, 5)."""
+    c, o = _host_f32(cam), _host_f32(objects)
+    _check(_gen_sigs().nsm_gen_gbuffer(H, W, _ptr(c), o.size // 5, _ptr(o) if o.size else None, _ptr(pos4),
+                                       _ptr(nrm4), _ptr(mask), _stream(stream)), "nsm_gen_gbuffer")
+
+
+def gen_shadowmap(Hs, Ws, lcam, z_far, objects, depth, stream=None):
+    c, o = _host_f32(lcam), _host_f32(objects)
+    _check(_gen_sigs().nsm_gen_shadowmap(Hs, Ws, _ptr(c), float(z_far), o.size // 5, _ptr(o) if o.size else None,
+                                         _ptr(depth), _stream(stream)), "nsm_gen_shadowmap")
+
+
+def gen_visibility(H, W, pos4, nrm4, mask, light_pos, radius, spp_side, seed, eps, objects, vis, stream=None):
+    L, o = _host_f32(light_pos), _host_f32(objects)
+    _check(_gen_sigs().nsm_gen_visibility(H, W, _ptr(pos4), _ptr(nrm4), _ptr(mask), _ptr(L), float(radius),
+                                          int(spp_side), ctypes.c_uint64(seed), float(eps), o.size // 5,
+                                          _ptr(o) if o.size else None, _ptr(vis), _stream(stream)),
+           "nsm_gen_visibility")
