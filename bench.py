@@ -485,6 +485,55 @@ def extra_sequence(nsm, scenegen, torch, device, theta, weights, ctx, with_error
     return out
 
 
+def extra_generation(nsm, scenegen, torch, device, reps, with_cpu):
+    """Training-data generation on the device (ray-cast G-buffer, shadow map,
+    64-sample soft visibility) for the 1080p soft scene, next to the OpenMP C
+    ray caster on a smaller frame of the same scene (host cores)."""
+    scene = scenegen.random_scene(SCENE_SEED + 10, N_OBJ, soft=True)
+    pos = torch.empty((H, W, 4), device=device)
+    nrm = torch.empty((H, W, 4), device=device)
+    mask = torch.empty((H, W), dtype=torch.uint8, device=device)
+    depth = torch.empty((HS, WS), device=device)
+    vis = torch.empty((H, W), device=device)
+    cam, lcam = scenegen.camera_vector(scene, H, W), scenegen.light_camera_vector(scene)
+    spp = 8
+    steps = {
+        "gbuffer": lambda: nsm.gen_gbuffer(H, W, cam, scene.objects, pos, nrm, mask),
+        "shadow_map": lambda: nsm.gen_shadowmap(HS, WS, lcam, scenegen.Z_FAR, scene.objects, depth),
+        "soft_visibility": lambda: nsm.gen_visibility(H, W, pos, nrm, mask, scene.light_pos, scene.light_radius, spp,
+                                                      7, scenegen.SHADOW_EPS, scene.objects, vis),
+    }
+    out = {"workload": f"1920x1080 eye rays, {HS}x{WS} light rays, {spp * spp} shadow rays per covered pixel; "
+                       f"{N_OBJ} objects + ground plane (FP32 on the GPU)"}
+    for name, fn in steps.items():
+        for _ in range(3):
+            fn()
+        ev = _events(torch, 2 * reps)
+        for k in range(reps):
+            ev[2 * k].record()
+            fn()
+            ev[2 * k + 1].record()
+        torch.cuda.synchronize()
+        ms = sum(ev[2 * k].elapsed_time(ev[2 * k + 1]) for k in range(reps)) / reps
+        rays = {"gbuffer": H * W, "shadow_map": HS * WS}.get(name)
+        if rays is None:
+            rays = int(mask.sum().item()) * spp * spp
+        out[name] = {"ms": ms, "rays": rays, "mrays_s": rays / (ms * 1e-3) / 1e6}
+    if with_cpu:
+        h, w, hs, ws = 270, 480, 512, 512
+        t0 = time.perf_counter()
+        f = scenegen.render_frame(scene, h, w, hs, ws)
+        t1 = time.perf_counter()
+        scenegen.soft_visibility(f, spp_side=spp, seed=7)
+        t2 = time.perf_counter()
+        n_soft = int(f.mask.sum()) * spp * spp
+        out["cpu_ray_caster"] = {"kind": "FP64 C ray caster (OpenMP)", "cores": cpu_threads(),
+                                 "sample": f"{w}x{h} frame, {ws}x{hs} map, {spp * spp} spp soft visibility",
+                                 "primary_mrays_s": (h * w + hs * ws) / (t1 - t0) / 1e6,
+                                 "shadow_mrays_s": n_soft / (t2 - t1) / 1e6}
+    return out
+
+
 def run_ours(args):
     import torch
     world, rank, local = dist_env()
@@ -634,7 +683,9 @@ def run_ours(args):
                          ("space_to_depth_1080p", lambda: extra_s2d(nsm, scenegen, torch, device, ctx, 10,
                                                                     not args.skip_error)),
                          ("serving_32_views", lambda: extra_serving(nsm, scenegen, torch, device, theta, 20)),
-                         ("train_step", lambda: extra_train(nsm, scenegen, torch, device, theta, 10))):
+                         ("train_step", lambda: extra_train(nsm, scenegen, torch, device, theta, 10)),
+                         ("scene_generation_1080p", lambda: extra_generation(nsm, scenegen, torch, device, 10,
+                                                                             not args.skip_cpu))):
             try:
                 extras[name] = fn()
             except Exception as exc:  # reported, never hidden

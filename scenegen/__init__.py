@@ -209,6 +209,21 @@ class Frame:
         return self.sm.shape[1]
 
 
+def camera_vector(scene: Scene, H: int, W: int) -> np.ndarray:
+    """The eye camera as the GPU generator takes it: eye, forward, right, up,
+    tan(fovy / 2), aspect W / H (14 values)."""
+    fwd, right, up = _look_basis(scene.cam_pos, scene.cam_target, scene.cam_up)
+    th = math.tan(math.radians(scene.cam_fovy_deg) * 0.5)
+    return np.concatenate([scene.cam_pos, fwd, right, up, [th, W / H]])
+
+
+def light_camera_vector(scene: Scene) -> np.ndarray:
+    """The light camera as the GPU generator takes it: centre, forward, right,
+    up, tan(fov / 2) (13 values)."""
+    lf, lr, lu, lt, _ = light_frustum(np.asarray(scene.light_pos, np.float64))
+    return np.concatenate([scene.light_pos, lf, lr, lu, [lt]])
+
+
 def default_bias(tan_half_fov: float, Ws: int) -> float:
     """Relative depth bias beta = two texel angular widths, 2 * (2 tan(fov/2) / Ws).
     The depth test compares z_f <= z + beta * z_f, so the bias grows with the

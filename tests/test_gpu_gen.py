@@ -4,8 +4,6 @@ casts in FP32, so decisions may differ on silhouette edges: hit masks agree on
 >= 99.9% of pixels, positions / depths where both hit agree to FP32 precision,
 and Monte-Carlo visibilities (same SplitMix64-keyed stratified samples, jitter
 rounded to 24 bits) agree on >= 98% of pixels with a mean difference <= 2e-3."""
-import math
-
 import numpy as np
 import pytest
 
@@ -17,22 +15,11 @@ torch = pytest.importorskip("torch")
 import paper_2301_05262_gb300 as nsm  # noqa: E402
 
 
-def _cam(scene, H, W):
-    fwd, right, up = scenegen._look_basis(scene.cam_pos, scene.cam_target, scene.cam_up)
-    th = math.tan(math.radians(scene.cam_fovy_deg) * 0.5)
-    return np.concatenate([scene.cam_pos, fwd, right, up, [th, W / H]])
-
-
-def _lcam(scene):
-    lf, lr, lu, lt, _ = scenegen.light_frustum(np.asarray(scene.light_pos, np.float64))
-    return np.concatenate([scene.light_pos, lf, lr, lu, [lt]])
-
-
 def _gpu_gbuffer(scene, H, W):
     pos = torch.empty((H, W, 4), device="cuda")
     nrm = torch.empty((H, W, 4), device="cuda")
     mask = torch.empty((H, W), dtype=torch.uint8, device="cuda")
-    nsm.gen_gbuffer(H, W, _cam(scene, H, W), scene.objects, pos, nrm, mask)
+    nsm.gen_gbuffer(H, W, scenegen.camera_vector(scene, H, W), scene.objects, pos, nrm, mask)
     torch.cuda.synchronize()
     return pos, nrm, mask
 
@@ -64,7 +51,7 @@ def test_shadowmap_matches_ray_caster(seed, n_obj, S):
     scene = scenegen.random_scene(seed, n_obj, soft=False)
     f = scenegen.render_frame(scene, 8, 8, S, S)
     depth = torch.empty((S, S), device="cuda")
-    nsm.gen_shadowmap(S, S, _lcam(scene), scenegen.Z_FAR, scene.objects, depth)
+    nsm.gen_shadowmap(S, S, scenegen.light_camera_vector(scene), scenegen.Z_FAR, scene.objects, depth)
     torch.cuda.synchronize()
     d = depth.cpu().numpy()
     rel = np.abs(d - f.sm) / f.sm
