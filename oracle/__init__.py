@@ -12,6 +12,11 @@ Contents
               search and the penumbra-width model (Sec. 3.6, suppl. Sec. 4).
   network  -- the compact encoder/decoder (Sec. 3.5), its adjoint, the
               Eq. 2 loss (L1 part) and an Adam step.
+  temporal -- the temporal-instability metric (Sec. 3.4, Eq. 3) and the
+              penumbra-size histogram / 95th percentile / depth rule (Sec. 3.6).
+  train_weights -- a script that trains seeded weights with the functions
+              above (an input for the tests and the benchmark, never an
+              expected value).
 
 Pinning status (what checks each function against something other than
 itself; the tests under tests/test_oracle_*.py):
@@ -31,6 +36,15 @@ itself; the tests under tests/test_oracle_*.py):
       is unpinned beyond the operator level.
   loss_l1 / adam_update / train_step -- closed forms on small vectors and
       finite differences of the loss.
+  reproject_fp32 / accept_fp32 / instability_pair / temporal_instability --
+      rays through pixel centres reproject to their pixel; identical frames
+      give 0; a constant difference gives the closed form; depth, normal and
+      coverage rejections by construction; with a moved camera the
+      reprojection finds the same surface point within about a pixel.
+  screen_width_px / penumbra_histogram / p95_from_histogram / depth_for_width
+      -- projected endpoints, hand histograms, the uniform distribution's
+      percentile, and the paper's 24 / 96 / 384-pixel receptive fields of the
+      3 / 5 / 7-level nets.
   space_to_depth / s2d_output / forward_s2d (Sec. 3.5, the space-to-depth
       topology) -- the index map by brute force, the detail placement and
       channel-0 bilinear by explicit loops, the whole network against a
