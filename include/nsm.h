@@ -345,6 +345,45 @@ nsm_status nsm_gen_visibility(int H, int W, const float* pos4, const float* nrm4
                               const float* light_pos, float radius, int spp_side, uint64_t seed, float eps,
                               int n_obj, const float* objects, float* vis, void* stream);
 
+/* ---------------------------------------------------------------- frame analysis */
+
+/* Temporal instability (Sec. 3.4, Eq. 3) of one pair of consecutive frames:
+ * adds sum over accepted pixels p of exp(alpha D(p)) - 1, D(p) = |vis(p) -
+ * vis_prev(m(p))|, to *sum_inout and the number of accepted pixels to
+ * *count_inout (both device, accumulated so that a sequence sums over its
+ * pairs; E = sum / (H W (T - 1)), alpha = 3 in the paper).  m(p): the world
+ * position pos4(p).xyz projected with the previous frame's pinhole camera
+ * cam_prev (host, 14 floats as in nsm_gen_gbuffer), nearest pixel.  p is
+ * accepted iff pos4(p).w > 0, the projection is in front of the camera and
+ * inside the image, pos4_prev(m).w > 0, |pos4_prev(m).w - z| <= 0.01 z (z the
+ * reprojected view depth) and n(p) . n_prev(m) >= 0.9.  Reprojection, the
+ * tests and D are binary32 with a fixed operation order (no contraction);
+ * exp(alpha D) - 1 is evaluated in binary32 and summed in binary64.
+ * vis / vis_prev [H][W] float; pos4 / nrm4 / pos4_prev / nrm4_prev [H][W]
+ * float4 as written by nsm_gen_gbuffer (device). */
+nsm_status nsm_temporal_instability(int H, int W, const float* vis, const float* vis_prev, const float* pos4,
+                                    const float* nrm4, const float* pos4_prev, const float* nrm4_prev,
+                                    const float* cam_prev, float alpha, double* sum_inout,
+                                    unsigned long long* count_inout, void* stream);
+
+#define NSM_MAX_PENUMBRA_BINS 8192
+
+/* Histogram of screen-space penumbra widths (Sec. 3.6): for every pixel with a
+ * blocker (blocker_out channel 1, z_max, > 0, as written by nsm_features) and
+ * view depth d = pos4.w > 0, w = width H / (2 d tan_half_fovy) pixels (width =
+ * blocker_out channel 2), counted in bin floor(w / bin_px) of hist_inout
+ * (device, nbins uint32, accumulated; negative widths in bin 0, the last bin
+ * open-ended).  binary32 arithmetic.  1 <= nbins <= NSM_MAX_PENUMBRA_BINS. */
+nsm_status nsm_penumbra_histogram(int H, int W, const float* blocker, const float* pos4, float tan_half_fovy,
+                                  float bin_px, int nbins, uint32_t* hist_inout, void* stream);
+
+/* Depth from a penumbra histogram (Sec. 3.6), host only: *p95_px = upper edge
+ * of the first bin at which the cumulative count reaches 95% of the total
+ * (exactly: 20 cum >= 19 total; 0 for an empty histogram) and *levels = the
+ * smallest l >= 1 with a receptive field 3 * 2^l >= *p95_px, i.e.
+ * ceil(log2(p95 / 3)). */
+nsm_status nsm_depth_for_penumbra(const uint32_t* hist, int nbins, float bin_px, float* p95_px, int* levels);
+
 /* ---------------------------------------------------------------- no-allocation variant */
 
 /* FP32 inference that allocates nothing and needs no workspace, for callers

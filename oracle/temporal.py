@@ -141,8 +141,8 @@ def p95_from_histogram(hist, bin_px: float) -> float:
     total = int(h.sum())
     if total == 0:
         return 0.0
-    need = 0.95 * total
-    k = int(np.nonzero(np.cumsum(h) >= need)[0][0])
+    # cumulative >= 95% of the total, compared exactly in integers (19 / 20)
+    k = int(np.nonzero(20 * np.cumsum(h) >= 19 * total)[0][0])
     return (k + 1) * bin_px
 
 
@@ -151,4 +151,4 @@ def depth_for_width(p_w: float) -> int:
     3 * 2^l covers a penumbra of p_w pixels."""
     if p_w <= 6.0:
         return 1
-    return max(1, int(math.ceil(math.log2(p_w / 3.0) - 1e-12)))
+    return max(1, int(math.ceil(math.log2(p_w / 3.0))))

@@ -486,6 +486,9 @@ def _gen_sigs():
             "nsm_gen_gbuffer": [I, I, P, I, P, P, P, P, P],
             "nsm_gen_shadowmap": [I, I, P, F, I, P, P, P],
             "nsm_gen_visibility": [I, I, P, P, P, P, F, I, ctypes.c_uint64, F, I, P, P, P],
+            "nsm_temporal_instability": [I, I, P, P, P, P, P, P, P, F, P, P, P],
+            "nsm_penumbra_histogram": [I, I, P, P, F, F, I, P, P],
+            "nsm_depth_for_penumbra": [P, I, F, P, P],
         }.items():
             fn = getattr(L, name)
             fn.argtypes = args
@@ -517,3 +520,34 @@ def gen_visibility(H, W, pos4, nrm4, mask, light_pos, radius, spp_side, seed, ep
                                           int(spp_side), ctypes.c_uint64(seed), float(eps), o.size // 5,
                                           _ptr(o) if o.size else None, _ptr(vis), _stream(stream)),
            "nsm_gen_visibility")
+
+
+def temporal_instability(vis, vis_prev, pos4, nrm4, pos4_prev, nrm4_prev, cam_prev, sum_inout, count_inout,
+                         alpha=3.0, stream=None):
+    """Adds one frame pair's Eq. 3 terms to sum_inout (float64 device scalar)
+    and its accepted-pixel count to count_inout (int64 device scalar)."""
+    H, W = int(vis.shape[0]), int(vis.shape[1])
+    c = _host_f32(cam_prev)
+    _check(_gen_sigs().nsm_temporal_instability(H, W, _ptr(vis), _ptr(vis_prev), _ptr(pos4), _ptr(nrm4),
+                                                _ptr(pos4_prev), _ptr(nrm4_prev), _ptr(c), float(alpha),
+                                                _ptr(sum_inout), _ptr(count_inout), _stream(stream)),
+           "nsm_temporal_instability")
+
+
+def penumbra_histogram(blocker, pos4, tan_half_fovy, bin_px, hist_inout, stream=None):
+    """Adds the frame's screen-space penumbra widths to hist_inout (int32
+    device array; its length is the bin count)."""
+    H, W = int(pos4.shape[0]), int(pos4.shape[1])
+    _check(_gen_sigs().nsm_penumbra_histogram(H, W, _ptr(blocker), _ptr(pos4), float(tan_half_fovy), float(bin_px),
+                                              int(hist_inout.numel()), _ptr(hist_inout), _stream(stream)),
+           "nsm_penumbra_histogram")
+
+
+def depth_for_penumbra(hist, bin_px):
+    """(95th-percentile width in pixels, levels) from a host histogram."""
+    h = np.ascontiguousarray(np.asarray(hist, np.uint32).reshape(-1))
+    p95 = ctypes.c_float()
+    lv = ctypes.c_int()
+    _check(_gen_sigs().nsm_depth_for_penumbra(_ptr(h), h.size, float(bin_px), ctypes.byref(p95), ctypes.byref(lv)),
+           "nsm_depth_for_penumbra")
+    return float(p95.value), int(lv.value)

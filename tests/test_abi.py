@@ -61,3 +61,25 @@ def test_binding_fails_loudly_without_library(tmp_path, monkeypatch):
     monkeypatch.setattr(nsm, "_lib", None)
     with pytest.raises(ImportError):
         nsm.lib()
+
+
+def test_depth_for_penumbra_host_logic(lib):
+    """nsm_depth_for_penumbra (host only) against the oracle's 95th-percentile
+    and depth rule on random histograms, and its argument checks."""
+    from oracle import temporal as TM
+    rng = np.random.default_rng(1)
+    for _ in range(500):
+        h = rng.integers(0, 50, size=int(rng.integers(1, 40)))
+        if rng.random() < 0.1:
+            h[:] = 0
+        b = float(rng.choice([0.25, 0.5, 1.0, 3.0]))
+        p95, lv = nsm.depth_for_penumbra(h, b)
+        assert p95 == pytest.approx(TM.p95_from_histogram(h, b), abs=1e-6)
+        assert lv == (TM.depth_for_width(p95) if p95 > 0 else 1)
+    # the paper's receptive fields: 24 / 96 / 384 pixels -> 3 / 5 / 7 levels
+    for w, l in ((24, 3), (96, 5), (384, 7)):
+        h = np.zeros(400, np.uint32)
+        h[w - 1] = 10
+        assert nsm.depth_for_penumbra(h, 1.0) == (float(w), l)
+    with pytest.raises(nsm.NSMError):
+        nsm.depth_for_penumbra(np.zeros(4, np.uint32), 0.0)
