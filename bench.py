@@ -452,21 +452,26 @@ def extra_s2d(nsm, scenegen, torch, device, ctx, reps, with_error):
 
 def extra_sequence(nsm, scenegen, torch, device, theta, weights, ctx, with_error):
     """The soft temporal sequence (8 frames: the emitter orbits 2 degrees per
-    frame, 4 objects move 0.01 per frame) at 1080p, BF16 and FP8 forms: per-frame
-    time and error against the FP64 oracle on a band of rows."""
+    frame, 4 objects move 0.01 per frame) at 1080p, FP32, BF16 and FP8 forms:
+    per-frame time and error against the FP64 oracle on a band of rows, and the
+    temporal instability E of Eq. 3 (alpha = 3) of each form's 8 outputs."""
     frames = scenegen.temporal_sequence(H, W, HS, WS, N_OBJ, SCENE_SEED + 10)
     y0, y1 = 520, 560
     out = {"workload": "8-frame soft sequence, 1920x1080, 2048^2 map; errors on rows 520-559 of every frame "
                        "(oracle on rows 488-591: the receptive field is ~20 pixels)", "frames": []}
     theta64 = theta.astype(np.float64)
+    forms = ("fp32", "bf16", "fp8")
+    outs = {p: [] for p in forms}
+    gbufs = []
     for f in frames:
         light = nsm.LightDesc(pos=tuple(f.light_pos), radius=f.light_radius, r_hat=f.r_hat, view_proj=f.view_proj,
                               z_far=f.z_far, bias=f.bias, tan_half_fov=f.tan_half_fov)
         t = tuple(torch.from_numpy(x).to(device) for x in (f.pos4, f.nrm4, f.sm))
+        gbufs.append(t)
         fr = nsm.make_frame(t[0], t[1], t[2], light, f.cam_pos)
         ref = oracle_band(f, theta64, y0, y1) if with_error else None
         rec = {}
-        for pname in ("bf16", "fp8"):
+        for pname in forms:
             prec = nsm.PRECISIONS[pname]
             ws = torch.empty((nsm.nsm_infer_workspace_bytes(H, W, prec),), dtype=torch.uint8, device=device)
             v = torch.empty((H, W), dtype=torch.float32, device=device)
@@ -476,13 +481,64 @@ def extra_sequence(nsm, scenegen, torch, device, theta, weights, ctx, with_error
             nsm.nsm_infer(ctx, fr, weights, prec, ws, v)
             ev[1].record()
             torch.cuda.synchronize()
+            outs[pname].append(v)
+            if pname == "fp32":
+                continue
             r = {"ms": ev[0].elapsed_time(ev[1])}
             if ref is not None:
                 e = np.abs(v[y0:y1].cpu().numpy().astype(np.float64) - ref)
                 r.update({"max_abs": float(e.max()), "mse": float(np.mean(e ** 2))})
             rec[pname] = r
         out["frames"].append(rec)
+    # Eq. 3 on the device (static camera: reprojection is the identity where
+    # the depth / normal test passes; moving objects' pixels are rejected)
+    cam = scenegen.camera_vector(frames[0].scene, H, W)
+    inst = {}
+    for pname in forms:
+        s = torch.zeros(1, dtype=torch.float64, device=device)
+        c = torch.zeros(1, dtype=torch.int64, device=device)
+        ev = _events(torch, 2)
+        ev[0].record()
+        for k in range(1, len(frames)):
+            nsm.temporal_instability(outs[pname][k], outs[pname][k - 1], gbufs[k][0], gbufs[k][1], gbufs[k - 1][0],
+                                     gbufs[k - 1][1], cam, s, c)
+        ev[1].record()
+        torch.cuda.synchronize()
+        inst[pname] = {"E": float(s.item()) / (H * W * (len(frames) - 1)), "accepted_px": int(c.item()),
+                       "ms_7_pairs": ev[0].elapsed_time(ev[1])}
+    out["temporal_instability_eq3"] = inst
     return out
+
+
+def extra_penumbra_depth(nsm, scenegen, torch, device, reps):
+    """Sec. 3.6 on the 1080p soft frame: blocker search, screen-space penumbra
+    histogram (0.5 px bins), 95th percentile and the depth it asks for."""
+    f = scenegen.soft_frame(H, W, HS, WS, N_OBJ, SCENE_SEED + 10)
+    light = nsm.LightDesc(pos=tuple(f.light_pos), radius=f.light_radius, r_hat=f.r_hat, view_proj=f.view_proj,
+                          z_far=f.z_far, bias=f.bias, tan_half_fov=f.tan_half_fov)
+    pos4, nrm4, sm = (torch.from_numpy(x).to(device) for x in (f.pos4, f.nrm4, f.sm))
+    fr = nsm.make_frame(pos4, nrm4, sm, light, f.cam_pos)
+    feat = torch.empty((4, H, W), dtype=torch.float32, device=device)
+    blk = torch.empty((3, H, W), dtype=torch.float32, device=device)
+    nsm.nsm_features(fr, feat, None, None, blk)
+    th = float(scenegen.camera_vector(f.scene, H, W)[12])
+    hist = torch.zeros(2048, dtype=torch.int32, device=device)
+    for _ in range(3):
+        nsm.penumbra_histogram(blk, pos4, th, 0.5, hist)
+    ev = _events(torch, 2 * reps)
+    for k in range(reps):
+        ev[2 * k].record()
+        nsm.penumbra_histogram(blk, pos4, th, 0.5, hist)
+        ev[2 * k + 1].record()
+    torch.cuda.synchronize()
+    hist.zero_()
+    nsm.penumbra_histogram(blk, pos4, th, 0.5, hist)
+    h = hist.cpu().numpy()
+    p95, levels = nsm.depth_for_penumbra(h, 0.5)
+    ms = sum(ev[2 * k].elapsed_time(ev[2 * k + 1]) for k in range(reps)) / reps
+    return {"workload": "1920x1080 soft frame, 2048^2 map, emitter radius %.3f" % f.light_radius,
+            "pixels_with_blocker": int(h.sum()), "p95_px": p95, "levels": levels,
+            "receptive_field_px": 3 * 2 ** levels, "histogram_ms": ms}
 
 
 def extra_generation(nsm, scenegen, torch, device, reps, with_cpu):
@@ -683,6 +739,7 @@ def run_ours(args):
                          ("space_to_depth_1080p", lambda: extra_s2d(nsm, scenegen, torch, device, ctx, 10,
                                                                     not args.skip_error)),
                          ("serving_32_views", lambda: extra_serving(nsm, scenegen, torch, device, theta, 20)),
+                         ("penumbra_depth_1080p", lambda: extra_penumbra_depth(nsm, scenegen, torch, device, 10)),
                          ("train_step", lambda: extra_train(nsm, scenegen, torch, device, theta, 10)),
                          ("scene_generation_1080p", lambda: extra_generation(nsm, scenegen, torch, device, 10,
                                                                              not args.skip_cpu))):
