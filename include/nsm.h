@@ -208,6 +208,23 @@ nsm_status nsm_infer_host(nsm_ctx* ctx, const nsm_frame* host_frame, const nsm_w
                           nsm_precision precision, void* dev_stage, size_t stage_bytes,
                           void* workspace, size_t workspace_bytes, float* vis_host, void* stream);
 
+/* nsm_infer_host over a sequence of n frames (frames[i]: host pointers, pinned
+ * for the copies to overlap; sizes may differ), pipelined: while frame i runs
+ * on `stream`, frame i + 1's G-buffer and map are copied to the device and
+ * frame i - 1's visibility is copied to vis_host[i - 1] (two copy streams
+ * owned by the context, events between them).  dev_stage holds 2 or 3
+ * staging slots of nsm_infer_host_stage_bytes of the largest frame (rounded
+ * up to 256 bytes) each: stage_bytes / slot slots are used (at most 3; fewer
+ * than 2 is NSM_ERR_WORKSPACE); a slot is refilled only after the read-back
+ * of the frame that used it.  workspace as for nsm_infer (largest frame).
+ * Every frame's results equal nsm_infer's on the same inputs.  Synchronises
+ * before returning (all vis_host[i] are then valid); on an error the copies
+ * already issued are waited for. */
+nsm_status nsm_infer_host_sequence(nsm_ctx* ctx, int n, const nsm_frame* frames, const nsm_weights* w,
+                                   nsm_precision precision, void* dev_stage, size_t stage_bytes,
+                                   void* workspace, size_t workspace_bytes, float* const* vis_host,
+                                   void* stream);
+
 /* ---------------------------------------------------------------- batched serving */
 
 /* One view of a batch: its inputs (as for nsm_infer) and its output. */

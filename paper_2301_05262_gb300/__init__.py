@@ -85,6 +85,7 @@ def lib():
             "nsm_infer": ([P, FP, P, I, P, Z, P, P], I),
             "nsm_infer_host_stage_bytes": ([I, I, I, I], Z),
             "nsm_infer_host": ([P, FP, P, I, P, Z, P, Z, P, P], I),
+            "nsm_infer_host_sequence": ([P, I, FP, P, I, P, Z, P, Z, P, P], I),
             "nsm_infer_fp32_static": ([FP, P, P, P], I),
         }
         for name, (args, res) in sig.items():
@@ -252,6 +253,21 @@ def nsm_infer_host(ctx: Context, host_frame: nsm_frame, weights: Weights, precis
                                 int(dev_stage.numel() * dev_stage.element_size()), _ptr(workspace),
                                 int(workspace.numel() * workspace.element_size()), _ptr(vis_host),
                                 _stream(stream)), "nsm_infer_host")
+
+
+def nsm_infer_host_sequence(ctx: Context, host_frames, weights: Weights, precision: int, dev_stage, workspace,
+                            vis_hosts, stream=None):
+    """Pipelined nsm_infer_host over a list of host frames; vis_hosts: one
+    C-contiguous float32 host array per frame (pinned for overlap)."""
+    n = len(host_frames)
+    arr = (nsm_frame * max(n, 1))(*host_frames)
+    outs = (ctypes.c_void_p * max(n, 1))(*[v.ctypes.data if isinstance(v, np.ndarray) else v.data_ptr()
+                                           for v in vis_hosts])
+    _check(lib().nsm_infer_host_sequence(ctx.h, n, arr, weights.h, precision, _ptr(dev_stage),
+                                         int(dev_stage.numel() * dev_stage.element_size()), _ptr(workspace),
+                                         int(workspace.numel() * workspace.element_size()),
+                                         ctypes.cast(outs, ctypes.c_void_p), _stream(stream)),
+           "nsm_infer_host_sequence")
 
 
 def nsm_infer_fp32_static(frame: nsm_frame, dev_params, vis_out, stream=None):

@@ -23,6 +23,10 @@ struct nsm_ctx {
     cudaGraphNode_t graph_nodes[nsm::kTcStages];
     cudaKernelNodeParams graph_params[nsm::kTcStages];
     int graph_launches;                      // replays of the cached graph (for tests)
+    // nsm_infer_host_sequence: copy streams and per-slot events (created on first use)
+    cudaStream_t h2d_stream, d2h_stream;
+    cudaEvent_t slot_h2d[nsm::kMaxHostSlots], slot_inf[nsm::kMaxHostSlots], slot_d2h[nsm::kMaxHostSlots];
+    bool slots_ready;
 };
 
 struct nsm_weights {
@@ -37,3 +41,4 @@ struct nsm_weights {
 };
 
 void ctx_release_graph(nsm_ctx* c);
+void ctx_release_host_slots(nsm_ctx* c);

@@ -205,6 +205,7 @@ nsm_status nsm_ctx_create(nsm_ctx** out) {
 void nsm_ctx_destroy(nsm_ctx* c) {
     if (!c) return;
     ctx_release_graph(c);
+    ctx_release_host_slots(c);
     cudaFree(c->d_err);
     delete c;
 }
@@ -404,6 +405,43 @@ size_t nsm_infer_host_stage_bytes(int H, int W, int Hs, int Ws) {
     return align_up(npx * 16, 256) * 2 + align_up(static_cast<size_t>(Hs) * Ws * 4, 256) + align_up(npx * 4, 256);
 }
 
+}  // extern "C"
+
+// Copy streams and per-slot events of nsm_infer_host_sequence.
+static nsm_status ctx_host_slots(nsm_ctx* c) {
+    if (c->slots_ready) return NSM_OK;
+    cudaError_t e = cudaStreamCreateWithFlags(&c->h2d_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->d2h_stream, cudaStreamNonBlocking);
+    for (int k = 0; k < kMaxHostSlots && e == cudaSuccess; ++k) {
+        e = cudaEventCreateWithFlags(&c->slot_h2d[k], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->slot_inf[k], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->slot_d2h[k], cudaEventDisableTiming);
+    }
+    if (e != cudaSuccess) {
+        c->slots_ready = true;  // release what was created
+        ctx_release_host_slots(c);
+        return cuda_fail(e, "copy streams / events");
+    }
+    c->slots_ready = true;
+    return NSM_OK;
+}
+
+void ctx_release_host_slots(nsm_ctx* c) {
+    if (!c->slots_ready) return;
+    if (c->h2d_stream) cudaStreamDestroy(c->h2d_stream);
+    if (c->d2h_stream) cudaStreamDestroy(c->d2h_stream);
+    for (int k = 0; k < kMaxHostSlots; ++k) {
+        if (c->slot_h2d[k]) cudaEventDestroy(c->slot_h2d[k]);
+        if (c->slot_inf[k]) cudaEventDestroy(c->slot_inf[k]);
+        if (c->slot_d2h[k]) cudaEventDestroy(c->slot_d2h[k]);
+        c->slot_h2d[k] = c->slot_inf[k] = c->slot_d2h[k] = nullptr;
+    }
+    c->h2d_stream = c->d2h_stream = nullptr;
+    c->slots_ready = false;
+}
+
+extern "C" {
+
 nsm_status nsm_infer_host(nsm_ctx* ctx, const nsm_frame* hf, const nsm_weights* w, nsm_precision precision,
                           void* dev_stage, size_t stage_bytes, void* workspace, size_t workspace_bytes,
                           float* vis_host, void* stream) {
@@ -436,6 +474,73 @@ nsm_status nsm_infer_host(nsm_ctx* ctx, const nsm_frame* hf, const nsm_weights* 
     if (s != NSM_OK) return s;
     if ((e = cudaMemcpyAsync(vis_host, d_vis, npx * 4, cudaMemcpyDeviceToHost, st)) != cudaSuccess) return cuda_fail(e, "D2H visibility");
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e, "stream synchronize");
+    return NSM_OK;
+}
+
+nsm_status nsm_infer_host_sequence(nsm_ctx* ctx, int n, const nsm_frame* frames, const nsm_weights* w,
+                                   nsm_precision precision, void* dev_stage, size_t stage_bytes, void* workspace,
+                                   size_t workspace_bytes, float* const* vis_host, void* stream) {
+    if (!ctx || !w) return fail(NSM_ERR_INVALID_ARG, "ctx and weights must be non-NULL");
+    if (n < 0 || (n > 0 && (!frames || !vis_host))) return fail(NSM_ERR_INVALID_ARG, "n >= 0, frames and vis_host");
+    if (n == 0) return NSM_OK;
+    size_t slot = 0;
+    for (int i = 0; i < n; ++i) {
+        const nsm_frame& f = frames[i];
+        if (!f.pos4 || !f.nrm4 || !f.sm || !vis_host[i])
+            return fail(NSM_ERR_INVALID_ARG, "frame %d: host pointers must be non-NULL", i);
+        if (f.H < 0 || f.W < 0 || f.Hs <= 0 || f.Ws <= 0) return fail(NSM_ERR_SHAPE, "frame %d: bad sizes", i);
+        const size_t b = nsm_infer_host_stage_bytes(f.H, f.W, f.Hs, f.Ws);
+        if (b > slot) slot = b;
+    }
+    slot = align_up(slot, 256);
+    const int nslots = slot ? static_cast<int>(stage_bytes / slot < kMaxHostSlots ? stage_bytes / slot : kMaxHostSlots)
+                            : kMaxHostSlots;
+    if (!dev_stage || nslots < 2)
+        return fail(NSM_ERR_WORKSPACE, "staging buffer of %zu bytes given, 2 x %zu needed", stage_bytes, slot);
+    nsm_status s = check_dev_ptr(dev_stage, "dev_stage", 256);
+    if (s != NSM_OK) return s;
+    if ((s = ctx_host_slots(ctx)) != NSM_OK) return s;
+    cudaStream_t st = static_cast<cudaStream_t>(stream), cs = ctx->h2d_stream, ds = ctx->d2h_stream;
+    cudaError_t e = cudaSuccess;
+    // slot k's buffers are free again once the read-back of the frame that used
+    // them is done (which itself waited for that frame's inference)
+    for (int i = 0; i < n && e == cudaSuccess; ++i) {
+        const int k = i % nslots;
+        const nsm_frame& hf = frames[i];
+        const size_t npx = static_cast<size_t>(hf.H) * hf.W;
+        if (npx == 0) continue;
+        char* base = static_cast<char*>(dev_stage) + k * slot;
+        float* d_pos = reinterpret_cast<float*>(base);
+        float* d_nrm = reinterpret_cast<float*>(base + align_up(npx * 16, 256));
+        float* d_sm = reinterpret_cast<float*>(base + 2 * align_up(npx * 16, 256));
+        float* d_vis = reinterpret_cast<float*>(base + 2 * align_up(npx * 16, 256) +
+                                                align_up(static_cast<size_t>(hf.Hs) * hf.Ws * 4, 256));
+        if (i >= nslots) e = cudaStreamWaitEvent(cs, ctx->slot_d2h[k], 0);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(d_pos, hf.pos4, npx * 16, cudaMemcpyHostToDevice, cs);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(d_nrm, hf.nrm4, npx * 16, cudaMemcpyHostToDevice, cs);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(d_sm, hf.sm, static_cast<size_t>(hf.Hs) * hf.Ws * 4, cudaMemcpyHostToDevice, cs);
+        if (e == cudaSuccess) e = cudaEventRecord(ctx->slot_h2d[k], cs);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ctx->slot_h2d[k], 0);
+        if (e != cudaSuccess) break;
+        nsm_frame df = hf;
+        df.pos4 = d_pos;
+        df.nrm4 = d_nrm;
+        df.sm = d_sm;
+        if ((s = nsm_infer(ctx, &df, w, precision, workspace, workspace_bytes, d_vis, stream)) != NSM_OK) {
+            cudaStreamSynchronize(cs);
+            cudaStreamSynchronize(ds);
+            return s;
+        }
+        e = cudaEventRecord(ctx->slot_inf[k], st);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(ds, ctx->slot_inf[k], 0);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(vis_host[i], d_vis, npx * 4, cudaMemcpyDeviceToHost, ds);
+        if (e == cudaSuccess) e = cudaEventRecord(ctx->slot_d2h[k], ds);
+    }
+    const cudaError_t e1 = cudaStreamSynchronize(cs), e2 = cudaStreamSynchronize(ds), e3 = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "pipelined copies");
+    if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess)
+        return cuda_fail(e1 != cudaSuccess ? e1 : (e2 != cudaSuccess ? e2 : e3), "stream synchronize");
     return NSM_OK;
 }
 

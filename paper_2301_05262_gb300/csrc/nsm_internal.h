@@ -10,6 +10,9 @@
 
 namespace nsm {
 
+// Device staging slots of nsm_infer_host_sequence (frames in flight).
+constexpr int kMaxHostSlots = 3;
+
 // Canonical layer table of the 3-level network (Sec. 3.5): offsets of each
 // layer's OIHW weights and bias in the canonical parameter vector.
 enum Layer { ENC0_3, ENC0_1, ENC1_3, ENC1_1, BOTT_3, BOTT_1, DEC1_3, DEC1_1, DEC0_3, DEC0_1, HEAD, NUM_LAYERS };

@@ -54,6 +54,9 @@ def test_host_validation_errors(lib):
     fr = nsm.nsm_frame(H=4, W=4)
     assert lib.nsm_infer_host(None, ctypes.byref(fr), None, 0, None, 0, None, 0, None, None) == 1
     assert nsm.nsm_infer_host_stage_bytes(4, 4, 8, 8) >= 4 * 4 * 32 + 8 * 8 * 4 + 4 * 4 * 4
+    # pipelined host entry point: NULL context / weights, negative count
+    assert lib.nsm_infer_host_sequence(None, 1, ctypes.byref(fr), None, 0, None, 0, None, 0, None, None) == 1
+    assert b"ctx" in lib.nsm_last_error()
 
 
 def test_binding_fails_loudly_without_library(tmp_path, monkeypatch):
