@@ -204,7 +204,7 @@ def run_reference(args):
     import scenegen
     from oracle import network as N
     frame = scenegen.hard_frame(H, W, HS, WS, N_OBJ, SCENE_SEED)
-    theta = scenegen.he_init_weights(WEIGHT_SEED, N.layer_table(3)).astype(np.float32).astype(np.float64)
+    theta = scenegen.trained_weights().astype(np.float64)
     rows = 256
     for _ in range(args.warmup):
         oracle_sample(frame, theta, rows)
@@ -220,7 +220,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": mpix, "unit": "Mpix/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs / args.steps * 1e3,
             "ms_per_frame": ms_frame, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64", "data": "synthetic (seeded ray-cast scene)",
+            "dtype": "f64", "data": "synthetic (seeded ray-cast scene, seeded oracle-trained weights)",
             "config": {"workload": WORKLOAD, "l2": "n/a (CPU)"},
             "cpu_baseline": {"value": mpix, "unit": "Mpix/s", "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": mpix, "unit": "Mpix/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -605,7 +605,9 @@ def run_ours(args):
     import scenegen
 
     frame = scenegen.hard_frame(H, W, HS, WS, N_OBJ, SCENE_SEED + rank)
-    theta = scenegen.he_init_weights(WEIGHT_SEED, nsm.LAYERS).astype(np.float32)
+    # the network as the paper uses it: trained (seeded, on ray-cast targets, by
+    # the oracle's training step); He-init weights only where no trained set exists
+    theta = scenegen.trained_weights()
     ctx = nsm.Context()
     weights = nsm.Weights(ctx, theta)
     pos4 = torch.from_numpy(frame.pos4).to(device)
@@ -802,7 +804,7 @@ def run_ours(args):
     line = {"metric": METRIC, "value": hf["mpix_s"], "unit": "Mpix/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": hf["ms_per_frame"], "ms_per_frame": hf["ms_per_frame"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32" if head == "fp32" else head,
-            "data": "synthetic (seeded ray-cast scene, He-init weights)",
+            "data": "synthetic (seeded ray-cast scene, seeded oracle-trained weights)",
             "config": {"workload": WORKLOAD, "precision": head, "l2": "flushed (256 MiB write) between timed steps",
                        "parallelism": f"{world} independent frame(s), one per GPU", "autotuned_plan": plan},
             "forms": {k: {kk: vv for kk, vv in v.items() if kk != "clocks"} for k, v in forms.items()},

@@ -360,6 +360,20 @@ def perturbed(scene: Scene, rng: SplitMix64) -> Scene:
                                cam_target=np.asarray(scene.cam_target) + 0.0)
 
 
+TRAINED_WEIGHTS = os.path.join(os.path.dirname(os.path.abspath(__file__)), "weights_trained_3level.npy")
+
+
+def trained_weights() -> np.ndarray:
+    """Seeded trained weights of the 3-level network (canonical order, float32):
+    one network for hard and soft shadows, trained on this module's ray-cast
+    targets by the oracle's training step (`python -m oracle.train_weights`,
+    which documents the recipe).  An input like the scenes, not an expected
+    value."""
+    if not os.path.exists(TRAINED_WEIGHTS):
+        raise FileNotFoundError(f"{TRAINED_WEIGHTS} is missing (python -m oracle.train_weights writes it)")
+    return np.load(TRAINED_WEIGHTS).astype(np.float32)
+
+
 def he_init_weights(seed: int, layers) -> np.ndarray:
     """Seeded He-normal weights (std sqrt(2 / fan_in)), zero biases, flattened
     in the canonical order: for each layer OIHW weights then its bias."""

@@ -95,6 +95,34 @@ def test_infer_bf16_vs_fp64(ctx):
         assert err.max() <= 1e-2, err.max()
 
 
+@pytest.mark.parametrize("precision", [nsm.NSM_FP32, nsm.NSM_BF16])
+def test_infer_trained_weights(ctx, precision):
+    """The seeded oracle-trained weights (saturating outputs, steep shadow
+    edges): FP32 within 1e-4 of the FP64 forward, BF16 within its rounding
+    model and within 1e-2 max-abs / 1e-4 MSE of the FP64 forward."""
+    theta = scenegen.trained_weights()
+    for f in (scenegen.hard_frame(256, 256, 512, 512, 8, 1), scenegen.soft_frame(256, 256, 512, 512, 8, 21),
+              scenegen.soft_frame(68, 132, 300, 200, 8, 5)):
+        _check(ctx, f, theta, precision)
+
+
+def test_infer_trained_weights_1080p_soft_bf16(ctx):
+    """Full-size 1080p soft frame with the trained weights, BF16 against FP64."""
+    f = scenegen.soft_frame(1080, 1920, 2048, 2048, 64, 21)
+    theta = scenegen.trained_weights()
+    vis = _run(ctx, f, theta, nsm.NSM_BF16)
+    err = np.abs(vis - N.forward(_features(f), theta.astype(np.float64)))
+    assert err.max() <= 1e-2 and float(np.mean(err ** 2)) <= 1e-4, (err.max(), float(np.mean(err ** 2)))
+
+
+def test_infer_fp8_trained_weights_follow_rounding_model(ctx):
+    theta = scenegen.trained_weights()
+    f = scenegen.soft_frame(256, 256, 512, 512, 8, 21)
+    vis = _run(ctx, f, theta, nsm.NSM_FP8)
+    q = _fp8_model(_features(f), theta)
+    assert float(np.mean((vis - q) ** 2)) <= 1e-6
+
+
 def test_infer_rejects_bad_shapes_and_workspace(ctx):
     f = scenegen.hard_frame(8, 8, 8, 8, 2, 1)
     df = DeviceFrame(f)

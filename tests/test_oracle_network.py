@@ -442,3 +442,22 @@ def test_forward_s2d_head_bias_closed_form():
     np.testing.assert_allclose(v[1::2, 0::2], sig(bias[0] + bias[2]), atol=1e-15)
     np.testing.assert_allclose(v[1::2, 1::2], sig(bias[0] + bias[3]), atol=1e-15)
     assert sum(ci * co * k * k for (_, ci, co, k) in t) == 35904  # 39,248 - level 0 - old head + 16x4 head
+
+
+def test_trained_weights_input():
+    """The committed trained weights (an input of the GPU tests and the
+    benchmark): canonical size, finite, and on held-out scenes (seeds outside
+    the training range) far closer to the ray-cast visibility than the He-init
+    weights training started from."""
+    import scenegen
+    from oracle import gather as G
+    th = scenegen.trained_weights().astype(np.float64)
+    assert th.shape == (N.param_count(3, with_bias=True),) and np.isfinite(th).all()
+    he = scenegen.he_init_weights(3, N.layer_table(3))
+    for soft in (False, True):
+        f = scenegen.render_frame(scenegen.random_scene(3000 + soft, 64, soft=soft), 128, 224, 512, 512)
+        target = (scenegen.soft_visibility(f, spp_side=8) if soft else scenegen.hard_visibility(f)).astype(np.float64)
+        feat, _, _ = G.features(f.pos4, f.nrm4, f.sm, f.view_proj, f.light_pos, f.cam_pos, f.r_hat, f.z_far, f.bias)
+        mse_tr = np.mean((N.forward(feat, th) - target) ** 2)
+        mse_he = np.mean((N.forward(feat, he) - target) ** 2)
+        assert mse_tr < 0.25 * mse_he, (soft, mse_tr, mse_he)
