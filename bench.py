@@ -634,7 +634,7 @@ def run_ours(args):
         rows, ctas, ms = nsm.nsm_autotune_report(ctx)
         ew, pw = nsm.nsm_autotune_report_warps(ctx)
         plan = {"tile_rows": rows, "ctas_per_sm": ctas, "epilogue_warps": ew, "producer_warps": pw,
-                "tuned_stage_ms": [round(x, 5) for x in ms]}
+                "mma_order": nsm.nsm_autotune_report_order(ctx), "tuned_stage_ms": [round(x, 5) for x in ms]}
         del ws_t, vtmp
     for pname in precisions:
         prec = nsm.PRECISIONS[pname]

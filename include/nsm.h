@@ -265,6 +265,19 @@ nsm_status nsm_autotune_report(nsm_ctx* ctx, int* rows_out, int* ctas_out, float
  * warps (4 or 8: TMEM readers) and producer warps (input staging). */
 nsm_status nsm_autotune_report_warps(nsm_ctx* ctx, int* epilogue_warps_out, int* producer_warps_out);
 
+/* The MMA schedule of the plan per stage (5 entries): 0 = each tile's 1x1
+ * convolution is issued right after its 3x3; 1 = the next tile's 3x3 is
+ * issued before the previous tile's 1x1, so the tensor core works on it while
+ * the epilogue turns the previous 3x3 result into the 1x1 operand. */
+nsm_status nsm_autotune_report_order(nsm_ctx* ctx, int* mma_order_out);
+
+/* Manual plan: the number of tile variants of a tensor-core stage (0 enc0,
+ * 1 enc1, 2 bottleneck, 3 dec1, 4 dec0; 0 for another index), and setting a
+ * stage's variant and CTAs per SM (0 = as many as fit) on the context, as
+ * nsm_autotune would.  Every variant computes the same result. */
+int nsm_plan_variants(int stage);
+nsm_status nsm_plan_set(nsm_ctx* ctx, int stage, int variant, int ctas_per_sm);
+
 /* ---------------------------------------------------------------- backward / training */
 
 /* Bytes of device workspace nsm_backward needs for an H x W view. */

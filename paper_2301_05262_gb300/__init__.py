@@ -428,6 +428,9 @@ def _batch_sigs():
         "nsm_autotune": ([P, I, VP, P, P, Z, I, P], I),
         "nsm_autotune_report": ([P, P, P, P], I),
         "nsm_autotune_report_warps": ([P, P, P], I),
+        "nsm_autotune_report_order": ([P, P], I),
+        "nsm_plan_variants": ([I], I),
+        "nsm_plan_set": ([P, I, I, I], I),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -475,6 +478,21 @@ def nsm_autotune_report(ctx: Context):
     ms = (ctypes.c_float * 5)()
     _check(_batch_sigs().nsm_autotune_report(ctx.h, rows, ctas, ms), "nsm_autotune_report")
     return list(rows), list(ctas), list(ms)
+
+
+def nsm_plan_variants(stage: int) -> int:
+    return int(_batch_sigs().nsm_plan_variants(stage))
+
+
+def nsm_plan_set(ctx: Context, stage: int, variant: int, ctas_per_sm: int = 0):
+    _check(_batch_sigs().nsm_plan_set(ctx.h, stage, variant, ctas_per_sm), "nsm_plan_set")
+
+
+def nsm_autotune_report_order(ctx: Context):
+    """MMA schedule (0 or 1) of every stage of the context's plan."""
+    o = (ctypes.c_int * 5)()
+    _check(_batch_sigs().nsm_autotune_report_order(ctx.h, o), "nsm_autotune_report_order")
+    return list(o)
 
 
 def nsm_autotune_report_warps(ctx: Context):

@@ -246,4 +246,24 @@ nsm_status nsm_autotune_report_warps(nsm_ctx* c, int* epilogue_warps_out, int* p
     return NSM_OK;
 }
 
+int nsm_plan_variants(int stage) { return tc_stage_variants(stage); }
+
+nsm_status nsm_plan_set(nsm_ctx* c, int stage, int variant, int ctas_per_sm) {
+    if (!c) return fail(NSM_ERR_INVALID_ARG, "ctx is NULL");
+    if (stage < 0 || stage >= kTcStages || variant < 0 || variant >= tc_stage_variants(stage) || ctas_per_sm < 0)
+        return fail(NSM_ERR_INVALID_ARG, "stage 0..%d, variant 0..nsm_plan_variants(stage)-1, ctas_per_sm >= 0",
+                    kTcStages - 1);
+    c->tc_variant[stage] = variant;
+    c->tc_ctas[stage] = ctas_per_sm;
+    c->tc_ms[stage] = 0.f;
+    ctx_release_graph(c);  // the plan changed
+    return NSM_OK;
+}
+
+nsm_status nsm_autotune_report_order(nsm_ctx* c, int* mma_order_out) {
+    if (!c || !mma_order_out) return fail(NSM_ERR_INVALID_ARG, "ctx and mma_order_out must be non-NULL");
+    for (int k = 0; k < kTcStages; ++k) mma_order_out[k] = tc_stage_order(k, c->tc_variant[k]);
+    return NSM_OK;
+}
+
 }  // extern "C"

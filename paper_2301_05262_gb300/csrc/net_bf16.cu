@@ -400,7 +400,7 @@ __device__ __forceinline__ void stage_flush(uint32_t stg, int lane, float* gdst,
     }
 }
 
-template <int CIN, int CMID, int COUT, int R, int PRO, int EPI, int NEW, int NPW, int KS>
+template <int CIN, int CMID, int COUT, int R, int PRO, int EPI, int NEW, int NPW, int KS, int ORD>
 __global__ void __launch_bounds__(32 * (NEW + NPW + 1), 1) level_tc_kernel(const __grid_constant__ TcBatch a) {
     using C = TcCfg<CIN, CMID, COUT, R, PRO, KS>;
     constexpr int NP = 32 * NPW, NT = 32 * (NEW + NPW + 1), MW = NEW + NPW, NE = 32 * NEW;
@@ -561,6 +561,26 @@ __global__ void __launch_bounds__(32 * (NEW + NPW + 1), 1) level_tc_kernel(const
             constexpr uint32_t id1 = idesc_bf16(128, C::N1);
             constexpr uint32_t kPlane = C::PLANE;
             constexpr int kA1Part = (CMID / 8) * kTileM;
+            // 1x1 of tile index j once the epilogue has written its operand:
+            // (A_hi + A_lo) [B_hi; B_lo] into the tile's accumulator buffer
+            auto issue_1x1 = [&](int j) -> bool {
+                if (!wait_phase(a1full, j & 1, s_abort)) return false;
+                fence_after_sync();
+                const uint32_t Dj = tbase + (j & 1) * C::TMEM_BUF;
+                for (int r = 0; r < R; ++r) {
+                    const uint32_t row = sA1 + 16 * (r * 2 * kA1Part);
+#pragma unroll
+                    for (int kk = 0; kk < CMID / 16; ++kk) {
+                        const uint64_t ahi = smem_desc(row + 16 * (2 * kk * kTileM), kTileM * 16, 128);
+                        const uint64_t alo = smem_desc(row + 16 * (kA1Part + 2 * kk * kTileM), kTileM * 16, 128);
+                        const uint64_t bd = smem_desc(sB1 + 16 * (2 * kk * C::N1), C::N1 * 16, 128);
+                        mma_bf16(Dj + r * C::N3, ahi, bd, id1, kk > 0);
+                        mma_bf16(Dj + r * C::N3, alo, bd, id1, 1);
+                    }
+                }
+                mma_commit(mma1);
+                return true;
+            };
             int it = 0, v = 0, ring = 0;
             bool failed = false;
             for (int tile = t_lo; tile < t_hi; ++tile, ++it) {
@@ -640,25 +660,15 @@ __global__ void __launch_bounds__(32 * (NEW + NPW + 1), 1) level_tc_kernel(const
                 }
                 if (failed) break;
                 mma_commit(accf + tb);     // 3x3 accumulators of this tile complete
-                // 1x1 once the epilogue has written its operand: (A_hi + A_lo) [B_hi; B_lo]
-                if (!wait_phase(a1full, it & 1, s_abort)) {
+                // ORD 0: this tile's 1x1 next; ORD 1: the previous tile's 1x1 now, so
+                // that this tile's 3x3 runs on the tensor core while the epilogue
+                // prepares the previous tile's 1x1 operand
+                if (ORD == 0 ? !issue_1x1(it) : (it > 0 && !issue_1x1(it - 1))) {
                     failed = true;
                     break;
                 }
-                fence_after_sync();
-                for (int r = 0; r < R; ++r) {
-                    const uint32_t row = sA1 + 16 * (r * 2 * kA1Part);
-#pragma unroll
-                    for (int kk = 0; kk < CMID / 16; ++kk) {
-                        const uint64_t ahi = smem_desc(row + 16 * (2 * kk * kTileM), kTileM * 16, 128);
-                        const uint64_t alo = smem_desc(row + 16 * (kA1Part + 2 * kk * kTileM), kTileM * 16, 128);
-                        const uint64_t bd = smem_desc(sB1 + 16 * (2 * kk * C::N1), C::N1 * 16, 128);
-                        mma_bf16(D + r * C::N3, ahi, bd, id1, kk > 0);
-                        mma_bf16(D + r * C::N3, alo, bd, id1, 1);
-                    }
-                }
-                mma_commit(mma1);
             }
+            if (ORD == 1 && !failed && it > 0 && !issue_1x1(it - 1)) failed = true;
             if (failed) {
                 atomicExch(a.err, 4);
                 *s_abort = 1;
@@ -862,10 +872,10 @@ __global__ void __launch_bounds__(32 * (NEW + NPW + 1), 1) level_tc_kernel(const
 }
 
 // ------------------------------------------------------------------ variants and launch
-template <int CIN, int CMID, int COUT, int R, int PRO, int EPI, int NEW, int NPW, int KS>
+template <int CIN, int CMID, int COUT, int R, int PRO, int EPI, int NEW, int NPW, int KS, int ORD>
 static cudaError_t launch_variant(const TcBatch& a, int ctas_per_sm, cudaStream_t stream) {
     using C = TcCfg<CIN, CMID, COUT, R, PRO, KS>;
-    auto kern = level_tc_kernel<CIN, CMID, COUT, R, PRO, EPI, NEW, NPW, KS>;
+    auto kern = level_tc_kernel<CIN, CMID, COUT, R, PRO, EPI, NEW, NPW, KS, ORD>;
     static int occ = -1;
     if (occ < 0) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::BYTES);
@@ -892,16 +902,16 @@ static cudaError_t launch_variant(const TcBatch& a, int ctas_per_sm, cudaStream_
     return cudaGetLastError();
 }
 
-template <int CIN, int CMID, int COUT, int R, int PRO, int EPI, int NEW, int NPW, int KS>
+template <int CIN, int CMID, int COUT, int R, int PRO, int EPI, int NEW, int NPW, int KS, int ORD>
 static const void* kernel_of() {
-    return reinterpret_cast<const void*>(level_tc_kernel<CIN, CMID, COUT, R, PRO, EPI, NEW, NPW, KS>);
+    return reinterpret_cast<const void*>(level_tc_kernel<CIN, CMID, COUT, R, PRO, EPI, NEW, NPW, KS, ORD>);
 }
 
-template <int CIN, int CMID, int COUT, int R, int PRO, int EPI, int NEW, int NPW, int KS>
+template <int CIN, int CMID, int COUT, int R, int PRO, int EPI, int NEW, int NPW, int KS, int ORD>
 static int occupancy_of() {
     using C = TcCfg<CIN, CMID, COUT, R, PRO, KS>;
     cudaFuncAttributes fa{};
-    if (cudaFuncGetAttributes(&fa, level_tc_kernel<CIN, CMID, COUT, R, PRO, EPI, NEW, NPW, KS>) != cudaSuccess) return 1;
+    if (cudaFuncGetAttributes(&fa, level_tc_kernel<CIN, CMID, COUT, R, PRO, EPI, NEW, NPW, KS, ORD>) != cudaSuccess) return 1;
     const int regs = ((fa.numRegs + 7) / 8) * 8 * (32 * (NEW + NPW + 1));
     const int by_regs = regs > 0 ? 65536 / regs : 8;
     const int by_smem = (228 * 1024) / (C::BYTES + 1024);
@@ -914,38 +924,42 @@ static int occupancy_of() {
 // Variant tables: tile height R and warp roles of every stage (the
 // autotuner's search space).
 using LaunchFn = cudaError_t (*)(const TcBatch&, int, cudaStream_t);
-struct Variant { int R, ew, pw, ks; LaunchFn fn; const void* (*func)(); int (*occ)(); };
-#define NSM_VARIANT(R_, EW_, PW_, KS_, CIN_, CMID_, COUT_, PRO_, EPI_)                                   \
-    {R_, EW_, PW_, KS_, launch_variant<CIN_, CMID_, COUT_, R_, PRO_, EPI_, EW_, PW_, KS_>,                \
-     kernel_of<CIN_, CMID_, COUT_, R_, PRO_, EPI_, EW_, PW_, KS_>,                                        \
-     occupancy_of<CIN_, CMID_, COUT_, R_, PRO_, EPI_, EW_, PW_, KS_>}
+struct Variant { int R, ew, pw, ks, ord; LaunchFn fn; const void* (*func)(); int (*occ)(); };
+#define NSM_VARIANT(R_, EW_, PW_, KS_, ORD_, CIN_, CMID_, COUT_, PRO_, EPI_)                              \
+    {R_, EW_, PW_, KS_, ORD_, launch_variant<CIN_, CMID_, COUT_, R_, PRO_, EPI_, EW_, PW_, KS_, ORD_>,      \
+     kernel_of<CIN_, CMID_, COUT_, R_, PRO_, EPI_, EW_, PW_, KS_, ORD_>,                                  \
+     occupancy_of<CIN_, CMID_, COUT_, R_, PRO_, EPI_, EW_, PW_, KS_, ORD_>}
+// both MMA schedules of one tile shape / warp split
+#define NSM_VARIANT2(R_, EW_, PW_, KS_, CIN_, CMID_, COUT_, PRO_, EPI_)                                   \
+    NSM_VARIANT(R_, EW_, PW_, KS_, 0, CIN_, CMID_, COUT_, PRO_, EPI_),                                     \
+    NSM_VARIANT(R_, EW_, PW_, KS_, 1, CIN_, CMID_, COUT_, PRO_, EPI_)
 
-// (rows, epilogue warps, producer warps, K slices, C_in, C_mid, C_out, prologue, epilogue)
+// (rows, epilogue warps, producer warps, K slices, [MMA order,] C_in, C_mid, C_out, prologue, epilogue)
 static const Variant kVarEnc0[] = {
-    NSM_VARIANT(4, 4, 8, 1, 4, 16, 16, TPRO_GATHER, TEPI_POOL),
-    NSM_VARIANT(4, 8, 8, 1, 4, 16, 16, TPRO_GATHER, TEPI_POOL),
-    NSM_VARIANT(8, 4, 8, 1, 4, 16, 16, TPRO_GATHER, TEPI_POOL),
-    NSM_VARIANT(8, 4, 16, 1, 4, 16, 16, TPRO_GATHER, TEPI_POOL),
-    NSM_VARIANT(8, 8, 12, 1, 4, 16, 16, TPRO_GATHER, TEPI_POOL)};
+    NSM_VARIANT(4, 4, 8, 1, 0, 4, 16, 16, TPRO_GATHER, TEPI_POOL),
+    NSM_VARIANT(4, 8, 8, 1, 0, 4, 16, 16, TPRO_GATHER, TEPI_POOL),
+    NSM_VARIANT2(8, 4, 8, 1, 4, 16, 16, TPRO_GATHER, TEPI_POOL),
+    NSM_VARIANT2(8, 4, 16, 1, 4, 16, 16, TPRO_GATHER, TEPI_POOL),
+    NSM_VARIANT(8, 8, 12, 1, 0, 4, 16, 16, TPRO_GATHER, TEPI_POOL)};
 static const Variant kVarEnc1[] = {
-    NSM_VARIANT(2, 4, 8, 1, 16, 32, 32, TPRO_PLAIN, TEPI_SKIP_POOL),
-    NSM_VARIANT(2, 8, 8, 1, 16, 32, 32, TPRO_PLAIN, TEPI_SKIP_POOL),
-    NSM_VARIANT(4, 4, 8, 1, 16, 32, 32, TPRO_PLAIN, TEPI_SKIP_POOL),
-    NSM_VARIANT(4, 8, 8, 1, 16, 32, 32, TPRO_PLAIN, TEPI_SKIP_POOL)};
+    NSM_VARIANT(2, 4, 8, 1, 0, 16, 32, 32, TPRO_PLAIN, TEPI_SKIP_POOL),
+    NSM_VARIANT(2, 8, 8, 1, 0, 16, 32, 32, TPRO_PLAIN, TEPI_SKIP_POOL),
+    NSM_VARIANT2(4, 4, 8, 1, 16, 32, 32, TPRO_PLAIN, TEPI_SKIP_POOL),
+    NSM_VARIANT2(4, 8, 8, 1, 16, 32, 32, TPRO_PLAIN, TEPI_SKIP_POOL)};
 static const Variant kVarBott[] = {
-    NSM_VARIANT(1, 4, 8, 1, 32, 64, 32, TPRO_PLAIN, TEPI_STORE),
-    NSM_VARIANT(2, 4, 8, 2, 32, 64, 32, TPRO_PLAIN, TEPI_STORE),
-    NSM_VARIANT(2, 8, 8, 2, 32, 64, 32, TPRO_PLAIN, TEPI_STORE)};
+    NSM_VARIANT(1, 4, 8, 1, 0, 32, 64, 32, TPRO_PLAIN, TEPI_STORE),
+    NSM_VARIANT2(2, 4, 8, 2, 32, 64, 32, TPRO_PLAIN, TEPI_STORE),
+    NSM_VARIANT2(2, 8, 8, 2, 32, 64, 32, TPRO_PLAIN, TEPI_STORE)};
 static const Variant kVarDec1[] = {
-    NSM_VARIANT(2, 4, 8, 2, 32, 32, 16, TPRO_UP_SKIP, TEPI_STORE),
-    NSM_VARIANT(2, 8, 8, 2, 32, 32, 16, TPRO_UP_SKIP, TEPI_STORE)};
+    NSM_VARIANT2(2, 4, 8, 2, 32, 32, 16, TPRO_UP_SKIP, TEPI_STORE),
+    NSM_VARIANT2(2, 8, 8, 2, 32, 32, 16, TPRO_UP_SKIP, TEPI_STORE)};
 static const Variant kVarDec0[] = {
-    NSM_VARIANT(4, 4, 8, 1, 16, 16, 16, TPRO_UP, TEPI_HEAD),
-    NSM_VARIANT(4, 8, 8, 1, 16, 16, 16, TPRO_UP, TEPI_HEAD),
-    NSM_VARIANT(4, 8, 12, 1, 16, 16, 16, TPRO_UP, TEPI_HEAD)};
+    NSM_VARIANT2(4, 4, 8, 1, 16, 16, 16, TPRO_UP, TEPI_HEAD),
+    NSM_VARIANT2(4, 8, 8, 1, 16, 16, 16, TPRO_UP, TEPI_HEAD),
+    NSM_VARIANT(4, 8, 12, 1, 0, 16, 16, 16, TPRO_UP, TEPI_HEAD)};
 
 static const Variant kVarDec1Head4[] = {
-    NSM_VARIANT(2, 4, 8, 2, 32, 32, 16, TPRO_UP_SKIP, TEPI_HEAD4)};
+    NSM_VARIANT2(2, 4, 8, 2, 32, 32, 16, TPRO_UP_SKIP, TEPI_HEAD4)};
 
 struct StageTable { const Variant* v; int n; };
 #define NSM_STAGE(t) {t, static_cast<int>(sizeof(t) / sizeof(t[0]))}
@@ -957,6 +971,8 @@ int tc_stage_rows(int stage, int variant) { return kStages[stage].v[variant].R; 
 const void* tc_stage_kernel(int stage, int variant) { return kStages[stage].v[variant].func(); }
 int tc_stage_occupancy(int stage, int variant) { return kStages[stage].v[variant].occ(); }
 
+int tc_stage_order(int stage, int variant) { return kStages[stage].v[variant].ord; }
+
 int tc_stage_warps(int stage, int variant, int* producer_warps) {
     if (producer_warps) *producer_warps = kStages[stage].v[variant].pw;
     return kStages[stage].v[variant].ew;
@@ -964,7 +980,7 @@ int tc_stage_warps(int stage, int variant, int* producer_warps) {
 
 int tc_default_variant(int stage) {
     // the fastest plan of the 1080p autotuning runs
-    static const int def[kTcStages] = {3, 2, 2, 0, 1};
+    static const int def[kTcStages] = {2, 5, 4, 0, 2};
     return def[stage];
 }
 

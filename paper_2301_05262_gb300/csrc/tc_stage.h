@@ -57,6 +57,9 @@ struct Activations;
 int tc_stage_variants(int stage);
 int tc_stage_rows(int stage, int variant);
 int tc_stage_warps(int stage, int variant, int* producer_warps);  // epilogue warps
+// MMA schedule: 0 = a tile's 1x1 right after its 3x3; 1 = the next tile's 3x3
+// first, then the previous tile's 1x1 (overlaps the epilogue's 3x3 read-out)
+int tc_stage_order(int stage, int variant);
 int tc_default_variant(int stage);
 const void* tc_stage_kernel(int stage, int variant);
 int tc_stage_occupancy(int stage, int variant);

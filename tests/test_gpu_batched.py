@@ -100,3 +100,26 @@ def test_batched_rejects_too_many_views(ctx):
     with pytest.raises(nsm.NSMError) as ei:
         nsm.nsm_infer_batched(ctx, views, w, ws)
     assert ei.value.status == 2
+
+
+def test_every_stage_variant_matches_the_default_plan():
+    """Each tile variant of each tensor-core stage (tile height, warp roles, K
+    slices, MMA schedule) gives the default plan's visibility on a ragged soft
+    frame, to FP32 accumulation-order noise (K slices change the order)."""
+    c = nsm.Context()
+    f = scenegen.soft_frame(100, 300, 256, 256, 8, 5)
+    w = nsm.Weights(c, scenegen.trained_weights())
+    df = DeviceFrame(f)
+    ref = run_infer(c, w, df, nsm.NSM_BF16).cpu().numpy()
+    for stage in range(5):
+        n = nsm.nsm_plan_variants(stage)
+        assert n >= 2
+        for v in range(n):
+            nsm.nsm_plan_set(c, stage, v, 1)
+            out = run_infer(c, w, df, nsm.NSM_BF16).cpu().numpy()
+            assert np.abs(out - ref).max() <= 1e-4, (stage, v, np.abs(out - ref).max())
+        nsm.nsm_plan_set(c, stage, 0, 0)
+    assert nsm.nsm_plan_variants(5) == 0
+    with pytest.raises(nsm.NSMError):
+        nsm.nsm_plan_set(c, 0, 99, 0)
+    c.check()
