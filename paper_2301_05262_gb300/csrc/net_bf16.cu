@@ -367,7 +367,12 @@ __device__ __forceinline__ void compute_up(const TcJob& job, int y0, int x0, uin
         else
             up_column<CIN, R, KS, SKIP, R, NRW>(job, y0, x0, raw, a0, s, 1 + i % kTileM, i / kTileM, 2, base);
     }
-    for (int i = pt; i < 2 * CGS * nrows; i += NP) {
+    // halo items go to the threads without an interior item when there are
+    // enough of them (their loads then overlap the interior items' instead of
+    // following them on the same threads)
+    const int nhalo = 2 * CGS * nrows;
+    const int hp = NP - MAIN >= nhalo ? pt - MAIN : pt;
+    for (int i = hp; i >= 0 && i < nhalo; i += NP) {
         const int sr = first + i % nrows, q = i / nrows;
         up_column<CIN, R, KS, SKIP, 1, NRW>(job, y0, x0, raw, a0, s, (q / CGS) ? 129 : 0, q % CGS, sr, base);
     }
@@ -952,11 +957,15 @@ static const Variant kVarBott[] = {
     NSM_VARIANT2(2, 8, 8, 2, 32, 64, 32, TPRO_PLAIN, TEPI_STORE)};
 static const Variant kVarDec1[] = {
     NSM_VARIANT2(2, 4, 8, 2, 32, 32, 16, TPRO_UP_SKIP, TEPI_STORE),
-    NSM_VARIANT2(2, 8, 8, 2, 32, 32, 16, TPRO_UP_SKIP, TEPI_STORE)};
+    NSM_VARIANT2(2, 8, 8, 2, 32, 32, 16, TPRO_UP_SKIP, TEPI_STORE),
+    NSM_VARIANT(2, 4, 9, 2, 0, 32, 32, 16, TPRO_UP_SKIP, TEPI_STORE),
+    NSM_VARIANT(2, 8, 9, 2, 0, 32, 32, 16, TPRO_UP_SKIP, TEPI_STORE)};
 static const Variant kVarDec0[] = {
     NSM_VARIANT2(4, 4, 8, 1, 16, 16, 16, TPRO_UP, TEPI_HEAD),
     NSM_VARIANT2(4, 8, 8, 1, 16, 16, 16, TPRO_UP, TEPI_HEAD),
-    NSM_VARIANT(4, 8, 12, 1, 0, 16, 16, 16, TPRO_UP, TEPI_HEAD)};
+    NSM_VARIANT(4, 8, 12, 1, 0, 16, 16, 16, TPRO_UP, TEPI_HEAD),
+    NSM_VARIANT(4, 8, 9, 1, 0, 16, 16, 16, TPRO_UP, TEPI_HEAD),
+    NSM_VARIANT(4, 4, 9, 1, 0, 16, 16, 16, TPRO_UP, TEPI_HEAD)};
 
 static const Variant kVarDec1Head4[] = {
     NSM_VARIANT2(2, 4, 8, 2, 32, 32, 16, TPRO_UP_SKIP, TEPI_HEAD4)};
@@ -980,7 +989,7 @@ int tc_stage_warps(int stage, int variant, int* producer_warps) {
 
 int tc_default_variant(int stage) {
     // the fastest plan of the 1080p autotuning runs
-    static const int def[kTcStages] = {2, 5, 4, 0, 2};
+    static const int def[kTcStages] = {2, 5, 4, 4, 2};
     return def[stage];
 }
 
