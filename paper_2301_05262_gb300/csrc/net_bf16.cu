@@ -86,12 +86,16 @@ struct TcCfg {
     static constexpr int PLN = SPLIT ? 1 : 2 * CGS;
     static constexpr int KSTEPS3 = SPLIT ? 5 : 9 * (CIN / 16);
     static constexpr int A0_CHUNKS = PLN * (R + 2) * kSW;        // one input buffer
-    // KS == 1: the two input buffers form one ring of 2 (R + 2) staged rows per
-    // plane, so a tile that continues the previous one down its column reuses
-    // the two overlapping rows and stages only R new ones; KS > 1: two buffers
-    // of R + 2 rows, one K slice each
-    static constexpr bool RING = (KS == 1);
-    static constexpr int NRW = RING ? 2 * (R + 2) : R + 2;      // staged rows per plane
+    // Staged rows form rings, so a tile that continues the previous one down
+    // its column reuses the two overlapping rows and stages only R new ones.
+    // KS == 1: the two input buffers form one ring of 2 (R + 2) rows per plane
+    // (the next tile's rows are staged while the MMAs read the current ones);
+    // KS > 1: each input buffer holds one K slice as its own ring of R + 2
+    // rows, refilled once the MMAs of the same slice of the previous tile are
+    // done (the new rows take the slots of that tile's rows 0 .. R - 1)
+    static constexpr bool RING = true;
+    static constexpr bool ONE_RING = (KS == 1);
+    static constexpr int NRW = ONE_RING ? 2 * (R + 2) : R + 2;  // staged rows per plane
     static constexpr uint32_t PLANE = NRW * kSW * 16;            // bytes per plane
     // 3x3 -> 1x1 intermediate as BF16 hi + lo parts: [row][part][channel group][pixel]
     static constexpr int A1_CHUNKS = R * 2 * (CMID / 8) * kTileM;
@@ -478,8 +482,9 @@ __global__ void __launch_bounds__(32 * (NEW + NPW + 1), 1) level_tc_kernel(const
         cont = C::RING && tile > t_lo && ys > 0;
         return job;
     };
-    // ring slots (KS == 1): staged row 0 of a tile sits in slot `base`; the
-    // counter `ring` is the slot after the last staged row produced so far
+    // ring slots: staged row 0 of a tile sits in slot `base` (of every plane,
+    // and of both slice buffers when KS > 1); the counter `ring` is the slot
+    // after the last staged row produced so far
     auto ring_next = [&](bool cont, int& ring, int& base, int& first) {
         if constexpr (C::RING) {
             first = cont ? 2 : 0;
@@ -536,7 +541,7 @@ __global__ void __launch_bounds__(32 * (NEW + NPW + 1), 1) level_tc_kernel(const
 #pragma unroll 1
             for (int s = 0; s < KS; ++s) {
                 const int st = it * KS + s, b = st & 1;
-                const uint32_t A0 = C::RING ? sA0 : sA0 + b * (C::A0_CHUNKS * 16);
+                const uint32_t A0 = C::ONE_RING ? sA0 : sA0 + b * (C::A0_CHUNKS * 16);
                 // the rows written now are free once the MMAs of step st - 2 are done
                 if (st >= 2 && !wait_phase(mma3 + b, ((st >> 1) - 1) & 1, s_abort)) { failed = true; break; }
                 if constexpr (PRO == TPRO_PLAIN) {
@@ -605,7 +610,7 @@ __global__ void __launch_bounds__(32 * (NEW + NPW + 1), 1) level_tc_kernel(const
                     }
                     fence_proxy_async_smem();  // cp.async / st.shared data -> tensor core
                     fence_after_sync();
-                    const uint32_t A0 = C::RING ? sA0 : sA0 + b * (C::A0_CHUNKS * 16);
+                    const uint32_t A0 = C::ONE_RING ? sA0 : sA0 + b * (C::A0_CHUNKS * 16);
                     if constexpr (C::STACK) {
                         // clear the R x N3 accumulator columns (zero A operand), then
                         // one MMA per (staged row j, K step) of width (#ky) x N3:
