@@ -13,8 +13,9 @@
 //   conv_fwd   y = conv(x~) (+ b) (masked by m > 0), x~ = x, relu(x) or x (m_in > 0);
 //              also the data gradient, as a convolution with the transposed,
 //              flipped weights;
-//   conv_wgrad dW += sum_p g~(p) x~(p + tap), db += sum_p g~(p), partial sums per
-//              CTA in shared memory, one atomicAdd per weight per CTA;
+//   conv_wgrad dW += sum_p g~(p) x~(p + tap), db += sum_p g~(p): 4 x 4 register
+//              blocks of outer products per thread, one atomicAdd per weight
+//              per CTA;
 //   pooling, bilinear x2 and their adjoints, head, loss, Adam.
 #include <vector>
 
@@ -24,7 +25,6 @@
 namespace nsm {
 namespace tr {
 
-constexpr int TH = 8, TW = 16, NT = TH * TW;  // pixel tile of the conv kernels, one pixel per thread
 
 // ------------------------------------------------------------------ convolution
 // y[n,p,o] = b[o] + sum_{c,tap} Wc[o][c][tap] * xin(n, p + off(tap), c), zero padded,
@@ -32,17 +32,30 @@ constexpr int TH = 8, TW = 16, NT = TH * TW;  // pixel tile of the conv kernels,
 // Weights come as canonical OIHW (transpose_flip = 0) or as the weights of the
 // layer whose data gradient this is (transpose_flip = 1): Wc[o][c][tap] =
 // W[c][o][8 - tap].
+// Tile: 8 rows x 16 PX columns; thread (r, j) computes the PX pixels of row r
+// at columns j, j + 16, ... (neighbouring threads read neighbouring words) for
+// every output; per (tap, input channel) PX input words and COUT / 4
+// broadcast float4 weight words feed PX COUT FMAs.  The input tile is staged
+// as channel planes with an odd plane stride (conflict-free transposing
+// stores from 16-byte NHWC loads).
+constexpr int TH = 8, TJ = 16, NT = TH * TJ;  // conv tile rows, threads per row
+
+// pixels per thread: 4, or 2 where 64 channels in or out would need too many
+// accumulators or too much shared memory
+template <int CIN, int COUT>
+struct FwdShape { static constexpr int PX = (COUT >= 64 || CIN >= 64) ? 2 : 4; };
+
 template <int CIN, int COUT, int K>
 __global__ void __launch_bounds__(NT) conv_fwd_kernel(const float* __restrict__ x, const float* __restrict__ xm,
                                                       int relu_in, int N, int H, int W,
                                                       const float* __restrict__ w, int transpose_flip,
                                                       const float* __restrict__ b, const float* __restrict__ ym,
                                                       float* __restrict__ y) {
-    constexpr int P = K / 2;
-    constexpr int RH = TH + 2 * P, RW = TW + 2 * P, PLANE = RH * RW;
+    constexpr int P = K / 2, PX = FwdShape<CIN, COUT>::PX, TW = TJ * PX;
+    constexpr int RH = TH + 2 * P, RW = TW + 2 * P, PS = (RH * RW) | 1;  // odd plane stride
     extern __shared__ float sm[];
-    float* xs = sm;                       // [CIN][RH][RW]
-    float* ws = xs + CIN * PLANE;         // [tap][ci][co]
+    float* xs = sm;                       // [CIN][PS]
+    float* ws = xs + CIN * PS;            // [tap][ci][co]
     const int tid = threadIdx.x;
     for (int i = tid; i < K * K * CIN * COUT; i += NT) {
         const int co = i % COUT, ci = (i / COUT) % CIN, tap = i / (COUT * CIN);
@@ -51,126 +64,213 @@ __global__ void __launch_bounds__(NT) conv_fwd_kernel(const float* __restrict__ 
     }
     const int tx = (W + TW - 1) / TW, ty = (H + TH - 1) / TH;
     const long long ntiles = static_cast<long long>(N) * tx * ty;
+    const int lr = tid / TJ, lj = tid % TJ;
     for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const int n = static_cast<int>(t / (tx * ty));
         const int r = static_cast<int>(t % (tx * ty));
         const int y0 = (r / tx) * TH, x0 = (r % tx) * TW;
         __syncthreads();
-        for (int i = tid; i < PLANE * CIN; i += NT) {
-            const int c = i % CIN, q = i / CIN;
+        for (int i = tid; i < RH * RW * (CIN / 4); i += NT) {
+            const int c4 = i % (CIN / 4), q = i / (CIN / 4);
             const int gy = y0 - P + q / RW, gx = x0 - P + q % RW;
-            float v = 0.f;
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
             if (gy >= 0 && gy < H && gx >= 0 && gx < W) {
-                const size_t idx = ((static_cast<size_t>(n) * H + gy) * W + gx) * CIN + c;
-                v = __ldg(x + idx);
-                if (relu_in) v = fmaxf(v, 0.f);
-                if (xm && !(__ldg(xm + idx) > 0.f)) v = 0.f;
+                const size_t idx = ((static_cast<size_t>(n) * H + gy) * W + gx) * CIN;
+                v = __ldg(reinterpret_cast<const float4*>(x + idx) + c4);
+                if (relu_in) v = make_float4(fmaxf(v.x, 0.f), fmaxf(v.y, 0.f), fmaxf(v.z, 0.f), fmaxf(v.w, 0.f));
+                if (xm) {
+                    const float4 m = __ldg(reinterpret_cast<const float4*>(xm + idx) + c4);
+                    v = make_float4(m.x > 0.f ? v.x : 0.f, m.y > 0.f ? v.y : 0.f, m.z > 0.f ? v.z : 0.f,
+                                    m.w > 0.f ? v.w : 0.f);
+                }
             }
-            xs[c * PLANE + q] = v;
+            xs[(4 * c4 + 0) * PS + q] = v.x;
+            xs[(4 * c4 + 1) * PS + q] = v.y;
+            xs[(4 * c4 + 2) * PS + q] = v.z;
+            xs[(4 * c4 + 3) * PS + q] = v.w;
         }
         __syncthreads();
-        const int ly = tid / TW, lx = tid % TW;
-        const int oy = y0 + ly, ox = x0 + lx;
-        float acc[COUT];
+        float acc[PX][COUT];
 #pragma unroll
-        for (int o = 0; o < COUT; ++o) acc[o] = b ? __ldg(b + o) : 0.f;
+        for (int o = 0; o < COUT; ++o) {
+            const float bo = b ? __ldg(b + o) : 0.f;
+#pragma unroll
+            for (int p = 0; p < PX; ++p) acc[p][o] = bo;
+        }
 #pragma unroll
         for (int tap = 0; tap < K * K; ++tap) {
-            const float* xin = xs + (ly + tap / K) * RW + (lx + tap % K);
-            const float* wt = ws + tap * CIN * COUT;
-#pragma unroll 4
+            const float* xin = xs + (lr + tap / K) * RW + (lj + tap % K);
+            const float4* wt = reinterpret_cast<const float4*>(ws + tap * CIN * COUT);
+#pragma unroll 2
             for (int c = 0; c < CIN; ++c) {
-                const float xv = xin[c * PLANE];
+                float xv[PX];
 #pragma unroll
-                for (int o = 0; o < COUT; ++o) acc[o] = fmaf(xv, wt[c * COUT + o], acc[o]);
+                for (int p = 0; p < PX; ++p) xv[p] = xin[c * PS + TJ * p];
+#pragma unroll
+                for (int o4 = 0; o4 < COUT / 4; ++o4) {
+                    const float4 wv = wt[c * (COUT / 4) + o4];
+#pragma unroll
+                    for (int p = 0; p < PX; ++p) {
+                        acc[p][4 * o4 + 0] = fmaf(xv[p], wv.x, acc[p][4 * o4 + 0]);
+                        acc[p][4 * o4 + 1] = fmaf(xv[p], wv.y, acc[p][4 * o4 + 1]);
+                        acc[p][4 * o4 + 2] = fmaf(xv[p], wv.z, acc[p][4 * o4 + 2]);
+                        acc[p][4 * o4 + 3] = fmaf(xv[p], wv.w, acc[p][4 * o4 + 3]);
+                    }
+                }
             }
         }
-        if (oy < H && ox < W) {
-            const size_t base = ((static_cast<size_t>(n) * H + oy) * W + ox) * COUT;
+        const int oy = y0 + lr;
 #pragma unroll
-            for (int o = 0; o < COUT; ++o) {
-                float v = acc[o];
-                if (ym && !(__ldg(ym + base + o) > 0.f)) v = 0.f;
-                y[base + o] = v;
+        for (int p = 0; p < PX; ++p) {
+            const int ox = x0 + lj + TJ * p;
+            if (oy < H && ox < W) {
+                const size_t base = ((static_cast<size_t>(n) * H + oy) * W + ox) * COUT;
+#pragma unroll
+                for (int o4 = 0; o4 < COUT / 4; ++o4) {
+                    float4 v = make_float4(acc[p][4 * o4], acc[p][4 * o4 + 1], acc[p][4 * o4 + 2], acc[p][4 * o4 + 3]);
+                    if (ym) {
+                        const float4 m = __ldg(reinterpret_cast<const float4*>(ym + base) + o4);
+                        v = make_float4(m.x > 0.f ? v.x : 0.f, m.y > 0.f ? v.y : 0.f, m.z > 0.f ? v.z : 0.f,
+                                        m.w > 0.f ? v.w : 0.f);
+                    }
+                    reinterpret_cast<float4*>(y + base)[o4] = v;
+                }
             }
         }
     }
 }
 
-// dW[o][c][tap] += sum_p g~[p][o] xin[p + off(tap)][c];  db[o] += sum_p g~[p][o]
-// g~ = g * (gm > 0) if gm.  Each CTA keeps the partial sums of all weights in
-// shared memory over the tiles it visits, then adds them to dW / db once.
+// dW[o][c][tap] += sum_p g~[p][o] xin[p + off(tap)][c];  db[o] += sum_p g~[p][o],
+// g~ = g * (gm > 0) if gm.  Register-blocked outer products: the weights are
+// cut into blocks of 4 outputs x 4 inputs of one tap; thread t owns blocks
+// t, t + WNT, ... (16 accumulators each, kept in registers over every tile
+// the CTA visits) and, when there are fewer blocks than threads, one residue
+// class of the tile's pixels.  Per pixel a block takes one 16-byte load of g~
+// (4 outputs) and one of xin (4 inputs) for 16 FMAs.  Pixel classes meet in
+// shared memory at the end; one atomicAdd per weight per CTA.
+constexpr int WTH = 8, WTW = 32, WNT = 256;  // wgrad pixel tile, threads
+
 template <int CIN, int COUT, int K>
-__global__ void __launch_bounds__(NT) conv_wgrad_kernel(const float* __restrict__ x, int relu_in,
-                                                        const float* __restrict__ g, const float* __restrict__ gm,
-                                                        int N, int H, int W, float* __restrict__ dW,
-                                                        float* __restrict__ db) {
+__global__ void __launch_bounds__(WNT) conv_wgrad_kernel(const float* __restrict__ x, int relu_in,
+                                                         const float* __restrict__ g, const float* __restrict__ gm,
+                                                         int N, int H, int W, float* __restrict__ dW,
+                                                         float* __restrict__ db) {
     constexpr int P = K / 2;
-    constexpr int RH = TH + 2 * P, RW = TW + 2 * P, PLANE = RH * RW;
-    constexpr int NW = COUT * CIN * K * K;
-    extern __shared__ float sm[];
-    float* xs = sm;                 // [CIN][RH][RW]
-    float* gs = xs + CIN * PLANE;   // [COUT][TH*TW]
-    float* acc = gs + COUT * NT;    // [NW + COUT]
+    constexpr int RH = WTH + 2 * P, RW = WTW + 2 * P, NPX = WTH * WTW;
+    constexpr int OB = COUT / 4, CB = CIN / 4, TAPS = K * K;
+    constexpr int NB = TAPS * OB * CB;                  // weight blocks
+    constexpr int PL = NB >= WNT ? 1 : WNT / NB;        // pixel classes
+    constexpr int NBT = (NB + WNT - 1) / WNT;           // blocks per thread
+    constexpr int NW = NB * 16;
+    static_assert(CIN % 4 == 0 && COUT % 4 == 0, "channel blocks of 4");
+    static_assert(PL == 1 || NW <= RH * RW * CIN, "pixel-class reduction reuses the input tile");
+    extern __shared__ float4 sm4[];
+    float* xs = reinterpret_cast<float*>(sm4);  // [RH][RW][CIN]
+    float* gs = xs + RH * RW * CIN;             // [NPX][COUT]
+    float* dbs = gs + NPX * COUT;               // [COUT]
     const int tid = threadIdx.x;
-    for (int i = tid; i < NW + COUT; i += NT) acc[i] = 0.f;
-    const int tx = (W + TW - 1) / TW, ty = (H + TH - 1) / TH;
+    const int pl = PL == 1 ? 0 : tid / NB;
+    const bool active = PL == 1 || tid < NB * PL;
+    float acc[NBT][16];
+#pragma unroll
+    for (int k = 0; k < NBT; ++k)
+#pragma unroll
+        for (int e = 0; e < 16; ++e) acc[k][e] = 0.f;
+    for (int i = tid; i < COUT; i += WNT) dbs[i] = 0.f;
+    const int tx = (W + WTW - 1) / WTW, ty = (H + WTH - 1) / WTH;
     const long long ntiles = static_cast<long long>(N) * tx * ty;
     for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const int n = static_cast<int>(t / (tx * ty));
         const int r = static_cast<int>(t % (tx * ty));
-        const int y0 = (r / tx) * TH, x0 = (r % tx) * TW;
+        const int y0 = (r / tx) * WTH, x0 = (r % tx) * WTW;
         __syncthreads();
-        for (int i = tid; i < PLANE * CIN; i += NT) {
-            const int c = i % CIN, q = i / CIN;
+        for (int i = tid; i < RH * RW * (CIN / 4); i += WNT) {
+            const int c4 = i % (CIN / 4), q = i / (CIN / 4);
             const int gy = y0 - P + q / RW, gx = x0 - P + q % RW;
-            float v = 0.f;
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
             if (gy >= 0 && gy < H && gx >= 0 && gx < W) {
-                v = __ldg(x + ((static_cast<size_t>(n) * H + gy) * W + gx) * CIN + c);
-                if (relu_in) v = fmaxf(v, 0.f);
+                v = __ldg(reinterpret_cast<const float4*>(x + ((static_cast<size_t>(n) * H + gy) * W + gx) * CIN) + c4);
+                if (relu_in) v = make_float4(fmaxf(v.x, 0.f), fmaxf(v.y, 0.f), fmaxf(v.z, 0.f), fmaxf(v.w, 0.f));
             }
-            xs[c * PLANE + q] = v;
+            reinterpret_cast<float4*>(xs)[i] = v;
         }
-        for (int i = tid; i < NT * COUT; i += NT) {
-            const int o = i % COUT, q = i / COUT;
-            const int gy = y0 + q / TW, gx = x0 + q % TW;
-            float v = 0.f;
+        for (int i = tid; i < NPX * (COUT / 4); i += WNT) {
+            const int o4 = i % (COUT / 4), q = i / (COUT / 4);
+            const int gy = y0 + q / WTW, gx = x0 + q % WTW;
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
             if (gy < H && gx < W) {
-                const size_t idx = ((static_cast<size_t>(n) * H + gy) * W + gx) * COUT + o;
-                v = __ldg(g + idx);
-                if (gm && !(__ldg(gm + idx) > 0.f)) v = 0.f;
+                const size_t idx = ((static_cast<size_t>(n) * H + gy) * W + gx) * COUT;
+                v = __ldg(reinterpret_cast<const float4*>(g + idx) + o4);
+                if (gm) {
+                    const float4 m = __ldg(reinterpret_cast<const float4*>(gm + idx) + o4);
+                    v = make_float4(m.x > 0.f ? v.x : 0.f, m.y > 0.f ? v.y : 0.f, m.z > 0.f ? v.z : 0.f,
+                                    m.w > 0.f ? v.w : 0.f);
+                }
             }
-            gs[o * NT + q] = v;
+            reinterpret_cast<float4*>(gs)[i] = v;
         }
         __syncthreads();
-        for (int e = tid; e < NW; e += NT) {
-            const int tap = e % (K * K);
-            const int c = (e / (K * K)) % CIN;
-            const int o = e / (K * K * CIN);
-            const float* xp = xs + c * PLANE + (tap / K) * RW + (tap % K);
-            const float* gp = gs + o * NT;
+        for (int o = tid; o < COUT; o += WNT) {
             float s = 0.f;
-#pragma unroll 4
-            for (int q = 0; q < NT; ++q) s = fmaf(gp[q], xp[(q / TW) * RW + (q % TW)], s);
-            acc[e] += s;
+            for (int q = 0; q < NPX; ++q) s += gs[q * COUT + o];
+            dbs[o] += s;
         }
-        for (int o = tid; o < COUT; o += NT) {
-            float s = 0.f;
-            for (int q = 0; q < NT; ++q) s += gs[o * NT + q];
-            acc[NW + o] += s;
+        if (active) {
+#pragma unroll
+            for (int k = 0; k < NBT; ++k) {
+                const int b = PL == 1 ? tid + k * WNT : tid % NB;
+                if (b >= NB) continue;
+                const int cb = b % CB, ob = (b / CB) % OB, tap = b / (CB * OB);
+                const float* gp = gs + 4 * ob;
+                const float* xp = xs + ((tap / K) * RW + (tap % K)) * CIN + 4 * cb;
+#pragma unroll 4
+                for (int q = pl; q < NPX; q += PL) {
+                    const float4 g4 = *reinterpret_cast<const float4*>(gp + q * COUT);
+                    const float4 x4 = *reinterpret_cast<const float4*>(xp + ((q / WTW) * RW + (q % WTW)) * CIN);
+                    const float gv[4] = {g4.x, g4.y, g4.z, g4.w}, xv[4] = {x4.x, x4.y, x4.z, x4.w};
+#pragma unroll
+                    for (int i = 0; i < 4; ++i)
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) acc[k][4 * i + j] = fmaf(gv[i], xv[j], acc[k][4 * i + j]);
+                }
+            }
         }
     }
     __syncthreads();
-    for (int e = tid; e < NW; e += NT) atomicAdd(dW + e, acc[e]);
+    // weight e = (o CIN + c) TAPS + tap of block b, element (i, j): o = 4 ob + i, c = 4 cb + j
+    auto widx = [&](int b, int i, int j) {
+        const int cb = b % CB, ob = (b / CB) % OB, tap = b / (CB * OB);
+        return ((4 * ob + i) * CIN + 4 * cb + j) * TAPS + tap;
+    };
+    if constexpr (PL == 1) {
+#pragma unroll
+        for (int k = 0; k < NBT; ++k) {
+            const int b = tid + k * WNT;
+            if (b >= NB) continue;
+#pragma unroll
+            for (int e = 0; e < 16; ++e) atomicAdd(dW + widx(b, e / 4, e % 4), acc[k][e]);
+        }
+    } else {
+        float* red = xs;  // the pixel classes' partial sums meet here
+        for (int e = tid; e < NW; e += WNT) red[e] = 0.f;
+        __syncthreads();
+        if (active) {
+            const int b = tid % NB;
+#pragma unroll
+            for (int e = 0; e < 16; ++e) atomicAdd(red + widx(b, e / 4, e % 4), acc[0][e]);
+        }
+        __syncthreads();
+        for (int e = tid; e < NW; e += WNT) atomicAdd(dW + e, red[e]);
+    }
     if (db)
-        for (int o = tid; o < COUT; o += NT) atomicAdd(db + o, acc[NW + o]);
+        for (int o = tid; o < COUT; o += WNT) atomicAdd(db + o, dbs[o]);
 }
 
 template <int CIN, int COUT, int K>
 cudaError_t conv_fwd(const float* x, const float* xm, int relu_in, int N, int H, int W, const float* w, int tf,
                      const float* b, const float* ym, float* y, cudaStream_t st) {
-    constexpr int P = K / 2;
-    const size_t smem = sizeof(float) * (CIN * (TH + 2 * P) * (TW + 2 * P) + K * K * CIN * COUT);
+    constexpr int P = K / 2, TW = TJ * FwdShape<CIN, COUT>::PX;
+    const size_t smem = sizeof(float) * (CIN * (((TH + 2 * P) * (TW + 2 * P)) | 1) + K * K * CIN * COUT);
     auto kern = conv_fwd_kernel<CIN, COUT, K>;
     static bool attr = false;
     if (!attr) {
@@ -180,7 +280,9 @@ cudaError_t conv_fwd(const float* x, const float* xm, int relu_in, int N, int H,
     }
     const long long tiles = static_cast<long long>(N) * ((W + TW - 1) / TW) * ((H + TH - 1) / TH);
     if (tiles == 0) return cudaSuccess;
-    const long long cap = static_cast<long long>(num_sms()) * 4;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem) != cudaSuccess || per_sm < 1) per_sm = 1;
+    const long long cap = static_cast<long long>(num_sms()) * per_sm;
     kern<<<static_cast<int>(tiles < cap ? tiles : cap), NT, smem, st>>>(x, xm, relu_in, N, H, W, w, tf, b, ym, y);
     return cudaGetLastError();
 }
@@ -189,7 +291,7 @@ template <int CIN, int COUT, int K>
 cudaError_t conv_wgrad(const float* x, int relu_in, const float* g, const float* gm, int N, int H, int W, float* dW,
                        float* db, cudaStream_t st) {
     constexpr int P = K / 2;
-    const size_t smem = sizeof(float) * (CIN * (TH + 2 * P) * (TW + 2 * P) + COUT * NT + COUT * CIN * K * K + COUT);
+    const size_t smem = sizeof(float) * ((WTH + 2 * P) * (WTW + 2 * P) * CIN + WTH * WTW * COUT + COUT);
     auto kern = conv_wgrad_kernel<CIN, COUT, K>;
     static bool attr = false;
     if (!attr) {
@@ -197,10 +299,10 @@ cudaError_t conv_wgrad(const float* x, int relu_in, const float* g, const float*
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    const long long tiles = static_cast<long long>(N) * ((W + TW - 1) / TW) * ((H + TH - 1) / TH);
+    const long long tiles = static_cast<long long>(N) * ((W + WTW - 1) / WTW) * ((H + WTH - 1) / WTH);
     if (tiles == 0) return cudaSuccess;
     const long long cap = static_cast<long long>(num_sms()) * 2;
-    kern<<<static_cast<int>(tiles < cap ? tiles : cap), NT, smem, st>>>(x, relu_in, g, gm, N, H, W, dW, db);
+    kern<<<static_cast<int>(tiles < cap ? tiles : cap), WNT, smem, st>>>(x, relu_in, g, gm, N, H, W, dW, db);
     return cudaGetLastError();
 }
 
@@ -247,22 +349,30 @@ __global__ void pool_adj_kernel(const float* __restrict__ gy, int N, int H, int 
 // y[n,y,x,c] = bilinear x2 of lo (H/2 x W/2) (+ skip[n,y,x,c])
 __global__ void up_fwd_kernel(const float* __restrict__ lo, const float* __restrict__ skip, int N, int H, int W, int C,
                               float* __restrict__ y) {
-    const int Hl = H / 2, Wl = W / 2;
-    const size_t total = static_cast<size_t>(N) * H * W * C;
+    // four channels (one float4) per thread; C % 4 == 0
+    const int Hl = H / 2, Wl = W / 2, C4 = C / 4;
+    const size_t total = static_cast<size_t>(N) * H * W * C4;
+    const float4* lo4 = reinterpret_cast<const float4*>(lo);
     for (size_t i = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; i < total;
          i += static_cast<size_t>(gridDim.x) * blockDim.x) {
-        const int c = static_cast<int>(i % C);
-        size_t q = i / C;
+        const int c4 = static_cast<int>(i % C4);
+        size_t q = i / C4;
         const int x = static_cast<int>(q % W); q /= W;
         const int yy = static_cast<int>(q % H);
         const int n = static_cast<int>(q / H);
         const BilinTap ty = bilin_tap(yy, Hl), tx = bilin_tap(x, Wl);
-        auto L = [&](int a, int b2) { return lo[((static_cast<size_t>(n) * Hl + a) * Wl + b2) * C + c]; };
-        const float r0 = L(ty.i0, tx.i0) * tx.w0 + L(ty.i0, tx.i1) * tx.w1;
-        const float r1 = L(ty.i1, tx.i0) * tx.w0 + L(ty.i1, tx.i1) * tx.w1;
-        float v = r0 * ty.w0 + r1 * ty.w1;
-        if (skip) v += skip[i];
-        y[i] = v;
+        auto L = [&](int a, int b2) { return __ldg(lo4 + ((static_cast<size_t>(n) * Hl + a) * Wl + b2) * C4 + c4); };
+        const float4 a00 = L(ty.i0, tx.i0), a01 = L(ty.i0, tx.i1), a10 = L(ty.i1, tx.i0), a11 = L(ty.i1, tx.i1);
+        auto mix = [&](float v00, float v01, float v10, float v11) {
+            return (v00 * tx.w0 + v01 * tx.w1) * ty.w0 + (v10 * tx.w0 + v11 * tx.w1) * ty.w1;
+        };
+        float4 v = make_float4(mix(a00.x, a01.x, a10.x, a11.x), mix(a00.y, a01.y, a10.y, a11.y),
+                               mix(a00.z, a01.z, a10.z, a11.z), mix(a00.w, a01.w, a10.w, a11.w));
+        if (skip) {
+            const float4 sk = __ldg(reinterpret_cast<const float4*>(skip) + i);
+            v.x += sk.x; v.y += sk.y; v.z += sk.z; v.w += sk.w;
+        }
+        reinterpret_cast<float4*>(y)[i] = v;
     }
 }
 
@@ -270,16 +380,18 @@ __global__ void up_fwd_kernel(const float* __restrict__ lo, const float* __restr
 // sums the fine-grid cotangents of the (at most 4 x 4) fine pixels whose taps
 // reach it, with those taps' weights.
 __global__ void up_adj_kernel(const float* __restrict__ g, int N, int H, int W, int C, float* __restrict__ glo) {
-    const int Hl = H / 2, Wl = W / 2;
-    const size_t total = static_cast<size_t>(N) * Hl * Wl * C;
+    // four channels (one float4) per thread; C % 4 == 0
+    const int Hl = H / 2, Wl = W / 2, C4 = C / 4;
+    const size_t total = static_cast<size_t>(N) * Hl * Wl * C4;
+    const float4* g4 = reinterpret_cast<const float4*>(g);
     for (size_t i = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; i < total;
          i += static_cast<size_t>(gridDim.x) * blockDim.x) {
-        const int c = static_cast<int>(i % C);
-        size_t q = i / C;
+        const int c4 = static_cast<int>(i % C4);
+        size_t q = i / C4;
         const int X = static_cast<int>(q % Wl); q /= Wl;
         const int Y = static_cast<int>(q % Hl);
         const int n = static_cast<int>(q / Hl);
-        float s = 0.f;
+        float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
         for (int yy = 2 * Y - 2; yy <= 2 * Y + 3; ++yy) {
             if (yy < 0 || yy >= H) continue;
             const BilinTap ty = bilin_tap(yy, Hl);
@@ -290,10 +402,12 @@ __global__ void up_adj_kernel(const float* __restrict__ g, int N, int H, int W, 
                 const BilinTap tx = bilin_tap(xx, Wl);
                 const float wx = (tx.i0 == X ? tx.w0 : 0.f) + (tx.i1 == X ? tx.w1 : 0.f);
                 if (wx == 0.f) continue;
-                s += wy * wx * g[((static_cast<size_t>(n) * H + yy) * W + xx) * C + c];
+                const float wt = wy * wx;
+                const float4 v = __ldg(g4 + ((static_cast<size_t>(n) * H + yy) * W + xx) * C4 + c4);
+                s.x += wt * v.x; s.y += wt * v.y; s.z += wt * v.z; s.w += wt * v.w;
             }
         }
-        glo[i] = s;
+        reinterpret_cast<float4*>(glo)[i] = s;
     }
 }
 
