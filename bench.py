@@ -354,7 +354,19 @@ def extra_train(nsm, scenegen, torch, device, theta, reps):
     torch.cuda.synchronize()
     ctx.check()
     ms = sum(ev[2 * k].elapsed_time(ev[2 * k + 1]) for k in range(reps)) / reps
+    # algorithmic work: forward of all B T instances, and for the B target
+    # instances the recomputed forward, the weight gradients and the data
+    # gradients (none for the input features): MACs per full-resolution pixel
+    mac_px = MACS["enc0"] + MACS["dec0"] + (MACS["enc1"] + MACS["dec1"]) / 4 + MACS["bott"] / 16
+    mac_first = 4 * 16 * 9
+    flop = 2.0 * S * S * (B * T * mac_px + B * (mac_px + mac_px + (mac_px - mac_first)))
+    sms = torch.cuda.get_device_properties(device).multi_processor_count
+    peak = fp32_alu_peak_tflops(sms, load_peaks()["sm_max_mhz"])
+    tflops = flop / (ms * 1e-3) / 1e12
     return {"ms_per_step": ms, "instances_per_s": B * T / (ms * 1e-3), "loss_last": float(loss.item()),
+            "algorithmic_gflop": flop / 1e9, "achieved_tflops": tflops,
+            "roofline": {"bound": "alu", "peak_tflops": peak, "frac": tflops / peak,
+                         "peak_src": "128 FP32 lanes x 2 FLOP x SMs x max SM clock"},
             "workload": "B=16 x T=3 soft 256^2 instances (seeded scenes + 2 perturbations each), 64-sample MC targets",
             "precision": "FP32 CUDA cores (forward checkpoints per level, recomputation in the backward, Adam)"}
 
