@@ -78,3 +78,17 @@ def device_batch(frames, targets):
     bt = nsm.make_batch(pos, nrm, sm, lights, cams, tgt, B, T)
     bt._tensors = (pos, nrm, sm, tgt)
     return bt
+
+
+def oracle_band(frame, theta64, y0, y1, margin=32):
+    """FP64 oracle visibility of rows [y0, y1) (multiples of 4) from the rows
+    [y0 - margin, y1 + margin) of the frame: the network's receptive field is
+    about 20 level-0 pixels, so these rows equal the full-frame forward (a CPU
+    test pins the band forward to the full one)."""
+    from oracle import gather as G
+    from oracle import network as N
+    a, b = max(0, y0 - margin), min(frame.H, y1 + margin)
+    sub = slice(a, b)
+    feat, _, _ = G.features(frame.pos4[sub], frame.nrm4[sub], frame.sm, frame.view_proj, frame.light_pos,
+                            frame.cam_pos, frame.r_hat, frame.z_far, frame.bias)
+    return N.forward(feat, theta64)[y0 - a:y1 - a]

@@ -123,3 +123,16 @@ def test_every_stage_variant_matches_the_default_plan():
     with pytest.raises(nsm.NSMError):
         nsm.nsm_plan_set(c, 0, 99, 0)
     c.check()
+
+
+def test_batched_with_a_2160p_view_matches_single_view_calls(ctx):
+    """The largest serving view (3840 x 2160, 4096^2 map) in one batch with
+    small ones: every view equals its own nsm_infer call bit for bit."""
+    w = nsm.Weights(ctx, scenegen.trained_weights())
+    dfs = [DeviceFrame(scenegen.soft_frame(2160, 3840, 4096, 4096, 64, 31)),
+           DeviceFrame(scenegen.hard_frame(68, 132, 300, 300, 8, 5)),
+           DeviceFrame(scenegen.soft_frame(540, 960, 1024, 1024, 16, 6))]
+    outs = [torch.full((d.f.H, d.f.W), float("nan"), device="cuda") for d in dfs]
+    got = _batched(ctx, w, dfs, outs)
+    for df, g in zip(dfs, got):
+        np.testing.assert_array_equal(g, run_infer(ctx, w, df, nsm.NSM_BF16).cpu().numpy())

@@ -115,6 +115,29 @@ def test_infer_trained_weights_1080p_soft_bf16(ctx):
     assert err.max() <= 1e-2 and float(np.mean(err ** 2)) <= 1e-4, (err.max(), float(np.mean(err ** 2)))
 
 
+@pytest.fixture(scope="module")
+def frame_2160p():
+    return scenegen.soft_frame(2160, 3840, 4096, 4096, 64, 31)
+
+
+@pytest.mark.parametrize("precision", [nsm.NSM_FP32, nsm.NSM_BF16])
+def test_infer_2160p_4096_map_bands(ctx, frame_2160p, precision):
+    """The largest serving size (3840 x 2160 view, 4096^2 map, soft emitter,
+    trained weights) against the FP64 oracle on row bands at the top, middle
+    and bottom edge."""
+    from gpu_helpers import oracle_band
+    f = frame_2160p
+    theta = scenegen.trained_weights()
+    vis = _run(ctx, f, theta, precision)
+    th64 = theta.astype(np.float64)
+    for y0, y1 in ((0, 40), (1060, 1100), (2120, 2160)):
+        err = np.abs(vis[y0:y1] - oracle_band(f, th64, y0, y1))
+        if precision == nsm.NSM_FP32:
+            assert err.max() <= 1e-4, (y0, err.max())
+        else:
+            assert err.max() <= 1e-2 and float(np.mean(err ** 2)) <= 1e-4, (y0, err.max())
+
+
 def test_infer_fp8_trained_weights_follow_rounding_model(ctx):
     theta = scenegen.trained_weights()
     f = scenegen.soft_frame(256, 256, 512, 512, 8, 21)
