@@ -334,10 +334,21 @@ void nsm_train_state_destroy(nsm_train_state* st);
 nsm_status nsm_train_step(nsm_ctx* ctx, nsm_train_state* st, const nsm_batch* batch, const nsm_train_cfg* cfg,
                           float* loss_out, void* stream);
 
-/* Copy a state vector (n = nsm_param_count floats) to device memory dev_out:
- * what = 0 master weights, 1 gradient of the last step, 2 Adam first moment,
- * 3 Adam second moment.  Asynchronous on stream. */
+/* nsm_train_step in two halves, for data parallelism (the gradient is
+ * exchanged between them): nsm_train_grad computes the loss and the gradient
+ * of the batch (the mean over its items) into the state without touching the
+ * weights; nsm_train_apply takes one Adam step with the state's gradient.
+ * nsm_train_step = nsm_train_grad + nsm_train_apply.  Asynchronous on stream. */
+nsm_status nsm_train_grad(nsm_ctx* ctx, nsm_train_state* st, const nsm_batch* batch, const nsm_train_cfg* cfg,
+                          float* loss_out, void* stream);
+nsm_status nsm_train_apply(nsm_ctx* ctx, nsm_train_state* st, const nsm_train_cfg* cfg, void* stream);
+
+/* Copy a state vector (n = nsm_param_count floats) to device memory dev_out,
+ * or set it from device memory dev_in: what = 0 master weights, 1 gradient of
+ * the last step, 2 Adam first moment, 3 Adam second moment.  Asynchronous on
+ * stream. */
 nsm_status nsm_train_state_read(nsm_train_state* st, int what, float* dev_out, size_t n, void* stream);
+nsm_status nsm_train_state_write(nsm_train_state* st, int what, const float* dev_in, size_t n, void* stream);
 
 /* ---------------------------------------------------------------- scene generation (GPU ray casting) */
 

@@ -301,6 +301,9 @@ def _train_sigs():
         "nsm_train_state_destroy": ([P], None),
         "nsm_train_step": ([P, P, ctypes.POINTER(nsm_batch), ctypes.POINTER(nsm_train_cfg), P, P], I),
         "nsm_train_state_read": ([P, I, P, Z, P], I),
+        "nsm_train_state_write": ([P, I, P, Z, P], I),
+        "nsm_train_grad": ([P, P, ctypes.POINTER(nsm_batch), ctypes.POINTER(nsm_train_cfg), P, P], I),
+        "nsm_train_apply": ([P, P, ctypes.POINTER(nsm_train_cfg), P], I),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -339,9 +342,25 @@ class TrainState:
         _check(_train_sigs().nsm_train_step(self.ctx.h, self.h, ctypes.byref(batch), ctypes.byref(cfg),
                                             _ptr(loss_out), _stream(stream)), "nsm_train_step")
 
+    def grad(self, batch: nsm_batch, alpha=0.9, loss_out=None, stream=None):
+        """Loss and gradient of the batch into the state (no weight update)."""
+        cfg = nsm_train_cfg(lr=1e-3, alpha=alpha, beta1=0.9, beta2=0.999, eps=1e-8)
+        _check(_train_sigs().nsm_train_grad(self.ctx.h, self.h, ctypes.byref(batch), ctypes.byref(cfg),
+                                            _ptr(loss_out), _stream(stream)), "nsm_train_grad")
+
+    def apply(self, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+        """One Adam step with the state's gradient."""
+        cfg = nsm_train_cfg(lr=lr, alpha=0.9, beta1=beta1, beta2=beta2, eps=eps)
+        _check(_train_sigs().nsm_train_apply(self.ctx.h, self.h, ctypes.byref(cfg), _stream(stream)),
+               "nsm_train_apply")
+
     def read(self, what: int, out, stream=None):
         _check(_train_sigs().nsm_train_state_read(self.h, what, _ptr(out), self.n, _stream(stream)),
                "nsm_train_state_read")
+
+    def write(self, what: int, src, stream=None):
+        _check(_train_sigs().nsm_train_state_write(self.h, what, _ptr(src), self.n, _stream(stream)),
+               "nsm_train_state_write")
 
     def close(self):
         if self.h:

@@ -109,7 +109,12 @@ void nsm_train_state_destroy(nsm_train_state* s) {
     delete s;
 }
 
-nsm_status nsm_train_step(nsm_ctx* ctx, nsm_train_state* s, const nsm_batch* bt, const nsm_train_cfg* cfg,
+static bool cfg_ok(const nsm_train_cfg* cfg) {
+    return cfg->lr > 0.f && cfg->alpha >= 0.f && cfg->beta1 >= 0.f && cfg->beta1 < 1.f && cfg->beta2 >= 0.f &&
+           cfg->beta2 < 1.f && cfg->eps > 0.f;
+}
+
+nsm_status nsm_train_grad(nsm_ctx* ctx, nsm_train_state* s, const nsm_batch* bt, const nsm_train_cfg* cfg,
                           float* loss_out, void* stream) {
     if (!ctx || !s || !bt || !cfg) return fail(NSM_ERR_INVALID_ARG, "ctx, state, batch and cfg must be non-NULL");
     if (bt->B < 1 || bt->T < 1 || bt->B > s->max_B || bt->T > s->max_T || bt->H != s->H || bt->W != s->W)
@@ -117,9 +122,7 @@ nsm_status nsm_train_step(nsm_ctx* ctx, nsm_train_state* s, const nsm_batch* bt,
                     bt->T, bt->H, bt->W, s->max_B, s->max_T, s->H, s->W);
     if (bt->Hs < 1 || bt->Ws < 1 || bt->Hs > 16384 || bt->Ws > 16384) return fail(NSM_ERR_SHAPE, "bad shadow-map size");
     if (!bt->lights || !bt->cameras) return fail(NSM_ERR_INVALID_ARG, "lights / cameras are NULL");
-    if (!(cfg->lr > 0.f) || !(cfg->alpha >= 0.f) || !(cfg->beta1 >= 0.f && cfg->beta1 < 1.f) ||
-        !(cfg->beta2 >= 0.f && cfg->beta2 < 1.f) || !(cfg->eps > 0.f))
-        return fail(NSM_ERR_INVALID_ARG, "bad training configuration");
+    if (!cfg_ok(cfg)) return fail(NSM_ERR_INVALID_ARG, "bad training configuration");
     nsm_status st;
     if ((st = check_dev_ptr(bt->pos4, "batch.pos4", 16)) != NSM_OK) return st;
     if ((st = check_dev_ptr(bt->nrm4, "batch.nrm4", 16)) != NSM_OK) return st;
@@ -152,13 +155,35 @@ nsm_status nsm_train_step(nsm_ctx* ctx, nsm_train_state* s, const nsm_batch* bt,
         return cuda_fail(e, "loss");
     if ((e = cudaMemsetAsync(s->grad, 0, s->n * 4, cs)) != cudaSuccess) return cuda_fail(e, "grad reset");
     if ((e = tr::backward(s->theta, s->grad, b, bt->B, H, W, nullptr, cs)) != cudaSuccess) return cuda_fail(e, "backward");
-    s->step += 1;
-    if ((e = tr::adam(s->theta, s->grad, s->m, s->v, s->n, cfg->lr, cfg->beta1, cfg->beta2, cfg->eps, s->step, cs)) !=
-        cudaSuccess)
-        return cuda_fail(e, "adam");
     if (loss_out && (e = cudaMemcpyAsync(loss_out, s->loss, sizeof(float), cudaMemcpyDeviceToDevice, cs)) != cudaSuccess)
         return cuda_fail(e, "copy loss");
     return NSM_OK;
+}
+
+nsm_status nsm_train_apply(nsm_ctx* ctx, nsm_train_state* s, const nsm_train_cfg* cfg, void* stream) {
+    if (!ctx || !s || !cfg) return fail(NSM_ERR_INVALID_ARG, "ctx, state and cfg must be non-NULL");
+    if (!cfg_ok(cfg)) return fail(NSM_ERR_INVALID_ARG, "bad training configuration");
+    s->step += 1;
+    const cudaError_t e = tr::adam(s->theta, s->grad, s->m, s->v, s->n, cfg->lr, cfg->beta1, cfg->beta2, cfg->eps,
+                                   s->step, static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? NSM_OK : cuda_fail(e, "adam");
+}
+
+nsm_status nsm_train_step(nsm_ctx* ctx, nsm_train_state* s, const nsm_batch* bt, const nsm_train_cfg* cfg,
+                          float* loss_out, void* stream) {
+    const nsm_status st = nsm_train_grad(ctx, s, bt, cfg, loss_out, stream);
+    return st != NSM_OK ? st : nsm_train_apply(ctx, s, cfg, stream);
+}
+
+nsm_status nsm_train_state_write(nsm_train_state* s, int what, const float* dev_in, size_t n, void* stream) {
+    if (!s) return fail(NSM_ERR_INVALID_ARG, "state is NULL");
+    if (n != s->n) return fail(NSM_ERR_SHAPE, "%zu floats given, the state holds %zu", n, s->n);
+    nsm_status st = check_dev_ptr(dev_in, "dev_in", 4);
+    if (st != NSM_OK) return st;
+    float* dst = what == 0 ? s->theta : what == 1 ? s->grad : what == 2 ? s->m : what == 3 ? s->v : nullptr;
+    if (!dst) return fail(NSM_ERR_INVALID_ARG, "unknown state vector %d", what);
+    cudaError_t e = cudaMemcpyAsync(dst, dev_in, n * 4, cudaMemcpyDeviceToDevice, static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? NSM_OK : cuda_fail(e, "copy state");
 }
 
 nsm_status nsm_train_state_read(nsm_train_state* s, int what, float* dev_out, size_t n, void* stream) {

@@ -216,3 +216,43 @@ def test_training_reduces_the_loss(ctx):
         losses.append(float(loss.item()))
     assert all(np.isfinite(losses))
     assert min(losses[-10:]) < 0.7 * losses[0], (losses[0], losses[-10:])
+
+
+def test_grad_apply_and_data_parallel_trainer_match_train_step(ctx):
+    """nsm_train_grad + nsm_train_apply is nsm_train_step; a gradient written
+    back through nsm_train_state_write is the one applied; the data-parallel
+    trainer on one rank (the exchange is the identity) takes the same steps."""
+    from paper_2301_05262_gb300.data_parallel import DataParallelTrainer
+    B, T, H, W, S = 2, 3, 32, 32, 128
+    frames, targets = train_batch_frames(B, T, H, W, S, seed=43)
+    theta = _theta(9)
+    bt = device_batch(frames, targets)
+    a = nsm.TrainState(ctx, theta, B, T, H, W)
+    b = nsm.TrainState(ctx, theta, B, T, H, W)
+    c = nsm.TrainState(ctx, theta, B, T, H, W)
+    dp = DataParallelTrainer(c)
+    g = torch.empty(theta.size, device="cuda")
+    for _ in range(2):
+        a.step(bt, lr=1e-3)
+        b.grad(bt)
+        b.read(1, g)
+        b.write(1, g.clone())
+        b.apply(lr=1e-3)
+        dp.step(bt, lr=1e-3)
+    out = [torch.empty(theta.size, device="cuda") for _ in range(3)]
+    for st, o in zip((a, b, c), out):
+        st.read(0, o)
+    torch.cuda.synchronize()
+    # weight gradients are summed with FP32 atomics across CTAs, so two runs of
+    # the same step agree to rounding, not bit for bit
+    np.testing.assert_allclose(out[0].cpu().numpy(), out[1].cpu().numpy(), rtol=1e-5, atol=1e-7)
+    np.testing.assert_allclose(out[0].cpu().numpy(), out[2].cpu().numpy(), rtol=1e-5, atol=1e-7)
+    # a gradient set by hand moves the weights by lr * sign(g) on the first Adam step
+    d = nsm.TrainState(ctx, theta, B, T, H, W)
+    gh = torch.from_numpy(np.where(np.arange(theta.size) % 2 == 0, 1.0, -1.0).astype(np.float32)).cuda()
+    d.write(1, gh)
+    d.apply(lr=1e-3)
+    w = torch.empty(theta.size, device="cuda")
+    d.read(0, w)
+    torch.cuda.synchronize()
+    np.testing.assert_allclose(w.cpu().numpy() - theta, -1e-3 * gh.cpu().numpy(), rtol=1e-4, atol=1e-7)
