@@ -315,33 +315,40 @@ __device__ __forceinline__ void up_column(const TcJob& job, int y0, int x0, uint
 #pragma unroll
         for (int c = 0; c < 8; ++c) h[c] = p0[c] * tx.w0 + p1[c] * tx.w1;
     };
-    int ia = -4, ib = -4;  // coarse rows held in ha, hb
-    float ha[8], hb[8];
+    // All coarse rows the item's staged rows need, interpolated horizontally up
+    // front (their shared-memory loads in flight together).  Fine row gy takes
+    // coarse rows i0 = gy odd ? (gy - 1) / 2 : gy / 2 - 1 and i0 + 1, weights
+    // (3/4, 1/4) for odd gy and (1/4, 3/4) for even gy, both indices clamped to
+    // the level (bilin_tap); items of several rows start on an odd row (tile
+    // origins are even), so row k uses rows k / 2 and k / 2 + 1 of the preload,
+    // single-row items rows 0 and 1.  Rows are loaded through the same clamp.
+    const int gy0 = y0 - 1 + sr0;
+    const int cu = (gy0 & 1) ? (gy0 - 1) / 2 : gy0 / 2 - 1;
+    constexpr int NCRI = (NROWS + 1) / 2 + 1;
+    // (only for a column inside the view: outside it c0 / c1 are not raw-buffer
+    // addresses, and the staged values are zeros)
+    float hv[NCRI][8];
+#pragma unroll
+    for (int j = 0; j < NCRI; ++j) {
+        const int ci = cu + j < 0 ? 0 : (cu + j > Hl - 1 ? Hl - 1 : cu + j);
+        if (okx) {
+            hrow(ci, hv[j]);
+        } else {
+#pragma unroll
+            for (int c = 0; c < 8; ++c) hv[j][c] = 0.f;
+        }
+    }
 #pragma unroll
     for (int k = 0; k < NROWS; ++k) {
         const int sr = sr0 + k;
         const int gy = y0 - 1 + sr;
         uint4 vh = make_uint4(0, 0, 0, 0), vl = vh;
         if (okx && gy >= 0 && gy < H) {
-            const BilinTap ty = bilin_tap(gy, Hl);
-            if (ty.i0 != ia) {
-                if (ty.i0 == ib) {
-#pragma unroll
-                    for (int c = 0; c < 8; ++c) ha[c] = hb[c];
-                } else {
-                    hrow(ty.i0, ha);
-                }
-                ia = ty.i0;
-                ib = ia;
-            }
-            if (ty.i1 != ia && ty.i1 != ib) {
-                hrow(ty.i1, hb);
-                ib = ty.i1;
-            }
-            const bool same = ty.i1 == ia;
+            const int j0 = NROWS == 1 ? 0 : k / 2;
+            const float w0 = (gy & 1) ? 0.75f : 0.25f, w1 = (gy & 1) ? 0.25f : 0.75f;
             float o[8];
 #pragma unroll
-            for (int c = 0; c < 8; ++c) o[c] = ha[c] * ty.w0 + (same ? ha[c] : hb[c]) * ty.w1;
+            for (int c = 0; c < 8; ++c) o[c] = hv[j0][c] * w0 + hv[j0 + 1][c] * w1;
             if constexpr (SKIP) {
                 const float sk[8] = {ska[k].x, ska[k].y, ska[k].z, ska[k].w, skb[k].x, skb[k].y, skb[k].z, skb[k].w};
 #pragma unroll
