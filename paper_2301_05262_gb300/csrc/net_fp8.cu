@@ -598,7 +598,7 @@ __global__ void __launch_bounds__(32 * (NEW + NPW + 1), 1) level_f8_kernel(const
                         }
                     }
                     if (EPI == TEPI_HEAD && oy < H && ox < W)
-                        job.vis[static_cast<size_t>(oy) * W + ox] = sigmoidf_acc(hsum + head_s[COUT]);
+                        job.vis[static_cast<size_t>(oy) * W + ox] = sigmoidf_fast(hsum + head_s[COUT]);
                 }
             }
             fence_before_sync();

@@ -117,6 +117,13 @@ __device__ __forceinline__ void gather_features(const GatherParams& g, int y, in
 }
 
 __device__ __forceinline__ float sigmoidf_acc(float x) { return 1.0f / (1.0f + expf(-x)); }
+// The hardware exponential and reciprocal (a few ulp, ~1e-6 relative): for
+// the tensor-core forms, whose stored values carry far larger rounding.  The
+// argument is clamped at -80 so the divisor stays below 2^126, where the fast
+// reciprocal is specified (the sigmoid is ~1.8e-35 there).
+__device__ __forceinline__ float sigmoidf_fast(float x) {
+    return __fdividef(1.0f, 1.0f + __expf(-fmaxf(x, -80.0f)));
+}
 
 // Bilinear x2 upsampling with half-pixel centres (align_corners = false) and
 // edge clamping: output index o samples the source at o / 2 - 1 / 4.
