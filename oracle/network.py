@@ -432,25 +432,111 @@ def s2d_output(o: np.ndarray) -> np.ndarray:
     return up
 
 
-def forward_s2d(feat: np.ndarray, theta: np.ndarray, levels: int = 3):
+def pack_s2d(params, levels: int = 3) -> np.ndarray:
+    parts = []
+    for (name, ci, co, k) in layer_table_s2d(levels):
+        W, b = params[name]
+        parts.append(np.asarray(W, np.float64).reshape(-1))
+        parts.append(np.asarray(b, np.float64).reshape(-1))
+    return np.concatenate(parts)
+
+
+def space_to_depth_adjoint(g: np.ndarray) -> np.ndarray:
+    """Adjoint (= inverse) of space_to_depth: (4C, H/2, W/2) -> (C, H, W)."""
+    C4, H2, W2 = g.shape
+    C = C4 // 4
+    x = np.empty((C, 2 * H2, 2 * W2), g.dtype)
+    for a in range(2):
+        for b in range(2):
+            x[:, a::2, b::2] = g[C * (2 * a + b):C * (2 * a + b + 1)]
+    return x
+
+
+def s2d_output_adjoint(g: np.ndarray) -> np.ndarray:
+    """Adjoint of s2d_output: (H, W) cotangent -> (4, H/2, W/2)."""
+    o = np.empty((4, g.shape[0] // 2, g.shape[1] // 2), g.dtype)
+    o[0] = upsample2_adjoint(g[None])[0]
+    o[1] = g[0::2, 1::2]
+    o[2] = g[1::2, 0::2]
+    o[3] = g[1::2, 1::2]
+    return o
+
+
+def forward_s2d(feat: np.ndarray, theta: np.ndarray, levels: int = 3, keep: bool = False):
     """Visibility of the space-to-depth network: the levels 1 .. L-1 of
     `forward` on space_to_depth(features), then the 4-channel head and the
-    2x2 recombination (Sec. 3.5)."""
+    2x2 recombination (Sec. 3.5).  With keep=True also the intermediates."""
     P = unpack_s2d(theta, levels)
+    t = {}
     h = space_to_depth(np.asarray(feat, np.float64))
     skips = {}
 
-    def pair(x, l3, l1):
-        return relu(conv2d(relu(conv2d(x, *P[l3])), *P[l1]))
+    def pair(x, name):
+        t[f"{name}_in"] = x
+        a3 = conv2d(x, *P[f"{name}_3x3"])
+        h3 = relu(a3)
+        a1 = conv2d(h3, *P[f"{name}_1x1"])
+        t[f"{name}_a3"], t[f"{name}_h3"], t[f"{name}_a1"] = a3, h3, a1
+        return relu(a1)
 
     for l in range(1, levels - 1):
-        h1 = pair(h, f"enc{l}_3x3", f"enc{l}_1x1")
+        h1 = pair(h, f"enc{l}")
         skips[l] = h1
         h = avgpool2(h1)
-    h = pair(h, "bott_3x3", "bott_1x1")
+    h = pair(h, "bott")
     for l in range(levels - 2, 0, -1):
-        h = pair(upsample2(h) + skips[l], f"dec{l}_3x3", f"dec{l}_1x1")
-    return sigmoid(s2d_output(conv2d(h, *P["head"])))
+        h = pair(upsample2(h) + skips[l], f"dec{l}")
+    t["head_in"] = h
+    vis = sigmoid(s2d_output(conv2d(h, *P["head"])))
+    t["vis"] = vis
+    return (vis, t) if keep else vis
+
+
+def backward_s2d(gvis: np.ndarray, theta: np.ndarray, t: dict, levels: int = 3):
+    """Adjoint of `forward_s2d`: (dtheta flat in layer_table_s2d order, dfeat)
+    for the cotangent gvis (H, W)."""
+    P = unpack_s2d(theta, levels)
+    G = {}
+    vis = t["vis"]
+    go = s2d_output_adjoint(gvis * vis * (1.0 - vis))
+    gh, dW, db = conv2d_adjoint(go, t["head_in"], P["head"][0])
+    G["head"] = (dW, db)
+
+    def pair_adj(gout, name):
+        ga1 = gout * (t[f"{name}_a1"] > 0)
+        gh3, dW1, db1 = conv2d_adjoint(ga1, t[f"{name}_h3"], P[f"{name}_1x1"][0])
+        G[f"{name}_1x1"] = (dW1, db1)
+        ga3 = gh3 * (t[f"{name}_a3"] > 0)
+        gx, dW3, db3 = conv2d_adjoint(ga3, t[f"{name}_in"], P[f"{name}_3x3"][0])
+        G[f"{name}_3x3"] = (dW3, db3)
+        return gx
+
+    gskip = {}
+    for l in range(1, levels - 1):
+        gx = pair_adj(gh, f"dec{l}")
+        gskip[l] = gx
+        gh = upsample2_adjoint(gx)
+    gh = pair_adj(gh, "bott")
+    for l in range(levels - 2, 0, -1):
+        gh = pair_adj(avgpool2_adjoint(gh) + gskip[l], f"enc{l}")
+    return pack_s2d(G, levels), space_to_depth_adjoint(gh)
+
+
+def train_step_s2d(batch_feats, targets, theta, m, v, step, lr=1e-3, alpha=0.9, levels=3):
+    """`train_step` for the space-to-depth network (same Eq. 2 loss, Adam)."""
+    B = len(batch_feats)
+    grad = np.zeros_like(np.asarray(theta, np.float64))
+    total = 0.0
+    for b in range(B):
+        insts = batch_feats[b]
+        x0, t = forward_s2d(insts[0], theta, levels, keep=True)
+        xs = [forward_s2d(f, theta, levels) for f in insts[1:]]
+        loss, g = loss_l1(x0, targets[b], xs, alpha)
+        total += loss / B
+        dth, _ = backward_s2d(g / B, theta, t, levels)
+        grad += dth
+    theta2, m2, v2 = adam_update(theta, grad, m, v, step, lr)
+    return theta2, m2, v2, total, grad
 
 
 # ------------------------------------------------------------------ loss (Eq. 2)

@@ -461,3 +461,84 @@ def test_trained_weights_input():
         mse_tr = np.mean((N.forward(feat, th) - target) ** 2)
         mse_he = np.mean((N.forward(feat, he) - target) ** 2)
         assert mse_tr < 0.25 * mse_he, (soft, mse_tr, mse_he)
+
+
+def test_s2d_adjoint_operators_dot_product():
+    """<A x, y> = <x, A^T y> for space_to_depth and s2d_output."""
+    rng = np.random.default_rng(21)
+    x = rng.standard_normal((4, 8, 12))
+    y = rng.standard_normal((16, 4, 6))
+    assert np.vdot(N.space_to_depth(x), y) == pytest.approx(np.vdot(x, N.space_to_depth_adjoint(y)), rel=1e-12)
+    o = rng.standard_normal((4, 4, 6))
+    g = rng.standard_normal((8, 12))
+    assert np.vdot(N.s2d_output(o), g) == pytest.approx(np.vdot(o, N.s2d_output_adjoint(g)), rel=1e-12)
+
+
+def test_s2d_backward_matches_central_finite_differences():
+    """The space-to-depth network's adjoint against central differences
+    (h = 1e-4, FP64: at 1e-3 the truncation error reaches ~2e-6 relative on
+    some weights) on a 16 x 16 input, stencils crossing a ReLU kink excluded;
+    weights and the input features."""
+    rng = np.random.default_rng(22)
+    x = rng.standard_normal((4, 16, 16))
+    th = scenegen_s2d_theta(23)
+    g = rng.standard_normal((16, 16))
+    v, t = N.forward_s2d(x, th, keep=True)
+    np.testing.assert_allclose(v, N.forward_s2d(x, th), rtol=0, atol=0)
+    grad, gfeat = N.backward_s2d(g, th, t)
+    h = 1e-4
+
+    def pattern(tt):
+        return np.concatenate([(tt[k] > 0).ravel() for k in tt if k.endswith(("_a3", "_a1"))])
+
+    offs = np.cumsum([0] + [co * ci * k * k + co for (_, ci, co, k) in N.layer_table_s2d(3)])
+    idx = np.concatenate([rng.choice(th.size, 60, replace=False), offs[:-1], offs[1:] - 1])
+    checked = 0
+    for i in idx:
+        tp = th.copy(); tp[i] += h
+        tm = th.copy(); tm[i] -= h
+        vp, ttp = N.forward_s2d(x, tp, keep=True)
+        vm, ttm = N.forward_s2d(x, tm, keep=True)
+        if not (np.array_equal(pattern(ttp), pattern(t)) and np.array_equal(pattern(ttm), pattern(t))):
+            continue
+        fd = (np.sum(g * vp) - np.sum(g * vm)) / (2 * h)
+        assert fd == pytest.approx(grad[i], rel=1e-6, abs=1e-9), i
+        checked += 1
+    assert checked >= 40
+    for (c, yy, xx) in [(0, 3, 4), (2, 10, 7), (3, 15, 15), (1, 0, 0)]:
+        xp = x.copy(); xp[c, yy, xx] += h
+        xm = x.copy(); xm[c, yy, xx] -= h
+        vp, ttp = N.forward_s2d(xp, th, keep=True)
+        vm, ttm = N.forward_s2d(xm, th, keep=True)
+        if np.array_equal(pattern(ttp), pattern(t)) and np.array_equal(pattern(ttm), pattern(t)):
+            assert (np.sum(g * vp) - np.sum(g * vm)) / (2 * h) == pytest.approx(gfeat[c, yy, xx], rel=1e-6, abs=1e-9)
+
+
+def test_s2d_train_step_matches_the_3level_form_of_its_parts():
+    """train_step_s2d's loss and gradient are the Eq. 2 loss of forward_s2d and
+    the adjoint above (composition check on a 2-item batch)."""
+    rng = np.random.default_rng(24)
+    feats = [[rng.standard_normal((4, 8, 8)) for _ in range(2)] for _ in range(2)]
+    targets = [rng.random((8, 8)) for _ in range(2)]
+    th = scenegen_s2d_theta(25)
+    z = np.zeros_like(th)
+    _, _, _, loss, grad = N.train_step_s2d(feats, targets, th, z, z, 1)
+    ref_loss, ref_grad = 0.0, np.zeros_like(th)
+    for b in range(2):
+        x0, t = N.forward_s2d(feats[b][0], th, keep=True)
+        l, g = N.loss_l1(x0, targets[b], [N.forward_s2d(feats[b][1], th)])
+        ref_loss += l / 2
+        ref_grad += N.backward_s2d(g / 2, th, t)[0]
+    assert loss == pytest.approx(ref_loss, rel=1e-12)
+    np.testing.assert_allclose(grad, ref_grad, rtol=1e-12, atol=1e-15)
+
+
+def scenegen_s2d_theta(seed):
+    import scenegen
+    rng = np.random.default_rng(seed)
+    parts = []
+    for (_, ci, co, k) in N.layer_table_s2d(3):
+        parts.append(rng.standard_normal(co * ci * k * k) * np.sqrt(2.0 / (ci * k * k)))
+        parts.append(rng.standard_normal(co) * 0.05)
+    del scenegen
+    return np.concatenate(parts)
