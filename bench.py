@@ -424,11 +424,10 @@ def oracle_band(frame, theta64, y0: int, y1: int, margin: int = 32):
 
 def extra_s2d(nsm, scenegen, torch, device, ctx, reps, with_error):
     """The space-to-depth topology (Sec. 3.5: level-0 convolutions removed) on the
-    1080p soft frame, BF16 form, seeded He-init weights of that topology; error
+    1080p soft frame, BF16 form, seeded trained weights of that topology; error
     against the FP64 oracle on a band of rows."""
-    from oracle import network as N
     f = scenegen.soft_frame(H, W, HS, WS, N_OBJ, SCENE_SEED + 10)
-    theta = scenegen.he_init_weights(WEIGHT_SEED, N.layer_table_s2d(3)).astype(np.float32)
+    theta = scenegen.trained_weights_s2d()
     w = nsm.Weights(ctx, theta, nsm.NSM_TOPO_S2D)
     light = nsm.LightDesc(pos=tuple(f.light_pos), radius=f.light_radius, r_hat=f.r_hat, view_proj=f.view_proj,
                           z_far=f.z_far, bias=f.bias, tan_half_fov=f.tan_half_fov)
@@ -448,10 +447,11 @@ def extra_s2d(nsm, scenegen, torch, device, ctx, reps, with_error):
         ev[2 * k + 1].record()
     torch.cuda.synchronize()
     ms = sum(ev[2 * k].elapsed_time(ev[2 * k + 1]) for k in range(reps)) / reps
-    out = {"workload": "1920x1080 soft frame, 2048^2 map, space-to-depth topology (36,116 parameters)",
+    out = {"workload": "1920x1080 soft frame, 2048^2 map, space-to-depth topology (36,116 parameters), trained weights",
            "bf16": {"ms_per_frame": ms, "mpix_s": H * W / (ms * 1e-3) / 1e6}}
     if with_error:
         from oracle import gather as G
+        from oracle import network as N
         y0, y1, m = 520, 560, 32
         sub = slice(y0 - m, y1 + m)
         feat, _, _ = G.features(f.pos4[sub], f.nrm4[sub], f.sm, f.view_proj, f.light_pos, f.cam_pos, f.r_hat,

@@ -50,4 +50,7 @@ itself; the tests under tests/test_oracle_*.py):
       channel-0 bilinear by explicit loops, the whole network against a
       direct-summation loop implementation on 8 x 8 inputs, and the head-bias
       closed form.
+  backward_s2d / train_step_s2d -- the dot-product identity of the two new
+      operator adjoints, central differences on weights and features, the
+      training step against its parts.
 """

@@ -1,8 +1,11 @@
-"""Seeded trained weights for the 3-level network, made with the FP64 oracle.
+"""Seeded trained weights for the 3-level network and the space-to-depth
+network (Sec. 3.5), made with the FP64 oracle.
 
 TEST INFRASTRUCTURE (see oracle/__init__.py): this script is run by hand and
-writes scenegen/weights_trained_3level.npy, the trained weight set the parity
-tests and the benchmark feed to both the oracle and the GPU path as an input.
+writes scenegen/weights_trained_3level.npy (--topology levels3) or
+scenegen/weights_trained_s2d.npy (--topology s2d), the trained weight sets the
+parity tests and the benchmark feed to both the oracle and the GPU path as an
+input.
 The weights never come from the GPU path: every step below is the oracle's
 own arithmetic (features, forward, adjoint, Eq. 2 loss, Adam).
 
@@ -23,7 +26,7 @@ emitter size entering through the r_hat feature of Sec. 3.1):
            alpha = 0.9 and the perturbed instances detached.
   start    He-normal weights, seed 3.
 
-Usage:  python -m oracle.train_weights [--steps N] [--scenes N]
+Usage:  python -m oracle.train_weights [--topology levels3|s2d] [--steps N] [--scenes N]
 """
 from __future__ import annotations
 
@@ -37,7 +40,8 @@ import scenegen
 from oracle import gather as G
 from oracle import network as N
 
-OUT = os.path.join(os.path.dirname(scenegen.__file__), "weights_trained_3level.npy")
+OUTS = {"levels3": os.path.join(os.path.dirname(scenegen.__file__), "weights_trained_3level.npy"),
+        "s2d": os.path.join(os.path.dirname(scenegen.__file__), "weights_trained_s2d.npy")}
 H, W, HS, WS, N_OBJ = 272, 480, 1024, 1024, 64
 CROP, BATCH = 64, 8
 
@@ -66,15 +70,21 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--steps", type=int, default=4000)
     ap.add_argument("--scenes", type=int, default=48)
-    ap.add_argument("--out", default=OUT)
+    ap.add_argument("--topology", choices=sorted(OUTS), default="levels3")
+    ap.add_argument("--out", default=None)
     args = ap.parse_args()
+    out = args.out or OUTS[args.topology]
+    s2d = args.topology == "s2d"
+    layers = N.layer_table_s2d(3) if s2d else N.layer_table(3)
+    fwd = N.forward_s2d if s2d else N.forward
+    step_fn = N.train_step_s2d if s2d else N.train_step
 
     t0 = time.time()
     data = [make_scene_data(k) for k in range(args.scenes)]
     val = [make_scene_data(k) for k in range(args.scenes, args.scenes + 2)]
     print(f"data: {args.scenes} scenes + 2 held out in {time.time() - t0:.0f} s", flush=True)
 
-    theta = scenegen.he_init_weights(3, N.layer_table(3)).astype(np.float64)
+    theta = scenegen.he_init_weights(3, layers).astype(np.float64)
     m = np.zeros_like(theta)
     v = np.zeros_like(theta)
     rng = np.random.Generator(np.random.PCG64(2301))
@@ -82,7 +92,7 @@ def main():
     def val_mse(th):
         errs = []
         for insts, target in val:
-            y = N.forward(insts[0], th)
+            y = fwd(insts[0], th)
             errs.append(float(np.mean((y - target) ** 2)))
         return errs
 
@@ -97,12 +107,12 @@ def main():
             feats.append([f[:, y0:y0 + CROP, x0:x0 + CROP] for f in insts])
             targets.append(target[y0:y0 + CROP, x0:x0 + CROP])
         lr = 2e-3 if 2 * step <= args.steps else (1e-3 if 5 * step <= 4 * args.steps else 3e-4)
-        theta, m, v, loss, _ = N.train_step(feats, targets, theta, m, v, step, lr=lr)
+        theta, m, v, loss, _ = step_fn(feats, targets, theta, m, v, step, lr=lr)
         if step % 100 == 0 or step == 1:
             print(f"step {step}: loss {loss:.5f} ({time.time() - t0:.0f} s)", flush=True)
     print(f"end: held-out MSE vs ray-cast target {val_mse(theta)}", flush=True)
-    np.save(args.out, theta.astype(np.float32))
-    print(f"wrote {args.out}", flush=True)
+    np.save(out, theta.astype(np.float32))
+    print(f"wrote {out}", flush=True)
 
 
 if __name__ == "__main__":

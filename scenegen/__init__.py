@@ -374,6 +374,18 @@ def trained_weights() -> np.ndarray:
     return np.load(TRAINED_WEIGHTS).astype(np.float32)
 
 
+TRAINED_WEIGHTS_S2D = os.path.join(os.path.dirname(os.path.abspath(__file__)), "weights_trained_s2d.npy")
+
+
+def trained_weights_s2d() -> np.ndarray:
+    """Seeded trained weights of the space-to-depth network (Sec. 3.5), same
+    recipe as trained_weights (`python -m oracle.train_weights --topology s2d`)."""
+    if not os.path.exists(TRAINED_WEIGHTS_S2D):
+        raise FileNotFoundError(f"{TRAINED_WEIGHTS_S2D} is missing "
+                                "(python -m oracle.train_weights --topology s2d writes it)")
+    return np.load(TRAINED_WEIGHTS_S2D).astype(np.float32)
+
+
 def he_init_weights(seed: int, layers) -> np.ndarray:
     """Seeded He-normal weights (std sqrt(2 / fan_in)), zero biases, flattened
     in the canonical order: for each layer OIHW weights then its bias."""

@@ -74,3 +74,12 @@ def test_s2d_weights_reject_other_forms_and_batches(ctx):
     assert ei.value.status == 7
     with pytest.raises(nsm.NSMError):
         nsm.Weights(ctx, _theta(9)[:-1], nsm.NSM_TOPO_S2D)
+
+
+@pytest.mark.parametrize("case", ["hard256", "soft256", "ragged"])
+def test_s2d_bf16_trained_weights(ctx, case):
+    """The seeded oracle-trained weights of the topology (steep shadow edges)."""
+    f = {"hard256": lambda: scenegen.hard_frame(256, 256, 512, 512, 8, 1),
+         "soft256": lambda: scenegen.soft_frame(256, 256, 512, 512, 8, 21),
+         "ragged": lambda: scenegen.soft_frame(68, 132, 300, 200, 8, 5)}[case]()
+    _check(ctx, f, scenegen.trained_weights_s2d())

@@ -542,3 +542,22 @@ def scenegen_s2d_theta(seed):
         parts.append(rng.standard_normal(co) * 0.05)
     del scenegen
     return np.concatenate(parts)
+
+
+def test_trained_s2d_weights_input():
+    """The committed trained weights of the space-to-depth network: canonical
+    size, finite, and on held-out scenes far closer to the ray-cast visibility
+    than the He-init weights training started from."""
+    import scenegen
+    from oracle import gather as G
+    th = scenegen.trained_weights_s2d().astype(np.float64)
+    assert th.shape == (sum(ci * co * k * k + co for (_, ci, co, k) in N.layer_table_s2d(3)),)
+    assert np.isfinite(th).all()
+    he = scenegen.he_init_weights(3, N.layer_table_s2d(3))
+    for soft in (False, True):
+        f = scenegen.render_frame(scenegen.random_scene(3000 + soft, 64, soft=soft), 128, 224, 512, 512)
+        target = (scenegen.soft_visibility(f, spp_side=8) if soft else scenegen.hard_visibility(f)).astype(np.float64)
+        feat, _, _ = G.features(f.pos4, f.nrm4, f.sm, f.view_proj, f.light_pos, f.cam_pos, f.r_hat, f.z_far, f.bias)
+        mse_tr = np.mean((N.forward_s2d(feat, th) - target) ** 2)
+        mse_he = np.mean((N.forward_s2d(feat, he) - target) ** 2)
+        assert mse_tr < 0.25 * mse_he, (soft, mse_tr, mse_he)
