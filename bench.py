@@ -553,6 +553,59 @@ def extra_penumbra_depth(nsm, scenegen, torch, device, reps):
             "receptive_field_px": 3 * 2 ** levels, "histogram_ms": ms}
 
 
+def deep_macs_per_pixel(levels):
+    """MACs per full-resolution pixel of the L-level network (level l runs at
+    1 / 4^l of the pixels): encoder 3x3 + 1x1, bottleneck, decoder 3x3 + 1x1, head."""
+    w = [16 << l for l in range(levels)]
+    m = 16.0
+    for l in range(levels - 1):
+        cin = 4 if l == 0 else w[l - 1]
+        cout = 16 if l == 0 else w[l - 1]
+        m += (cin * w[l] * 9 + w[l] * w[l] + w[l] * w[l] * 9 + w[l] * cout) / 4.0 ** l
+    b = levels - 1
+    return m + (w[b - 1] * w[b] * 9 + w[b] * w[b - 1]) / 4.0 ** b
+
+
+def extra_deep(nsm, scenegen, torch, device, reps):
+    """Sec. 3.6's deeper networks (3, 5, 7 levels; receptive fields 24, 96,
+    384 px) on a 1088x1920 soft frame (both sides multiples of 2^6), FP32 on
+    CUDA cores, unfused, He-initialised weights."""
+    Hd = 1088
+    f = scenegen.soft_frame(Hd, W, HS, WS, N_OBJ, SCENE_SEED + 10)
+    light = nsm.LightDesc(pos=tuple(f.light_pos), radius=f.light_radius, r_hat=f.r_hat, view_proj=f.view_proj,
+                          z_far=f.z_far, bias=f.bias, tan_half_fov=f.tan_half_fov)
+    pos4, nrm4, sm = (torch.from_numpy(x).to(device) for x in (f.pos4, f.nrm4, f.sm))
+    fr = nsm.make_frame(pos4, nrm4, sm, light, f.cam_pos)
+    ctx = nsm.Context()
+    vis = torch.empty((Hd, W), device=device)
+    sms = torch.cuda.get_device_properties(device).multi_processor_count
+    peak = fp32_alu_peak_tflops(sms, load_peaks()["sm_max_mhz"])
+    out = {"workload": f"{W}x{Hd} soft frame, 2048^2 map; He-initialised weights",
+           "precision": "FP32 CUDA cores, one kernel per layer (NHWC tensors in HBM)"}
+    for L in (3, 5, 7):
+        rng = np.random.default_rng(L)
+        n = nsm.nsm_param_count_levels(L)
+        theta = torch.from_numpy((rng.standard_normal(n) * 0.05).astype(np.float32)).to(device)
+        ws = torch.empty((nsm.nsm_infer_deep_workspace_bytes(Hd, W, L),), dtype=torch.uint8, device=device)
+        for _ in range(3):
+            nsm.nsm_infer_deep(ctx, fr, theta, L, ws, vis)
+        ev = _events(torch, 2 * reps)
+        for k in range(reps):
+            ev[2 * k].record()
+            nsm.nsm_infer_deep(ctx, fr, theta, L, ws, vis)
+            ev[2 * k + 1].record()
+        torch.cuda.synchronize()
+        ctx.check()
+        ms = sum(ev[2 * k].elapsed_time(ev[2 * k + 1]) for k in range(reps)) / reps
+        mac = deep_macs_per_pixel(L)
+        tflops = 2.0 * mac * Hd * W / (ms * 1e-3) / 1e12
+        out[f"levels_{L}"] = {"params": n, "receptive_field_px": 3 * 2 ** L, "mac_per_px": mac, "ms": ms,
+                              "mpix_s": Hd * W / (ms * 1e-3) / 1e6, "achieved_tflops": tflops,
+                              "roofline": {"bound": "alu", "peak_tflops": peak, "frac": tflops / peak}}
+    ctx.close()
+    return out
+
+
 def extra_generation(nsm, scenegen, torch, device, reps, with_cpu):
     """Training-data generation on the device (ray-cast G-buffer, shadow map,
     64-sample soft visibility) for the 1080p soft scene, next to the OpenMP C
@@ -773,6 +826,7 @@ def run_ours(args):
                                                                     not args.skip_error)),
                          ("serving_32_views", lambda: extra_serving(nsm, scenegen, torch, device, theta, 20)),
                          ("penumbra_depth_1080p", lambda: extra_penumbra_depth(nsm, scenegen, torch, device, 10)),
+                         ("deep_networks_1088p", lambda: extra_deep(nsm, scenegen, torch, device, 5)),
                          ("train_step", lambda: extra_train(nsm, scenegen, torch, device, theta, 10)),
                          ("scene_generation_1080p", lambda: extra_generation(nsm, scenegen, torch, device, 10,
                                                                              not args.skip_cpu))):

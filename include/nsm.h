@@ -386,6 +386,24 @@ nsm_status nsm_gen_visibility(int H, int W, const float* pos4, const float* nrm4
                               const float* light_pos, float radius, int spp_side, uint64_t seed, float eps,
                               int n_obj, const float* objects, float* vis, void* stream);
 
+/* ---------------------------------------------------------------- deeper networks */
+
+/* The encoder / decoder with L = 2 .. 7 levels (Sec. 3.6: the depth the 95th
+ * percentile penumbra asks for; 3, 5 and 7 levels have receptive fields of
+ * 24, 96 and 384 pixels), FP32 on CUDA cores, unfused.  Channel plan as for
+ * three levels with widths 16 * 2^l (see nsm_param_count): for each layer in
+ * the order enc0 3x3, enc0 1x1, ..., enc(L-2) 1x1, bottleneck 3x3, 1x1,
+ * dec(L-2) 3x3, 1x1, ..., dec0 3x3, 1x1, head, its OIHW weights then bias.
+ * nsm_param_count_levels: the vector's length (0 outside 2 .. 7; 39,521 for
+ * 3 levels, 654,881 for 5).  nsm_infer_deep: visibility of a device frame
+ * (H, W multiples of 2^(L-1), else NSM_ERR_SHAPE) from canonical FP32
+ * parameters on the device; workspace (device, 256-byte aligned) of
+ * nsm_infer_deep_workspace_bytes (84 floats per pixel).  Asynchronous. */
+size_t nsm_param_count_levels(int levels);
+size_t nsm_infer_deep_workspace_bytes(int H, int W, int levels);
+nsm_status nsm_infer_deep(nsm_ctx* ctx, const nsm_frame* frame, const float* dev_params, int levels,
+                          void* workspace, size_t workspace_bytes, float* vis_out, void* stream);
+
 /* ---------------------------------------------------------------- frame analysis */
 
 /* Temporal instability (Sec. 3.4, Eq. 3) of one pair of consecutive frames:

@@ -540,6 +540,7 @@ def _gen_sigs():
             "nsm_gen_shadowmap": [I, I, P, F, I, P, P, P],
             "nsm_gen_visibility": [I, I, P, P, P, P, F, I, ctypes.c_uint64, F, I, P, P, P],
             "nsm_temporal_instability": [I, I, P, P, P, P, P, P, P, F, P, P, P],
+            "nsm_infer_deep": [P, ctypes.POINTER(nsm_frame), P, I, P, ctypes.c_size_t, P, P],
             "nsm_penumbra_histogram": [I, I, P, P, F, F, I, P, P],
             "nsm_depth_for_penumbra": [P, I, F, P, P],
         }.items():
@@ -594,6 +595,27 @@ def penumbra_histogram(blocker, pos4, tan_half_fovy, bin_px, hist_inout, stream=
     _check(_gen_sigs().nsm_penumbra_histogram(H, W, _ptr(blocker), _ptr(pos4), float(tan_half_fovy), float(bin_px),
                                               int(hist_inout.numel()), _ptr(hist_inout), _stream(stream)),
            "nsm_penumbra_histogram")
+
+
+def nsm_param_count_levels(levels: int) -> int:
+    L = lib()
+    L.nsm_param_count_levels.restype = ctypes.c_size_t
+    L.nsm_param_count_levels.argtypes = [ctypes.c_int]
+    return int(L.nsm_param_count_levels(levels))
+
+
+def nsm_infer_deep_workspace_bytes(H: int, W: int, levels: int) -> int:
+    L = lib()
+    L.nsm_infer_deep_workspace_bytes.restype = ctypes.c_size_t
+    L.nsm_infer_deep_workspace_bytes.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int]
+    return int(L.nsm_infer_deep_workspace_bytes(H, W, levels))
+
+
+def nsm_infer_deep(ctx: Context, frame: nsm_frame, dev_params, levels: int, workspace, vis_out, stream=None):
+    """FP32 forward of the L-level network (L = 2 .. 7) on a device frame."""
+    _check(_gen_sigs().nsm_infer_deep(ctx.h, ctypes.byref(frame), _ptr(dev_params), int(levels), _ptr(workspace),
+                                      int(workspace.numel() * workspace.element_size()), _ptr(vis_out),
+                                      _stream(stream)), "nsm_infer_deep")
 
 
 def depth_for_penumbra(hist, bin_px):

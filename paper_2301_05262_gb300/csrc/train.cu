@@ -45,23 +45,32 @@ constexpr int TH = 8, TJ = 16, NT = TH * TJ;  // conv tile rows, threads per row
 template <int CIN, int COUT>
 struct FwdShape { static constexpr int PX = (COUT >= 64 || CIN >= 64) ? 2 : 4; };
 
-template <int CIN, int COUT, int K>
+// CB input channels are staged at a time (CB < CIN: the weights of each chunk
+// are staged with it), and a CTA computes the OB outputs of block blockIdx.y
+// (OB < COUT for wide layers); CB = CIN, OB = COUT stage everything once.
+template <int CIN, int COUT, int K, int CB = CIN, int OB = COUT>
 __global__ void __launch_bounds__(NT) conv_fwd_kernel(const float* __restrict__ x, const float* __restrict__ xm,
                                                       int relu_in, int N, int H, int W,
                                                       const float* __restrict__ w, int transpose_flip,
                                                       const float* __restrict__ b, const float* __restrict__ ym,
                                                       float* __restrict__ y) {
-    constexpr int P = K / 2, PX = FwdShape<CIN, COUT>::PX, TW = TJ * PX;
+    constexpr int P = K / 2, PX = FwdShape<CB, OB>::PX, TW = TJ * PX;
     constexpr int RH = TH + 2 * P, RW = TW + 2 * P, PS = (RH * RW) | 1;  // odd plane stride
+    constexpr bool ONCE = (CB == CIN);
+    static_assert(CIN % CB == 0 && COUT % OB == 0 && CB % 4 == 0 && OB % 4 == 0, "channel blocks");
     extern __shared__ float sm[];
-    float* xs = sm;                       // [CIN][PS]
-    float* ws = xs + CIN * PS;            // [tap][ci][co]
+    float* xs = sm;                       // [CB][PS]
+    float* ws = xs + CB * PS;             // [tap][ci of the chunk][co of the block]
     const int tid = threadIdx.x;
-    for (int i = tid; i < K * K * CIN * COUT; i += NT) {
-        const int co = i % COUT, ci = (i / COUT) % CIN, tap = i / (COUT * CIN);
-        ws[i] = transpose_flip ? __ldg(w + (static_cast<size_t>(ci) * COUT + co) * K * K + (K * K - 1 - tap))
-                               : __ldg(w + (static_cast<size_t>(co) * CIN + ci) * K * K + tap);
-    }
+    const int ob0 = blockIdx.y * OB;
+    auto stage_w = [&](int c0) {
+        for (int i = tid; i < K * K * CB * OB; i += NT) {
+            const int co = ob0 + i % OB, ci = c0 + (i / OB) % CB, tap = i / (OB * CB);
+            ws[i] = transpose_flip ? __ldg(w + (static_cast<size_t>(ci) * COUT + co) * K * K + (K * K - 1 - tap))
+                                   : __ldg(w + (static_cast<size_t>(co) * CIN + ci) * K * K + tap);
+        }
+    };
+    if (ONCE) stage_w(0);
     const int tx = (W + TW - 1) / TW, ty = (H + TH - 1) / TH;
     const long long ntiles = static_cast<long long>(N) * tx * ty;
     const int lr = tid / TJ, lj = tid % TJ;
@@ -69,52 +78,56 @@ __global__ void __launch_bounds__(NT) conv_fwd_kernel(const float* __restrict__ 
         const int n = static_cast<int>(t / (tx * ty));
         const int r = static_cast<int>(t % (tx * ty));
         const int y0 = (r / tx) * TH, x0 = (r % tx) * TW;
-        __syncthreads();
-        for (int i = tid; i < RH * RW * (CIN / 4); i += NT) {
-            const int c4 = i % (CIN / 4), q = i / (CIN / 4);
-            const int gy = y0 - P + q / RW, gx = x0 - P + q % RW;
-            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (gy >= 0 && gy < H && gx >= 0 && gx < W) {
-                const size_t idx = ((static_cast<size_t>(n) * H + gy) * W + gx) * CIN;
-                v = __ldg(reinterpret_cast<const float4*>(x + idx) + c4);
-                if (relu_in) v = make_float4(fmaxf(v.x, 0.f), fmaxf(v.y, 0.f), fmaxf(v.z, 0.f), fmaxf(v.w, 0.f));
-                if (xm) {
-                    const float4 m = __ldg(reinterpret_cast<const float4*>(xm + idx) + c4);
-                    v = make_float4(m.x > 0.f ? v.x : 0.f, m.y > 0.f ? v.y : 0.f, m.z > 0.f ? v.z : 0.f,
-                                    m.w > 0.f ? v.w : 0.f);
-                }
-            }
-            xs[(4 * c4 + 0) * PS + q] = v.x;
-            xs[(4 * c4 + 1) * PS + q] = v.y;
-            xs[(4 * c4 + 2) * PS + q] = v.z;
-            xs[(4 * c4 + 3) * PS + q] = v.w;
-        }
-        __syncthreads();
-        float acc[PX][COUT];
+        float acc[PX][OB];
 #pragma unroll
-        for (int o = 0; o < COUT; ++o) {
-            const float bo = b ? __ldg(b + o) : 0.f;
+        for (int o = 0; o < OB; ++o) {
+            const float bo = b ? __ldg(b + ob0 + o) : 0.f;
 #pragma unroll
             for (int p = 0; p < PX; ++p) acc[p][o] = bo;
         }
+#pragma unroll 1
+        for (int c0 = 0; c0 < CIN; c0 += CB) {
+            __syncthreads();
+            if (!ONCE) stage_w(c0);
+            for (int i = tid; i < RH * RW * (CB / 4); i += NT) {
+                const int c4 = i % (CB / 4), q = i / (CB / 4);
+                const int gy = y0 - P + q / RW, gx = x0 - P + q % RW;
+                float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (gy >= 0 && gy < H && gx >= 0 && gx < W) {
+                    const size_t idx = ((static_cast<size_t>(n) * H + gy) * W + gx) * CIN + c0;
+                    v = __ldg(reinterpret_cast<const float4*>(x + idx) + c4);
+                    if (relu_in) v = make_float4(fmaxf(v.x, 0.f), fmaxf(v.y, 0.f), fmaxf(v.z, 0.f), fmaxf(v.w, 0.f));
+                    if (xm) {
+                        const float4 m = __ldg(reinterpret_cast<const float4*>(xm + idx) + c4);
+                        v = make_float4(m.x > 0.f ? v.x : 0.f, m.y > 0.f ? v.y : 0.f, m.z > 0.f ? v.z : 0.f,
+                                        m.w > 0.f ? v.w : 0.f);
+                    }
+                }
+                xs[(4 * c4 + 0) * PS + q] = v.x;
+                xs[(4 * c4 + 1) * PS + q] = v.y;
+                xs[(4 * c4 + 2) * PS + q] = v.z;
+                xs[(4 * c4 + 3) * PS + q] = v.w;
+            }
+            __syncthreads();
 #pragma unroll
-        for (int tap = 0; tap < K * K; ++tap) {
-            const float* xin = xs + (lr + tap / K) * RW + (lj + tap % K);
-            const float4* wt = reinterpret_cast<const float4*>(ws + tap * CIN * COUT);
+            for (int tap = 0; tap < K * K; ++tap) {
+                const float* xin = xs + (lr + tap / K) * RW + (lj + tap % K);
+                const float4* wt = reinterpret_cast<const float4*>(ws + tap * CB * OB);
 #pragma unroll 2
-            for (int c = 0; c < CIN; ++c) {
-                float xv[PX];
+                for (int c = 0; c < CB; ++c) {
+                    float xv[PX];
 #pragma unroll
-                for (int p = 0; p < PX; ++p) xv[p] = xin[c * PS + TJ * p];
+                    for (int p = 0; p < PX; ++p) xv[p] = xin[c * PS + TJ * p];
 #pragma unroll
-                for (int o4 = 0; o4 < COUT / 4; ++o4) {
-                    const float4 wv = wt[c * (COUT / 4) + o4];
+                    for (int o4 = 0; o4 < OB / 4; ++o4) {
+                        const float4 wv = wt[c * (OB / 4) + o4];
 #pragma unroll
-                    for (int p = 0; p < PX; ++p) {
-                        acc[p][4 * o4 + 0] = fmaf(xv[p], wv.x, acc[p][4 * o4 + 0]);
-                        acc[p][4 * o4 + 1] = fmaf(xv[p], wv.y, acc[p][4 * o4 + 1]);
-                        acc[p][4 * o4 + 2] = fmaf(xv[p], wv.z, acc[p][4 * o4 + 2]);
-                        acc[p][4 * o4 + 3] = fmaf(xv[p], wv.w, acc[p][4 * o4 + 3]);
+                        for (int p = 0; p < PX; ++p) {
+                            acc[p][4 * o4 + 0] = fmaf(xv[p], wv.x, acc[p][4 * o4 + 0]);
+                            acc[p][4 * o4 + 1] = fmaf(xv[p], wv.y, acc[p][4 * o4 + 1]);
+                            acc[p][4 * o4 + 2] = fmaf(xv[p], wv.z, acc[p][4 * o4 + 2]);
+                            acc[p][4 * o4 + 3] = fmaf(xv[p], wv.w, acc[p][4 * o4 + 3]);
+                        }
                     }
                 }
             }
@@ -124,9 +137,9 @@ __global__ void __launch_bounds__(NT) conv_fwd_kernel(const float* __restrict__ 
         for (int p = 0; p < PX; ++p) {
             const int ox = x0 + lj + TJ * p;
             if (oy < H && ox < W) {
-                const size_t base = ((static_cast<size_t>(n) * H + oy) * W + ox) * COUT;
+                const size_t base = ((static_cast<size_t>(n) * H + oy) * W + ox) * COUT + ob0;
 #pragma unroll
-                for (int o4 = 0; o4 < COUT / 4; ++o4) {
+                for (int o4 = 0; o4 < OB / 4; ++o4) {
                     float4 v = make_float4(acc[p][4 * o4], acc[p][4 * o4 + 1], acc[p][4 * o4 + 2], acc[p][4 * o4 + 3]);
                     if (ym) {
                         const float4 m = __ldg(reinterpret_cast<const float4*>(ym + base) + o4);
@@ -266,12 +279,12 @@ __global__ void __launch_bounds__(WNT) conv_wgrad_kernel(const float* __restrict
         for (int o = tid; o < COUT; o += WNT) atomicAdd(db + o, dbs[o]);
 }
 
-template <int CIN, int COUT, int K>
+template <int CIN, int COUT, int K, int CB = CIN, int OB = COUT>
 cudaError_t conv_fwd(const float* x, const float* xm, int relu_in, int N, int H, int W, const float* w, int tf,
                      const float* b, const float* ym, float* y, cudaStream_t st) {
-    constexpr int P = K / 2, TW = TJ * FwdShape<CIN, COUT>::PX;
-    const size_t smem = sizeof(float) * (CIN * (((TH + 2 * P) * (TW + 2 * P)) | 1) + K * K * CIN * COUT);
-    auto kern = conv_fwd_kernel<CIN, COUT, K>;
+    constexpr int P = K / 2, TW = TJ * FwdShape<CB, OB>::PX;
+    const size_t smem = sizeof(float) * (CB * (((TH + 2 * P) * (TW + 2 * P)) | 1) + K * K * CB * OB);
+    auto kern = conv_fwd_kernel<CIN, COUT, K, CB, OB>;
     static bool attr = false;
     if (!attr) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
@@ -283,7 +296,8 @@ cudaError_t conv_fwd(const float* x, const float* xm, int relu_in, int N, int H,
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem) != cudaSuccess || per_sm < 1) per_sm = 1;
     const long long cap = static_cast<long long>(num_sms()) * per_sm;
-    kern<<<static_cast<int>(tiles < cap ? tiles : cap), NT, smem, st>>>(x, xm, relu_in, N, H, W, w, tf, b, ym, y);
+    const dim3 grid(static_cast<unsigned>(tiles < cap ? tiles : cap), COUT / OB);
+    kern<<<grid, NT, smem, st>>>(x, xm, relu_in, N, H, W, w, tf, b, ym, y);
     return cudaGetLastError();
 }
 
@@ -712,6 +726,47 @@ cudaError_t backward(const float* th, float* grad, const Buffers& b, int Nb, int
     NSM_TRY((conv_fwd<16, 16, 1>(b.gtmp, b.a1, 0, n, H, W, L.w1, 1, nullptr, b.a3, b.ga3, st)));
     NSM_TRY((conv_wgrad<4, 16, 3>(b.feat, 0, b.ga3, nullptr, n, H, W, L.dw3, L.db3, st)));
     if (gfeat) NSM_TRY((conv_fwd<16, 4, 3>(b.ga3, nullptr, 0, n, H, W, L.w3, 1, nullptr, nullptr, gfeat, st)));
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ layers of the deeper networks
+// Forward layers by runtime shape for the 2- to 7-level networks (Sec. 3.6):
+// the (C_in, C_out, k) of their layer tables; layers with more than 64
+// channels in or out staged in 32-channel input chunks and computed in blocks
+// of 64 outputs.
+cudaError_t conv_layer(int cin, int cout, int k, const float* x, int relu_in, int N, int H, int W, const float* w,
+                       const float* b, float* y, cudaStream_t st) {
+#define NSM_L(ci, co, kk, cb, ob)                                                                           \
+    if (cin == ci && cout == co && k == kk)                                                                 \
+        return conv_fwd<ci, co, kk, cb, ob>(x, nullptr, relu_in, N, H, W, w, 0, b, nullptr, y, st);
+    NSM_L(4, 16, 3, 4, 16) NSM_L(16, 16, 1, 16, 16) NSM_L(16, 16, 3, 16, 16) NSM_L(16, 32, 3, 16, 32)
+    NSM_L(32, 32, 1, 32, 32) NSM_L(32, 32, 3, 32, 32) NSM_L(32, 16, 1, 32, 16) NSM_L(32, 64, 3, 32, 64)
+    NSM_L(64, 64, 1, 64, 64) NSM_L(64, 64, 3, 32, 64) NSM_L(64, 32, 1, 64, 32) NSM_L(64, 128, 3, 32, 64)
+    NSM_L(128, 128, 1, 32, 64) NSM_L(128, 128, 3, 32, 64) NSM_L(128, 64, 1, 32, 64) NSM_L(128, 256, 3, 32, 64)
+    NSM_L(256, 128, 1, 32, 64) NSM_L(256, 256, 1, 32, 64) NSM_L(256, 256, 3, 32, 64) NSM_L(256, 512, 3, 32, 64)
+    NSM_L(512, 512, 1, 32, 64) NSM_L(512, 512, 3, 32, 64) NSM_L(512, 256, 1, 32, 64) NSM_L(512, 1024, 3, 32, 64)
+    NSM_L(1024, 512, 1, 32, 64)
+#undef NSM_L
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t pool_relu(const float* x, int N, int H, int W, int C, float* y, cudaStream_t st) {
+    pool_fwd_kernel<<<ew_grid(static_cast<size_t>(N) * (H / 2) * (W / 2) * C), 256, 0, st>>>(x, 1, N, H, W, C, y);
+    return cudaGetLastError();
+}
+
+cudaError_t up_add(const float* lo, const float* skip, int N, int H, int W, int C, float* y, cudaStream_t st) {
+    up_fwd_kernel<<<ew_grid(static_cast<size_t>(N) * H * W * C), 256, 0, st>>>(lo, skip, N, H, W, C, y);
+    return cudaGetLastError();
+}
+
+cudaError_t relu_copy(const float* x, size_t n, float* y, cudaStream_t st) {
+    relu_copy_kernel<<<ew_grid(n), 256, 0, st>>>(x, n, y);
+    return cudaGetLastError();
+}
+
+cudaError_t head(const float* a1, const float* wh, size_t npx, float* vis, cudaStream_t st) {
+    head_fwd_kernel<<<ew_grid(npx), 256, 0, st>>>(a1, wh, npx, vis);
     return cudaGetLastError();
 }
 

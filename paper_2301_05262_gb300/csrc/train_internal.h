@@ -29,5 +29,15 @@ cudaError_t loss_l1(const float* vis, const float* target, int B, int T, size_t 
 cudaError_t adam(float* theta, const float* grad, float* m, float* v, size_t n, float lr, float b1, float b2,
                  float eps, int step, cudaStream_t st);
 
+// Forward layers of the deeper networks (FP32 NHWC; conv_layer: zero-padded
+// "same" k x k convolution of relu?(x) plus bias, cudaErrorInvalidValue for a
+// shape outside the 2- to 7-level layer tables).
+cudaError_t conv_layer(int cin, int cout, int k, const float* x, int relu_in, int N, int H, int W, const float* w,
+                       const float* b, float* y, cudaStream_t st);
+cudaError_t pool_relu(const float* x, int N, int H, int W, int C, float* y, cudaStream_t st);        // avg2x2(relu(x))
+cudaError_t up_add(const float* lo, const float* skip, int N, int H, int W, int C, float* y, cudaStream_t st);
+cudaError_t relu_copy(const float* x, size_t n, float* y, cudaStream_t st);
+cudaError_t head(const float* a1, const float* wh, size_t npx, float* vis, cudaStream_t st);         // 16 -> 1, sigmoid
+
 }  // namespace tr
 }  // namespace nsm

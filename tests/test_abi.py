@@ -86,3 +86,14 @@ def test_depth_for_penumbra_host_logic(lib):
         assert nsm.depth_for_penumbra(h, 1.0) == (float(w), l)
     with pytest.raises(nsm.NSMError):
         nsm.depth_for_penumbra(np.zeros(4, np.uint32), 0.0)
+
+
+def test_deep_network_sizes(lib):
+    """Parameter counts of the 2- to 7-level networks equal the oracle's layer
+    tables (the paper prints 39,248 / 653,648 weights for 3 / 5 levels)."""
+    for L in range(2, 8):
+        assert nsm.nsm_param_count_levels(L) == N.param_count(L, with_bias=True)
+    assert N.param_count(5) == 653648
+    assert nsm.nsm_param_count_levels(1) == 0 and nsm.nsm_param_count_levels(8) == 0
+    assert nsm.nsm_infer_deep_workspace_bytes(64, 64, 5) >= 64 * 64 * 84 * 4
+    assert nsm.nsm_infer_deep_workspace_bytes(64, 64, 9) == 0

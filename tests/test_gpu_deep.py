@@ -1,0 +1,67 @@
+"""GPU parity of the deeper networks (Sec. 3.6: 2 to 7 levels, FP32, unfused)
+against the FP64 oracle forward with the same number of levels: max-abs
+<= 1e-4 on visibility; the 3-level result equals the fused FP32 form's to
+rounding."""
+import numpy as np
+import pytest
+
+import scenegen
+from oracle import gather as G
+from oracle import network as N
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+import paper_2301_05262_gb300 as nsm  # noqa: E402
+from gpu_helpers import DeviceFrame, run_infer  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = nsm.Context()
+    yield c
+    c.check()
+    c.close()
+
+
+def _deep(ctx, df, theta, L):
+    f = df.f
+    ws = torch.empty((nsm.nsm_infer_deep_workspace_bytes(f.H, f.W, L),), dtype=torch.uint8, device="cuda")
+    vis = torch.empty((f.H, f.W), device="cuda")
+    nsm.nsm_infer_deep(ctx, df.frame, torch.from_numpy(theta).cuda(), L, ws, vis)
+    torch.cuda.synchronize()
+    return vis.cpu().numpy().astype(np.float64)
+
+
+@pytest.mark.parametrize("L,H,W", [(2, 68, 132), (3, 96, 128), (4, 64, 200), (5, 128, 192), (6, 128, 192),
+                                   (7, 128, 192)])
+def test_deep_forward_matches_oracle(ctx, L, H, W):
+    f = scenegen.soft_frame(H, W, 256, 256, 16, 40 + L)
+    theta = scenegen.he_init_weights(L, N.layer_table(L)).astype(np.float32)
+    vis = _deep(ctx, DeviceFrame(f), theta, L)
+    feat, _, _ = G.features(f.pos4, f.nrm4, f.sm, f.view_proj, f.light_pos, f.cam_pos, f.r_hat, f.z_far, f.bias)
+    ref = N.forward(feat, theta.astype(np.float64), levels=L)
+    err = np.abs(vis - ref)
+    print(f"L={L} {H}x{W}: max {err.max():.2e}")
+    assert np.isfinite(vis).all() and err.max() <= 1e-4, err.max()
+
+
+def test_deep_three_levels_equals_the_fused_form(ctx):
+    f = scenegen.hard_frame(128, 256, 512, 512, 8, 1)
+    theta = scenegen.trained_weights()
+    df = DeviceFrame(f)
+    w = nsm.Weights(ctx, theta)
+    fused = run_infer(ctx, w, df, nsm.NSM_FP32).cpu().numpy().astype(np.float64)
+    assert np.abs(_deep(ctx, df, theta, 3) - fused).max() <= 2e-6
+
+
+def test_deep_rejects_bad_shapes(ctx):
+    f = scenegen.hard_frame(40, 64, 64, 64, 4, 2)   # 40 is not a multiple of 16
+    df = DeviceFrame(f)
+    theta = scenegen.he_init_weights(5, N.layer_table(5)).astype(np.float32)
+    ws = torch.empty((nsm.nsm_infer_deep_workspace_bytes(40, 64, 5),), dtype=torch.uint8, device="cuda")
+    with pytest.raises(nsm.NSMError) as ei:
+        nsm.nsm_infer_deep(ctx, df.frame, torch.from_numpy(theta).cuda(), 5, ws, torch.empty((40, 64), device="cuda"))
+    assert ei.value.status == 2
+    with pytest.raises(nsm.NSMError):
+        nsm.nsm_infer_deep(ctx, df.frame, torch.from_numpy(theta).cuda(), 8, ws, torch.empty((40, 64), device="cuda"))
