@@ -169,7 +169,10 @@ void nsm_weights_destroy(nsm_weights* w);
  *             (Sec. 3.6, suppl. Sec. 4); all three 0 where no blocker is found.
  * Texel index, hard bit and blocker window are computed in binary32 with a
  * fixed operation order and no contraction, so they are reproducible bit for
- * bit.  H, W >= 0 (0 = nothing to do). */
+ * bit.  H, W >= 0 (0 = nothing to do).  With blocker_out the call takes
+ * Ws * Hs * 16 bytes of device scratch (the map's 8 x 8 and 4 x 4 min / max
+ * tables) from a library-owned pool, in stream order, for the duration of its
+ * kernels; NSM_ERR_CUDA if that allocation fails. */
 nsm_status nsm_features(const nsm_frame* frame, float* feat_out, int32_t* texel_out,
                         uint32_t* hard_out, float* blocker_out, void* stream);
 

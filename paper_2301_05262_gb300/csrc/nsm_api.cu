@@ -65,6 +65,36 @@ LayerOffsets layer_offsets_s2d() {
     return o;
 }
 
+// A memory pool owned by the library, one per device, for scratch buffers that
+// live only for the kernels of one call (allocated and freed in stream order).
+// It keeps up to 512 MiB mapped between calls, so a per-frame caller does not
+// map and unmap pages every frame; the device's default pool is left alone.
+cudaError_t scratch_pool(cudaMemPool_t* out) {
+    static std::mutex m;
+    static cudaMemPool_t pools[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lk(m);
+    if (!pools[dev]) {
+        cudaMemPoolProps props{};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t p;
+        if ((e = cudaMemPoolCreate(&p, &props)) != cudaSuccess) return e;
+        uint64_t keep = 512ull << 20;
+        if ((e = cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &keep)) != cudaSuccess) {
+            cudaMemPoolDestroy(p);
+            return e;
+        }
+        pools[dev] = p;
+    }
+    *out = pools[dev];
+    return cudaSuccess;
+}
+
 int num_sms() {
     static int cached[64] = {0};
     int dev = 0;

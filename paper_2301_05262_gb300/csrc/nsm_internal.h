@@ -30,6 +30,8 @@ LayerOffsets layer_offsets_s2d();
 constexpr int kS2dHeadOut = 4;
 
 int num_sms();
+// The library's stream-ordered scratch pool for the current device.
+cudaError_t scratch_pool(cudaMemPool_t* out);
 
 // Message returned by nsm_last_error() on this thread.
 void set_last_error(const std::string& msg);

@@ -67,7 +67,7 @@ def test_features_1080p_full_size():
 
 
 def test_features_1080p_blocker_sampled_rows():
-    # full 16-row tile bands of the blocker kernel (staged windows), top and bottom edges
+    # 16-row bands of blocker CTAs (windows up to 65 texels, both table levels), top and bottom edges
     f = scenegen.soft_frame(1080, 1920, 2048, 2048, 64, 21)
     for rows in (np.s_[496:512, :], np.s_[1064:1080, :], np.s_[0:2, :]):
         _check_frame(f, blocker=True, sample=rows)
@@ -80,7 +80,7 @@ def test_features_hard_blocker_point_light_windows():
 
 
 def test_features_blocker_wide_texel_spacing():
-    # few pixels over a large map: tile boxes exceed the staging capacity (global-memory scan)
+    # few pixels over a large map: neighbouring windows barely overlap
     f = scenegen.soft_frame(48, 64, 2048, 2048, 16, 22)
     _check_frame(f, blocker=True)
 
@@ -102,3 +102,9 @@ def test_features_rejects_host_pointer():
     with pytest.raises(nsm.NSMError) as ei:
         nsm.nsm_features(fr, feat)
     assert ei.value.status == 1
+
+
+def test_features_blocker_map_smaller_than_a_square():
+    # a 7 x 6 map: every 8 x 8 / 4 x 4 table entry near the edges is clipped; windows < 8 texels
+    f = scenegen.soft_frame(24, 40, 6, 7, 6, 24)
+    _check_frame(f, blocker=True)
