@@ -401,7 +401,8 @@ nsm_status nsm_gen_visibility(int H, int W, const float* pos4, const float* nrm4
  * 3 levels, 654,881 for 5).  nsm_infer_deep: visibility of a device frame
  * (H, W multiples of 2^(L-1), else NSM_ERR_SHAPE) from canonical FP32
  * parameters on the device; workspace (device, 256-byte aligned) of
- * nsm_infer_deep_workspace_bytes (84 floats per pixel).  Asynchronous. */
+ * nsm_infer_deep_workspace_bytes (84 floats per pixel plus one per parameter:
+ * the weights re-laid out per call).  Asynchronous. */
 size_t nsm_param_count_levels(int levels);
 size_t nsm_infer_deep_workspace_bytes(int H, int W, int levels);
 nsm_status nsm_infer_deep(nsm_ctx* ctx, const nsm_frame* frame, const float* dev_params, int levels,

@@ -48,9 +48,12 @@ static size_t deep_param_count(int L) {
     return t.back().b + 1;
 }
 
-// workspace: gather parameters, features (4), and five full-resolution
-// 16-channel FP32 tensors (every level's tensors fit: w_l (H W / 4^l) <= 16 H W)
-static size_t deep_ws_floats(int H, int W) { return 64 + static_cast<size_t>(H) * W * (4 + 5 * 16); }
+// workspace: gather parameters, features (4), five full-resolution 16-channel
+// FP32 tensors (every level's tensors fit: w_l (H W / 4^l) <= 16 H W), and the
+// weights transposed to [tap][C_in][C_out] at their offsets in the vector
+static size_t deep_ws_floats(int H, int W, int L) {
+    return 64 + static_cast<size_t>(H) * W * (4 + 5 * 16) + deep_param_count(L);
+}
 
 }  // namespace nsm
 
@@ -65,7 +68,7 @@ size_t nsm_param_count_levels(int levels) {
 
 size_t nsm_infer_deep_workspace_bytes(int H, int W, int levels) {
     if (H <= 0 || W <= 0 || levels < 2 || levels > 7) return 0;
-    return deep_ws_floats(H, W) * sizeof(float);
+    return deep_ws_floats(H, W, levels) * sizeof(float);
 }
 
 nsm_status nsm_infer_deep(nsm_ctx* ctx, const nsm_frame* frame, const float* dev_params, int levels, void* workspace,
@@ -95,14 +98,17 @@ nsm_status nsm_infer_deep(nsm_ctx* ctx, const nsm_frame* frame, const float* dev
     float* h = a1 + 16 * hw;     // a level's input (pooled / bottleneck / decoder output)
     float* xin = h + 16 * hw;    // decoder input (up-sampled + skip)
     float* skip = xin + 16 * hw; // encoder outputs of levels 1 .. L-2, one after the other
+    float* wt = base + 64 + hw * (4 + 5 * 16);  // transposed weights
     const GatherParams g = make_gather(frame);
     cudaError_t e = cudaMemcpyAsync(dgp, &g, sizeof(g), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = tr::features_batch(dgp, 1, H, W, feat, st);
     const std::vector<DeepLayer> Ls = deep_layers(levels);
+    for (size_t i = 0; i + 1 < Ls.size() && e == cudaSuccess; ++i)  // every layer but the head
+        e = tr::transpose_to_tap_major(dev_params + Ls[i].w, Ls[i].cin, Ls[i].cout, Ls[i].k, wt + Ls[i].w, st);
     auto wd = [](int l) { return 16 << l; };
     auto conv = [&](int li, const float* x, int relu_in, int Hl, int Wl, float* y) {
         const DeepLayer& d = Ls[li];
-        return tr::conv_layer(d.cin, d.cout, d.k, x, relu_in, 1, Hl, Wl, dev_params + d.w, dev_params + d.b, y, st);
+        return tr::conv_layer(d.cin, d.cout, d.k, x, relu_in, 1, Hl, Wl, wt + d.w, dev_params + d.b, y, st);
     };
     std::vector<float*> skips(levels, nullptr);
     const float* cur = feat;

@@ -29,9 +29,10 @@ namespace tr {
 // ------------------------------------------------------------------ convolution
 // y[n,p,o] = b[o] + sum_{c,tap} Wc[o][c][tap] * xin(n, p + off(tap), c), zero padded,
 // xin = relu(x) if relu_in, x * (xm > 0) if xm, else x;  y *= (ym > 0) if ym.
-// Weights come as canonical OIHW (transpose_flip = 0) or as the weights of the
+// Weights come as canonical OIHW (transpose_flip = 0), as the weights of the
 // layer whose data gradient this is (transpose_flip = 1): Wc[o][c][tap] =
-// W[c][o][8 - tap].
+// W[c][o][8 - tap], or pre-transposed to [tap][c][o] (transpose_flip = 2,
+// so a chunk's weights are contiguous rows of outputs: coalesced staging).
 // Tile: 8 rows x 16 PX columns; thread (r, j) computes the PX pixels of row r
 // at columns j, j + 16, ... (neighbouring threads read neighbouring words) for
 // every output; per (tap, input channel) PX input words and COUT / 4
@@ -64,6 +65,14 @@ __global__ void __launch_bounds__(NT) conv_fwd_kernel(const float* __restrict__ 
     const int tid = threadIdx.x;
     const int ob0 = blockIdx.y * OB;
     auto stage_w = [&](int c0) {
+        if (transpose_flip == 2) {
+            for (int i = tid; i < K * K * CB * (OB / 4); i += NT) {  // float4 rows of OB outputs
+                const int o4 = i % (OB / 4), ci = c0 + (i / (OB / 4)) % CB, tap = i / ((OB / 4) * CB);
+                reinterpret_cast<float4*>(ws)[i] =
+                    __ldg(reinterpret_cast<const float4*>(w + (static_cast<size_t>(tap) * CIN + ci) * COUT + ob0) + o4);
+            }
+            return;
+        }
         for (int i = tid; i < K * K * CB * OB; i += NT) {
             const int co = ob0 + i % OB, ci = c0 + (i / OB) % CB, tap = i / (OB * CB);
             ws[i] = transpose_flip ? __ldg(w + (static_cast<size_t>(ci) * COUT + co) * K * K + (K * K - 1 - tap))
@@ -731,23 +740,53 @@ cudaError_t backward(const float* th, float* grad, const Buffers& b, int Nb, int
 
 // ------------------------------------------------------------------ layers of the deeper networks
 // Forward layers by runtime shape for the 2- to 7-level networks (Sec. 3.6):
-// the (C_in, C_out, k) of their layer tables; layers with more than 64
-// channels in or out staged in 32-channel input chunks and computed in blocks
-// of 64 outputs.
+// the (C_in, C_out, k) of their layer tables, weights pre-transposed to
+// [tap][C_in][C_out] (transpose_to_tap_major).  Layers with 64 or more
+// channels in or out are staged in 32-channel input chunks and computed in
+// blocks of 64 outputs; where that gives fewer than two CTAs per SM (the
+// coarse levels: few pixels, many channels) they take blocks of 16 outputs
+// and 16-channel chunks instead (4 pixels per thread, ~51 KB of shared
+// memory, several CTAs per SM).
 cudaError_t conv_layer(int cin, int cout, int k, const float* x, int relu_in, int N, int H, int W, const float* w,
                        const float* b, float* y, cudaStream_t st) {
+    const long long t64 = static_cast<long long>(N) * ((W + 31) / 32) * ((H + TH - 1) / TH) * (cout >= 64 ? cout / 64 : 1);
+    const bool narrow = t64 < 2LL * num_sms();
 #define NSM_L(ci, co, kk, cb, ob)                                                                           \
     if (cin == ci && cout == co && k == kk)                                                                 \
-        return conv_fwd<ci, co, kk, cb, ob>(x, nullptr, relu_in, N, H, W, w, 0, b, nullptr, y, st);
+        return conv_fwd<ci, co, kk, cb, ob>(x, nullptr, relu_in, N, H, W, w, 2, b, nullptr, y, st);
+#define NSM_W(ci, co, kk, cb, ob)                                                                           \
+    if (cin == ci && cout == co && k == kk)                                                                 \
+        return narrow ? conv_fwd<ci, co, kk, 16, 16>(x, nullptr, relu_in, N, H, W, w, 2, b, nullptr, y, st)  \
+                      : conv_fwd<ci, co, kk, cb, ob>(x, nullptr, relu_in, N, H, W, w, 2, b, nullptr, y, st);
     NSM_L(4, 16, 3, 4, 16) NSM_L(16, 16, 1, 16, 16) NSM_L(16, 16, 3, 16, 16) NSM_L(16, 32, 3, 16, 32)
-    NSM_L(32, 32, 1, 32, 32) NSM_L(32, 32, 3, 32, 32) NSM_L(32, 16, 1, 32, 16) NSM_L(32, 64, 3, 32, 64)
-    NSM_L(64, 64, 1, 64, 64) NSM_L(64, 64, 3, 32, 64) NSM_L(64, 32, 1, 64, 32) NSM_L(64, 128, 3, 32, 64)
-    NSM_L(128, 128, 1, 32, 64) NSM_L(128, 128, 3, 32, 64) NSM_L(128, 64, 1, 32, 64) NSM_L(128, 256, 3, 32, 64)
-    NSM_L(256, 128, 1, 32, 64) NSM_L(256, 256, 1, 32, 64) NSM_L(256, 256, 3, 32, 64) NSM_L(256, 512, 3, 32, 64)
-    NSM_L(512, 512, 1, 32, 64) NSM_L(512, 512, 3, 32, 64) NSM_L(512, 256, 1, 32, 64) NSM_L(512, 1024, 3, 32, 64)
-    NSM_L(1024, 512, 1, 32, 64)
+    NSM_L(32, 32, 1, 32, 32) NSM_L(32, 32, 3, 32, 32) NSM_L(32, 16, 1, 32, 16) NSM_W(32, 64, 3, 32, 64)
+    NSM_W(64, 64, 1, 64, 64) NSM_W(64, 64, 3, 16, 64) NSM_W(64, 32, 1, 64, 32) NSM_W(64, 128, 3, 16, 64)
+    NSM_W(128, 128, 1, 16, 64) NSM_W(128, 128, 3, 16, 64) NSM_W(128, 64, 1, 16, 64) NSM_W(128, 256, 3, 16, 64)
+    NSM_W(256, 128, 1, 16, 64) NSM_W(256, 256, 1, 16, 64) NSM_W(256, 256, 3, 16, 64) NSM_W(256, 512, 3, 16, 64)
+    NSM_W(512, 512, 1, 16, 64) NSM_W(512, 512, 3, 16, 64) NSM_W(512, 256, 1, 16, 64) NSM_W(512, 1024, 3, 16, 64)
+    NSM_W(1024, 512, 1, 16, 64)
+#undef NSM_W
 #undef NSM_L
     return cudaErrorInvalidValue;
+}
+
+// wt[(tap C_in + c) C_out + o] = w[(o C_in + c) k^2 + tap] for one layer
+__global__ void transpose_tap_major_kernel(const float* __restrict__ w, int cin, int cout, int kk,
+                                           float* __restrict__ wt) {
+    const size_t n = static_cast<size_t>(cin) * cout * kk;
+    for (size_t i = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; i < n;
+         i += static_cast<size_t>(gridDim.x) * blockDim.x) {
+        const int o = static_cast<int>(i % cout);
+        const size_t r = i / cout;
+        const int c = static_cast<int>(r % cin), tap = static_cast<int>(r / cin);
+        wt[i] = __ldg(w + (static_cast<size_t>(o) * cin + c) * kk + tap);
+    }
+}
+
+cudaError_t transpose_to_tap_major(const float* w, int cin, int cout, int k, float* wt, cudaStream_t st) {
+    transpose_tap_major_kernel<<<ew_grid(static_cast<size_t>(cin) * cout * k * k), 256, 0, st>>>(w, cin, cout, k * k,
+                                                                                                 wt);
+    return cudaGetLastError();
 }
 
 cudaError_t pool_relu(const float* x, int N, int H, int W, int C, float* y, cudaStream_t st) {

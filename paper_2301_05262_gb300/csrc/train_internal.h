@@ -30,9 +30,11 @@ cudaError_t adam(float* theta, const float* grad, float* m, float* v, size_t n, 
                  float eps, int step, cudaStream_t st);
 
 // Forward layers of the deeper networks (FP32 NHWC; conv_layer: zero-padded
-// "same" k x k convolution of relu?(x) plus bias, cudaErrorInvalidValue for a
-// shape outside the 2- to 7-level layer tables).
-cudaError_t conv_layer(int cin, int cout, int k, const float* x, int relu_in, int N, int H, int W, const float* w,
+// "same" k x k convolution of relu?(x) plus bias, weights in the [tap][C_in]
+// [C_out] layout transpose_to_tap_major writes from OIHW (16-byte aligned),
+// cudaErrorInvalidValue for a shape outside the 2- to 7-level layer tables).
+cudaError_t transpose_to_tap_major(const float* w, int cin, int cout, int k, float* wt, cudaStream_t st);
+cudaError_t conv_layer(int cin, int cout, int k, const float* x, int relu_in, int N, int H, int W, const float* wt,
                        const float* b, float* y, cudaStream_t st);
 cudaError_t pool_relu(const float* x, int N, int H, int W, int C, float* y, cudaStream_t st);        // avg2x2(relu(x))
 cudaError_t up_add(const float* lo, const float* skip, int N, int H, int W, int C, float* y, cudaStream_t st);

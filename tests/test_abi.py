@@ -95,5 +95,5 @@ def test_deep_network_sizes(lib):
         assert nsm.nsm_param_count_levels(L) == N.param_count(L, with_bias=True)
     assert N.param_count(5) == 653648
     assert nsm.nsm_param_count_levels(1) == 0 and nsm.nsm_param_count_levels(8) == 0
-    assert nsm.nsm_infer_deep_workspace_bytes(64, 64, 5) >= 64 * 64 * 84 * 4
+    assert nsm.nsm_infer_deep_workspace_bytes(64, 64, 5) >= (64 * 64 * 84 + N.param_count(5, with_bias=True)) * 4
     assert nsm.nsm_infer_deep_workspace_bytes(64, 64, 9) == 0
