@@ -655,13 +655,13 @@ cudaError_t forward(const float* th, const Buffers& b, int N, int Nb, int H, int
         relu_copy_kernel<<<ew_grid(n * p1 * 32), 256, 0, st>>>(b.a1, n * p1 * 32, s1);
         // bottleneck
         L = level(th, nullptr, BOTT_3, BOTT_1);
-        NSM_TRY((conv_fwd<32, 64, 3>(pp1, nullptr, 0, n, H2, W2, L.w3, 0, L.b3, nullptr, b.a3, st)));
+        NSM_TRY((conv_fwd<32, 64, 3, 16>(pp1, nullptr, 0, n, H2, W2, L.w3, 0, L.b3, nullptr, b.a3, st)));
         NSM_TRY((conv_fwd<64, 32, 1>(b.a3, nullptr, 1, n, H2, W2, L.w1, 0, L.b1, nullptr, b.a1, st)));
         relu_copy_kernel<<<ew_grid(n * p2 * 32), 256, 0, st>>>(b.a1, n * p2 * 32, bo);
         // level 1 decoder
         L = level(th, nullptr, DEC1_3, DEC1_1);
         up_fwd_kernel<<<ew_grid(n * p1 * 32), 256, 0, st>>>(bo, s1, n, H1, W1, 32, b.xin);
-        NSM_TRY((conv_fwd<32, 32, 3>(b.xin, nullptr, 0, n, H1, W1, L.w3, 0, L.b3, nullptr, b.a3, st)));
+        NSM_TRY((conv_fwd<32, 32, 3, 16>(b.xin, nullptr, 0, n, H1, W1, L.w3, 0, L.b3, nullptr, b.a3, st)));
         NSM_TRY((conv_fwd<32, 16, 1>(b.a3, nullptr, 1, n, H1, W1, L.w1, 0, L.b1, nullptr, b.a1, st)));
         relu_copy_kernel<<<ew_grid(n * p1 * 16), 256, 0, st>>>(b.a1, n * p1 * 16, d1);
         // level 0 decoder + head
@@ -700,22 +700,22 @@ cudaError_t backward(const float* th, float* grad, const Buffers& b, int Nb, int
     // ---- level 1 decoder: recompute x = up(bo) + s1, a3, a1
     L = level(th, grad, DEC1_3, DEC1_1);
     up_fwd_kernel<<<ew_grid(n * p1 * 32), 256, 0, st>>>(b.bo, b.s1, n, H1, W1, 32, b.xin);
-    NSM_TRY((conv_fwd<32, 32, 3>(b.xin, nullptr, 0, n, H1, W1, L.w3, 0, L.b3, nullptr, b.a3, st)));
+    NSM_TRY((conv_fwd<32, 32, 3, 16>(b.xin, nullptr, 0, n, H1, W1, L.w3, 0, L.b3, nullptr, b.a3, st)));
     NSM_TRY((conv_fwd<32, 16, 1>(b.a3, nullptr, 1, n, H1, W1, L.w1, 0, L.b1, nullptr, b.a1, st)));
     // g_a1 = g_d1 (a1 > 0)
     NSM_TRY((conv_wgrad<32, 16, 1>(b.a3, 1, b.glo, b.a1, n, H1, W1, L.dw1, L.db1, st)));
     NSM_TRY((conv_fwd<16, 32, 1>(b.glo, b.a1, 0, n, H1, W1, L.w1, 1, nullptr, b.a3, b.ga3, st)));
     NSM_TRY((conv_wgrad<32, 32, 3>(b.xin, 0, b.ga3, nullptr, n, H1, W1, L.dw3, L.db3, st)));
-    NSM_TRY((conv_fwd<32, 32, 3>(b.ga3, nullptr, 0, n, H1, W1, L.w3, 1, nullptr, nullptr, b.gskip, st)));  // g x1
+    NSM_TRY((conv_fwd<32, 32, 3, 16>(b.ga3, nullptr, 0, n, H1, W1, L.w3, 1, nullptr, nullptr, b.gskip, st)));  // g x1
     up_adj_kernel<<<ew_grid(n * p2 * 32), 256, 0, st>>>(b.gskip, n, H1, W1, 32, b.glo);  // g bo [n][H2][W2][32]
     // ---- bottleneck: recompute a3 = conv3(p1), a1
     L = level(th, grad, BOTT_3, BOTT_1);
-    NSM_TRY((conv_fwd<32, 64, 3>(b.p1, nullptr, 0, n, H2, W2, L.w3, 0, L.b3, nullptr, b.a3, st)));
+    NSM_TRY((conv_fwd<32, 64, 3, 16>(b.p1, nullptr, 0, n, H2, W2, L.w3, 0, L.b3, nullptr, b.a3, st)));
     NSM_TRY((conv_fwd<64, 32, 1>(b.a3, nullptr, 1, n, H2, W2, L.w1, 0, L.b1, nullptr, b.a1, st)));
     NSM_TRY((conv_wgrad<64, 32, 1>(b.a3, 1, b.glo, b.a1, n, H2, W2, L.dw1, L.db1, st)));
     NSM_TRY((conv_fwd<32, 64, 1>(b.glo, b.a1, 0, n, H2, W2, L.w1, 1, nullptr, b.a3, b.ga3, st)));
     NSM_TRY((conv_wgrad<32, 64, 3>(b.p1, 0, b.ga3, nullptr, n, H2, W2, L.dw3, L.db3, st)));
-    NSM_TRY((conv_fwd<64, 32, 3>(b.ga3, nullptr, 0, n, H2, W2, L.w3, 1, nullptr, nullptr, b.gx, st)));  // g p1
+    NSM_TRY((conv_fwd<64, 32, 3, 16>(b.ga3, nullptr, 0, n, H2, W2, L.w3, 1, nullptr, nullptr, b.gx, st)));  // g p1
     // ---- level 1 encoder: g_h1 = pool_adj(g p1) + g s1 ; recompute a3 = conv3(e0), a1
     L = level(th, grad, ENC1_3, ENC1_1);
     pool_adj_kernel<<<ew_grid(n * p1 * 32), 256, 0, st>>>(b.gx, n, H1, W1, 32, 0, b.glo);
