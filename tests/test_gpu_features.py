@@ -108,3 +108,10 @@ def test_features_blocker_map_smaller_than_a_square():
     # a 7 x 6 map: every 8 x 8 / 4 x 4 table entry near the edges is clipped; windows < 8 texels
     f = scenegen.soft_frame(24, 40, 6, 7, 6, 24)
     _check_frame(f, blocker=True)
+
+
+def test_features_2160p_4096_map_blocker_sampled_rows():
+    # the largest configuration: 256 MiB of table scratch, windows on a denser texel grid
+    f = scenegen.soft_frame(2160, 3840, 4096, 4096, 64, 31)
+    for rows in (np.s_[1072:1088, :], np.s_[2144:2160, :]):
+        _check_frame(f, blocker=True, sample=rows)
