@@ -49,20 +49,31 @@ struct FwdShape { static constexpr int PX = (COUT >= 64 || CIN >= 64) ? 2 : 4; }
 // CB input channels are staged at a time (CB < CIN: the weights of each chunk
 // are staged with it), and a CTA computes the OB outputs of block blockIdx.y
 // (OB < COUT for wide layers); CB = CIN, OB = COUT stage everything once.
-template <int CIN, int COUT, int K, int CB = CIN, int OB = COUT>
+// C1 > 0 fuses the level's 1x1 convolution (C1 outputs, OIHW weights w1, bias
+// b1) into the epilogue: y gets b1 + W1 relu(conv), rectified as well with
+// relu_out; the 3x3 result itself is not stored (the checkpointed forward
+// needs only the 1x1 output); the sums run in the order of the separate 1x1
+// layer, so the result is the same.
+template <int CIN, int COUT, int K, int CB = CIN, int OB = COUT, int C1 = 0>
 __global__ void __launch_bounds__(NT) conv_fwd_kernel(const float* __restrict__ x, const float* __restrict__ xm,
                                                       int relu_in, int N, int H, int W,
                                                       const float* __restrict__ w, int transpose_flip,
                                                       const float* __restrict__ b, const float* __restrict__ ym,
-                                                      float* __restrict__ y) {
+                                                      float* __restrict__ y, const float* __restrict__ w1,
+                                                      const float* __restrict__ b1, int relu_out) {
     constexpr int P = K / 2, PX = FwdShape<CB, OB>::PX, TW = TJ * PX;
     constexpr int RH = TH + 2 * P, RW = TW + 2 * P, PS = (RH * RW) | 1;  // odd plane stride
     constexpr bool ONCE = (CB == CIN);
     static_assert(CIN % CB == 0 && COUT % OB == 0 && CB % 4 == 0 && OB % 4 == 0, "channel blocks");
+    static_assert(C1 == 0 || (OB == COUT && C1 % 4 == 0), "the fused 1x1 needs every 3x3 output of a pixel");
     extern __shared__ float sm[];
     float* xs = sm;                       // [CB][PS]
     float* ws = xs + CB * PS;             // [tap][ci of the chunk][co of the block]
+    float* w1s = ws + K * K * CB * OB;    // fused 1x1: [c][o]
     const int tid = threadIdx.x;
+    if constexpr (C1 > 0) {
+        for (int i = tid; i < C1 * COUT; i += NT) w1s[i] = __ldg(w1 + (i % C1) * COUT + i / C1);
+    }
     const int ob0 = blockIdx.y * OB;
     auto stage_w = [&](int c0) {
         if (transpose_flip == 2) {
@@ -142,6 +153,33 @@ __global__ void __launch_bounds__(NT) conv_fwd_kernel(const float* __restrict__ 
             }
         }
         const int oy = y0 + lr;
+        if constexpr (C1 > 0) {
+            const float4* w14 = reinterpret_cast<const float4*>(w1s);
+#pragma unroll
+            for (int p = 0; p < PX; ++p) {
+                const int ox = x0 + lj + TJ * p;
+                if (oy < H && ox < W) {
+#pragma unroll
+                    for (int c = 0; c < COUT; ++c) acc[p][c] = fmaxf(acc[p][c], 0.f);
+                    float4* dst = reinterpret_cast<float4*>(y + ((static_cast<size_t>(n) * H + oy) * W + ox) * C1);
+#pragma unroll 1
+                    for (int o4 = 0; o4 < C1 / 4; ++o4) {
+                        float4 s = __ldg(reinterpret_cast<const float4*>(b1) + o4);
+#pragma unroll
+                        for (int c = 0; c < COUT; ++c) {
+                            const float4 wv = w14[c * (C1 / 4) + o4];
+                            s.x = fmaf(acc[p][c], wv.x, s.x);
+                            s.y = fmaf(acc[p][c], wv.y, s.y);
+                            s.z = fmaf(acc[p][c], wv.z, s.z);
+                            s.w = fmaf(acc[p][c], wv.w, s.w);
+                        }
+                        if (relu_out) s = make_float4(fmaxf(s.x, 0.f), fmaxf(s.y, 0.f), fmaxf(s.z, 0.f), fmaxf(s.w, 0.f));
+                        dst[o4] = s;
+                    }
+                }
+            }
+            continue;
+        }
 #pragma unroll
         for (int p = 0; p < PX; ++p) {
             const int ox = x0 + lj + TJ * p;
@@ -288,12 +326,13 @@ __global__ void __launch_bounds__(WNT) conv_wgrad_kernel(const float* __restrict
         for (int o = tid; o < COUT; o += WNT) atomicAdd(db + o, dbs[o]);
 }
 
-template <int CIN, int COUT, int K, int CB = CIN, int OB = COUT>
+template <int CIN, int COUT, int K, int CB = CIN, int OB = COUT, int C1 = 0>
 cudaError_t conv_fwd(const float* x, const float* xm, int relu_in, int N, int H, int W, const float* w, int tf,
-                     const float* b, const float* ym, float* y, cudaStream_t st) {
+                     const float* b, const float* ym, float* y, cudaStream_t st, const float* w1 = nullptr,
+                     const float* b1 = nullptr, int relu_out = 0) {
     constexpr int P = K / 2, TW = TJ * FwdShape<CB, OB>::PX;
-    const size_t smem = sizeof(float) * (CB * (((TH + 2 * P) * (TW + 2 * P)) | 1) + K * K * CB * OB);
-    auto kern = conv_fwd_kernel<CIN, COUT, K, CB, OB>;
+    const size_t smem = sizeof(float) * (CB * (((TH + 2 * P) * (TW + 2 * P)) | 1) + K * K * CB * OB + C1 * COUT);
+    auto kern = conv_fwd_kernel<CIN, COUT, K, CB, OB, C1>;
     static bool attr = false;
     if (!attr) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
@@ -306,7 +345,7 @@ cudaError_t conv_fwd(const float* x, const float* xm, int relu_in, int N, int H,
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem) != cudaSuccess || per_sm < 1) per_sm = 1;
     const long long cap = static_cast<long long>(num_sms()) * per_sm;
     const dim3 grid(static_cast<unsigned>(tiles < cap ? tiles : cap), COUT / OB);
-    kern<<<grid, NT, smem, st>>>(x, xm, relu_in, N, H, W, w, tf, b, ym, y);
+    kern<<<grid, NT, smem, st>>>(x, xm, relu_in, N, H, W, w, tf, b, ym, y, w1, b1, relu_out);
     return cudaGetLastError();
 }
 
@@ -643,32 +682,28 @@ cudaError_t forward(const float* th, const Buffers& b, int N, int Nb, int H, int
         Level L;
         // level 0 encoder
         L = level(th, nullptr, ENC0_3, ENC0_1);
-        NSM_TRY((conv_fwd<4, 16, 3>(feat, nullptr, 0, n, H, W, L.w3, 0, L.b3, nullptr, b.a3, st)));
-        NSM_TRY((conv_fwd<16, 16, 1>(b.a3, nullptr, 1, n, H, W, L.w1, 0, L.b1, nullptr, b.a1, st)));
+        NSM_TRY((conv_fwd<4, 16, 3, 4, 16, 16>(feat, nullptr, 0, n, H, W, L.w3, 0, L.b3, nullptr, b.a1, st, L.w1, L.b1)));
         pool_fwd_kernel<<<ew_grid(n * p1 * 16), 256, 0, st>>>(b.a1, 1, n, H, W, 16, e0);
         // level 1 encoder
         L = level(th, nullptr, ENC1_3, ENC1_1);
-        NSM_TRY((conv_fwd<16, 32, 3>(e0, nullptr, 0, n, H1, W1, L.w3, 0, L.b3, nullptr, b.a3, st)));
-        NSM_TRY((conv_fwd<32, 32, 1>(b.a3, nullptr, 1, n, H1, W1, L.w1, 0, L.b1, nullptr, b.a1, st)));
-        pool_fwd_kernel<<<ew_grid(n * p2 * 32), 256, 0, st>>>(b.a1, 1, n, H1, W1, 32, pp1);
-        // the decoder skip is relu(a1) of level 1
-        relu_copy_kernel<<<ew_grid(n * p1 * 32), 256, 0, st>>>(b.a1, n * p1 * 32, s1);
+        // the decoder skip relu(a1) of level 1 is written directly
+        NSM_TRY((conv_fwd<16, 32, 3, 16, 32, 32>(e0, nullptr, 0, n, H1, W1, L.w3, 0, L.b3, nullptr, s1, st, L.w1, L.b1,
+                                                 1)));
+        pool_fwd_kernel<<<ew_grid(n * p2 * 32), 256, 0, st>>>(s1, 1, n, H1, W1, 32, pp1);
         // bottleneck
         L = level(th, nullptr, BOTT_3, BOTT_1);
-        NSM_TRY((conv_fwd<32, 64, 3, 16>(pp1, nullptr, 0, n, H2, W2, L.w3, 0, L.b3, nullptr, b.a3, st)));
-        NSM_TRY((conv_fwd<64, 32, 1>(b.a3, nullptr, 1, n, H2, W2, L.w1, 0, L.b1, nullptr, b.a1, st)));
-        relu_copy_kernel<<<ew_grid(n * p2 * 32), 256, 0, st>>>(b.a1, n * p2 * 32, bo);
+        NSM_TRY((conv_fwd<32, 64, 3, 16, 64, 32>(pp1, nullptr, 0, n, H2, W2, L.w3, 0, L.b3, nullptr, bo, st, L.w1, L.b1,
+                                                 1)));
         // level 1 decoder
         L = level(th, nullptr, DEC1_3, DEC1_1);
         up_fwd_kernel<<<ew_grid(n * p1 * 32), 256, 0, st>>>(bo, s1, n, H1, W1, 32, b.xin);
-        NSM_TRY((conv_fwd<32, 32, 3, 16>(b.xin, nullptr, 0, n, H1, W1, L.w3, 0, L.b3, nullptr, b.a3, st)));
-        NSM_TRY((conv_fwd<32, 16, 1>(b.a3, nullptr, 1, n, H1, W1, L.w1, 0, L.b1, nullptr, b.a1, st)));
-        relu_copy_kernel<<<ew_grid(n * p1 * 16), 256, 0, st>>>(b.a1, n * p1 * 16, d1);
+        NSM_TRY((conv_fwd<32, 32, 3, 16, 32, 16>(b.xin, nullptr, 0, n, H1, W1, L.w3, 0, L.b3, nullptr, d1, st, L.w1, L.b1,
+                                                 1)));
         // level 0 decoder + head
         L = level(th, nullptr, DEC0_3, DEC0_1);
         up_fwd_kernel<<<ew_grid(n * p0 * 16), 256, 0, st>>>(d1, nullptr, n, H, W, 16, b.xin);
-        NSM_TRY((conv_fwd<16, 16, 3>(b.xin, nullptr, 0, n, H, W, L.w3, 0, L.b3, nullptr, b.a3, st)));
-        NSM_TRY((conv_fwd<16, 16, 1>(b.a3, nullptr, 1, n, H, W, L.w1, 0, L.b1, nullptr, b.a1, st)));
+        NSM_TRY((conv_fwd<16, 16, 3, 16, 16, 16>(b.xin, nullptr, 0, n, H, W, L.w3, 0, L.b3, nullptr, b.a1, st, L.w1,
+                                                 L.b1)));
         head_fwd_kernel<<<ew_grid(n * p0), 256, 0, st>>>(b.a1, th + o.w[HEAD], n * p0, vis);
         NSM_TRY(cudaGetLastError());
     }
