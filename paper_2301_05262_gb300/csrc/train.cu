@@ -202,27 +202,29 @@ __global__ void __launch_bounds__(NT) conv_fwd_kernel(const float* __restrict__ 
 
 // dW[o][c][tap] += sum_p g~[p][o] xin[p + off(tap)][c];  db[o] += sum_p g~[p][o],
 // g~ = g * (gm > 0) if gm.  Register-blocked outer products: the weights are
-// cut into blocks of 4 outputs x 4 inputs of one tap; thread t owns blocks
-// t, t + WNT, ... (16 accumulators each, kept in registers over every tile
-// the CTA visits) and, when there are fewer blocks than threads, one residue
-// class of the tile's pixels.  Per pixel a block takes one 16-byte load of g~
-// (4 outputs) and one of xin (4 inputs) for 16 FMAs.  Pixel classes meet in
-// shared memory at the end; one atomicAdd per weight per CTA.
-constexpr int WTH = 8, WTW = 32, WNT = 256;  // wgrad pixel tile, threads
+// cut into blocks of 8 outputs x 8 inputs (4 where C_in = 4) of one tap;
+// thread t owns blocks t, t + WNT, ... (64 accumulators each, kept in
+// registers over every tile the CTA visits) and, when there are fewer blocks
+// than threads, one residue class of the tile's pixels.  Per pixel a block
+// takes two 16-byte loads of g~ and two of xin for 64 FMAs.  WNT = 9 x 32:
+// every layer's block count times its pixel classes fills it exactly.  Pixel
+// classes meet in shared memory at the end; one atomicAdd per weight per CTA.
+constexpr int WTH = 8, WTW = 32, WNT = 288;  // wgrad pixel tile, threads
 
 template <int CIN, int COUT, int K>
-__global__ void __launch_bounds__(WNT) conv_wgrad_kernel(const float* __restrict__ x, int relu_in,
-                                                         const float* __restrict__ g, const float* __restrict__ gm,
-                                                         int N, int H, int W, float* __restrict__ dW,
-                                                         float* __restrict__ db) {
+__global__ void __launch_bounds__(WNT, 2) conv_wgrad_kernel(const float* __restrict__ x, int relu_in,
+                                                            const float* __restrict__ g, const float* __restrict__ gm,
+                                                            int N, int H, int W, float* __restrict__ dW,
+                                                            float* __restrict__ db) {
     constexpr int P = K / 2;
     constexpr int RH = WTH + 2 * P, RW = WTW + 2 * P, NPX = WTH * WTW;
-    constexpr int OB = COUT / 4, CB = CIN / 4, TAPS = K * K;
+    constexpr int BO = 8, BI = CIN % 8 == 0 ? 8 : 4, BE = BO * BI;
+    constexpr int OB = COUT / BO, CB = CIN / BI, TAPS = K * K;
     constexpr int NB = TAPS * OB * CB;                  // weight blocks
     constexpr int PL = NB >= WNT ? 1 : WNT / NB;        // pixel classes
     constexpr int NBT = (NB + WNT - 1) / WNT;           // blocks per thread
-    constexpr int NW = NB * 16;
-    static_assert(CIN % 4 == 0 && COUT % 4 == 0, "channel blocks of 4");
+    constexpr int NW = NB * BE;
+    static_assert(CIN % BI == 0 && COUT % BO == 0, "channel blocks");
     static_assert(PL == 1 || NW <= RH * RW * CIN, "pixel-class reduction reuses the input tile");
     extern __shared__ float4 sm4[];
     float* xs = reinterpret_cast<float*>(sm4);  // [RH][RW][CIN]
@@ -231,11 +233,11 @@ __global__ void __launch_bounds__(WNT) conv_wgrad_kernel(const float* __restrict
     const int tid = threadIdx.x;
     const int pl = PL == 1 ? 0 : tid / NB;
     const bool active = PL == 1 || tid < NB * PL;
-    float acc[NBT][16];
+    float acc[NBT][BE];
 #pragma unroll
     for (int k = 0; k < NBT; ++k)
 #pragma unroll
-        for (int e = 0; e < 16; ++e) acc[k][e] = 0.f;
+        for (int e = 0; e < BE; ++e) acc[k][e] = 0.f;
     for (int i = tid; i < COUT; i += WNT) dbs[i] = 0.f;
     const int tx = (W + WTW - 1) / WTW, ty = (H + WTH - 1) / WTH;
     const long long ntiles = static_cast<long long>(N) * tx * ty;
@@ -281,26 +283,35 @@ __global__ void __launch_bounds__(WNT) conv_wgrad_kernel(const float* __restrict
                 const int b = PL == 1 ? tid + k * WNT : tid % NB;
                 if (b >= NB) continue;
                 const int cb = b % CB, ob = (b / CB) % OB, tap = b / (CB * OB);
-                const float* gp = gs + 4 * ob;
-                const float* xp = xs + ((tap / K) * RW + (tap % K)) * CIN + 4 * cb;
-#pragma unroll 4
+                const float* gp = gs + BO * ob;
+                const float* xp = xs + ((tap / K) * RW + (tap % K)) * CIN + BI * cb;
+#pragma unroll 2
                 for (int q = pl; q < NPX; q += PL) {
-                    const float4 g4 = *reinterpret_cast<const float4*>(gp + q * COUT);
-                    const float4 x4 = *reinterpret_cast<const float4*>(xp + ((q / WTW) * RW + (q % WTW)) * CIN);
-                    const float gv[4] = {g4.x, g4.y, g4.z, g4.w}, xv[4] = {x4.x, x4.y, x4.z, x4.w};
+                    float gv[BO], xv[BI];
 #pragma unroll
-                    for (int i = 0; i < 4; ++i)
+                    for (int h = 0; h < BO / 4; ++h) {
+                        const float4 g4 = *reinterpret_cast<const float4*>(gp + q * COUT + 4 * h);
+                        gv[4 * h] = g4.x; gv[4 * h + 1] = g4.y; gv[4 * h + 2] = g4.z; gv[4 * h + 3] = g4.w;
+                    }
 #pragma unroll
-                        for (int j = 0; j < 4; ++j) acc[k][4 * i + j] = fmaf(gv[i], xv[j], acc[k][4 * i + j]);
+                    for (int h = 0; h < BI / 4; ++h) {
+                        const float4 x4 =
+                            *reinterpret_cast<const float4*>(xp + ((q / WTW) * RW + (q % WTW)) * CIN + 4 * h);
+                        xv[4 * h] = x4.x; xv[4 * h + 1] = x4.y; xv[4 * h + 2] = x4.z; xv[4 * h + 3] = x4.w;
+                    }
+#pragma unroll
+                    for (int i = 0; i < BO; ++i)
+#pragma unroll
+                        for (int j = 0; j < BI; ++j) acc[k][BI * i + j] = fmaf(gv[i], xv[j], acc[k][BI * i + j]);
                 }
             }
         }
     }
     __syncthreads();
-    // weight e = (o CIN + c) TAPS + tap of block b, element (i, j): o = 4 ob + i, c = 4 cb + j
+    // weight e = (o CIN + c) TAPS + tap of block b, element (i, j): o = BO ob + i, c = BI cb + j
     auto widx = [&](int b, int i, int j) {
         const int cb = b % CB, ob = (b / CB) % OB, tap = b / (CB * OB);
-        return ((4 * ob + i) * CIN + 4 * cb + j) * TAPS + tap;
+        return ((BO * ob + i) * CIN + BI * cb + j) * TAPS + tap;
     };
     if constexpr (PL == 1) {
 #pragma unroll
@@ -308,7 +319,7 @@ __global__ void __launch_bounds__(WNT) conv_wgrad_kernel(const float* __restrict
             const int b = tid + k * WNT;
             if (b >= NB) continue;
 #pragma unroll
-            for (int e = 0; e < 16; ++e) atomicAdd(dW + widx(b, e / 4, e % 4), acc[k][e]);
+            for (int e = 0; e < BE; ++e) atomicAdd(dW + widx(b, e / BI, e % BI), acc[k][e]);
         }
     } else {
         float* red = xs;  // the pixel classes' partial sums meet here
@@ -317,7 +328,7 @@ __global__ void __launch_bounds__(WNT) conv_wgrad_kernel(const float* __restrict
         if (active) {
             const int b = tid % NB;
 #pragma unroll
-            for (int e = 0; e < 16; ++e) atomicAdd(red + widx(b, e / 4, e % 4), acc[0][e]);
+            for (int e = 0; e < BE; ++e) atomicAdd(red + widx(b, e / BI, e % BI), acc[0][e]);
         }
         __syncthreads();
         for (int e = tid; e < NW; e += WNT) atomicAdd(dW + e, red[e]);
