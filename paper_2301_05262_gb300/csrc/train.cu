@@ -337,6 +337,74 @@ __global__ void __launch_bounds__(WNT, 2) conv_wgrad_kernel(const float* __restr
         for (int o = tid; o < COUT; o += WNT) atomicAdd(db + o, dbs[o]);
 }
 
+// 1x1 weight gradients (no halo, so no tile staging): dW[o][c] += sum_p g~[p][o]
+// relu?(x[p][c]), db[o] += sum_p g~[p][o].  Thread t owns the 8 x 8 block
+// t % NB of (output, input) channels and walks the pixels t / NB, + PL, ...
+// of a grid-stride range with 16-byte loads straight from global memory (the
+// NB threads of a pixel share its lines in L1); lanes of a block meet by warp
+// shuffles, warps in shared memory, CTAs by one atomicAdd per weight.
+template <int CIN, int COUT>
+__global__ void __launch_bounds__(256) wgrad1x1_kernel(const float* __restrict__ x, int relu_in,
+                                                       const float* __restrict__ g, const float* __restrict__ gm,
+                                                       size_t npx, float* __restrict__ dW, float* __restrict__ db) {
+    constexpr int BO = 8, BI = 8, BE = BO * BI, OB = COUT / BO, CB = CIN / BI, NB = OB * CB, PL = 256 / NB;
+    static_assert(CIN % BI == 0 && COUT % BO == 0 && 256 % NB == 0 && NB <= 32, "1x1 blocks");
+    __shared__ float red[CIN * COUT + COUT];
+    const int tid = threadIdx.x, b = tid % NB, pl = tid / NB, ob = b / CB, cb = b % CB;
+    for (int i = tid; i < CIN * COUT + COUT; i += 256) red[i] = 0.f;
+    float acc[BE], dacc[BO];
+#pragma unroll
+    for (int e = 0; e < BE; ++e) acc[e] = 0.f;
+#pragma unroll
+    for (int i = 0; i < BO; ++i) dacc[i] = 0.f;
+    for (size_t p = static_cast<size_t>(blockIdx.x) * PL + pl; p < npx; p += static_cast<size_t>(gridDim.x) * PL) {
+        const float4* gp = reinterpret_cast<const float4*>(g + p * COUT + BO * ob);
+        const float4* xp = reinterpret_cast<const float4*>(x + p * CIN + BI * cb);
+        float4 g0 = __ldg(gp), g1 = __ldg(gp + 1), x0 = __ldg(xp), x1 = __ldg(xp + 1);
+        if (gm) {
+            const float4* mp = reinterpret_cast<const float4*>(gm + p * COUT + BO * ob);
+            const float4 m0 = __ldg(mp), m1 = __ldg(mp + 1);
+            g0 = make_float4(m0.x > 0.f ? g0.x : 0.f, m0.y > 0.f ? g0.y : 0.f, m0.z > 0.f ? g0.z : 0.f,
+                             m0.w > 0.f ? g0.w : 0.f);
+            g1 = make_float4(m1.x > 0.f ? g1.x : 0.f, m1.y > 0.f ? g1.y : 0.f, m1.z > 0.f ? g1.z : 0.f,
+                             m1.w > 0.f ? g1.w : 0.f);
+        }
+        const float gv[BO] = {g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, g1.z, g1.w};
+        float xv[BI] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
+        if (relu_in) {
+#pragma unroll
+            for (int j = 0; j < BI; ++j) xv[j] = fmaxf(xv[j], 0.f);
+        }
+#pragma unroll
+        for (int i = 0; i < BO; ++i) {
+            dacc[i] += gv[i];
+#pragma unroll
+            for (int j = 0; j < BI; ++j) acc[BI * i + j] = fmaf(gv[i], xv[j], acc[BI * i + j]);
+        }
+    }
+    // lanes l, l + NB, ... of a warp hold the same block
+#pragma unroll
+    for (int o = NB; o < 32; o <<= 1) {
+#pragma unroll
+        for (int e = 0; e < BE; ++e) acc[e] += __shfl_xor_sync(0xffffffffu, acc[e], o);
+#pragma unroll
+        for (int i = 0; i < BO; ++i) dacc[i] += __shfl_xor_sync(0xffffffffu, dacc[i], o);
+    }
+    __syncthreads();
+    if ((tid & 31) < NB) {
+#pragma unroll
+        for (int e = 0; e < BE; ++e) atomicAdd(red + (BO * ob + e / BI) * CIN + BI * cb + e % BI, acc[e]);
+        if (cb == 0) {
+#pragma unroll
+            for (int i = 0; i < BO; ++i) atomicAdd(red + CIN * COUT + BO * ob + i, dacc[i]);
+        }
+    }
+    __syncthreads();
+    for (int i = tid; i < CIN * COUT; i += 256) atomicAdd(dW + i, red[i]);
+    if (db)
+        for (int i = tid; i < COUT; i += 256) atomicAdd(db + i, red[CIN * COUT + i]);
+}
+
 template <int CIN, int COUT, int K, int CB = CIN, int OB = COUT, int C1 = 0>
 cudaError_t conv_fwd(const float* x, const float* xm, int relu_in, int N, int H, int W, const float* w, int tf,
                      const float* b, const float* ym, float* y, cudaStream_t st, const float* w1 = nullptr,
@@ -363,6 +431,15 @@ cudaError_t conv_fwd(const float* x, const float* xm, int relu_in, int N, int H,
 template <int CIN, int COUT, int K>
 cudaError_t conv_wgrad(const float* x, int relu_in, const float* g, const float* gm, int N, int H, int W, float* dW,
                        float* db, cudaStream_t st) {
+    if constexpr (K == 1 && CIN % 8 == 0) {
+        const size_t npx = static_cast<size_t>(N) * H * W;
+        if (npx == 0) return cudaSuccess;
+        const size_t per = 256 / ((COUT / 8) * (CIN / 8));  // pixels per CTA sweep
+        const size_t need = (npx + per - 1) / per, cap = static_cast<size_t>(num_sms()) * 4;
+        wgrad1x1_kernel<CIN, COUT><<<static_cast<int>(need < cap ? need : cap), 256, 0, st>>>(x, relu_in, g, gm, npx,
+                                                                                                dW, db);
+        return cudaGetLastError();
+    }
     constexpr int P = K / 2;
     const size_t smem = sizeof(float) * ((WTH + 2 * P) * (WTW + 2 * P) * CIN + WTH * WTW * COUT + COUT);
     auto kern = conv_wgrad_kernel<CIN, COUT, K>;
