@@ -40,6 +40,7 @@ namespace tr {
 // as channel planes with an odd plane stride (conflict-free transposing
 // stores from 16-byte NHWC loads).
 constexpr int TH = 8, TJ = 16, NT = TH * TJ;  // conv tile rows, threads per row
+static int ew_grid(size_t n);                  // grid of the element-wise kernels
 
 // pixels per thread: 4, or 2 where 64 channels in or out would need too many
 // accumulators or too much shared memory
@@ -405,10 +406,69 @@ __global__ void __launch_bounds__(256) wgrad1x1_kernel(const float* __restrict__
         for (int i = tid; i < COUT; i += 256) atomicAdd(db + i, red[CIN * COUT + i]);
 }
 
+// 1x1 layers (no halo, so no tile staging): one thread per pixel, the pixel's
+// input channels in registers, the weights ws[c][o] broadcast from shared
+// memory; same operand semantics as conv_fwd_kernel with K = 1, and the same
+// summation order (bias, then c = 0, 1, ...), so the same values.
+template <int CIN, int COUT>
+__global__ void __launch_bounds__(256) conv1x1_kernel(const float* __restrict__ x, const float* __restrict__ xm,
+                                                      int relu_in, size_t npx, const float* __restrict__ w, int tf,
+                                                      const float* __restrict__ b, const float* __restrict__ ym,
+                                                      float* __restrict__ y) {
+    static_assert(CIN % 4 == 0 && COUT % 4 == 0, "float4 channels");
+    __shared__ float4 ws4[CIN * COUT / 4];
+    float* ws = reinterpret_cast<float*>(ws4);
+    for (int i = threadIdx.x; i < CIN * COUT; i += blockDim.x) {
+        const int c = i / COUT, o = i % COUT;
+        ws[i] = tf ? __ldg(w + c * COUT + o) : __ldg(w + o * CIN + c);
+    }
+    __syncthreads();
+    for (size_t p = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; p < npx;
+         p += static_cast<size_t>(gridDim.x) * blockDim.x) {
+        float xv[CIN];
+#pragma unroll
+        for (int c4 = 0; c4 < CIN / 4; ++c4) {
+            float4 v = __ldg(reinterpret_cast<const float4*>(x + p * CIN) + c4);
+            if (relu_in) v = make_float4(fmaxf(v.x, 0.f), fmaxf(v.y, 0.f), fmaxf(v.z, 0.f), fmaxf(v.w, 0.f));
+            if (xm) {
+                const float4 m = __ldg(reinterpret_cast<const float4*>(xm + p * CIN) + c4);
+                v = make_float4(m.x > 0.f ? v.x : 0.f, m.y > 0.f ? v.y : 0.f, m.z > 0.f ? v.z : 0.f,
+                                m.w > 0.f ? v.w : 0.f);
+            }
+            xv[4 * c4] = v.x; xv[4 * c4 + 1] = v.y; xv[4 * c4 + 2] = v.z; xv[4 * c4 + 3] = v.w;
+        }
+        float4* dst = reinterpret_cast<float4*>(y + p * COUT);
+#pragma unroll 2
+        for (int o4 = 0; o4 < COUT / 4; ++o4) {
+            float4 s = b ? __ldg(reinterpret_cast<const float4*>(b) + o4) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+            for (int c = 0; c < CIN; ++c) {
+                const float4 wv = ws4[c * (COUT / 4) + o4];
+                s.x = fmaf(xv[c], wv.x, s.x);
+                s.y = fmaf(xv[c], wv.y, s.y);
+                s.z = fmaf(xv[c], wv.z, s.z);
+                s.w = fmaf(xv[c], wv.w, s.w);
+            }
+            if (ym) {
+                const float4 m = __ldg(reinterpret_cast<const float4*>(ym + p * COUT) + o4);
+                s = make_float4(m.x > 0.f ? s.x : 0.f, m.y > 0.f ? s.y : 0.f, m.z > 0.f ? s.z : 0.f,
+                                m.w > 0.f ? s.w : 0.f);
+            }
+            dst[o4] = s;
+        }
+    }
+}
+
 template <int CIN, int COUT, int K, int CB = CIN, int OB = COUT, int C1 = 0>
 cudaError_t conv_fwd(const float* x, const float* xm, int relu_in, int N, int H, int W, const float* w, int tf,
                      const float* b, const float* ym, float* y, cudaStream_t st, const float* w1 = nullptr,
                      const float* b1 = nullptr, int relu_out = 0) {
+    if constexpr (K == 1 && CB == CIN && OB == COUT && C1 == 0 && CIN * COUT <= 4096) {
+        const size_t npx = static_cast<size_t>(N) * H * W;
+        if (npx == 0) return cudaSuccess;
+        conv1x1_kernel<CIN, COUT><<<ew_grid(npx), 256, 0, st>>>(x, xm, relu_in, npx, w, tf, b, ym, y);
+        return cudaGetLastError();
+    }
     constexpr int P = K / 2, TW = TJ * FwdShape<CB, OB>::PX;
     const size_t smem = sizeof(float) * (CB * (((TH + 2 * P) * (TW + 2 * P)) | 1) + K * K * CB * OB + C1 * COUT);
     auto kern = conv_fwd_kernel<CIN, COUT, K, CB, OB, C1>;
