@@ -54,19 +54,24 @@ struct FwdShape { static constexpr int PX = (COUT >= 64 || CIN >= 64) ? 2 : 4; }
 // b1) into the epilogue: y gets b1 + W1 relu(conv), rectified as well with
 // relu_out; the 3x3 result itself is not stored (the checkpointed forward
 // needs only the 1x1 output); the sums run in the order of the separate 1x1
-// layer, so the result is the same.
-template <int CIN, int COUT, int K, int CB = CIN, int OB = COUT, int C1 = 0>
+// layer, so the result is the same.  POOL also writes yp = 2x2 average of
+// relu(y) (H, W even): the four pixels of a block are lanes l, l + 1, l + 16,
+// l + 17 of one warp, summed in the separate pooling kernel's order; y may
+// then be null.
+template <int CIN, int COUT, int K, int CB = CIN, int OB = COUT, int C1 = 0, int POOL = 0>
 __global__ void __launch_bounds__(NT) conv_fwd_kernel(const float* __restrict__ x, const float* __restrict__ xm,
                                                       int relu_in, int N, int H, int W,
                                                       const float* __restrict__ w, int transpose_flip,
                                                       const float* __restrict__ b, const float* __restrict__ ym,
                                                       float* __restrict__ y, const float* __restrict__ w1,
-                                                      const float* __restrict__ b1, int relu_out) {
+                                                      const float* __restrict__ b1, int relu_out,
+                                                      float* __restrict__ yp) {
     constexpr int P = K / 2, PX = FwdShape<CB, OB>::PX, TW = TJ * PX;
     constexpr int RH = TH + 2 * P, RW = TW + 2 * P, PS = (RH * RW) | 1;  // odd plane stride
     constexpr bool ONCE = (CB == CIN);
     static_assert(CIN % CB == 0 && COUT % OB == 0 && CB % 4 == 0 && OB % 4 == 0, "channel blocks");
     static_assert(C1 == 0 || (OB == COUT && C1 % 4 == 0), "the fused 1x1 needs every 3x3 output of a pixel");
+    static_assert(POOL == 0 || C1 > 0, "pooling follows the fused 1x1");
     extern __shared__ float sm[];
     float* xs = sm;                       // [CB][PS]
     float* ws = xs + CB * PS;             // [tap][ci of the chunk][co of the block]
@@ -159,42 +164,57 @@ __global__ void __launch_bounds__(NT) conv_fwd_kernel(const float* __restrict__ 
 #pragma unroll
             for (int p = 0; p < PX; ++p) {
                 const int ox = x0 + lj + TJ * p;
-                if (oy < H && ox < W) {
+                const bool ok = oy < H && ox < W;  // a 2x2 block is wholly in or out (H, W even)
+                if (!POOL && !ok) continue;
 #pragma unroll
-                    for (int c = 0; c < COUT; ++c) acc[p][c] = fmaxf(acc[p][c], 0.f);
-                    float4* dst = reinterpret_cast<float4*>(y + ((static_cast<size_t>(n) * H + oy) * W + ox) * C1);
+                for (int c = 0; c < COUT; ++c) acc[p][c] = fmaxf(acc[p][c], 0.f);
+                const size_t pix = (static_cast<size_t>(n) * H + oy) * W + ox;
 #pragma unroll 1
-                    for (int o4 = 0; o4 < C1 / 4; ++o4) {
-                        float4 s = __ldg(reinterpret_cast<const float4*>(b1) + o4);
+                for (int o4 = 0; o4 < C1 / 4; ++o4) {
+                    float4 s = __ldg(reinterpret_cast<const float4*>(b1) + o4);
 #pragma unroll
-                        for (int c = 0; c < COUT; ++c) {
-                            const float4 wv = w14[c * (C1 / 4) + o4];
-                            s.x = fmaf(acc[p][c], wv.x, s.x);
-                            s.y = fmaf(acc[p][c], wv.y, s.y);
-                            s.z = fmaf(acc[p][c], wv.z, s.z);
-                            s.w = fmaf(acc[p][c], wv.w, s.w);
+                    for (int c = 0; c < COUT; ++c) {
+                        const float4 wv = w14[c * (C1 / 4) + o4];
+                        s.x = fmaf(acc[p][c], wv.x, s.x);
+                        s.y = fmaf(acc[p][c], wv.y, s.y);
+                        s.z = fmaf(acc[p][c], wv.z, s.z);
+                        s.w = fmaf(acc[p][c], wv.w, s.w);
+                    }
+                    if (relu_out) s = make_float4(fmaxf(s.x, 0.f), fmaxf(s.y, 0.f), fmaxf(s.z, 0.f), fmaxf(s.w, 0.f));
+                    if (ok && y) reinterpret_cast<float4*>(y + pix * C1)[o4] = s;
+                    if constexpr (POOL) {
+                        const float v[4] = {fmaxf(s.x, 0.f), fmaxf(s.y, 0.f), fmaxf(s.z, 0.f), fmaxf(s.w, 0.f)};
+                        float q[4];
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            const float v01 = __shfl_down_sync(0xffffffffu, v[e], 1);
+                            const float v10 = __shfl_down_sync(0xffffffffu, v[e], 16);
+                            const float v11 = __shfl_down_sync(0xffffffffu, v[e], 17);
+                            q[e] = 0.25f * (((v[e] + v01) + v10) + v11);
                         }
-                        if (relu_out) s = make_float4(fmaxf(s.x, 0.f), fmaxf(s.y, 0.f), fmaxf(s.z, 0.f), fmaxf(s.w, 0.f));
-                        dst[o4] = s;
+                        if (ok && ((lr | lj) & 1) == 0)
+                            reinterpret_cast<float4*>(
+                                yp + ((static_cast<size_t>(n) * (H / 2) + oy / 2) * (W / 2) + ox / 2) * C1)[o4] =
+                                make_float4(q[0], q[1], q[2], q[3]);
                     }
                 }
             }
-            continue;
-        }
+        } else {
 #pragma unroll
-        for (int p = 0; p < PX; ++p) {
-            const int ox = x0 + lj + TJ * p;
-            if (oy < H && ox < W) {
-                const size_t base = ((static_cast<size_t>(n) * H + oy) * W + ox) * COUT + ob0;
+            for (int p = 0; p < PX; ++p) {
+                const int ox = x0 + lj + TJ * p;
+                if (oy < H && ox < W) {
+                    const size_t base = ((static_cast<size_t>(n) * H + oy) * W + ox) * COUT + ob0;
 #pragma unroll
-                for (int o4 = 0; o4 < OB / 4; ++o4) {
-                    float4 v = make_float4(acc[p][4 * o4], acc[p][4 * o4 + 1], acc[p][4 * o4 + 2], acc[p][4 * o4 + 3]);
-                    if (ym) {
-                        const float4 m = __ldg(reinterpret_cast<const float4*>(ym + base) + o4);
-                        v = make_float4(m.x > 0.f ? v.x : 0.f, m.y > 0.f ? v.y : 0.f, m.z > 0.f ? v.z : 0.f,
-                                        m.w > 0.f ? v.w : 0.f);
+                    for (int o4 = 0; o4 < OB / 4; ++o4) {
+                        float4 v = make_float4(acc[p][4 * o4], acc[p][4 * o4 + 1], acc[p][4 * o4 + 2], acc[p][4 * o4 + 3]);
+                        if (ym) {
+                            const float4 m = __ldg(reinterpret_cast<const float4*>(ym + base) + o4);
+                            v = make_float4(m.x > 0.f ? v.x : 0.f, m.y > 0.f ? v.y : 0.f, m.z > 0.f ? v.z : 0.f,
+                                            m.w > 0.f ? v.w : 0.f);
+                        }
+                        reinterpret_cast<float4*>(y + base)[o4] = v;
                     }
-                    reinterpret_cast<float4*>(y + base)[o4] = v;
                 }
             }
         }
@@ -459,10 +479,10 @@ __global__ void __launch_bounds__(256) conv1x1_kernel(const float* __restrict__ 
     }
 }
 
-template <int CIN, int COUT, int K, int CB = CIN, int OB = COUT, int C1 = 0>
+template <int CIN, int COUT, int K, int CB = CIN, int OB = COUT, int C1 = 0, int POOL = 0>
 cudaError_t conv_fwd(const float* x, const float* xm, int relu_in, int N, int H, int W, const float* w, int tf,
                      const float* b, const float* ym, float* y, cudaStream_t st, const float* w1 = nullptr,
-                     const float* b1 = nullptr, int relu_out = 0) {
+                     const float* b1 = nullptr, int relu_out = 0, float* yp = nullptr) {
     if constexpr (K == 1 && CB == CIN && OB == COUT && C1 == 0 && CIN * COUT <= 4096) {
         const size_t npx = static_cast<size_t>(N) * H * W;
         if (npx == 0) return cudaSuccess;
@@ -471,7 +491,7 @@ cudaError_t conv_fwd(const float* x, const float* xm, int relu_in, int N, int H,
     }
     constexpr int P = K / 2, TW = TJ * FwdShape<CB, OB>::PX;
     const size_t smem = sizeof(float) * (CB * (((TH + 2 * P) * (TW + 2 * P)) | 1) + K * K * CB * OB + C1 * COUT);
-    auto kern = conv_fwd_kernel<CIN, COUT, K, CB, OB, C1>;
+    auto kern = conv_fwd_kernel<CIN, COUT, K, CB, OB, C1, POOL>;
     static bool attr = false;
     if (!attr) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
@@ -484,7 +504,7 @@ cudaError_t conv_fwd(const float* x, const float* xm, int relu_in, int N, int H,
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem) != cudaSuccess || per_sm < 1) per_sm = 1;
     const long long cap = static_cast<long long>(num_sms()) * per_sm;
     const dim3 grid(static_cast<unsigned>(tiles < cap ? tiles : cap), COUT / OB);
-    kern<<<grid, NT, smem, st>>>(x, xm, relu_in, N, H, W, w, tf, b, ym, y, w1, b1, relu_out);
+    kern<<<grid, NT, smem, st>>>(x, xm, relu_in, N, H, W, w, tf, b, ym, y, w1, b1, relu_out, yp);
     return cudaGetLastError();
 }
 
@@ -830,14 +850,13 @@ cudaError_t forward(const float* th, const Buffers& b, int N, int Nb, int H, int
         Level L;
         // level 0 encoder
         L = level(th, nullptr, ENC0_3, ENC0_1);
-        NSM_TRY((conv_fwd<4, 16, 3, 4, 16, 16>(feat, nullptr, 0, n, H, W, L.w3, 0, L.b3, nullptr, b.a1, st, L.w1, L.b1)));
-        pool_fwd_kernel<<<ew_grid(n * p1 * 16), 256, 0, st>>>(b.a1, 1, n, H, W, 16, e0);
+        NSM_TRY((conv_fwd<4, 16, 3, 4, 16, 16, 1>(feat, nullptr, 0, n, H, W, L.w3, 0, L.b3, nullptr, nullptr, st, L.w1,
+                                                  L.b1, 0, e0)));
         // level 1 encoder
         L = level(th, nullptr, ENC1_3, ENC1_1);
         // the decoder skip relu(a1) of level 1 is written directly
-        NSM_TRY((conv_fwd<16, 32, 3, 16, 32, 32>(e0, nullptr, 0, n, H1, W1, L.w3, 0, L.b3, nullptr, s1, st, L.w1, L.b1,
-                                                 1)));
-        pool_fwd_kernel<<<ew_grid(n * p2 * 32), 256, 0, st>>>(s1, 1, n, H1, W1, 32, pp1);
+        NSM_TRY((conv_fwd<16, 32, 3, 16, 32, 32, 1>(e0, nullptr, 0, n, H1, W1, L.w3, 0, L.b3, nullptr, s1, st, L.w1,
+                                                    L.b1, 1, pp1)));
         // bottleneck
         L = level(th, nullptr, BOTT_3, BOTT_1);
         NSM_TRY((conv_fwd<32, 64, 3, 16, 64, 32>(pp1, nullptr, 0, n, H2, W2, L.w3, 0, L.b3, nullptr, bo, st, L.w1, L.b1,
