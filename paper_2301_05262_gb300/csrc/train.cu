@@ -42,6 +42,21 @@ namespace tr {
 constexpr int TH = 8, TJ = 16, NT = TH * TJ;  // conv tile rows, threads per row
 static int ew_grid(size_t n);                  // grid of the element-wise kernels
 
+// Bilinear x2 up-sampling (half-pixel centres, clamped) of channel group c4
+// (4 channels) of the coarse NHWC tensor lo (Hl x Wl, C4 groups) at fine
+// pixel (yy, x); one definition for every kernel that up-samples.
+__device__ __forceinline__ float4 up_sample4(const float4* __restrict__ lo4, int n, int Hl, int Wl, int C4, int yy,
+                                             int x, int c4) {
+    const BilinTap ty = bilin_tap(yy, Hl), tx = bilin_tap(x, Wl);
+    auto L = [&](int a, int b2) { return __ldg(lo4 + ((static_cast<size_t>(n) * Hl + a) * Wl + b2) * C4 + c4); };
+    const float4 a00 = L(ty.i0, tx.i0), a01 = L(ty.i0, tx.i1), a10 = L(ty.i1, tx.i0), a11 = L(ty.i1, tx.i1);
+    auto mix = [&](float v00, float v01, float v10, float v11) {
+        return (v00 * tx.w0 + v01 * tx.w1) * ty.w0 + (v10 * tx.w0 + v11 * tx.w1) * ty.w1;
+    };
+    return make_float4(mix(a00.x, a01.x, a10.x, a11.x), mix(a00.y, a01.y, a10.y, a11.y),
+                       mix(a00.z, a01.z, a10.z, a11.z), mix(a00.w, a01.w, a10.w, a11.w));
+}
+
 // pixels per thread: 4, or 2 where 64 channels in or out would need too many
 // accumulators or too much shared memory
 template <int CIN, int COUT>
@@ -57,8 +72,9 @@ struct FwdShape { static constexpr int PX = (COUT >= 64 || CIN >= 64) ? 2 : 4; }
 // layer, so the result is the same.  POOL also writes yp = 2x2 average of
 // relu(y) (H, W even): the four pixels of a block are lanes l, l + 1, l + 16,
 // l + 17 of one warp, summed in the separate pooling kernel's order; y may
-// then be null.
-template <int CIN, int COUT, int K, int CB = CIN, int OB = COUT, int C1 = 0, int POOL = 0>
+// then be null.  UPIN: the input is up(x) + xm, x the coarse (H/2 x W/2)
+// tensor and xm the skip (nullable), up-sampled while staging (no mask).
+template <int CIN, int COUT, int K, int CB = CIN, int OB = COUT, int C1 = 0, int POOL = 0, int UPIN = 0>
 __global__ void __launch_bounds__(NT) conv_fwd_kernel(const float* __restrict__ x, const float* __restrict__ xm,
                                                       int relu_in, int N, int H, int W,
                                                       const float* __restrict__ w, int transpose_flip,
@@ -119,7 +135,14 @@ __global__ void __launch_bounds__(NT) conv_fwd_kernel(const float* __restrict__ 
                 const int c4 = i % (CB / 4), q = i / (CB / 4);
                 const int gy = y0 - P + q / RW, gx = x0 - P + q % RW;
                 float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (gy >= 0 && gy < H && gx >= 0 && gx < W) {
+                if (UPIN && gy >= 0 && gy < H && gx >= 0 && gx < W) {
+                    v = up_sample4(reinterpret_cast<const float4*>(x), n, H / 2, W / 2, CIN / 4, gy, gx, c0 / 4 + c4);
+                    if (xm) {
+                        const float4 sk = __ldg(reinterpret_cast<const float4*>(
+                                                    xm + ((static_cast<size_t>(n) * H + gy) * W + gx) * CIN + c0) + c4);
+                        v.x += sk.x; v.y += sk.y; v.z += sk.z; v.w += sk.w;
+                    }
+                } else if (gy >= 0 && gy < H && gx >= 0 && gx < W) {
                     const size_t idx = ((static_cast<size_t>(n) * H + gy) * W + gx) * CIN + c0;
                     v = __ldg(reinterpret_cast<const float4*>(x + idx) + c4);
                     if (relu_in) v = make_float4(fmaxf(v.x, 0.f), fmaxf(v.y, 0.f), fmaxf(v.z, 0.f), fmaxf(v.w, 0.f));
@@ -479,11 +502,11 @@ __global__ void __launch_bounds__(256) conv1x1_kernel(const float* __restrict__ 
     }
 }
 
-template <int CIN, int COUT, int K, int CB = CIN, int OB = COUT, int C1 = 0, int POOL = 0>
+template <int CIN, int COUT, int K, int CB = CIN, int OB = COUT, int C1 = 0, int POOL = 0, int UPIN = 0>
 cudaError_t conv_fwd(const float* x, const float* xm, int relu_in, int N, int H, int W, const float* w, int tf,
                      const float* b, const float* ym, float* y, cudaStream_t st, const float* w1 = nullptr,
                      const float* b1 = nullptr, int relu_out = 0, float* yp = nullptr) {
-    if constexpr (K == 1 && CB == CIN && OB == COUT && C1 == 0 && CIN * COUT <= 4096) {
+    if constexpr (K == 1 && CB == CIN && OB == COUT && C1 == 0 && !UPIN && CIN * COUT <= 4096) {
         const size_t npx = static_cast<size_t>(N) * H * W;
         if (npx == 0) return cudaSuccess;
         conv1x1_kernel<CIN, COUT><<<ew_grid(npx), 256, 0, st>>>(x, xm, relu_in, npx, w, tf, b, ym, y);
@@ -491,7 +514,7 @@ cudaError_t conv_fwd(const float* x, const float* xm, int relu_in, int N, int H,
     }
     constexpr int P = K / 2, TW = TJ * FwdShape<CB, OB>::PX;
     const size_t smem = sizeof(float) * (CB * (((TH + 2 * P) * (TW + 2 * P)) | 1) + K * K * CB * OB + C1 * COUT);
-    auto kern = conv_fwd_kernel<CIN, COUT, K, CB, OB, C1, POOL>;
+    auto kern = conv_fwd_kernel<CIN, COUT, K, CB, OB, C1, POOL, UPIN>;
     static bool attr = false;
     if (!attr) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
@@ -590,14 +613,7 @@ __global__ void up_fwd_kernel(const float* __restrict__ lo, const float* __restr
         const int x = static_cast<int>(q % W); q /= W;
         const int yy = static_cast<int>(q % H);
         const int n = static_cast<int>(q / H);
-        const BilinTap ty = bilin_tap(yy, Hl), tx = bilin_tap(x, Wl);
-        auto L = [&](int a, int b2) { return __ldg(lo4 + ((static_cast<size_t>(n) * Hl + a) * Wl + b2) * C4 + c4); };
-        const float4 a00 = L(ty.i0, tx.i0), a01 = L(ty.i0, tx.i1), a10 = L(ty.i1, tx.i0), a11 = L(ty.i1, tx.i1);
-        auto mix = [&](float v00, float v01, float v10, float v11) {
-            return (v00 * tx.w0 + v01 * tx.w1) * ty.w0 + (v10 * tx.w0 + v11 * tx.w1) * ty.w1;
-        };
-        float4 v = make_float4(mix(a00.x, a01.x, a10.x, a11.x), mix(a00.y, a01.y, a10.y, a11.y),
-                               mix(a00.z, a01.z, a10.z, a11.z), mix(a00.w, a01.w, a10.w, a11.w));
+        float4 v = up_sample4(lo4, n, Hl, Wl, C4, yy, x, c4);
         if (skip) {
             const float4 sk = __ldg(reinterpret_cast<const float4*>(skip) + i);
             v.x += sk.x; v.y += sk.y; v.z += sk.z; v.w += sk.w;
@@ -863,14 +879,12 @@ cudaError_t forward(const float* th, const Buffers& b, int N, int Nb, int H, int
                                                  1)));
         // level 1 decoder
         L = level(th, nullptr, DEC1_3, DEC1_1);
-        up_fwd_kernel<<<ew_grid(n * p1 * 32), 256, 0, st>>>(bo, s1, n, H1, W1, 32, b.xin);
-        NSM_TRY((conv_fwd<32, 32, 3, 16, 32, 16>(b.xin, nullptr, 0, n, H1, W1, L.w3, 0, L.b3, nullptr, d1, st, L.w1, L.b1,
-                                                 1)));
+        NSM_TRY((conv_fwd<32, 32, 3, 16, 32, 16, 0, 1>(bo, s1, 0, n, H1, W1, L.w3, 0, L.b3, nullptr, d1, st, L.w1, L.b1,
+                                                       1)));  // input up(bo) + s1
         // level 0 decoder + head
         L = level(th, nullptr, DEC0_3, DEC0_1);
-        up_fwd_kernel<<<ew_grid(n * p0 * 16), 256, 0, st>>>(d1, nullptr, n, H, W, 16, b.xin);
-        NSM_TRY((conv_fwd<16, 16, 3, 16, 16, 16>(b.xin, nullptr, 0, n, H, W, L.w3, 0, L.b3, nullptr, b.a1, st, L.w1,
-                                                 L.b1)));
+        NSM_TRY((conv_fwd<16, 16, 3, 16, 16, 16, 0, 1>(d1, nullptr, 0, n, H, W, L.w3, 0, L.b3, nullptr, b.a1, st, L.w1,
+                                                       L.b1)));  // input up(d1)
         head_fwd_kernel<<<ew_grid(n * p0), 256, 0, st>>>(b.a1, th + o.w[HEAD], n * p0, vis);
         NSM_TRY(cudaGetLastError());
     }
