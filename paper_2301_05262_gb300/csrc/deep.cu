@@ -6,9 +6,11 @@
 // bottleneck: 3x3 w_{L-2} -> w_{L-1}, 1x1 w_{L-1} -> w_{L-2}; decoder level l:
 // bilinear x2 of the coarser output plus the level's encoder output (l >= 1),
 // 3x3 w_l -> w_l, 1x1 w_l -> w_{l-1} (16 at level 0); head 16 -> 1 and the
-// sigmoid.  Unfused: every layer reads and writes NHWC FP32 tensors in the
-// workspace (the 3-level net has the fused forms); the layers are the training
-// path's register-blocked kernels, with wide layers blocked over channels.
+// sigmoid.  Levels 0 and 1 (the 3-level network's shapes) run as the training
+// forward's fused kernels (encoder: 3x3, ReLU, 1x1, skip and pooling in one
+// kernel; decoder: up-sampling while staging, 3x3, ReLU, 1x1); the coarser,
+// wider levels run one kernel per layer on NHWC FP32 tensors in the
+// workspace, the wide layers blocked over channels.
 #include <vector>
 
 #include "nsm_internal.h"
@@ -114,30 +116,52 @@ nsm_status nsm_infer_deep(nsm_ctx* ctx, const nsm_frame* frame, const float* dev
     const float* cur = feat;
     int li = 0;
     size_t skip_off = 0;
-    for (int l = 0; l < levels - 1 && e == cudaSuccess; ++l) {
+    // encoder: levels with the 3-level network's shapes (0, 1) in one fused
+    // kernel each (3x3, ReLU, 1x1, skip, pooling); the pooled output never
+    // overwrites the level's input
+    for (int l = 0; l < levels - 1 && e == cudaSuccess; ++l, li += 2) {
         const int Hl = H >> l, Wl = W >> l;
-        e = conv(li++, cur, 0, Hl, Wl, a3);
-        if (e == cudaSuccess) e = conv(li++, a3, 1, Hl, Wl, a1);
-        if (e == cudaSuccess && l >= 1) {
+        const DeepLayer &d3 = Ls[li], &d1 = Ls[li + 1];
+        float* pooled = cur == h ? xin : h;
+        if (l >= 1) {
             skips[l] = skip + skip_off;
             skip_off += static_cast<size_t>(Hl) * Wl * wd(l);
-            e = tr::relu_copy(a1, static_cast<size_t>(Hl) * Wl * wd(l), skips[l], st);
         }
-        if (e == cudaSuccess) e = tr::pool_relu(a1, 1, Hl, Wl, wd(l), h, st);
-        cur = h;
+        if (tr::enc_level_fusable(d3.cin, d3.cout)) {
+            e = tr::enc_level_fused(d3.cin, d3.cout, cur, 1, Hl, Wl, wt + d3.w, dev_params + d3.b, dev_params + d1.w,
+                                    dev_params + d1.b, skips[l], pooled, st);
+        } else {
+            e = conv(li, cur, 0, Hl, Wl, a3);
+            if (e == cudaSuccess) e = conv(li + 1, a3, 1, Hl, Wl, a1);
+            if (e == cudaSuccess && l >= 1) e = tr::relu_copy(a1, static_cast<size_t>(Hl) * Wl * wd(l), skips[l], st);
+            if (e == cudaSuccess) e = tr::pool_relu(a1, 1, Hl, Wl, wd(l), pooled, st);
+        }
+        cur = pooled;
     }
     const int Hb = H >> (levels - 1), Wb = W >> (levels - 1);
     if (e == cudaSuccess) e = conv(li++, cur, 0, Hb, Wb, a3);
     if (e == cudaSuccess) e = conv(li++, a3, 1, Hb, Wb, a1);
     if (e == cudaSuccess) e = tr::relu_copy(a1, static_cast<size_t>(Hb) * Wb * wd(levels - 2), h, st);
-    for (int l = levels - 2; l >= 0 && e == cudaSuccess; --l) {
+    // decoder: levels 1 and 0 up-sample while staging (fused kernels); a level
+    // writes whichever scratch tensor its input does not occupy
+    const float* lo = h;
+    for (int l = levels - 2; l >= 0 && e == cudaSuccess; --l, li += 2) {
         const int Hl = H >> l, Wl = W >> l;
-        e = tr::up_add(h, l >= 1 ? skips[l] : nullptr, 1, Hl, Wl, wd(l), xin, st);
-        if (e == cudaSuccess) e = conv(li++, xin, 0, Hl, Wl, a3);
-        if (e == cudaSuccess) e = conv(li++, a3, 1, Hl, Wl, a1);
-        if (e == cudaSuccess && l >= 1) e = tr::relu_copy(a1, static_cast<size_t>(Hl) * Wl * wd(l - 1), h, st);
+        const DeepLayer &d3 = Ls[li], &d1 = Ls[li + 1];
+        if (tr::dec_level_fusable(d3.cin, d1.cout)) {
+            float* out = l >= 1 ? (lo == h ? a1 : h) : (lo == a1 ? a3 : a1);
+            e = tr::dec_level_fused(d3.cin, d1.cout, lo, l >= 1 ? skips[l] : nullptr, 1, Hl, Wl, wt + d3.w,
+                                    dev_params + d3.b, dev_params + d1.w, dev_params + d1.b, l >= 1, out, st);
+            lo = out;
+        } else {
+            e = tr::up_add(lo, l >= 1 ? skips[l] : nullptr, 1, Hl, Wl, wd(l), xin, st);
+            if (e == cudaSuccess) e = conv(li, xin, 0, Hl, Wl, a3);
+            if (e == cudaSuccess) e = conv(li + 1, a3, 1, Hl, Wl, a1);
+            if (e == cudaSuccess && l >= 1) e = tr::relu_copy(a1, static_cast<size_t>(Hl) * Wl * wd(l - 1), h, st);
+            lo = l >= 1 ? h : a1;
+        }
     }
-    if (e == cudaSuccess) e = tr::head(a1, dev_params + Ls[li].w, hw, vis_out, st);
+    if (e == cudaSuccess) e = tr::head(lo, dev_params + Ls[li].w, hw, vis_out, st);
     return e == cudaSuccess ? NSM_OK : cuda_fail(e, "deep forward");
 }
 

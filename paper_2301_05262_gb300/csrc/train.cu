@@ -1005,6 +1005,35 @@ cudaError_t transpose_to_tap_major(const float* w, int cin, int cout, int k, flo
     return cudaGetLastError();
 }
 
+// Levels of the deeper networks with the shapes of the 3-level network's
+// levels 0 and 1 run as the training forward's fused kernels (3x3 weights
+// tap-major, 1x1 weights OIHW).  Encoder: skip (nullable) = relu(1x1), pooled =
+// its 2x2 average.  Decoder: y = 1x1 of the 3x3 of up(lo) + skip (nullable),
+// rectified with relu_out.
+bool enc_level_fusable(int cin, int cout) { return (cin == 4 && cout == 16) || (cin == 16 && cout == 32); }
+bool dec_level_fusable(int cin, int cout1) { return (cin == 32 && cout1 == 16) || (cin == 16 && cout1 == 16); }
+
+cudaError_t enc_level_fused(int cin, int cout, const float* x, int N, int H, int W, const float* wt3, const float* b3,
+                            const float* w1, const float* b1, float* skip, float* pooled, cudaStream_t st) {
+    if (cin == 4 && cout == 16)
+        return conv_fwd<4, 16, 3, 4, 16, 16, 1>(x, nullptr, 0, N, H, W, wt3, 2, b3, nullptr, skip, st, w1, b1, 1,
+                                                pooled);
+    if (cin == 16 && cout == 32)
+        return conv_fwd<16, 32, 3, 16, 32, 32, 1>(x, nullptr, 0, N, H, W, wt3, 2, b3, nullptr, skip, st, w1, b1, 1,
+                                                  pooled);
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t dec_level_fused(int cin, int cout1, const float* lo, const float* skip, int N, int H, int W,
+                            const float* wt3, const float* b3, const float* w1, const float* b1, int relu_out, float* y,
+                            cudaStream_t st) {
+    if (cin == 32 && cout1 == 16)
+        return conv_fwd<32, 32, 3, 16, 32, 16, 0, 1>(lo, skip, 0, N, H, W, wt3, 2, b3, nullptr, y, st, w1, b1, relu_out);
+    if (cin == 16 && cout1 == 16)
+        return conv_fwd<16, 16, 3, 16, 16, 16, 0, 1>(lo, skip, 0, N, H, W, wt3, 2, b3, nullptr, y, st, w1, b1, relu_out);
+    return cudaErrorInvalidValue;
+}
+
 cudaError_t pool_relu(const float* x, int N, int H, int W, int C, float* y, cudaStream_t st) {
     pool_fwd_kernel<<<ew_grid(static_cast<size_t>(N) * (H / 2) * (W / 2) * C), 256, 0, st>>>(x, 1, N, H, W, C, y);
     return cudaGetLastError();
