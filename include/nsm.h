@@ -393,7 +393,7 @@ nsm_status nsm_gen_visibility(int H, int W, const float* pos4, const float* nrm4
 
 /* The encoder / decoder with L = 2 .. 7 levels (Sec. 3.6: the depth the 95th
  * percentile penumbra asks for; 3, 5 and 7 levels have receptive fields of
- * 24, 96 and 384 pixels), FP32 on CUDA cores, unfused.  Channel plan as for
+ * 24, 96 and 384 pixels), FP32 on CUDA cores.  Channel plan as for
  * three levels with widths 16 * 2^l (see nsm_param_count): for each layer in
  * the order enc0 3x3, enc0 1x1, ..., enc(L-2) 1x1, bottleneck 3x3, 1x1,
  * dec(L-2) 3x3, 1x1, ..., dec0 3x3, 1x1, head, its OIHW weights then bias.
