@@ -172,9 +172,15 @@ void nsm_weights_destroy(nsm_weights* w);
  * bit.  H, W >= 0 (0 = nothing to do).  With blocker_out the call takes
  * Ws * Hs * 16 bytes of device scratch (the map's 8 x 8 and 4 x 4 min / max
  * tables) from a library-owned pool, in stream order, for the duration of its
- * kernels; NSM_ERR_CUDA if that allocation fails. */
+ * kernels; NSM_ERR_CUDA if that allocation fails.  nsm_features_ws takes that
+ * scratch from the caller instead (no allocation): workspace (device, 256-byte
+ * aligned) of nsm_features_workspace_bytes(Hs, Ws) bytes when blocker_out is
+ * given, NSM_ERR_WORKSPACE if missing or short; ignored otherwise. */
 nsm_status nsm_features(const nsm_frame* frame, float* feat_out, int32_t* texel_out,
                         uint32_t* hard_out, float* blocker_out, void* stream);
+size_t nsm_features_workspace_bytes(int Hs, int Ws);
+nsm_status nsm_features_ws(const nsm_frame* frame, float* feat_out, int32_t* texel_out, uint32_t* hard_out,
+                           float* blocker_out, void* workspace, size_t workspace_bytes, void* stream);
 
 /* ---------------------------------------------------------------- inference */
 

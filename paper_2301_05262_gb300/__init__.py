@@ -81,6 +81,8 @@ def lib():
             "nsm_weights_load_device": ([P, P, Z, P], I),
             "nsm_weights_destroy": ([P], None),
             "nsm_features": ([FP, P, P, P, P, P], I),
+            "nsm_features_workspace_bytes": ([ctypes.c_int, ctypes.c_int], Z),
+            "nsm_features_ws": ([FP, P, P, P, P, P, Z, P], I),
             "nsm_infer_workspace_bytes": ([I, I, I], Z),
             "nsm_infer": ([P, FP, P, I, P, Z, P, P], I),
             "nsm_infer_host_stage_bytes": ([I, I, I, I], Z),
@@ -229,6 +231,18 @@ def nsm_param_count() -> int:
 def nsm_features(frame: nsm_frame, feat_out, texel_out=None, hard_out=None, blocker_out=None, stream=None):
     _check(lib().nsm_features(ctypes.byref(frame), _ptr(feat_out), _ptr(texel_out), _ptr(hard_out),
                               _ptr(blocker_out), _stream(stream)), "nsm_features")
+
+
+def nsm_features_workspace_bytes(Hs: int, Ws: int) -> int:
+    return int(lib().nsm_features_workspace_bytes(Hs, Ws))
+
+
+def nsm_features_ws(frame: nsm_frame, feat_out, texel_out=None, hard_out=None, blocker_out=None, workspace=None,
+                    stream=None):
+    """nsm_features with the blocker search's table scratch taken from `workspace`."""
+    nbytes = 0 if workspace is None else int(workspace.numel() * workspace.element_size())
+    _check(lib().nsm_features_ws(ctypes.byref(frame), _ptr(feat_out), _ptr(texel_out), _ptr(hard_out),
+                                 _ptr(blocker_out), _ptr(workspace), nbytes, _stream(stream)), "nsm_features_ws")
 
 
 def nsm_infer_workspace_bytes(H: int, W: int, precision: int) -> int:

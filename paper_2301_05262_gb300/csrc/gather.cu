@@ -196,7 +196,7 @@ __global__ void __launch_bounds__(kBTile * kBTile) blocker_kernel(GatherParams g
 }
 
 cudaError_t launch_features(const GatherParams& g, float* feat, int32_t* texel_out, uint32_t* hard_out,
-                            float* blocker_out, cudaStream_t stream) {
+                            float* blocker_out, void* table_ws, cudaStream_t stream) {
     const size_t npx = static_cast<size_t>(g.H) * g.W;
     if (npx == 0) return cudaSuccess;
     const int threads = 256;
@@ -207,12 +207,15 @@ cudaError_t launch_features(const GatherParams& g, float* feat, int32_t* texel_o
     features_kernel<<<blocks, threads, 0, stream>>>(g, feat, texel_out, hard_out);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || !blocker_out) return e;
-    cudaMemPool_t pool;
-    if ((e = scratch_pool(&pool)) != cudaSuccess) return e;
-    void* tab = nullptr;
+    // the tables: the caller's workspace, else stream-ordered scratch from the library's pool
+    void* tab = table_ws;
     const size_t nt = static_cast<size_t>(g.Ws) * g.Hs;
-    e = cudaMallocFromPoolAsync(&tab, 2 * nt * sizeof(float2), pool, stream);
-    if (e != cudaSuccess) return e;
+    if (!tab) {
+        cudaMemPool_t pool;
+        if ((e = scratch_pool(&pool)) != cudaSuccess) return e;
+        e = cudaMallocFromPoolAsync(&tab, 2 * nt * sizeof(float2), pool, stream);
+        if (e != cudaSuccess) return e;
+    }
     float2* t8 = static_cast<float2*>(tab);
     float2* t4 = t8 + nt;
     const dim3 tgrid((g.Ws + kTabX - 1) / kTabX, (g.Hs + kTabY - 1) / kTabY);
@@ -223,7 +226,7 @@ cudaError_t launch_features(const GatherParams& g, float* feat, int32_t* texel_o
         blocker_kernel<<<grid, kBTile * kBTile, 0, stream>>>(g, t8, t4, blocker_out);
         e = cudaGetLastError();
     }
-    const cudaError_t ef = cudaFreeAsync(tab, stream);
+    const cudaError_t ef = table_ws ? cudaSuccess : cudaFreeAsync(tab, stream);
     return e != cudaSuccess ? e : ef;
 }
 

@@ -359,8 +359,8 @@ void nsm_weights_destroy(nsm_weights* w) {
     delete w;
 }
 
-nsm_status nsm_features(const nsm_frame* frame, float* feat_out, int32_t* texel_out, uint32_t* hard_out,
-                        float* blocker_out, void* stream) {
+static nsm_status features_impl(const nsm_frame* frame, float* feat_out, int32_t* texel_out, uint32_t* hard_out,
+                                float* blocker_out, void* workspace, void* stream) {
     nsm_status s = check_frame(frame, false);
     if (s != NSM_OK) return s;
     if (static_cast<size_t>(frame->H) * frame->W == 0) return NSM_OK;
@@ -370,9 +370,32 @@ nsm_status nsm_features(const nsm_frame* frame, float* feat_out, int32_t* texel_
     if ((s = check_dev_ptr(hard_out, "hard_out", 4, true)) != NSM_OK) return s;
     if ((s = check_dev_ptr(blocker_out, "blocker_out", 4, true)) != NSM_OK) return s;
     GatherParams g = make_gather(frame);
-    cudaError_t e = launch_features(g, feat_out, texel_out, hard_out, blocker_out, static_cast<cudaStream_t>(stream));
+    cudaError_t e = launch_features(g, feat_out, texel_out, hard_out, blocker_out, workspace,
+                                    static_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) return cuda_fail(e, "features kernel launch");
     return NSM_OK;
+}
+
+nsm_status nsm_features(const nsm_frame* frame, float* feat_out, int32_t* texel_out, uint32_t* hard_out,
+                        float* blocker_out, void* stream) {
+    return features_impl(frame, feat_out, texel_out, hard_out, blocker_out, nullptr, stream);
+}
+
+size_t nsm_features_workspace_bytes(int Hs, int Ws) {
+    if (Hs <= 0 || Ws <= 0) return 0;
+    return static_cast<size_t>(Hs) * Ws * 16;
+}
+
+nsm_status nsm_features_ws(const nsm_frame* frame, float* feat_out, int32_t* texel_out, uint32_t* hard_out,
+                           float* blocker_out, void* workspace, size_t workspace_bytes, void* stream) {
+    if (blocker_out && frame && static_cast<size_t>(frame->H) * frame->W > 0) {
+        const size_t need = nsm_features_workspace_bytes(frame->Hs, frame->Ws);
+        if (!workspace || workspace_bytes < need)
+            return fail(NSM_ERR_WORKSPACE, "workspace of %zu bytes given, %zu needed", workspace_bytes, need);
+        nsm_status s = check_dev_ptr(workspace, "workspace", 256);
+        if (s != NSM_OK) return s;
+    }
+    return features_impl(frame, feat_out, texel_out, hard_out, blocker_out, blocker_out ? workspace : nullptr, stream);
 }
 
 size_t nsm_infer_workspace_bytes(int H, int W, nsm_precision precision) {

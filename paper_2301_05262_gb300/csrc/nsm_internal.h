@@ -70,8 +70,10 @@ struct StageEvents {
     }
 };
 
+// table_ws: >= 16 Ws Hs bytes, 16-byte aligned, for the blocker search's
+// tables; null takes stream-ordered scratch from scratch_pool
 cudaError_t launch_features(const GatherParams& g, float* feat, int32_t* texel_out, uint32_t* hard_out,
-                            float* blocker_out, cudaStream_t stream);
+                            float* blocker_out, void* table_ws, cudaStream_t stream);
 
 constexpr int kInferKernelsFp32 = 5;
 extern const char* const kInferKernelNamesFp32[kInferKernelsFp32];

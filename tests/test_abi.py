@@ -97,3 +97,9 @@ def test_deep_network_sizes(lib):
     assert nsm.nsm_param_count_levels(1) == 0 and nsm.nsm_param_count_levels(8) == 0
     assert nsm.nsm_infer_deep_workspace_bytes(64, 64, 5) >= (64 * 64 * 84 + N.param_count(5, with_bias=True)) * 4
     assert nsm.nsm_infer_deep_workspace_bytes(64, 64, 9) == 0
+
+
+def test_features_workspace_size(lib):
+    # two float2 tables (8 x 8 and 4 x 4 squares) per map texel
+    assert nsm.nsm_features_workspace_bytes(2048, 2048) == 2048 * 2048 * 16
+    assert nsm.nsm_features_workspace_bytes(0, 16) == 0

@@ -115,3 +115,20 @@ def test_features_2160p_4096_map_blocker_sampled_rows():
     f = scenegen.soft_frame(2160, 3840, 4096, 4096, 64, 31)
     for rows in (np.s_[1072:1088, :], np.s_[2144:2160, :]):
         _check_frame(f, blocker=True, sample=rows)
+
+
+def test_features_blocker_with_caller_workspace():
+    # the no-allocation entry point gives the same bits as the pooled one
+    import paper_2301_05262_gb300 as nsm
+    f = scenegen.soft_frame(64, 96, 512, 512, 16, 21)
+    df = DeviceFrame(f)
+    _, _, _, blk = run_features(df, blocker=True)
+    feat = torch.empty((4, f.H, f.W), device="cuda")
+    blk2 = torch.empty_like(blk)
+    ws = torch.empty((nsm.nsm_features_workspace_bytes(512, 512),), dtype=torch.uint8, device="cuda")
+    nsm.nsm_features_ws(df.frame, feat, None, None, blk2, ws)
+    torch.cuda.synchronize()
+    assert torch.equal(blk, blk2)
+    with pytest.raises(nsm.NSMError) as ei:
+        nsm.nsm_features_ws(df.frame, feat, None, None, blk2, ws[: ws.numel() // 2])
+    assert ei.value.status == 8
