@@ -149,9 +149,11 @@ nsm_status nsm_infer_deep(nsm_ctx* ctx, const nsm_frame* frame, const float* dev
         const int Hl = H >> l, Wl = W >> l;
         const DeepLayer &d3 = Ls[li], &d1 = Ls[li + 1];
         if (tr::dec_level_fusable(d3.cin, d1.cout)) {
-            float* out = l >= 1 ? (lo == h ? a1 : h) : (lo == a1 ? a3 : a1);
+            // level 0 also applies the head (the layer after its 1x1) and writes only the visibility
+            float* out = l >= 1 ? (lo == h ? a1 : h) : nullptr;
             e = tr::dec_level_fused(d3.cin, d1.cout, lo, l >= 1 ? skips[l] : nullptr, 1, Hl, Wl, wt + d3.w,
-                                    dev_params + d3.b, dev_params + d1.w, dev_params + d1.b, l >= 1, out, st);
+                                    dev_params + d3.b, dev_params + d1.w, dev_params + d1.b, l >= 1, out,
+                                    l == 0 ? dev_params + Ls[li + 2].w : nullptr, l == 0 ? vis_out : nullptr, st);
             lo = out;
         } else {
             e = tr::up_add(lo, l >= 1 ? skips[l] : nullptr, 1, Hl, Wl, wd(l), xin, st);
@@ -161,7 +163,7 @@ nsm_status nsm_infer_deep(nsm_ctx* ctx, const nsm_frame* frame, const float* dev
             lo = l >= 1 ? h : a1;
         }
     }
-    if (e == cudaSuccess) e = tr::head(lo, dev_params + Ls[li].w, hw, vis_out, st);
+    if (e == cudaSuccess && lo) e = tr::head(lo, dev_params + Ls[li].w, hw, vis_out, st);
     return e == cudaSuccess ? NSM_OK : cuda_fail(e, "deep forward");
 }
 

@@ -74,20 +74,25 @@ struct FwdShape { static constexpr int PX = (COUT >= 64 || CIN >= 64) ? 2 : 4; }
 // l + 17 of one warp, summed in the separate pooling kernel's order; y may
 // then be null.  UPIN: the input is up(x) + xm, x the coarse (H/2 x W/2)
 // tensor and xm the skip (nullable), up-sampled while staging (no mask).
-template <int CIN, int COUT, int K, int CB = CIN, int OB = COUT, int C1 = 0, int POOL = 0, int UPIN = 0>
+// HEAD (C1 = 16): also vis = sigmoid(wh[16] + sum_o wh[o] relu(y_o)), summed
+// in the head kernel's order; y may then be null.
+template <int CIN, int COUT, int K, int CB = CIN, int OB = COUT, int C1 = 0, int POOL = 0, int UPIN = 0,
+          int HEAD = 0>
 __global__ void __launch_bounds__(NT) conv_fwd_kernel(const float* __restrict__ x, const float* __restrict__ xm,
                                                       int relu_in, int N, int H, int W,
                                                       const float* __restrict__ w, int transpose_flip,
                                                       const float* __restrict__ b, const float* __restrict__ ym,
                                                       float* __restrict__ y, const float* __restrict__ w1,
                                                       const float* __restrict__ b1, int relu_out,
-                                                      float* __restrict__ yp) {
+                                                      float* __restrict__ yp, const float* __restrict__ wh,
+                                                      float* __restrict__ vis) {
     constexpr int P = K / 2, PX = FwdShape<CB, OB>::PX, TW = TJ * PX;
     constexpr int RH = TH + 2 * P, RW = TW + 2 * P, PS = (RH * RW) | 1;  // odd plane stride
     constexpr bool ONCE = (CB == CIN);
     static_assert(CIN % CB == 0 && COUT % OB == 0 && CB % 4 == 0 && OB % 4 == 0, "channel blocks");
     static_assert(C1 == 0 || (OB == COUT && C1 % 4 == 0), "the fused 1x1 needs every 3x3 output of a pixel");
     static_assert(POOL == 0 || C1 > 0, "pooling follows the fused 1x1");
+    static_assert(HEAD == 0 || (C1 == 16 && POOL == 0), "the head reads the 16 outputs of the fused 1x1");
     extern __shared__ float sm[];
     float* xs = sm;                       // [CB][PS]
     float* ws = xs + CB * PS;             // [tap][ci of the chunk][co of the block]
@@ -192,6 +197,7 @@ __global__ void __launch_bounds__(NT) conv_fwd_kernel(const float* __restrict__ 
 #pragma unroll
                 for (int c = 0; c < COUT; ++c) acc[p][c] = fmaxf(acc[p][c], 0.f);
                 const size_t pix = (static_cast<size_t>(n) * H + oy) * W + ox;
+                float logit = HEAD ? __ldg(wh + 16) : 0.f;
 #pragma unroll 1
                 for (int o4 = 0; o4 < C1 / 4; ++o4) {
                     float4 s = __ldg(reinterpret_cast<const float4*>(b1) + o4);
@@ -205,6 +211,12 @@ __global__ void __launch_bounds__(NT) conv_fwd_kernel(const float* __restrict__ 
                     }
                     if (relu_out) s = make_float4(fmaxf(s.x, 0.f), fmaxf(s.y, 0.f), fmaxf(s.z, 0.f), fmaxf(s.w, 0.f));
                     if (ok && y) reinterpret_cast<float4*>(y + pix * C1)[o4] = s;
+                    if constexpr (HEAD) {
+                        logit = fmaf(__ldg(wh + 4 * o4), fmaxf(s.x, 0.f), logit);
+                        logit = fmaf(__ldg(wh + 4 * o4 + 1), fmaxf(s.y, 0.f), logit);
+                        logit = fmaf(__ldg(wh + 4 * o4 + 2), fmaxf(s.z, 0.f), logit);
+                        logit = fmaf(__ldg(wh + 4 * o4 + 3), fmaxf(s.w, 0.f), logit);
+                    }
                     if constexpr (POOL) {
                         const float v[4] = {fmaxf(s.x, 0.f), fmaxf(s.y, 0.f), fmaxf(s.z, 0.f), fmaxf(s.w, 0.f)};
                         float q[4];
@@ -221,6 +233,7 @@ __global__ void __launch_bounds__(NT) conv_fwd_kernel(const float* __restrict__ 
                                 make_float4(q[0], q[1], q[2], q[3]);
                     }
                 }
+                if (HEAD && ok) vis[pix] = sigmoidf_acc(logit);
             }
         } else {
 #pragma unroll
@@ -502,11 +515,13 @@ __global__ void __launch_bounds__(256) conv1x1_kernel(const float* __restrict__ 
     }
 }
 
-template <int CIN, int COUT, int K, int CB = CIN, int OB = COUT, int C1 = 0, int POOL = 0, int UPIN = 0>
+template <int CIN, int COUT, int K, int CB = CIN, int OB = COUT, int C1 = 0, int POOL = 0, int UPIN = 0,
+          int HEAD = 0>
 cudaError_t conv_fwd(const float* x, const float* xm, int relu_in, int N, int H, int W, const float* w, int tf,
                      const float* b, const float* ym, float* y, cudaStream_t st, const float* w1 = nullptr,
-                     const float* b1 = nullptr, int relu_out = 0, float* yp = nullptr) {
-    if constexpr (K == 1 && CB == CIN && OB == COUT && C1 == 0 && !UPIN && CIN * COUT <= 4096) {
+                     const float* b1 = nullptr, int relu_out = 0, float* yp = nullptr, const float* wh = nullptr,
+                     float* vis = nullptr) {
+    if constexpr (K == 1 && CB == CIN && OB == COUT && C1 == 0 && !UPIN && !HEAD && CIN * COUT <= 4096) {
         const size_t npx = static_cast<size_t>(N) * H * W;
         if (npx == 0) return cudaSuccess;
         conv1x1_kernel<CIN, COUT><<<ew_grid(npx), 256, 0, st>>>(x, xm, relu_in, npx, w, tf, b, ym, y);
@@ -514,7 +529,7 @@ cudaError_t conv_fwd(const float* x, const float* xm, int relu_in, int N, int H,
     }
     constexpr int P = K / 2, TW = TJ * FwdShape<CB, OB>::PX;
     const size_t smem = sizeof(float) * (CB * (((TH + 2 * P) * (TW + 2 * P)) | 1) + K * K * CB * OB + C1 * COUT);
-    auto kern = conv_fwd_kernel<CIN, COUT, K, CB, OB, C1, POOL, UPIN>;
+    auto kern = conv_fwd_kernel<CIN, COUT, K, CB, OB, C1, POOL, UPIN, HEAD>;
     static bool attr = false;
     if (!attr) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
@@ -527,7 +542,7 @@ cudaError_t conv_fwd(const float* x, const float* xm, int relu_in, int N, int H,
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem) != cudaSuccess || per_sm < 1) per_sm = 1;
     const long long cap = static_cast<long long>(num_sms()) * per_sm;
     const dim3 grid(static_cast<unsigned>(tiles < cap ? tiles : cap), COUT / OB);
-    kern<<<grid, NT, smem, st>>>(x, xm, relu_in, N, H, W, w, tf, b, ym, y, w1, b1, relu_out, yp);
+    kern<<<grid, NT, smem, st>>>(x, xm, relu_in, N, H, W, w, tf, b, ym, y, w1, b1, relu_out, yp, wh, vis);
     return cudaGetLastError();
 }
 
@@ -883,9 +898,8 @@ cudaError_t forward(const float* th, const Buffers& b, int N, int Nb, int H, int
                                                        1)));  // input up(bo) + s1
         // level 0 decoder + head
         L = level(th, nullptr, DEC0_3, DEC0_1);
-        NSM_TRY((conv_fwd<16, 16, 3, 16, 16, 16, 0, 1>(d1, nullptr, 0, n, H, W, L.w3, 0, L.b3, nullptr, b.a1, st, L.w1,
-                                                       L.b1)));  // input up(d1)
-        head_fwd_kernel<<<ew_grid(n * p0), 256, 0, st>>>(b.a1, th + o.w[HEAD], n * p0, vis);
+        NSM_TRY((conv_fwd<16, 16, 3, 16, 16, 16, 0, 1, 1>(d1, nullptr, 0, n, H, W, L.w3, 0, L.b3, nullptr, nullptr, st,
+                                                          L.w1, L.b1, 0, nullptr, th + o.w[HEAD], vis)));  // up(d1)
         NSM_TRY(cudaGetLastError());
     }
     return cudaSuccess;
@@ -1008,8 +1022,8 @@ cudaError_t transpose_to_tap_major(const float* w, int cin, int cout, int k, flo
 // Levels of the deeper networks with the shapes of the 3-level network's
 // levels 0 and 1 run as the training forward's fused kernels (3x3 weights
 // tap-major, 1x1 weights OIHW).  Encoder: skip (nullable) = relu(1x1), pooled =
-// its 2x2 average.  Decoder: y = 1x1 of the 3x3 of up(lo) + skip (nullable),
-// rectified with relu_out.
+// its 2x2 average.  Decoder: y (nullable) = 1x1 of the 3x3 of up(lo) + skip
+// (nullable), rectified with relu_out; with vis (16 outputs) also the head.
 bool enc_level_fusable(int cin, int cout) { return (cin == 4 && cout == 16) || (cin == 16 && cout == 32); }
 bool dec_level_fusable(int cin, int cout1) { return (cin == 32 && cout1 == 16) || (cin == 16 && cout1 == 16); }
 
@@ -1026,9 +1040,12 @@ cudaError_t enc_level_fused(int cin, int cout, const float* x, int N, int H, int
 
 cudaError_t dec_level_fused(int cin, int cout1, const float* lo, const float* skip, int N, int H, int W,
                             const float* wt3, const float* b3, const float* w1, const float* b1, int relu_out, float* y,
-                            cudaStream_t st) {
+                            const float* wh, float* vis, cudaStream_t st) {
     if (cin == 32 && cout1 == 16)
         return conv_fwd<32, 32, 3, 16, 32, 16, 0, 1>(lo, skip, 0, N, H, W, wt3, 2, b3, nullptr, y, st, w1, b1, relu_out);
+    if (cin == 16 && cout1 == 16 && vis)
+        return conv_fwd<16, 16, 3, 16, 16, 16, 0, 1, 1>(lo, skip, 0, N, H, W, wt3, 2, b3, nullptr, y, st, w1, b1,
+                                                         relu_out, nullptr, wh, vis);
     if (cin == 16 && cout1 == 16)
         return conv_fwd<16, 16, 3, 16, 16, 16, 0, 1>(lo, skip, 0, N, H, W, wt3, 2, b3, nullptr, y, st, w1, b1, relu_out);
     return cudaErrorInvalidValue;

@@ -42,7 +42,7 @@ cudaError_t enc_level_fused(int cin, int cout, const float* x, int N, int H, int
                             const float* w1, const float* b1, float* skip, float* pooled, cudaStream_t st);
 cudaError_t dec_level_fused(int cin, int cout1, const float* lo, const float* skip, int N, int H, int W,
                             const float* wt3, const float* b3, const float* w1, const float* b1, int relu_out, float* y,
-                            cudaStream_t st);
+                            const float* wh, float* vis, cudaStream_t st);
 cudaError_t pool_relu(const float* x, int N, int H, int W, int C, float* y, cudaStream_t st);        // avg2x2(relu(x))
 cudaError_t up_add(const float* lo, const float* skip, int N, int H, int W, int C, float* y, cudaStream_t st);
 cudaError_t relu_copy(const float* x, size_t n, float* y, cudaStream_t st);
