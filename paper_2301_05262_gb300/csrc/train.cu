@@ -12,10 +12,14 @@
 // Kernels (CUDA cores, FP32):
 //   conv_fwd   y = conv(x~) (+ b) (masked by m > 0), x~ = x, relu(x) or x (m_in > 0);
 //              also the data gradient, as a convolution with the transposed,
-//              flipped weights;
-//   conv_wgrad dW += sum_p g~(p) x~(p + tap), db += sum_p g~(p): 4 x 4 register
+//              flipped weights.  In the checkpointed forward one launch covers
+//              a whole level: the input up-sampled while staging (decoders),
+//              3x3, ReLU, the 1x1 in the epilogue, then the rectified
+//              checkpoint, the 2x2 pooling (encoders) or the head (level 0);
+//   conv1x1    1x1 layers without tile staging (one thread per pixel);
+//   conv_wgrad dW += sum_p g~(p) x~(p + tap), db += sum_p g~(p): 8 x 8 register
 //              blocks of outer products per thread, one atomicAdd per weight
-//              per CTA;
+//              per CTA; wgrad1x1 for the 1x1 layers (grid-stride, no staging);
 //   pooling, bilinear x2 and their adjoints, head, loss, Adam.
 #include <vector>
 
