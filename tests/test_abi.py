@@ -103,3 +103,15 @@ def test_features_workspace_size(lib):
     # two float2 tables (8 x 8 and 4 x 4 squares) per map texel
     assert nsm.nsm_features_workspace_bytes(2048, 2048) == 2048 * 2048 * 16
     assert nsm.nsm_features_workspace_bytes(0, 16) == 0
+
+
+def test_host_validation_of_the_newer_entry_points(lib):
+    # rejected before any CUDA call: NULL frame / context, depth out of range
+    # (through the prototypes the binding declares)
+    assert lib.nsm_features_ws(None, None, None, None, None, None, 0, None) == 1
+    assert b"frame" in lib.nsm_last_error()
+    typed = nsm._gen_sigs()
+    assert typed.nsm_infer_deep(None, None, None, 5, None, 0, None, None) == 1
+    assert b"ctx" in lib.nsm_last_error()
+    assert nsm.nsm_infer_deep_workspace_bytes(0, 64, 5) == 0
+    assert nsm.nsm_infer_deep_workspace_bytes(64, 64, 1) == 0
