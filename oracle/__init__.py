@@ -26,6 +26,11 @@ itself; the tests under tests/test_oracle_*.py):
   features -- closed forms on hand-built pixels; invariants on rendered frames.
   blocker_search -- brute force over the whole map on tiny inputs, the
       no-occluder and k = 0 special cases.
+  blocker_window_half -- the emitter radius carried to the receiver's depth
+      and projected through the light's own view-projection matrix, in
+      texels, over several light distances (fov) and map widths; a
+      hand-worked case that a Ws-for-Ws/2, tan(fov)-for-tan(fov/2) or
+      diameter-for-radius error would change.
   penumbra_width -- the r_e = 0 and r_s = 0 closed forms (similar triangles).
   conv2d / avgpool2 / upsample2 -- direct summation loops, torch FP64
       library routines, adjoint dot-product identities.

@@ -206,6 +206,69 @@ def test_blocker_search_special_cases():
     assert found[0, 1] and zmin[0, 1] == 1.0
 
 
+def _footprint_texels(VP64, L, fwd, right, up, z_f, r, Ws, Hs):
+    """Half-separation, in texels, of the light-space images of a segment of
+    half-length r centred on a receiver that sits on the light's view axis at
+    distance z_f and lies perpendicular to that axis (along the map's right
+    and up axes).  Projective geometry through the light's own FP64
+    world->clip matrix; nothing here uses a window formula."""
+    P = np.asarray(L, np.float64) + z_f * fwd
+
+    def uv(Q):
+        c = VP64 @ np.append(Q, 1.0)
+        return (c[0] / c[3] * 0.5 + 0.5) * Ws, (c[1] / c[3] * 0.5 + 0.5) * Hs
+
+    (xa, _), (xb, _) = uv(P - r * right), uv(P + r * right)
+    (_, ya), (_, yb) = uv(P - r * up), uv(P + r * up)
+    return 0.5 * abs(xb - xa), 0.5 * abs(yb - ya)
+
+
+@pytest.mark.parametrize("light_dist,Ws", [(3.0, 2048), (3.0, 512), (5.0, 1024), (8.0, 4096)])
+def test_blocker_window_is_emitter_footprint_in_texels(light_dist, Ws):
+    """The window half-size is the emitter radius, carried to the receiver's
+    depth and measured in shadow-map texels through the light's projection
+    (the PCSS search region of the penumbra model, suppl. Sec. 4): project the
+    receiver's two points at +-r along the map axes and take half their
+    separation, rounded up and capped at 32.  Several light distances change
+    the light frustum's fov (fov = 2 asin(2/|L|)), so tan(fov/2) against
+    tan(fov), and Ws/2 against Ws, give different windows."""
+    rng = np.random.default_rng(int(light_dist * 10) + Ws)
+    checked = 0
+    for _ in range(40):
+        d = rng.normal(size=3)
+        d[2] = abs(d[2]) + 0.5
+        L = light_dist * d / np.linalg.norm(d)
+        fwd, right, up, t, VP = scenegen.light_frustum(L)
+        z_f = float(rng.uniform(0.5, 1.0) * light_dist)
+        r = float(rng.uniform(0.005, 0.3))
+        hx, hy = _footprint_texels(VP, L, fwd, right, up, z_f, r, Ws, Ws)
+        assert hx == pytest.approx(hy, rel=1e-9)          # square texels, square window
+        frac = hx - math.floor(hx)
+        if min(frac, 1.0 - frac) < 1e-3:                  # too close to an integer to judge ceil
+            continue
+        want = min(32, math.ceil(hx))
+        got = int(G.blocker_window_half(F32(z_f), r, Ws, t))
+        assert got == want, (L, z_f, r, hx)
+        checked += 1
+    assert checked >= 30
+
+
+def test_blocker_window_distinguishes_scale_errors():
+    """A hand-picked case where the footprint is well below the cap: a light at
+    distance 3 (tan(fov/2) = 2/sqrt(5)), Ws = 512, r = 0.05, receiver at 2.5.
+    The footprint is r (Ws/2) / (z_f tan(fov/2)) = 5.72 texels -> k = 6; a
+    window built on Ws (11.4 -> 12), on tan(fov) (0.57 -> 1) or on the
+    diameter (11.4 -> 12) would differ."""
+    L = np.array([0.0, -1.0, 2.8284271247461903])
+    fwd, right, up, t, VP = scenegen.light_frustum(L)
+    assert t == pytest.approx(2.0 / math.sqrt(5.0), rel=1e-12)
+    hx, _ = _footprint_texels(VP, L, fwd, right, up, 2.5, 0.05, 512, 512)
+    assert hx == pytest.approx(5.7243340, rel=1e-6)
+    assert int(G.blocker_window_half(F32(2.5), 0.05, 512, t)) == 6
+    # the cap: a large emitter close to the light reaches 32
+    assert int(G.blocker_window_half(F32(0.2), 0.3, 512, t)) == 32
+
+
 def test_penumbra_model_closed_forms():
     zf = np.array([2.0, 3.0, 5.0])
     zmin = np.array([1.0, 1.5, 2.0])
