@@ -469,9 +469,17 @@ nsm_status nsm_depth_for_penumbra(const uint32_t* hist, int nbins, float bin_px,
  * 512 x 512; about 21 MB, held on every device that loads the library until
  * the process exits); larger views return NSM_ERR_SHAPE.  Every call shares
  * that array: calls whose work overlaps on the GPU race and must be ordered by
- * the caller (one stream, or events).  The first call on a device looks up
- * the array's device address (once per device); make that first call before
- * any stream capture.  Asynchronous on stream. */
+ * the caller (one stream, or events).  Every call looks up the array's
+ * device address in the current context (a host-side lookup that allocates
+ * nothing); the first call in a context may load the library's device code,
+ * so make it before any stream capture.
+ * Errors: the frame checks of nsm_infer (NULL frame, sizes, H and W multiples
+ * of 4, finite light / camera values, radius and bias >= 0, tan_half_fov > 0,
+ * device pointers of the current device) give NSM_ERR_INVALID_ARG /
+ * NSM_ERR_SHAPE / NSM_ERR_ALIGNMENT before any work; so does a buffer whose
+ * allocation is shorter than it must be (dev_params nsm_param_count floats,
+ * vis_out H*W floats, pos4 / nrm4 H*W float4, sm Hs*Ws floats).
+ * Asynchronous on stream. */
 nsm_status nsm_infer_fp32_static(const nsm_frame* frame, const float* dev_params, float* vis_out, void* stream);
 
 #ifdef __cplusplus

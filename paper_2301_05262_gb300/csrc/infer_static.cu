@@ -12,8 +12,10 @@
 // host threads without ordering) race on it.  Each call overwrites every
 // activation element before reading it, so nothing needs clearing between
 // calls.
-#include <cstring>
-#include <mutex>
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <string>
 
 #include "../../include/nsm.h"
 #include "nsm_internal.h"
@@ -28,43 +30,40 @@ constexpr size_t kStaticScratchBytes = 80 * kStaticMaxPixels + 5 * 256;
 
 static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
 
-// Device address of g_static_scratch, looked up once per device.  In host
-// code the array's name is only a host-side stand-in, so kernels must get
-// this address, never the symbol itself.
-static std::mutex g_static_mu;
-static void* g_static_addr[64] = {nullptr};
-
-static cudaError_t static_scratch_address(int dev, void** out) {
-    std::lock_guard<std::mutex> lock(g_static_mu);
-    if (!g_static_addr[dev]) {
-        void* p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
-        if (e != cudaSuccess) return e;
-        g_static_addr[dev] = p;
-    }
-    *out = g_static_addr[dev];
-    return cudaSuccess;
+// Device address of g_static_scratch in the current context.  In host code
+// the array's name is only a host-side stand-in, so kernels must get this
+// address, never the symbol itself.  It is looked up on every call (a host-side
+// table lookup that allocates nothing): after a device reset, or once the
+// primary context has been released and made again, the module is loaded anew
+// and the array can sit at another address, so a cached value could go stale.
+static cudaError_t static_scratch_address(void** out) {
+    *out = nullptr;
+    return cudaGetSymbolAddress(out, g_static_scratch);
 }
 
-static nsm_status static_check_ptr(const void* p, const char* name, size_t align, int dev) {
-    if (!p) {
-        set_last_error(std::string(name) + " is NULL");
-        return NSM_ERR_INVALID_ARG;
-    }
-    cudaPointerAttributes at{};
-    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
-        cudaGetLastError();
-        set_last_error(std::string(name) + ": cannot query pointer");
-        return NSM_ERR_INVALID_ARG;
-    }
-    if ((at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged) || at.device != dev) {
-        set_last_error(std::string(name) + " is not device memory of the current device");
-        return NSM_ERR_INVALID_ARG;
-    }
-    if (reinterpret_cast<uintptr_t>(p) % align) {
-        set_last_error(std::string(name) + " is misaligned");
-        return NSM_ERR_ALIGNMENT;
-    }
+// The allocation that holds p must extend at least `bytes` past p.  Buffers
+// from a caching allocator are checked against the block they were carved
+// from, which still keeps every access inside mapped memory.
+// The driver function is resolved through the runtime, so the library does
+// not link libcuda itself (it loads on machines without a driver, where only
+// its host-side checks run).
+static nsm_status check_extent(const void* p, size_t bytes, const char* name) {
+    static const PFN_cuMemGetAddressRange_v3020 get_range = [] {
+        void* fn = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        cudaError_t e = cudaGetDriverEntryPointByVersion("cuMemGetAddressRange", &fn, 3020, cudaEnableDefault, &q);
+        return (e == cudaSuccess && q == cudaDriverEntryPointSuccess) ? reinterpret_cast<PFN_cuMemGetAddressRange_v3020>(fn)
+                                                                     : nullptr;
+    }();
+    if (!get_range) return fail(NSM_ERR_CUDA, "cannot resolve cuMemGetAddressRange");
+    CUdeviceptr base = 0;
+    size_t size = 0;
+    CUresult r = get_range(&base, &size, reinterpret_cast<CUdeviceptr>(p));
+    if (r != CUDA_SUCCESS) return fail(NSM_ERR_INVALID_ARG, "%s: cannot query its allocation (CUresult %d)", name, r);
+    const size_t avail = static_cast<size_t>(base + size - reinterpret_cast<CUdeviceptr>(p));
+    if (avail < bytes)
+        return fail(NSM_ERR_INVALID_ARG, "%s: its allocation holds %zu bytes from this address, %zu needed", name, avail,
+                    bytes);
     return NSM_OK;
 }
 
@@ -74,67 +73,35 @@ using namespace nsm;
 
 extern "C" nsm_status nsm_infer_fp32_static(const nsm_frame* f, const float* dev_params, float* vis_out,
                                             void* stream) {
-    if (!f) { set_last_error("frame is NULL"); return NSM_ERR_INVALID_ARG; }
-    if (f->H < 0 || f->W < 0 || (f->H % 4) || (f->W % 4)) {
-        set_last_error("view size must be non-negative multiples of 4");
-        return NSM_ERR_SHAPE;
-    }
+    // sizes and light / camera values first: no CUDA call before these
+    nsm_status s = check_frame_host(f, true);
+    if (s != NSM_OK) return s;
     const size_t npx = static_cast<size_t>(f->H) * f->W;
-    if (npx > kStaticMaxPixels) {
-        set_last_error("view of " + std::to_string(f->H) + " x " + std::to_string(f->W) + " = " +
-                       std::to_string(npx) + " pixels exceeds the static scratch limit of " +
-                       std::to_string(kStaticMaxPixels) + " pixels; use nsm_infer with a workspace");
-        return NSM_ERR_SHAPE;
-    }
-    if (f->Hs < 1 || f->Ws < 1 || f->Hs > 16384 || f->Ws > 16384) {
-        set_last_error("shadow map size outside [1, 16384]");
-        return NSM_ERR_SHAPE;
-    }
+    if (npx > kStaticMaxPixels)
+        return fail(NSM_ERR_SHAPE,
+                    "view of %d x %d = %zu pixels exceeds the static scratch limit of %zu pixels; use nsm_infer "
+                    "with a workspace",
+                    f->H, f->W, npx, kStaticMaxPixels);
     if (npx == 0) return NSM_OK;
-    int dev = -1;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess || dev < 0 || dev >= 64) { set_last_error("no usable CUDA device"); return NSM_ERR_DEVICE; }
-    int major = 0, minor = 0;
-    cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
-    cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
-    if (major != 10 || minor != 3) { set_last_error("this library is built for sm_103a only"); return NSM_ERR_DEVICE; }
-    nsm_status s;
-    if ((s = static_check_ptr(f->pos4, "frame.pos4", 16, dev)) != NSM_OK) return s;
-    if ((s = static_check_ptr(f->nrm4, "frame.nrm4", 16, dev)) != NSM_OK) return s;
-    if ((s = static_check_ptr(f->sm, "frame.sm", 4, dev)) != NSM_OK) return s;
-    if ((s = static_check_ptr(dev_params, "dev_params", 4, dev)) != NSM_OK) return s;
-    if ((s = static_check_ptr(vis_out, "vis_out", 4, dev)) != NSM_OK) return s;
+    if ((s = check_device()) != NSM_OK) return s;
+    if ((s = check_frame(f, true)) != NSM_OK) return s;
+    if ((s = check_dev_ptr(dev_params, "dev_params", 4)) != NSM_OK) return s;
+    if ((s = check_dev_ptr(vis_out, "vis_out", 4)) != NSM_OK) return s;
+    const LayerOffsets lo = layer_offsets();
+    if ((s = check_extent(dev_params, lo.total * sizeof(float), "dev_params")) != NSM_OK) return s;
+    if ((s = check_extent(vis_out, npx * sizeof(float), "vis_out")) != NSM_OK) return s;
+    if ((s = check_extent(f->pos4, npx * 16, "frame.pos4")) != NSM_OK) return s;
+    if ((s = check_extent(f->nrm4, npx * 16, "frame.nrm4")) != NSM_OK) return s;
+    if ((s = check_extent(f->sm, static_cast<size_t>(f->Hs) * f->Ws * sizeof(float), "frame.sm")) != NSM_OK)
+        return s;
 
     void* scratch = nullptr;
-    e = static_scratch_address(dev, &scratch);
-    if (e != cudaSuccess) {
-        set_last_error(std::string("cudaGetSymbolAddress(static scratch): ") + cudaGetErrorString(e));
-        return NSM_ERR_CUDA;
-    }
+    cudaError_t e = static_scratch_address(&scratch);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(static scratch)");
     Activations act{};
-    if (activations_bytes(f->H, f->W, 4, &act, scratch) > kStaticScratchBytes) {
-        set_last_error("internal: activations exceed the static scratch");
-        return NSM_ERR_SHAPE;
-    }
-    GatherParams g{};
-    std::memcpy(g.M, f->light.view_proj, sizeof(g.M));
-    for (int k = 0; k < 3; ++k) { g.L[k] = f->light.pos[k]; g.C[k] = f->camera.pos[k]; }
-    g.r_hat = f->light.r_hat;
-    g.z_far = f->light.z_far;
-    g.beta = f->light.bias;
-    g.radius = f->light.radius;
-    g.tan_half_fov = f->light.tan_half_fov;
-    g.Ws = f->Ws; g.Hs = f->Hs;
-    g.Ws_f = static_cast<float>(f->Ws); g.Hs_f = static_cast<float>(f->Hs);
-    g.half_Ws = 0.5f * static_cast<float>(f->Ws);
-    g.H = f->H; g.W = f->W;
-    g.pos4 = reinterpret_cast<const float4*>(f->pos4);
-    g.nrm4 = reinterpret_cast<const float4*>(f->nrm4);
-    g.sm = f->sm;
-    e = launch_infer_fp32(g, dev_params, act, vis_out, static_cast<cudaStream_t>(stream), StageEvents{});
-    if (e != cudaSuccess) {
-        set_last_error(std::string("inference kernel launch: ") + cudaGetErrorString(e));
-        return NSM_ERR_CUDA;
-    }
+    if (activations_bytes(f->H, f->W, 4, &act, scratch) > kStaticScratchBytes)
+        return fail(NSM_ERR_SHAPE, "internal: activations exceed the static scratch");
+    e = launch_infer_fp32(make_gather(f), dev_params, act, vis_out, static_cast<cudaStream_t>(stream), StageEvents{});
+    if (e != cudaSuccess) return cuda_fail(e, "inference kernel launch");
     return NSM_OK;
 }

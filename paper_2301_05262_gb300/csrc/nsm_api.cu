@@ -163,7 +163,7 @@ bool finite_all(const float* v, int n) {
     return true;
 }
 
-nsm_status check_frame(const nsm_frame* f, bool need_mult4) {
+nsm_status check_frame_host(const nsm_frame* f, bool need_mult4) {
     if (!f) return fail(NSM_ERR_INVALID_ARG, "frame is NULL");
     if (f->H < 0 || f->W < 0 || f->H > 16384 || f->W > 16384)
         return fail(NSM_ERR_SHAPE, "view size %d x %d outside [0, 16384]", f->H, f->W);
@@ -178,8 +178,13 @@ nsm_status check_frame(const nsm_frame* f, bool need_mult4) {
         return fail(NSM_ERR_INVALID_ARG, "light / camera parameters must be finite");
     if (l.radius < 0.f || l.bias < 0.f || l.tan_half_fov <= 0.f)
         return fail(NSM_ERR_INVALID_ARG, "light radius and bias must be >= 0, tan_half_fov > 0");
+    return NSM_OK;
+}
+
+nsm_status check_frame(const nsm_frame* f, bool need_mult4) {
+    nsm_status s = check_frame_host(f, need_mult4);
+    if (s != NSM_OK) return s;
     if (static_cast<size_t>(f->H) * f->W == 0) return NSM_OK;
-    nsm_status s;
     if ((s = check_dev_ptr(f->pos4, "frame.pos4", 16)) != NSM_OK) return s;
     if ((s = check_dev_ptr(f->nrm4, "frame.nrm4", 16)) != NSM_OK) return s;
     if ((s = check_dev_ptr(f->sm, "frame.sm", 4)) != NSM_OK) return s;

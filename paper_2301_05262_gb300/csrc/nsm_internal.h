@@ -45,6 +45,9 @@ nsm_status cuda_fail(cudaError_t e, const char* what);
 nsm_status check_device();
 nsm_status check_dev_ptr(const void* p, const char* name, size_t align, bool nullable = false);
 bool finite_all(const float* v, int n);
+// Sizes and light / camera values only (no CUDA call); check_frame adds the
+// device-pointer checks of the G-buffer and the map.
+nsm_status check_frame_host(const nsm_frame* f, bool need_mult4);
 nsm_status check_frame(const nsm_frame* f, bool need_mult4);
 GatherParams make_gather(const nsm_frame* f);
 size_t align_up(size_t v, size_t a);

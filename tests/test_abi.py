@@ -115,3 +115,35 @@ def test_host_validation_of_the_newer_entry_points(lib):
     assert b"ctx" in lib.nsm_last_error()
     assert nsm.nsm_infer_deep_workspace_bytes(0, 64, 5) == 0
     assert nsm.nsm_infer_deep_workspace_bytes(64, 64, 1) == 0
+
+
+def test_host_validation_of_the_static_entry_point(lib):
+    """nsm_infer_fp32_static rejects bad frames before any CUDA call: NULL
+    frame, sizes that are not multiples of 4, views above its fixed scratch
+    limit, non-finite or out-of-range light values."""
+    import math
+    f = lib.nsm_infer_fp32_static
+    assert f(None, None, None, None) == 1
+    assert b"frame" in lib.nsm_last_error()
+
+    def frame(H, W, **light):
+        fr = nsm.nsm_frame(H=H, W=W, Hs=64, Ws=64)
+        fr.light.tan_half_fov = 1.0
+        fr.light.z_far = 10.0
+        for k, v in light.items():
+            setattr(fr.light, k, v)
+        return fr
+
+    assert f(ctypes.byref(frame(6, 8)), None, None, None) == 2          # H % 4 != 0
+    assert b"multiples of 4" in lib.nsm_last_error()
+    assert f(ctypes.byref(frame(516, 512)), None, None, None) == 2      # 264,192 > 262,144 pixels
+    assert b"static scratch limit" in lib.nsm_last_error()
+    assert f(ctypes.byref(frame(65536, 4)), None, None, None) == 2      # outside [0, 16384]
+    bad = frame(64, 64)
+    bad.light.pos[1] = math.nan
+    assert f(ctypes.byref(bad), None, None, None) == 1
+    assert b"finite" in lib.nsm_last_error()
+    assert f(ctypes.byref(frame(64, 64, tan_half_fov=0.0)), None, None, None) == 1
+    assert f(ctypes.byref(frame(64, 64, radius=-0.1)), None, None, None) == 1
+    assert f(ctypes.byref(frame(64, 64, bias=-1e-3)), None, None, None) == 1
+    assert f(ctypes.byref(frame(0, 64)), None, None, None) == 0         # empty view: nothing to do
