@@ -102,3 +102,63 @@ def test_exchange_is_the_identity_on_one_rank():
     lo = torch.tensor([2.5], dtype=torch.float64)
     GradientExchange().reduce(g, lo, 7)
     assert g.tolist() == [0.0, 1.0, 2.0, 3.0, 4.0] and lo.item() == 2.5
+
+
+class _FakeState:
+    """Stands in for TrainState on CPU: grad() writes a rank-specific mean
+    gradient and loss, apply() records the gradient it was given."""
+
+    def __init__(self, rank, n=7):
+        self.n = n
+        self.rank = rank
+        self.g = torch.zeros(n)
+        self.applied = None
+
+    def grad(self, batch, alpha, loss_out, stream=None):
+        self.g = torch.arange(self.n, dtype=torch.float32) * (self.rank + 1) + 10 * self.rank
+        loss_out.fill_(1.5 + self.rank)
+
+    def read(self, k, out, stream=None):
+        out.copy_(self.g)
+
+    def write(self, k, src, stream=None):
+        self.g = src.clone()
+
+    def apply(self, **kw):
+        self.applied = self.g.clone()
+
+
+def _rank_trainer(rank, world, port, q):
+    sys.path.insert(0, ROOT)
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    from types import SimpleNamespace
+    from paper_2301_05262_gb300.data_parallel import DataParallelTrainer
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        st = _FakeState(rank)
+        tr = DataParallelTrainer(st, device=torch.device("cpu"))
+        loss = tr.step(SimpleNamespace(B=2 if rank == 0 else 1))
+        q.put((rank, st.applied.numpy(), float(loss.item())))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_trainer_exchanges_one_packed_buffer():
+    """The trainer's packed [grad | loss | count] exchange on two gloo ranks
+    with 2 + 1 items: the applied gradient and the loss are the item-weighted
+    means on both ranks."""
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank_trainer, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    got = sorted((q.get(timeout=300) for _ in range(2)), key=lambda t: t[0])
+    for p in procs:
+        p.join(60)
+        assert p.exitcode == 0
+    a = np.arange(7, dtype=np.float64)
+    want = (2 * a + (2 * a + 10)) / 3
+    for _, g, lo in got:
+        np.testing.assert_allclose(g, want, rtol=1e-6)
+        assert lo == pytest.approx((2 * 1.5 + 2.5) / 3, rel=1e-6)

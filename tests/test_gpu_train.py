@@ -189,13 +189,22 @@ def test_train_step_matches_oracle(ctx):
     grad = out[1].cpu().numpy().astype(np.float64)
     # FP32 may take either sign of |x0 - x_i| at near-ties: fit those signs, then
     # the rest must agree to FP32 accuracy and every fitted sign lie in [-1, 1]
+    # (one free sign per near-tie term, so their number is bounded, and the
+    # signs are fitted on the even-indexed parameters only: the odd-indexed
+    # half, held out, checks the fit)
     g_rest, Ct = _near_tie_split(feats, [targets[b] for b in range(B)], th64, alpha=0.9)
-    sgn = np.linalg.lstsq(Ct, grad - g_rest, rcond=None)[0] if Ct.shape[1] else np.zeros(0)
+    n_terms = B * T * H * W
+    print(f"near-tie L1 terms: {Ct.shape[1]} of {n_terms}")
+    assert Ct.shape[1] <= 0.01 * n_terms
+    even = np.arange(th64.size) % 2 == 0
+    sgn = np.linalg.lstsq(Ct[even], (grad - g_rest)[even], rcond=None)[0] if Ct.shape[1] else np.zeros(0)
     assert np.all(np.abs(sgn) <= 1.05), sgn
     fit = g_rest + Ct @ sgn
     for name, sl in _layer_slices():
         scale = max(np.abs(ref_grad[sl]).max(), 1e-12)
         assert np.abs(grad[sl] - fit[sl]).max() <= 2e-3 * scale, name
+        held = sl.start + np.nonzero(~even[sl])[0]
+        assert np.abs(grad[held] - fit[held]).max(initial=0.0) <= 2e-3 * scale, name
     # Adam's first step moves every weight by about lr * sign(g); compare where the
     # gradient is clearly non-zero and no near-tie can change its sign
     new = out[0].cpu().numpy().astype(np.float64)
