@@ -73,3 +73,59 @@ def test_border_ring_differs():
     ring = np.ones(d.shape[1:], bool)
     ring[2:-2, 2:-2] = False
     assert d[:, ring].max() > 1e-3  # the ring needs the exact path
+
+
+def parity_form_replicate(x, W, bias):
+    """The parity form over the coarse input extended by edge replication (one
+    coarse pixel each side) instead of zeros: the form the level-0 decoder
+    kernels evaluate."""
+    E = effective_weights(W)
+    xp = np.pad(x, ((0, 0), (1, 1), (1, 1)), mode="edge")
+    C, h, w = x.shape
+    y = np.zeros((W.shape[0], 2 * h, 2 * w))
+    for a in range(2):
+        for b in range(2):
+            y[:, a::2, b::2] = N.conv2d(xp, E[a, b], bias)[:, 1:-1, 1:-1]
+    return y
+
+
+def test_replicate_extension_leaves_a_one_pixel_ring():
+    """With the coarse input extended by replication, the up-sampled input is
+    reproduced exactly on every fine row and column of the image (the clamp of
+    the bilinear taps), and also one step outside it, where the convolution
+    reads zeros instead: only the outermost fine ring differs."""
+    rng = np.random.default_rng(7)
+    for (c, o, h, w) in ((16, 16, 9, 13), (4, 4, 6, 8), (16, 16, 2, 3)):
+        x = rng.standard_normal((c, h, w))
+        W = rng.standard_normal((o, c, 3, 3))
+        bias = rng.standard_normal(o)
+        ref = N.conv2d(N.upsample2(x), W, bias)
+        got = parity_form_replicate(x, W, bias)
+        np.testing.assert_allclose(got[:, 1:-1, 1:-1], ref[:, 1:-1, 1:-1], rtol=1e-12, atol=1e-12)
+        ring = np.ones(got.shape[1:], bool)
+        ring[1:-1, 1:-1] = False
+        assert np.abs(got - ref)[:, ring].max() > 1e-3
+
+
+def test_ring_correction_by_the_taps_outside():
+    """On the ring, the replicate form minus the exact value is the sum of the
+    taps that fall outside the fine image, each applied to the up-sampled
+    input at the clamped position."""
+    rng = np.random.default_rng(8)
+    c, o, h, w = 3, 2, 4, 5
+    x = rng.standard_normal((c, h, w))
+    W = rng.standard_normal((o, c, 3, 3))
+    U = N.upsample2(x)
+    H2, W2 = 2 * h, 2 * w
+    diff = parity_form_replicate(x, W, np.zeros(o)) - N.conv2d(U, W, np.zeros(o))
+    for fy in range(H2):
+        for fx in range(W2):
+            corr = np.zeros(o)
+            for ky in range(3):
+                for kx in range(3):
+                    y, xx = fy + ky - 1, fx + kx - 1
+                    if 0 <= y < H2 and 0 <= xx < W2:
+                        continue
+                    u = U[:, min(max(y, 0), H2 - 1), min(max(xx, 0), W2 - 1)]
+                    corr += W[:, :, ky, kx] @ u
+            np.testing.assert_allclose(diff[:, fy, fx], corr, rtol=1e-12, atol=1e-12)
