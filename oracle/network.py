@@ -345,14 +345,69 @@ def round_e4m3_per_out_channel(W):
     return round_e4m3(W / s) * s
 
 
-def forward_rounded(feat, theta, rnd, rnd_in=None, rnd_w=None, rnd_mid=None, levels: int = 3):
+def upsample_coef(a: int, k: int, d: int) -> float:
+    """Bilinear weight of coarse index i + d - 1 in fine index 2i + a + k - 1
+    (half-pixel centres, as `upsample2` away from the clamped edge): fine
+    index 2j takes coarse j - 1 and j with 1/4 and 3/4, fine 2j + 1 takes j
+    and j + 1 with 3/4 and 1/4."""
+    t = a + k - 1
+    m, par = t // 2, t % 2
+    taps = {m - 1: 0.25, m: 0.75} if par == 0 else {m: 0.75, m + 1: 0.25}
+    return taps.get(d - 1, 0.0)
+
+
+def upsample_conv_weights(W: np.ndarray) -> np.ndarray:
+    """Effective 3x3 weights E[a, b] (O, C, 3, 3) on the coarse grid of a 3x3
+    convolution W (O, C, 3, 3) that follows a bilinear x2 up-sampling: output
+    pixel (2i + a, 2j + b) = sum_{dy,dx} E[a, b][:, :, dy, dx] x[:, i+dy-1, j+dx-1]
+    wherever the up-sampled pixels it reads are inside the image (and their
+    coarse taps unclamped, or the coarse input extended by edge replication)."""
+    E = np.zeros((2, 2) + W.shape)
+    for a in range(2):
+        for b in range(2):
+            for dy in range(3):
+                for dx in range(3):
+                    for ky in range(3):
+                        for kx in range(3):
+                            q = upsample_coef(a, ky, dy) * upsample_coef(b, kx, dx)
+                            if q:
+                                E[a, b, :, :, dy, dx] += q * W[:, :, ky, kx]
+    return E
+
+
+def _coarse_grid_dec0(h, W3, b3, Weff, W1, b1, rnd_mid, Wexact):
+    """Level-0 decoder pair (3x3 + ReLU -> 1x1 + ReLU) of the coarse input h,
+    evaluated as the coarse-grid form does: the four output parities from the
+    effective weights `Weff` over h extended by edge replication; the
+    outermost ring of fine pixels exactly, from the up-sampled h with the
+    unrounded weights `Wexact` (and no rounding of its 3x3 output)."""
+    C, hh, ww = h.shape
+    hp = np.pad(h, ((0, 0), (1, 1), (1, 1)), mode="edge")
+    y = np.zeros((W3.shape[0], 2 * hh, 2 * ww))
+    for a in range(2):
+        for b in range(2):
+            y[:, a::2, b::2] = conv2d(hp, Weff[a, b], b3)[:, 1:-1, 1:-1]
+    out = relu(conv2d(rnd_mid(relu(y)), W1, b1))
+    exact = relu(conv2d(relu(conv2d(upsample2(h), *Wexact[0])), *Wexact[1]))
+    ring = np.ones(y.shape[1:], bool)
+    ring[1:-1, 1:-1] = False
+    out[:, ring] = exact[:, ring]
+    return out
+
+
+def forward_rounded(feat, theta, rnd, rnd_in=None, rnd_w=None, rnd_mid=None, levels: int = 3,
+                    coarse_dec0: bool = False):
     """`forward` with values rounded wherever a reduced-precision form stores
     them: every convolution weight by `rnd_w` (not biases or the head), the
     3x3 output that feeds each 1x1 by `rnd_mid`, and by `rnd` each level's
     output (after pooling where the level pools; the level-1 skip separately;
     the up-sampled (+ skip) decoder inputs).  The input features are rounded
     by `rnd_in`.  `rnd_w` / `rnd_mid` default to `rnd`.  All arithmetic between
-    those points is exact (FP64)."""
+    those points is exact (FP64).
+    coarse_dec0: the level-0 decoder as a coarse-grid form evaluates it
+    (`_coarse_grid_dec0`): no rounding of its up-sampled input, its 3x3 from
+    the effective weights of `upsample_conv_weights` rounded by `rnd_w`, and
+    the outermost fine ring with the unrounded weights."""
     rnd_w = rnd if rnd_w is None else rnd_w
     rnd_mid = rnd if rnd_mid is None else rnd_mid
     P = unpack(theta, levels)
@@ -371,6 +426,12 @@ def forward_rounded(feat, theta, rnd, rnd_in=None, rnd_w=None, rnd_mid=None, lev
         h = rnd(avgpool2(h1))
     h = rnd(pair(h, "bott_3x3", "bott_1x1"))
     for l in range(levels - 2, -1, -1):
+        if l == 0 and coarse_dec0:
+            W3, b3 = P["dec0_3x3"]
+            Weff = rnd_w(upsample_conv_weights(W3))
+            h = _coarse_grid_dec0(h, W3, b3, Weff, *Wr["dec0_1x1"], rnd_mid,
+                                  (P["dec0_3x3"], P["dec0_1x1"]))
+            continue
         u = upsample2(h)
         x = rnd(u + skips[l]) if l >= 1 else rnd(u)
         h = pair(x, f"dec{l}_3x3", f"dec{l}_1x1")

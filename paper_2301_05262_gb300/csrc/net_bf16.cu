@@ -75,7 +75,10 @@ using namespace tc;
 // Warp roles of a CTA (NEW epilogue warps, NPW producer warps, one MMA warp):
 // warps [0, NEW) epilogue (warp w reads TMEM lane quarter w % 4 and the tile
 // rows r = w / 4 (mod NEW / 4)), [NEW, NEW + NPW) producers, NEW + NPW MMA.
-template <int CIN, int CMID, int COUT, int R, int PRO, int KS>
+// PAR: the level-0 decoder on the coarse grid (C_mid = 4 output parities x
+// C_out channels of the 3x3; the 1x1 applies per parity, so its weight image
+// is the plain C_out -> C_out one).
+template <int CIN, int CMID, int COUT, int R, int PRO, int KS, bool PAR = false>
 struct TcCfg {
     static constexpr bool SPLIT = (PRO == TPRO_GATHER);
     static constexpr bool UP = (PRO == TPRO_UP || PRO == TPRO_UP_SKIP);
@@ -108,7 +111,7 @@ struct TcCfg {
     // one MMA over staged input row j accumulates into output rows j, j-1, j-2
     static constexpr bool STACK = 3 * N3 <= 256;
     static constexpr int B3_CHUNKS = STACK ? (SPLIT ? 12 * N3 : 9 * CG_IN * N3) : KSTEPS3 * 2 * N3;
-    static constexpr int B1_CHUNKS = (CMID / 8) * N1;
+    static constexpr int B1_CHUNKS = (PAR ? COUT / 8 : CMID / 8) * N1;
     static constexpr int OFF_A0 = 0;                                // two input buffers
     static constexpr int OFF_A1 = OFF_A0 + 2 * A0_CHUNKS * 16;
     static constexpr int OFF_RAW = OFF_A1 + A1_CHUNKS * 16;         // two raw buffers
@@ -117,7 +120,10 @@ struct TcCfg {
     static constexpr int OFF_BIAS3 = OFF_B1 + B1_CHUNKS * 16;
     static constexpr int OFF_BIAS1 = OFF_BIAS3 + CMID * 4;
     static constexpr int OFF_HEAD = OFF_BIAS1 + COUT * 4;
-    static constexpr int OFF_ZERO = ((OFF_HEAD + 4 * (COUT + 1) * 4) + 127) / 128 * 128;  // zero A operand
+    // PAR: FP32 3x3 [tap][c][o] and 1x1 [c][o] weights for the exact border ring
+    static constexpr int OFF_RINGW = OFF_HEAD + 4 * (COUT + 1) * 4;
+    static constexpr int RINGW_BYTES = PAR ? (9 * COUT * COUT + COUT * COUT) * 4 : 0;
+    static constexpr int OFF_ZERO = ((OFF_RINGW + RINGW_BYTES) + 127) / 128 * 128;  // zero A operand
     static constexpr int ZERO_BYTES = STACK ? kTileM * 16 + 128 : 0;
     static constexpr int OFF_BAR = OFF_ZERO + ZERO_BYTES;
     static constexpr int BYTES_USED = OFF_BAR + 144;
@@ -132,6 +138,7 @@ struct TcCfg {
     static_assert(TMEM_COLS == 32 || TMEM_COLS == 64 || TMEM_COLS == 128 || TMEM_COLS == 256 || TMEM_COLS == 512,
                   "TMEM columns");
     static_assert(CMID % 16 == 0 && COUT % 16 == 0 && COUT <= CMID, "channel shapes");
+    static_assert(!PAR || (CMID == 4 * COUT && PRO == TPRO_PLAIN && KS == 1 && !STACK), "coarse-grid decoder shape");
     static_assert(!UP || (R % 2 == 0), "up-sampling stages need an even tile height");
     static_assert(!STACK || R * N3 <= 256, "row-stacked accumulators are cleared by one MMA");
     static_assert(SPLIT ? KS == 1 : (CG_IN % KS == 0 && CGS % 2 == 0), "a K slice holds whole 16-channel K steps");
@@ -146,8 +153,10 @@ struct TcCfg {
 // chunk part * CG + g of a pixel holds channels 8g .. 8g+7 of that part.
 
 // PLAIN: K slice s of an NHWC tile straight into the input buffer, zeros
-// outside the image (planes [part][group of the slice])
-template <int NP, int CIN, int R, int KS, int NRW>
+// outside the image, or (CLAMP) the nearest pixel of the image: the
+// edge-replicated input of the coarse-grid level-0 decoder (planes [part][group
+// of the slice])
+template <int NP, int CIN, int R, int KS, int NRW, bool CLAMP = false>
 __device__ __forceinline__ void copy_slice(const uint16_t* src, int H, int W, int y0, int x0, uint32_t a0, int s,
                                            int base, int first, int pt) {
     constexpr int CG = CIN / 8, CGS = CG / KS, PLN = 2 * CGS;
@@ -156,13 +165,15 @@ __device__ __forceinline__ void copy_slice(const uint16_t* src, int H, int W, in
     for (int ci = pt; ci < 130 * PLN; ci += NP) {
         const int pl = ci % PLN, sp = ci / PLN;
         const int chunk = (pl / CGS) * CG + s * CGS + pl % CGS;
-        const int gx = x0 - 1 + sp;
+        int gx = x0 - 1 + sp;
         const bool okx = gx >= 0 && gx < W;
+        if (CLAMP) gx = gx < 0 ? 0 : (gx > W - 1 ? W - 1 : gx);
         const uint32_t dst = a0 + pl * kPlane + 16 * sp;
 #pragma unroll 2
         for (int sr = first; sr < R + 2; ++sr) {
-            const int gy = y0 - 1 + sr;
-            const bool ok = okx && gy >= 0 && gy < H;
+            int gy = y0 - 1 + sr;
+            const bool ok = CLAMP || (okx && gy >= 0 && gy < H);
+            if (CLAMP) gy = gy < 0 ? 0 : (gy > H - 1 ? H - 1 : gy);
             const uint16_t* p = ok ? src + ((static_cast<size_t>(gy) * W + gx) * 2 * CG + chunk) * 8 : src;
             cp_async16(dst + 16 * (row_slot<NRW>(base, sr) * kSW), p, ok ? 16u : 0u);
         }
@@ -251,16 +262,18 @@ __device__ __forceinline__ void compute_gather(const TcJob& job, int y0, int x0,
     }
 }
 
-// BF16 hi + lo chunks of 8 FP32 values: hi = bf16(v), lo = bf16(v - hi)
+// BF16 hi + lo chunks of 8 FP32 values: hi = bf16(v), lo = bf16(v - hi) (v - hi
+// is exact in FP32).  One packed rounding per pair of values and part; the hi
+// values are read back from the packed bits.
 __device__ __forceinline__ void split_chunks(const float* f, uint4& hi, uint4& lo) {
-    float h[8], l[8];
+    uint32_t h[4], l[4];
 #pragma unroll
-    for (int c = 0; c < 8; ++c) {
-        h[c] = __bfloat162float(__float2bfloat16_rn(f[c]));
-        l[c] = f[c] - h[c];
+    for (int k = 0; k < 4; ++k) {
+        h[k] = pack_bf16x2(f[2 * k], f[2 * k + 1]);
+        l[k] = pack_bf16x2(f[2 * k] - __uint_as_float(h[k] << 16), f[2 * k + 1] - __uint_as_float(h[k] & 0xffff0000u));
     }
-    hi = f32_to_chunk(h);
-    lo = f32_to_chunk(l);
+    hi = make_uint4(h[0], h[1], h[2], h[3]);
+    lo = make_uint4(l[0], l[1], l[2], l[3]);
 }
 // FP32 value of a hi + lo chunk pair
 __device__ __forceinline__ void pair_to_f32(uint4 hi, uint4 lo, float (&f)[8]) {
@@ -416,9 +429,88 @@ __device__ __forceinline__ void stage_flush(uint32_t stg, int lane, float* gdst,
     }
 }
 
+// ------------------------------------------------------------------ exact border ring of the coarse-grid decoder
+// The coarse-grid level-0 decoder reads the edge-replicated coarse input,
+// which reproduces the up-sampled input on every fine row and column of the
+// image but also one step outside it, where the 3x3 convolution reads zero
+// padding instead: on its outermost ring of fine pixels (rows 0 and H - 1,
+// columns 0 and W - 1) the epilogue writes nothing, and the producer warps,
+// idle between their tiles' copies, compute those pixels exactly as the level
+// is defined (Sec. 3.5): bilinear x2 up-sampling of the coarse input, 3x3 +
+// ReLU, 1x1 + ReLU, head, sigmoid, in FP32 with the FP32 weights.  A warp
+// takes one ring pixel: lane = output channel o (16) x half of the taps.
+__host__ __device__ inline int ring_pixels(int Hf, int Wf) {
+    return (Hf <= 0 || Wf <= 0) ? 0 : (Hf <= 2 ? Hf * Wf : 2 * Wf + 2 * (Hf - 2));
+}
+
+// ring pixel `item` of the batch -> view, fine row and column (false past the end)
+__device__ __forceinline__ bool ring_locate(const TcBatch& a, int item, int& v, int& fy, int& fx) {
+    for (v = 0; v < a.nviews; ++v) {
+        const int n = ring_pixels(2 * a.job[v].H, 2 * a.job[v].W);
+        if (item < n) break;
+        item -= n;
+    }
+    if (v >= a.nviews) return false;
+    const int Hf = 2 * a.job[v].H, Wf = 2 * a.job[v].W;
+    if (Hf <= 2) { fy = item / Wf; fx = item % Wf; }
+    else if (item < Wf) { fy = 0; fx = item; }
+    else if (item < 2 * Wf) { fy = Hf - 1; fx = item - Wf; }
+    else if (item < 2 * Wf + Hf - 2) { fy = 1 + item - 2 * Wf; fx = 0; }
+    else { fy = 1 + item - 2 * Wf - (Hf - 2); fx = Wf - 1; }
+    return true;
+}
+
+// one ring pixel by one warp; w3s [tap][c][o] and w1s [c][o] FP32 weights in
+// shared memory, b3 / b1 biases, hs head weights then bias (C = 16)
+__device__ __forceinline__ void ring_pixel(const TcBatch& a, int item, const float* w3s, const float* w1s,
+                                           const float* b3, const float* b1, const float* hs, int lane) {
+    constexpr int C = 16;
+    int v, fy, fx;
+    if (!ring_locate(a, item, v, fy, fx)) return;  // (uniform over the warp)
+    const TcJob& job = a.job[v];
+    const int Hl = job.H, Wl = job.W, Hf = 2 * Hl, Wf = 2 * Wl;
+    const int o = lane & 15, t0 = (lane & 16) ? 5 : 0;
+    // channel o of the up-sampled input at this lane's taps (0 outside the image)
+    float u[5];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        const int tap = t0 + k, y = fy + tap / 3 - 1, x = fx + tap % 3 - 1;
+        u[k] = 0.f;
+        if (tap < 9 && y >= 0 && y < Hf && x >= 0 && x < Wf) {
+            const BilinTap ty = bilin_tap(y, Hl), tx = bilin_tap(x, Wl);
+            auto px = [&](int ci, int cj) {
+                const uint16_t* p = job.in + (static_cast<size_t>(ci) * Wl + cj) * 2 * C + o;
+                return __bfloat162float(__ushort_as_bfloat16(p[0])) + __bfloat162float(__ushort_as_bfloat16(p[C]));
+            };
+            u[k] = ty.w0 * (tx.w0 * px(ty.i0, tx.i0) + tx.w1 * px(ty.i0, tx.i1)) +
+                   ty.w1 * (tx.w0 * px(ty.i1, tx.i0) + tx.w1 * px(ty.i1, tx.i1));
+        }
+    }
+    float acc = 0.f;
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        const int tap = t0 + k;
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+            const float uc = __shfl_sync(0xffffffffu, u[k], (lane & 16) | c);
+            if (tap < 9) acc = fmaf(w3s[(tap * C + c) * C + o], uc, acc);
+        }
+    }
+    acc += __shfl_xor_sync(0xffffffffu, acc, 16);
+    const float h = fmaxf(acc + b3[o], 0.f);
+    float z = b1[o];
+#pragma unroll
+    for (int c = 0; c < C; ++c) z = fmaf(w1s[c * C + o], __shfl_sync(0xffffffffu, h, c), z);
+    float t = hs[o] * fmaxf(z, 0.f);
+#pragma unroll
+    for (int m = 8; m >= 1; m >>= 1) t += __shfl_xor_sync(0xffffffffu, t, m);
+    if (lane == 0) job.vis[static_cast<size_t>(fy) * Wf + fx] = sigmoidf_fast(t + hs[C]);
+}
+
 template <int CIN, int CMID, int COUT, int R, int PRO, int EPI, int NEW, int NPW, int KS, int ORD>
 __global__ void __launch_bounds__(32 * (NEW + NPW + 1), 1) level_tc_kernel(const __grid_constant__ TcBatch a) {
-    using C = TcCfg<CIN, CMID, COUT, R, PRO, KS>;
+    constexpr bool PAR = (EPI == TEPI_HEAD_PAR);
+    using C = TcCfg<CIN, CMID, COUT, R, PRO, KS, PAR>;
     constexpr int NP = 32 * NPW, NT = 32 * (NEW + NPW + 1), MW = NEW + NPW, NE = 32 * NEW;
     static_assert(NEW == 4 || NEW == 8, "epilogue warps cover the four TMEM lane quarters");
     extern __shared__ __align__(1024) unsigned char smem[];
@@ -447,11 +539,19 @@ __global__ void __launch_bounds__(32 * (NEW + NPW + 1), 1) level_tc_kernel(const
     // ---- one-time set-up: weights, barriers, TMEM
     for (int i = tid; i < C::B3_CHUNKS; i += NT) st_shared_v4(sB3 + 16 * i, __ldg(a.b3img + i));
     for (int i = tid; i < C::B1_CHUNKS; i += NT) st_shared_v4(sB1 + 16 * i, __ldg(a.b1img + i));
-    for (int i = tid; i < CMID; i += NT) bias3_s[i] = __ldg(a.bias3 + i);
+    for (int i = tid; i < CMID; i += NT) bias3_s[i] = __ldg(a.bias3 + (PAR ? i % COUT : i));
     for (int i = tid; i < COUT; i += NT) bias1_s[i] = __ldg(a.bias1 + i);
-    if (EPI == TEPI_HEAD || EPI == TEPI_HEAD4)
+    if (EPI == TEPI_HEAD || EPI == TEPI_HEAD4 || EPI == TEPI_HEAD_PAR)
         for (int i = tid; i < (EPI == TEPI_HEAD4 ? 4 : 1) * (COUT + 1); i += NT) head_s[i] = __ldg(a.head + i);
     for (int i = tid; i < C::ZERO_BYTES / 16; i += NT) st_shared_v4(sbase + C::OFF_ZERO + 16 * i, make_uint4(0, 0, 0, 0));
+    float* ringw = reinterpret_cast<float*>(smem + C::OFF_RINGW);
+    if constexpr (PAR) {
+        for (int i = tid; i < 9 * COUT * COUT; i += NT) {
+            const int o = i % COUT, c = (i / COUT) % COUT, tap = i / (COUT * COUT);
+            ringw[i] = __ldg(a.w3 + (o * COUT + c) * 9 + tap);
+        }
+        for (int i = tid; i < COUT * COUT; i += NT) ringw[9 * COUT * COUT + i] = __ldg(a.w1 + (i % COUT) * COUT + i / COUT);
+    }
     if (tid == 0) {
         for (int k = 0; k < 2; ++k) {
             mbar_init(full + k, NP);
@@ -520,6 +620,14 @@ __global__ void __launch_bounds__(32 * (NEW + NPW + 1), 1) level_tc_kernel(const
             }
         }
         bool failed = false;
+        // PAR: this CTA's share [ring_lo, ring_hi) of the batch's border-ring pixels
+        int ring_lo = 0, ring_hi = 0;
+        if constexpr (PAR) {
+            long long nr = 0;
+            for (int q = 0; q < a.nviews; ++q) nr += ring_pixels(2 * a.job[q].H, 2 * a.job[q].W);
+            ring_lo = static_cast<int>(nr * blockIdx.x / gridDim.x);
+            ring_hi = static_cast<int>(nr * (blockIdx.x + 1) / gridDim.x);
+        }
         for (int tile = t_lo; tile < t_hi && !failed; ++tile, ++it) {
             int y0, x0, base, first;
             bool cont;
@@ -552,7 +660,7 @@ __global__ void __launch_bounds__(32 * (NEW + NPW + 1), 1) level_tc_kernel(const
                 // the rows written now are free once the MMAs of step st - 2 are done
                 if (st >= 2 && !wait_phase(mma3 + b, ((st >> 1) - 1) & 1, s_abort)) { failed = true; break; }
                 if constexpr (PRO == TPRO_PLAIN) {
-                    copy_slice<NP, CIN, R, KS, C::NRW>(job.in, job.H, job.W, y0, x0, A0, s, base, first, pt);
+                    copy_slice<NP, CIN, R, KS, C::NRW, PAR>(job.in, job.H, job.W, y0, x0, A0, s, base, first, pt);
                     cp_async_arrive(full + b);
                 } else {
                     if constexpr (PRO == TPRO_GATHER)
@@ -566,6 +674,15 @@ __global__ void __launch_bounds__(32 * (NEW + NPW + 1), 1) level_tc_kernel(const
             }
             if (failed) break;
             if constexpr (PRO != TPRO_PLAIN) mbar_arrive(rfree + rb);
+            if constexpr (PAR) {
+                const int k = ring_lo + it * NPW + pt / 32;
+                if (k < ring_hi)
+                    ring_pixel(a, k, ringw, ringw + 9 * COUT * COUT, bias3_s, bias1_s, head_s, tid & 31);
+            }
+        }
+        if constexpr (PAR) {
+            for (int k = ring_lo + it * NPW + pt / 32; !failed && k < ring_hi; k += NPW)
+                ring_pixel(a, k, ringw, ringw + 9 * COUT * COUT, bias3_s, bias1_s, head_s, tid & 31);
         }
         if (failed) {
             atomicExch(a.err, 3);
@@ -584,6 +701,24 @@ __global__ void __launch_bounds__(32 * (NEW + NPW + 1), 1) level_tc_kernel(const
                 if (!wait_phase(a1full, j & 1, s_abort)) return false;
                 fence_after_sync();
                 const uint32_t Dj = tbase + (j & 1) * C::TMEM_BUF;
+                if constexpr (PAR) {
+                    // per output parity p: its C_out channels (K = 16) times the
+                    // C_out -> C_out weights, into columns [p N1, (p + 1) N1)
+                    static_assert(COUT == 16, "one K step per parity");
+                    const uint64_t bd = smem_desc(sB1, C::N1 * 16, 128);
+                    for (int r = 0; r < R; ++r) {
+                        const uint32_t row = sA1 + 16 * (r * 2 * kA1Part);
+#pragma unroll
+                        for (int p = 0; p < 4; ++p) {
+                            const uint64_t ahi = smem_desc(row + 16 * (2 * p * kTileM), kTileM * 16, 128);
+                            const uint64_t alo = smem_desc(row + 16 * (kA1Part + 2 * p * kTileM), kTileM * 16, 128);
+                            mma_bf16(Dj + r * C::N3 + p * C::N1, ahi, bd, id1, 0);
+                            mma_bf16(Dj + r * C::N3 + p * C::N1, alo, bd, id1, 1);
+                        }
+                    }
+                    mma_commit(mma1);
+                    return true;
+                }
                 for (int r = 0; r < R; ++r) {
                     const uint32_t row = sA1 + 16 * (r * 2 * kA1Part);
 #pragma unroll
@@ -704,8 +839,9 @@ __global__ void __launch_bounds__(32 * (NEW + NPW + 1), 1) level_tc_kernel(const
         // it has room for every epilogue warp
         constexpr int kStg = 32 * COUT * 4;                              // one row of a warp
         constexpr int kRows = EPI == TEPI_SKIP_POOL ? 2 : 1;            // rows staged at once
-        constexpr bool kStage = (EPI == TEPI_STORE || EPI == TEPI_SKIP_POOL) &&
+        constexpr bool kStage = (EPI == TEPI_STORE || EPI == TEPI_STORE_PAIR || EPI == TEPI_SKIP_POOL) &&
                                 NEW * kRows * kStg <= C::A1_CHUNKS * 16;
+        static_assert(EPI != TEPI_STORE_PAIR || (kStage && COUT == 16), "pair rows go out through the staging area");
         int v = 0, it = 0;
         for (int tile = t_lo; tile < t_hi; ++tile, ++it) {
             const int tb = it & 1;
@@ -729,6 +865,29 @@ __global__ void __launch_bounds__(32 * (NEW + NPW + 1), 1) level_tc_kernel(const
                 }
             }
             // ---- 3x3 result: bias + ReLU -> BF16 hi + lo -> operand of the 1x1
+            if constexpr (PAR) {
+                // two parities (32 columns of each weight part) in flight at once
+                for (int r = rg; r < R; r += G) {
+                    const uint32_t row = sA1 + 16 * (r * 2 * kA1Part);
+#pragma unroll
+                    for (int q = 0; q < CMID; q += 32) {
+                        float val[32], lo[32];
+                        tmem_ld32(Dl + r * C::N3 + q, val);
+                        tmem_ld32(Dl + r * C::N3 + CMID + q, lo);
+                        tmem_ld_wait();
+#pragma unroll
+                        for (int c0 = 0; c0 < 32; c0 += 8) {
+                            float x[8];
+#pragma unroll
+                            for (int j = 0; j < 8; ++j) x[j] = fmaxf(val[c0 + j] + lo[c0 + j] + bias3_s[q + c0 + j], 0.f);
+                            uint4 h, l;
+                            split_chunks(x, h, l);
+                            st_shared_v4(row + 16 * (((q + c0) / 8) * kTileM + m), h);
+                            st_shared_v4(row + 16 * (kA1Part + ((q + c0) / 8) * kTileM + m), l);
+                        }
+                    }
+                }
+            } else
             for (int r = rg; r < R; r += G) {
 #pragma unroll
                 for (int c0 = 0; c0 < CMID; c0 += 16) {
@@ -738,18 +897,16 @@ __global__ void __launch_bounds__(32 * (NEW + NPW + 1), 1) level_tc_kernel(const
                     tmem_ld16(Dl + col + CMID + c0, lo);   // x W_lo
                     tmem_ld_wait();
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) {
-                        val[j] = fmaxf(val[j] + lo[j] + bias3_s[c0 + j], 0.f);
-                        const float hi = __bfloat162float(__float2bfloat16_rn(val[j]));
-                        lo[j] = val[j] - hi;
-                        val[j] = hi;
-                    }
+                    for (int j = 0; j < 16; ++j) val[j] = fmaxf(val[j] + lo[j] + bias3_s[c0 + j], 0.f);
                     const int cg = c0 / 8;
                     const uint32_t row = sA1 + 16 * (r * 2 * kA1Part);
-                    st_shared_v4(row + 16 * (cg * kTileM + m), f32_to_chunk(val));
-                    st_shared_v4(row + 16 * ((cg + 1) * kTileM + m), f32_to_chunk(val + 8));
-                    st_shared_v4(row + 16 * (kA1Part + cg * kTileM + m), f32_to_chunk(lo));
-                    st_shared_v4(row + 16 * (kA1Part + (cg + 1) * kTileM + m), f32_to_chunk(lo + 8));
+                    uint4 h0, l0, h1, l1;
+                    split_chunks(val, h0, l0);
+                    split_chunks(val + 8, h1, l1);
+                    st_shared_v4(row + 16 * (cg * kTileM + m), h0);
+                    st_shared_v4(row + 16 * ((cg + 1) * kTileM + m), h1);
+                    st_shared_v4(row + 16 * (kA1Part + cg * kTileM + m), l0);
+                    st_shared_v4(row + 16 * (kA1Part + (cg + 1) * kTileM + m), l1);
                 }
             }
             fence_proxy_async_smem();
@@ -827,6 +984,44 @@ __global__ void __launch_bounds__(32 * (NEW + NPW + 1), 1) level_tc_kernel(const
                         }
                     }
                 }
+            } else if constexpr (EPI == TEPI_HEAD_PAR) {
+                // coarse pixel (oy, ox) -> fine pixels (2 oy + a, 2 ox + b), parity
+                // p = 2a + b in TMEM columns [p N1, (p + 1) N1): 1x1 hi | lo parts
+                const int Wf = 2 * W;
+                for (int r = rg; r < R; r += G) {
+                    const int oy = y0 + r;
+                    float o4[4];
+#pragma unroll
+                    for (int q = 0; q < 4; q += 2) {
+                        // parities q, q + 1: columns [q N1, (q + 2) N1), hi | lo parts of each
+                        float d[2][32];
+                        tmem_ld32(Dl + r * C::N3 + q * C::N1, d[0]);
+                        tmem_ld32(Dl + r * C::N3 + (q + 1) * C::N1, d[1]);
+                        tmem_ld_wait();
+#pragma unroll
+                        for (int k = 0; k < 2; ++k) {
+                            float hsum = 0.f;
+#pragma unroll
+                            for (int j = 0; j < 16; ++j)
+                                hsum = fmaf(head_s[j], fmaxf(d[k][j] + d[k][COUT + j] + bias1_s[j], 0.f), hsum);
+                            o4[q + k] = sigmoidf_fast(hsum + head_s[COUT]);
+                        }
+                    }
+                    if (oy < H && ox < W) {
+                        float* v0 = job.vis + static_cast<size_t>(2 * oy) * Wf + 2 * ox;
+                        if (oy > 0 && oy < H - 1 && ox > 0 && ox < W - 1) {
+                            reinterpret_cast<float2*>(v0)[0] = make_float2(o4[0], o4[1]);
+                            reinterpret_cast<float2*>(v0 + Wf)[0] = make_float2(o4[2], o4[3]);
+                        } else {
+                            // the outermost fine ring is the producers' (exact path)
+#pragma unroll
+                            for (int p = 0; p < 4; ++p) {
+                                const int fy = 2 * oy + (p >> 1), fx = 2 * ox + (p & 1);
+                                if (fy > 0 && fy < 2 * H - 1 && fx > 0 && fx < Wf - 1) v0[(p >> 1) * Wf + (p & 1)] = o4[p];
+                            }
+                        }
+                    }
+                }
             } else {
                 for (int r = rg; r < R; r += G) {
                     const int oy = y0 + r;
@@ -840,7 +1035,18 @@ __global__ void __launch_bounds__(32 * (NEW + NPW + 1), 1) level_tc_kernel(const
                         tmem_ld_wait();
 #pragma unroll
                         for (int j = 0; j < 16; ++j) val[j] = fmaxf(val[j] + lo[j] + bias1_s[c0 + j], 0.f);
-                        if constexpr (EPI == TEPI_STORE) {
+                        if constexpr (EPI == TEPI_STORE_PAIR) {
+                            // [part][16 channels] of the pixel: hi chunks, then lo chunks
+                            uint4 h0, l0, h1, l1;
+                            split_chunks(val, h0, l0);
+                            split_chunks(val + 8, h1, l1);
+                            const float pk[16] = {
+                                __uint_as_float(h0.x), __uint_as_float(h0.y), __uint_as_float(h0.z), __uint_as_float(h0.w),
+                                __uint_as_float(h1.x), __uint_as_float(h1.y), __uint_as_float(h1.z), __uint_as_float(h1.w),
+                                __uint_as_float(l0.x), __uint_as_float(l0.y), __uint_as_float(l0.z), __uint_as_float(l0.w),
+                                __uint_as_float(l1.x), __uint_as_float(l1.y), __uint_as_float(l1.z), __uint_as_float(l1.w)};
+                            stage_put<COUT>(stg, lane, c0, pk);
+                        } else if constexpr (EPI == TEPI_STORE) {
                             if constexpr (kStage) {
                                 stage_put<COUT>(stg, lane, c0, val);
                             } else if (oy < H && ox < W) {
@@ -866,10 +1072,11 @@ __global__ void __launch_bounds__(32 * (NEW + NPW + 1), 1) level_tc_kernel(const
                         reinterpret_cast<float4*>(job.out_f)[static_cast<size_t>(oy) * W + ox] =
                             make_float4(h4[0] + head_s[4 * COUT], h4[1] + head_s[4 * COUT + 1],
                                         h4[2] + head_s[4 * COUT + 2], h4[3] + head_s[4 * COUT + 3]);
-                    if constexpr (EPI == TEPI_STORE && kStage) {
+                    if constexpr ((EPI == TEPI_STORE || EPI == TEPI_STORE_PAIR) && kStage) {
                         __syncwarp();
+                        float* orow = EPI == TEPI_STORE_PAIR ? reinterpret_cast<float*>(job.out) : job.out_f;
                         if (oy < H && npix > 0)
-                            stage_flush<COUT>(stg, lane, job.out_f + (static_cast<size_t>(oy) * W + px0) * COUT, npix);
+                            stage_flush<COUT>(stg, lane, orow + (static_cast<size_t>(oy) * W + px0) * COUT, npix);
                         __syncwarp();
                     }
                 }
@@ -891,7 +1098,7 @@ __global__ void __launch_bounds__(32 * (NEW + NPW + 1), 1) level_tc_kernel(const
 // ------------------------------------------------------------------ variants and launch
 template <int CIN, int CMID, int COUT, int R, int PRO, int EPI, int NEW, int NPW, int KS, int ORD>
 static cudaError_t launch_variant(const TcBatch& a, int ctas_per_sm, cudaStream_t stream) {
-    using C = TcCfg<CIN, CMID, COUT, R, PRO, KS>;
+    using C = TcCfg<CIN, CMID, COUT, R, PRO, KS, EPI == TEPI_HEAD_PAR>;
     auto kern = level_tc_kernel<CIN, CMID, COUT, R, PRO, EPI, NEW, NPW, KS, ORD>;
     static int occ = -1;
     if (occ < 0) {
@@ -926,7 +1133,7 @@ static const void* kernel_of() {
 
 template <int CIN, int CMID, int COUT, int R, int PRO, int EPI, int NEW, int NPW, int KS, int ORD>
 static int occupancy_of() {
-    using C = TcCfg<CIN, CMID, COUT, R, PRO, KS>;
+    using C = TcCfg<CIN, CMID, COUT, R, PRO, KS, EPI == TEPI_HEAD_PAR>;
     cudaFuncAttributes fa{};
     if (cudaFuncGetAttributes(&fa, level_tc_kernel<CIN, CMID, COUT, R, PRO, EPI, NEW, NPW, KS, ORD>) != cudaSuccess) return 1;
     const int regs = ((fa.numRegs + 7) / 8) * 8 * (32 * (NEW + NPW + 1));
@@ -968,16 +1175,16 @@ static const Variant kVarBott[] = {
     NSM_VARIANT2(2, 4, 8, 2, 32, 64, 32, TPRO_PLAIN, TEPI_STORE),
     NSM_VARIANT2(2, 8, 8, 2, 32, 64, 32, TPRO_PLAIN, TEPI_STORE)};
 static const Variant kVarDec1[] = {
-    NSM_VARIANT2(2, 4, 8, 2, 32, 32, 16, TPRO_UP_SKIP, TEPI_STORE),
-    NSM_VARIANT2(2, 8, 8, 2, 32, 32, 16, TPRO_UP_SKIP, TEPI_STORE),
-    NSM_VARIANT(2, 4, 9, 2, 0, 32, 32, 16, TPRO_UP_SKIP, TEPI_STORE),
-    NSM_VARIANT(2, 8, 9, 2, 0, 32, 32, 16, TPRO_UP_SKIP, TEPI_STORE)};
+    NSM_VARIANT2(2, 4, 8, 2, 32, 32, 16, TPRO_UP_SKIP, TEPI_STORE_PAIR),
+    NSM_VARIANT2(2, 8, 8, 2, 32, 32, 16, TPRO_UP_SKIP, TEPI_STORE_PAIR),
+    NSM_VARIANT(2, 4, 9, 2, 0, 32, 32, 16, TPRO_UP_SKIP, TEPI_STORE_PAIR),
+    NSM_VARIANT(2, 8, 9, 2, 0, 32, 32, 16, TPRO_UP_SKIP, TEPI_STORE_PAIR)};
+// level-0 decoder on the coarse grid: the tile is R coarse rows x 128 coarse
+// pixels (2R fine rows x 256 fine pixels), C_mid = 4 parities x 16 channels
 static const Variant kVarDec0[] = {
-    NSM_VARIANT2(4, 4, 8, 1, 16, 16, 16, TPRO_UP, TEPI_HEAD),
-    NSM_VARIANT2(4, 8, 8, 1, 16, 16, 16, TPRO_UP, TEPI_HEAD),
-    NSM_VARIANT(4, 8, 12, 1, 0, 16, 16, 16, TPRO_UP, TEPI_HEAD),
-    NSM_VARIANT(4, 8, 9, 1, 0, 16, 16, 16, TPRO_UP, TEPI_HEAD),
-    NSM_VARIANT(4, 4, 9, 1, 0, 16, 16, 16, TPRO_UP, TEPI_HEAD)};
+    NSM_VARIANT2(1, 4, 4, 1, 16, 64, 16, TPRO_PLAIN, TEPI_HEAD_PAR),
+    NSM_VARIANT2(2, 4, 4, 1, 16, 64, 16, TPRO_PLAIN, TEPI_HEAD_PAR),
+    NSM_VARIANT2(2, 8, 4, 1, 16, 64, 16, TPRO_PLAIN, TEPI_HEAD_PAR)};
 
 static const Variant kVarDec1Head4[] = {
     NSM_VARIANT2(2, 4, 8, 2, 32, 32, 16, TPRO_UP_SKIP, TEPI_HEAD4)};
@@ -1001,7 +1208,7 @@ int tc_stage_warps(int stage, int variant, int* producer_warps) {
 
 int tc_default_variant(int stage) {
     // the fastest plan of the 1080p autotuning runs
-    static const int def[kTcStages] = {2, 5, 4, 4, 3};
+    static const int def[kTcStages] = {2, 5, 4, 4, 5};
     return def[stage];
 }
 
@@ -1043,6 +1250,8 @@ void tc_make_batches(const GatherParams* g, const Activations* act, float* const
         b.bias3 = params + off.b[l3[s]];
         b.bias1 = params + off.b[l1[s]];
         b.head = params + off.w[HEAD];  // head weights followed by its bias
+        b.w3 = params + off.w[l3[s]];
+        b.w1 = params + off.w[l1[s]];
         b.err = err;
         for (int i = 0; i < n; ++i) {
             TcJob& j = b.job[i];
@@ -1056,8 +1265,9 @@ void tc_make_batches(const GatherParams* g, const Activations* act, float* const
                 case 2: j.H = H / 4; j.W = W / 4; j.in = static_cast<const uint16_t*>(A.p1);
                         j.out_f = static_cast<float*>(A.bo); break;
                 case 3: j.H = H / 2; j.W = W / 2; j.in_f = static_cast<const float*>(A.bo);
-                        j.skip = static_cast<const float*>(A.s1); j.out_f = static_cast<float*>(A.d1); break;
-                default: j.H = H; j.W = W; j.in_f = static_cast<const float*>(A.d1); j.vis = vis[i]; break;
+                        j.skip = static_cast<const float*>(A.s1); j.out = static_cast<uint16_t*>(A.d1); break;
+                // the level-0 decoder runs on the coarse (level-1) grid
+                default: j.H = H / 2; j.W = W / 2; j.in = static_cast<const uint16_t*>(A.d1); j.vis = vis[i]; break;
             }
         }
     }

@@ -21,7 +21,22 @@ namespace nsm {
 //   3x3, C_in >= 16:  chunk (kx, g, ky, n) = W[n][8g .. 8g+7][ky][kx]
 //   3x3 first level:  chunk (p, h, ky, n)  = column kx = 2p + h (zero for
 //                     kx = 3), channels [c0..c3 | c0..c3] as above
+// Coarse-grid form of an up-sampling decoder level (bilinear x2 then 3x3):
+//   chunk (tap, g, n), n = 16 p + o for output parity p = 2a + b:
+//   E[p][o][8g .. 8g+7][tap], where the effective weight of coarse offset
+//   (dy, dx) = tap is  E = sum_{ky,kx} W[o][c][ky][kx] q(a, ky, dy) q(b, kx, dx)
+//   and q(a, k, d) is the bilinear weight of coarse index i + d - 1 in fine
+//   index 2i + a + k - 1 (1/4 or 3/4, half-pixel centres), summed in FP64.
 using PackDesc = PackDescHost;
+
+__device__ double up_coef(int a, int k, int d) {
+    const int t = a + k - 1;           // fine index 2i + t
+    const int m = t >= 0 ? t / 2 : -1;  // = floor(t / 2)
+    const int par = t - 2 * m;
+    const int off = d - 1;
+    if (par == 0) return off == m - 1 ? 0.25 : (off == m ? 0.75 : 0.0);
+    return off == m ? 0.75 : (off == m + 1 ? 0.25 : 0.0);
+}
 
 __global__ void pack_bf16_kernel(const float* __restrict__ params, uint16_t* __restrict__ img,
                                  const PackDesc* __restrict__ descs, int ndesc) {
@@ -57,6 +72,21 @@ __global__ void pack_bf16_kernel(const float* __restrict__ params, uint16_t* __r
                 const int ky = static_cast<int>(t2 % 3);
                 const int kx = static_cast<int>(t2 / 3);  // = 2p + h
                 if (kx < 3) v = params[pd.w_off + (static_cast<size_t>(n) * 4 + (e % 4)) * 9 + ky * 3 + kx];
+            } else if (pd.kind == 5) {  // coarse-grid 3x3: chunk = (tap * (cin/8) + g) * cout + n
+                const int n = static_cast<int>(chunk % pd.cout);
+                const size_t t2 = chunk / pd.cout;
+                const int g = static_cast<int>(t2 % (pd.cin / 8));
+                const int tap = static_cast<int>(t2 / (pd.cin / 8));
+                const int co = pd.cout / 4, p = n / co, o = n % co, a = p >> 1, b = p & 1;
+                const int dy = tap / 3, dx = tap % 3;
+                double acc = 0.0;
+                for (int ky = 0; ky < 3; ++ky)
+                    for (int kx = 0; kx < 3; ++kx) {
+                        const double q = up_coef(a, ky, dy) * up_coef(b, kx, dx);
+                        if (q != 0.0)
+                            acc += q * params[pd.w_off + (static_cast<size_t>(o) * pd.cin + 8 * g + e) * 9 + ky * 3 + kx];
+                    }
+                v = static_cast<float>(acc);
             } else {  // 1x1: chunk = g * cout + n
                 const int n = static_cast<int>(chunk % pd.cout);
                 const int g = static_cast<int>(chunk / pd.cout);
@@ -79,9 +109,9 @@ BF16Images bf16_images(bool s2d) {
     BF16Images im{};
     size_t pos = 0;
     auto add = [&](int layer, int kind) {
-        const int ci = kLayers[layer].cin, co = kLayers[layer].cout;
+        const int ci = kLayers[layer].cin, co = (kind == 5 ? 4 : 1) * kLayers[layer].cout;
         size_t count;
-        if (kind == 0 || kind == 3) count = static_cast<size_t>(9) * ci * co;
+        if (kind == 0 || kind == 3 || kind == 5) count = static_cast<size_t>(9) * ci * co;
         else if (kind == 1) count = static_cast<size_t>(10) * co * 8;
         else if (kind == 4) count = static_cast<size_t>(12) * co * 8;
         else count = static_cast<size_t>(ci) * co;
@@ -96,7 +126,8 @@ BF16Images bf16_images(bool s2d) {
     if (!s2d) { add(ENC0_3, 3 * 2 * kLayers[ENC0_3].cout <= 256 ? 4 : 1); add(ENC0_1, 2); }
     add(ENC1_3, k3(ENC1_3)); add(ENC1_1, 2); add(BOTT_3, k3(BOTT_3)); add(BOTT_1, 2);
     add(DEC1_3, k3(DEC1_3)); add(DEC1_1, 2);
-    if (!s2d) { add(DEC0_3, k3(DEC0_3)); add(DEC0_1, 2); }
+    // the level-0 decoder runs on the coarse grid: effective weights of its 4 output parities
+    if (!s2d) { add(DEC0_3, 5); add(DEC0_1, 2); }
     im.total = pos;
     return im;
 }

@@ -13,7 +13,11 @@ constexpr int kMaxViews = 32;
 constexpr int kTcStages = 5;  // enc0 (+ gather), enc1, bottleneck, dec1, dec0 (+ head)
 
 enum TcPro { TPRO_GATHER = 0, TPRO_PLAIN = 1, TPRO_UP_SKIP = 2, TPRO_UP = 3 };
-enum TcEpi { TEPI_POOL = 0, TEPI_SKIP_POOL = 1, TEPI_STORE = 2, TEPI_HEAD = 3, TEPI_HEAD4 = 4 };
+// STORE_PAIR: like STORE, as BF16 hi + lo pairs [H][W][2][COUT];
+// HEAD_PAR: the level-0 decoder on the coarse grid (four output parities per
+// coarse pixel, 1x1 per parity, head, sigmoid; fine visibility [2H][2W])
+enum TcEpi { TEPI_POOL = 0, TEPI_SKIP_POOL = 1, TEPI_STORE = 2, TEPI_HEAD = 3, TEPI_HEAD4 = 4, TEPI_STORE_PAIR = 5,
+             TEPI_HEAD_PAR = 6 };
 
 // One view's work in one stage.
 struct TcJob {
@@ -26,7 +30,7 @@ struct TcJob {
     const uint16_t* in;         // PLAIN: [H][W][2][CIN]
     const float* in_f;          // UP*: [H/2][W/2][CIN]
     const float* skip;          // UP_SKIP: [H][W][CIN]
-    uint16_t* out;              // POOL / SKIP_POOL: pooled [H/2][W/2][2][COUT]
+    uint16_t* out;              // POOL / SKIP_POOL: pooled [H/2][W/2][2][COUT]; STORE_PAIR: [H][W][2][COUT]
     float* out_f;               // STORE: [H][W][COUT]
     float* out_skip;            // SKIP_POOL: [H][W][COUT]
     // FP8 form: every activation E4M3 [pixel][C], 1 byte per channel
@@ -34,7 +38,7 @@ struct TcJob {
     const uint8_t* skip8;       // UP_SKIP: [H][W][CIN]
     uint8_t* out8;              // POOL / SKIP_POOL: pooled [H/2][W/2][COUT]; STORE: [H][W][COUT]
     uint8_t* out_skip8;         // SKIP_POOL: [H][W][COUT]
-    float* vis;                 // HEAD: [H][W]; HEAD4 writes out_f [H][W][4]
+    float* vis;                 // HEAD: [H][W]; HEAD_PAR: [2H][2W]; HEAD4 writes out_f [H][W][4]
 };
 
 // Kernel parameter of a stage launch (passed by value, __grid_constant__).
@@ -47,6 +51,8 @@ struct TcBatch {
     const float* bias3;
     const float* bias1;
     const float* head;          // HEAD: weights [16] then bias; HEAD4: weights [4][16] then biases [4]
+    const float* w3;            // HEAD_PAR: FP32 3x3 weights [COUT][CIN][3][3] (exact border ring)
+    const float* w1;            // HEAD_PAR: FP32 1x1 weights [COUT][COUT]
     const float* scale3;        // FP8 form: per-output-channel weight scales of the 3x3
     const float* scale1;        // and of the 1x1
     int* err;                   // device error word

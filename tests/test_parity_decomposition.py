@@ -129,3 +129,20 @@ def test_ring_correction_by_the_taps_outside():
                     u = U[:, min(max(y, 0), H2 - 1), min(max(xx, 0), W2 - 1)]
                     corr += W[:, :, ky, kx] @ u
             np.testing.assert_allclose(diff[:, fy, fx], corr, rtol=1e-12, atol=1e-12)
+
+
+def test_oracle_effective_weights_and_coarse_model():
+    """The oracle's own statement of the effective weights equals this file's;
+    its coarse-grid level-0 decoder with no rounding equals the plain forward
+    on a rendered frame (interior by the identity, ring by the exact path)."""
+    import scenegen
+    from oracle import gather as G
+    rng = np.random.default_rng(9)
+    W = rng.standard_normal((16, 16, 3, 3))
+    np.testing.assert_allclose(N.upsample_conv_weights(W), effective_weights(W), rtol=0, atol=1e-13)
+    f = scenegen.soft_frame(36, 52, 128, 128, 6, 3)
+    feat, _, _ = G.features(f.pos4, f.nrm4, f.sm, f.view_proj, f.light_pos, f.cam_pos, f.r_hat, f.z_far, f.bias)
+    th = scenegen.trained_weights().astype(np.float64)
+    ref = N.forward(feat, th)
+    got = N.forward_rounded(feat, th, lambda x: x, coarse_dec0=True)
+    np.testing.assert_allclose(got, ref, rtol=0, atol=1e-13)
