@@ -122,7 +122,7 @@ struct TcCfg {
     static constexpr int OFF_HEAD = OFF_BIAS1 + COUT * 4;
     // PAR: FP32 3x3 [tap][c][o] and 1x1 [c][o] weights for the exact border ring
     static constexpr int OFF_RINGW = OFF_HEAD + 4 * (COUT + 1) * 4;
-    static constexpr int RINGW_BYTES = PAR ? (9 * COUT * COUT + COUT * COUT) * 4 : 0;
+    static constexpr int RINGW_BYTES = PAR ? (9 * COUT * COUT + COUT * COUT + 8 * 2 * 9 * COUT) * 4 : 0;
     static constexpr int OFF_ZERO = ((OFF_RINGW + RINGW_BYTES) + 127) / 128 * 128;  // zero A operand
     static constexpr int ZERO_BYTES = STACK ? kTileM * 16 + 128 : 0;
     static constexpr int OFF_BAR = OFF_ZERO + ZERO_BYTES;
@@ -437,8 +437,8 @@ __device__ __forceinline__ void stage_flush(uint32_t stg, int lane, float* gdst,
 // columns 0 and W - 1) the epilogue writes nothing, and the producer warps,
 // idle between their tiles' copies, compute those pixels exactly as the level
 // is defined (Sec. 3.5): bilinear x2 up-sampling of the coarse input, 3x3 +
-// ReLU, 1x1 + ReLU, head, sigmoid, in FP32 with the FP32 weights.  A warp
-// takes one ring pixel: lane = output channel o (16) x half of the taps.
+// ReLU, 1x1 + ReLU, head, sigmoid, in FP32 with the FP32 weights; a producer
+// warp takes one pair of ring pixels after each tile's copies.
 __host__ __device__ inline int ring_pixels(int Hf, int Wf) {
     return (Hf <= 0 || Wf <= 0) ? 0 : (Hf <= 2 ? Hf * Wf : 2 * Wf + 2 * (Hf - 2));
 }
@@ -460,58 +460,70 @@ __device__ __forceinline__ bool ring_locate(const TcBatch& a, int item, int& v, 
     return true;
 }
 
-// one ring pixel by one warp; w3s [tap][c][o] and w1s [c][o] FP32 weights in
-// shared memory, b3 / b1 biases, hs head weights then bias (C = 16)
-__device__ __forceinline__ void ring_pixel(const TcBatch& a, int item, const float* w3s, const float* w1s,
-                                           const float* b3, const float* b1, const float* hs, int lane) {
+// Two ring pixels per warp pass, items `item` and `item + 1` (below n_end):
+// half-warp h takes item + h, lane o of it output channel o.  FP32 weights in
+// shared memory: w3s [tap][c][o], w1s [c][o]; b3 / b1 biases; hs the head
+// weights then its bias; us a per-warp scratch of 2 x 9 x 16 floats (C = 16).
+__device__ __forceinline__ void ring_pair(const TcBatch& a, int item, int n_end, const float* w3s, const float* w1s,
+                                          const float* b3, const float* b1, const float* hs, float* us, int lane) {
     constexpr int C = 16;
-    int v, fy, fx;
-    if (!ring_locate(a, item, v, fy, fx)) return;  // (uniform over the warp)
-    const TcJob& job = a.job[v];
-    const int Hl = job.H, Wl = job.W, Hf = 2 * Hl, Wf = 2 * Wl;
-    const int o = lane & 15, t0 = (lane & 16) ? 5 : 0;
-    // channel o of the up-sampled input at this lane's taps (0 outside the image)
-    float u[5];
+    const int h = lane >> 4, o = lane & 15;
+    int v = 0, fy = 0, fx = 0;
+    const bool live = item + h < n_end && ring_locate(a, item + h, v, fy, fx);
+    // channel o of the up-sampled input at the pixel's nine taps (0 outside the image)
+    float u[9];
 #pragma unroll
-    for (int k = 0; k < 5; ++k) {
-        const int tap = t0 + k, y = fy + tap / 3 - 1, x = fx + tap % 3 - 1;
-        u[k] = 0.f;
-        if (tap < 9 && y >= 0 && y < Hf && x >= 0 && x < Wf) {
-            const BilinTap ty = bilin_tap(y, Hl), tx = bilin_tap(x, Wl);
-            auto px = [&](int ci, int cj) {
-                const uint16_t* p = job.in + (static_cast<size_t>(ci) * Wl + cj) * 2 * C + o;
-                return __bfloat162float(__ushort_as_bfloat16(p[0])) + __bfloat162float(__ushort_as_bfloat16(p[C]));
-            };
-            u[k] = ty.w0 * (tx.w0 * px(ty.i0, tx.i0) + tx.w1 * px(ty.i0, tx.i1)) +
-                   ty.w1 * (tx.w0 * px(ty.i1, tx.i0) + tx.w1 * px(ty.i1, tx.i1));
+    for (int tap = 0; tap < 9; ++tap) u[tap] = 0.f;
+    if (live) {
+        const TcJob& job = a.job[v];
+        const int Hl = job.H, Wl = job.W;
+#pragma unroll
+        for (int tap = 0; tap < 9; ++tap) {
+            const int y = fy + tap / 3 - 1, x = fx + tap % 3 - 1;
+            if (y >= 0 && y < 2 * Hl && x >= 0 && x < 2 * Wl) {
+                const BilinTap ty = bilin_tap(y, Hl), tx = bilin_tap(x, Wl);
+                auto px = [&](int ci, int cj) {
+                    const uint16_t* p = job.in + (static_cast<size_t>(ci) * Wl + cj) * 2 * C + o;
+                    return __bfloat162float(__ushort_as_bfloat16(p[0])) + __bfloat162float(__ushort_as_bfloat16(p[C]));
+                };
+                u[tap] = ty.w0 * (tx.w0 * px(ty.i0, tx.i0) + tx.w1 * px(ty.i0, tx.i1)) +
+                         ty.w1 * (tx.w0 * px(ty.i1, tx.i0) + tx.w1 * px(ty.i1, tx.i1));
+            }
         }
     }
-    float acc = 0.f;
 #pragma unroll
-    for (int k = 0; k < 5; ++k) {
-        const int tap = t0 + k;
+    for (int tap = 0; tap < 9; ++tap) us[(h * 9 + tap) * C + o] = u[tap];
+    __syncwarp();
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-        for (int c = 0; c < C; ++c) {
-            const float uc = __shfl_sync(0xffffffffu, u[k], (lane & 16) | c);
-            if (tap < 9) acc = fmaf(w3s[(tap * C + c) * C + o], uc, acc);
+    for (int tap = 0; tap < 9; ++tap)
+#pragma unroll
+        for (int c = 0; c < C; c += 4) {
+            const float4 u4 = *reinterpret_cast<const float4*>(us + (h * 9 + tap) * C + c);
+            acc[0] = fmaf(w3s[(tap * C + c) * C + o], u4.x, acc[0]);
+            acc[1] = fmaf(w3s[(tap * C + c + 1) * C + o], u4.y, acc[1]);
+            acc[2] = fmaf(w3s[(tap * C + c + 2) * C + o], u4.z, acc[2]);
+            acc[3] = fmaf(w3s[(tap * C + c + 3) * C + o], u4.w, acc[3]);
         }
-    }
-    acc += __shfl_xor_sync(0xffffffffu, acc, 16);
-    const float h = fmaxf(acc + b3[o], 0.f);
+    const float hv = fmaxf((acc[0] + acc[1]) + (acc[2] + acc[3]) + b3[o], 0.f);
     float z = b1[o];
 #pragma unroll
-    for (int c = 0; c < C; ++c) z = fmaf(w1s[c * C + o], __shfl_sync(0xffffffffu, h, c), z);
+    for (int c = 0; c < C; ++c) z = fmaf(w1s[c * C + o], __shfl_sync(0xffffffffu, hv, (lane & 16) | c), z);
     float t = hs[o] * fmaxf(z, 0.f);
 #pragma unroll
     for (int m = 8; m >= 1; m >>= 1) t += __shfl_xor_sync(0xffffffffu, t, m);
-    if (lane == 0) job.vis[static_cast<size_t>(fy) * Wf + fx] = sigmoidf_fast(t + hs[C]);
+    if (live && o == 0) a.job[v].vis[static_cast<size_t>(fy) * (2 * a.job[v].W) + fx] = sigmoidf_fast(t + hs[C]);
+    __syncwarp();  // us is reused by the next pass
 }
 
+// warps of a CTA: NEW epilogue, NPW producer, one MMA
+constexpr int tc_warps(int NEW, int NPW, int EPI) { return NEW + NPW + 1 + 0 * EPI; }
+
 template <int CIN, int CMID, int COUT, int R, int PRO, int EPI, int NEW, int NPW, int KS, int ORD>
-__global__ void __launch_bounds__(32 * (NEW + NPW + 1), 1) level_tc_kernel(const __grid_constant__ TcBatch a) {
+__global__ void __launch_bounds__(32 * tc_warps(NEW, NPW, EPI), 1) level_tc_kernel(const __grid_constant__ TcBatch a) {
     constexpr bool PAR = (EPI == TEPI_HEAD_PAR);
     using C = TcCfg<CIN, CMID, COUT, R, PRO, KS, PAR>;
-    constexpr int NP = 32 * NPW, NT = 32 * (NEW + NPW + 1), MW = NEW + NPW, NE = 32 * NEW;
+    constexpr int NP = 32 * NPW, NT = 32 * tc_warps(NEW, NPW, EPI), MW = NEW + NPW, NE = 32 * NEW;
     static_assert(NEW == 4 || NEW == 8, "epilogue warps cover the four TMEM lane quarters");
     extern __shared__ __align__(1024) unsigned char smem[];
     const uint32_t sbase = smem_u32(smem);
@@ -620,9 +632,12 @@ __global__ void __launch_bounds__(32 * (NEW + NPW + 1), 1) level_tc_kernel(const
             }
         }
         bool failed = false;
-        // PAR: this CTA's share [ring_lo, ring_hi) of the batch's border-ring pixels
+        // PAR: this CTA's share [ring_lo, ring_hi) of the batch's border-ring
+        // pixels; producer warp w takes pairs w, w + NPW, ... one per tile
         int ring_lo = 0, ring_hi = 0;
+        float* ring_us = ringw + 10 * COUT * COUT + (pt / 32) * 2 * 9 * COUT;
         if constexpr (PAR) {
+            static_assert(NPW <= 8, "ring scratch per producer warp");
             long long nr = 0;
             for (int q = 0; q < a.nviews; ++q) nr += ring_pixels(2 * a.job[q].H, 2 * a.job[q].W);
             ring_lo = static_cast<int>(nr * blockIdx.x / gridDim.x);
@@ -675,14 +690,14 @@ __global__ void __launch_bounds__(32 * (NEW + NPW + 1), 1) level_tc_kernel(const
             if (failed) break;
             if constexpr (PRO != TPRO_PLAIN) mbar_arrive(rfree + rb);
             if constexpr (PAR) {
-                const int k = ring_lo + it * NPW + pt / 32;
+                const int k = ring_lo + 2 * (it * NPW + pt / 32);
                 if (k < ring_hi)
-                    ring_pixel(a, k, ringw, ringw + 9 * COUT * COUT, bias3_s, bias1_s, head_s, tid & 31);
+                    ring_pair(a, k, ring_hi, ringw, ringw + 9 * COUT * COUT, bias3_s, bias1_s, head_s, ring_us, tid & 31);
             }
         }
         if constexpr (PAR) {
-            for (int k = ring_lo + it * NPW + pt / 32; !failed && k < ring_hi; k += NPW)
-                ring_pixel(a, k, ringw, ringw + 9 * COUT * COUT, bias3_s, bias1_s, head_s, tid & 31);
+            for (int k = ring_lo + 2 * (it * NPW + pt / 32); !failed && k < ring_hi; k += 2 * NPW)
+                ring_pair(a, k, ring_hi, ringw, ringw + 9 * COUT * COUT, bias3_s, bias1_s, head_s, ring_us, tid & 31);
         }
         if (failed) {
             atomicExch(a.err, 3);
@@ -1109,7 +1124,7 @@ static cudaError_t launch_variant(const TcBatch& a, int ctas_per_sm, cudaStream_
         cudaFuncAttributes fa{};
         e = cudaFuncGetAttributes(&fa, kern);
         if (e != cudaSuccess) return e;
-        const int regs = ((fa.numRegs + 7) / 8) * 8 * (32 * (NEW + NPW + 1));
+        const int regs = ((fa.numRegs + 7) / 8) * 8 * (32 * tc_warps(NEW, NPW, EPI));
         const int by_regs = regs > 0 ? 65536 / regs : 8;
         const int by_smem = (228 * 1024) / (C::BYTES + 1024);
         int o = by_regs < by_smem ? by_regs : by_smem;
@@ -1122,7 +1137,7 @@ static cudaError_t launch_variant(const TcBatch& a, int ctas_per_sm, cudaStream_
     const int per_sm = (ctas_per_sm <= 0 || ctas_per_sm > occ) ? occ : ctas_per_sm;
     const int cap = per_sm * num_sms();
     const int grid = tiles < cap ? tiles : cap;
-    kern<<<grid, 32 * (NEW + NPW + 1), C::BYTES, stream>>>(a);
+    kern<<<grid, 32 * tc_warps(NEW, NPW, EPI), C::BYTES, stream>>>(a);
     return cudaGetLastError();
 }
 
@@ -1136,7 +1151,7 @@ static int occupancy_of() {
     using C = TcCfg<CIN, CMID, COUT, R, PRO, KS, EPI == TEPI_HEAD_PAR>;
     cudaFuncAttributes fa{};
     if (cudaFuncGetAttributes(&fa, level_tc_kernel<CIN, CMID, COUT, R, PRO, EPI, NEW, NPW, KS, ORD>) != cudaSuccess) return 1;
-    const int regs = ((fa.numRegs + 7) / 8) * 8 * (32 * (NEW + NPW + 1));
+    const int regs = ((fa.numRegs + 7) / 8) * 8 * (32 * tc_warps(NEW, NPW, EPI));
     const int by_regs = regs > 0 ? 65536 / regs : 8;
     const int by_smem = (228 * 1024) / (C::BYTES + 1024);
     int o = by_regs < by_smem ? by_regs : by_smem;
