@@ -408,6 +408,44 @@ def extra_soft_frame(nsm, scenegen, torch, device, theta, weights, ctx, reps, wi
     return out
 
 
+def extra_sensitivity(nsm, scenegen, torch, device, theta, weights, ctx):
+    """Eq. 1 feature sensitivity of the trained net on a 1080p hard and a 1080p
+    soft frame (BF16 form): sigma over both frames' pixels, two standard
+    normal draws per channel and frame (seed 31)."""
+    frames = [scenegen.hard_frame(H, W, HS, WS, N_OBJ, SCENE_SEED), scenegen.soft_frame(H, W, HS, WS, N_OBJ,
+                                                                                         SCENE_SEED + 10)]
+    dev = []
+    for f in frames:
+        light = nsm.LightDesc(pos=tuple(f.light_pos), radius=f.light_radius, r_hat=f.r_hat, view_proj=f.view_proj,
+                              z_far=f.z_far, bias=f.bias, tan_half_fov=f.tan_half_fov)
+        t = tuple(torch.from_numpy(x).to(device) for x in (f.pos4, f.nrm4, f.sm))
+        dev.append((t, nsm.make_frame(t[0], t[1], t[2], light, f.cam_pos)))
+    mom = torch.zeros(8, dtype=torch.float64, device=device)
+    for _, fr in dev:
+        nsm.feature_moments(fr, mom)
+    n = len(frames) * H * W
+    m = mom.cpu().numpy()
+    sigma = np.sqrt(np.maximum(m[4:] / n - (m[:4] / n) ** 2, 0.0))
+    draws = 2
+    gen = torch.Generator(device=device)
+    gen.manual_seed(31)
+    ws = torch.empty(nsm.nsm_sensitivity_workspace_bytes(H, W), dtype=torch.uint8, device=device)
+    s = torch.zeros(4, dtype=torch.float64, device=device)
+    ev = _events(torch, 2)
+    ev[0].record()
+    for _, fr in dev:
+        noise = torch.randn((draws, 4, H, W), generator=gen, device=device)
+        nsm.sensitivity(ctx, fr, weights, nsm.NSM_BF16, noise, sigma, ws, s)
+    ev[1].record()
+    torch.cuda.synchronize()
+    S = s.cpu().numpy() / (len(frames) * draws * H * W)
+    names = ["c_e + r_e", "z / z_f", "z - z_f", "c_c / d"]
+    return {"workload": "1920x1080 hard + soft frames, 2048^2 maps, trained weights, BF16 form, 2 draws per channel",
+            "sigma": dict(zip(names, sigma.tolist())), "absolute": dict(zip(names, S.tolist())),
+            "relative": dict(zip(names, (S / S.sum()).tolist())), "ms": ev[0].elapsed_time(ev[1]),
+            "passes": len(frames) * (1 + 4 * draws)}
+
+
 def oracle_band(frame, theta64, y0: int, y1: int, margin: int = 32):
     """FP64 oracle visibility of rows [y0, y1) (y0, y1 multiples of 4), computed
     on the rows [y0 - margin, y1 + margin) clipped to the frame: the network's
@@ -825,6 +863,8 @@ def run_ours(args):
                          ("space_to_depth_1080p", lambda: extra_s2d(nsm, scenegen, torch, device, ctx, 10,
                                                                     not args.skip_error)),
                          ("serving_32_views", lambda: extra_serving(nsm, scenegen, torch, device, theta, 20)),
+                         ("feature_sensitivity_1080p", lambda: extra_sensitivity(nsm, scenegen, torch, device, theta,
+                                                                                 weights, ctx)),
                          ("penumbra_depth_1080p", lambda: extra_penumbra_depth(nsm, scenegen, torch, device, 10)),
                          ("deep_networks_1088p", lambda: extra_deep(nsm, scenegen, torch, device, 5)),
                          ("train_step", lambda: extra_train(nsm, scenegen, torch, device, theta, 10)),

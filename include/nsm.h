@@ -453,6 +453,37 @@ nsm_status nsm_penumbra_histogram(int H, int W, const float* blocker, const floa
  * ceil(log2(p95 / 3)). */
 nsm_status nsm_depth_for_penumbra(const uint32_t* hist, int nbins, float bin_px, float* p95_px, int* levels);
 
+/* ---------------------------------------------------------------- feature sensitivity (Sec. 3.2, Eq. 1) */
+
+/* Per-channel sums of the four input features over the frame's pixels, added
+ * to moments_inout (device, 8 doubles: sum f_0..f_3, then sum f_0^2..f_3^2),
+ * for the standard deviation sigma_i of each channel over a set of frames
+ * (the paper estimates it over all pixels of its dataset).  H, W any size.
+ * Asynchronous on stream. */
+nsm_status nsm_feature_moments(const nsm_frame* frame, double* moments_inout, void* stream);
+
+/* Workspace bytes of nsm_sensitivity for an H x W view (0 if invalid). */
+size_t nsm_sensitivity_workspace_bytes(int H, int W);
+
+/* Sensitivity of the network output to each input feature channel (Eq. 1):
+ * one base inference and, for every channel i and draw k, one inference with
+ * feature channel i perturbed by eps = 0.1 sigma[i] noise[k][i][p] inside the
+ * gather; adds sum_p |phi_pert(p) - phi(p)| / (0.1 sigma[i]) to s_inout[i]
+ * (device, 4 doubles).  Dividing by the number of pixels and draws gives
+ * S_i = E|phi(f_i + eps_i) - phi(f_i)| / (0.1 sigma_i); s_i = S_i / sum S the
+ * relative sensitivity.  Reading: Eq. 1's expectation is taken of the
+ * absolute change (the signed change averages to about zero for symmetric
+ * noise); eps_i has standard deviation 0.1 sigma_i.
+ *   noise      device, [draws][4][H][W] floats: the caller's standard normal
+ *              draws (the method's random numbers are inputs)
+ *   sigma      host, 4 floats > 0
+ *   precision  NSM_FP32 or NSM_BF16 (3-level weights); others NSM_ERR_UNSUPPORTED
+ *   workspace  device, nsm_sensitivity_workspace_bytes(H, W), 256-byte aligned
+ * H, W multiples of 4.  1 + 4 draws inference passes.  Asynchronous on stream. */
+nsm_status nsm_sensitivity(nsm_ctx* ctx, const nsm_frame* frame, const nsm_weights* weights, nsm_precision precision,
+                           const float* noise, int draws, const float* sigma, void* workspace, size_t workspace_bytes,
+                           double* s_inout, void* stream);
+
 /* ---------------------------------------------------------------- no-allocation variant */
 
 /* FP32 inference that allocates nothing and needs no workspace, for callers

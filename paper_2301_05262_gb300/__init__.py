@@ -640,3 +640,47 @@ def depth_for_penumbra(hist, bin_px):
     _check(_gen_sigs().nsm_depth_for_penumbra(_ptr(h), h.size, float(bin_px), ctypes.byref(p95), ctypes.byref(lv)),
            "nsm_depth_for_penumbra")
     return float(p95.value), int(lv.value)
+
+
+# ------------------------------------------------------------------ feature sensitivity (Sec. 3.2, Eq. 1)
+_SENS = None
+
+
+def _sens_sigs():
+    global _SENS
+    if _SENS is None:
+        L = lib()
+        P, I, Z = ctypes.c_void_p, ctypes.c_int, ctypes.c_size_t
+        FP = ctypes.POINTER(nsm_frame)
+        for name, (args, res) in {
+            "nsm_feature_moments": ([FP, P, P], I),
+            "nsm_sensitivity_workspace_bytes": ([I, I], Z),
+            "nsm_sensitivity": ([P, FP, P, I, P, I, P, P, Z, P, P], I),
+        }.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = res
+        _SENS = L
+    return _SENS
+
+
+def feature_moments(frame: nsm_frame, moments_inout, stream=None):
+    """Adds the frame's per-channel sums of f and f^2 to a device float64[8]."""
+    _check(_sens_sigs().nsm_feature_moments(ctypes.byref(frame), _ptr(moments_inout), _stream(stream)),
+           "nsm_feature_moments")
+
+
+def nsm_sensitivity_workspace_bytes(H: int, W: int) -> int:
+    return int(_sens_sigs().nsm_sensitivity_workspace_bytes(H, W))
+
+
+def sensitivity(ctx: Context, frame: nsm_frame, weights: Weights, precision: int, noise, sigma, workspace, s_inout,
+                stream=None):
+    """Adds sum_p |phi_pert - phi| / (0.1 sigma_i) over pixels and draws to a
+    device float64[4]; noise is a device float32 [draws][4][H][W] of standard
+    normal draws, sigma 4 host floats."""
+    sig = _host_f32(sigma)
+    draws = int(noise.shape[0])
+    _check(_sens_sigs().nsm_sensitivity(ctx.h, ctypes.byref(frame), weights.h, precision, _ptr(noise), draws,
+                                        _ptr(sig), _ptr(workspace), int(workspace.numel() * workspace.element_size()),
+                                        _ptr(s_inout), _stream(stream)), "nsm_sensitivity")

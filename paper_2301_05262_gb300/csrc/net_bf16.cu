@@ -248,6 +248,8 @@ __device__ __forceinline__ void compute_gather(const TcJob& job, int y0, int x0,
             if (ok[k]) {
                 float f[4];
                 pixel_features(g, P[k], Nv[k], z[k], f);
+                if (g.feat_eps)
+                    f[g.eps_ch] += g.eps_scale * __ldg(g.feat_eps + static_cast<size_t>(y0 - 1 + sr) * W + (x0 - 1 + sp));
                 float hl[8];
 #pragma unroll
                 for (int c = 0; c < 4; ++c) {

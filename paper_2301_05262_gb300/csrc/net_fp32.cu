@@ -96,7 +96,11 @@ __global__ void __launch_bounds__(QH * QW) level_fp32_kernel(LevelArgs a) {
                 const int ry = r / S::RW, rx = r % S::RW;
                 const int gy = y0 - 1 + ry, gx = x0 - 1 + rx;
                 float f[4] = {0.f, 0.f, 0.f, 0.f};
-                if (gy >= 0 && gy < H && gx >= 0 && gx < W) gather_features(a.g, gy, gx, f);
+                if (gy >= 0 && gy < H && gx >= 0 && gx < W) {
+                    gather_features(a.g, gy, gx, f);
+                    if (a.g.feat_eps)
+                        f[a.g.eps_ch] += a.g.eps_scale * __ldg(a.g.feat_eps + static_cast<size_t>(gy) * W + gx);
+                }
 #pragma unroll
                 for (int c = 0; c < 4; ++c) in_s[c * S::PLANE + r] = f[c];
             }

@@ -411,6 +411,16 @@ size_t nsm_infer_workspace_bytes(int H, int W, nsm_precision precision) {
 
 nsm_status nsm_infer(nsm_ctx* ctx, const nsm_frame* frame, const nsm_weights* w, nsm_precision precision,
                      void* workspace, size_t workspace_bytes, float* vis_out, void* stream) {
+    return infer_impl(ctx, frame, w, precision, workspace, workspace_bytes, vis_out, stream, nullptr, 0.f, 0);
+}
+
+}  // extern "C"
+
+namespace nsm {
+
+nsm_status infer_impl(nsm_ctx* ctx, const nsm_frame* frame, const nsm_weights* w, nsm_precision precision,
+                      void* workspace, size_t workspace_bytes, float* vis_out, void* stream, const float* feat_eps,
+                      float eps_scale, int eps_ch) {
     if (!ctx) return fail(NSM_ERR_INVALID_ARG, "ctx is NULL");
     if (!w) return fail(NSM_ERR_INVALID_ARG, "weights is NULL");
     if (precision != NSM_FP32 && precision != NSM_BF16 && precision != NSM_FP8)
@@ -430,6 +440,13 @@ nsm_status nsm_infer(nsm_ctx* ctx, const nsm_frame* frame, const nsm_weights* w,
     Activations act{};
     activations_bytes(frame->H, frame->W, 4, &act, workspace);
     GatherParams g = make_gather(frame);
+    if (feat_eps) {
+        if (w->topology != NSM_TOPO_LEVELS3 || (precision != NSM_FP32 && precision != NSM_BF16))
+            return fail(NSM_ERR_UNSUPPORTED, "feature perturbations run in the 3-level FP32 and BF16 forms");
+        g.feat_eps = feat_eps;
+        g.eps_scale = eps_scale;
+        g.eps_ch = eps_ch;
+    }
     StageEvents se;
     const int k = nsm_infer_kernel_count(precision);
     if (!ctx->stage_events.empty()) {
@@ -456,6 +473,10 @@ nsm_status nsm_infer(nsm_ctx* ctx, const nsm_frame* frame, const nsm_weights* w,
     if (e != cudaSuccess) return cuda_fail(e, "inference kernel launch");
     return NSM_OK;
 }
+
+}  // namespace nsm
+
+extern "C" {
 
 size_t nsm_infer_host_stage_bytes(int H, int W, int Hs, int Ws) {
     if (H <= 0 || W <= 0 || Hs <= 0 || Ws <= 0) return 0;

@@ -25,6 +25,12 @@ struct GatherParams {
     const float4* __restrict__ pos4;
     const float4* __restrict__ nrm4;
     const float* __restrict__ sm;
+    // Feature perturbation of the sensitivity analysis (Sec. 3.2, Eq. 1): when
+    // set, feature channel eps_ch of pixel p gets eps_scale * feat_eps[p] added
+    // in the gather (FP32 and BF16 forms); null otherwise
+    const float* __restrict__ feat_eps;
+    float eps_scale;
+    int eps_ch;
 };
 
 // Texel choice for world position P, binary32 with the operation order that

@@ -50,6 +50,10 @@ bool finite_all(const float* v, int n);
 nsm_status check_frame_host(const nsm_frame* f, bool need_mult4);
 nsm_status check_frame(const nsm_frame* f, bool need_mult4);
 GatherParams make_gather(const nsm_frame* f);
+// nsm_infer with an optional feature perturbation (feat_eps null: none; see GatherParams)
+nsm_status infer_impl(nsm_ctx* ctx, const nsm_frame* frame, const nsm_weights* w, nsm_precision precision,
+                      void* workspace, size_t workspace_bytes, float* vis_out, void* stream, const float* feat_eps,
+                      float eps_scale, int eps_ch);
 size_t align_up(size_t v, size_t a);
 
 // Activation buffers of one inference, carved out of the caller's workspace.

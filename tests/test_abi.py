@@ -147,3 +147,14 @@ def test_host_validation_of_the_static_entry_point(lib):
     assert f(ctypes.byref(frame(64, 64, radius=-0.1)), None, None, None) == 1
     assert f(ctypes.byref(frame(64, 64, bias=-1e-3)), None, None, None) == 1
     assert f(ctypes.byref(frame(0, 64)), None, None, None) == 0         # empty view: nothing to do
+
+
+def test_host_validation_of_the_sensitivity_entry_points(lib):
+    typed = nsm._sens_sigs()
+    assert typed.nsm_feature_moments(None, None, None) == 1
+    assert b"frame" in lib.nsm_last_error()
+    assert typed.nsm_sensitivity(None, None, None, 0, None, 1, None, None, 0, None, None) == 1
+    assert b"ctx" in lib.nsm_last_error()
+    assert nsm.nsm_sensitivity_workspace_bytes(0, 64) == 0
+    H, W = 64, 96
+    assert nsm.nsm_sensitivity_workspace_bytes(H, W) >= nsm.nsm_infer_workspace_bytes(H, W, nsm.NSM_FP32) + 2 * H * W * 4
