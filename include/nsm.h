@@ -261,6 +261,17 @@ nsm_status nsm_ctx_set_graph(nsm_ctx* ctx, int enable);
 /* Graph launches of the currently cached plan since it was captured. */
 int nsm_ctx_graph_replays(nsm_ctx* ctx);
 
+/* Per-view latency of nsm_infer_batched (a serving measurement beside the
+ * paper's per-frame timings, Sec. 4): with dev_records set (device, 65
+ * uint64, 8-byte aligned), every later batched call writes there the
+ * %globaltimer time (ns) at which its first kernel started ([0]) and the time
+ * the last output pixel of view v was written ([1 + v], v < n); words
+ * [33 .. 64] are the kernels' completion counters.  Read them after the call
+ * has finished (e.g. after a stream synchronisation); view v's latency is
+ * [1 + v] - [0].  NULL turns the records off (the default).  Costs one atomic
+ * per epilogue warp and tile of the last stage. */
+nsm_status nsm_ctx_set_view_timing(nsm_ctx* ctx, unsigned long long* dev_records);
+
 /* Autotuner: time every tile height and every CTAs-per-SM choice of each of
  * the five tensor-core stages on this batch (reps timed launches each, after
  * one warm-up) and keep the fastest per stage in the context's plan, used by

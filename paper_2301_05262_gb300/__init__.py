@@ -457,6 +457,7 @@ def _batch_sigs():
         "nsm_infer_batched_workspace_bytes": ([I, VP], Z),
         "nsm_infer_batched": ([P, I, VP, P, P, Z, P], I),
         "nsm_ctx_set_graph": ([P, I], I),
+        "nsm_ctx_set_view_timing": ([P, P], I),
         "nsm_ctx_graph_replays": ([P], I),
         "nsm_autotune": ([P, I, VP, P, P, Z, I, P], I),
         "nsm_autotune_report": ([P, P, P, P], I),
@@ -493,6 +494,12 @@ def nsm_infer_batched(ctx: Context, views, weights: Weights, workspace, stream=N
 
 def nsm_ctx_set_graph(ctx: Context, enable: bool):
     _check(_batch_sigs().nsm_ctx_set_graph(ctx.h, 1 if enable else 0), "nsm_ctx_set_graph")
+
+
+def nsm_ctx_set_view_timing(ctx: Context, records=None):
+    """Per-view completion records of later batched calls: a device int64[65]
+    tensor ([0] start, [1 + v] view v done, %globaltimer ns), or None (off)."""
+    _check(_batch_sigs().nsm_ctx_set_view_timing(ctx.h, _ptr(records)), "nsm_ctx_set_view_timing")
 
 
 def nsm_ctx_graph_replays(ctx: Context) -> int:

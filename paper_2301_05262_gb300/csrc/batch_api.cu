@@ -74,6 +74,15 @@ size_t nsm_infer_batched_workspace_bytes(int n, const nsm_view* views) {
     return t;
 }
 
+nsm_status nsm_ctx_set_view_timing(nsm_ctx* c, unsigned long long* dev_records) {
+    if (!c) return fail(NSM_ERR_INVALID_ARG, "ctx is NULL");
+    nsm_status s;
+    if (dev_records && (s = check_dev_ptr(dev_records, "dev_records", 8)) != NSM_OK) return s;
+    c->view_timing = dev_records;
+    ctx_release_graph(c);  // the kernels' argument changes
+    return NSM_OK;
+}
+
 nsm_status nsm_ctx_set_graph(nsm_ctx* c, int enable) {
     if (!c) return fail(NSM_ERR_INVALID_ARG, "ctx is NULL");
     c->use_graph = enable ? 1 : 0;
@@ -100,6 +109,7 @@ nsm_status nsm_infer_batched(nsm_ctx* c, int n, const nsm_view* views, const nsm
     carve_views(n, views, workspace, act, gp, vis);
     TcBatch b[kTcStages];
     tc_make_batches(gp.data(), act.data(), vis.data(), n, w->d_params, w->d_bf16, c->d_err, b);
+    b[0].timing = b[kTcStages - 1].timing = c->view_timing;
     cudaError_t e;
     if (!c->use_graph) {
         for (int k = 0; k < kTcStages; ++k)

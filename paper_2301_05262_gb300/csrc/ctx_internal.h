@@ -23,6 +23,7 @@ struct nsm_ctx {
     cudaGraphNode_t graph_nodes[nsm::kTcStages];
     cudaKernelNodeParams graph_params[nsm::kTcStages];
     int graph_launches;                      // replays of the cached graph (for tests)
+    unsigned long long* view_timing;         // per-view completion records of nsm_infer_batched (null: off)
     // nsm_infer_host_sequence: copy streams and per-slot events (created on first use)
     cudaStream_t h2d_stream, d2h_stream;
     cudaEvent_t slot_h2d[nsm::kMaxHostSlots], slot_inf[nsm::kMaxHostSlots], slot_d2h[nsm::kMaxHostSlots];

@@ -462,12 +462,32 @@ __device__ __forceinline__ bool ring_locate(const TcBatch& a, int item, int& v, 
     return true;
 }
 
+// One more finished unit (a tile row group of an epilogue warp, or a ring
+// pixel) of view v; the arrival that completes the view stamps its time.
+__device__ __forceinline__ void view_unit_done(const TcBatch& a, int v, unsigned expected) {
+    __threadfence();
+    unsigned long long* cnt = a.timing + 1 + kMaxViews + v;
+    if (atomicAdd(cnt, 1ull) + 1 == expected) {
+        unsigned long long t;
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+        a.timing[1 + v] = t;
+    }
+}
+
+// units of view v that view_unit_done counts in the level-0 decoder: every
+// epilogue warp's pass over each tile, and every ring pixel
+__device__ __forceinline__ unsigned view_units(const TcBatch& a, int v, int new_warps) {
+    return static_cast<unsigned>(a.tile_start[v + 1] - a.tile_start[v]) * new_warps +
+           ring_pixels(2 * a.job[v].H, 2 * a.job[v].W);
+}
+
 // Two ring pixels per warp pass, items `item` and `item + 1` (below n_end):
 // half-warp h takes item + h, lane o of it output channel o.  FP32 weights in
 // shared memory: w3s [tap][c][o], w1s [c][o]; b3 / b1 biases; hs the head
 // weights then its bias; us a per-warp scratch of 2 x 9 x 16 floats (C = 16).
 __device__ __forceinline__ void ring_pair(const TcBatch& a, int item, int n_end, const float* w3s, const float* w1s,
-                                          const float* b3, const float* b1, const float* hs, float* us, int lane) {
+                                          const float* b3, const float* b1, const float* hs, float* us, int lane,
+                                          int new_warps) {
     constexpr int C = 16;
     const int h = lane >> 4, o = lane & 15;
     int v = 0, fy = 0, fx = 0;
@@ -514,7 +534,10 @@ __device__ __forceinline__ void ring_pair(const TcBatch& a, int item, int n_end,
     float t = hs[o] * fmaxf(z, 0.f);
 #pragma unroll
     for (int m = 8; m >= 1; m >>= 1) t += __shfl_xor_sync(0xffffffffu, t, m);
-    if (live && o == 0) a.job[v].vis[static_cast<size_t>(fy) * (2 * a.job[v].W) + fx] = sigmoidf_fast(t + hs[C]);
+    if (live && o == 0) {
+        a.job[v].vis[static_cast<size_t>(fy) * (2 * a.job[v].W) + fx] = sigmoidf_fast(t + hs[C]);
+        if (a.timing) view_unit_done(a, v, view_units(a, v, new_warps));
+    }
     __syncwarp();  // us is reused by the next pass
 }
 
@@ -582,6 +605,13 @@ __global__ void __launch_bounds__(32 * tc_warps(NEW, NPW, EPI), 1) level_tc_kern
         *s_abort = 0;
     }
     if (warp == MW) tmem_alloc(tslot, C::TMEM_COLS);
+    if (PRO == TPRO_GATHER && a.timing && blockIdx.x == 0 && tid == 0) {
+        // batched serving: the batch starts now; clear the views' completion records
+        unsigned long long t;
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+        a.timing[0] = t;
+        for (int v = 0; v < a.nviews; ++v) a.timing[1 + v] = a.timing[1 + kMaxViews + v] = 0;
+    }
     fence_proxy_async_smem();  // the weights are read by the tensor core
     fence_before_sync();
     __syncthreads();
@@ -694,12 +724,14 @@ __global__ void __launch_bounds__(32 * tc_warps(NEW, NPW, EPI), 1) level_tc_kern
             if constexpr (PAR) {
                 const int k = ring_lo + 2 * (it * NPW + pt / 32);
                 if (k < ring_hi)
-                    ring_pair(a, k, ring_hi, ringw, ringw + 9 * COUT * COUT, bias3_s, bias1_s, head_s, ring_us, tid & 31);
+                    ring_pair(a, k, ring_hi, ringw, ringw + 9 * COUT * COUT, bias3_s, bias1_s, head_s, ring_us, tid & 31,
+                              NEW);
             }
         }
         if constexpr (PAR) {
             for (int k = ring_lo + 2 * (it * NPW + pt / 32); !failed && k < ring_hi; k += 2 * NPW)
-                ring_pair(a, k, ring_hi, ringw, ringw + 9 * COUT * COUT, bias3_s, bias1_s, head_s, ring_us, tid & 31);
+                ring_pair(a, k, ring_hi, ringw, ringw + 9 * COUT * COUT, bias3_s, bias1_s, head_s, ring_us, tid & 31,
+                          NEW);
         }
         if (failed) {
             atomicExch(a.err, 3);
@@ -1097,6 +1129,10 @@ __global__ void __launch_bounds__(32 * tc_warps(NEW, NPW, EPI), 1) level_tc_kern
                         __syncwarp();
                     }
                 }
+            }
+            if (PAR && a.timing) {
+                __syncwarp();
+                if ((tid & 31) == 0) view_unit_done(a, v, view_units(a, v, NEW));
             }
             // the next tile's 3x3 result goes where the rows were staged
             if constexpr (kStage) mbar_arrive(sfree);

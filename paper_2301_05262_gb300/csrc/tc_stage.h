@@ -56,7 +56,13 @@ struct TcBatch {
     const float* scale3;        // FP8 form: per-output-channel weight scales of the 3x3
     const float* scale1;        // and of the 1x1
     int* err;                   // device error word
+    // Per-view completion times (batched serving), or null: [0] the batch's
+    // start (%globaltimer, ns, written by the first stage), [1 + v] the time
+    // view v's last output pixel was written (level-0 decoder), [1 + kMaxViews
+    // + v] the completion counter of view v
+    unsigned long long* timing;
 };
+constexpr int kTimingWords = 1 + 2 * kMaxViews;
 
 struct Activations;
 

@@ -137,3 +137,40 @@ def test_batched_with_a_2160p_view_matches_single_view_calls(ctx):
     got = _batched(ctx, w, dfs, outs)
     for df, g in zip(dfs, got):
         np.testing.assert_array_equal(g, run_infer(ctx, w, df, nsm.NSM_BF16).cpu().numpy())
+
+
+@pytest.mark.parametrize("graph", [False, True])
+def test_per_view_completion_records(ctx, graph):
+    """With view timing on, every view of a batch gets a completion time after
+    the batch's start and no later than the batch's end (host wall clock
+    around the synchronised call), the outputs are unchanged, and a second
+    batch overwrites the records."""
+    import time
+    theta = scenegen.he_init_weights(5, N.layer_table(3)).astype(np.float32)
+    w = nsm.Weights(ctx, theta)
+    rec = torch.zeros(65, dtype=torch.int64, device="cuda")
+    nsm.nsm_ctx_set_graph(ctx, graph)
+    try:
+        dfs, outs = _views(SIZES, 60)
+        ref = _batched(ctx, w, dfs, outs)
+        nsm.nsm_ctx_set_view_timing(ctx, rec)
+        first = None
+        for rep in range(2):
+            dfs2, outs2 = _views(SIZES, 60)
+            t0 = time.perf_counter()
+            got = _batched(ctx, w, dfs2, outs2)
+            wall_ns = (time.perf_counter() - t0) * 1e9
+            r = rec.cpu().numpy()
+            lat = r[1:1 + len(SIZES)] - r[0]
+            assert r[0] > 0 and (lat > 0).all(), r
+            assert lat.max() <= wall_ns, (lat.max(), wall_ns)
+            for a, b in zip(got, ref):
+                np.testing.assert_array_equal(a, b)
+            if first is not None:
+                assert r[0] > first
+            first = r[0]
+            # the counters reached each view's unit count exactly once
+            assert (r[1 + 32:1 + 32 + len(SIZES)] > 0).all()
+    finally:
+        nsm.nsm_ctx_set_view_timing(ctx, None)
+        nsm.nsm_ctx_set_graph(ctx, False)
