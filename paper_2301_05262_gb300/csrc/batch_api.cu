@@ -169,7 +169,7 @@ nsm_status nsm_infer_batched(nsm_ctx* c, int n, const nsm_view* views, const nsm
         for (int k = 0; k < kTcStages; ++k) {
             // the tile tables are a pure function of the plan; refill them for the job copy
             TcBatch& bk = b[k];
-            tc_fill_tiles(bk, tc_stage_rows(k, c->tc_variant[k]));
+            if ((e = tc_prepare_stage(k, c->tc_variant[k], bk)) != cudaSuccess) return cuda_fail(e, "stage set-up");
             cudaKernelNodeParams p = c->graph_params[k];
             void* args[1] = {&bk};
             p.kernelParams = args;

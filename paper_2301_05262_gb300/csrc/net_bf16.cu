@@ -63,6 +63,8 @@
 //   a1full    epilogue -> MMA: 1x1 operand written
 //   mma1      MMA -> epilogue: 1x1 done (and its operand free)
 //   tfree[t]  epilogue -> MMA: accumulator buffer t read out
+#include <cudaTypedefs.h>
+
 #include "nsm_internal.h"
 #include "tc_common.cuh"
 #include "tc_stage.h"
@@ -177,6 +179,25 @@ __device__ __forceinline__ void copy_slice(const uint16_t* src, int H, int W, in
             const uint16_t* p = ok ? src + ((static_cast<size_t>(gy) * W + gx) * 2 * CG + chunk) * 8 : src;
             cp_async16(dst + 16 * (row_slot<NRW>(base, sr) * kSW), p, ok ? 16u : 0u);
         }
+    }
+}
+
+// TMA: K slice s of an NHWC tile by tensor copies, one per (plane, staged row):
+// a box of kSW pixels starting at the halo column lands in the row's ring slot
+// (rows 2176 bytes apart, so every destination is 128-byte aligned); the tensor
+// map fills zeros outside the image.  One thread; `bar` receives the bytes.
+template <int CIN, int R, int KS, int NRW>
+__device__ __forceinline__ void tma_slice(const CUtensorMap* map, int y0, int x0, uint32_t a0, int s, int base,
+                                          int first, uint64_t* bar) {
+    constexpr int CG = CIN / 8, CGS = CG / KS, PLN = 2 * CGS;
+    constexpr uint32_t kPlane = NRW * kSW * 16;
+    mbar_arrive_expect_tx(bar, static_cast<uint32_t>(PLN * (R + 2 - first) * kSW * 16));
+#pragma unroll
+    for (int pl = 0; pl < PLN; ++pl) {
+        const int chunk = (pl / CGS) * CG + s * CGS + pl % CGS;
+        for (int sr = first; sr < R + 2; ++sr)
+            tma_load_4d(a0 + pl * kPlane + 16 * (row_slot<NRW>(base, sr) * kSW), map, 0, chunk, x0 - 1, y0 - 1 + sr,
+                        bar);
     }
 }
 
@@ -591,7 +612,7 @@ __global__ void __launch_bounds__(32 * tc_warps(NEW, NPW, EPI), 1) level_tc_kern
     }
     if (tid == 0) {
         for (int k = 0; k < 2; ++k) {
-            mbar_init(full + k, NP);
+            mbar_init(full + k, PRO == TPRO_TMA ? 1 : NP);
             mbar_init(mma3 + k, 1);
             mbar_init(tfree + k, NE);
             mbar_init(gfull + k, NP);
@@ -651,8 +672,9 @@ __global__ void __launch_bounds__(32 * tc_warps(NEW, NPW, EPI), 1) level_tc_kern
     if (warp >= NEW && warp < MW) {
         // ================= producers: step st = (tile it, K slice s) fills input buffer st % 2
         const int pt = tid - NE;
+        constexpr bool RAWP = (PRO == TPRO_GATHER || C::UP);  // raw inputs prefetched by cp.async
         int v = 0, vn = 0, it = 0, ring = 0;
-        if constexpr (PRO != TPRO_PLAIN) {
+        if constexpr (RAWP) {
             // prefetch the first tile's raw inputs into raw buffer 0
             if (t_lo < t_hi) {
                 int y0, x0;
@@ -681,7 +703,7 @@ __global__ void __launch_bounds__(32 * tc_warps(NEW, NPW, EPI), 1) level_tc_kern
             const TcJob& job = locate(tile, v, y0, x0, cont);
             ring_next(cont, ring, base, first);
             const int rb = it & 1;
-            if constexpr (PRO != TPRO_PLAIN) {
+            if constexpr (RAWP) {
                 // prefetch tile it + 1 into the other raw buffer
                 const int next = tile + 1;
                 if (next < t_hi) {
@@ -705,10 +727,13 @@ __global__ void __launch_bounds__(32 * tc_warps(NEW, NPW, EPI), 1) level_tc_kern
                 const int st = it * KS + s, b = st & 1;
                 const uint32_t A0 = C::ONE_RING ? sA0 : sA0 + b * (C::A0_CHUNKS * 16);
                 // the rows written now are free once the MMAs of step st - 2 are done
+                if (PRO == TPRO_TMA && pt != 0) continue;  // one thread issues the tensor copies
                 if (st >= 2 && !wait_phase(mma3 + b, ((st >> 1) - 1) & 1, s_abort)) { failed = true; break; }
                 if constexpr (PRO == TPRO_PLAIN) {
                     copy_slice<NP, CIN, R, KS, C::NRW, PAR>(job.in, job.H, job.W, y0, x0, A0, s, base, first, pt);
                     cp_async_arrive(full + b);
+                } else if constexpr (PRO == TPRO_TMA) {
+                    tma_slice<CIN, R, KS, C::NRW>(&job.tmap, y0, x0, A0, s, base, first, full + b);
                 } else {
                     if constexpr (PRO == TPRO_GATHER)
                         compute_gather<NP, R, C::NRW>(job, y0, x0, raw, A0, base, first, pt);
@@ -720,7 +745,7 @@ __global__ void __launch_bounds__(32 * tc_warps(NEW, NPW, EPI), 1) level_tc_kern
                 }
             }
             if (failed) break;
-            if constexpr (PRO != TPRO_PLAIN) mbar_arrive(rfree + rb);
+            if constexpr (RAWP) mbar_arrive(rfree + rb);
             if constexpr (PAR) {
                 const int k = ring_lo + 2 * (it * NPW + pt / 32);
                 if (k < ring_hi)
@@ -1201,11 +1226,11 @@ static int occupancy_of() {
 // Variant tables: tile height R and warp roles of every stage (the
 // autotuner's search space).
 using LaunchFn = cudaError_t (*)(const TcBatch&, int, cudaStream_t);
-struct Variant { int R, ew, pw, ks, ord; LaunchFn fn; const void* (*func)(); int (*occ)(); };
+struct Variant { int R, ew, pw, ks, ord; LaunchFn fn; const void* (*func)(); int (*occ)(); int tma, cin; };
 #define NSM_VARIANT(R_, EW_, PW_, KS_, ORD_, CIN_, CMID_, COUT_, PRO_, EPI_)                              \
     {R_, EW_, PW_, KS_, ORD_, launch_variant<CIN_, CMID_, COUT_, R_, PRO_, EPI_, EW_, PW_, KS_, ORD_>,      \
      kernel_of<CIN_, CMID_, COUT_, R_, PRO_, EPI_, EW_, PW_, KS_, ORD_>,                                  \
-     occupancy_of<CIN_, CMID_, COUT_, R_, PRO_, EPI_, EW_, PW_, KS_, ORD_>}
+     occupancy_of<CIN_, CMID_, COUT_, R_, PRO_, EPI_, EW_, PW_, KS_, ORD_>, (PRO_) == TPRO_TMA, CIN_}
 // both MMA schedules of one tile shape / warp split
 #define NSM_VARIANT2(R_, EW_, PW_, KS_, CIN_, CMID_, COUT_, PRO_, EPI_)                                   \
     NSM_VARIANT(R_, EW_, PW_, KS_, 0, CIN_, CMID_, COUT_, PRO_, EPI_),                                     \
@@ -1222,11 +1247,15 @@ static const Variant kVarEnc1[] = {
     NSM_VARIANT(2, 4, 8, 1, 0, 16, 32, 32, TPRO_PLAIN, TEPI_SKIP_POOL),
     NSM_VARIANT(2, 8, 8, 1, 0, 16, 32, 32, TPRO_PLAIN, TEPI_SKIP_POOL),
     NSM_VARIANT2(4, 4, 8, 1, 16, 32, 32, TPRO_PLAIN, TEPI_SKIP_POOL),
-    NSM_VARIANT2(4, 8, 8, 1, 16, 32, 32, TPRO_PLAIN, TEPI_SKIP_POOL)};
+    NSM_VARIANT2(4, 8, 8, 1, 16, 32, 32, TPRO_PLAIN, TEPI_SKIP_POOL),
+    NSM_VARIANT2(4, 4, 1, 1, 16, 32, 32, TPRO_TMA, TEPI_SKIP_POOL),
+    NSM_VARIANT2(4, 8, 1, 1, 16, 32, 32, TPRO_TMA, TEPI_SKIP_POOL)};
 static const Variant kVarBott[] = {
     NSM_VARIANT(1, 4, 8, 1, 0, 32, 64, 32, TPRO_PLAIN, TEPI_STORE),
     NSM_VARIANT2(2, 4, 8, 2, 32, 64, 32, TPRO_PLAIN, TEPI_STORE),
-    NSM_VARIANT2(2, 8, 8, 2, 32, 64, 32, TPRO_PLAIN, TEPI_STORE)};
+    NSM_VARIANT2(2, 8, 8, 2, 32, 64, 32, TPRO_PLAIN, TEPI_STORE),
+    NSM_VARIANT2(2, 4, 1, 2, 32, 64, 32, TPRO_TMA, TEPI_STORE),
+    NSM_VARIANT2(2, 8, 1, 2, 32, 64, 32, TPRO_TMA, TEPI_STORE)};
 static const Variant kVarDec1[] = {
     NSM_VARIANT2(2, 4, 8, 2, 32, 32, 16, TPRO_UP_SKIP, TEPI_STORE_PAIR),
     NSM_VARIANT2(2, 8, 8, 2, 32, 32, 16, TPRO_UP_SKIP, TEPI_STORE_PAIR),
@@ -1261,7 +1290,7 @@ int tc_stage_warps(int stage, int variant, int* producer_warps) {
 
 int tc_default_variant(int stage) {
     // the fastest plan of the 1080p autotuning runs
-    static const int def[kTcStages] = {2, 5, 4, 4, 5};
+    static const int def[kTcStages] = {2, 8, 6, 4, 5};
     return def[stage];
 }
 
@@ -1276,11 +1305,46 @@ void tc_fill_tiles(TcBatch& b, int rows) {
     }
 }
 
-cudaError_t tc_launch_stage(int stage, int variant, TcBatch& b, int ctas_per_sm, cudaStream_t stream) {
+cudaError_t tc_encode_input_map(CUtensorMap* map, const uint16_t* in, int H, int W, int cin) {
+    // cuTensorMapEncodeTiled, resolved through the runtime (the library does not link the driver library)
+    static const PFN_cuTensorMapEncodeTiled_v12000 encode = [] {
+        void* fn = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+        return (e == cudaSuccess && q == cudaDriverEntryPointSuccess) ? reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn)
+                                                                     : nullptr;
+    }();
+    if (!encode) return cudaErrorNotSupported;
+    const cuuint64_t nch = 2 * cin / 8;  // 16-byte chunks per pixel: [part][channel group]
+    const cuuint64_t dims[4] = {8, nch, static_cast<cuuint64_t>(W), static_cast<cuuint64_t>(H)};
+    const cuuint64_t strides[3] = {16, nch * 16, static_cast<cuuint64_t>(W) * nch * 16};
+    const cuuint32_t box[4] = {8, 1, kSW, 1};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    const CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_UINT16, 4, const_cast<uint16_t*>(in), dims, strides, box, estr,
+                              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+cudaError_t tc_prepare_stage(int stage, int variant, TcBatch& b) {
     if (stage < 0 || stage >= kTcStages || variant < 0 || variant >= kStages[stage].n) return cudaErrorInvalidValue;
     const Variant& v = kStages[stage].v[variant];
     tc_fill_tiles(b, v.R);
-    return v.fn(b, ctas_per_sm, stream);
+    if (v.tma)
+        for (int i = 0; i < b.nviews; ++i) {
+            TcJob& j = b.job[i];
+            if (j.H > 0 && j.W > 0) {
+                cudaError_t e = tc_encode_input_map(&j.tmap, j.in, j.H, j.W, v.cin);
+                if (e != cudaSuccess) return e;
+            }
+        }
+    return cudaSuccess;
+}
+
+cudaError_t tc_launch_stage(int stage, int variant, TcBatch& b, int ctas_per_sm, cudaStream_t stream) {
+    cudaError_t e = tc_prepare_stage(stage, variant, b);
+    if (e != cudaSuccess) return e;
+    return kStages[stage].v[variant].fn(b, ctas_per_sm, stream);
 }
 
 const char* const kInferKernelNamesBf16[kInferKernelsBf16] = {

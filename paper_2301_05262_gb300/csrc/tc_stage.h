@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cstdint>
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include "nsm_common.cuh"
@@ -12,7 +13,8 @@ namespace nsm {
 constexpr int kMaxViews = 32;
 constexpr int kTcStages = 5;  // enc0 (+ gather), enc1, bottleneck, dec1, dec0 (+ head)
 
-enum TcPro { TPRO_GATHER = 0, TPRO_PLAIN = 1, TPRO_UP_SKIP = 2, TPRO_UP = 3 };
+// TMA: as PLAIN, the rows staged by tensor-memory-access copies (one thread)
+enum TcPro { TPRO_GATHER = 0, TPRO_PLAIN = 1, TPRO_UP_SKIP = 2, TPRO_UP = 3, TPRO_TMA = 4 };
 // STORE_PAIR: like STORE, as BF16 hi + lo pairs [H][W][2][COUT];
 // HEAD_PAR: the level-0 decoder on the coarse grid (four output parities per
 // coarse pixel, 1x1 per parity, head, sigmoid; fine visibility [2H][2W])
@@ -39,6 +41,9 @@ struct TcJob {
     uint8_t* out8;              // POOL / SKIP_POOL: pooled [H/2][W/2][COUT]; STORE: [H][W][COUT]
     uint8_t* out_skip8;         // SKIP_POOL: [H][W][COUT]
     float* vis;                 // HEAD: [H][W]; HEAD_PAR: [2H][2W]; HEAD4 writes out_f [H][W][4]
+    // TMA prologue: tensor map of `in` as [H][W][2 CIN / 8 chunks][8 BF16],
+    // box = one 16-byte chunk plane of kSW pixels of one row (zero fill outside)
+    alignas(64) CUtensorMap tmap;
 };
 
 // Kernel parameter of a stage launch (passed by value, __grid_constant__).
@@ -79,5 +84,9 @@ void tc_make_batches(const GatherParams* g, const Activations* act, float* const
                      const uint16_t* img, int* err, TcBatch* out);
 cudaError_t tc_launch_stage(int stage, int variant, TcBatch& b, int ctas_per_sm, cudaStream_t stream);
 void tc_fill_tiles(TcBatch& b, int rows);  // tile counts of every view for tile height rows
+// Tile table (and, for TMA variants, the views' tensor maps) of a stage's batch
+cudaError_t tc_prepare_stage(int stage, int variant, TcBatch& b);
+// Tensor map of a PLAIN stage input ([H][W][2][cin] BF16) for the TMA prologue
+cudaError_t tc_encode_input_map(CUtensorMap* map, const uint16_t* in, int H, int W, int cin);
 
 }  // namespace nsm
