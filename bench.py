@@ -371,6 +371,22 @@ def extra_train(nsm, scenegen, torch, device, theta, reps):
     torch.cuda.synchronize()
     ctx.check()
     ms = sum(ev[2 * k].elapsed_time(ev[2 * k + 1]) for k in range(reps)) / reps
+    loss_fp = float(loss.item())
+    # the same steps with the detached instances x_1, x_2 on the BF16 tensor-core stages
+    state_bf = nsm.TrainState(ctx, theta, B, T, S, S)
+    state_bf.set_detached_precision(nsm.NSM_BF16)
+    for _ in range(3):
+        state_bf.step(batch, loss_out=loss)
+    ev2 = _events(torch, 2 * reps)
+    for k in range(reps):
+        ev2[2 * k].record()
+        state_bf.step(batch, loss_out=loss)
+        ev2[2 * k + 1].record()
+    torch.cuda.synchronize()
+    ctx.check()
+    ms_bf = sum(ev2[2 * k].elapsed_time(ev2[2 * k + 1]) for k in range(reps)) / reps
+    loss_bf = float(loss.item())
+    state_bf.close()
     # algorithmic work: forward of all B T instances, and for the B target
     # instances the recomputed forward, the weight gradients and the data
     # gradients (none for the input features): MACs per full-resolution pixel
@@ -380,7 +396,10 @@ def extra_train(nsm, scenegen, torch, device, theta, reps):
     sms = torch.cuda.get_device_properties(device).multi_processor_count
     peak = fp32_alu_peak_tflops(sms, load_peaks()["sm_max_mhz"])
     tflops = flop / (ms * 1e-3) / 1e12
-    return {"ms_per_step": ms, "instances_per_s": B * T / (ms * 1e-3), "loss_last": float(loss.item()),
+    return {"ms_per_step": ms, "instances_per_s": B * T / (ms * 1e-3), "loss_last": loss_fp,
+            "bf16_detached": {"ms_per_step": ms_bf, "instances_per_s": B * T / (ms_bf * 1e-3), "loss_last": loss_bf,
+                              "form": "x_1, x_2 (gradient stopped, Eq. 2) on the compensated-BF16 tcgen05 stage "
+                                      "kernels, 32 instances per launch; x_0 and the backward FP32"},
             "algorithmic_gflop": flop / 1e9, "achieved_tflops": tflops,
             "roofline": {"bound": "alu", "peak_tflops": peak, "frac": tflops / peak,
                          "peak_src": "128 FP32 lanes x 2 FLOP x SMs x max SM clock"},

@@ -370,6 +370,20 @@ nsm_status nsm_train_apply(nsm_ctx* ctx, nsm_train_state* st, const nsm_train_cf
 nsm_status nsm_train_state_read(nsm_train_state* st, int what, float* dev_out, size_t n, void* stream);
 nsm_status nsm_train_state_write(nsm_train_state* st, int what, const float* dev_in, size_t n, void* stream);
 
+/* Form of the forward passes of the detached instances x_1 .. x_{T-1} of
+ * Eq. 2 (Sec. 3.3: their outputs enter the loss with the gradient stopped, so
+ * they are pure inference): NSM_FP32 (default; the FP32 training kernels) or
+ * NSM_BF16 (the compensated-BF16 tcgen05 stage kernels of nsm_infer, up to 32
+ * instances per launch, with BF16 images of the master weights packed on the
+ * device at every step).  x_0 and the whole backward stay FP32.  Other
+ * precisions: NSM_ERR_UNSUPPORTED. */
+nsm_status nsm_train_state_set_detached_precision(nsm_train_state* st, nsm_precision precision);
+
+/* The visibility of every instance of the last nsm_train_grad / nsm_train_step
+ * call on this state, [T][B][H][W] floats (n = B T H W) into device memory:
+ * x_0 of every item, then the detached instances.  Asynchronous on stream. */
+nsm_status nsm_train_state_read_vis(nsm_train_state* st, float* dev_out, size_t n, void* stream);
+
 /* ---------------------------------------------------------------- scene generation (GPU ray casting) */
 
 /* Training data as the method uses it (Sec. 3.1: a G-buffer and shadow-map

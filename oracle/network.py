@@ -629,20 +629,24 @@ def adam_update(theta, grad, m, v, step, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e
     return theta, m, v
 
 
-def train_step(batch_feats, targets, theta, m, v, step, lr=1e-3, alpha=0.9, levels=3):
+def train_step(batch_feats, targets, theta, m, v, step, lr=1e-3, alpha=0.9, levels=3, detached_forward=None):
     """One temporal-window training step (Sec. 3.3, Eq. 2).
 
     batch_feats: list over batch items of lists over window instances of
     features (4, H, W); instance 0 carries the target and the gradient, the
     others are evaluated without gradient.  The per-item losses are averaged
-    over the batch.  Returns (theta, m, v, loss, grad)."""
+    over the batch.  detached_forward(features, theta) evaluates the
+    instances without gradient (default: `forward`; a reduced-precision
+    form's rounding model, e.g. `forward_rounded`, for a form that runs them
+    at lower precision).  Returns (theta, m, v, loss, grad)."""
     B = len(batch_feats)
     grad = np.zeros_like(np.asarray(theta, np.float64))
     total = 0.0
+    fwd_detached = detached_forward if detached_forward is not None else (lambda f, th: forward(f, th, levels))
     for b in range(B):
         insts = batch_feats[b]
         x0, t = forward(insts[0], theta, levels, keep=True)
-        xs = [forward(f, theta, levels) for f in insts[1:]]
+        xs = [fwd_detached(f, theta) for f in insts[1:]]
         loss, g = loss_l1(x0, targets[b], xs, alpha)
         total += loss / B
         dth, _ = backward(g / B, theta, t, levels)

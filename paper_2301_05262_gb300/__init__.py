@@ -318,6 +318,8 @@ def _train_sigs():
         "nsm_train_state_write": ([P, I, P, Z, P], I),
         "nsm_train_grad": ([P, P, ctypes.POINTER(nsm_batch), ctypes.POINTER(nsm_train_cfg), P, P], I),
         "nsm_train_apply": ([P, P, ctypes.POINTER(nsm_train_cfg), P], I),
+        "nsm_train_state_set_detached_precision": ([P, I], I),
+        "nsm_train_state_read_vis": ([P, P, Z, P], I),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -375,6 +377,16 @@ class TrainState:
     def write(self, what: int, src, stream=None):
         _check(_train_sigs().nsm_train_state_write(self.h, what, _ptr(src), self.n, _stream(stream)),
                "nsm_train_state_write")
+
+    def set_detached_precision(self, precision: int):
+        """Form of the detached instances' forward (NSM_FP32 or NSM_BF16)."""
+        _check(_train_sigs().nsm_train_state_set_detached_precision(self.h, precision),
+               "nsm_train_state_set_detached_precision")
+
+    def read_vis(self, out, stream=None):
+        """Visibility [T][B][H][W] of the last step's instances into a device tensor."""
+        _check(_train_sigs().nsm_train_state_read_vis(self.h, _ptr(out), int(out.numel()), _stream(stream)),
+               "nsm_train_state_read_vis")
 
     def close(self):
         if self.h:

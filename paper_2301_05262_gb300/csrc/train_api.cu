@@ -3,6 +3,8 @@
 
 #include "nsm_internal.h"
 #include "train_internal.h"
+#include "ctx_internal.h"
+#include "tc_stage.h"
 
 struct nsm_train_state {
     int device;
@@ -16,6 +18,14 @@ struct nsm_train_state {
     nsm::GatherParams* gp;  // per-instance gather parameters (device)
     float* work;         // FP32 workspace
     int step;
+    // Forward of the detached instances x_i (i >= 1) of Eq. 2: NSM_FP32 (the
+    // checkpointed FP32 kernels, default) or NSM_BF16 (the tensor-core stage
+    // kernels, BF16 images of the master weights packed every step)
+    int detached_precision;
+    uint16_t* bf16;      // packed BF16 weight images
+    void* descs;         // their packing table (device)
+    int ndesc;
+    int last_N;          // instances of the last nsm_train_grad call
 };
 
 namespace nsm {
@@ -90,6 +100,12 @@ nsm_status nsm_train_state_create(nsm_ctx* ctx, const float* host_params, size_t
     alloc(reinterpret_cast<void**>(&s->loss), 256);
     alloc(reinterpret_cast<void**>(&s->gp), sizeof(GatherParams) * N);
     alloc(reinterpret_cast<void**>(&s->work), tr::workspace_floats(N, max_B, H, W) * 4);
+    const BF16Images im = bf16_images();
+    s->ndesc = im.n;
+    alloc(reinterpret_cast<void**>(&s->bf16), im.total * sizeof(uint16_t));
+    alloc(&s->descs, pack_desc_bytes() * im.n);
+    if (e == cudaSuccess) e = cudaMemcpy(s->descs, im.desc, pack_desc_bytes() * im.n, cudaMemcpyHostToDevice);
+    s->detached_precision = NSM_FP32;
     if (e == cudaSuccess) e = cudaMemcpy(s->theta, host_params, n * 4, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(s->m, 0, n * 4);
     if (e == cudaSuccess) e = cudaMemset(s->v, 0, n * 4);
@@ -106,6 +122,7 @@ void nsm_train_state_destroy(nsm_train_state* s) {
     if (!s) return;
     cudaFree(s->theta); cudaFree(s->m); cudaFree(s->v); cudaFree(s->grad);
     cudaFree(s->loss); cudaFree(s->gp); cudaFree(s->work);
+    cudaFree(s->bf16); cudaFree(s->descs);
     delete s;
 }
 
@@ -148,8 +165,39 @@ nsm_status nsm_train_grad(nsm_ctx* ctx, nsm_train_state* s, const nsm_batch* bt,
     cudaError_t e = cudaMemcpyAsync(s->gp, gps.data(), sizeof(GatherParams) * N, cudaMemcpyHostToDevice, cs);
     if (e != cudaSuccess) return cuda_fail(e, "upload gather parameters");
     tr::Buffers b = tr::carve(s->work, N, bt->B, H, W);
-    if ((e = tr::features_batch(s->gp, N, H, W, b.feat, cs)) != cudaSuccess) return cuda_fail(e, "features");
-    if ((e = tr::forward(s->theta, b, N, bt->B, H, W, cs)) != cudaSuccess) return cuda_fail(e, "forward");
+    s->last_N = N;
+    if (s->detached_precision == NSM_BF16 && bt->T > 1) {
+        // x_0 (instances 0 .. B-1): FP32 with the checkpoints the backward needs
+        if ((e = tr::features_batch(s->gp, bt->B, H, W, b.feat, cs)) != cudaSuccess) return cuda_fail(e, "features");
+        if ((e = tr::forward(s->theta, b, bt->B, bt->B, H, W, cs)) != cudaSuccess) return cuda_fail(e, "forward");
+        // the detached x_i: inference only, on the tensor-core stage kernels (gather fused
+        // into the first stage), their activations in the instances' checkpoint slots
+        if ((e = launch_pack_bf16(s->theta, s->bf16, s->descs, s->ndesc, cs)) != cudaSuccess)
+            return cuda_fail(e, "pack BF16 weights");
+        const size_t p1 = npx / 4, p2 = npx / 16;
+        for (int i0 = bt->B; i0 < N; i0 += kMaxViews) {
+            const int n = (N - i0) < kMaxViews ? (N - i0) : kMaxViews;
+            std::vector<Activations> act(n);
+            std::vector<float*> vis(n);
+            for (int k = 0; k < n; ++k) {
+                const size_t i = static_cast<size_t>(i0 + k);
+                act[k].e0 = b.e0 + i * p1 * 16;
+                act[k].s1 = b.s1 + i * p1 * 32;
+                act[k].p1 = b.p1 + i * p2 * 32;
+                act[k].bo = b.bo + i * p2 * 32;
+                act[k].d1 = b.d1 + i * p1 * 16;
+                vis[k] = b.vis + i * npx;
+            }
+            TcBatch tb[kTcStages];
+            tc_make_batches(gps.data() + i0, act.data(), vis.data(), n, s->theta, s->bf16, ctx->d_err, tb);
+            for (int k = 0; k < kTcStages; ++k)
+                if ((e = tc_launch_stage(k, ctx->tc_variant[k], tb[k], ctx->tc_ctas[k], cs)) != cudaSuccess)
+                    return cuda_fail(e, "detached forward (tensor-core stages)");
+        }
+    } else {
+        if ((e = tr::features_batch(s->gp, N, H, W, b.feat, cs)) != cudaSuccess) return cuda_fail(e, "features");
+        if ((e = tr::forward(s->theta, b, N, bt->B, H, W, cs)) != cudaSuccess) return cuda_fail(e, "forward");
+    }
     if ((e = cudaMemsetAsync(s->loss, 0, sizeof(float), cs)) != cudaSuccess) return cuda_fail(e, "loss reset");
     if ((e = tr::loss_l1(b.vis, bt->target, bt->B, bt->T, npx, cfg->alpha, b.gvis, s->loss, cs)) != cudaSuccess)
         return cuda_fail(e, "loss");
@@ -184,6 +232,26 @@ nsm_status nsm_train_state_write(nsm_train_state* s, int what, const float* dev_
     if (!dst) return fail(NSM_ERR_INVALID_ARG, "unknown state vector %d", what);
     cudaError_t e = cudaMemcpyAsync(dst, dev_in, n * 4, cudaMemcpyDeviceToDevice, static_cast<cudaStream_t>(stream));
     return e == cudaSuccess ? NSM_OK : cuda_fail(e, "copy state");
+}
+
+nsm_status nsm_train_state_set_detached_precision(nsm_train_state* s, nsm_precision precision) {
+    if (!s) return fail(NSM_ERR_INVALID_ARG, "state is NULL");
+    if (precision != NSM_FP32 && precision != NSM_BF16)
+        return fail(NSM_ERR_UNSUPPORTED, "the detached instances run in the FP32 or the BF16 form");
+    s->detached_precision = precision;
+    return NSM_OK;
+}
+
+nsm_status nsm_train_state_read_vis(nsm_train_state* s, float* dev_out, size_t n, void* stream) {
+    if (!s) return fail(NSM_ERR_INVALID_ARG, "state is NULL");
+    const size_t npx = static_cast<size_t>(s->H) * s->W;
+    if (s->last_N < 1) return fail(NSM_ERR_INVALID_ARG, "no training step has run on this state");
+    if (n != s->last_N * npx) return fail(NSM_ERR_SHAPE, "%zu floats requested, the last step has %zu", n, s->last_N * npx);
+    nsm_status st = check_dev_ptr(dev_out, "dev_out", 4);
+    if (st != NSM_OK) return st;
+    const tr::Buffers b = tr::carve(s->work, s->last_N, s->max_B, s->H, s->W);
+    cudaError_t e = cudaMemcpyAsync(dev_out, b.vis, n * 4, cudaMemcpyDeviceToDevice, static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? NSM_OK : cuda_fail(e, "copy visibility");
 }
 
 nsm_status nsm_train_state_read(nsm_train_state* s, int what, float* dev_out, size_t n, void* stream) {

@@ -130,7 +130,7 @@ def test_autograd_function_matches_oracle(ctx):
     assert np.abs(got - ref_g).max() <= 2e-4 * np.abs(ref_g).max()
 
 
-def _near_tie_split(feats, targets, theta, alpha, tau=1e-5):
+def _near_tie_split(feats, targets, theta, alpha, tau=1e-5, detached=None):
     """The Eq. 2 gradient split at the kink of |u| at 0.  Where |x0 - x_i| (or
     |x0 - target|) is below tau an FP32 evaluation may take either sign of the
     L1 term (or 0 at an exact tie), so the FP64 gradient with those terms left
@@ -142,7 +142,8 @@ def _near_tie_split(feats, targets, theta, alpha, tau=1e-5):
     cols = []
     for b in range(B):
         x0, t = N.forward(feats[b][0], theta, keep=True)
-        others = [np.asarray(targets[b], np.float64)] + [N.forward(f, theta) for f in feats[b][1:]]
+        fwd = detached if detached is not None else N.forward
+        others = [np.asarray(targets[b], np.float64)] + [fwd(f, theta) for f in feats[b][1:]]
         n = x0.size
         cot = np.zeros_like(x0)
         for o in others:
@@ -265,3 +266,62 @@ def test_grad_apply_and_data_parallel_trainer_match_train_step(ctx):
     d.read(0, w)
     torch.cuda.synchronize()
     np.testing.assert_allclose(w.cpu().numpy() - theta, -1e-3 * gh.cpu().numpy(), rtol=1e-4, atol=1e-7)
+
+
+def test_train_step_with_bf16_detached_instances(ctx):
+    """The detached instances x_1, x_2 of Eq. 2 on the BF16 tensor-core stage
+    kernels: their visibilities follow the BF16 form's rounding model (and lie
+    within 1e-2 of FP64), x_0 stays FP32, and the loss, gradient and Adam step
+    match the oracle's step with that rounding model as the detached forward."""
+    B, T, H, W, S = 2, 3, 32, 32, 128
+    frames, targets = train_batch_frames(B, T, H, W, S, seed=41)
+    theta = _theta(8)
+    st = nsm.TrainState(ctx, theta, B, T, H, W)
+    st.set_detached_precision(nsm.NSM_BF16)
+    bt = device_batch(frames, targets)
+    loss = torch.zeros(1, device="cuda")
+    lr = 1e-3
+    st.step(bt, lr=lr, alpha=0.9, loss_out=loss)
+    vis = torch.empty(T * B * H * W, device="cuda")
+    st.read_vis(vis)
+    out = {k: torch.empty(theta.size, device="cuda") for k in (0, 1)}
+    for k, v in out.items():
+        st.read(k, v)
+    torch.cuda.synchronize()
+    v = vis.cpu().numpy().astype(np.float64).reshape(T, B, H, W)
+    th64 = theta.astype(np.float64)
+    model = lambda f, th: N.forward_rounded(f, th, N.round_bf16_pair, rnd_in=N.round_bf16_pair, coarse_dec0=True)
+    feats = []
+    for b in range(B):
+        insts = []
+        for t in range(T):
+            fr = frames[t][b]
+            insts.append(G.features(fr.pos4, fr.nrm4, fr.sm, fr.view_proj, fr.light_pos, fr.cam_pos, fr.r_hat,
+                                    fr.z_far, fr.bias)[0])
+        feats.append(insts)
+        assert np.abs(v[0, b] - N.forward(insts[0], th64)).max() <= 1e-4          # x_0: FP32
+        for t in range(1, T):
+            q = model(insts[t], th64)
+            assert float(np.mean((v[t, b] - q) ** 2)) <= 1e-8
+            assert np.abs(v[t, b] - q).max() <= 1e-3
+            assert np.abs(v[t, b] - N.forward(insts[t], th64)).max() <= 1e-2
+    th2, _, _, ref_loss, ref_grad = N.train_step(feats, [targets[b].astype(np.float64) for b in range(B)], th64,
+                                                 np.zeros_like(th64), np.zeros_like(th64), 1, lr=lr, alpha=0.9,
+                                                 detached_forward=model)
+    assert float(loss.item()) == pytest.approx(ref_loss, rel=1e-4)
+    grad = out[1].cpu().numpy().astype(np.float64)
+    g_rest, Ct = _near_tie_split(feats, [targets[b] for b in range(B)], th64, alpha=0.9, detached=model)
+    n_terms = B * T * H * W
+    print(f"near-tie L1 terms: {Ct.shape[1]} of {n_terms}")
+    assert Ct.shape[1] <= 0.01 * n_terms
+    even = np.arange(th64.size) % 2 == 0
+    sgn = np.linalg.lstsq(Ct[even], (grad - g_rest)[even], rcond=None)[0] if Ct.shape[1] else np.zeros(0)
+    assert np.all(np.abs(sgn) <= 1.05), sgn
+    fit = g_rest + Ct @ sgn
+    for name, sl in _layer_slices():
+        scale = max(np.abs(ref_grad[sl]).max(), 1e-12)
+        assert np.abs(grad[sl] - fit[sl]).max() <= 2e-3 * scale, name
+    new = out[0].cpu().numpy().astype(np.float64)
+    big = (np.abs(ref_grad) > 1e-3 * np.abs(ref_grad).max()) & (np.abs(ref_grad) > 2.0 * np.abs(Ct).sum(axis=1))
+    np.testing.assert_allclose((new - th64)[big], (th2 - th64)[big], rtol=1e-3, atol=1e-7)
+    st.close()
