@@ -466,13 +466,20 @@ __host__ __device__ inline int ring_pixels(int Hf, int Wf) {
     return (Hf <= 0 || Wf <= 0) ? 0 : (Hf <= 2 ? Hf * Wf : 2 * Wf + 2 * (Hf - 2));
 }
 
-// ring pixel `item` of the batch -> view, fine row and column (false past the end)
-__device__ __forceinline__ bool ring_locate(const TcBatch& a, int item, int& v, int& fy, int& fx) {
-    for (v = 0; v < a.nviews; ++v) {
+// ring pixel `item` of the batch -> view, fine row and column (false past the
+// end); vh / vbase: a view at or before the item's and the number of ring pixels
+// of the views before it (a search hint carried between calls; 0, 0 = none)
+__device__ __forceinline__ bool ring_locate(const TcBatch& a, int item, int& v, int& fy, int& fx, int& vh,
+                                            int& vbase) {
+    if (item < vbase) vh = vbase = 0;
+    item -= vbase;
+    for (v = vh; v < a.nviews; ++v) {
         const int n = ring_pixels(2 * a.job[v].H, 2 * a.job[v].W);
         if (item < n) break;
         item -= n;
+        vbase += n;
     }
+    vh = v;
     if (v >= a.nviews) return false;
     const int Hf = 2 * a.job[v].H, Wf = 2 * a.job[v].W;
     if (Hf <= 2) { fy = item / Wf; fx = item % Wf; }
@@ -505,32 +512,40 @@ __device__ __forceinline__ unsigned view_units(const TcBatch& a, int v, int new_
 // Two ring pixels per warp pass, items `item` and `item + 1` (below n_end):
 // half-warp h takes item + h, lane o of it output channel o.  FP32 weights in
 // shared memory: w3s [tap][c][o], w1s [c][o]; b3 / b1 biases; hs the head
-// weights then its bias; us a per-warp scratch of 2 x 9 x 16 floats (C = 16).
+// weights then its bias; us a per-warp scratch of 2 x 9 x 16 floats (C = 16);
+// vh / vbase the view-search hint of ring_locate.
 __device__ __forceinline__ void ring_pair(const TcBatch& a, int item, int n_end, const float* w3s, const float* w1s,
                                           const float* b3, const float* b1, const float* hs, float* us, int lane,
-                                          int new_warps) {
+                                          int new_warps, int& vh, int& vbase) {
     constexpr int C = 16;
     const int h = lane >> 4, o = lane & 15;
     int v = 0, fy = 0, fx = 0;
-    const bool live = item + h < n_end && ring_locate(a, item + h, v, fy, fx);
-    // channel o of the up-sampled input at the pixel's nine taps (0 outside the image)
+    const bool live = item + h < n_end && ring_locate(a, item + h, v, fy, fx, vh, vbase);
+    // channel o of the up-sampled input at the pixel's nine taps (0 outside the image),
+    // from the (at most 3 x 3) coarse pixels those taps read, each loaded once
     float u[9];
 #pragma unroll
     for (int tap = 0; tap < 9; ++tap) u[tap] = 0.f;
     if (live) {
         const TcJob& job = a.job[v];
         const int Hl = job.H, Wl = job.W;
+        const int cy0 = max(0, min(Hl - 1, (fy - 2) >> 1)), cx0 = max(0, min(Wl - 1, (fx - 2) >> 1));
+        float pc[3][3];
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                const int ci = min(Hl - 1, cy0 + r), cj = min(Wl - 1, cx0 + q);
+                const uint16_t* p = job.in + (static_cast<size_t>(ci) * Wl + cj) * 2 * C + o;
+                pc[r][q] = __bfloat162float(__ushort_as_bfloat16(p[0])) + __bfloat162float(__ushort_as_bfloat16(p[C]));
+            }
 #pragma unroll
         for (int tap = 0; tap < 9; ++tap) {
             const int y = fy + tap / 3 - 1, x = fx + tap % 3 - 1;
             if (y >= 0 && y < 2 * Hl && x >= 0 && x < 2 * Wl) {
                 const BilinTap ty = bilin_tap(y, Hl), tx = bilin_tap(x, Wl);
-                auto px = [&](int ci, int cj) {
-                    const uint16_t* p = job.in + (static_cast<size_t>(ci) * Wl + cj) * 2 * C + o;
-                    return __bfloat162float(__ushort_as_bfloat16(p[0])) + __bfloat162float(__ushort_as_bfloat16(p[C]));
-                };
-                u[tap] = ty.w0 * (tx.w0 * px(ty.i0, tx.i0) + tx.w1 * px(ty.i0, tx.i1)) +
-                         ty.w1 * (tx.w0 * px(ty.i1, tx.i0) + tx.w1 * px(ty.i1, tx.i1));
+                const int r0 = ty.i0 - cy0, r1 = ty.i1 - cy0, q0 = tx.i0 - cx0, q1 = tx.i1 - cx0;
+                u[tap] = ty.w0 * (tx.w0 * pc[r0][q0] + tx.w1 * pc[r0][q1]) + ty.w1 * (tx.w0 * pc[r1][q0] + tx.w1 * pc[r1][q1]);
             }
         }
     }
@@ -688,7 +703,7 @@ __global__ void __launch_bounds__(32 * tc_warps(NEW, NPW, EPI), 1) level_tc_kern
         bool failed = false;
         // PAR: this CTA's share [ring_lo, ring_hi) of the batch's border-ring
         // pixels; producer warp w takes pairs w, w + NPW, ... one per tile
-        int ring_lo = 0, ring_hi = 0;
+        int ring_lo = 0, ring_hi = 0, ring_vh = 0, ring_vb = 0;
         float* ring_us = ringw + 10 * COUT * COUT + (pt / 32) * 2 * 9 * COUT;
         if constexpr (PAR) {
             static_assert(NPW <= 8, "ring scratch per producer warp");
@@ -750,13 +765,13 @@ __global__ void __launch_bounds__(32 * tc_warps(NEW, NPW, EPI), 1) level_tc_kern
                 const int k = ring_lo + 2 * (it * NPW + pt / 32);
                 if (k < ring_hi)
                     ring_pair(a, k, ring_hi, ringw, ringw + 9 * COUT * COUT, bias3_s, bias1_s, head_s, ring_us, tid & 31,
-                              NEW);
+                              NEW, ring_vh, ring_vb);
             }
         }
         if constexpr (PAR) {
             for (int k = ring_lo + 2 * (it * NPW + pt / 32); !failed && k < ring_hi; k += 2 * NPW)
                 ring_pair(a, k, ring_hi, ringw, ringw + 9 * COUT * COUT, bias3_s, bias1_s, head_s, ring_us, tid & 31,
-                          NEW);
+                          NEW, ring_vh, ring_vb);
         }
         if (failed) {
             atomicExch(a.err, 3);
