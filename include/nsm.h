@@ -234,6 +234,21 @@ nsm_status nsm_infer_host_sequence(nsm_ctx* ctx, int n, const nsm_frame* frames,
                                    void* workspace, size_t workspace_bytes, float* const* vis_host,
                                    void* stream);
 
+/* Rows [y0, y1) of a frame's visibility, computed from the slab of rows
+ * [y0 - halo, y1 + halo) clipped to the frame: the unit of a single frame
+ * split across GPUs (each device takes a band of rows and recomputes its halo
+ * locally; no exchange).  The network's receptive field reaches fewer than 16
+ * rows, so with halo >= 16 the rows equal those of nsm_infer on the whole frame
+ * bit for bit in every form (the stage kernels' per-pixel arithmetic does not
+ * depend on where a tile starts); smaller halos give an approximation near the
+ * band edges.  y0, y1, halo multiples of 4 (the pooling grid), 0 <= y0 < y1 <= H;
+ * otherwise NSM_ERR_SHAPE.  frame as for nsm_infer (the whole frame's buffers);
+ * vis_rows device, (y1 - y0) * W floats; workspace >=
+ * nsm_infer_rows_workspace_bytes(...), 256-byte aligned.  Asynchronous on stream. */
+size_t nsm_infer_rows_workspace_bytes(int H, int W, int y0, int y1, int halo, nsm_precision precision);
+nsm_status nsm_infer_rows(nsm_ctx* ctx, const nsm_frame* frame, const nsm_weights* w, nsm_precision precision, int y0,
+                          int y1, int halo, void* workspace, size_t workspace_bytes, float* vis_rows, void* stream);
+
 /* ---------------------------------------------------------------- batched serving */
 
 /* One view of a batch: its inputs (as for nsm_infer) and its output. */

@@ -89,6 +89,8 @@ def lib():
             "nsm_infer_host": ([P, FP, P, I, P, Z, P, Z, P, P], I),
             "nsm_infer_host_sequence": ([P, I, FP, P, I, P, Z, P, Z, P, P], I),
             "nsm_infer_fp32_static": ([FP, P, P, P], I),
+            "nsm_infer_rows_workspace_bytes": ([I, I, I, I, I, I], Z),
+            "nsm_infer_rows": ([P, FP, P, I, I, I, I, P, Z, P, P], I),
         }
         for name, (args, res) in sig.items():
             fn = getattr(L, name)
@@ -282,6 +284,27 @@ def nsm_infer_host_sequence(ctx: Context, host_frames, weights: Weights, precisi
                                          int(workspace.numel() * workspace.element_size()),
                                          ctypes.cast(outs, ctypes.c_void_p), _stream(stream)),
            "nsm_infer_host_sequence")
+
+
+def nsm_infer_rows_workspace_bytes(H: int, W: int, y0: int, y1: int, halo: int, precision: int) -> int:
+    return int(lib().nsm_infer_rows_workspace_bytes(H, W, y0, y1, halo, precision))
+
+
+def nsm_infer_rows(ctx: Context, frame: nsm_frame, weights: Weights, precision: int, y0: int, y1: int, halo: int,
+                   workspace, vis_rows, stream=None):
+    """Rows [y0, y1) of the frame's visibility from a slab with `halo` rows of context."""
+    _check(lib().nsm_infer_rows(ctx.h, ctypes.byref(frame), weights.h, precision, y0, y1, halo, _ptr(workspace),
+                                int(workspace.numel() * workspace.element_size()), _ptr(vis_rows), _stream(stream)),
+           "nsm_infer_rows")
+
+
+def frame_rows(H: int, rank: int, world: int):
+    """The band of rows [y0, y1) of an H-row frame that `rank` of `world` devices
+    computes when one frame is split across them: contiguous bands, bounds on
+    the 4-row pooling grid, sizes within 4 rows of each other (empty bands when
+    H / 4 < world)."""
+    q = H // 4
+    return 4 * (q * rank // world), 4 * (q * (rank + 1) // world)
 
 
 def nsm_infer_fp32_static(frame: nsm_frame, dev_params, vis_out, stream=None):

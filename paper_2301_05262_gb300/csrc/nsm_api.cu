@@ -478,6 +478,50 @@ nsm_status infer_impl(nsm_ctx* ctx, const nsm_frame* frame, const nsm_weights* w
 
 extern "C" {
 
+// Row slab of a frame: rows [y0, y1) computed from the sub-frame [sy0, sy1) =
+// [y0 - halo, y1 + halo] clipped to the frame (every bound a multiple of 4,
+// so the pooling grids of the slab and the frame coincide).
+static void slab_bounds(int H, int y0, int y1, int halo, int* sy0, int* sy1) {
+    *sy0 = y0 - halo < 0 ? 0 : y0 - halo;
+    *sy1 = y1 + halo > H ? H : y1 + halo;
+}
+
+size_t nsm_infer_rows_workspace_bytes(int H, int W, int y0, int y1, int halo, nsm_precision precision) {
+    if (H <= 0 || W <= 0 || y0 < 0 || y1 > H || y0 >= y1 || halo < 0) return 0;
+    int sy0, sy1;
+    slab_bounds(H, y0, y1, halo, &sy0, &sy1);
+    const size_t hs = static_cast<size_t>(sy1 - sy0);
+    return nsm_infer_workspace_bytes(static_cast<int>(hs), W, precision) + align_up(hs * W * sizeof(float), 256);
+}
+
+nsm_status nsm_infer_rows(nsm_ctx* ctx, const nsm_frame* frame, const nsm_weights* w, nsm_precision precision, int y0,
+                          int y1, int halo, void* workspace, size_t workspace_bytes, float* vis_rows, void* stream) {
+    nsm_status s = check_frame_host(frame, true);
+    if (s != NSM_OK) return s;
+    if (y0 < 0 || y1 > frame->H || y0 >= y1 || (y0 % 4) || (y1 % 4) || halo < 0 || (halo % 4))
+        return fail(NSM_ERR_SHAPE, "rows [%d, %d) of %d with halo %d: bounds in the frame, multiples of 4", y0, y1,
+                    frame->H, halo);
+    if ((s = check_dev_ptr(vis_rows, "vis_rows", 4)) != NSM_OK) return s;
+    const size_t need = nsm_infer_rows_workspace_bytes(frame->H, frame->W, y0, y1, halo, precision);
+    if (!workspace || workspace_bytes < need)
+        return fail(NSM_ERR_WORKSPACE, "workspace of %zu bytes given, %zu needed", workspace_bytes, need);
+    if ((s = check_dev_ptr(workspace, "workspace", 256)) != NSM_OK) return s;
+    int sy0, sy1;
+    slab_bounds(frame->H, y0, y1, halo, &sy0, &sy1);
+    nsm_frame sub = *frame;
+    sub.H = sy1 - sy0;
+    sub.pos4 = frame->pos4 + static_cast<size_t>(sy0) * frame->W * 4;
+    sub.nrm4 = frame->nrm4 + static_cast<size_t>(sy0) * frame->W * 4;
+    const size_t act = nsm_infer_workspace_bytes(sub.H, sub.W, precision);
+    float* vis = reinterpret_cast<float*>(static_cast<char*>(workspace) + act);
+    if ((s = infer_impl(ctx, &sub, w, precision, workspace, act, vis, stream, nullptr, 0.f, 0)) != NSM_OK) return s;
+    const size_t W = static_cast<size_t>(frame->W);
+    cudaError_t e = cudaMemcpyAsync(vis_rows, vis + static_cast<size_t>(y0 - sy0) * W,
+                                    static_cast<size_t>(y1 - y0) * W * sizeof(float), cudaMemcpyDeviceToDevice,
+                                    static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? NSM_OK : cuda_fail(e, "copy the slab's rows");
+}
+
 size_t nsm_infer_host_stage_bytes(int H, int W, int Hs, int Ws) {
     if (H <= 0 || W <= 0 || Hs <= 0 || Ws <= 0) return 0;
     const size_t npx = static_cast<size_t>(H) * W;

@@ -158,3 +158,12 @@ def test_host_validation_of_the_sensitivity_entry_points(lib):
     assert nsm.nsm_sensitivity_workspace_bytes(0, 64) == 0
     H, W = 64, 96
     assert nsm.nsm_sensitivity_workspace_bytes(H, W) >= nsm.nsm_infer_workspace_bytes(H, W, nsm.NSM_FP32) + 2 * H * W * 4
+
+
+def test_row_band_workspace_and_validation(lib):
+    H, W = 1080, 1920
+    n = nsm.nsm_infer_rows_workspace_bytes(H, W, 540, 1080, 32, nsm.NSM_BF16)
+    rows = 1080 - 508
+    assert n >= nsm.nsm_infer_workspace_bytes(rows, W, nsm.NSM_BF16) + rows * W * 4
+    assert nsm.nsm_infer_rows_workspace_bytes(H, W, 540, 540, 32, nsm.NSM_BF16) == 0
+    assert lib.nsm_infer_rows(None, None, None, 0, 0, 4, 0, None, 0, None, None) == 1
