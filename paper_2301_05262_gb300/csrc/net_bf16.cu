@@ -652,6 +652,12 @@ __global__ void __launch_bounds__(32 * tc_warps(NEW, NPW, EPI), 1) level_tc_kern
     fence_before_sync();
     __syncthreads();
     fence_after_sync();
+    // The set-up above reads only weights and parameters, which no stage kernel
+    // writes: with a programmatic launch it overlaps the previous stage's tail.
+    // The next stage may start its own set-up now; this stage's inputs are read
+    // only after the previous stage has completed.
+    griddep_launch_dependents();
+    griddep_wait();
     const uint32_t tbase = *tslot;
     // this CTA's tiles: a contiguous range of the tile list, which runs
     // column-major within each view (vertical strips of 128-pixel columns)
@@ -1189,8 +1195,10 @@ __global__ void __launch_bounds__(32 * tc_warps(NEW, NPW, EPI), 1) level_tc_kern
 }
 
 // ------------------------------------------------------------------ variants and launch
+// pdl: launch with programmatic stream serialisation (the kernel's set-up may
+// overlap the previous kernel of the stream, see griddep_wait)
 template <int CIN, int CMID, int COUT, int R, int PRO, int EPI, int NEW, int NPW, int KS, int ORD>
-static cudaError_t launch_variant(const TcBatch& a, int ctas_per_sm, cudaStream_t stream) {
+static cudaError_t launch_variant(const TcBatch& a, int ctas_per_sm, cudaStream_t stream, bool pdl) {
     using C = TcCfg<CIN, CMID, COUT, R, PRO, KS, EPI == TEPI_HEAD_PAR>;
     auto kern = level_tc_kernel<CIN, CMID, COUT, R, PRO, EPI, NEW, NPW, KS, ORD>;
     static int occ = -1;
@@ -1215,8 +1223,17 @@ static cudaError_t launch_variant(const TcBatch& a, int ctas_per_sm, cudaStream_
     const int per_sm = (ctas_per_sm <= 0 || ctas_per_sm > occ) ? occ : ctas_per_sm;
     const int cap = per_sm * num_sms();
     const int grid = tiles < cap ? tiles : cap;
-    kern<<<grid, 32 * tc_warps(NEW, NPW, EPI), C::BYTES, stream>>>(a);
-    return cudaGetLastError();
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(32 * tc_warps(NEW, NPW, EPI));
+    cfg.dynamicSmemBytes = C::BYTES;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kern, a);
 }
 
 template <int CIN, int CMID, int COUT, int R, int PRO, int EPI, int NEW, int NPW, int KS, int ORD>
@@ -1240,7 +1257,7 @@ static int occupancy_of() {
 
 // Variant tables: tile height R and warp roles of every stage (the
 // autotuner's search space).
-using LaunchFn = cudaError_t (*)(const TcBatch&, int, cudaStream_t);
+using LaunchFn = cudaError_t (*)(const TcBatch&, int, cudaStream_t, bool);
 struct Variant { int R, ew, pw, ks, ord; LaunchFn fn; const void* (*func)(); int (*occ)(); int tma, cin; };
 #define NSM_VARIANT(R_, EW_, PW_, KS_, ORD_, CIN_, CMID_, COUT_, PRO_, EPI_)                              \
     {R_, EW_, PW_, KS_, ORD_, launch_variant<CIN_, CMID_, COUT_, R_, PRO_, EPI_, EW_, PW_, KS_, ORD_>,      \
@@ -1359,7 +1376,8 @@ cudaError_t tc_prepare_stage(int stage, int variant, TcBatch& b) {
 cudaError_t tc_launch_stage(int stage, int variant, TcBatch& b, int ctas_per_sm, cudaStream_t stream) {
     cudaError_t e = tc_prepare_stage(stage, variant, b);
     if (e != cudaSuccess) return e;
-    return kStages[stage].v[variant].fn(b, ctas_per_sm, stream);
+    // stages after the first overlap their set-up with the previous stage's tail
+    return kStages[stage].v[variant].fn(b, ctas_per_sm, stream, stage > 0);
 }
 
 const char* const kInferKernelNamesBf16[kInferKernelsBf16] = {
@@ -1462,7 +1480,7 @@ cudaError_t launch_infer_s2d_bf16(const GatherParams& g, const float* params, co
             j.H = H / 2; j.W = W / 2; j.in_f = static_cast<const float*>(A.bo);
             j.skip = static_cast<const float*>(A.s1); j.out_f = static_cast<float*>(A.d1);
             tc_fill_tiles(b, kVarDec1Head4[0].R);
-            e = kVarDec1Head4[0].fn(b, 0, stream);
+            e = kVarDec1Head4[0].fn(b, 0, stream, true);
         }
         if (e != cudaSuccess) return e;
     }

@@ -146,6 +146,16 @@ __device__ __forceinline__ void tma_load_4d(uint32_t dst, const void* tmap, int 
         : "memory");
 }
 
+// ---------------------------------------------------------------- programmatic dependent launch
+// Let the next kernel of the stream (launched with the programmatic-serialisation
+// attribute) start its CTAs once every CTA of this grid has issued this or exited.
+__device__ __forceinline__ void griddep_launch_dependents() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+// Wait until the grid this one programmatically depends on has completed and its
+// memory operations are visible (returns at once for an ordinary launch).
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 // ---------------------------------------------------------------- mbarrier
 // Arrive once and announce `bytes` of transactions (TMA copies) for this phase.
 __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* mbar, uint32_t bytes) {
