@@ -386,6 +386,19 @@ def extra_train(nsm, scenegen, torch, device, theta, reps):
     ctx.check()
     ms_bf = sum(ev2[2 * k].elapsed_time(ev2[2 * k + 1]) for k in range(reps)) / reps
     loss_bf = float(loss.item())
+    # and with x_0's forward on the tensor-core stages as well (the backward FP32)
+    state_bf.set_forward_precision(nsm.NSM_BF16)
+    for _ in range(3):
+        state_bf.step(batch, loss_out=loss)
+    ev3 = _events(torch, 2 * reps)
+    for k in range(reps):
+        ev3[2 * k].record()
+        state_bf.step(batch, loss_out=loss)
+        ev3[2 * k + 1].record()
+    torch.cuda.synchronize()
+    ctx.check()
+    ms_tc = sum(ev3[2 * k].elapsed_time(ev3[2 * k + 1]) for k in range(reps)) / reps
+    loss_tc = float(loss.item())
     state_bf.close()
     # algorithmic work: forward of all B T instances, and for the B target
     # instances the recomputed forward, the weight gradients and the data
@@ -400,6 +413,9 @@ def extra_train(nsm, scenegen, torch, device, theta, reps):
             "bf16_detached": {"ms_per_step": ms_bf, "instances_per_s": B * T / (ms_bf * 1e-3), "loss_last": loss_bf,
                               "form": "x_1, x_2 (gradient stopped, Eq. 2) on the compensated-BF16 tcgen05 stage "
                                       "kernels, 32 instances per launch; x_0 and the backward FP32"},
+            "bf16_forward": {"ms_per_step": ms_tc, "instances_per_s": B * T / (ms_tc * 1e-3), "loss_last": loss_tc,
+                             "form": "every forward pass (x_0 with its checkpoints, x_1, x_2) on the tcgen05 stage "
+                                     "kernels with BF16-pair activations; the backward FP32 with recomputation"},
             "algorithmic_gflop": flop / 1e9, "achieved_tflops": tflops,
             "roofline": {"bound": "alu", "peak_tflops": peak, "frac": tflops / peak,
                          "peak_src": "128 FP32 lanes x 2 FLOP x SMs x max SM clock"},

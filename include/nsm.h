@@ -394,6 +394,15 @@ nsm_status nsm_train_state_write(nsm_train_state* st, int what, const float* dev
  * precisions: NSM_ERR_UNSUPPORTED. */
 nsm_status nsm_train_state_set_detached_precision(nsm_train_state* st, nsm_precision precision);
 
+/* Form of the forward pass of the target instances x_0, whose level outputs
+ * the backward recomputes from: NSM_FP32 (default; the FP32 training kernels)
+ * or NSM_BF16 (the compensated-BF16 tcgen05 stage kernels: the checkpoints
+ * carry their ~2^-16 relative rounding, the ones stored as BF16 pairs are
+ * converted to FP32 in place, and the backward stays FP32).  With both this
+ * and the detached form in BF16, every forward pass of a step runs on the
+ * tensor cores.  Other precisions: NSM_ERR_UNSUPPORTED. */
+nsm_status nsm_train_state_set_forward_precision(nsm_train_state* st, nsm_precision precision);
+
 /* The visibility of every instance of the last nsm_train_grad / nsm_train_step
  * call on this state, [T][B][H][W] floats (n = B T H W) into device memory:
  * x_0 of every item, then the detached instances.  Asynchronous on stream. */

@@ -396,7 +396,7 @@ def _coarse_grid_dec0(h, W3, b3, Weff, W1, b1, rnd_mid, Wexact):
 
 
 def forward_rounded(feat, theta, rnd, rnd_in=None, rnd_w=None, rnd_mid=None, levels: int = 3,
-                    coarse_dec0: bool = False):
+                    coarse_dec0: bool = False, ckpt: dict | None = None):
     """`forward` with values rounded wherever a reduced-precision form stores
     them: every convolution weight by `rnd_w` (not biases or the head), the
     3x3 output that feeds each 1x1 by `rnd_mid`, and by `rnd` each level's
@@ -407,7 +407,11 @@ def forward_rounded(feat, theta, rnd, rnd_in=None, rnd_w=None, rnd_mid=None, lev
     coarse_dec0: the level-0 decoder as a coarse-grid form evaluates it
     (`_coarse_grid_dec0`): no rounding of its up-sampled input, its 3x3 from
     the effective weights of `upsample_conv_weights` rounded by `rnd_w`, and
-    the outermost fine ring with the unrounded weights."""
+    the outermost fine ring with the unrounded weights.
+    ckpt: if a dict is given, it receives the stored level outputs as a form
+    keeps them for a backward pass: "e0" (pooled level-0 encoder output),
+    "s1" (level-1 skip), "p1" (pooled level-1 output), "bo" (bottleneck
+    output), "d1" (level-1 decoder output) and "vis" (3-level network)."""
     rnd_w = rnd if rnd_w is None else rnd_w
     rnd_mid = rnd if rnd_mid is None else rnd_mid
     P = unpack(theta, levels)
@@ -419,12 +423,16 @@ def forward_rounded(feat, theta, rnd, rnd_in=None, rnd_w=None, rnd_mid=None, lev
         a = rnd_mid(relu(conv2d(x, *Wr[l3])))
         return relu(conv2d(a, *Wr[l1]))
 
+    store = ckpt if ckpt is not None else {}
     for l in range(levels - 1):
         h1 = pair(h, f"enc{l}_3x3", f"enc{l}_1x1")
         if l >= 1:
             skips[l] = rnd(h1)
+            store[f"s{l}"] = skips[l]
         h = rnd(avgpool2(h1))
+        store["e0" if l == 0 else f"p{l}"] = h
     h = rnd(pair(h, "bott_3x3", "bott_1x1"))
+    store["bo"] = h
     for l in range(levels - 2, -1, -1):
         if l == 0 and coarse_dec0:
             W3, b3 = P["dec0_3x3"]
@@ -437,7 +445,42 @@ def forward_rounded(feat, theta, rnd, rnd_in=None, rnd_w=None, rnd_mid=None, lev
         h = pair(x, f"dec{l}_3x3", f"dec{l}_1x1")
         if l >= 1:
             h = rnd(h)
-    return sigmoid(conv2d(h, *Wr["head"])[0])
+            store[f"d{l}"] = h
+    vis = sigmoid(conv2d(h, *Wr["head"])[0])
+    store["vis"] = vis
+    return vis
+
+
+def recompute_from_checkpoints(feat, ckpt: dict, theta) -> dict:
+    """The intermediates `backward` needs (the `t` of `forward(keep=True)`,
+    3-level network), recomputed exactly level by level from stored level
+    inputs, as a backward with activation recomputation does: the level-0
+    encoder from the features, the level-1 encoder from ckpt["e0"], the
+    bottleneck from ckpt["p1"], the level-1 decoder from up(ckpt["bo"]) +
+    ckpt["s1"], the level-0 decoder from up(ckpt["d1"]); the output
+    visibility is the stored ckpt["vis"].  With exact checkpoints this is
+    `forward`'s t."""
+    P = unpack(theta, 3)
+    t = {}
+
+    def level(name, x):
+        t[f"{name}_in"] = x
+        a = conv2d(x, *P[f"{name}_3x3"])
+        t[f"{name}_a3"] = a
+        h3 = relu(a)
+        t[f"{name}_h3"] = h3
+        a1 = conv2d(h3, *P[f"{name}_1x1"])
+        t[f"{name}_a1"] = a1
+        return relu(a1)
+
+    t["enc0_h1"] = level("enc0", np.asarray(feat, np.float64))
+    t["enc1_h1"] = level("enc1", ckpt["e0"])
+    t["bott_out"] = level("bott", ckpt["p1"])
+    t["dec1_out"] = level("dec1", upsample2(ckpt["bo"]) + ckpt["s1"])
+    t["dec0_out"] = level("dec0", upsample2(ckpt["d1"]))
+    t["logit"] = conv2d(t["dec0_out"], *P["head"])[0]
+    t["vis"] = ckpt["vis"]
+    return t
 
 
 # ------------------------------------------------------------------ space-to-depth topology (Sec. 3.5)
@@ -629,7 +672,8 @@ def adam_update(theta, grad, m, v, step, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e
     return theta, m, v
 
 
-def train_step(batch_feats, targets, theta, m, v, step, lr=1e-3, alpha=0.9, levels=3, detached_forward=None):
+def train_step(batch_feats, targets, theta, m, v, step, lr=1e-3, alpha=0.9, levels=3, detached_forward=None,
+               target_forward=None):
     """One temporal-window training step (Sec. 3.3, Eq. 2).
 
     batch_feats: list over batch items of lists over window instances of
@@ -638,7 +682,10 @@ def train_step(batch_feats, targets, theta, m, v, step, lr=1e-3, alpha=0.9, leve
     over the batch.  detached_forward(features, theta) evaluates the
     instances without gradient (default: `forward`; a reduced-precision
     form's rounding model, e.g. `forward_rounded`, for a form that runs them
-    at lower precision).  Returns (theta, m, v, loss, grad)."""
+    at lower precision).  target_forward(features, theta), if given, gives
+    the visibility of instance 0 that enters the loss (a form that runs the
+    target's forward at lower precision); the adjoint is still taken at the
+    exact activations of `forward`.  Returns (theta, m, v, loss, grad)."""
     B = len(batch_feats)
     grad = np.zeros_like(np.asarray(theta, np.float64))
     total = 0.0
@@ -646,6 +693,8 @@ def train_step(batch_feats, targets, theta, m, v, step, lr=1e-3, alpha=0.9, leve
     for b in range(B):
         insts = batch_feats[b]
         x0, t = forward(insts[0], theta, levels, keep=True)
+        if target_forward is not None:
+            x0 = target_forward(insts[0], theta)
         xs = [fwd_detached(f, theta) for f in insts[1:]]
         loss, g = loss_l1(x0, targets[b], xs, alpha)
         total += loss / B

@@ -342,6 +342,7 @@ def _train_sigs():
         "nsm_train_grad": ([P, P, ctypes.POINTER(nsm_batch), ctypes.POINTER(nsm_train_cfg), P, P], I),
         "nsm_train_apply": ([P, P, ctypes.POINTER(nsm_train_cfg), P], I),
         "nsm_train_state_set_detached_precision": ([P, I], I),
+        "nsm_train_state_set_forward_precision": ([P, I], I),
         "nsm_train_state_read_vis": ([P, P, Z, P], I),
     }
     for name, (args, res) in sig.items():
@@ -405,6 +406,11 @@ class TrainState:
         """Form of the detached instances' forward (NSM_FP32 or NSM_BF16)."""
         _check(_train_sigs().nsm_train_state_set_detached_precision(self.h, precision),
                "nsm_train_state_set_detached_precision")
+
+    def set_forward_precision(self, precision: int):
+        """Form of the target instances' forward (NSM_FP32 or NSM_BF16)."""
+        _check(_train_sigs().nsm_train_state_set_forward_precision(self.h, precision),
+               "nsm_train_state_set_forward_precision")
 
     def read_vis(self, out, stream=None):
         """Visibility [T][B][H][W] of the last step's instances into a device tensor."""

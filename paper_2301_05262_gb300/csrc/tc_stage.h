@@ -43,7 +43,7 @@ struct TcJob {
     float* vis;                 // HEAD: [H][W]; HEAD_PAR: [2H][2W]; HEAD4 writes out_f [H][W][4]
     // TMA prologue: tensor map of `in` as [H][W][2 CIN / 8 chunks][8 BF16],
     // box = one 16-byte chunk plane of kSW pixels of one row (zero fill outside)
-    alignas(64) CUtensorMap tmap;
+    CUtensorMap tmap;           // (the type carries the 64-byte alignment TMA needs)
 };
 
 // Kernel parameter of a stage launch (passed by value, __grid_constant__).

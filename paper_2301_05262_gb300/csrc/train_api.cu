@@ -1,6 +1,8 @@
 // C ABI of the backward and training entry points (include/nsm.h).
 #include <vector>
 
+#include <cuda_bf16.h>
+
 #include "nsm_internal.h"
 #include "train_internal.h"
 #include "ctx_internal.h"
@@ -22,6 +24,10 @@ struct nsm_train_state {
     // checkpointed FP32 kernels, default) or NSM_BF16 (the tensor-core stage
     // kernels, BF16 images of the master weights packed every step)
     int detached_precision;
+    // Forward of the target instances x_0 (the backward's checkpoints): NSM_FP32
+    // (default) or NSM_BF16 (the stage kernels; their BF16-pair checkpoints
+    // converted to FP32 for the FP32 backward)
+    int forward_precision;
     uint16_t* bf16;      // packed BF16 weight images
     void* descs;         // their packing table (device)
     int ndesc;
@@ -31,6 +37,62 @@ struct nsm_train_state {
 namespace nsm {
 
 static size_t backward_floats(int H, int W) { return tr::workspace_floats(1, 1, H, W); }
+
+// In place: n pixels of BF16 hi + lo pairs [pixel][part][C] -> FP32 [pixel][C]
+// (same bytes per pixel; each thread reads a whole pixel before writing it).
+template <int C>
+__global__ void pairs_to_f32_kernel(void* buf, size_t n) {
+    for (size_t p = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; p < n;
+         p += static_cast<size_t>(gridDim.x) * blockDim.x) {
+        uint4* px = static_cast<uint4*>(buf) + p * (C / 4);
+        uint4 c[C / 4];
+#pragma unroll
+        for (int k = 0; k < C / 4; ++k) c[k] = px[k];
+        const uint16_t* h = reinterpret_cast<const uint16_t*>(c);
+        float f[C];
+#pragma unroll
+        for (int k = 0; k < C; ++k)
+            f[k] = __bfloat162float(__ushort_as_bfloat16(h[k])) + __bfloat162float(__ushort_as_bfloat16(h[C + k]));
+#pragma unroll
+        for (int k = 0; k < C / 4; ++k) px[k] = make_uint4(__float_as_uint(f[4 * k]), __float_as_uint(f[4 * k + 1]),
+                                                            __float_as_uint(f[4 * k + 2]), __float_as_uint(f[4 * k + 3]));
+    }
+}
+
+template <int C>
+static cudaError_t pairs_to_f32(float* buf, size_t n, cudaStream_t st) {
+    const size_t blocks = (n + 255) / 256;
+    pairs_to_f32_kernel<C><<<static_cast<int>(blocks < 4096 ? blocks : 4096), 256, 0, st>>>(buf, n);
+    return cudaGetLastError();
+}
+
+// The network on the tensor-core stage kernels for instances [i0, i1): gather
+// fused, activations in the instances' checkpoint slots, visibility in b.vis.
+static cudaError_t tc_forward(nsm_ctx* ctx, const nsm_train_state* s, const std::vector<GatherParams>& gps,
+                              const tr::Buffers& b, int i0, int i1, size_t npx, cudaStream_t cs) {
+    const size_t p1 = npx / 4, p2 = npx / 16;
+    for (int j0 = i0; j0 < i1; j0 += kMaxViews) {
+        const int n = (i1 - j0) < kMaxViews ? (i1 - j0) : kMaxViews;
+        std::vector<Activations> act(n);
+        std::vector<float*> vis(n);
+        for (int k = 0; k < n; ++k) {
+            const size_t i = static_cast<size_t>(j0 + k);
+            act[k].e0 = b.e0 + i * p1 * 16;
+            act[k].s1 = b.s1 + i * p1 * 32;
+            act[k].p1 = b.p1 + i * p2 * 32;
+            act[k].bo = b.bo + i * p2 * 32;
+            act[k].d1 = b.d1 + i * p1 * 16;
+            vis[k] = b.vis + i * npx;
+        }
+        TcBatch tb[kTcStages];
+        tc_make_batches(gps.data() + j0, act.data(), vis.data(), n, s->theta, s->bf16, ctx->d_err, tb);
+        for (int k = 0; k < kTcStages; ++k) {
+            cudaError_t e = tc_launch_stage(k, ctx->tc_variant[k], tb[k], ctx->tc_ctas[k], cs);
+            if (e != cudaSuccess) return e;
+        }
+    }
+    return cudaSuccess;
+}
 
 }  // namespace nsm
 
@@ -106,6 +168,7 @@ nsm_status nsm_train_state_create(nsm_ctx* ctx, const float* host_params, size_t
     alloc(&s->descs, pack_desc_bytes() * im.n);
     if (e == cudaSuccess) e = cudaMemcpy(s->descs, im.desc, pack_desc_bytes() * im.n, cudaMemcpyHostToDevice);
     s->detached_precision = NSM_FP32;
+    s->forward_precision = NSM_FP32;
     if (e == cudaSuccess) e = cudaMemcpy(s->theta, host_params, n * 4, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(s->m, 0, n * 4);
     if (e == cudaSuccess) e = cudaMemset(s->v, 0, n * 4);
@@ -166,38 +229,38 @@ nsm_status nsm_train_grad(nsm_ctx* ctx, nsm_train_state* s, const nsm_batch* bt,
     if (e != cudaSuccess) return cuda_fail(e, "upload gather parameters");
     tr::Buffers b = tr::carve(s->work, N, bt->B, H, W);
     s->last_N = N;
-    if (s->detached_precision == NSM_BF16 && bt->T > 1) {
-        // x_0 (instances 0 .. B-1): FP32 with the checkpoints the backward needs
-        if ((e = tr::features_batch(s->gp, bt->B, H, W, b.feat, cs)) != cudaSuccess) return cuda_fail(e, "features");
-        if ((e = tr::forward(s->theta, b, bt->B, bt->B, H, W, cs)) != cudaSuccess) return cuda_fail(e, "forward");
-        // the detached x_i: inference only, on the tensor-core stage kernels (gather fused
-        // into the first stage), their activations in the instances' checkpoint slots
+    const int B = bt->B;
+    const bool tc0 = s->forward_precision == NSM_BF16;                   // x_0 on the tensor cores
+    const bool tcd = s->detached_precision == NSM_BF16 && bt->T > 1;     // x_1 .. x_{T-1} on the tensor cores
+    // features of the instances the FP32 kernels run, and of every x_0 (the
+    // backward recomputes its first level from them)
+    const int nfeat = tcd ? B : N;
+    if ((e = tr::features_batch(s->gp, nfeat, H, W, b.feat, cs)) != cudaSuccess) return cuda_fail(e, "features");
+    if (tc0 || tcd) {
         if ((e = launch_pack_bf16(s->theta, s->bf16, s->descs, s->ndesc, cs)) != cudaSuccess)
             return cuda_fail(e, "pack BF16 weights");
-        const size_t p1 = npx / 4, p2 = npx / 16;
-        for (int i0 = bt->B; i0 < N; i0 += kMaxViews) {
-            const int n = (N - i0) < kMaxViews ? (N - i0) : kMaxViews;
-            std::vector<Activations> act(n);
-            std::vector<float*> vis(n);
-            for (int k = 0; k < n; ++k) {
-                const size_t i = static_cast<size_t>(i0 + k);
-                act[k].e0 = b.e0 + i * p1 * 16;
-                act[k].s1 = b.s1 + i * p1 * 32;
-                act[k].p1 = b.p1 + i * p2 * 32;
-                act[k].bo = b.bo + i * p2 * 32;
-                act[k].d1 = b.d1 + i * p1 * 16;
-                vis[k] = b.vis + i * npx;
-            }
-            TcBatch tb[kTcStages];
-            tc_make_batches(gps.data() + i0, act.data(), vis.data(), n, s->theta, s->bf16, ctx->d_err, tb);
-            for (int k = 0; k < kTcStages; ++k)
-                if ((e = tc_launch_stage(k, ctx->tc_variant[k], tb[k], ctx->tc_ctas[k], cs)) != cudaSuccess)
-                    return cuda_fail(e, "detached forward (tensor-core stages)");
-        }
-    } else {
-        if ((e = tr::features_batch(s->gp, N, H, W, b.feat, cs)) != cudaSuccess) return cuda_fail(e, "features");
-        if ((e = tr::forward(s->theta, b, N, bt->B, H, W, cs)) != cudaSuccess) return cuda_fail(e, "forward");
     }
+    if (!tc0) {
+        // x_0 (and, unless they run on the tensor cores, the detached instances) in FP32
+        if ((e = tr::forward(s->theta, b, tcd ? B : N, B, H, W, cs)) != cudaSuccess) return cuda_fail(e, "forward");
+    } else {
+        if ((e = tc_forward(ctx, s, gps, b, 0, B, npx, cs)) != cudaSuccess) return cuda_fail(e, "forward (tensor cores)");
+        // the FP32 backward reads FP32 checkpoints: e0, p1 and d1 were stored as BF16 pairs
+        const size_t p1 = npx / 4, p2 = npx / 16;
+        if ((e = pairs_to_f32<16>(b.e0, B * p1, cs)) != cudaSuccess ||
+            (e = pairs_to_f32<32>(b.p1, B * p2, cs)) != cudaSuccess ||
+            (e = pairs_to_f32<16>(b.d1, B * p1, cs)) != cudaSuccess)
+            return cuda_fail(e, "checkpoint conversion");
+        if (!tcd && bt->T > 1) {
+            // detached instances in FP32: the fused forward over instances B .. N-1
+            tr::Buffers bd = b;
+            bd.feat += static_cast<size_t>(B) * npx * 4; bd.e0 += B * p1 * 16; bd.s1 += B * p1 * 32;
+            bd.p1 += B * p2 * 32; bd.bo += B * p2 * 32; bd.d1 += B * p1 * 16; bd.vis += static_cast<size_t>(B) * npx;
+            if ((e = tr::forward(s->theta, bd, N - B, B, H, W, cs)) != cudaSuccess) return cuda_fail(e, "forward");
+        }
+    }
+    if (tcd && (e = tc_forward(ctx, s, gps, b, B, N, npx, cs)) != cudaSuccess)
+        return cuda_fail(e, "detached forward (tensor cores)");
     if ((e = cudaMemsetAsync(s->loss, 0, sizeof(float), cs)) != cudaSuccess) return cuda_fail(e, "loss reset");
     if ((e = tr::loss_l1(b.vis, bt->target, bt->B, bt->T, npx, cfg->alpha, b.gvis, s->loss, cs)) != cudaSuccess)
         return cuda_fail(e, "loss");
@@ -239,6 +302,14 @@ nsm_status nsm_train_state_set_detached_precision(nsm_train_state* s, nsm_precis
     if (precision != NSM_FP32 && precision != NSM_BF16)
         return fail(NSM_ERR_UNSUPPORTED, "the detached instances run in the FP32 or the BF16 form");
     s->detached_precision = precision;
+    return NSM_OK;
+}
+
+nsm_status nsm_train_state_set_forward_precision(nsm_train_state* s, nsm_precision precision) {
+    if (!s) return fail(NSM_ERR_INVALID_ARG, "state is NULL");
+    if (precision != NSM_FP32 && precision != NSM_BF16)
+        return fail(NSM_ERR_UNSUPPORTED, "the target instances run in the FP32 or the BF16 form");
+    s->forward_precision = precision;
     return NSM_OK;
 }
 

@@ -561,3 +561,24 @@ def test_trained_s2d_weights_input():
         mse_tr = np.mean((N.forward_s2d(feat, th) - target) ** 2)
         mse_he = np.mean((N.forward_s2d(feat, he) - target) ** 2)
         assert mse_tr < 0.25 * mse_he, (soft, mse_tr, mse_he)
+
+
+def test_recompute_from_exact_checkpoints_is_forward():
+    """With no rounding, the checkpoints of forward_rounded and the
+    intermediates recomputed from them equal forward's, and the adjoint built
+    on them equals backward on forward's intermediates."""
+    rng = np.random.default_rng(11)
+    x = rng.standard_normal((4, 16, 24))
+    th = N.pack({n: (rng.standard_normal((co, ci, k, k)) * 0.3, rng.standard_normal(co) * 0.1)
+                 for (n, ci, co, k) in N.layer_table(3)})
+    ident = lambda a: a
+    ck = {}
+    vis = N.forward_rounded(x, th, ident, ckpt=ck)
+    ref, t = N.forward(x, th, keep=True)
+    np.testing.assert_allclose(vis, ref, rtol=0, atol=1e-14)
+    t2 = N.recompute_from_checkpoints(x, ck, th)
+    for k in ("enc0_a3", "enc1_in", "enc1_a1", "bott_in", "bott_a3", "dec1_in", "dec1_a1", "dec0_in", "dec0_a3",
+              "dec0_out", "vis"):
+        np.testing.assert_allclose(t2[k], t[k], rtol=0, atol=1e-12, err_msg=k)
+    g = rng.standard_normal(vis.shape)
+    np.testing.assert_allclose(N.backward(g, th, t2)[0], N.backward(g, th, t)[0], rtol=1e-12, atol=1e-13)
