@@ -332,6 +332,17 @@ nsm_status nsm_backward(nsm_ctx* ctx, const nsm_frame* frame, const float* dev_p
                         float* grad_params, float* grad_feat, float* vis_out, void* workspace,
                         size_t workspace_bytes, void* stream);
 
+/* nsm_backward with the form of its 3x3 convolutions chosen (the level
+ * recomputations and the data gradients through them): NSM_FP32 (exactly
+ * nsm_backward) or NSM_BF16 (tcgen05 implicit GEMMs, compensated BF16 operands
+ * and FP32 accumulation, as nsm_train_state_set_backward_precision; the weight
+ * images are packed into the same workspace).  Other precisions:
+ * NSM_ERR_UNSUPPORTED.  A bounded device wait that gives up sets the context's
+ * error word (nsm_ctx_check). */
+nsm_status nsm_backward_ex(nsm_ctx* ctx, const nsm_frame* frame, const float* dev_params, const float* grad_vis,
+                           float* grad_params, float* grad_feat, float* vis_out, nsm_precision precision,
+                           void* workspace, size_t workspace_bytes, void* stream);
+
 /* One training batch of the temporal-window loss (Sec. 3.3, Eq. 2). */
 typedef struct {
     int B, T;                   /* items; window instances per item (T >= 1), instance 0 carries
@@ -402,6 +413,19 @@ nsm_status nsm_train_state_set_detached_precision(nsm_train_state* st, nsm_preci
  * and the detached form in BF16, every forward pass of a step runs on the
  * tensor cores.  Other precisions: NSM_ERR_UNSUPPORTED. */
 nsm_status nsm_train_state_set_forward_precision(nsm_train_state* st, nsm_precision precision);
+
+/* Form of the backward's 3x3 convolutions (Sec. 3.3, Eq. 2 adjoint): the
+ * recomputed 3x3 pre-activations of every level and the data gradients
+ * through them (the transposed, flipped weights).  NSM_FP32 (default; FP32
+ * CUDA-core kernels) or NSM_BF16 (tcgen05 implicit GEMMs with compensated
+ * BF16 operands: activations and weights as hi + lo BF16 pairs, all four
+ * products accumulated in FP32 in tensor memory, ~2^-16 relative per operand;
+ * weight images packed on the device at every step).  Tensors stay FP32
+ * between the layers; the weight gradients and the 1x1 layers stay FP32.  A
+ * bounded device wait that gives up sets the context's error word
+ * (nsm_ctx_check: NSM_ERR_TIMEOUT, code 7).  Other precisions:
+ * NSM_ERR_UNSUPPORTED. */
+nsm_status nsm_train_state_set_backward_precision(nsm_train_state* st, nsm_precision precision);
 
 /* The visibility of every instance of the last nsm_train_grad / nsm_train_step
  * call on this state, [T][B][H][W] floats (n = B T H W) into device memory:

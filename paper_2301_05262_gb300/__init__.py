@@ -334,6 +334,7 @@ def _train_sigs():
     sig = {
         "nsm_backward_workspace_bytes": ([I, I], Z),
         "nsm_backward": ([P, ctypes.POINTER(nsm_frame), P, P, P, P, P, P, Z, P], I),
+        "nsm_backward_ex": ([P, ctypes.POINTER(nsm_frame), P, P, P, P, P, I, P, Z, P], I),
         "nsm_train_state_create": ([P, P, Z, I, I, I, I, ctypes.POINTER(P)], I),
         "nsm_train_state_destroy": ([P], None),
         "nsm_train_step": ([P, P, ctypes.POINTER(nsm_batch), ctypes.POINTER(nsm_train_cfg), P, P], I),
@@ -343,6 +344,7 @@ def _train_sigs():
         "nsm_train_apply": ([P, P, ctypes.POINTER(nsm_train_cfg), P], I),
         "nsm_train_state_set_detached_precision": ([P, I], I),
         "nsm_train_state_set_forward_precision": ([P, I], I),
+        "nsm_train_state_set_backward_precision": ([P, I], I),
         "nsm_train_state_read_vis": ([P, P, Z, P], I),
     }
     for name, (args, res) in sig.items():
@@ -358,11 +360,17 @@ def nsm_backward_workspace_bytes(H: int, W: int) -> int:
 
 
 def nsm_backward(ctx: Context, frame: nsm_frame, dev_params, grad_vis, grad_params, workspace, grad_feat=None,
-                 vis_out=None, stream=None):
+                 vis_out=None, stream=None, precision=None):
+    """precision None: nsm_backward; NSM_FP32 / NSM_BF16: nsm_backward_ex with that form of the 3x3 layers."""
     L = _train_sigs()
-    _check(L.nsm_backward(ctx.h, ctypes.byref(frame), _ptr(dev_params), _ptr(grad_vis), _ptr(grad_params),
-                          _ptr(grad_feat), _ptr(vis_out), _ptr(workspace),
-                          int(workspace.numel() * workspace.element_size()), _stream(stream)), "nsm_backward")
+    if precision is None:
+        _check(L.nsm_backward(ctx.h, ctypes.byref(frame), _ptr(dev_params), _ptr(grad_vis), _ptr(grad_params),
+                              _ptr(grad_feat), _ptr(vis_out), _ptr(workspace),
+                              int(workspace.numel() * workspace.element_size()), _stream(stream)), "nsm_backward")
+        return
+    _check(L.nsm_backward_ex(ctx.h, ctypes.byref(frame), _ptr(dev_params), _ptr(grad_vis), _ptr(grad_params),
+                             _ptr(grad_feat), _ptr(vis_out), int(precision), _ptr(workspace),
+                             int(workspace.numel() * workspace.element_size()), _stream(stream)), "nsm_backward_ex")
 
 
 class TrainState:
@@ -411,6 +419,11 @@ class TrainState:
         """Form of the target instances' forward (NSM_FP32 or NSM_BF16)."""
         _check(_train_sigs().nsm_train_state_set_forward_precision(self.h, precision),
                "nsm_train_state_set_forward_precision")
+
+    def set_backward_precision(self, precision: int):
+        """Form of the backward's 3x3 recomputations and data gradients (NSM_FP32 or NSM_BF16)."""
+        _check(_train_sigs().nsm_train_state_set_backward_precision(self.h, precision),
+               "nsm_train_state_set_backward_precision")
 
     def read_vis(self, out, stream=None):
         """Visibility [T][B][H][W] of the last step's instances into a device tensor."""

@@ -911,9 +911,13 @@ cudaError_t forward(const float* th, const Buffers& b, int N, int Nb, int H, int
 
 // Backward of the first Nb views (cotangent b.gvis) into grad (canonical
 // layout, accumulated), recomputing each level from its checkpoint.
-// With gfeat != nullptr also the feature gradient [Nb][H][W][4].
+// With gfeat != nullptr also the feature gradient [Nb][H][W][4].  With img
+// != nullptr (the conv3_pack images of th) the 3x3 recomputations and data
+// gradients run on the tensor cores (conv3_tc), else on the FP32 kernels.
 cudaError_t backward(const float* th, float* grad, const Buffers& b, int Nb, int H, int W, float* gfeat,
-                     cudaStream_t st) {
+                     cudaStream_t st, const uint4* img, int* err) {
+    const Conv3Images im = conv3_images();
+    auto I = [&](int i) { return img + im.off[i]; };
     const size_t p0 = static_cast<size_t>(H) * W, p1 = p0 / 4, p2 = p0 / 16;
     const int H1 = H / 2, W1 = W / 2, H2 = H / 4, W2 = W / 4;
     const LayerOffsets o = layer_offsets();
@@ -922,53 +926,63 @@ cudaError_t backward(const float* th, float* grad, const Buffers& b, int Nb, int
     // ---- level 0 decoder + head: recompute x = up(d1), a3, a1
     L = level(th, grad, DEC0_3, DEC0_1);
     up_fwd_kernel<<<ew_grid(n * p0 * 16), 256, 0, st>>>(b.d1, nullptr, n, H, W, 16, b.xin);
-    NSM_TRY((conv_fwd<16, 16, 3>(b.xin, nullptr, 0, n, H, W, L.w3, 0, L.b3, nullptr, b.a3, st)));
+    if (img) NSM_TRY(conv3_tc(16, 16, b.xin, n, H, W, I(8), L.b3, b.a3, err, st));
+    else NSM_TRY((conv_fwd<16, 16, 3>(b.xin, nullptr, 0, n, H, W, L.w3, 0, L.b3, nullptr, b.a3, st)));
     NSM_TRY((conv_fwd<16, 16, 1>(b.a3, nullptr, 1, n, H, W, L.w1, 0, L.b1, nullptr, b.a1, st)));
     head_bwd_kernel<<<ew_grid(n * p0), 256, 0, st>>>(b.a1, b.vis, b.gvis, th + o.w[HEAD], n * p0, b.ga1,
                                                      grad + o.w[HEAD]);
     NSM_TRY((conv_wgrad<16, 16, 1>(b.a3, 1, b.ga1, nullptr, n, H, W, L.dw1, L.db1, st)));
     NSM_TRY((conv_fwd<16, 16, 1>(b.ga1, nullptr, 0, n, H, W, L.w1, 1, nullptr, b.a3, b.ga3, st)));
     NSM_TRY((conv_wgrad<16, 16, 3>(b.xin, 0, b.ga3, nullptr, n, H, W, L.dw3, L.db3, st)));
-    NSM_TRY((conv_fwd<16, 16, 3>(b.ga3, nullptr, 0, n, H, W, L.w3, 1, nullptr, nullptr, b.gx, st)));
+    if (img) NSM_TRY(conv3_tc(16, 16, b.ga3, n, H, W, I(9), nullptr, b.gx, err, st));
+    else NSM_TRY((conv_fwd<16, 16, 3>(b.ga3, nullptr, 0, n, H, W, L.w3, 1, nullptr, nullptr, b.gx, st)));
     up_adj_kernel<<<ew_grid(n * p1 * 16), 256, 0, st>>>(b.gx, n, H, W, 16, b.glo);  // g d1 [n][H1][W1][16]
     // ---- level 1 decoder: recompute x = up(bo) + s1, a3, a1
     L = level(th, grad, DEC1_3, DEC1_1);
     up_fwd_kernel<<<ew_grid(n * p1 * 32), 256, 0, st>>>(b.bo, b.s1, n, H1, W1, 32, b.xin);
-    NSM_TRY((conv_fwd<32, 32, 3, 16>(b.xin, nullptr, 0, n, H1, W1, L.w3, 0, L.b3, nullptr, b.a3, st)));
+    if (img) NSM_TRY(conv3_tc(32, 32, b.xin, n, H1, W1, I(6), L.b3, b.a3, err, st));
+    else NSM_TRY((conv_fwd<32, 32, 3, 16>(b.xin, nullptr, 0, n, H1, W1, L.w3, 0, L.b3, nullptr, b.a3, st)));
     NSM_TRY((conv_fwd<32, 16, 1>(b.a3, nullptr, 1, n, H1, W1, L.w1, 0, L.b1, nullptr, b.a1, st)));
     // g_a1 = g_d1 (a1 > 0)
     NSM_TRY((conv_wgrad<32, 16, 1>(b.a3, 1, b.glo, b.a1, n, H1, W1, L.dw1, L.db1, st)));
     NSM_TRY((conv_fwd<16, 32, 1>(b.glo, b.a1, 0, n, H1, W1, L.w1, 1, nullptr, b.a3, b.ga3, st)));
     NSM_TRY((conv_wgrad<32, 32, 3>(b.xin, 0, b.ga3, nullptr, n, H1, W1, L.dw3, L.db3, st)));
-    NSM_TRY((conv_fwd<32, 32, 3, 16>(b.ga3, nullptr, 0, n, H1, W1, L.w3, 1, nullptr, nullptr, b.gskip, st)));  // g x1
+    if (img) NSM_TRY(conv3_tc(32, 32, b.ga3, n, H1, W1, I(7), nullptr, b.gskip, err, st));  // g x1
+    else NSM_TRY((conv_fwd<32, 32, 3, 16>(b.ga3, nullptr, 0, n, H1, W1, L.w3, 1, nullptr, nullptr, b.gskip, st)));
     up_adj_kernel<<<ew_grid(n * p2 * 32), 256, 0, st>>>(b.gskip, n, H1, W1, 32, b.glo);  // g bo [n][H2][W2][32]
     // ---- bottleneck: recompute a3 = conv3(p1), a1
     L = level(th, grad, BOTT_3, BOTT_1);
-    NSM_TRY((conv_fwd<32, 64, 3, 16>(b.p1, nullptr, 0, n, H2, W2, L.w3, 0, L.b3, nullptr, b.a3, st)));
+    if (img) NSM_TRY(conv3_tc(32, 64, b.p1, n, H2, W2, I(4), L.b3, b.a3, err, st));
+    else NSM_TRY((conv_fwd<32, 64, 3, 16>(b.p1, nullptr, 0, n, H2, W2, L.w3, 0, L.b3, nullptr, b.a3, st)));
     NSM_TRY((conv_fwd<64, 32, 1>(b.a3, nullptr, 1, n, H2, W2, L.w1, 0, L.b1, nullptr, b.a1, st)));
     NSM_TRY((conv_wgrad<64, 32, 1>(b.a3, 1, b.glo, b.a1, n, H2, W2, L.dw1, L.db1, st)));
     NSM_TRY((conv_fwd<32, 64, 1>(b.glo, b.a1, 0, n, H2, W2, L.w1, 1, nullptr, b.a3, b.ga3, st)));
     NSM_TRY((conv_wgrad<32, 64, 3>(b.p1, 0, b.ga3, nullptr, n, H2, W2, L.dw3, L.db3, st)));
-    NSM_TRY((conv_fwd<64, 32, 3, 16>(b.ga3, nullptr, 0, n, H2, W2, L.w3, 1, nullptr, nullptr, b.gx, st)));  // g p1
+    if (img) NSM_TRY(conv3_tc(64, 32, b.ga3, n, H2, W2, I(5), nullptr, b.gx, err, st));  // g p1
+    else NSM_TRY((conv_fwd<64, 32, 3, 16>(b.ga3, nullptr, 0, n, H2, W2, L.w3, 1, nullptr, nullptr, b.gx, st)));
     // ---- level 1 encoder: g_h1 = pool_adj(g p1) + g s1 ; recompute a3 = conv3(e0), a1
     L = level(th, grad, ENC1_3, ENC1_1);
     pool_adj_kernel<<<ew_grid(n * p1 * 32), 256, 0, st>>>(b.gx, n, H1, W1, 32, 0, b.glo);
     add_kernel<<<ew_grid(n * p1 * 32), 256, 0, st>>>(b.glo, b.gskip, n * p1 * 32);
-    NSM_TRY((conv_fwd<16, 32, 3>(b.e0, nullptr, 0, n, H1, W1, L.w3, 0, L.b3, nullptr, b.a3, st)));
+    if (img) NSM_TRY(conv3_tc(16, 32, b.e0, n, H1, W1, I(2), L.b3, b.a3, err, st));
+    else NSM_TRY((conv_fwd<16, 32, 3>(b.e0, nullptr, 0, n, H1, W1, L.w3, 0, L.b3, nullptr, b.a3, st)));
     NSM_TRY((conv_fwd<32, 32, 1>(b.a3, nullptr, 1, n, H1, W1, L.w1, 0, L.b1, nullptr, b.a1, st)));
     NSM_TRY((conv_wgrad<32, 32, 1>(b.a3, 1, b.glo, b.a1, n, H1, W1, L.dw1, L.db1, st)));
     NSM_TRY((conv_fwd<32, 32, 1>(b.glo, b.a1, 0, n, H1, W1, L.w1, 1, nullptr, b.a3, b.ga3, st)));
     NSM_TRY((conv_wgrad<16, 32, 3>(b.e0, 0, b.ga3, nullptr, n, H1, W1, L.dw3, L.db3, st)));
-    NSM_TRY((conv_fwd<32, 16, 3>(b.ga3, nullptr, 0, n, H1, W1, L.w3, 1, nullptr, nullptr, b.gx, st)));  // g e0
+    if (img) NSM_TRY(conv3_tc(32, 16, b.ga3, n, H1, W1, I(3), nullptr, b.gx, err, st));  // g e0
+    else NSM_TRY((conv_fwd<32, 16, 3>(b.ga3, nullptr, 0, n, H1, W1, L.w3, 1, nullptr, nullptr, b.gx, st)));
     // ---- level 0 encoder: g_h1 = pool_adj(g e0); recompute a3 = conv3(feat), a1
     L = level(th, grad, ENC0_3, ENC0_1);
     pool_adj_kernel<<<ew_grid(n * p0 * 16), 256, 0, st>>>(b.gx, n, H, W, 16, 0, b.gtmp);
-    NSM_TRY((conv_fwd<4, 16, 3>(b.feat, nullptr, 0, n, H, W, L.w3, 0, L.b3, nullptr, b.a3, st)));
+    if (img) NSM_TRY(conv3_tc(4, 16, b.feat, n, H, W, I(0), L.b3, b.a3, err, st));
+    else NSM_TRY((conv_fwd<4, 16, 3>(b.feat, nullptr, 0, n, H, W, L.w3, 0, L.b3, nullptr, b.a3, st)));
     NSM_TRY((conv_fwd<16, 16, 1>(b.a3, nullptr, 1, n, H, W, L.w1, 0, L.b1, nullptr, b.a1, st)));
     NSM_TRY((conv_wgrad<16, 16, 1>(b.a3, 1, b.gtmp, b.a1, n, H, W, L.dw1, L.db1, st)));
     NSM_TRY((conv_fwd<16, 16, 1>(b.gtmp, b.a1, 0, n, H, W, L.w1, 1, nullptr, b.a3, b.ga3, st)));
     NSM_TRY((conv_wgrad<4, 16, 3>(b.feat, 0, b.ga3, nullptr, n, H, W, L.dw3, L.db3, st)));
-    if (gfeat) NSM_TRY((conv_fwd<16, 4, 3>(b.ga3, nullptr, 0, n, H, W, L.w3, 1, nullptr, nullptr, gfeat, st)));
+    if (gfeat && img) NSM_TRY(conv3_tc(16, 4, b.ga3, n, H, W, I(1), nullptr, gfeat, err, st));
+    else if (gfeat) NSM_TRY((conv_fwd<16, 4, 3>(b.ga3, nullptr, 0, n, H, W, L.w3, 1, nullptr, nullptr, gfeat, st)));
     return cudaGetLastError();
 }
 

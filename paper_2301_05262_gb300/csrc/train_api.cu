@@ -28,6 +28,10 @@ struct nsm_train_state {
     // (default) or NSM_BF16 (the stage kernels; their BF16-pair checkpoints
     // converted to FP32 for the FP32 backward)
     int forward_precision;
+    // 3x3 recomputations and data gradients of the backward: NSM_FP32 (default)
+    // or NSM_BF16 (tcgen05, compensated BF16 operands, FP32 accumulation)
+    int backward_precision;
+    uint4* conv3;        // their weight images, packed every step
     uint16_t* bf16;      // packed BF16 weight images
     void* descs;         // their packing table (device)
     int ndesc;
@@ -37,6 +41,9 @@ struct nsm_train_state {
 namespace nsm {
 
 static size_t backward_floats(int H, int W) { return tr::workspace_floats(1, 1, H, W); }
+static size_t conv3_image_bytes() {
+    return align_up(static_cast<size_t>(tr::conv3_images().total_chunks) * sizeof(uint4), 256);
+}
 
 // In place: n pixels of BF16 hi + lo pairs [pixel][part][C] -> FP32 [pixel][C]
 // (same bytes per pixel; each thread reads a whole pixel before writing it).
@@ -102,13 +109,22 @@ extern "C" {
 
 size_t nsm_backward_workspace_bytes(int H, int W) {
     if (H <= 0 || W <= 0) return 0;
-    return align_up(sizeof(GatherParams), 256) + backward_floats(H, W) * sizeof(float);
+    return align_up(sizeof(GatherParams), 256) + conv3_image_bytes() + backward_floats(H, W) * sizeof(float);
 }
 
 nsm_status nsm_backward(nsm_ctx* ctx, const nsm_frame* frame, const float* dev_params, const float* grad_vis,
                         float* grad_params, float* grad_feat, float* vis_out, void* workspace,
                         size_t workspace_bytes, void* stream) {
+    return nsm_backward_ex(ctx, frame, dev_params, grad_vis, grad_params, grad_feat, vis_out, NSM_FP32, workspace,
+                           workspace_bytes, stream);
+}
+
+nsm_status nsm_backward_ex(nsm_ctx* ctx, const nsm_frame* frame, const float* dev_params, const float* grad_vis,
+                           float* grad_params, float* grad_feat, float* vis_out, nsm_precision precision,
+                           void* workspace, size_t workspace_bytes, void* stream) {
     if (!ctx) return fail(NSM_ERR_INVALID_ARG, "ctx is NULL");
+    if (precision != NSM_FP32 && precision != NSM_BF16)
+        return fail(NSM_ERR_UNSUPPORTED, "the backward's 3x3 layers run in the FP32 or the BF16 form");
     nsm_status s = check_frame(frame, true);
     if (s != NSM_OK) return s;
     const int H = frame->H, W = frame->W;
@@ -125,7 +141,8 @@ nsm_status nsm_backward(nsm_ctx* ctx, const nsm_frame* frame, const float* dev_p
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     GatherParams g = make_gather(frame);
     GatherParams* dgp = static_cast<GatherParams*>(workspace);
-    float* base = reinterpret_cast<float*>(static_cast<char*>(workspace) + align_up(sizeof(GatherParams), 256));
+    uint4* img = reinterpret_cast<uint4*>(static_cast<char*>(workspace) + align_up(sizeof(GatherParams), 256));
+    float* base = reinterpret_cast<float*>(reinterpret_cast<char*>(img) + conv3_image_bytes());
     cudaError_t e = cudaMemcpyAsync(dgp, &g, sizeof(g), cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return cuda_fail(e, "upload gather parameters");
     tr::Buffers b = tr::carve(base, 1, 1, H, W);
@@ -136,7 +153,10 @@ nsm_status nsm_backward(nsm_ctx* ctx, const nsm_frame* frame, const float* dev_p
         return cuda_fail(e, "copy cotangent");
     if (vis_out && (e = cudaMemcpyAsync(vis_out, b.vis, npx * 4, cudaMemcpyDeviceToDevice, st)) != cudaSuccess)
         return cuda_fail(e, "copy visibility");
-    if ((e = tr::backward(dev_params, grad_params, b, 1, H, W, grad_feat, st)) != cudaSuccess)
+    const bool tcb = precision == NSM_BF16;
+    if (tcb && (e = tr::conv3_pack(dev_params, img, st)) != cudaSuccess) return cuda_fail(e, "pack 3x3 images");
+    if ((e = tr::backward(dev_params, grad_params, b, 1, H, W, grad_feat, st, tcb ? img : nullptr, ctx->d_err)) !=
+        cudaSuccess)
         return cuda_fail(e, "backward");
     return NSM_OK;
 }
@@ -166,9 +186,11 @@ nsm_status nsm_train_state_create(nsm_ctx* ctx, const float* host_params, size_t
     s->ndesc = im.n;
     alloc(reinterpret_cast<void**>(&s->bf16), im.total * sizeof(uint16_t));
     alloc(&s->descs, pack_desc_bytes() * im.n);
+    alloc(reinterpret_cast<void**>(&s->conv3), static_cast<size_t>(tr::conv3_images().total_chunks) * sizeof(uint4));
     if (e == cudaSuccess) e = cudaMemcpy(s->descs, im.desc, pack_desc_bytes() * im.n, cudaMemcpyHostToDevice);
     s->detached_precision = NSM_FP32;
     s->forward_precision = NSM_FP32;
+    s->backward_precision = NSM_FP32;
     if (e == cudaSuccess) e = cudaMemcpy(s->theta, host_params, n * 4, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(s->m, 0, n * 4);
     if (e == cudaSuccess) e = cudaMemset(s->v, 0, n * 4);
@@ -185,7 +207,7 @@ void nsm_train_state_destroy(nsm_train_state* s) {
     if (!s) return;
     cudaFree(s->theta); cudaFree(s->m); cudaFree(s->v); cudaFree(s->grad);
     cudaFree(s->loss); cudaFree(s->gp); cudaFree(s->work);
-    cudaFree(s->bf16); cudaFree(s->descs);
+    cudaFree(s->bf16); cudaFree(s->descs); cudaFree(s->conv3);
     delete s;
 }
 
@@ -265,7 +287,11 @@ nsm_status nsm_train_grad(nsm_ctx* ctx, nsm_train_state* s, const nsm_batch* bt,
     if ((e = tr::loss_l1(b.vis, bt->target, bt->B, bt->T, npx, cfg->alpha, b.gvis, s->loss, cs)) != cudaSuccess)
         return cuda_fail(e, "loss");
     if ((e = cudaMemsetAsync(s->grad, 0, s->n * 4, cs)) != cudaSuccess) return cuda_fail(e, "grad reset");
-    if ((e = tr::backward(s->theta, s->grad, b, bt->B, H, W, nullptr, cs)) != cudaSuccess) return cuda_fail(e, "backward");
+    const bool tcb = s->backward_precision == NSM_BF16;
+    if (tcb && (e = tr::conv3_pack(s->theta, s->conv3, cs)) != cudaSuccess) return cuda_fail(e, "pack 3x3 images");
+    if ((e = tr::backward(s->theta, s->grad, b, bt->B, H, W, nullptr, cs, tcb ? s->conv3 : nullptr, ctx->d_err)) !=
+        cudaSuccess)
+        return cuda_fail(e, "backward");
     if (loss_out && (e = cudaMemcpyAsync(loss_out, s->loss, sizeof(float), cudaMemcpyDeviceToDevice, cs)) != cudaSuccess)
         return cuda_fail(e, "copy loss");
     return NSM_OK;
@@ -310,6 +336,14 @@ nsm_status nsm_train_state_set_forward_precision(nsm_train_state* s, nsm_precisi
     if (precision != NSM_FP32 && precision != NSM_BF16)
         return fail(NSM_ERR_UNSUPPORTED, "the target instances run in the FP32 or the BF16 form");
     s->forward_precision = precision;
+    return NSM_OK;
+}
+
+nsm_status nsm_train_state_set_backward_precision(nsm_train_state* s, nsm_precision precision) {
+    if (!s) return fail(NSM_ERR_INVALID_ARG, "state is NULL");
+    if (precision != NSM_FP32 && precision != NSM_BF16)
+        return fail(NSM_ERR_UNSUPPORTED, "the backward's 3x3 layers run in the FP32 or the BF16 form");
+    s->backward_precision = precision;
     return NSM_OK;
 }
 

@@ -23,7 +23,22 @@ Buffers carve(float* base, int N, int Nb, int H, int W);
 cudaError_t features_batch(const GatherParams* dev_params, int N, int H, int W, float* feat, cudaStream_t st);
 cudaError_t forward(const float* theta, const Buffers& b, int N, int Nb, int H, int W, cudaStream_t st);
 cudaError_t backward(const float* theta, float* grad, const Buffers& b, int Nb, int H, int W, float* gfeat,
-                     cudaStream_t st);
+                     cudaStream_t st, const uint4* img = nullptr, int* err = nullptr);
+// Tensor-core 3x3 convolutions of the backward (train_tc.cu): compensated
+// BF16 operands (hi + lo pairs), FP32 accumulation, FP32 NHWC in and out.
+// Images 2 l and 2 l + 1 are the l-th 3x3 layer (ENC0_3, ENC1_3, BOTT_3,
+// DEC1_3, DEC0_3) and its data gradient (transposed, flipped weights), as
+// 16-byte chunks at off[i] of one buffer of total_chunks chunks.
+constexpr int kConv3Images = 10;
+struct Conv3Images { int off[kConv3Images]; int total_chunks; };
+Conv3Images conv3_images();
+// Packs every image from the FP32 parameter vector (once per step).
+cudaError_t conv3_pack(const float* theta, uint4* img, cudaStream_t st);
+// y = conv3x3(x) (+ bias), zero padded; (cin, cout) one of the layers' shapes
+// or their transposes (cudaErrorInvalidValue otherwise); err: device error
+// word, set to 7 when a bounded wait gave up.
+cudaError_t conv3_tc(int cin, int cout, const float* x, int N, int H, int W, const uint4* img, const float* bias,
+                     float* y, int* err, cudaStream_t st);
 cudaError_t loss_l1(const float* vis, const float* target, int B, int T, size_t npx, float alpha, float* gvis,
                     float* loss, cudaStream_t st);
 cudaError_t adam(float* theta, const float* grad, float* m, float* v, size_t n, float lr, float b1, float b2,

@@ -167,3 +167,23 @@ def test_row_band_workspace_and_validation(lib):
     assert n >= nsm.nsm_infer_workspace_bytes(rows, W, nsm.NSM_BF16) + rows * W * 4
     assert nsm.nsm_infer_rows_workspace_bytes(H, W, 540, 540, 32, nsm.NSM_BF16) == 0
     assert lib.nsm_infer_rows(None, None, None, 0, 0, 4, 0, None, 0, None, None) == 1
+
+
+def test_host_validation_of_the_training_precision_entry_points(lib):
+    # rejected before any CUDA call: NULL state / context
+    typed = nsm._train_sigs()
+    for f in ("nsm_train_state_set_detached_precision", "nsm_train_state_set_forward_precision",
+              "nsm_train_state_set_backward_precision"):
+        assert getattr(typed, f)(None, nsm.NSM_BF16) == 1
+        assert b"state" in lib.nsm_last_error()
+    assert typed.nsm_backward_ex(None, None, None, None, None, None, None, nsm.NSM_BF16, None, 0, None) == 1
+    assert b"ctx" in lib.nsm_last_error()
+    # the backward's workspace also holds the 3x3 weight images of the tensor-core form
+    # (18,144 chunks of 16 bytes: 9 taps x K steps x 2 halves x 2 C_out rows per image)
+    chunks = 0
+    for ci, co in ((4, 16), (16, 32), (32, 64), (32, 32), (16, 16)):
+        for a, b in ((ci, co), (co, ci)):
+            chunks += 9 * ((a + 15) // 16) * 2 * 2 * max(b, 8)
+    assert chunks == 18144
+    small = nsm.nsm_backward_workspace_bytes(4, 4)
+    assert small >= chunks * 16

@@ -46,7 +46,7 @@ def _layer_slices():
     return out
 
 
-def _gpu_backward(ctx, f, theta, gvis):
+def _gpu_backward(ctx, f, theta, gvis, precision=None):
     df = DeviceFrame(f)
     params = torch.from_numpy(theta).cuda()
     gv = torch.from_numpy(gvis.astype(np.float32)).cuda()
@@ -54,8 +54,9 @@ def _gpu_backward(ctx, f, theta, gvis):
     gf = torch.empty((f.H, f.W, 4), device="cuda")
     vis = torch.empty((f.H, f.W), device="cuda")
     ws = torch.empty((nsm.nsm_backward_workspace_bytes(f.H, f.W),), dtype=torch.uint8, device="cuda")
-    nsm.nsm_backward(ctx, df.frame, params, gv, gp, ws, grad_feat=gf, vis_out=vis)
+    nsm.nsm_backward(ctx, df.frame, params, gv, gp, ws, grad_feat=gf, vis_out=vis, precision=precision)
     torch.cuda.synchronize()
+    ctx.check()
     return gp.cpu().numpy().astype(np.float64), gf.cpu().numpy().astype(np.float64), vis.cpu().numpy()
 
 
@@ -76,6 +77,89 @@ def test_backward_matches_oracle_adjoint(ctx, size):
         assert np.abs(a - b).max() <= 2e-4 * scale, (name, np.abs(a - b).max(), scale)
     scale = np.abs(ref_gf).max()
     assert np.abs(gf - ref_gf.transpose(1, 2, 0)).max() <= 2e-4 * scale
+
+
+def _relu_tie_columns(gvis, theta, t, tau=1e-5):
+    """ReLU masks a recomputation with ~2^-17 relative operand rounding may
+    decide either way: for every pre-activation (*_a3, *_a1) within tau of 0,
+    relative to its tensor's largest, the change of the FP64 adjoint's
+    (dtheta, dfeat) when that mask bit flips.  A correct gradient is the
+    adjoint plus a 0 / 1 combination of these columns."""
+    g0, f0 = N.backward(gvis, theta, t)
+    cg, cf = [], []
+    for k, v in t.items():
+        if not k.endswith(("_a3", "_a1")):
+            continue
+        m = np.abs(v).max()
+        for idx in zip(*np.nonzero(np.abs(v) < tau * m)):
+            v2 = v.copy()
+            v2[idx] = -v2[idx] if v2[idx] != 0 else -1e-300
+            g2, f2 = N.backward(gvis, theta, {**t, k: v2})
+            cg.append(g2 - g0)
+            cf.append((f2 - f0).ravel())
+    if not cg:
+        return g0, f0, np.zeros((g0.size, 0)), np.zeros((f0.size, 0))
+    return g0, f0, np.stack(cg, axis=1), np.stack(cf, axis=1)
+
+
+def _fit_flips(gp, gf, ref_g, ref_gf, Cg, Cf):
+    """Greedy 0 / 1 choice of the flipped masks (columns of _relu_tie_columns):
+    add, one at a time, the column that most reduces the squared residual, on
+    the even-indexed parameters and the feature gradient, each normalised by
+    its layer's largest entry (the odd-indexed half is left to check it)."""
+    even = np.arange(ref_g.size) % 2 == 0
+    rows = [(sl.start + np.nonzero(even[sl])[0], max(np.abs(ref_g[sl]).max(), 1e-12)) for _, sl in _layer_slices()]
+    fs = np.abs(ref_gf).max()
+    A = np.concatenate([Cg[i] / sc for i, sc in rows] + [Cf / fs])
+    r = np.concatenate([(gp - ref_g)[i] / sc for i, sc in rows] + [(gf - ref_gf) / fs])
+    sgn = np.zeros(Cg.shape[1])
+    norms = (A * A).sum(axis=0)
+    while True:
+        gain = 2.0 * (r @ A) - norms       # |r|^2 - |r - a_j|^2
+        gain[sgn > 0] = -np.inf
+        j = int(np.argmax(gain)) if gain.size else -1
+        if j < 0 or gain[j] <= 0.0:
+            break
+        sgn[j] = 1.0
+        r = r - A[:, j]
+    return sgn
+
+
+@pytest.mark.parametrize("size", [(32, 32), (36, 68), (40, 260)])
+def test_backward_bf16_convolutions_match_oracle_adjoint(ctx, size):
+    """The backward with its 3x3 recomputations and data gradients on the
+    tcgen05 kernels (compensated BF16 operands, FP32 accumulation) against the
+    FP64 adjoint, layer by layer and for the feature gradient.  The sizes span
+    several 128-pixel tiles with ragged tails at every level (260 = 2 x 128 + 4
+    columns at level 0, 130 at level 1) and rows that are not a multiple of the
+    tile's.  Each operand keeps ~2^-17 of relative rounding, which can flip the
+    recomputed ReLU mask of a pre-activation within ~1e-6 of 0: those flips
+    are fitted (0 / 1 per near-zero pre-activation, on the even-indexed
+    parameters), and the rest must meet the FP32 backward's bar on every
+    parameter and on the feature gradient."""
+    H, W = size
+    f = scenegen.soft_frame(H, W, 128, 128, 8, 31)
+    theta = _theta(1)
+    gvis = np.random.default_rng(2).standard_normal((H, W))
+    gp, gf, vis = _gpu_backward(ctx, f, theta, gvis, precision=nsm.NSM_BF16)
+    feat, _, _ = G.features(f.pos4, f.nrm4, f.sm, f.view_proj, f.light_pos, f.cam_pos, f.r_hat, f.z_far, f.bias)
+    th64 = theta.astype(np.float64)
+    ref_vis, t = N.forward(feat, th64, keep=True)
+    ref_g, ref_gf, Cg, Cf = _relu_tie_columns(gvis, th64, t)
+    assert np.abs(vis - ref_vis).max() < 1e-4
+    gf_flat = gf.transpose(2, 0, 1).ravel()
+    sgn = _fit_flips(gp, gf_flat, ref_g, ref_gf.ravel(), Cg, Cf)
+    print(f"near-zero pre-activations: {Cg.shape[1]}, fitted as flipped: {int(sgn.sum())}")
+    fit_g, fit_f = ref_g + Cg @ sgn, ref_gf.ravel() + Cf @ sgn
+    worst = 0.0
+    for name, sl in _layer_slices():
+        scale = max(np.abs(ref_g[sl]).max(), 1e-12)
+        err = np.abs(gp[sl] - fit_g[sl]).max() / scale
+        worst = max(worst, err)
+        assert err <= 2e-4, (name, err)
+    gerr = np.abs(gf_flat - fit_f).max() / np.abs(ref_gf).max()
+    print(f"worst per-layer gradient error {worst:.2e}, feature gradient {gerr:.2e} (relative to the largest)")
+    assert gerr <= 2e-4
 
 
 def test_backward_central_finite_differences(ctx):
@@ -161,13 +245,18 @@ def _near_tie_split(feats, targets, theta, alpha, tau=1e-5, detached=None, targe
     return g_rest, C
 
 
-def test_train_step_matches_oracle(ctx):
+@pytest.mark.parametrize("backward", ["fp32", "bf16"])
+def test_train_step_matches_oracle(ctx, backward):
     """One temporal-window step (B = 2 items, T = 3 instances, 32 x 32 crops):
-    loss, gradient and Adam-updated weights against the oracle's train_step."""
+    loss, gradient and Adam-updated weights against the oracle's train_step;
+    the backward's 3x3 layers on the FP32 kernels or on the tcgen05 kernels
+    (compensated BF16 operands)."""
     B, T, H, W, S = 2, 3, 32, 32, 128
     frames, targets = train_batch_frames(B, T, H, W, S, seed=41)
     theta = _theta(8)
     st = nsm.TrainState(ctx, theta, B, T, H, W)
+    if backward == "bf16":
+        st.set_backward_precision(nsm.NSM_BF16)
     bt = device_batch(frames, targets)
     loss = torch.zeros(1, device="cuda")
     lr = 1e-3
@@ -329,7 +418,8 @@ def test_train_step_with_bf16_detached_instances(ctx):
     st.close()
 
 
-def test_train_step_with_every_forward_on_the_tensor_cores(ctx):
+@pytest.mark.parametrize("backward", ["fp32", "bf16"])
+def test_train_step_with_every_forward_on_the_tensor_cores(ctx, backward):
     """x_0 and the detached instances on the BF16 tcgen05 stage kernels (the
     backward FP32 from the converted checkpoints): every visibility follows the
     BF16 rounding model; loss and gradient match the oracle's with x_0's
@@ -342,6 +432,8 @@ def test_train_step_with_every_forward_on_the_tensor_cores(ctx):
     st = nsm.TrainState(ctx, theta, B, T, H, W)
     st.set_detached_precision(nsm.NSM_BF16)
     st.set_forward_precision(nsm.NSM_BF16)
+    if backward == "bf16":
+        st.set_backward_precision(nsm.NSM_BF16)
     bt = device_batch(frames, targets)
     loss = torch.zeros(1, device="cuda")
     lr = 1e-3
