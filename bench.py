@@ -399,7 +399,7 @@ def extra_train(nsm, scenegen, torch, device, theta, reps):
     ctx.check()
     ms_tc = sum(ev3[2 * k].elapsed_time(ev3[2 * k + 1]) for k in range(reps)) / reps
     loss_tc = float(loss.item())
-    # and with the backward's 3x3 recomputations and data gradients on the tensor cores
+    # and with the backward's 3x3 convolutions and every weight gradient on the tensor cores
     state_bf.set_backward_precision(nsm.NSM_BF16)
     for _ in range(3):
         state_bf.step(batch, loss_out=loss)
@@ -429,11 +429,14 @@ def extra_train(nsm, scenegen, torch, device, theta, reps):
             "bf16_forward": {"ms_per_step": ms_tc, "instances_per_s": B * T / (ms_tc * 1e-3), "loss_last": loss_tc,
                              "form": "every forward pass (x_0 with its checkpoints, x_1, x_2) on the tcgen05 stage "
                                      "kernels with BF16-pair activations; the backward FP32 with recomputation"},
-            "bf16_forward_and_conv3_backward": {
+            "bf16_forward_and_backward": {
                 "ms_per_step": ms_tb, "instances_per_s": B * T / (ms_tb * 1e-3), "loss_last": loss_tb,
-                "form": "every forward pass on the tcgen05 stage kernels, and the backward's 3x3 recomputations "
-                        "and data gradients on tcgen05 implicit GEMMs (compensated BF16 operands, FP32 "
-                        "accumulation); weight gradients and 1x1 layers FP32"},
+                "achieved_tflops": flop / (ms_tb * 1e-3) / 1e12,
+                "form": "every forward pass on the tcgen05 stage kernels; in the backward the 3x3 recomputations "
+                        "and data gradients as tcgen05 implicit GEMMs and every weight gradient as a tcgen05 "
+                        "pixel-reduction GEMM (compensated BF16 operands, FP32 accumulation in tensor memory, "
+                        "per-CTA slots summed in a fixed order: the same gradient bits every run); 1x1 "
+                        "recomputations and data gradients, pooling / up-sampling adjoints and Adam FP32"},
             "algorithmic_gflop": flop / 1e9, "achieved_tflops": tflops,
             "roofline": {"bound": "alu", "peak_tflops": peak, "frac": tflops / peak,
                          "peak_src": "128 FP32 lanes x 2 FLOP x SMs x max SM clock"},

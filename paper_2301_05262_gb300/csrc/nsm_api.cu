@@ -1,3 +1,4 @@
+#include <algorithm>
 // C ABI of the library (include/nsm.h): argument validation, weight upload,
 // workspace carving and dispatch to the kernels.
 #include <cstdarg>
@@ -93,6 +94,27 @@ cudaError_t scratch_pool(cudaMemPool_t* out) {
     }
     *out = pools[dev];
     return cudaSuccess;
+}
+
+int resident_ctas_per_sm(const void* func, int threads, size_t dyn_smem) {
+    cudaFuncAttributes fa{};
+    int dev = 0, smem_sm = 0, resv = 0, regs_sm = 0, thr_sm = 0, blk_sm = 0;
+    if (cudaFuncGetAttributes(&fa, func) != cudaSuccess || cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&resv, cudaDevAttrReservedSharedMemoryPerBlock, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&thr_sm, cudaDevAttrMaxThreadsPerMultiProcessor, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&blk_sm, cudaDevAttrMaxBlocksPerMultiprocessor, dev) != cudaSuccess)
+        return 1;
+    const size_t smem = dyn_smem + fa.sharedSizeBytes + static_cast<size_t>(resv);
+    const int warps = (threads + 31) / 32;
+    // registers are allocated per warp in units of 256 (8 per thread, rounded up)
+    const int regs_warp = (fa.numRegs * 32 + 255) / 256 * 256;
+    int n = blk_sm;
+    if (smem > 0) n = std::min<long long>(n, static_cast<long long>(smem_sm) / static_cast<long long>(smem));
+    if (regs_warp > 0) n = std::min(n, regs_sm / (regs_warp * warps));
+    n = std::min(n, thr_sm / (32 * warps));
+    return n < 1 ? 1 : n;
 }
 
 int num_sms() {

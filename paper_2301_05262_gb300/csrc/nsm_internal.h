@@ -30,6 +30,13 @@ LayerOffsets layer_offsets_s2d();
 constexpr int kS2dHeadOut = 4;
 
 int num_sms();
+// CTAs of `func` (block of `threads`, `dyn_smem` bytes of dynamic shared
+// memory) that fit on one SM of the current device, counted from the
+// function's registers and shared memory against the SM's registers, shared
+// memory (less the per-block reservation), threads and block slots.  The
+// tcgen05 kernels size their grids with this: the runtime's occupancy query
+// answers one CTA per SM for them where several fit.
+int resident_ctas_per_sm(const void* func, int threads, size_t dyn_smem);
 // The library's stream-ordered scratch pool for the current device.
 cudaError_t scratch_pool(cudaMemPool_t* out);
 

@@ -705,7 +705,7 @@ __global__ void head_fwd_kernel(const float* __restrict__ a1, const float* __res
 // dwh[c] += sum g_logit relu(a1[c]); dbh += sum g_logit
 __global__ void head_bwd_kernel(const float* __restrict__ a1, const float* __restrict__ vis,
                                 const float* __restrict__ gvis, const float* __restrict__ wh, size_t npx,
-                                float* __restrict__ ga1, float* __restrict__ dwh) {
+                                float* __restrict__ ga1, float* __restrict__ dwh, float* __restrict__ slots) {
     __shared__ float red[17][8];
     float part[17];
 #pragma unroll
@@ -733,7 +733,8 @@ __global__ void head_bwd_kernel(const float* __restrict__ a1, const float* __res
     if (threadIdx.x < 17) {
         float s = 0.f;
         for (int w = 0; w < static_cast<int>(blockDim.x / 32); ++w) s += red[threadIdx.x][w];
-        atomicAdd(dwh + threadIdx.x, s);
+        if (slots) slots[blockIdx.x * 17 + threadIdx.x] = s;  // slot of this block, summed in order afterwards
+        else atomicAdd(dwh + threadIdx.x, s);
     }
 }
 
@@ -838,7 +839,8 @@ size_t workspace_floats(int N, int Nb, int H, int W) {
     // per-level scratch (largest level: level 0): x_in, a3, a1, g_a1, g_a3, g_x, g_low, g_skip
     f += Nb * p0 * 16 * 6 + Nb * p1 * 32 * 2;
     f += Nb * p0 * 16;          // conv scratch (level-0 1x1 input gradient)
-    return f + 64;
+    f += kWgPartFloats;         // weight-gradient partial sums
+    return f + 128;
 }
 
 Buffers carve(float* base, int N, int Nb, int H, int W) {
@@ -863,6 +865,7 @@ Buffers carve(float* base, int N, int Nb, int H, int W) {
     b.glo = take(Nb * p1 * 32);
     b.gskip = take(Nb * p1 * 32);
     b.gtmp = take(Nb * p0 * 16);
+    b.wpart = take(kWgPartFloats);
     return b;
 }
 
@@ -913,7 +916,9 @@ cudaError_t forward(const float* th, const Buffers& b, int N, int Nb, int H, int
 // layout, accumulated), recomputing each level from its checkpoint.
 // With gfeat != nullptr also the feature gradient [Nb][H][W][4].  With img
 // != nullptr (the conv3_pack images of th) the 3x3 recomputations and data
-// gradients run on the tensor cores (conv3_tc), else on the FP32 kernels.
+// gradients (conv3_tc) and every weight gradient (wgrad_tc, the head's by
+// per-block slots) run on the tensor cores, reduced in a fixed order, else on
+// the FP32 kernels.
 cudaError_t backward(const float* th, float* grad, const Buffers& b, int Nb, int H, int W, float* gfeat,
                      cudaStream_t st, const uint4* img, int* err) {
     const Conv3Images im = conv3_images();
@@ -929,11 +934,17 @@ cudaError_t backward(const float* th, float* grad, const Buffers& b, int Nb, int
     if (img) NSM_TRY(conv3_tc(16, 16, b.xin, n, H, W, I(8), L.b3, b.a3, err, st));
     else NSM_TRY((conv_fwd<16, 16, 3>(b.xin, nullptr, 0, n, H, W, L.w3, 0, L.b3, nullptr, b.a3, st)));
     NSM_TRY((conv_fwd<16, 16, 1>(b.a3, nullptr, 1, n, H, W, L.w1, 0, L.b1, nullptr, b.a1, st)));
-    head_bwd_kernel<<<ew_grid(n * p0), 256, 0, st>>>(b.a1, b.vis, b.gvis, th + o.w[HEAD], n * p0, b.ga1,
-                                                     grad + o.w[HEAD]);
-    NSM_TRY((conv_wgrad<16, 16, 1>(b.a3, 1, b.ga1, nullptr, n, H, W, L.dw1, L.db1, st)));
+    {
+        const int hb = ew_grid(n * p0);
+        head_bwd_kernel<<<hb, 256, 0, st>>>(b.a1, b.vis, b.gvis, th + o.w[HEAD], n * p0, b.ga1, grad + o.w[HEAD],
+                                            img ? b.wpart : nullptr);
+        if (img) NSM_TRY(slot_reduce(b.wpart, hb, 17, 17, grad + o.w[HEAD], nullptr, st));
+    }
+    if (img) NSM_TRY(wgrad_tc(16, 16, 1, b.a3, 1, b.ga1, nullptr, n, H, W, b.wpart, L.dw1, L.db1, err, st));
+    else NSM_TRY((conv_wgrad<16, 16, 1>(b.a3, 1, b.ga1, nullptr, n, H, W, L.dw1, L.db1, st)));
     NSM_TRY((conv_fwd<16, 16, 1>(b.ga1, nullptr, 0, n, H, W, L.w1, 1, nullptr, b.a3, b.ga3, st)));
-    NSM_TRY((conv_wgrad<16, 16, 3>(b.xin, 0, b.ga3, nullptr, n, H, W, L.dw3, L.db3, st)));
+    if (img) NSM_TRY(wgrad_tc(16, 16, 3, b.xin, 0, b.ga3, nullptr, n, H, W, b.wpart, L.dw3, L.db3, err, st));
+    else NSM_TRY((conv_wgrad<16, 16, 3>(b.xin, 0, b.ga3, nullptr, n, H, W, L.dw3, L.db3, st)));
     if (img) NSM_TRY(conv3_tc(16, 16, b.ga3, n, H, W, I(9), nullptr, b.gx, err, st));
     else NSM_TRY((conv_fwd<16, 16, 3>(b.ga3, nullptr, 0, n, H, W, L.w3, 1, nullptr, nullptr, b.gx, st)));
     up_adj_kernel<<<ew_grid(n * p1 * 16), 256, 0, st>>>(b.gx, n, H, W, 16, b.glo);  // g d1 [n][H1][W1][16]
@@ -944,9 +955,11 @@ cudaError_t backward(const float* th, float* grad, const Buffers& b, int Nb, int
     else NSM_TRY((conv_fwd<32, 32, 3, 16>(b.xin, nullptr, 0, n, H1, W1, L.w3, 0, L.b3, nullptr, b.a3, st)));
     NSM_TRY((conv_fwd<32, 16, 1>(b.a3, nullptr, 1, n, H1, W1, L.w1, 0, L.b1, nullptr, b.a1, st)));
     // g_a1 = g_d1 (a1 > 0)
-    NSM_TRY((conv_wgrad<32, 16, 1>(b.a3, 1, b.glo, b.a1, n, H1, W1, L.dw1, L.db1, st)));
+    if (img) NSM_TRY(wgrad_tc(32, 16, 1, b.a3, 1, b.glo, b.a1, n, H1, W1, b.wpart, L.dw1, L.db1, err, st));
+    else NSM_TRY((conv_wgrad<32, 16, 1>(b.a3, 1, b.glo, b.a1, n, H1, W1, L.dw1, L.db1, st)));
     NSM_TRY((conv_fwd<16, 32, 1>(b.glo, b.a1, 0, n, H1, W1, L.w1, 1, nullptr, b.a3, b.ga3, st)));
-    NSM_TRY((conv_wgrad<32, 32, 3>(b.xin, 0, b.ga3, nullptr, n, H1, W1, L.dw3, L.db3, st)));
+    if (img) NSM_TRY(wgrad_tc(32, 32, 3, b.xin, 0, b.ga3, nullptr, n, H1, W1, b.wpart, L.dw3, L.db3, err, st));
+    else NSM_TRY((conv_wgrad<32, 32, 3>(b.xin, 0, b.ga3, nullptr, n, H1, W1, L.dw3, L.db3, st)));
     if (img) NSM_TRY(conv3_tc(32, 32, b.ga3, n, H1, W1, I(7), nullptr, b.gskip, err, st));  // g x1
     else NSM_TRY((conv_fwd<32, 32, 3, 16>(b.ga3, nullptr, 0, n, H1, W1, L.w3, 1, nullptr, nullptr, b.gskip, st)));
     up_adj_kernel<<<ew_grid(n * p2 * 32), 256, 0, st>>>(b.gskip, n, H1, W1, 32, b.glo);  // g bo [n][H2][W2][32]
@@ -955,9 +968,11 @@ cudaError_t backward(const float* th, float* grad, const Buffers& b, int Nb, int
     if (img) NSM_TRY(conv3_tc(32, 64, b.p1, n, H2, W2, I(4), L.b3, b.a3, err, st));
     else NSM_TRY((conv_fwd<32, 64, 3, 16>(b.p1, nullptr, 0, n, H2, W2, L.w3, 0, L.b3, nullptr, b.a3, st)));
     NSM_TRY((conv_fwd<64, 32, 1>(b.a3, nullptr, 1, n, H2, W2, L.w1, 0, L.b1, nullptr, b.a1, st)));
-    NSM_TRY((conv_wgrad<64, 32, 1>(b.a3, 1, b.glo, b.a1, n, H2, W2, L.dw1, L.db1, st)));
+    if (img) NSM_TRY(wgrad_tc(64, 32, 1, b.a3, 1, b.glo, b.a1, n, H2, W2, b.wpart, L.dw1, L.db1, err, st));
+    else NSM_TRY((conv_wgrad<64, 32, 1>(b.a3, 1, b.glo, b.a1, n, H2, W2, L.dw1, L.db1, st)));
     NSM_TRY((conv_fwd<32, 64, 1>(b.glo, b.a1, 0, n, H2, W2, L.w1, 1, nullptr, b.a3, b.ga3, st)));
-    NSM_TRY((conv_wgrad<32, 64, 3>(b.p1, 0, b.ga3, nullptr, n, H2, W2, L.dw3, L.db3, st)));
+    if (img) NSM_TRY(wgrad_tc(32, 64, 3, b.p1, 0, b.ga3, nullptr, n, H2, W2, b.wpart, L.dw3, L.db3, err, st));
+    else NSM_TRY((conv_wgrad<32, 64, 3>(b.p1, 0, b.ga3, nullptr, n, H2, W2, L.dw3, L.db3, st)));
     if (img) NSM_TRY(conv3_tc(64, 32, b.ga3, n, H2, W2, I(5), nullptr, b.gx, err, st));  // g p1
     else NSM_TRY((conv_fwd<64, 32, 3, 16>(b.ga3, nullptr, 0, n, H2, W2, L.w3, 1, nullptr, nullptr, b.gx, st)));
     // ---- level 1 encoder: g_h1 = pool_adj(g p1) + g s1 ; recompute a3 = conv3(e0), a1
@@ -967,9 +982,11 @@ cudaError_t backward(const float* th, float* grad, const Buffers& b, int Nb, int
     if (img) NSM_TRY(conv3_tc(16, 32, b.e0, n, H1, W1, I(2), L.b3, b.a3, err, st));
     else NSM_TRY((conv_fwd<16, 32, 3>(b.e0, nullptr, 0, n, H1, W1, L.w3, 0, L.b3, nullptr, b.a3, st)));
     NSM_TRY((conv_fwd<32, 32, 1>(b.a3, nullptr, 1, n, H1, W1, L.w1, 0, L.b1, nullptr, b.a1, st)));
-    NSM_TRY((conv_wgrad<32, 32, 1>(b.a3, 1, b.glo, b.a1, n, H1, W1, L.dw1, L.db1, st)));
+    if (img) NSM_TRY(wgrad_tc(32, 32, 1, b.a3, 1, b.glo, b.a1, n, H1, W1, b.wpart, L.dw1, L.db1, err, st));
+    else NSM_TRY((conv_wgrad<32, 32, 1>(b.a3, 1, b.glo, b.a1, n, H1, W1, L.dw1, L.db1, st)));
     NSM_TRY((conv_fwd<32, 32, 1>(b.glo, b.a1, 0, n, H1, W1, L.w1, 1, nullptr, b.a3, b.ga3, st)));
-    NSM_TRY((conv_wgrad<16, 32, 3>(b.e0, 0, b.ga3, nullptr, n, H1, W1, L.dw3, L.db3, st)));
+    if (img) NSM_TRY(wgrad_tc(16, 32, 3, b.e0, 0, b.ga3, nullptr, n, H1, W1, b.wpart, L.dw3, L.db3, err, st));
+    else NSM_TRY((conv_wgrad<16, 32, 3>(b.e0, 0, b.ga3, nullptr, n, H1, W1, L.dw3, L.db3, st)));
     if (img) NSM_TRY(conv3_tc(32, 16, b.ga3, n, H1, W1, I(3), nullptr, b.gx, err, st));  // g e0
     else NSM_TRY((conv_fwd<32, 16, 3>(b.ga3, nullptr, 0, n, H1, W1, L.w3, 1, nullptr, nullptr, b.gx, st)));
     // ---- level 0 encoder: g_h1 = pool_adj(g e0); recompute a3 = conv3(feat), a1
@@ -978,9 +995,11 @@ cudaError_t backward(const float* th, float* grad, const Buffers& b, int Nb, int
     if (img) NSM_TRY(conv3_tc(4, 16, b.feat, n, H, W, I(0), L.b3, b.a3, err, st));
     else NSM_TRY((conv_fwd<4, 16, 3>(b.feat, nullptr, 0, n, H, W, L.w3, 0, L.b3, nullptr, b.a3, st)));
     NSM_TRY((conv_fwd<16, 16, 1>(b.a3, nullptr, 1, n, H, W, L.w1, 0, L.b1, nullptr, b.a1, st)));
-    NSM_TRY((conv_wgrad<16, 16, 1>(b.a3, 1, b.gtmp, b.a1, n, H, W, L.dw1, L.db1, st)));
+    if (img) NSM_TRY(wgrad_tc(16, 16, 1, b.a3, 1, b.gtmp, b.a1, n, H, W, b.wpart, L.dw1, L.db1, err, st));
+    else NSM_TRY((conv_wgrad<16, 16, 1>(b.a3, 1, b.gtmp, b.a1, n, H, W, L.dw1, L.db1, st)));
     NSM_TRY((conv_fwd<16, 16, 1>(b.gtmp, b.a1, 0, n, H, W, L.w1, 1, nullptr, b.a3, b.ga3, st)));
-    NSM_TRY((conv_wgrad<4, 16, 3>(b.feat, 0, b.ga3, nullptr, n, H, W, L.dw3, L.db3, st)));
+    if (img) NSM_TRY(wgrad_tc(4, 16, 3, b.feat, 0, b.ga3, nullptr, n, H, W, b.wpart, L.dw3, L.db3, err, st));
+    else NSM_TRY((conv_wgrad<4, 16, 3>(b.feat, 0, b.ga3, nullptr, n, H, W, L.dw3, L.db3, st)));
     if (gfeat && img) NSM_TRY(conv3_tc(16, 4, b.ga3, n, H, W, I(1), nullptr, gfeat, err, st));
     else if (gfeat) NSM_TRY((conv_fwd<16, 4, 3>(b.ga3, nullptr, 0, n, H, W, L.w3, 1, nullptr, nullptr, gfeat, st)));
     return cudaGetLastError();

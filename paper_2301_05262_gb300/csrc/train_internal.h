@@ -16,7 +16,11 @@ struct Buffers {
     float *feat, *e0, *s1, *p1, *bo, *d1, *vis;
     float *gvis;
     float *xin, *a3, *a1, *ga1, *ga3, *gx, *glo, *gskip, *gtmp;
+    float* wpart;  // per-CTA partial sums of the tensor-core weight gradients (kWgPartFloats)
 };
+
+// Floats of the partial-sum slots of one weight-gradient launch (8 MiB).
+constexpr long long kWgPartFloats = 1ll << 21;
 
 size_t workspace_floats(int N, int Nb, int H, int W);
 Buffers carve(float* base, int N, int Nb, int H, int W);
@@ -39,6 +43,17 @@ cudaError_t conv3_pack(const float* theta, uint4* img, cudaStream_t st);
 // word, set to 7 when a bounded wait gave up.
 cudaError_t conv3_tc(int cin, int cout, const float* x, int N, int H, int W, const uint4* img, const float* bias,
                      float* y, int* err, cudaStream_t st);
+// Tensor-core weight gradients (train_wgrad.cu): dW += sum_p g~[p][o] x~[p + tap][c]
+// (OIHW), db += sum_p g~[p][o], x~ = relu(x) if relu_in, g~ = g (m > 0) if gm;
+// k = 3 (zero padded) or 1.  Compensated BF16 operands, FP32 accumulation in
+// tensor memory, per-CTA partial sums in part (kWgPartFloats floats) added in a
+// fixed order: no atomics.  (cin, cout, k) one of the network's layers
+// (cudaErrorInvalidValue otherwise); err: device error word, set to 8 when a
+// bounded wait gave up.
+cudaError_t wgrad_tc(int cin, int cout, int k, const float* x, int relu_in, const float* g, const float* gm, int N,
+                     int H, int W, float* part, float* dW, float* db, int* err, cudaStream_t st);
+// dW[e] += sum_s part[s][e] for e < nw, db[e - nw] += ... for nw <= e < entries, s in order.
+cudaError_t slot_reduce(const float* part, int slots, int entries, int nw, float* dW, float* db, cudaStream_t st);
 cudaError_t loss_l1(const float* vis, const float* target, int B, int T, size_t npx, float alpha, float* gvis,
                     float* loss, cudaStream_t st);
 cudaError_t adam(float* theta, const float* grad, float* m, float* v, size_t n, float lr, float b1, float b2,

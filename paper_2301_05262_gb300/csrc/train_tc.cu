@@ -122,16 +122,6 @@ __device__ __forceinline__ void split8(const float* f, uint4& hi, uint4& lo) {
     lo = make_uint4(l[0], l[1], l[2], l[3]);
 }
 
-// 8 columns of 32 lanes (the x16 / x32 forms are in tc_common.cuh)
-__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
-    uint32_t r[8];
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
-                 : "r"(taddr));
-#pragma unroll
-    for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
-}
-
 constexpr int kConv3Threads = 256;
 constexpr int kConv3ErrCode = 7;  // error word value of a wait in conv3_tc_kernel that gave up
 
@@ -313,13 +303,15 @@ static cudaError_t launch_conv3(const float* x, int N, int H, int W, const uint4
         cudaError_t e = cudaFuncSetAttribute(conv3_tc_kernel<CIN, COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              static_cast<int>(C::BYTES));
         if (e != cudaSuccess) return e;
+        // all of the unified L1 / shared storage as shared memory: two to four CTAs per SM
+        e = cudaFuncSetAttribute(conv3_tc_kernel<CIN, COUT>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 cudaSharedmemCarveoutMaxShared);
+        if (e != cudaSuccess) return e;
         int dev = 0, sms = 0, per_sm = 0;
         if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
         if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, conv3_tc_kernel<CIN, COUT>, kConv3Threads,
-                                                               C::BYTES)) != cudaSuccess)
-            return e;
-        if (per_sm < 1) return cudaErrorInvalidConfiguration;
+        per_sm = resident_ctas_per_sm(reinterpret_cast<const void*>(conv3_tc_kernel<CIN, COUT>), kConv3Threads,
+                                      C::BYTES);
         grid_cap = sms * (per_sm < C::TMEM_CAP ? per_sm : C::TMEM_CAP);
     }
     const long long tiles = static_cast<long long>(N) * ((H + C::R - 1) / C::R) * ((W + kTileM - 1) / kTileM);

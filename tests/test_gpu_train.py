@@ -127,12 +127,14 @@ def _fit_flips(gp, gf, ref_g, ref_gf, Cg, Cf):
 
 @pytest.mark.parametrize("size", [(32, 32), (36, 68), (40, 260)])
 def test_backward_bf16_convolutions_match_oracle_adjoint(ctx, size):
-    """The backward with its 3x3 recomputations and data gradients on the
-    tcgen05 kernels (compensated BF16 operands, FP32 accumulation) against the
-    FP64 adjoint, layer by layer and for the feature gradient.  The sizes span
+    """The backward with its 3x3 recomputations, data gradients and every
+    weight gradient on the tcgen05 kernels (compensated BF16 operands, FP32
+    accumulation, per-CTA slots added in a fixed order) against the FP64
+    adjoint, layer by layer and for the feature gradient.  The sizes span
     several 128-pixel tiles with ragged tails at every level (260 = 2 x 128 + 4
-    columns at level 0, 130 at level 1) and rows that are not a multiple of the
-    tile's.  Each operand keeps ~2^-17 of relative rounding, which can flip the
+    columns at level 0, 130 at level 1; 260 = 8 x 32 + 4 and 130 = 8 x 16 + 2
+    columns of the weight-gradient tiles) and rows that are not a multiple of
+    the tiles'.  Each operand keeps ~2^-17 of relative rounding, which can flip the
     recomputed ReLU mask of a pre-activation within ~1e-6 of 0: those flips
     are fitted (0 / 1 per near-zero pre-activation, on the even-indexed
     parameters), and the rest must meet the FP32 backward's bar on every
@@ -160,6 +162,36 @@ def test_backward_bf16_convolutions_match_oracle_adjoint(ctx, size):
     gerr = np.abs(gf_flat - fit_f).max() / np.abs(ref_gf).max()
     print(f"worst per-layer gradient error {worst:.2e}, feature gradient {gerr:.2e} (relative to the largest)")
     assert gerr <= 2e-4
+
+
+def test_bf16_backward_gradient_is_the_same_bits_every_run(ctx):
+    """With the backward on the tensor cores no gradient is summed by atomics:
+    every weight gradient (and the head's) is reduced from per-CTA slots in a
+    fixed order, so two steps' gradients from the same state and batch are
+    bit-identical.  B = 8 items of 128 x 128 crops: hundreds of CTAs at every
+    level.  The FP32 backward, whose weight gradients are summed by atomics,
+    agrees with it to FP32 accuracy."""
+    B, T, H, W, S = 8, 1, 128, 128, 256
+    frames, targets = train_batch_frames(B, T, H, W, S, seed=47)
+    theta = _theta(10)
+    bt = device_batch(frames, targets)
+    grads = []
+    for prec in (nsm.NSM_BF16, nsm.NSM_BF16, nsm.NSM_FP32):
+        st = nsm.TrainState(ctx, theta, B, T, H, W)
+        st.set_backward_precision(prec)
+        for _ in range(2):
+            st.grad(bt, alpha=0.9)
+            g = torch.empty(theta.size, device="cuda")
+            st.read(1, g)
+            torch.cuda.synchronize()
+            grads.append(g.cpu().numpy())
+        st.close()
+    a, b, c, d, e, _ = grads
+    for other in (b, c, d):
+        assert np.array_equal(a, other)
+    for name, sl in _layer_slices():
+        scale = max(np.abs(e[sl]).max(), 1e-12)
+        assert np.abs(a[sl] - e[sl]).max() <= 1e-3 * scale, name
 
 
 def test_backward_central_finite_differences(ctx):
