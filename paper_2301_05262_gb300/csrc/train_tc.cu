@@ -23,7 +23,8 @@
 //             pack_conv3_kernel into the same chunk layout and staged once
 //             per CTA
 // Each CTA loops over tiles: all threads stage the tile (FP32 -> hi + lo),
-// one thread issues the tile's MMAs and commits them to an mbarrier, all
+// one thread issues the tile's MMAs and commits them to an mbarrier while
+// every thread loads part of the next tile into registers, then all
 // threads read the accumulators out (hi + lo parts summed, bias added) and
 // store FP32.  Shared memory and TMEM are sized so that two to four CTAs
 // share an SM and one CTA's staging overlaps another's MMAs and stores.
@@ -125,29 +126,64 @@ __device__ __forceinline__ void split8(const float* f, uint4& hi, uint4& lo) {
 constexpr int kConv3Threads = 256;
 constexpr int kConv3ErrCode = 7;  // error word value of a wait in conv3_tc_kernel that gave up
 
-// Stage tile (n, y0, x0) with its halo: staged row sr = image row y0 - 1 + sr,
-// staged pixel sp = column x0 - 1 + sp; zeros outside the image and beyond C_in.
+// One tile's input with its halo, item by item: thread t takes items t,
+// t + 256, ... (item = staged row sr, staged pixel sp, channel group g of 8
+// channels); staged row sr = image row y0 - 1 + sr, staged pixel sp = column
+// x0 - 1 + sp; zeros outside the image and beyond C_in.  The first PS items of
+// a thread are loaded into registers one tile ahead (in flight while the
+// current tile's MMAs run), the rest when the tile is staged; a thread issues
+// all of a phase's loads before it uses any.
 template <int CIN, int COUT>
-__device__ __forceinline__ void conv3_stage(uint32_t sbase, const float* __restrict__ x, int n, int H, int W, int y0,
-                                            int x0) {
+struct Conv3Regs {
     using C = Conv3Cfg<CIN, COUT>;
-    constexpr int ITEMS = C::SR * C::SP * C::G;
-    for (int i = threadIdx.x; i < ITEMS; i += kConv3Threads) {
+    static constexpr int ITEMS = C::SR * C::SP * C::G;
+    static constexpr int S = (ITEMS + kConv3Threads - 1) / kConv3Threads;
+    static constexpr int PS = S < 4 ? S : 4;  // items loaded ahead (registers)
+    float4 a[PS], b[PS];
+};
+
+template <int CIN, int COUT>
+__device__ __forceinline__ void conv3_item_load(const float* __restrict__ x, int i, int n, int H, int W, int y0,
+                                                int x0, float4& a, float4& b) {
+    using C = Conv3Cfg<CIN, COUT>;
+    const int g = i % C::G, rest = i / C::G;
+    const int sp = rest % C::SP, sr = rest / C::SP;
+    const int yy = y0 - 1 + sr, xx = x0 - 1 + sp;
+    const bool in = i < Conv3Regs<CIN, COUT>::ITEMS && yy >= 0 && yy < H && xx >= 0 && xx < W && 8 * g < CIN;
+    const float4* p = reinterpret_cast<const float4*>(
+        x + ((static_cast<size_t>(n) * H + (in ? yy : 0)) * W + (in ? xx : 0)) * CIN + (in ? 8 * g : 0));
+    const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+    a = in ? __ldg(p) : z;
+    b = (in && CIN >= 8) ? __ldg(p + 1) : z;
+}
+
+template <int CIN, int COUT>
+__device__ __forceinline__ void conv3_load(Conv3Regs<CIN, COUT>& R, const float* __restrict__ x, int n, int H, int W,
+                                           int y0, int x0) {
+#pragma unroll
+    for (int s = 0; s < Conv3Regs<CIN, COUT>::PS; ++s)
+        conv3_item_load<CIN, COUT>(x, threadIdx.x + s * kConv3Threads, n, H, W, y0, x0, R.a[s], R.b[s]);
+}
+
+template <int CIN, int COUT>
+__device__ __forceinline__ void conv3_store(const Conv3Regs<CIN, COUT>& R, uint32_t sbase, const float* __restrict__ x,
+                                            int n, int H, int W, int y0, int x0) {
+    using C = Conv3Cfg<CIN, COUT>;
+    using RT = Conv3Regs<CIN, COUT>;
+    constexpr int NL = RT::S - RT::PS;  // items loaded now
+    float4 la[NL > 0 ? NL : 1], lb[NL > 0 ? NL : 1];
+#pragma unroll
+    for (int s = 0; s < NL; ++s)
+        conv3_item_load<CIN, COUT>(x, threadIdx.x + (RT::PS + s) * kConv3Threads, n, H, W, y0, x0, la[s], lb[s]);
+#pragma unroll
+    for (int s = 0; s < RT::S; ++s) {
+        const int i = threadIdx.x + s * kConv3Threads;
+        if (i >= RT::ITEMS) break;
         const int g = i % C::G, rest = i / C::G;
         const int sp = rest % C::SP, sr = rest / C::SP;
-        const int yy = y0 - 1 + sr, xx = x0 - 1 + sp;
-        float f[8];
-#pragma unroll
-        for (int j = 0; j < 8; ++j) f[j] = 0.f;
-        if (yy >= 0 && yy < H && xx >= 0 && xx < W && 8 * g < CIN) {
-            const float4* p = reinterpret_cast<const float4*>(x + ((static_cast<size_t>(n) * H + yy) * W + xx) * CIN + 8 * g);
-            const float4 a = __ldg(p);
-            f[0] = a.x; f[1] = a.y; f[2] = a.z; f[3] = a.w;
-            if (CIN >= 8) {
-                const float4 b = __ldg(p + 1);
-                f[4] = b.x; f[5] = b.y; f[6] = b.z; f[7] = b.w;
-            }
-        }
+        const float4 a = s < RT::PS ? R.a[s < RT::PS ? s : 0] : la[s < RT::PS ? 0 : s - RT::PS];
+        const float4 b = s < RT::PS ? R.b[s < RT::PS ? s : 0] : lb[s < RT::PS ? 0 : s - RT::PS];
+        const float f[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
         uint4 hi, lo;
         split8(f, hi, lo);
         const uint32_t off = static_cast<uint32_t>(g) * C::PLANE + static_cast<uint32_t>(sr * kSW + sp) * 16;
@@ -263,19 +299,35 @@ __global__ void __launch_bounds__(kConv3Threads) conv3_tc_kernel(const float* __
 
     const int tiles_x = (W + kTileM - 1) / kTileM, tiles_y = (H + C::R - 1) / C::R;
     const long long ntiles = static_cast<long long>(NI) * tiles_y * tiles_x;
-    uint32_t phase = 0;
-    for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    auto tile_origin = [&](long long t, int& n, int& y0, int& x0) {
         const int tx = static_cast<int>(t % tiles_x);
         const long long t2 = t / tiles_x;
-        const int ty = static_cast<int>(t2 % tiles_y), n = static_cast<int>(t2 / tiles_y);
-        const int x0 = tx * kTileM, y0 = ty * C::R;
-        conv3_stage<CIN, COUT>(sbase, x, n, H, W, y0, x0);
+        n = static_cast<int>(t2 / tiles_y);
+        y0 = static_cast<int>(t2 % tiles_y) * C::R;
+        x0 = tx * kTileM;
+    };
+    Conv3Regs<CIN, COUT> Rg;
+    if (blockIdx.x < ntiles) {
+        int n, y0, x0;
+        tile_origin(blockIdx.x, n, y0, x0);
+        conv3_load<CIN, COUT>(Rg, x, n, H, W, y0, x0);
+    }
+    uint32_t phase = 0;
+    for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        int n, y0, x0;
+        tile_origin(t, n, y0, x0);
+        conv3_store<CIN, COUT>(Rg, sbase, x, n, H, W, y0, x0);
         fence_proxy_async_smem();  // the staged operand, visible to the tensor core
         __syncthreads();
         if (tid == 0) {
             fence_after_sync();
             conv3_mma<CIN, COUT>(sbase, tbase);
             mma_commit(bar);
+        }
+        if (t + gridDim.x < ntiles) {  // the next tile's loads, in flight during the MMAs
+            int n2, y2, x2;
+            tile_origin(t + gridDim.x, n2, y2, x2);
+            conv3_load<CIN, COUT>(Rg, x, n2, H, W, y2, x2);
         }
         bool ok = mbar_wait_bounded(bar, phase, kWaitNs);
         phase ^= 1u;
