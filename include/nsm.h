@@ -332,11 +332,12 @@ nsm_status nsm_backward(nsm_ctx* ctx, const nsm_frame* frame, const float* dev_p
                         float* grad_params, float* grad_feat, float* vis_out, void* workspace,
                         size_t workspace_bytes, void* stream);
 
-/* nsm_backward with the form of its 3x3 convolutions chosen (the level
- * recomputations and the data gradients through them): NSM_FP32 (exactly
- * nsm_backward) or NSM_BF16 (tcgen05 implicit GEMMs, compensated BF16 operands
- * and FP32 accumulation, as nsm_train_state_set_backward_precision; the weight
- * images are packed into the same workspace).  Other precisions:
+/* nsm_backward with the form of its contractions chosen (the 3x3 level
+ * recomputations, the data gradients through them and every weight
+ * gradient): NSM_FP32 (exactly nsm_backward) or NSM_BF16 (tcgen05, compensated
+ * BF16 operands and FP32 accumulation, weight gradients reduced in a fixed
+ * order, as nsm_train_state_set_backward_precision; the weight images and the
+ * partial sums use the same workspace).  Other precisions:
  * NSM_ERR_UNSUPPORTED.  A bounded device wait that gives up sets the context's
  * error word (nsm_ctx_check). */
 nsm_status nsm_backward_ex(nsm_ctx* ctx, const nsm_frame* frame, const float* dev_params, const float* grad_vis,
@@ -414,16 +415,21 @@ nsm_status nsm_train_state_set_detached_precision(nsm_train_state* st, nsm_preci
  * tensor cores.  Other precisions: NSM_ERR_UNSUPPORTED. */
 nsm_status nsm_train_state_set_forward_precision(nsm_train_state* st, nsm_precision precision);
 
-/* Form of the backward's 3x3 convolutions (Sec. 3.3, Eq. 2 adjoint): the
- * recomputed 3x3 pre-activations of every level and the data gradients
- * through them (the transposed, flipped weights).  NSM_FP32 (default; FP32
- * CUDA-core kernels) or NSM_BF16 (tcgen05 implicit GEMMs with compensated
- * BF16 operands: activations and weights as hi + lo BF16 pairs, all four
- * products accumulated in FP32 in tensor memory, ~2^-16 relative per operand;
- * weight images packed on the device at every step).  Tensors stay FP32
- * between the layers; the weight gradients and the 1x1 layers stay FP32.  A
- * bounded device wait that gives up sets the context's error word
- * (nsm_ctx_check: NSM_ERR_TIMEOUT, code 7).  Other precisions:
+/* Form of the backward's contractions (Sec. 3.3, Eq. 2 adjoint): the
+ * recomputed 3x3 pre-activations of every level, the data gradients through
+ * them (the transposed, flipped weights) and the weight and bias gradients of
+ * every 3x3 and 1x1 layer.  NSM_FP32 (default; FP32 CUDA-core kernels, weight
+ * gradients summed with atomics, so their last bits vary from run to run) or
+ * NSM_BF16 (tcgen05: implicit GEMMs for the 3x3 convolutions and a GEMM over
+ * the pixels for each weight gradient, with compensated BF16 operands:
+ * activations, gradients and weights as hi + lo BF16 pairs, all four products
+ * accumulated in FP32 in tensor memory, ~2^-16 relative per operand; weight
+ * images packed on the device at every step; every weight gradient, the
+ * head's included, reduced from per-CTA partial sums in a fixed order, so the
+ * gradient is the same bits from run to run on one device).  Tensors stay
+ * FP32 between the layers; the 1x1 layers' recomputations and data gradients
+ * stay FP32.  A bounded device wait that gives up sets the context's error
+ * word (nsm_ctx_check: NSM_ERR_TIMEOUT, code 7 or 8).  Other precisions:
  * NSM_ERR_UNSUPPORTED. */
 nsm_status nsm_train_state_set_backward_precision(nsm_train_state* st, nsm_precision precision);
 
