@@ -679,8 +679,9 @@ def deep_macs_per_pixel(levels):
 
 def extra_deep(nsm, scenegen, torch, device, reps):
     """Sec. 3.6's deeper networks (3, 5, 7 levels; receptive fields 24, 96,
-    384 px) on a 1088x1920 soft frame (both sides multiples of 2^6), FP32 on
-    CUDA cores, unfused, He-initialised weights."""
+    384 px) on a 1088x1920 soft frame (both sides multiples of 2^6),
+    He-initialised weights: the FP32 form (CUDA cores) and the tensor-core
+    form (BF16), whose visibility is compared with the FP32 form's."""
     Hd = 1088
     f = scenegen.soft_frame(Hd, W, HS, WS, N_OBJ, SCENE_SEED + 10)
     light = nsm.LightDesc(pos=tuple(f.light_pos), radius=f.light_radius, r_hat=f.r_hat, view_proj=f.view_proj,
@@ -713,6 +714,28 @@ def extra_deep(nsm, scenegen, torch, device, reps):
         out[f"levels_{L}"] = {"params": n, "receptive_field_px": 3 * 2 ** L, "mac_per_px": mac, "ms": ms,
                               "mpix_s": Hd * W / (ms * 1e-3) / 1e6, "achieved_tflops": tflops,
                               "roofline": {"bound": "alu", "peak_tflops": peak, "frac": tflops / peak}}
+        # the tensor-core form: levels 0, 1 on the BF16 stage kernels, levels 2 .. L-1 on tcgen05 layers
+        vis32 = vis.clone()
+        wsb = torch.empty((nsm.nsm_infer_deep_workspace_bytes(Hd, W, L, nsm.NSM_BF16),), dtype=torch.uint8,
+                          device=device)
+        for _ in range(3):
+            nsm.nsm_infer_deep(ctx, fr, theta, L, wsb, vis, precision=nsm.NSM_BF16)
+        ev = _events(torch, 2 * reps)
+        for k in range(reps):
+            ev[2 * k].record()
+            nsm.nsm_infer_deep(ctx, fr, theta, L, wsb, vis, precision=nsm.NSM_BF16)
+            ev[2 * k + 1].record()
+        torch.cuda.synchronize()
+        ctx.check()
+        msb = sum(ev[2 * k].elapsed_time(ev[2 * k + 1]) for k in range(reps)) / reps
+        d = (vis - vis32).abs()
+        out[f"levels_{L}"]["bf16"] = {
+            "ms": msb, "mpix_s": Hd * W / (msb * 1e-3) / 1e6,
+            "achieved_tflops": 2.0 * mac * Hd * W / (msb * 1e-3) / 1e12,
+            "max_abs_vs_fp32": float(d.max()), "mse_vs_fp32": float((d * d).mean()),
+            "form": "levels 0, 1 on the compensated-BF16 stage kernels; every 3x3 / 1x1 of levels 2 .. L-1 "
+                    "as a tcgen05 implicit GEMM (compensated BF16 operands, FP32 accumulation)"}
+        del wsb
     ctx.close()
     return out
 

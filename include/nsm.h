@@ -493,6 +493,22 @@ size_t nsm_infer_deep_workspace_bytes(int H, int W, int levels);
 nsm_status nsm_infer_deep(nsm_ctx* ctx, const nsm_frame* frame, const float* dev_params, int levels,
                           void* workspace, size_t workspace_bytes, float* vis_out, void* stream);
 
+/* nsm_infer_deep with the form chosen: NSM_FP32 (exactly nsm_infer_deep) or
+ * NSM_BF16 (levels >= 3; NSM_ERR_UNSUPPORTED for 2): levels 0 and 1, whose
+ * shapes are the 3-level network's, on its compensated-BF16 tensor-core stage
+ * kernels (gather fused into the level-0 encoder, the level-0 decoder on the
+ * coarse grid with the head), their weight images packed per call from this
+ * network's vector; every 3x3 and 1x1 layer of levels 2 .. L-1 on a tcgen05
+ * implicit GEMM over FP32 NHWC tensors with compensated BF16 operands (hi + lo
+ * pairs, FP32 accumulation).  Workspace (device, 256-byte aligned) of
+ * nsm_infer_deep_ex_workspace_bytes (0 for an unsupported combination).  A
+ * bounded device wait that gives up sets the context's error word
+ * (nsm_ctx_check).  Asynchronous. */
+size_t nsm_infer_deep_ex_workspace_bytes(int H, int W, int levels, nsm_precision precision);
+nsm_status nsm_infer_deep_ex(nsm_ctx* ctx, const nsm_frame* frame, const float* dev_params, int levels,
+                             nsm_precision precision, void* workspace, size_t workspace_bytes, float* vis_out,
+                             void* stream);
+
 /* ---------------------------------------------------------------- frame analysis */
 
 /* Temporal instability (Sec. 3.4, Eq. 3) of one pair of consecutive frames:

@@ -616,6 +616,7 @@ def _gen_sigs():
             "nsm_gen_visibility": [I, I, P, P, P, P, F, I, ctypes.c_uint64, F, I, P, P, P],
             "nsm_temporal_instability": [I, I, P, P, P, P, P, P, P, F, P, P, P],
             "nsm_infer_deep": [P, ctypes.POINTER(nsm_frame), P, I, P, ctypes.c_size_t, P, P],
+            "nsm_infer_deep_ex": [P, ctypes.POINTER(nsm_frame), P, I, I, P, ctypes.c_size_t, P, P],
             "nsm_penumbra_histogram": [I, I, P, P, F, F, I, P, P],
             "nsm_depth_for_penumbra": [P, I, F, P, P],
         }.items():
@@ -679,18 +680,30 @@ def nsm_param_count_levels(levels: int) -> int:
     return int(L.nsm_param_count_levels(levels))
 
 
-def nsm_infer_deep_workspace_bytes(H: int, W: int, levels: int) -> int:
+def nsm_infer_deep_workspace_bytes(H: int, W: int, levels: int, precision=None) -> int:
+    """Workspace of nsm_infer_deep (precision None) or nsm_infer_deep_ex."""
     L = lib()
-    L.nsm_infer_deep_workspace_bytes.restype = ctypes.c_size_t
-    L.nsm_infer_deep_workspace_bytes.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int]
-    return int(L.nsm_infer_deep_workspace_bytes(H, W, levels))
+    if precision is None:
+        L.nsm_infer_deep_workspace_bytes.restype = ctypes.c_size_t
+        L.nsm_infer_deep_workspace_bytes.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int]
+        return int(L.nsm_infer_deep_workspace_bytes(H, W, levels))
+    L.nsm_infer_deep_ex_workspace_bytes.restype = ctypes.c_size_t
+    L.nsm_infer_deep_ex_workspace_bytes.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+    return int(L.nsm_infer_deep_ex_workspace_bytes(H, W, levels, int(precision)))
 
 
-def nsm_infer_deep(ctx: Context, frame: nsm_frame, dev_params, levels: int, workspace, vis_out, stream=None):
-    """FP32 forward of the L-level network (L = 2 .. 7) on a device frame."""
-    _check(_gen_sigs().nsm_infer_deep(ctx.h, ctypes.byref(frame), _ptr(dev_params), int(levels), _ptr(workspace),
-                                      int(workspace.numel() * workspace.element_size()), _ptr(vis_out),
-                                      _stream(stream)), "nsm_infer_deep")
+def nsm_infer_deep(ctx: Context, frame: nsm_frame, dev_params, levels: int, workspace, vis_out, stream=None,
+                   precision=None):
+    """Forward of the L-level network (L = 2 .. 7) on a device frame: FP32
+    (precision None: nsm_infer_deep) or the form nsm_infer_deep_ex runs."""
+    nbytes = int(workspace.numel() * workspace.element_size())
+    if precision is None:
+        _check(_gen_sigs().nsm_infer_deep(ctx.h, ctypes.byref(frame), _ptr(dev_params), int(levels), _ptr(workspace),
+                                          nbytes, _ptr(vis_out), _stream(stream)), "nsm_infer_deep")
+    else:
+        _check(_gen_sigs().nsm_infer_deep_ex(ctx.h, ctypes.byref(frame), _ptr(dev_params), int(levels),
+                                             int(precision), _ptr(workspace), nbytes, _ptr(vis_out),
+                                             _stream(stream)), "nsm_infer_deep_ex")
 
 
 def depth_for_penumbra(hist, bin_px):

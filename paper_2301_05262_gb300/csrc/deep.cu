@@ -11,9 +11,23 @@
 // kernel; decoder: up-sampling while staging, 3x3, ReLU, 1x1); the coarser,
 // wider levels run one kernel per layer on NHWC FP32 tensors in the
 // workspace, the wide layers blocked over channels.
+//
+// Tensor-core form (nsm_infer_deep_ex with NSM_BF16): levels 0 and 1 have the
+// 3-level network's shapes, so they run on its compensated-BF16 stage kernels
+// (gather + level-0 encoder, level-1 encoder with skip, level-1 decoder,
+// level-0 decoder on the coarse grid with the head), their weight images
+// packed from this network's vector; the inner levels 2 .. L-1 run one
+// tcgen05 layer per 3x3 / 1x1 (deep_tc.cu) on FP32 NHWC tensors, entering
+// from the level-1 encoder's pooled BF16 pairs and leaving as the FP32
+// input the level-1 decoder up-samples.
+#include <algorithm>
 #include <vector>
 
+#include <cuda_bf16.h>
+
+#include "ctx_internal.h"
 #include "nsm_internal.h"
+#include "tc_stage.h"
 #include "train_internal.h"
 
 namespace nsm {
@@ -57,6 +71,151 @@ static size_t deep_ws_floats(int H, int W, int L) {
     return 64 + static_cast<size_t>(H) * W * (4 + 5 * 16) + deep_param_count(L);
 }
 
+// Layers of the inner levels (2 .. L-1): indices [4, 4L - 6) of deep_layers;
+// the 3-level network's layers map to 0 .. 3 (encoders), 4L - 6 .. 4L - 3
+// (decoders) and 4L - 2 (head).
+static int deep_index_of(Layer l, int L) {
+    switch (l) {
+        case ENC0_3: return 0; case ENC0_1: return 1; case ENC1_3: return 2; case ENC1_1: return 3;
+        case DEC1_3: return 4 * L - 6; case DEC1_1: return 4 * L - 5;
+        case DEC0_3: return 4 * L - 4; case DEC0_1: return 4 * L - 3;
+        case HEAD: return 4 * L - 2;
+        default: return -1;
+    }
+}
+
+// Bytes the tensor-core form adds after the FP32 form's workspace: the stage
+// kernels' activations, their BF16 weight images and packing table, and the
+// inner levels' weight images.
+static size_t deep_bf16_extra_bytes(int H, int W, int L) {
+    size_t b = activations_bytes(H, W, 4, nullptr, nullptr);
+    b += align_up(bf16_images().total * sizeof(uint16_t), 256);
+    b += align_up(pack_desc_bytes() * NUM_LAYERS, 256);
+    const std::vector<DeepLayer> t = deep_layers(L);
+    for (int i = 4; i < 4 * L - 6; ++i) b += align_up(tr::deep_tc_image_bytes(t[i].cin, t[i].cout, t[i].k), 256);
+    return b;
+}
+
+// BF16 hi + lo pairs [n][2][C] -> FP32 [n][C] (another buffer)
+template <int C>
+__global__ void deep_pairs_to_f32_kernel(const uint16_t* __restrict__ in, size_t n, float* __restrict__ out) {
+    for (size_t i = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; i < n * C;
+         i += static_cast<size_t>(gridDim.x) * blockDim.x) {
+        const size_t p = i / C, c = i % C;
+        out[i] = __bfloat162float(__ushort_as_bfloat16(in[p * 2 * C + c])) +
+                 __bfloat162float(__ushort_as_bfloat16(in[p * 2 * C + C + c]));
+    }
+}
+
+// The L-level network with levels 0, 1 on the BF16 stage kernels and the inner
+// levels on the tcgen05 layers; fp32 = the FP32 form's workspace regions
+// (a3, a1, h, xin, skip: 16 H W floats each), extra = deep_bf16_extra_bytes.
+static cudaError_t deep_forward_bf16(nsm_ctx* ctx, const nsm_frame* frame, const float* params, int L, float* a3,
+                                     float* a1, float* h, float* xin, float* skip, char* extra, float* vis,
+                                     cudaStream_t st) {
+    const int H = frame->H, W = frame->W;
+    const std::vector<DeepLayer> Ls = deep_layers(L);
+    Activations act{};
+    char* q = extra;
+    q += activations_bytes(H, W, 4, &act, q);
+    BF16Images im = bf16_images();
+    uint16_t* img16 = reinterpret_cast<uint16_t*>(q);
+    q += align_up(im.total * sizeof(uint16_t), 256);
+    void* ddesc = q;
+    q += align_up(pack_desc_bytes() * NUM_LAYERS, 256);
+    // the stage kernels' weight images, packed from this network's levels 0 and 1
+    PackDescHost desc[NUM_LAYERS];
+    int nd = 0;
+    for (int i = 0; i < im.n; ++i) {
+        int layer = -1;
+        for (int l = 0; l < NUM_LAYERS; ++l)
+            if (im.desc[i].img_off == im.img_off[l] && kLayers[l].cin == im.desc[i].cin) layer = l;
+        const int di = layer < 0 ? -1 : deep_index_of(static_cast<Layer>(layer), L);
+        if (di < 0) continue;  // the 3-level bottleneck: replaced by the inner levels
+        desc[nd] = im.desc[i];
+        desc[nd].w_off = Ls[di].w;
+        ++nd;
+    }
+    cudaError_t e = cudaMemcpyAsync(ddesc, desc, pack_desc_bytes() * nd, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = launch_pack_bf16(params, img16, ddesc, nd, st);
+    std::vector<const uint4*> mid(Ls.size(), nullptr);
+    for (int i = 4; i < 4 * L - 6 && e == cudaSuccess; ++i) {
+        mid[i] = reinterpret_cast<const uint4*>(q);
+        e = tr::deep_tc_pack(params + Ls[i].w, Ls[i].cin, Ls[i].cout, Ls[i].k, reinterpret_cast<uint4*>(q), st);
+        q += align_up(tr::deep_tc_image_bytes(Ls[i].cin, Ls[i].cout, Ls[i].k), 256);
+    }
+    if (e != cudaSuccess) return e;
+    auto I = [&](Layer l) { return reinterpret_cast<const uint4*>(img16 + im.img_off[l]); };
+    const GatherParams g = make_gather(frame);
+    const int head = deep_index_of(HEAD, L);
+    auto stage = [&](int s, Layer l3, Layer l1) {
+        TcBatch b{};
+        b.nviews = 1;
+        b.b3img = I(l3);
+        b.b1img = I(l1);
+        const DeepLayer &d3 = Ls[deep_index_of(l3, L)], &d1 = Ls[deep_index_of(l1, L)];
+        b.bias3 = params + d3.b;
+        b.bias1 = params + d1.b;
+        b.w3 = params + d3.w;
+        b.w1 = params + d1.w;
+        b.head = params + Ls[head].w;  // head weights followed by its bias
+        b.err = ctx->d_err;
+        TcJob& j = b.job[0];
+        j.g = g;
+        switch (s) {
+            case 0: j.H = H; j.W = W; j.out = static_cast<uint16_t*>(act.e0); break;
+            case 1: j.H = H / 2; j.W = W / 2; j.in = static_cast<const uint16_t*>(act.e0);
+                    j.out_skip = static_cast<float*>(act.s1); j.out = static_cast<uint16_t*>(act.p1); break;
+            case 3: j.H = H / 2; j.W = W / 2; j.in_f = static_cast<const float*>(act.bo);
+                    j.skip = static_cast<const float*>(act.s1); j.out = static_cast<uint16_t*>(act.d1); break;
+            default: j.H = H / 2; j.W = W / 2; j.in = static_cast<const uint16_t*>(act.d1); j.vis = vis; break;
+        }
+        return tc_launch_stage(s, tc_default_variant(s), b, 0, st);
+    };
+    if ((e = stage(0, ENC0_3, ENC0_1)) != cudaSuccess || (e = stage(1, ENC1_3, ENC1_1)) != cudaSuccess) return e;
+    // inner levels on FP32 NHWC tensors, from the pooled level-1 output
+    auto wd = [](int l) { return 16 << l; };
+    auto conv = [&](int li, const float* x, int relu_in, int Hl, int Wl, float* y) {
+        const DeepLayer& d = Ls[li];
+        return tr::deep_tc_conv(d.cin, d.cout, d.k, x, relu_in, Hl, Wl, mid[li], params + d.b, y, ctx->d_err, st);
+    };
+    const size_t n2 = static_cast<size_t>(H / 4) * (W / 4);
+    deep_pairs_to_f32_kernel<32><<<static_cast<int>(std::min<size_t>((n2 * 32 + 255) / 256, 4096)), 256, 0, st>>>(
+        static_cast<const uint16_t*>(act.p1), n2, xin);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const float* cur = xin;
+    std::vector<float*> skips(L, nullptr);
+    size_t skip_off = 0;
+    int li = 4;
+    for (int l = 2; l < L - 1 && e == cudaSuccess; ++l, li += 2) {
+        const int Hl = H >> l, Wl = W >> l;
+        float* pooled = cur == h ? xin : h;
+        skips[l] = skip + skip_off;
+        skip_off += static_cast<size_t>(Hl) * Wl * wd(l);
+        e = conv(li, cur, 0, Hl, Wl, a3);
+        if (e == cudaSuccess) e = conv(li + 1, a3, 1, Hl, Wl, a1);
+        if (e == cudaSuccess) e = tr::relu_copy(a1, static_cast<size_t>(Hl) * Wl * wd(l), skips[l], st);
+        if (e == cudaSuccess) e = tr::pool_relu(a1, 1, Hl, Wl, wd(l), pooled, st);
+        cur = pooled;
+    }
+    const int Hb = H >> (L - 1), Wb = W >> (L - 1);
+    if (e == cudaSuccess) e = conv(li++, cur, 0, Hb, Wb, a3);
+    if (e == cudaSuccess) e = conv(li++, a3, 1, Hb, Wb, a1);
+    if (e == cudaSuccess) e = tr::relu_copy(a1, static_cast<size_t>(Hb) * Wb * wd(L - 2), h, st);
+    for (int l = L - 2; l >= 2 && e == cudaSuccess; --l, li += 2) {
+        const int Hl = H >> l, Wl = W >> l;
+        e = tr::up_add(h, skips[l], 1, Hl, Wl, wd(l), xin, st);
+        if (e == cudaSuccess) e = conv(li, xin, 0, Hl, Wl, a3);
+        if (e == cudaSuccess) e = conv(li + 1, a3, 1, Hl, Wl, a1);
+        if (e == cudaSuccess) e = tr::relu_copy(a1, static_cast<size_t>(Hl) * Wl * wd(l - 1), h, st);
+    }
+    if (e != cudaSuccess) return e;
+    // the level-2 output (32 channels at H / 4) is what the level-1 decoder up-samples
+    act.bo = h;
+    if ((e = stage(3, DEC1_3, DEC1_1)) != cudaSuccess) return e;
+    return stage(4, DEC0_3, DEC0_1);
+}
+
 }  // namespace nsm
 
 using namespace nsm;
@@ -73,10 +232,27 @@ size_t nsm_infer_deep_workspace_bytes(int H, int W, int levels) {
     return deep_ws_floats(H, W, levels) * sizeof(float);
 }
 
+size_t nsm_infer_deep_ex_workspace_bytes(int H, int W, int levels, nsm_precision precision) {
+    if (H <= 0 || W <= 0 || levels < 2 || levels > 7) return 0;
+    if (precision == NSM_FP32) return nsm_infer_deep_workspace_bytes(H, W, levels);
+    if (precision != NSM_BF16 || levels < 3) return 0;
+    return align_up(deep_ws_floats(H, W, levels) * sizeof(float), 256) + deep_bf16_extra_bytes(H, W, levels);
+}
+
 nsm_status nsm_infer_deep(nsm_ctx* ctx, const nsm_frame* frame, const float* dev_params, int levels, void* workspace,
                           size_t workspace_bytes, float* vis_out, void* stream) {
+    return nsm_infer_deep_ex(ctx, frame, dev_params, levels, NSM_FP32, workspace, workspace_bytes, vis_out, stream);
+}
+
+nsm_status nsm_infer_deep_ex(nsm_ctx* ctx, const nsm_frame* frame, const float* dev_params, int levels,
+                             nsm_precision precision, void* workspace, size_t workspace_bytes, float* vis_out,
+                             void* stream) {
     if (!ctx) return fail(NSM_ERR_INVALID_ARG, "ctx is NULL");
     if (levels < 2 || levels > 7) return fail(NSM_ERR_INVALID_ARG, "levels must be 2 .. 7, got %d", levels);
+    if (precision != NSM_FP32 && precision != NSM_BF16)
+        return fail(NSM_ERR_UNSUPPORTED, "the deeper networks run in the FP32 or the BF16 form");
+    if (precision == NSM_BF16 && levels < 3)
+        return fail(NSM_ERR_UNSUPPORTED, "the BF16 form needs 3 or more levels, got %d", levels);
     nsm_status s = check_frame(frame, false);
     if (s != NSM_OK) return s;
     const int H = frame->H, W = frame->W;
@@ -85,7 +261,7 @@ nsm_status nsm_infer_deep(nsm_ctx* ctx, const nsm_frame* frame, const float* dev
     if (H % m || W % m) return fail(NSM_ERR_SHAPE, "H, W must be multiples of 2^(levels - 1) = %d", m);
     if ((s = check_dev_ptr(dev_params, "dev_params", 4)) != NSM_OK || (s = check_dev_ptr(vis_out, "vis_out", 4)) != NSM_OK)
         return s;
-    const size_t need = nsm_infer_deep_workspace_bytes(H, W, levels);
+    const size_t need = nsm_infer_deep_ex_workspace_bytes(H, W, levels, precision);
     if (!workspace || workspace_bytes < need)
         return fail(NSM_ERR_WORKSPACE, "workspace of %zu bytes given, %zu needed", workspace_bytes, need);
     if ((s = check_dev_ptr(workspace, "workspace", 256)) != NSM_OK) return s;
@@ -101,6 +277,11 @@ nsm_status nsm_infer_deep(nsm_ctx* ctx, const nsm_frame* frame, const float* dev
     float* xin = h + 16 * hw;    // decoder input (up-sampled + skip)
     float* skip = xin + 16 * hw; // encoder outputs of levels 1 .. L-2, one after the other
     float* wt = base + 64 + hw * (4 + 5 * 16);  // transposed weights
+    if (precision == NSM_BF16) {
+        char* extra = static_cast<char*>(workspace) + align_up(deep_ws_floats(H, W, levels) * sizeof(float), 256);
+        const cudaError_t e = deep_forward_bf16(ctx, frame, dev_params, levels, a3, a1, h, xin, skip, extra, vis_out, st);
+        return e == cudaSuccess ? NSM_OK : cuda_fail(e, "deep forward (tensor cores)");
+    }
     const GatherParams g = make_gather(frame);
     cudaError_t e = cudaMemcpyAsync(dgp, &g, sizeof(g), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = tr::features_batch(dgp, 1, H, W, feat, st);

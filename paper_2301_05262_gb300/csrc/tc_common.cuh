@@ -155,6 +155,14 @@ __device__ __forceinline__ void tma_load_4d(uint32_t dst, const void* tmap, int 
         : "memory");
 }
 
+// Contiguous bulk copy global -> this CTA's shared memory (no tensor map);
+// both addresses 16-byte aligned, `bytes` a multiple of 16; completion is
+// signalled on the mbarrier as transaction bytes.
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes, uint64_t* mbar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 :: "r"(dst), "l"(src), "r"(bytes), "r"(smem_u32(mbar)) : "memory");
+}
+
 // ---------------------------------------------------------------- programmatic dependent launch
 // Let the next kernel of the stream (launched with the programmatic-serialisation
 // attribute) start its CTAs once every CTA of this grid has issued this or exited.

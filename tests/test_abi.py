@@ -115,6 +115,16 @@ def test_host_validation_of_the_newer_entry_points(lib):
     assert b"ctx" in lib.nsm_last_error()
     assert nsm.nsm_infer_deep_workspace_bytes(0, 64, 5) == 0
     assert nsm.nsm_infer_deep_workspace_bytes(64, 64, 1) == 0
+    assert typed.nsm_infer_deep_ex(None, None, None, 5, nsm.NSM_BF16, None, 0, None, None) == 1
+    assert b"ctx" in lib.nsm_last_error()
+    # the tensor-core form: 3 .. 7 levels, FP32 and BF16 only; its workspace
+    # holds the FP32 form's plus the stage activations and weight images
+    for L in (3, 5, 7):
+        fp32 = nsm.nsm_infer_deep_workspace_bytes(64, 128, L, nsm.NSM_FP32)
+        assert fp32 == nsm.nsm_infer_deep_workspace_bytes(64, 128, L)
+        assert nsm.nsm_infer_deep_workspace_bytes(64, 128, L, nsm.NSM_BF16) > fp32
+    assert nsm.nsm_infer_deep_workspace_bytes(64, 128, 2, nsm.NSM_BF16) == 0
+    assert nsm.nsm_infer_deep_workspace_bytes(64, 128, 5, nsm.NSM_FP8) == 0
 
 
 def test_host_validation_of_the_static_entry_point(lib):

@@ -1,7 +1,9 @@
-"""GPU parity of the deeper networks (Sec. 3.6: 2 to 7 levels, FP32)
-against the FP64 oracle forward with the same number of levels: max-abs
-<= 1e-4 on visibility; the 3-level result equals the fused FP32 form's to
-rounding (both FP32: within the sum of their distances to FP64)."""
+"""GPU parity of the deeper networks (Sec. 3.6: 2 to 7 levels) against the
+FP64 oracle forward with the same number of levels: the FP32 form within
+1e-4 max-abs on visibility; the 3-level result equals the fused FP32 form's
+to rounding (both FP32: within the sum of their distances to FP64); the
+tensor-core form (compensated BF16, 3 to 7 levels) within 2e-3 max-abs and
+1e-8 MSE, under the 1e-2 / 1e-4 bar of the BF16 inference."""
 import numpy as np
 import pytest
 
@@ -24,12 +26,13 @@ def ctx():
     c.close()
 
 
-def _deep(ctx, df, theta, L):
+def _deep(ctx, df, theta, L, precision=None):
     f = df.f
-    ws = torch.empty((nsm.nsm_infer_deep_workspace_bytes(f.H, f.W, L),), dtype=torch.uint8, device="cuda")
+    ws = torch.empty((nsm.nsm_infer_deep_workspace_bytes(f.H, f.W, L, precision),), dtype=torch.uint8, device="cuda")
     vis = torch.empty((f.H, f.W), device="cuda")
-    nsm.nsm_infer_deep(ctx, df.frame, torch.from_numpy(theta).cuda(), L, ws, vis)
+    nsm.nsm_infer_deep(ctx, df.frame, torch.from_numpy(theta).cuda(), L, ws, vis, precision=precision)
     torch.cuda.synchronize()
+    ctx.check()
     return vis.cpu().numpy().astype(np.float64)
 
 
@@ -44,6 +47,34 @@ def test_deep_forward_matches_oracle(ctx, L, H, W):
     err = np.abs(vis - ref)
     print(f"L={L} {H}x{W}: max {err.max():.2e}")
     assert np.isfinite(vis).all() and err.max() <= 1e-4, err.max()
+
+
+@pytest.mark.parametrize("L,H,W", [(3, 96, 136), (5, 128, 192), (5, 256, 656), (6, 128, 256), (7, 128, 192),
+                                   (7, 192, 576)])
+def test_deep_bf16_forward_matches_oracle(ctx, L, H, W):
+    """Levels 0 and 1 on the BF16 stage kernels, levels 2 .. L-1 on the tcgen05
+    layers: at 256 x 656 the level-2 rows are 164 = 128 + 36 pixels (two
+    M tiles, ragged); 7 levels reach 1024 channels (the bottleneck's 3x3 has
+    32 input chunks of 16 and 16 output blocks of 64)."""
+    f = scenegen.soft_frame(H, W, 256, 256, 16, 60 + L)
+    theta = scenegen.he_init_weights(L, N.layer_table(L)).astype(np.float32)
+    vis = _deep(ctx, DeviceFrame(f), theta, L, nsm.NSM_BF16)
+    feat, _, _ = G.features(f.pos4, f.nrm4, f.sm, f.view_proj, f.light_pos, f.cam_pos, f.r_hat, f.z_far, f.bias)
+    ref = N.forward(feat, theta.astype(np.float64), levels=L)
+    err = np.abs(vis - ref)
+    mse = float(np.mean(err ** 2))
+    print(f"BF16 L={L} {H}x{W}: max {err.max():.2e}, MSE {mse:.2e}")
+    assert np.isfinite(vis).all() and err.max() <= 2e-3 and mse <= 1e-8, (err.max(), mse)
+
+
+def test_deep_bf16_rejects_two_levels(ctx):
+    f = scenegen.hard_frame(64, 64, 64, 64, 4, 2)
+    theta = scenegen.he_init_weights(2, N.layer_table(2)).astype(np.float32)
+    ws = torch.empty((1 << 20,), dtype=torch.uint8, device="cuda")
+    with pytest.raises(nsm.NSMError) as ei:
+        nsm.nsm_infer_deep(ctx, DeviceFrame(f).frame, torch.from_numpy(theta).cuda(), 2, ws,
+                           torch.empty((64, 64), device="cuda"), precision=nsm.NSM_BF16)
+    assert ei.value.status == 7  # NSM_ERR_UNSUPPORTED
 
 
 def test_deep_three_levels_equals_the_fused_form(ctx):
