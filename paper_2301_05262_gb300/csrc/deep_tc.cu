@@ -5,10 +5,12 @@
 // activation and weight is a pair hi = bf16(v), lo = bf16(v - hi); all four
 // part products accumulate in FP32 in tensor memory.
 //
-// Implicit GEMM, D[128 pixels x 64 outputs] per CTA and tile (one image row
-// segment of 128 pixels, one block of 64 output channels), K = taps x C_in
-// walked in chunks of CC input channels:
-//   A  the chunk's rows y - 1 .. y + 1 (y for a 1x1 layer) with a one-pixel
+// Implicit GEMM, D[R x 128 pixels x 64 outputs] per CTA and tile (R image
+// rows of a 128-pixel column segment, one block of 64 output channels; R = 4,
+// 2 or 1 for a 3x3 layer, the largest that still gives every SM a tile, so a
+// streamed weight chunk serves R MMA row blocks), K = taps x C_in walked in
+// chunks of CC input channels:
+//   A  the chunk's rows y - 1 .. y + R (y for a 1x1 layer) with a one-pixel
 //      halo, staged by all threads from FP32 as [part][channel group][staged
 //      row][staged pixel] 16-byte chunks (the no-swizzle K-major layout, so
 //      tap (ky, kx) is the same planes started ky rows and kx chunks on)
@@ -37,9 +39,9 @@ constexpr int kDcNB = 64;          // output channels per CTA
 constexpr int kDcN = 2 * kDcNB;    // MMA width: W_hi | W_lo
 constexpr int kDcErrCode = 9;      // error word value of a wait in deep_conv_kernel that gave up
 
-template <int K, int CC>
+template <int K, int CC, int R>
 struct DcCfg {
-    static constexpr int SR = K;                        // staged rows
+    static constexpr int SR = R + K - 1;                // staged rows
     static constexpr int SP = K == 3 ? 130 : 128;       // staged pixels used
     static constexpr int G = CC / 8;                    // channel groups per part
     static constexpr int KS = CC / 16;                  // K = 16 steps per tap
@@ -51,10 +53,11 @@ struct DcCfg {
     static constexpr uint32_t BYTES = OFF_BAR + 64;     // 4 mbarriers, TMEM address slot
     static constexpr int ITEMS = SR * SP * G;
     static constexpr int S = (ITEMS + kDcThreads - 1) / kDcThreads;
-    static constexpr int TMEM_COLS = kDcN;
+    static constexpr int TMEM_COLS = R * kDcN;          // one accumulator block per image row
     static_assert(CC % 16 == 0, "whole K = 16 steps");
     static_assert(A_BYTES % 16 == 0 && B_BYTES % 16 == 0, "bulk-copy granularity");
     static_assert(BYTES <= 227 * 1024, "shared memory per CTA");
+    static_assert(TMEM_COLS <= 512, "tensor memory");
     static_assert(PLANE / 16 < (1u << 14), "LBO field");
 };
 
@@ -88,23 +91,24 @@ __global__ void deep_pack_kernel(const float* __restrict__ w, int cin, int cout,
     }
 }
 
-template <int K, int CC>
+template <int K, int CC, int R>
 struct DcRegs {
-    float4 a[DcCfg<K, CC>::S], b[DcCfg<K, CC>::S];
+    float4 a[DcCfg<K, CC, R>::S], b[DcCfg<K, CC, R>::S];
 };
 
-// Chunk c of tile (row yr, x0): item i = (staged row sr, staged pixel sp,
-// group g) covers image row yr - (K / 2) + sr, column x0 - (K / 2) + sp,
-// channels CC c + 8 g .. + 8; zeros outside the image.
-template <int K, int CC>
-__device__ __forceinline__ void dc_load(DcRegs<K, CC>& R, const float* __restrict__ x, int H, int W, int CIN, int yr,
-                                        int x0, int c) {
-    using C = DcCfg<K, CC>;
+// Chunk c of tile (rows yr .. yr + R - 1, x0): item i = (staged row sr,
+// group g, staged pixel sp; pixel fastest, so a warp's 16-byte stores fill
+// whole rows of banks) covers image row yr - (K / 2) + sr, column
+// x0 - (K / 2) + sp, channels CC c + 8 g .. + 8; zeros outside the image.
+template <int K, int CC, int RR>
+__device__ __forceinline__ void dc_load(DcRegs<K, CC, RR>& R, const float* __restrict__ x, int H, int W, int CIN,
+                                        int yr, int x0, int c) {
+    using C = DcCfg<K, CC, RR>;
 #pragma unroll
     for (int s = 0; s < C::S; ++s) {
         const int i = threadIdx.x + s * kDcThreads;
-        const int g = i % C::G, rest = i / C::G;
-        const int sp = rest % C::SP, sr = rest / C::SP;
+        const int sp = i % C::SP, rest = i / C::SP;
+        const int g = rest % C::G, sr = rest / C::G;
         const int yy = yr - K / 2 + sr, xx = x0 - K / 2 + sp;
         const bool in = i < C::ITEMS && yy >= 0 && yy < H && xx >= 0 && xx < W;
         const float4* p = reinterpret_cast<const float4*>(
@@ -119,15 +123,15 @@ __device__ __forceinline__ uint32_t dc_bits(float v) {
     return static_cast<uint32_t>(__bfloat16_as_ushort(__float2bfloat16_rn(v)));
 }
 
-template <int K, int CC>
-__device__ __forceinline__ void dc_store(const DcRegs<K, CC>& R, uint32_t abase, int relu_in) {
-    using C = DcCfg<K, CC>;
+template <int K, int CC, int RR>
+__device__ __forceinline__ void dc_store(const DcRegs<K, CC, RR>& R, uint32_t abase, int relu_in) {
+    using C = DcCfg<K, CC, RR>;
 #pragma unroll
     for (int s = 0; s < C::S; ++s) {
         const int i = threadIdx.x + s * kDcThreads;
         if (i >= C::ITEMS) break;
-        const int g = i % C::G, rest = i / C::G;
-        const int sp = rest % C::SP, sr = rest / C::SP;
+        const int sp = i % C::SP, rest = i / C::SP;
+        const int g = rest % C::G, sr = rest / C::G;
         float f[8] = {R.a[s].x, R.a[s].y, R.a[s].z, R.a[s].w, R.b[s].x, R.b[s].y, R.b[s].z, R.b[s].w};
         uint32_t h[4], l[4];
 #pragma unroll
@@ -144,35 +148,40 @@ __device__ __forceinline__ void dc_store(const DcRegs<K, CC>& R, uint32_t abase,
     }
 }
 
-// The chunk's MMAs (one thread): every tap, K step and activation part.
-template <int K, int CC>
-__device__ __forceinline__ void dc_mma(uint32_t abase, uint32_t bbase, uint32_t tbase, uint32_t acc) {
-    using C = DcCfg<K, CC>;
+// The chunk's MMAs (one thread): every image row of the tile, tap, K step and
+// activation part; row r accumulates in tensor-memory columns r N .. + N.
+template <int K, int CC, int R>
+__device__ __forceinline__ void dc_mma(uint32_t abase, uint32_t bbase, uint32_t tbase, uint32_t acc0) {
+    using C = DcCfg<K, CC, R>;
     constexpr uint32_t idesc = idesc_bf16(kTileM, kDcN);
+#pragma unroll 1
+    for (int r = 0; r < R; ++r) {
+        uint32_t acc = acc0;
 #pragma unroll
-    for (int tap = 0; tap < K * K; ++tap) {
-        const int ky = tap / K, kx = tap % K;
+        for (int tap = 0; tap < K * K; ++tap) {
+            const int ky = tap / K, kx = tap % K;
 #pragma unroll
-        for (int ks = 0; ks < C::KS; ++ks) {
-            const uint64_t bdesc =
-                smem_desc(bbase + static_cast<uint32_t>((tap * C::KS + ks) * 2 * kDcN) * 16, kDcN * 16, 128);
+            for (int ks = 0; ks < C::KS; ++ks) {
+                const uint64_t bdesc =
+                    smem_desc(bbase + static_cast<uint32_t>((tap * C::KS + ks) * 2 * kDcN) * 16, kDcN * 16, 128);
 #pragma unroll
-            for (int p = 0; p < 2; ++p) {
-                const uint32_t a = abase + static_cast<uint32_t>(p * C::G + 2 * ks) * C::PLANE +
-                                   static_cast<uint32_t>(ky * kSW + kx) * 16;
-                mma_bf16(tbase, smem_desc(a, C::PLANE, 128), bdesc, idesc, acc);
-                acc = 1;
+                for (int p = 0; p < 2; ++p) {
+                    const uint32_t a = abase + static_cast<uint32_t>(p * C::G + 2 * ks) * C::PLANE +
+                                       static_cast<uint32_t>((r + ky) * kSW + kx) * 16;
+                    mma_bf16(tbase + static_cast<uint32_t>(r * kDcN), smem_desc(a, C::PLANE, 128), bdesc, idesc, acc);
+                    acc = 1;
+                }
             }
         }
     }
 }
 
-template <int K, int CC>
+template <int K, int CC, int RR>
 __global__ void __launch_bounds__(kDcThreads) deep_conv_kernel(const float* __restrict__ x, int relu_in, int H, int W,
                                                                int CIN, int COUT, const uint4* __restrict__ img,
                                                                const float* __restrict__ bias, float* __restrict__ y,
                                                                int* err) {
-    using C = DcCfg<K, CC>;
+    using C = DcCfg<K, CC, RR>;
     extern __shared__ __align__(1024) uint8_t smem[];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     uint64_t* full = reinterpret_cast<uint64_t*>(smem + C::OFF_BAR);       // [2] weights landed
@@ -191,21 +200,22 @@ __global__ void __launch_bounds__(kDcThreads) deep_conv_kernel(const float* __re
     const uint32_t tbase = *tslot;
 
     const int tiles_x = (W + kTileM - 1) / kTileM, nob = (COUT + kDcNB - 1) / kDcNB, nc = CIN / CC;
-    const long long ntiles = static_cast<long long>(H) * tiles_x * nob;
+    const int tiles_y = (H + RR - 1) / RR;
+    const long long ntiles = static_cast<long long>(tiles_y) * tiles_x * nob;
     const uint32_t block_chunks = C::B_BYTES / 16;
     uint32_t fph[2] = {0u, 0u}, dph[2] = {0u, 0u};  // phase parities of full[] (thread 0) and done[]
     int pend[2] = {0, 0};                           // commits on done[s] not yet waited for
     bool ok = true;
     int it = 0;
-    DcRegs<K, CC> R;
+    DcRegs<K, CC, RR> R;
     for (long long t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
         const int ob = static_cast<int>(t % nob);
         const long long r = t / nob;
-        const int x0 = static_cast<int>(r % tiles_x) * kTileM, yr = static_cast<int>(r / tiles_x);
+        const int x0 = static_cast<int>(r % tiles_x) * kTileM, yr = static_cast<int>(r / tiles_x) * RR;
         for (int c = 0; c < nc; ++c, ++it) {
             const int s = it & 1;
             const uint32_t abase = sbase + s * C::STAGE, bbase = abase + C::A_BYTES;
-            dc_load<K, CC>(R, x, H, W, CIN, yr, x0, c);  // in flight while the other stage's MMAs run
+            dc_load<K, CC, RR>(R, x, H, W, CIN, yr, x0, c);  // in flight while the other stage's MMAs run
             if (pend[s]) {                               // stage s free: its last MMAs finished
                 ok = mbar_wait_bounded(&done[s], dph[s], kWaitNs);
                 dph[s] ^= 1u;
@@ -216,13 +226,13 @@ __global__ void __launch_bounds__(kDcThreads) deep_conv_kernel(const float* __re
                 mbar_arrive_expect_tx(&full[s], C::B_BYTES);
                 bulk_load(bbase, img + (static_cast<size_t>(ob) * nc + c) * block_chunks, C::B_BYTES, &full[s]);
             }
-            dc_store<K, CC>(R, abase, relu_in);
+            dc_store<K, CC, RR>(R, abase, relu_in);
             fence_proxy_async_smem();  // the staged operand, visible to the tensor core
             __syncthreads();
             if (tid == 0) {
                 if (mbar_wait_bounded(&full[s], fph[s], kWaitNs)) {
                     fence_after_sync();
-                    dc_mma<K, CC>(abase, bbase, tbase, c > 0 ? 1u : 0u);
+                    dc_mma<K, CC, RR>(abase, bbase, tbase, c > 0 ? 1u : 0u);
                 } else {
                     atomicExch(err, kDcErrCode);
                 }
@@ -239,22 +249,28 @@ __global__ void __launch_bounds__(kDcThreads) deep_conv_kernel(const float* __re
         pend[sl] = 0;
         if (__syncthreads_or(!ok)) { ok = false; break; }
         fence_after_sync();
-        const int lq = warp & 3, half = warp >> 2;
-        const int o0 = ob * kDcNB + 32 * half;
+        // warp w: TMEM lane quarter w % 4 (pixels); (row, 32-output half) pairs
+        // j = w / 4, w / 4 + 4, ... of the tile
+        const int lq = warp & 3;
         const int px = x0 + 32 * lq + lane;
-        float a[32], b[32];
-        const uint32_t tq = tbase + (static_cast<uint32_t>(32 * lq) << 16) + static_cast<uint32_t>(32 * half);
-        tmem_ld32(tq, a);
-        tmem_ld32(tq + kDcNB, b);
-        tmem_ld_wait();
-        if (px < W && o0 < COUT) {
-            float* out = y + (static_cast<size_t>(yr) * W + px) * COUT + o0;
+#pragma unroll 1
+        for (int j = warp >> 2; j < 2 * RR; j += kDcThreads / 128) {
+            const int rr = j >> 1, o0 = ob * kDcNB + 32 * (j & 1);
+            float a[32], b[32];
+            const uint32_t tq = tbase + (static_cast<uint32_t>(32 * lq) << 16) +
+                                static_cast<uint32_t>(rr * kDcN + 32 * (j & 1));
+            tmem_ld32(tq, a);
+            tmem_ld32(tq + kDcNB, b);
+            tmem_ld_wait();
+            if (px < W && yr + rr < H && o0 < COUT) {
+                float* out = y + (static_cast<size_t>(yr + rr) * W + px) * COUT + o0;
 #pragma unroll
-            for (int o = 0; o < 32; o += 4)
-                *reinterpret_cast<float4*>(out + o) =
-                    make_float4(a[o] + b[o] + __ldg(bias + o0 + o), a[o + 1] + b[o + 1] + __ldg(bias + o0 + o + 1),
-                                a[o + 2] + b[o + 2] + __ldg(bias + o0 + o + 2),
-                                a[o + 3] + b[o + 3] + __ldg(bias + o0 + o + 3));
+                for (int o = 0; o < 32; o += 4)
+                    *reinterpret_cast<float4*>(out + o) =
+                        make_float4(a[o] + b[o] + __ldg(bias + o0 + o), a[o + 1] + b[o + 1] + __ldg(bias + o0 + o + 1),
+                                    a[o + 2] + b[o + 2] + __ldg(bias + o0 + o + 2),
+                                    a[o + 3] + b[o + 3] + __ldg(bias + o0 + o + 3));
+            }
         }
         // accumulators read out before the next tile's first MMA overwrites them
         fence_before_sync();
@@ -271,27 +287,28 @@ __global__ void __launch_bounds__(kDcThreads) deep_conv_kernel(const float* __re
     if (warp == 0) tmem_dealloc(tbase, C::TMEM_COLS);
 }
 
-template <int K, int CC>
+template <int K, int CC, int RR>
 cudaError_t launch_deep_conv(const float* x, int relu_in, int H, int W, int cin, int cout, const uint4* img,
                              const float* bias, float* y, int* err, cudaStream_t st) {
-    using C = DcCfg<K, CC>;
+    using C = DcCfg<K, CC, RR>;
     static int per_sm = 0;  // CTAs resident per SM (per instantiation, set on first use)
     if (per_sm == 0) {
-        cudaError_t e = cudaFuncSetAttribute(deep_conv_kernel<K, CC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaError_t e = cudaFuncSetAttribute(deep_conv_kernel<K, CC, RR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              static_cast<int>(C::BYTES));
         if (e != cudaSuccess) return e;
-        e = cudaFuncSetAttribute(deep_conv_kernel<K, CC>, cudaFuncAttributePreferredSharedMemoryCarveout,
+        e = cudaFuncSetAttribute(deep_conv_kernel<K, CC, RR>, cudaFuncAttributePreferredSharedMemoryCarveout,
                                  cudaSharedmemCarveoutMaxShared);
         if (e != cudaSuccess) return e;
-        const int occ = resident_ctas_per_sm(reinterpret_cast<const void*>(deep_conv_kernel<K, CC>), kDcThreads,
+        const int occ = resident_ctas_per_sm(reinterpret_cast<const void*>(deep_conv_kernel<K, CC, RR>), kDcThreads,
                                              C::BYTES);
         per_sm = occ < 512 / C::TMEM_COLS ? occ : 512 / C::TMEM_COLS;
     }
-    const long long tiles = static_cast<long long>(H) * ((W + kTileM - 1) / kTileM) * ((cout + kDcNB - 1) / kDcNB);
+    const long long tiles =
+        static_cast<long long>((H + RR - 1) / RR) * ((W + kTileM - 1) / kTileM) * ((cout + kDcNB - 1) / kDcNB);
     if (tiles == 0) return cudaSuccess;
     const long long cap = static_cast<long long>(num_sms()) * per_sm;
     const int grid = static_cast<int>(tiles < cap ? tiles : cap);
-    deep_conv_kernel<K, CC><<<grid, kDcThreads, C::BYTES, st>>>(x, relu_in, H, W, cin, cout, img, bias, y, err);
+    deep_conv_kernel<K, CC, RR><<<grid, kDcThreads, C::BYTES, st>>>(x, relu_in, H, W, cin, cout, img, bias, y, err);
     return cudaGetLastError();
 }
 
@@ -320,8 +337,16 @@ cudaError_t deep_tc_pack(const float* w, int cin, int cout, int k, uint4* img, c
 cudaError_t deep_tc_conv(int cin, int cout, int k, const float* x, int relu_in, int H, int W, const uint4* img,
                          const float* bias, float* y, int* err, cudaStream_t st) {
     if (!deep_tc_supported(cin, cout, k)) return cudaErrorInvalidValue;
-    if (k == 3) return launch_deep_conv<3, 16>(x, relu_in, H, W, cin, cout, img, bias, y, err, st);
-    return launch_deep_conv<1, 64>(x, relu_in, H, W, cin, cout, img, bias, y, err, st);
+    if (k == 1) return launch_deep_conv<1, 64, 1>(x, relu_in, H, W, cin, cout, img, bias, y, err, st);
+    // a 3x3 tile of R image rows reuses each streamed weight chunk R times:
+    // the largest R whose tiles still give every SM one
+    const long long per_row = static_cast<long long>((W + kTileM - 1) / kTileM) * ((cout + kDcNB - 1) / kDcNB);
+    const long long sms = num_sms();
+    if (static_cast<long long>((H + 3) / 4) * per_row >= sms)
+        return launch_deep_conv<3, 16, 4>(x, relu_in, H, W, cin, cout, img, bias, y, err, st);
+    if (static_cast<long long>((H + 1) / 2) * per_row >= sms)
+        return launch_deep_conv<3, 16, 2>(x, relu_in, H, W, cin, cout, img, bias, y, err, st);
+    return launch_deep_conv<3, 16, 1>(x, relu_in, H, W, cin, cout, img, bias, y, err, st);
 }
 
 }  // namespace tr

@@ -127,8 +127,9 @@ constexpr int kConv3Threads = 256;
 constexpr int kConv3ErrCode = 7;  // error word value of a wait in conv3_tc_kernel that gave up
 
 // One tile's input with its halo, item by item: thread t takes items t,
-// t + 256, ... (item = staged row sr, staged pixel sp, channel group g of 8
-// channels); staged row sr = image row y0 - 1 + sr, staged pixel sp = column
+// t + 256, ... (item = staged row sr, channel group g of 8 channels, staged
+// pixel sp; pixel fastest, so a warp's 16-byte stores fill whole rows of
+// banks); staged row sr = image row y0 - 1 + sr, staged pixel sp = column
 // x0 - 1 + sp; zeros outside the image and beyond C_in.  The first PS items of
 // a thread are loaded into registers one tile ahead (in flight while the
 // current tile's MMAs run), the rest when the tile is staged; a thread issues
@@ -146,8 +147,8 @@ template <int CIN, int COUT>
 __device__ __forceinline__ void conv3_item_load(const float* __restrict__ x, int i, int n, int H, int W, int y0,
                                                 int x0, float4& a, float4& b) {
     using C = Conv3Cfg<CIN, COUT>;
-    const int g = i % C::G, rest = i / C::G;
-    const int sp = rest % C::SP, sr = rest / C::SP;
+    const int sp = i % C::SP, rest = i / C::SP;
+    const int g = rest % C::G, sr = rest / C::G;
     const int yy = y0 - 1 + sr, xx = x0 - 1 + sp;
     const bool in = i < Conv3Regs<CIN, COUT>::ITEMS && yy >= 0 && yy < H && xx >= 0 && xx < W && 8 * g < CIN;
     const float4* p = reinterpret_cast<const float4*>(
@@ -179,8 +180,8 @@ __device__ __forceinline__ void conv3_store(const Conv3Regs<CIN, COUT>& R, uint3
     for (int s = 0; s < RT::S; ++s) {
         const int i = threadIdx.x + s * kConv3Threads;
         if (i >= RT::ITEMS) break;
-        const int g = i % C::G, rest = i / C::G;
-        const int sp = rest % C::SP, sr = rest / C::SP;
+        const int sp = i % C::SP, rest = i / C::SP;
+        const int g = rest % C::G, sr = rest / C::G;
         const float4 a = s < RT::PS ? R.a[s < RT::PS ? s : 0] : la[s < RT::PS ? 0 : s - RT::PS];
         const float4 b = s < RT::PS ? R.b[s < RT::PS ? s : 0] : lb[s < RT::PS ? 0 : s - RT::PS];
         const float f[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};

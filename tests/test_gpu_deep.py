@@ -50,12 +50,15 @@ def test_deep_forward_matches_oracle(ctx, L, H, W):
 
 
 @pytest.mark.parametrize("L,H,W", [(3, 96, 136), (5, 128, 192), (5, 256, 656), (6, 128, 256), (7, 128, 192),
-                                   (7, 192, 576)])
+                                   (7, 192, 576), (5, 832, 1280)])
 def test_deep_bf16_forward_matches_oracle(ctx, L, H, W):
     """Levels 0 and 1 on the BF16 stage kernels, levels 2 .. L-1 on the tcgen05
     layers: at 256 x 656 the level-2 rows are 164 = 128 + 36 pixels (two
     M tiles, ragged); 7 levels reach 1024 channels (the bottleneck's 3x3 has
-    32 input chunks of 16 and 16 output blocks of 64)."""
+    32 input chunks of 16 and 16 output blocks of 64).  At 832 x 1280 (152
+    SMs) the 3x3 layers take tiles of 4 image rows at level 2, 2 at level 3
+    and 1 at level 4 (the largest row count that still gives every SM a
+    tile), so every tile height is checked against the oracle."""
     f = scenegen.soft_frame(H, W, 256, 256, 16, 60 + L)
     theta = scenegen.he_init_weights(L, N.layer_table(L)).astype(np.float32)
     vis = _deep(ctx, DeviceFrame(f), theta, L, nsm.NSM_BF16)
