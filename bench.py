@@ -444,6 +444,38 @@ def extra_train(nsm, scenegen, torch, device, theta, reps):
             "precision": "FP32 CUDA cores (forward checkpoints per level, recomputation in the backward, Adam)"}
 
 
+def extra_fp8_three_term(nsm, torch, device, fr, theta, ctx, ref, reps):
+    """The headline 1080p frame in the three-term E4M3 form (nsm_infer_deep_ex
+    with 3 levels and NSM_FP8: activations and per-channel-scaled weights as
+    three E4M3 terms each, kind::f8f6f4 products in FP32, one layer per
+    kernel), timed with CUDA events after an L2 flush, and its error against the
+    headline's FP64 oracle forward."""
+    th = torch.from_numpy(theta.astype(np.float32)).to(device)
+    ws = torch.empty((nsm.nsm_infer_deep_workspace_bytes(H, W, 3, nsm.NSM_FP8),), dtype=torch.uint8, device=device)
+    v = torch.empty((H, W), dtype=torch.float32, device=device)
+    flush = torch.empty(256 * 2 ** 20, dtype=torch.uint8, device=device)
+    for _ in range(3):
+        nsm.nsm_infer_deep(ctx, fr, th, 3, ws, v, precision=nsm.NSM_FP8)
+    ev = _events(torch, 2 * reps)
+    for k in range(reps):
+        flush.zero_()
+        ev[2 * k].record()
+        nsm.nsm_infer_deep(ctx, fr, th, 3, ws, v, precision=nsm.NSM_FP8)
+        ev[2 * k + 1].record()
+    torch.cuda.synchronize()
+    ctx.check()
+    ms = sum(ev[2 * k].elapsed_time(ev[2 * k + 1]) for k in range(reps)) / reps
+    out = {"ms_per_frame": ms, "mpix_s": H * W / (ms * 1e-3) / 1e6,
+           "form": "three E4M3 terms (scales 1, 2^-4, 2^-8) per activation and per weight (times a per-output-"
+                   "channel scale), tcgen05 kind::f8f6f4 with FP32 accumulation, one layer per kernel on FP32 NHWC "
+                   "tensors (weight images packed per call)",
+           "workload": WORKLOAD}
+    if ref is not None:
+        e = np.abs(v.cpu().numpy().astype(np.float64) - ref)
+        out["error_vs_fp64_oracle"] = {"max_abs": float(e.max()), "mse": float(np.mean(e ** 2))}
+    return out
+
+
 def extra_soft_frame(nsm, scenegen, torch, device, theta, weights, ctx, reps, with_error):
     """The 1080p soft-shadow frame in both forms, with the error against the FP64 oracle."""
     f = scenegen.soft_frame(H, W, HS, WS, N_OBJ, SCENE_SEED + 10)
@@ -933,6 +965,7 @@ def run_ours(args):
 
     # accuracy of the timed output vs the FP64 oracle (rank 0 only, full frame)
     errs = {}
+    ref = None
     if rank == 0 and not args.skip_error:
         from oracle import gather as G
         from oracle import network as N
@@ -960,6 +993,8 @@ def run_ours(args):
     if world == 1 and not args.skip_extras:
         extras = {}
         for name, fn in (("features", lambda: extra_features(nsm, scenegen, torch, device, peaks, 10)),
+                         ("fp8_three_term_1080p", lambda: extra_fp8_three_term(nsm, torch, device, fr, theta, ctx,
+                                                                               ref, 20)),
                          ("soft_1080p", lambda: extra_soft_frame(nsm, scenegen, torch, device, theta, weights, ctx, 10,
                                                                  not args.skip_error)),
                          ("soft_sequence_1080p", lambda: extra_sequence(nsm, scenegen, torch, device, theta, weights,

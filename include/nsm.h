@@ -493,7 +493,15 @@ size_t nsm_infer_deep_workspace_bytes(int H, int W, int levels);
 nsm_status nsm_infer_deep(nsm_ctx* ctx, const nsm_frame* frame, const float* dev_params, int levels,
                           void* workspace, size_t workspace_bytes, float* vis_out, void* stream);
 
-/* nsm_infer_deep with the form chosen: NSM_FP32 (exactly nsm_infer_deep) or
+/* nsm_infer_deep with the form chosen: NSM_FP32 (exactly nsm_infer_deep),
+ * NSM_FP8 (the three-term E4M3 form, 2 .. 7 levels: every 3x3 and 1x1 layer a
+ * tcgen05 kind::f8f6f4 implicit GEMM over FP32 NHWC tensors, each activation
+ * held as three E4M3 terms at fixed scales 1, 2^-4, 2^-8 and each weight of
+ * output channel o as s_o times three such terms of W / s_o, s_o = max |W[o]| /
+ * 448; the nine term products of a K step accumulate in FP32 in five blocks,
+ * one per combined scale; activations above ~478 saturate; the head FP32 --
+ * unlike nsm_infer's single-term NSM_FP8 form, within 1e-2 max-abs / 1e-4 MSE
+ * of the FP64 network) or
  * NSM_BF16 (levels >= 3; NSM_ERR_UNSUPPORTED for 2): levels 0 and 1, whose
  * shapes are the 3-level network's, on its compensated-BF16 tensor-core stage
  * kernels (gather fused into the level-0 encoder, the level-0 decoder on the

@@ -107,6 +107,73 @@ __global__ void deep_pairs_to_f32_kernel(const uint16_t* __restrict__ in, size_t
     }
 }
 
+// Bytes the three-term FP8 form adds after the FP32 form's workspace: every
+// layer's E4M3 image (the head stays FP32).
+static size_t deep_f8x3_extra_bytes(int L) {
+    const std::vector<DeepLayer> t = deep_layers(L);
+    size_t b = 0;
+    for (size_t i = 0; i + 1 < t.size(); ++i) b += align_up(tr::f8x3_image_bytes(t[i].cin, t[i].cout, t[i].k), 256);
+    return b;
+}
+
+// The L-level network with every convolution in the three-term FP8 form, one
+// layer per kernel on FP32 NHWC tensors (features, a3, a1, h, xin, skip: the
+// FP32 form's workspace regions), as the FP32 form's unfused levels run.
+static cudaError_t deep_forward_f8x3(nsm_ctx* ctx, const nsm_frame* frame, const float* params, int L,
+                                     GatherParams* dgp, float* feat, float* a3, float* a1, float* h, float* xin,
+                                     float* skip, char* extra, float* vis, cudaStream_t st) {
+    const int H = frame->H, W = frame->W;
+    const std::vector<DeepLayer> Ls = deep_layers(L);
+    std::vector<const void*> img(Ls.size(), nullptr);
+    cudaError_t e = cudaSuccess;
+    char* q = extra;
+    for (size_t i = 0; i + 1 < Ls.size() && e == cudaSuccess; ++i) {
+        img[i] = q;
+        e = tr::f8x3_pack(params + Ls[i].w, Ls[i].cin, Ls[i].cout, Ls[i].k, q, st);
+        q += align_up(tr::f8x3_image_bytes(Ls[i].cin, Ls[i].cout, Ls[i].k), 256);
+    }
+    const GatherParams g = make_gather(frame);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dgp, &g, sizeof(g), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = tr::features_batch(dgp, 1, H, W, feat, st);
+    auto wd = [](int l) { return 16 << l; };
+    auto conv = [&](int li, const float* x, int relu_in, int Hl, int Wl, float* y) {
+        const DeepLayer& d = Ls[li];
+        return tr::f8x3_conv(d.cin, d.cout, d.k, x, relu_in, Hl, Wl, img[li], params + d.b, y, ctx->d_err, st);
+    };
+    std::vector<float*> skips(L, nullptr);
+    const float* cur = feat;
+    size_t skip_off = 0;
+    int li = 0;
+    for (int l = 0; l < L - 1 && e == cudaSuccess; ++l, li += 2) {
+        const int Hl = H >> l, Wl = W >> l;
+        float* pooled = cur == h ? xin : h;
+        if (l >= 1) {
+            skips[l] = skip + skip_off;
+            skip_off += static_cast<size_t>(Hl) * Wl * wd(l);
+        }
+        e = conv(li, cur, 0, Hl, Wl, a3);
+        if (e == cudaSuccess) e = conv(li + 1, a3, 1, Hl, Wl, a1);
+        if (e == cudaSuccess && l >= 1) e = tr::relu_copy(a1, static_cast<size_t>(Hl) * Wl * wd(l), skips[l], st);
+        if (e == cudaSuccess) e = tr::pool_relu(a1, 1, Hl, Wl, wd(l), pooled, st);
+        cur = pooled;
+    }
+    const int Hb = H >> (L - 1), Wb = W >> (L - 1);
+    if (e == cudaSuccess) e = conv(li++, cur, 0, Hb, Wb, a3);
+    if (e == cudaSuccess) e = conv(li++, a3, 1, Hb, Wb, a1);
+    if (e == cudaSuccess) e = tr::relu_copy(a1, static_cast<size_t>(Hb) * Wb * wd(L - 2), h, st);
+    const float* lo = h;
+    for (int l = L - 2; l >= 0 && e == cudaSuccess; --l, li += 2) {
+        const int Hl = H >> l, Wl = W >> l;
+        e = tr::up_add(lo, l >= 1 ? skips[l] : nullptr, 1, Hl, Wl, wd(l), xin, st);
+        if (e == cudaSuccess) e = conv(li, xin, 0, Hl, Wl, a3);
+        if (e == cudaSuccess) e = conv(li + 1, a3, 1, Hl, Wl, a1);
+        if (e == cudaSuccess && l >= 1) e = tr::relu_copy(a1, static_cast<size_t>(Hl) * Wl * wd(l - 1), h, st);
+        lo = l >= 1 ? h : a1;
+    }
+    if (e == cudaSuccess) e = tr::head(lo, params + Ls[li].w, static_cast<size_t>(H) * W, vis, st);
+    return e;
+}
+
 // The L-level network with levels 0, 1 on the BF16 stage kernels and the inner
 // levels on the tcgen05 layers; fp32 = the FP32 form's workspace regions
 // (a3, a1, h, xin, skip: 16 H W floats each), extra = deep_bf16_extra_bytes.
@@ -235,6 +302,8 @@ size_t nsm_infer_deep_workspace_bytes(int H, int W, int levels) {
 size_t nsm_infer_deep_ex_workspace_bytes(int H, int W, int levels, nsm_precision precision) {
     if (H <= 0 || W <= 0 || levels < 2 || levels > 7) return 0;
     if (precision == NSM_FP32) return nsm_infer_deep_workspace_bytes(H, W, levels);
+    if (precision == NSM_FP8)
+        return align_up(deep_ws_floats(H, W, levels) * sizeof(float), 256) + deep_f8x3_extra_bytes(levels);
     if (precision != NSM_BF16 || levels < 3) return 0;
     return align_up(deep_ws_floats(H, W, levels) * sizeof(float), 256) + deep_bf16_extra_bytes(H, W, levels);
 }
@@ -249,8 +318,8 @@ nsm_status nsm_infer_deep_ex(nsm_ctx* ctx, const nsm_frame* frame, const float* 
                              void* stream) {
     if (!ctx) return fail(NSM_ERR_INVALID_ARG, "ctx is NULL");
     if (levels < 2 || levels > 7) return fail(NSM_ERR_INVALID_ARG, "levels must be 2 .. 7, got %d", levels);
-    if (precision != NSM_FP32 && precision != NSM_BF16)
-        return fail(NSM_ERR_UNSUPPORTED, "the deeper networks run in the FP32 or the BF16 form");
+    if (precision != NSM_FP32 && precision != NSM_BF16 && precision != NSM_FP8)
+        return fail(NSM_ERR_UNSUPPORTED, "the deeper networks run in the FP32, BF16 or three-term FP8 form");
     if (precision == NSM_BF16 && levels < 3)
         return fail(NSM_ERR_UNSUPPORTED, "the BF16 form needs 3 or more levels, got %d", levels);
     nsm_status s = check_frame(frame, false);
@@ -277,6 +346,12 @@ nsm_status nsm_infer_deep_ex(nsm_ctx* ctx, const nsm_frame* frame, const float* 
     float* xin = h + 16 * hw;    // decoder input (up-sampled + skip)
     float* skip = xin + 16 * hw; // encoder outputs of levels 1 .. L-2, one after the other
     float* wt = base + 64 + hw * (4 + 5 * 16);  // transposed weights
+    if (precision == NSM_FP8) {
+        char* extra = static_cast<char*>(workspace) + align_up(deep_ws_floats(H, W, levels) * sizeof(float), 256);
+        const cudaError_t e =
+            deep_forward_f8x3(ctx, frame, dev_params, levels, dgp, feat, a3, a1, h, xin, skip, extra, vis_out, st);
+        return e == cudaSuccess ? NSM_OK : cuda_fail(e, "deep forward (three-term FP8)");
+    }
     if (precision == NSM_BF16) {
         char* extra = static_cast<char*>(workspace) + align_up(deep_ws_floats(H, W, levels) * sizeof(float), 256);
         const cudaError_t e = deep_forward_bf16(ctx, frame, dev_params, levels, a3, a1, h, xin, skip, extra, vis_out, st);

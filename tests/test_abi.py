@@ -124,7 +124,10 @@ def test_host_validation_of_the_newer_entry_points(lib):
         assert fp32 == nsm.nsm_infer_deep_workspace_bytes(64, 128, L)
         assert nsm.nsm_infer_deep_workspace_bytes(64, 128, L, nsm.NSM_BF16) > fp32
     assert nsm.nsm_infer_deep_workspace_bytes(64, 128, 2, nsm.NSM_BF16) == 0
-    assert nsm.nsm_infer_deep_workspace_bytes(64, 128, 5, nsm.NSM_FP8) == 0
+    # the three-term FP8 form: 2 .. 7 levels, the FP32 form's workspace plus the E4M3 images
+    for L in (2, 3, 5, 7):
+        assert nsm.nsm_infer_deep_workspace_bytes(64, 128, L, nsm.NSM_FP8) > nsm.nsm_infer_deep_workspace_bytes(64, 128, L)
+    assert nsm.nsm_infer_deep_workspace_bytes(64, 128, 5, 3) == 0
 
 
 def test_host_validation_of_the_static_entry_point(lib):
