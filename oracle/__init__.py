@@ -58,4 +58,10 @@ itself; the tests under tests/test_oracle_*.py):
   backward_s2d / train_step_s2d -- the dot-product identity of the two new
       operator adjoints, central differences on weights and features, the
       training step against its parts.
+  round_bf16 / round_bf16_pair / round_e4m3 -- the formats' bit fields
+      (enumerated value sets, ties to even, saturation).
+  round_e4m3_terms / round_e4m3_terms_per_out_channel -- one term equals
+      round_e4m3; E4M3 values reproduce exactly and a quarter-ulp offset needs
+      the second term; the three-term error bound (2^-12 relative plus a
+      subnormal floor) over random values; saturation at 448 + 28 + 1.75.
 """

@@ -345,6 +345,30 @@ def round_e4m3_per_out_channel(W):
     return round_e4m3(W / s) * s
 
 
+def round_e4m3_terms(x, terms: int = 3):
+    """x held as the sum of `terms` E4M3 values at fixed scales 1, 2^-4, 2^-8,
+    ...: a_0 = e4m3(x) and a_k = e4m3(16^k r_k) 16^-k for the residual r_k = x
+    - (a_0 + ... + a_{k-1}) (each conversion rounds to nearest even and
+    saturates at +-448, as `round_e4m3`), returned as the float64 sum.  Each
+    term keeps the residual's top four significant bits, so ~12 bits survive
+    for three terms; magnitudes beyond 448 (1 + 1/16 + 1/256 + ...) saturate."""
+    x = np.asarray(x, np.float32).astype(np.float64)
+    acc = np.zeros_like(x)
+    for k in range(terms):
+        s = 16.0 ** k
+        acc = acc + round_e4m3((x - acc) * s) / s
+    return acc
+
+
+def round_e4m3_terms_per_out_channel(W, terms: int = 3):
+    """`round_e4m3_terms` of W / s_o times s_o, one scale per output channel
+    (axis 0): s_o = max|W[o]| / 448 (1 for an all-zero channel)."""
+    W = np.asarray(W, np.float64)
+    s = np.abs(W).reshape(W.shape[0], -1).max(axis=1) / 448.0
+    s = np.where(s > 0, s, 1.0).reshape((-1,) + (1,) * (W.ndim - 1))
+    return round_e4m3_terms(W / s, terms) * s
+
+
 def upsample_coef(a: int, k: int, d: int) -> float:
     """Bilinear weight of coarse index i + d - 1 in fine index 2i + a + k - 1
     (half-pixel centres, as `upsample2` away from the clamped edge): fine

@@ -316,6 +316,57 @@ def test_round_e4m3_per_out_channel_keeps_each_row_maximum():
         assert np.all(np.abs(Q[o] - W[o])[big] <= 2 ** -4 * np.abs(W[o])[big] + 1e-15)
 
 
+def test_round_e4m3_terms_pins():
+    """The multi-term E4M3 split: one term is round_e4m3; an E4M3 value is
+    reproduced exactly (later terms zero) and a value a quarter-ulp off one by
+    its second term; otherwise the error of three terms is within half a unit of
+    the third term's last place: 2^-12 of |x| in the normal range, plus 2^-18
+    absolute where a residual falls into the subnormals (2^-10 / 256); values
+    beyond 448 + 28 + 1.75 saturate there."""
+    rng = np.random.default_rng(11)
+    x = rng.standard_normal(5000) * 50.0
+    np.testing.assert_array_equal(N.round_e4m3_terms(x, 1), N.round_e4m3(x))
+    # an E4M3 value is its own first term, and the later terms are zero
+    v = N.e4m3_values()
+    vs = np.concatenate([v, -v])
+    np.testing.assert_array_equal(N.round_e4m3_terms(vs, 3), vs)
+    # a value one E4M3 ulp-quarter off a binade start needs the second term:
+    # 1 + 2^-5 -> a_0 = 1, a_1 = e4m3(16 * 2^-5) / 16 = 2^-5 exactly
+    assert N.round_e4m3(np.array([1.0 + 2.0 ** -5]))[0] == 1.0
+    assert N.round_e4m3_terms(np.array([1.0 + 2.0 ** -5]), 2)[0] == 1.0 + 2.0 ** -5
+    y = np.concatenate([rng.uniform(-400, 400, 20000), rng.uniform(-1e-2, 1e-2, 5000)])
+    err = np.abs(N.round_e4m3_terms(y, 3) - y)
+    assert np.all(err <= 2.0 ** -12 * np.abs(y) + 2.0 ** -18)
+    assert N.round_e4m3_terms(np.array([1e4]), 3)[0] == 448.0 + 448.0 / 16.0 + 448.0 / 256.0
+    # fewer terms are coarser: two terms leave up to 2^-8 of |x|
+    e2 = np.abs(N.round_e4m3_terms(y, 2) - y)
+    assert e2.max() > 16 * err.max()
+    W = rng.standard_normal((8, 5, 3, 3))
+    Q = N.round_e4m3_terms_per_out_channel(W, 3)
+    assert np.all(np.abs(Q - W) <= 2.0 ** -12 * np.abs(W) + 2.0 ** -18 * np.abs(W).reshape(8, -1).max(1)[:, None, None, None] / 448)
+
+
+def test_three_term_e4m3_network_meets_the_bar():
+    """The trained 3-level network with every stored value (features, level
+    outputs, 3x3 outputs, up-sampled inputs) and every weight in the
+    three-term E4M3 form stays within 5e-3 max-abs / 1e-8 MSE of the FP64
+    forward (under the 1e-2 / 1e-4 bar) on a 64-object frame, while one term
+    per value does not meet the bar."""
+    import scenegen
+    from oracle import gather as G
+    f = scenegen.soft_frame(96, 128, 512, 512, 64, 7)
+    feat, _, _ = G.features(f.pos4, f.nrm4, f.sm, f.view_proj, f.light_pos, f.cam_pos, f.r_hat, f.z_far, f.bias)
+    theta = scenegen.trained_weights().astype(np.float64)
+    ref = N.forward(feat, theta)
+    r3 = lambda x: N.round_e4m3_terms(x, 3)
+    q3 = N.forward_rounded(feat, theta, r3, rnd_in=r3, rnd_w=N.round_e4m3_terms_per_out_channel, rnd_mid=r3)
+    e3 = np.abs(q3 - ref)
+    assert e3.max() <= 5e-3 and np.mean(e3 ** 2) <= 1e-8, (e3.max(), np.mean(e3 ** 2))
+    q1 = N.forward_rounded(feat, theta, N.round_e4m3, rnd_in=N.round_e4m3, rnd_w=N.round_e4m3_per_out_channel,
+                           rnd_mid=N.round_e4m3)
+    assert np.abs(q1 - ref).max() > 1e-2
+
+
 def test_band_forward_equals_the_full_frame():
     """bench.py measures errors on a band of rows with the oracle run on the
     band plus a 32-row margin: the receptive field of the 3-level net is about
