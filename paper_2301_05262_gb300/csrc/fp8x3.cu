@@ -13,10 +13,12 @@
 // epilogue sums with their scales (times s_o, plus the bias).  About 12 bits
 // of each operand survive (three 4-bit significands), against 3 for one term.
 //
-// Tile: 128 pixels of one image row x 32 output channels; K = taps x C_in in
-// chunks of 32 input channels (one K = 32 step per tap and term pair), two
-// stages: the threads stage chunk c + 1 (FP32 -> three E4M3 planes) and one
-// bulk copy brings its weights while the tensor core works on chunk c.
+// Tile: 128 pixels of one image row x 32 output channels (16 for a 16-channel
+// layer); K = taps x C_in in
+// chunks of 32 input channels (one K = 32 step per tap and term pair).  The
+// 1x1 kernel has two stages (the threads stage chunk c + 1, FP32 -> three E4M3
+// planes, and one bulk copy brings its weights while the tensor core works on
+// chunk c); the 3x3 kernel one, with two CTAs per SM overlapping instead.
 #include <cuda_fp8.h>
 
 #include "nsm_internal.h"
@@ -31,27 +33,31 @@ using namespace tc;
 namespace {
 
 constexpr int kF8Threads = 256;
-constexpr int kF8NB = 32;               // output channels per CTA
 constexpr int kF8T = 3;                 // E4M3 terms per value
 constexpr int kF8Blk = 2 * kF8T - 1;    // accumulator blocks (j + k = 0 .. 4)
 constexpr int kF8CC = 32;               // input channels per K chunk
 constexpr int kF8ErrCode = 10;          // error word value of a wait in f8x3_conv_kernel that gave up
 
-template <int K>
+// NB: output channels per CTA (32, or 16 for a 16-channel layer)
+template <int K, int NB>
 struct F8Cfg {
+    // stages of (A, B): the 3x3 kernel keeps one (68 KB, so two CTAs share an SM
+    // and one's staging overlaps the other's MMAs), the 1x1 kernel two
+    static constexpr int NS = K == 3 ? 1 : 2;
     static constexpr int SR = K;                        // staged rows
     static constexpr int SP = K == 3 ? 130 : 128;       // staged pixels used
     static constexpr int G = kF8CC / 16;                // 16-channel groups per term (the K halves)
     static constexpr uint32_t PLANE = SR * kSW * 16;    // bytes per (term, group) plane
     static constexpr uint32_t A_BYTES = kF8T * G * PLANE;
-    static constexpr uint32_t B_BYTES = K * K * kF8T * 2 * kF8NB * 16;
+    static constexpr uint32_t B_BYTES = K * K * kF8T * 2 * NB * 16;
     static constexpr uint32_t STAGE = (A_BYTES + B_BYTES + 1023) / 1024 * 1024;
-    static constexpr uint32_t OFF_BAR = 2 * STAGE;
+    static constexpr uint32_t OFF_BAR = NS * STAGE;
     static constexpr uint32_t BYTES = OFF_BAR + 64;     // 4 mbarriers, TMEM address slot
     static constexpr int ITEMS = SR * SP * G;
     static constexpr int S = (ITEMS + kF8Threads - 1) / kF8Threads;
-    static constexpr int TMEM_COLS = 256;               // 5 blocks x 32 columns
-    static_assert(kF8Blk * kF8NB <= TMEM_COLS, "accumulator blocks");
+    static constexpr int TMEM_COLS = kF8Blk * NB <= 128 ? 128 : 256;  // 5 blocks of NB columns
+    static_assert(kF8Blk * NB <= TMEM_COLS, "accumulator blocks");
+    static_assert(NB == 16 || NB == 32, "output block");
     static_assert(A_BYTES % 16 == 0 && B_BYTES % 16 == 0, "bulk-copy granularity");
     static_assert(BYTES <= 227 * 1024, "shared memory per CTA");
     static_assert(PLANE / 16 < (1u << 14), "LBO field");
@@ -99,23 +105,23 @@ __global__ void f8_scale_kernel(const float* __restrict__ w, int cin, int cout, 
     scale[o] = m > 0.f ? m / 448.f : 1.f;
 }
 
-// Weight image of one layer: block (ob, c) = outputs 32 ob .. + 32, inputs
+// Weight image of one layer: block (ob, c) = outputs nb ob .. + nb, inputs
 // 32 c .. + 32; inside it chunk (tap, term k, half h, row n) holds term k of
-// W[32 ob + n][32 c + 16 h .. + 16][tap] / s_o as 16 E4M3 codes.
+// W[nb ob + n][32 c + 16 h .. + 16][tap] / s_o as 16 E4M3 codes.
 __global__ void f8_pack_kernel(const float* __restrict__ w, const float* __restrict__ scale, int cin, int cout, int k,
-                               uint4* __restrict__ img) {
-    const int taps = k * k, nc = (cin + kF8CC - 1) / kF8CC, nob = (cout + kF8NB - 1) / kF8NB;
-    const size_t chunks = static_cast<size_t>(nob) * nc * taps * kF8T * 2 * kF8NB;
+                               int nb, uint4* __restrict__ img) {
+    const int taps = k * k, nc = (cin + kF8CC - 1) / kF8CC, nob = (cout + nb - 1) / nb;
+    const size_t chunks = static_cast<size_t>(nob) * nc * taps * kF8T * 2 * nb;
     for (size_t i = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; i < chunks;
          i += static_cast<size_t>(gridDim.x) * blockDim.x) {
-        const int n = static_cast<int>(i % kF8NB);
-        size_t r = i / kF8NB;
+        const int n = static_cast<int>(i % nb);
+        size_t r = i / nb;
         const int h = static_cast<int>(r % 2); r /= 2;
         const int term = static_cast<int>(r % kF8T); r /= kF8T;
         const int tap = static_cast<int>(r % taps); r /= taps;
         const int c = static_cast<int>(r % nc);
         const int ob = static_cast<int>(r / nc);
-        const int o = ob * kF8NB + n;
+        const int o = ob * nb + n;
         float v[16];
         const float s = o < cout ? __ldg(scale + o) : 1.f;
 #pragma unroll
@@ -129,19 +135,19 @@ __global__ void f8_pack_kernel(const float* __restrict__ w, const float* __restr
     }
 }
 
-template <int K>
+template <int K, int NB>
 struct F8Regs {
-    float4 v[F8Cfg<K>::S][4];
+    float4 v[F8Cfg<K, NB>::S][4];
 };
 
 // Chunk c of tile (row yr, x0): item i = (staged row sr, group g, staged
 // pixel sp; pixel fastest) covers image row yr - K / 2 + sr, column
 // x0 - K / 2 + sp, input channels 32 c + 16 g .. + 16; zeros outside the image
 // and beyond C_in.
-template <int K>
-__device__ __forceinline__ void f8_load(F8Regs<K>& R, const float* __restrict__ x, int H, int W, int CIN, int yr,
+template <int K, int NB>
+__device__ __forceinline__ void f8_load(F8Regs<K, NB>& R, const float* __restrict__ x, int H, int W, int CIN, int yr,
                                         int x0, int c) {
-    using C = F8Cfg<K>;
+    using C = F8Cfg<K, NB>;
 #pragma unroll
     for (int s = 0; s < C::S; ++s) {
         const int i = threadIdx.x + s * kF8Threads;
@@ -160,9 +166,9 @@ __device__ __forceinline__ void f8_load(F8Regs<K>& R, const float* __restrict__ 
     }
 }
 
-template <int K>
-__device__ __forceinline__ void f8_store(const F8Regs<K>& R, uint32_t abase, int relu_in) {
-    using C = F8Cfg<K>;
+template <int K, int NB>
+__device__ __forceinline__ void f8_store(const F8Regs<K, NB>& R, uint32_t abase, int relu_in) {
+    using C = F8Cfg<K, NB>;
 #pragma unroll
     for (int s = 0; s < C::S; ++s) {
         const int i = threadIdx.x + s * kF8Threads;
@@ -187,37 +193,37 @@ __device__ __forceinline__ void f8_store(const F8Regs<K>& R, uint32_t abase, int
 
 // The chunk's MMAs (one thread): per tap, weight term k and activation term
 // j, D block j + k; the first product into each block of a tile starts it.
-template <int K>
+template <int K, int NB>
 __device__ __forceinline__ void f8_mma(uint32_t abase, uint32_t bbase, uint32_t tbase, bool first_chunk) {
-    using C = F8Cfg<K>;
-    constexpr uint32_t idesc = idesc_e4m3(kTileM, kF8NB);
+    using C = F8Cfg<K, NB>;
+    constexpr uint32_t idesc = idesc_e4m3(kTileM, NB);
 #pragma unroll
     for (int tap = 0; tap < K * K; ++tap) {
         const int ky = tap / K, kx = tap % K;
 #pragma unroll
         for (int k = 0; k < kF8T; ++k) {
             const uint64_t bdesc =
-                smem_desc(bbase + static_cast<uint32_t>((tap * kF8T + k) * 2 * kF8NB) * 16, kF8NB * 16, 128);
+                smem_desc(bbase + static_cast<uint32_t>((tap * kF8T + k) * 2 * NB) * 16, NB * 16, 128);
 #pragma unroll
             for (int j = 0; j < kF8T; ++j) {
                 // in the (k, j) order above, block j + k is first written by (0, j) or, for j + k > 2, by (k, 2)
                 const bool starts = tap == 0 && (k == 0 || j == kF8T - 1);
                 const uint32_t a = abase + static_cast<uint32_t>(j * C::G) * C::PLANE +
                                    static_cast<uint32_t>(ky * kSW + kx) * 16;
-                mma_e4m3(tbase + static_cast<uint32_t>((j + k) * kF8NB), smem_desc(a, C::PLANE, 128), bdesc, idesc,
+                mma_e4m3(tbase + static_cast<uint32_t>((j + k) * NB), smem_desc(a, C::PLANE, 128), bdesc, idesc,
                          (first_chunk && starts) ? 0u : 1u);
             }
         }
     }
 }
 
-template <int K>
-__global__ void __launch_bounds__(kF8Threads) f8x3_conv_kernel(const float* __restrict__ x, int relu_in, int H, int W,
+template <int K, int NB>
+__global__ void __launch_bounds__(kF8Threads, 2) f8x3_conv_kernel(const float* __restrict__ x, int relu_in, int H, int W,
                                                                int CIN, int COUT, const uint4* __restrict__ img,
                                                                const float* __restrict__ scale,
                                                                const float* __restrict__ bias, float* __restrict__ y,
                                                                int* err) {
-    using C = F8Cfg<K>;
+    using C = F8Cfg<K, NB>;
     extern __shared__ __align__(1024) uint8_t smem[];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     uint64_t* full = reinterpret_cast<uint64_t*>(smem + C::OFF_BAR);       // [2] weights landed
@@ -235,22 +241,22 @@ __global__ void __launch_bounds__(kF8Threads) f8x3_conv_kernel(const float* __re
     fence_after_sync();
     const uint32_t tbase = *tslot;
 
-    const int tiles_x = (W + kTileM - 1) / kTileM, nob = (COUT + kF8NB - 1) / kF8NB, nc = (CIN + kF8CC - 1) / kF8CC;
+    const int tiles_x = (W + kTileM - 1) / kTileM, nob = (COUT + NB - 1) / NB, nc = (CIN + kF8CC - 1) / kF8CC;
     const long long ntiles = static_cast<long long>(H) * tiles_x * nob;
     const uint32_t block_chunks = C::B_BYTES / 16;
     uint32_t fph[2] = {0u, 0u}, dph[2] = {0u, 0u};
     int pend[2] = {0, 0};
     bool ok = true;
     int it = 0;
-    F8Regs<K> R;
+    F8Regs<K, NB> R;
     for (long long t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
         const int ob = static_cast<int>(t % nob);
         const long long r = t / nob;
         const int x0 = static_cast<int>(r % tiles_x) * kTileM, yr = static_cast<int>(r / tiles_x);
         for (int c = 0; c < nc; ++c, ++it) {
-            const int s = it & 1;
+            const int s = C::NS == 2 ? (it & 1) : 0;
             const uint32_t abase = sbase + s * C::STAGE, bbase = abase + C::A_BYTES;
-            f8_load<K>(R, x, H, W, CIN, yr, x0, c);  // in flight while the other stage's MMAs run
+            f8_load<K, NB>(R, x, H, W, CIN, yr, x0, c);  // in flight while the other stage's MMAs run
             if (pend[s]) {
                 ok = mbar_wait_bounded(&done[s], dph[s], kWaitNs);
                 dph[s] ^= 1u;
@@ -261,13 +267,13 @@ __global__ void __launch_bounds__(kF8Threads) f8x3_conv_kernel(const float* __re
                 mbar_arrive_expect_tx(&full[s], C::B_BYTES);
                 bulk_load(bbase, img + (static_cast<size_t>(ob) * nc + c) * block_chunks, C::B_BYTES, &full[s]);
             }
-            f8_store<K>(R, abase, relu_in);
+            f8_store<K, NB>(R, abase, relu_in);
             fence_proxy_async_smem();
             __syncthreads();
             if (tid == 0) {
                 if (mbar_wait_bounded(&full[s], fph[s], kWaitNs)) {
                     fence_after_sync();
-                    f8_mma<K>(abase, bbase, tbase, c == 0);
+                    f8_mma<K, NB>(abase, bbase, tbase, c == 0);
                 } else {
                     atomicExch(err, kF8ErrCode);
                 }
@@ -277,36 +283,42 @@ __global__ void __launch_bounds__(kF8Threads) f8x3_conv_kernel(const float* __re
             pend[s] = 1;
         }
         if (!ok) break;
-        const int sl = (it - 1) & 1;
+        const int sl = C::NS == 2 ? ((it - 1) & 1) : 0;
         ok = mbar_wait_bounded(&done[sl], dph[sl], kWaitNs);
         dph[sl] ^= 1u;
         pend[sl] = 0;
         if (__syncthreads_or(!ok)) { ok = false; break; }
         fence_after_sync();
-        // warp w: TMEM lane quarter w % 4 (pixels), outputs 16 (w / 4) .. + 16 of the block
-        const int lq = warp & 3, o0 = ob * kF8NB + 16 * (warp >> 2);
+        // warp w: TMEM lane quarter w % 4 (pixels), outputs NB / 2 (w / 4) .. + NB / 2 of the block
+        const int lq = warp & 3, o0 = ob * NB + (NB / 2) * (warp >> 2);
         const int px = x0 + 32 * lq + lane;
-        float d[kF8Blk][16];
-        const uint32_t tq = tbase + (static_cast<uint32_t>(32 * lq) << 16) + static_cast<uint32_t>(16 * (warp >> 2));
+        // passes of 8 columns: the five blocks' values of 8 outputs live at a time
 #pragma unroll
-        for (int b = 0; b < kF8Blk; ++b) tmem_ld16(tq + static_cast<uint32_t>(b * kF8NB), d[b]);
-        tmem_ld_wait();
-        if (px < W && o0 < COUT) {
-            float* out = y + (static_cast<size_t>(yr) * W + px) * COUT + o0;
+        for (int hp = 0; hp < NB / 16; ++hp) {
+            float d[kF8Blk][8];
+            const uint32_t tq = tbase + (static_cast<uint32_t>(32 * lq) << 16) +
+                                static_cast<uint32_t>((NB / 2) * (warp >> 2) + 8 * hp);
 #pragma unroll
-            for (int o = 0; o < 16; o += 4) {
-                float v[4];
+            for (int b = 0; b < kF8Blk; ++b) tmem_ld8(tq + static_cast<uint32_t>(b * NB), d[b]);
+            tmem_ld_wait();
+            if (px < W && o0 < COUT) {
+                float* out = y + (static_cast<size_t>(yr) * W + px) * COUT + o0 + 8 * hp;
 #pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    // smallest-scale blocks first
-                    float a = d[4][o + e];
-                    a = fmaf(a, 1.f / 16.f, d[3][o + e]);
-                    a = fmaf(a, 1.f / 16.f, d[2][o + e]);
-                    a = fmaf(a, 1.f / 16.f, d[1][o + e]);
-                    a = fmaf(a, 1.f / 16.f, d[0][o + e]);
-                    v[e] = fmaf(a, __ldg(scale + o0 + o + e), __ldg(bias + o0 + o + e));
+                for (int o = 0; o < 8; o += 4) {
+                    float v[4];
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        // smallest-scale blocks first
+                        float a = d[4][o + e];
+                        a = fmaf(a, 1.f / 16.f, d[3][o + e]);
+                        a = fmaf(a, 1.f / 16.f, d[2][o + e]);
+                        a = fmaf(a, 1.f / 16.f, d[1][o + e]);
+                        a = fmaf(a, 1.f / 16.f, d[0][o + e]);
+                        const int oc = o0 + 8 * hp + o + e;
+                        v[e] = fmaf(a, __ldg(scale + oc), __ldg(bias + oc));
+                    }
+                    *reinterpret_cast<float4*>(out + o) = make_float4(v[0], v[1], v[2], v[3]);
                 }
-                *reinterpret_cast<float4*>(out + o) = make_float4(v[0], v[1], v[2], v[3]);
             }
         }
         fence_before_sync();
@@ -322,28 +334,32 @@ __global__ void __launch_bounds__(kF8Threads) f8x3_conv_kernel(const float* __re
     if (warp == 0) tmem_dealloc(tbase, C::TMEM_COLS);
 }
 
-template <int K>
+template <int K, int NB>
 cudaError_t launch_f8x3(const float* x, int relu_in, int H, int W, int cin, int cout, const uint4* img,
                         const float* scale, const float* bias, float* y, int* err, cudaStream_t st) {
-    using C = F8Cfg<K>;
+    using C = F8Cfg<K, NB>;
     static int per_sm = 0;  // CTAs resident per SM (per instantiation, set on first use)
     if (per_sm == 0) {
-        cudaError_t e = cudaFuncSetAttribute(f8x3_conv_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaError_t e = cudaFuncSetAttribute(f8x3_conv_kernel<K, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              static_cast<int>(C::BYTES));
         if (e != cudaSuccess) return e;
-        e = cudaFuncSetAttribute(f8x3_conv_kernel<K>, cudaFuncAttributePreferredSharedMemoryCarveout,
+        e = cudaFuncSetAttribute(f8x3_conv_kernel<K, NB>, cudaFuncAttributePreferredSharedMemoryCarveout,
                                  cudaSharedmemCarveoutMaxShared);
         if (e != cudaSuccess) return e;
-        const int occ = resident_ctas_per_sm(reinterpret_cast<const void*>(f8x3_conv_kernel<K>), kF8Threads, C::BYTES);
+        const int occ = resident_ctas_per_sm(reinterpret_cast<const void*>(f8x3_conv_kernel<K, NB>), kF8Threads,
+                                             C::BYTES);
         per_sm = occ < 512 / C::TMEM_COLS ? occ : 512 / C::TMEM_COLS;
     }
-    const long long tiles = static_cast<long long>(H) * ((W + kTileM - 1) / kTileM) * ((cout + kF8NB - 1) / kF8NB);
+    const long long tiles = static_cast<long long>(H) * ((W + kTileM - 1) / kTileM) * ((cout + NB - 1) / NB);
     if (tiles == 0) return cudaSuccess;
     const long long cap = static_cast<long long>(num_sms()) * per_sm;
     const int grid = static_cast<int>(tiles < cap ? tiles : cap);
-    f8x3_conv_kernel<K><<<grid, kF8Threads, C::BYTES, st>>>(x, relu_in, H, W, cin, cout, img, scale, bias, y, err);
+    f8x3_conv_kernel<K, NB><<<grid, kF8Threads, C::BYTES, st>>>(x, relu_in, H, W, cin, cout, img, scale, bias, y, err);
     return cudaGetLastError();
 }
+
+// output channels per CTA: 16 for a 16-channel layer, else 32
+constexpr int f8_nb(int cout) { return cout % 32 == 0 ? 32 : 16; }
 
 }  // namespace
 
@@ -353,20 +369,21 @@ bool f8x3_supported(int cin, int cout, int k) {
 
 size_t f8x3_image_bytes(int cin, int cout, int k) {
     if (!f8x3_supported(cin, cout, k)) return 0;
-    const size_t nob = (cout + kF8NB - 1) / kF8NB, nc = (cin + kF8CC - 1) / kF8CC;
-    return nob * nc * k * k * kF8T * 2 * kF8NB * 16 + align_up(nob * kF8NB * sizeof(float), 256);
+    const size_t nb = f8_nb(cout), nob = (cout + nb - 1) / nb, nc = (cin + kF8CC - 1) / kF8CC;
+    return nob * nc * k * k * kF8T * 2 * nb * 16 + align_up(nob * nb * sizeof(float), 256);
 }
 
 cudaError_t f8x3_pack(const float* w, int cin, int cout, int k, void* img, cudaStream_t st) {
     if (!f8x3_supported(cin, cout, k)) return cudaErrorInvalidValue;
-    const size_t nob = (cout + kF8NB - 1) / kF8NB, nc = (cin + kF8CC - 1) / kF8CC;
-    const size_t chunks = nob * nc * k * k * kF8T * 2 * kF8NB;
+    const size_t nb = f8_nb(cout), nob = (cout + nb - 1) / nb, nc = (cin + kF8CC - 1) / kF8CC;
+    const size_t chunks = nob * nc * k * k * kF8T * 2 * nb;
     float* scale = reinterpret_cast<float*>(static_cast<char*>(img) + chunks * 16);
     f8_scale_kernel<<<(cout + 127) / 128, 128, 0, st>>>(w, cin, cout, k * k, scale);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const size_t blocks = (chunks + 255) / 256, cap = static_cast<size_t>(num_sms()) * 8;
     f8_pack_kernel<<<static_cast<int>(blocks < cap ? blocks : cap), 256, 0, st>>>(w, scale, cin, cout, k,
+                                                                                  static_cast<int>(nb),
                                                                                   static_cast<uint4*>(img));
     return cudaGetLastError();
 }
@@ -374,12 +391,15 @@ cudaError_t f8x3_pack(const float* w, int cin, int cout, int k, void* img, cudaS
 cudaError_t f8x3_conv(int cin, int cout, int k, const float* x, int relu_in, int H, int W, const void* img,
                       const float* bias, float* y, int* err, cudaStream_t st) {
     if (!f8x3_supported(cin, cout, k)) return cudaErrorInvalidValue;
-    const size_t nob = (cout + kF8NB - 1) / kF8NB, nc = (cin + kF8CC - 1) / kF8CC;
-    const size_t chunks = nob * nc * k * k * kF8T * 2 * kF8NB;
+    const size_t nb = f8_nb(cout), nob = (cout + nb - 1) / nb, nc = (cin + kF8CC - 1) / kF8CC;
+    const size_t chunks = nob * nc * k * k * kF8T * 2 * nb;
     const uint4* im = static_cast<const uint4*>(img);
     const float* scale = reinterpret_cast<const float*>(static_cast<const char*>(img) + chunks * 16);
-    if (k == 3) return launch_f8x3<3>(x, relu_in, H, W, cin, cout, im, scale, bias, y, err, st);
-    return launch_f8x3<1>(x, relu_in, H, W, cin, cout, im, scale, bias, y, err, st);
+    if (k == 3)
+        return nb == 16 ? launch_f8x3<3, 16>(x, relu_in, H, W, cin, cout, im, scale, bias, y, err, st)
+                        : launch_f8x3<3, 32>(x, relu_in, H, W, cin, cout, im, scale, bias, y, err, st);
+    return nb == 16 ? launch_f8x3<1, 16>(x, relu_in, H, W, cin, cout, im, scale, bias, y, err, st)
+                    : launch_f8x3<1, 32>(x, relu_in, H, W, cin, cout, im, scale, bias, y, err, st);
 }
 
 }  // namespace tr
