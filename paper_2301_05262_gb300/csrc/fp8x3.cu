@@ -38,18 +38,23 @@ constexpr int kF8Blk = 2 * kF8T - 1;    // accumulator blocks (j + k = 0 .. 4)
 constexpr int kF8CC = 32;               // input channels per K chunk
 constexpr int kF8ErrCode = 10;          // error word value of a wait in f8x3_conv_kernel that gave up
 
-// NB: output channels per CTA (32, or 16 for a 16-channel layer)
-template <int K, int NB>
+// NB: output channels per CTA (32, or 16 for a 16-channel layer).  PAIR (3x3
+// layers with at most 16 input channels): one K = 32 step covers two
+// horizontal taps -- its K halves are staged pixels m + kx and m + kx + 1 of the
+// one 16-channel plane (16 bytes apart) -- so a kernel row takes 2 steps
+// (kx = 0, 1 and kx = 2 with zero weights for the missing fourth tap), not 3.
+template <int K, int NB, bool PAIR = false>
 struct F8Cfg {
     // stages of (A, B): the 3x3 kernel keeps one (68 KB, so two CTAs share an SM
     // and one's staging overlaps the other's MMAs), the 1x1 kernel two
     static constexpr int NS = K == 3 ? 1 : 2;
     static constexpr int SR = K;                        // staged rows
-    static constexpr int SP = K == 3 ? 130 : 128;       // staged pixels used
-    static constexpr int G = kF8CC / 16;                // 16-channel groups per term (the K halves)
+    static constexpr int SP = K == 3 ? (PAIR ? 131 : 130) : 128;  // staged pixels used
+    static constexpr int G = PAIR ? 1 : kF8CC / 16;     // 16-channel groups per term (the K halves unless PAIR)
+    static constexpr int NSTEP = PAIR ? 2 * K : K * K;  // K = 32 steps per chunk and term pair
     static constexpr uint32_t PLANE = SR * kSW * 16;    // bytes per (term, group) plane
     static constexpr uint32_t A_BYTES = kF8T * G * PLANE;
-    static constexpr uint32_t B_BYTES = K * K * kF8T * 2 * NB * 16;
+    static constexpr uint32_t B_BYTES = NSTEP * kF8T * 2 * NB * 16;
     static constexpr uint32_t STAGE = (A_BYTES + B_BYTES + 1023) / 1024 * 1024;
     static constexpr uint32_t OFF_BAR = NS * STAGE;
     static constexpr uint32_t BYTES = OFF_BAR + 64;     // 4 mbarriers, TMEM address slot
@@ -58,6 +63,8 @@ struct F8Cfg {
     static constexpr int TMEM_COLS = kF8Blk * NB <= 128 ? 128 : 256;  // 5 blocks of NB columns
     static_assert(kF8Blk * NB <= TMEM_COLS, "accumulator blocks");
     static_assert(NB == 16 || NB == 32, "output block");
+    static_assert(!PAIR || K == 3, "tap pairs are horizontal taps of a 3x3");
+    static_assert(SP <= kSW, "staged row");
     static_assert(A_BYTES % 16 == 0 && B_BYTES % 16 == 0, "bulk-copy granularity");
     static_assert(BYTES <= 227 * 1024, "shared memory per CTA");
     static_assert(PLANE / 16 < (1u << 14), "LBO field");
@@ -106,28 +113,35 @@ __global__ void f8_scale_kernel(const float* __restrict__ w, int cin, int cout, 
 }
 
 // Weight image of one layer: block (ob, c) = outputs nb ob .. + nb, inputs
-// 32 c .. + 32; inside it chunk (tap, term k, half h, row n) holds term k of
-// W[nb ob + n][32 c + 16 h .. + 16][tap] / s_o as 16 E4M3 codes.
+// 32 c .. + 32; inside it chunk (step, term k, half h, row n) holds term k of
+// W[nb ob + n][32 c + 16 h .. + 16][tap = step] / s_o as 16 E4M3 codes, or with
+// tap pairs (pair) W[nb ob + n][0 .. 16][kernel row step / 2, column
+// 2 (step % 2) + h] (zero for column 3).
 __global__ void f8_pack_kernel(const float* __restrict__ w, const float* __restrict__ scale, int cin, int cout, int k,
-                               int nb, uint4* __restrict__ img) {
+                               int nb, int pair, uint4* __restrict__ img) {
     const int taps = k * k, nc = (cin + kF8CC - 1) / kF8CC, nob = (cout + nb - 1) / nb;
-    const size_t chunks = static_cast<size_t>(nob) * nc * taps * kF8T * 2 * nb;
+    const int nstep = pair ? 2 * k : taps;
+    const size_t chunks = static_cast<size_t>(nob) * nc * nstep * kF8T * 2 * nb;
     for (size_t i = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; i < chunks;
          i += static_cast<size_t>(gridDim.x) * blockDim.x) {
         const int n = static_cast<int>(i % nb);
         size_t r = i / nb;
         const int h = static_cast<int>(r % 2); r /= 2;
         const int term = static_cast<int>(r % kF8T); r /= kF8T;
-        const int tap = static_cast<int>(r % taps); r /= taps;
+        const int step = static_cast<int>(r % nstep); r /= nstep;
         const int c = static_cast<int>(r % nc);
         const int ob = static_cast<int>(r / nc);
         const int o = ob * nb + n;
+        // a pair step's half h is horizontal tap 2 (step % 2) + h of kernel row step / 2 (none past kx = 2)
+        const int kx = pair ? 2 * (step % 2) + h : 0;
+        const int tap = pair ? (kx < k ? (step / 2) * k + kx : -1) : step;
         float v[16];
         const float s = o < cout ? __ldg(scale + o) : 1.f;
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
-            const int ch = c * kF8CC + h * 16 + j;
-            v[j] = (o < cout && ch < cin) ? __ldg(w + (static_cast<size_t>(o) * cin + ch) * taps + tap) / s : 0.f;
+            const int ch = pair ? j : c * kF8CC + h * 16 + j;
+            v[j] = (o < cout && ch < cin && tap >= 0)
+                       ? __ldg(w + (static_cast<size_t>(o) * cin + ch) * taps + tap) / s : 0.f;
         }
         uint4 t[kF8T];
         f8_split3(v, t);
@@ -135,19 +149,19 @@ __global__ void f8_pack_kernel(const float* __restrict__ w, const float* __restr
     }
 }
 
-template <int K, int NB>
+template <int K, int NB, bool PAIR>
 struct F8Regs {
-    float4 v[F8Cfg<K, NB>::S][4];
+    float4 v[F8Cfg<K, NB, PAIR>::S][4];
 };
 
 // Chunk c of tile (row yr, x0): item i = (staged row sr, group g, staged
 // pixel sp; pixel fastest) covers image row yr - K / 2 + sr, column
 // x0 - K / 2 + sp, input channels 32 c + 16 g .. + 16; zeros outside the image
 // and beyond C_in.
-template <int K, int NB>
-__device__ __forceinline__ void f8_load(F8Regs<K, NB>& R, const float* __restrict__ x, int H, int W, int CIN, int yr,
+template <int K, int NB, bool PAIR>
+__device__ __forceinline__ void f8_load(F8Regs<K, NB, PAIR>& R, const float* __restrict__ x, int H, int W, int CIN, int yr,
                                         int x0, int c) {
-    using C = F8Cfg<K, NB>;
+    using C = F8Cfg<K, NB, PAIR>;
 #pragma unroll
     for (int s = 0; s < C::S; ++s) {
         const int i = threadIdx.x + s * kF8Threads;
@@ -166,9 +180,9 @@ __device__ __forceinline__ void f8_load(F8Regs<K, NB>& R, const float* __restric
     }
 }
 
-template <int K, int NB>
-__device__ __forceinline__ void f8_store(const F8Regs<K, NB>& R, uint32_t abase, int relu_in) {
-    using C = F8Cfg<K, NB>;
+template <int K, int NB, bool PAIR>
+__device__ __forceinline__ void f8_store(const F8Regs<K, NB, PAIR>& R, uint32_t abase, int relu_in) {
+    using C = F8Cfg<K, NB, PAIR>;
 #pragma unroll
     for (int s = 0; s < C::S; ++s) {
         const int i = threadIdx.x + s * kF8Threads;
@@ -191,39 +205,42 @@ __device__ __forceinline__ void f8_store(const F8Regs<K, NB>& R, uint32_t abase,
     }
 }
 
-// The chunk's MMAs (one thread): per tap, weight term k and activation term
-// j, D block j + k; the first product into each block of a tile starts it.
-template <int K, int NB>
+// The chunk's MMAs (one thread): per K step, weight term k and activation
+// term j, D block j + k; the first product into each block of a tile starts it.
+template <int K, int NB, bool PAIR>
 __device__ __forceinline__ void f8_mma(uint32_t abase, uint32_t bbase, uint32_t tbase, bool first_chunk) {
-    using C = F8Cfg<K, NB>;
+    using C = F8Cfg<K, NB, PAIR>;
     constexpr uint32_t idesc = idesc_e4m3(kTileM, NB);
 #pragma unroll
-    for (int tap = 0; tap < K * K; ++tap) {
-        const int ky = tap / K, kx = tap % K;
+    for (int step = 0; step < C::NSTEP; ++step) {
+        // the step's first tap (ky, kx); its K halves: channel groups 0 and 1 of
+        // that tap's pixels, or (PAIR) the 16 channels of pixels m + kx and m + kx + 1
+        const int ky = PAIR ? step / 2 : step / K, kx = PAIR ? 2 * (step % 2) : step % K;
+        const uint32_t lbo = PAIR ? 16u : C::PLANE;
 #pragma unroll
         for (int k = 0; k < kF8T; ++k) {
             const uint64_t bdesc =
-                smem_desc(bbase + static_cast<uint32_t>((tap * kF8T + k) * 2 * NB) * 16, NB * 16, 128);
+                smem_desc(bbase + static_cast<uint32_t>((step * kF8T + k) * 2 * NB) * 16, NB * 16, 128);
 #pragma unroll
             for (int j = 0; j < kF8T; ++j) {
                 // in the (k, j) order above, block j + k is first written by (0, j) or, for j + k > 2, by (k, 2)
-                const bool starts = tap == 0 && (k == 0 || j == kF8T - 1);
+                const bool starts = step == 0 && (k == 0 || j == kF8T - 1);
                 const uint32_t a = abase + static_cast<uint32_t>(j * C::G) * C::PLANE +
                                    static_cast<uint32_t>(ky * kSW + kx) * 16;
-                mma_e4m3(tbase + static_cast<uint32_t>((j + k) * NB), smem_desc(a, C::PLANE, 128), bdesc, idesc,
+                mma_e4m3(tbase + static_cast<uint32_t>((j + k) * NB), smem_desc(a, lbo, 128), bdesc, idesc,
                          (first_chunk && starts) ? 0u : 1u);
             }
         }
     }
 }
 
-template <int K, int NB>
+template <int K, int NB, bool PAIR>
 __global__ void __launch_bounds__(kF8Threads, 2) f8x3_conv_kernel(const float* __restrict__ x, int relu_in, int H, int W,
                                                                int CIN, int COUT, const uint4* __restrict__ img,
                                                                const float* __restrict__ scale,
                                                                const float* __restrict__ bias, float* __restrict__ y,
                                                                int* err) {
-    using C = F8Cfg<K, NB>;
+    using C = F8Cfg<K, NB, PAIR>;
     extern __shared__ __align__(1024) uint8_t smem[];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     uint64_t* full = reinterpret_cast<uint64_t*>(smem + C::OFF_BAR);       // [2] weights landed
@@ -248,7 +265,7 @@ __global__ void __launch_bounds__(kF8Threads, 2) f8x3_conv_kernel(const float* _
     int pend[2] = {0, 0};
     bool ok = true;
     int it = 0;
-    F8Regs<K, NB> R;
+    F8Regs<K, NB, PAIR> R;
     for (long long t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
         const int ob = static_cast<int>(t % nob);
         const long long r = t / nob;
@@ -256,7 +273,7 @@ __global__ void __launch_bounds__(kF8Threads, 2) f8x3_conv_kernel(const float* _
         for (int c = 0; c < nc; ++c, ++it) {
             const int s = C::NS == 2 ? (it & 1) : 0;
             const uint32_t abase = sbase + s * C::STAGE, bbase = abase + C::A_BYTES;
-            f8_load<K, NB>(R, x, H, W, CIN, yr, x0, c);  // in flight while the other stage's MMAs run
+            f8_load<K, NB, PAIR>(R, x, H, W, CIN, yr, x0, c);  // in flight while the other stage's MMAs run
             if (pend[s]) {
                 ok = mbar_wait_bounded(&done[s], dph[s], kWaitNs);
                 dph[s] ^= 1u;
@@ -267,13 +284,13 @@ __global__ void __launch_bounds__(kF8Threads, 2) f8x3_conv_kernel(const float* _
                 mbar_arrive_expect_tx(&full[s], C::B_BYTES);
                 bulk_load(bbase, img + (static_cast<size_t>(ob) * nc + c) * block_chunks, C::B_BYTES, &full[s]);
             }
-            f8_store<K, NB>(R, abase, relu_in);
+            f8_store<K, NB, PAIR>(R, abase, relu_in);
             fence_proxy_async_smem();
             __syncthreads();
             if (tid == 0) {
                 if (mbar_wait_bounded(&full[s], fph[s], kWaitNs)) {
                     fence_after_sync();
-                    f8_mma<K, NB>(abase, bbase, tbase, c == 0);
+                    f8_mma<K, NB, PAIR>(abase, bbase, tbase, c == 0);
                 } else {
                     atomicExch(err, kF8ErrCode);
                 }
@@ -334,19 +351,19 @@ __global__ void __launch_bounds__(kF8Threads, 2) f8x3_conv_kernel(const float* _
     if (warp == 0) tmem_dealloc(tbase, C::TMEM_COLS);
 }
 
-template <int K, int NB>
+template <int K, int NB, bool PAIR>
 cudaError_t launch_f8x3(const float* x, int relu_in, int H, int W, int cin, int cout, const uint4* img,
                         const float* scale, const float* bias, float* y, int* err, cudaStream_t st) {
-    using C = F8Cfg<K, NB>;
+    using C = F8Cfg<K, NB, PAIR>;
     static int per_sm = 0;  // CTAs resident per SM (per instantiation, set on first use)
     if (per_sm == 0) {
-        cudaError_t e = cudaFuncSetAttribute(f8x3_conv_kernel<K, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaError_t e = cudaFuncSetAttribute(f8x3_conv_kernel<K, NB, PAIR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              static_cast<int>(C::BYTES));
         if (e != cudaSuccess) return e;
-        e = cudaFuncSetAttribute(f8x3_conv_kernel<K, NB>, cudaFuncAttributePreferredSharedMemoryCarveout,
+        e = cudaFuncSetAttribute(f8x3_conv_kernel<K, NB, PAIR>, cudaFuncAttributePreferredSharedMemoryCarveout,
                                  cudaSharedmemCarveoutMaxShared);
         if (e != cudaSuccess) return e;
-        const int occ = resident_ctas_per_sm(reinterpret_cast<const void*>(f8x3_conv_kernel<K, NB>), kF8Threads,
+        const int occ = resident_ctas_per_sm(reinterpret_cast<const void*>(f8x3_conv_kernel<K, NB, PAIR>), kF8Threads,
                                              C::BYTES);
         per_sm = occ < 512 / C::TMEM_COLS ? occ : 512 / C::TMEM_COLS;
     }
@@ -354,12 +371,15 @@ cudaError_t launch_f8x3(const float* x, int relu_in, int H, int W, int cin, int 
     if (tiles == 0) return cudaSuccess;
     const long long cap = static_cast<long long>(num_sms()) * per_sm;
     const int grid = static_cast<int>(tiles < cap ? tiles : cap);
-    f8x3_conv_kernel<K, NB><<<grid, kF8Threads, C::BYTES, st>>>(x, relu_in, H, W, cin, cout, img, scale, bias, y, err);
+    f8x3_conv_kernel<K, NB, PAIR><<<grid, kF8Threads, C::BYTES, st>>>(x, relu_in, H, W, cin, cout, img, scale, bias, y,
+                                                                        err);
     return cudaGetLastError();
 }
 
-// output channels per CTA: 16 for a 16-channel layer, else 32
+// output channels per CTA: 16 for a 16-channel layer, else 32; tap pairs for a
+// 3x3 layer with at most 16 input channels
 constexpr int f8_nb(int cout) { return cout % 32 == 0 ? 32 : 16; }
+constexpr bool f8_pair(int cin, int k) { return k == 3 && cin <= 16; }
 
 }  // namespace
 
@@ -370,36 +390,46 @@ bool f8x3_supported(int cin, int cout, int k) {
 size_t f8x3_image_bytes(int cin, int cout, int k) {
     if (!f8x3_supported(cin, cout, k)) return 0;
     const size_t nb = f8_nb(cout), nob = (cout + nb - 1) / nb, nc = (cin + kF8CC - 1) / kF8CC;
-    return nob * nc * k * k * kF8T * 2 * nb * 16 + align_up(nob * nb * sizeof(float), 256);
+    const size_t nstep = f8_pair(cin, k) ? 2 * k : k * k;
+    return nob * nc * nstep * kF8T * 2 * nb * 16 + align_up(nob * nb * sizeof(float), 256);
+}
+
+// the weight terms' chunks of a layer's image (the scales follow them)
+static size_t f8x3_chunks(int cin, int cout, int k) {
+    const size_t nb = f8_nb(cout), nob = (cout + nb - 1) / nb, nc = (cin + kF8CC - 1) / kF8CC;
+    const size_t nstep = f8_pair(cin, k) ? 2 * k : k * k;
+    return nob * nc * nstep * kF8T * 2 * nb;
 }
 
 cudaError_t f8x3_pack(const float* w, int cin, int cout, int k, void* img, cudaStream_t st) {
     if (!f8x3_supported(cin, cout, k)) return cudaErrorInvalidValue;
-    const size_t nb = f8_nb(cout), nob = (cout + nb - 1) / nb, nc = (cin + kF8CC - 1) / kF8CC;
-    const size_t chunks = nob * nc * k * k * kF8T * 2 * nb;
+    const size_t chunks = f8x3_chunks(cin, cout, k);
     float* scale = reinterpret_cast<float*>(static_cast<char*>(img) + chunks * 16);
     f8_scale_kernel<<<(cout + 127) / 128, 128, 0, st>>>(w, cin, cout, k * k, scale);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const size_t blocks = (chunks + 255) / 256, cap = static_cast<size_t>(num_sms()) * 8;
-    f8_pack_kernel<<<static_cast<int>(blocks < cap ? blocks : cap), 256, 0, st>>>(w, scale, cin, cout, k,
-                                                                                  static_cast<int>(nb),
-                                                                                  static_cast<uint4*>(img));
+    f8_pack_kernel<<<static_cast<int>(blocks < cap ? blocks : cap), 256, 0, st>>>(
+        w, scale, cin, cout, k, f8_nb(cout), f8_pair(cin, k) ? 1 : 0, static_cast<uint4*>(img));
     return cudaGetLastError();
 }
 
 cudaError_t f8x3_conv(int cin, int cout, int k, const float* x, int relu_in, int H, int W, const void* img,
                       const float* bias, float* y, int* err, cudaStream_t st) {
     if (!f8x3_supported(cin, cout, k)) return cudaErrorInvalidValue;
-    const size_t nb = f8_nb(cout), nob = (cout + nb - 1) / nb, nc = (cin + kF8CC - 1) / kF8CC;
-    const size_t chunks = nob * nc * k * k * kF8T * 2 * nb;
     const uint4* im = static_cast<const uint4*>(img);
-    const float* scale = reinterpret_cast<const float*>(static_cast<const char*>(img) + chunks * 16);
-    if (k == 3)
-        return nb == 16 ? launch_f8x3<3, 16>(x, relu_in, H, W, cin, cout, im, scale, bias, y, err, st)
-                        : launch_f8x3<3, 32>(x, relu_in, H, W, cin, cout, im, scale, bias, y, err, st);
-    return nb == 16 ? launch_f8x3<1, 16>(x, relu_in, H, W, cin, cout, im, scale, bias, y, err, st)
-                    : launch_f8x3<1, 32>(x, relu_in, H, W, cin, cout, im, scale, bias, y, err, st);
+    const float* scale =
+        reinterpret_cast<const float*>(static_cast<const char*>(img) + f8x3_chunks(cin, cout, k) * 16);
+    const bool nb16 = f8_nb(cout) == 16;
+    if (k == 3) {
+        if (f8_pair(cin, k))
+            return nb16 ? launch_f8x3<3, 16, true>(x, relu_in, H, W, cin, cout, im, scale, bias, y, err, st)
+                        : launch_f8x3<3, 32, true>(x, relu_in, H, W, cin, cout, im, scale, bias, y, err, st);
+        return nb16 ? launch_f8x3<3, 16, false>(x, relu_in, H, W, cin, cout, im, scale, bias, y, err, st)
+                    : launch_f8x3<3, 32, false>(x, relu_in, H, W, cin, cout, im, scale, bias, y, err, st);
+    }
+    return nb16 ? launch_f8x3<1, 16, false>(x, relu_in, H, W, cin, cout, im, scale, bias, y, err, st)
+                : launch_f8x3<1, 32, false>(x, relu_in, H, W, cin, cout, im, scale, bias, y, err, st);
 }
 
 }  // namespace tr
