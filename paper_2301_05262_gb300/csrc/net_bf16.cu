@@ -641,13 +641,6 @@ __global__ void __launch_bounds__(32 * tc_warps(NEW, NPW, EPI), 1) level_tc_kern
         *s_abort = 0;
     }
     if (warp == MW) tmem_alloc(tslot, C::TMEM_COLS);
-    if (PRO == TPRO_GATHER && a.timing && blockIdx.x == 0 && tid == 0) {
-        // batched serving: the batch starts now; clear the views' completion records
-        unsigned long long t;
-        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-        a.timing[0] = t;
-        for (int v = 0; v < a.nviews; ++v) a.timing[1 + v] = a.timing[1 + kMaxViews + v] = 0;
-    }
     fence_proxy_async_smem();  // the weights are read by the tensor core
     fence_before_sync();
     __syncthreads();
@@ -658,6 +651,15 @@ __global__ void __launch_bounds__(32 * tc_warps(NEW, NPW, EPI), 1) level_tc_kern
     // only after the previous stage has completed.
     griddep_launch_dependents();
     griddep_wait();
+    if (PRO == TPRO_GATHER && a.timing && blockIdx.x == 0 && tid == 0) {
+        // batched serving: the batch starts now (after the previous kernel of the
+        // stream, which may be the previous batch's level-0 decoder still writing
+        // these records); clear the views' completion records
+        unsigned long long t;
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+        a.timing[0] = t;
+        for (int v = 0; v < a.nviews; ++v) a.timing[1 + v] = a.timing[1 + kMaxViews + v] = 0;
+    }
     const uint32_t tbase = *tslot;
     // this CTA's tiles: a contiguous range of the tile list, which runs
     // column-major within each view (vertical strips of 128-pixel columns)
@@ -1376,8 +1378,10 @@ cudaError_t tc_prepare_stage(int stage, int variant, TcBatch& b) {
 cudaError_t tc_launch_stage(int stage, int variant, TcBatch& b, int ctas_per_sm, cudaStream_t stream) {
     cudaError_t e = tc_prepare_stage(stage, variant, b);
     if (e != cudaSuccess) return e;
-    // stages after the first overlap their set-up with the previous stage's tail
-    return kStages[stage].v[variant].fn(b, ctas_per_sm, stream, stage > 0);
+    // every stage overlaps its set-up with the tail of the previous kernel of the
+    // stream (for the first stage: the previous frame's level-0 decoder); each
+    // reads its inputs only after griddepcontrol.wait
+    return kStages[stage].v[variant].fn(b, ctas_per_sm, stream, true);
 }
 
 const char* const kInferKernelNamesBf16[kInferKernelsBf16] = {
