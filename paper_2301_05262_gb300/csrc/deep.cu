@@ -136,9 +136,10 @@ static cudaError_t deep_forward_f8x3(nsm_ctx* ctx, const nsm_frame* frame, const
     if (e == cudaSuccess) e = cudaMemcpyAsync(dgp, &g, sizeof(g), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = tr::features_batch(dgp, 1, H, W, feat, st);
     auto wd = [](int l) { return 16 << l; };
-    auto conv = [&](int li, const float* x, int relu_in, int Hl, int Wl, float* y) {
+    auto conv = [&](int li, const float* x, int relu_in, int Hl, int Wl, float* y, int relu_out = 0) {
         const DeepLayer& d = Ls[li];
-        return tr::f8x3_conv(d.cin, d.cout, d.k, x, relu_in, Hl, Wl, img[li], params + d.b, y, ctx->d_err, st);
+        return tr::f8x3_conv(d.cin, d.cout, d.k, x, relu_in, Hl, Wl, img[li], params + d.b, y, relu_out, ctx->d_err,
+                             st);
     };
     std::vector<float*> skips(L, nullptr);
     const float* cur = feat;
@@ -147,27 +148,28 @@ static cudaError_t deep_forward_f8x3(nsm_ctx* ctx, const nsm_frame* frame, const
     for (int l = 0; l < L - 1 && e == cudaSuccess; ++l, li += 2) {
         const int Hl = H >> l, Wl = W >> l;
         float* pooled = cur == h ? xin : h;
+        // the 1x1 writes its rectified output: the skip (levels >= 1) or a1; the pooling reads it
+        float* out1 = a1;
         if (l >= 1) {
             skips[l] = skip + skip_off;
             skip_off += static_cast<size_t>(Hl) * Wl * wd(l);
+            out1 = skips[l];
         }
         e = conv(li, cur, 0, Hl, Wl, a3);
-        if (e == cudaSuccess) e = conv(li + 1, a3, 1, Hl, Wl, a1);
-        if (e == cudaSuccess && l >= 1) e = tr::relu_copy(a1, static_cast<size_t>(Hl) * Wl * wd(l), skips[l], st);
-        if (e == cudaSuccess) e = tr::pool_relu(a1, 1, Hl, Wl, wd(l), pooled, st);
+        if (e == cudaSuccess) e = conv(li + 1, a3, 1, Hl, Wl, out1, 1);
+        if (e == cudaSuccess) e = tr::pool_relu(out1, 1, Hl, Wl, wd(l), pooled, st);
         cur = pooled;
     }
     const int Hb = H >> (L - 1), Wb = W >> (L - 1);
     if (e == cudaSuccess) e = conv(li++, cur, 0, Hb, Wb, a3);
-    if (e == cudaSuccess) e = conv(li++, a3, 1, Hb, Wb, a1);
-    if (e == cudaSuccess) e = tr::relu_copy(a1, static_cast<size_t>(Hb) * Wb * wd(L - 2), h, st);
+    if (e == cudaSuccess) e = conv(li++, a3, 1, Hb, Wb, h, 1);  // cur was read by the 3x3 already
     const float* lo = h;
     for (int l = L - 2; l >= 0 && e == cudaSuccess; --l, li += 2) {
         const int Hl = H >> l, Wl = W >> l;
         e = tr::up_add(lo, l >= 1 ? skips[l] : nullptr, 1, Hl, Wl, wd(l), xin, st);
         if (e == cudaSuccess) e = conv(li, xin, 0, Hl, Wl, a3);
-        if (e == cudaSuccess) e = conv(li + 1, a3, 1, Hl, Wl, a1);
-        if (e == cudaSuccess && l >= 1) e = tr::relu_copy(a1, static_cast<size_t>(Hl) * Wl * wd(l - 1), h, st);
+        // levels >= 1: the rectified output into h (read by the up-sampling already); level 0: a1 for the head
+        if (e == cudaSuccess) e = conv(li + 1, a3, 1, Hl, Wl, l >= 1 ? h : a1, l >= 1 ? 1 : 0);
         lo = l >= 1 ? h : a1;
     }
     if (e == cudaSuccess) e = tr::head(lo, params + Ls[li].w, static_cast<size_t>(H) * W, vis, st);
@@ -242,9 +244,10 @@ static cudaError_t deep_forward_bf16(nsm_ctx* ctx, const nsm_frame* frame, const
     if ((e = stage(0, ENC0_3, ENC0_1)) != cudaSuccess || (e = stage(1, ENC1_3, ENC1_1)) != cudaSuccess) return e;
     // inner levels on FP32 NHWC tensors, from the pooled level-1 output
     auto wd = [](int l) { return 16 << l; };
-    auto conv = [&](int li, const float* x, int relu_in, int Hl, int Wl, float* y) {
+    auto conv = [&](int li, const float* x, int relu_in, int Hl, int Wl, float* y, int relu_out = 0) {
         const DeepLayer& d = Ls[li];
-        return tr::deep_tc_conv(d.cin, d.cout, d.k, x, relu_in, Hl, Wl, mid[li], params + d.b, y, ctx->d_err, st);
+        return tr::deep_tc_conv(d.cin, d.cout, d.k, x, relu_in, Hl, Wl, mid[li], params + d.b, y, relu_out,
+                                ctx->d_err, st);
     };
     const size_t n2 = static_cast<size_t>(H / 4) * (W / 4);
     deep_pairs_to_f32_kernel<32><<<static_cast<int>(std::min<size_t>((n2 * 32 + 255) / 256, 4096)), 256, 0, st>>>(
@@ -259,22 +262,20 @@ static cudaError_t deep_forward_bf16(nsm_ctx* ctx, const nsm_frame* frame, const
         float* pooled = cur == h ? xin : h;
         skips[l] = skip + skip_off;
         skip_off += static_cast<size_t>(Hl) * Wl * wd(l);
+        // the 1x1 writes the rectified skip directly; the pooling reads it
         e = conv(li, cur, 0, Hl, Wl, a3);
-        if (e == cudaSuccess) e = conv(li + 1, a3, 1, Hl, Wl, a1);
-        if (e == cudaSuccess) e = tr::relu_copy(a1, static_cast<size_t>(Hl) * Wl * wd(l), skips[l], st);
-        if (e == cudaSuccess) e = tr::pool_relu(a1, 1, Hl, Wl, wd(l), pooled, st);
+        if (e == cudaSuccess) e = conv(li + 1, a3, 1, Hl, Wl, skips[l], 1);
+        if (e == cudaSuccess) e = tr::pool_relu(skips[l], 1, Hl, Wl, wd(l), pooled, st);
         cur = pooled;
     }
     const int Hb = H >> (L - 1), Wb = W >> (L - 1);
     if (e == cudaSuccess) e = conv(li++, cur, 0, Hb, Wb, a3);
-    if (e == cudaSuccess) e = conv(li++, a3, 1, Hb, Wb, a1);
-    if (e == cudaSuccess) e = tr::relu_copy(a1, static_cast<size_t>(Hb) * Wb * wd(L - 2), h, st);
+    if (e == cudaSuccess) e = conv(li++, a3, 1, Hb, Wb, h, 1);  // cur was read by the 3x3 already
     for (int l = L - 2; l >= 2 && e == cudaSuccess; --l, li += 2) {
         const int Hl = H >> l, Wl = W >> l;
         e = tr::up_add(h, skips[l], 1, Hl, Wl, wd(l), xin, st);
         if (e == cudaSuccess) e = conv(li, xin, 0, Hl, Wl, a3);
-        if (e == cudaSuccess) e = conv(li + 1, a3, 1, Hl, Wl, a1);
-        if (e == cudaSuccess) e = tr::relu_copy(a1, static_cast<size_t>(Hl) * Wl * wd(l - 1), h, st);
+        if (e == cudaSuccess) e = conv(li + 1, a3, 1, Hl, Wl, h, 1);  // h was read by the up-sampling
     }
     if (e != cudaSuccess) return e;
     // the level-2 output (32 channels at H / 4) is what the level-1 decoder up-samples

@@ -1,5 +1,5 @@
 // Tensor-core layers of the deeper networks' inner levels (Sec. 3.6; layers
-// of Sec. 3.5 with widths 16 * 2^l): y = conv_k(relu?(x)) + b for k = 3
+// of Sec. 3.5 with widths 16 * 2^l): y = relu?(conv_k(relu?(x)) + b) for k = 3
 // (zero padded) and k = 1, FP32 NHWC tensors in and out, 32 .. 1024
 // channels.  The products run on tcgen05 in compensated BF16: every
 // activation and weight is a pair hi = bf16(v), lo = bf16(v - hi); all four
@@ -180,7 +180,7 @@ template <int K, int CC, int RR>
 __global__ void __launch_bounds__(kDcThreads) deep_conv_kernel(const float* __restrict__ x, int relu_in, int H, int W,
                                                                int CIN, int COUT, const uint4* __restrict__ img,
                                                                const float* __restrict__ bias, float* __restrict__ y,
-                                                               int* err) {
+                                                               int relu_out, int* err) {
     using C = DcCfg<K, CC, RR>;
     extern __shared__ __align__(1024) uint8_t smem[];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -265,11 +265,13 @@ __global__ void __launch_bounds__(kDcThreads) deep_conv_kernel(const float* __re
             if (px < W && yr + rr < H && o0 < COUT) {
                 float* out = y + (static_cast<size_t>(yr + rr) * W + px) * COUT + o0;
 #pragma unroll
-                for (int o = 0; o < 32; o += 4)
-                    *reinterpret_cast<float4*>(out + o) =
-                        make_float4(a[o] + b[o] + __ldg(bias + o0 + o), a[o + 1] + b[o + 1] + __ldg(bias + o0 + o + 1),
-                                    a[o + 2] + b[o + 2] + __ldg(bias + o0 + o + 2),
-                                    a[o + 3] + b[o + 3] + __ldg(bias + o0 + o + 3));
+                for (int o = 0; o < 32; o += 4) {
+                    float4 v = make_float4(a[o] + b[o] + __ldg(bias + o0 + o), a[o + 1] + b[o + 1] + __ldg(bias + o0 + o + 1),
+                                           a[o + 2] + b[o + 2] + __ldg(bias + o0 + o + 2),
+                                           a[o + 3] + b[o + 3] + __ldg(bias + o0 + o + 3));
+                    if (relu_out) v = make_float4(fmaxf(v.x, 0.f), fmaxf(v.y, 0.f), fmaxf(v.z, 0.f), fmaxf(v.w, 0.f));
+                    *reinterpret_cast<float4*>(out + o) = v;
+                }
             }
         }
         // accumulators read out before the next tile's first MMA overwrites them
@@ -289,7 +291,7 @@ __global__ void __launch_bounds__(kDcThreads) deep_conv_kernel(const float* __re
 
 template <int K, int CC, int RR>
 cudaError_t launch_deep_conv(const float* x, int relu_in, int H, int W, int cin, int cout, const uint4* img,
-                             const float* bias, float* y, int* err, cudaStream_t st) {
+                             const float* bias, float* y, int relu_out, int* err, cudaStream_t st) {
     using C = DcCfg<K, CC, RR>;
     static int per_sm = 0;  // CTAs resident per SM (per instantiation, set on first use)
     if (per_sm == 0) {
@@ -308,7 +310,8 @@ cudaError_t launch_deep_conv(const float* x, int relu_in, int H, int W, int cin,
     if (tiles == 0) return cudaSuccess;
     const long long cap = static_cast<long long>(num_sms()) * per_sm;
     const int grid = static_cast<int>(tiles < cap ? tiles : cap);
-    deep_conv_kernel<K, CC, RR><<<grid, kDcThreads, C::BYTES, st>>>(x, relu_in, H, W, cin, cout, img, bias, y, err);
+    deep_conv_kernel<K, CC, RR><<<grid, kDcThreads, C::BYTES, st>>>(x, relu_in, H, W, cin, cout, img, bias, y,
+                                                                      relu_out, err);
     return cudaGetLastError();
 }
 
@@ -335,18 +338,18 @@ cudaError_t deep_tc_pack(const float* w, int cin, int cout, int k, uint4* img, c
 }
 
 cudaError_t deep_tc_conv(int cin, int cout, int k, const float* x, int relu_in, int H, int W, const uint4* img,
-                         const float* bias, float* y, int* err, cudaStream_t st) {
+                         const float* bias, float* y, int relu_out, int* err, cudaStream_t st) {
     if (!deep_tc_supported(cin, cout, k)) return cudaErrorInvalidValue;
-    if (k == 1) return launch_deep_conv<1, 64, 1>(x, relu_in, H, W, cin, cout, img, bias, y, err, st);
+    if (k == 1) return launch_deep_conv<1, 64, 1>(x, relu_in, H, W, cin, cout, img, bias, y, relu_out, err, st);
     // a 3x3 tile of R image rows reuses each streamed weight chunk R times:
     // the largest R whose tiles still give every SM one
     const long long per_row = static_cast<long long>((W + kTileM - 1) / kTileM) * ((cout + kDcNB - 1) / kDcNB);
     const long long sms = num_sms();
     if (static_cast<long long>((H + 3) / 4) * per_row >= sms)
-        return launch_deep_conv<3, 16, 4>(x, relu_in, H, W, cin, cout, img, bias, y, err, st);
+        return launch_deep_conv<3, 16, 4>(x, relu_in, H, W, cin, cout, img, bias, y, relu_out, err, st);
     if (static_cast<long long>((H + 1) / 2) * per_row >= sms)
-        return launch_deep_conv<3, 16, 2>(x, relu_in, H, W, cin, cout, img, bias, y, err, st);
-    return launch_deep_conv<3, 16, 1>(x, relu_in, H, W, cin, cout, img, bias, y, err, st);
+        return launch_deep_conv<3, 16, 2>(x, relu_in, H, W, cin, cout, img, bias, y, relu_out, err, st);
+    return launch_deep_conv<3, 16, 1>(x, relu_in, H, W, cin, cout, img, bias, y, relu_out, err, st);
 }
 
 }  // namespace tr

@@ -1,5 +1,5 @@
 // Three-term FP8 (E4M3) layers (network of Sec. 3.5 / 3.6; 8-bit storage is
-// among the paper's Sec. 3.5 directions): y = conv_k(relu?(x)) + b, k = 3
+// among the paper's Sec. 3.5 directions): y = relu?(conv_k(relu?(x)) + b), k = 3
 // (zero padded) or 1, FP32 NHWC tensors in and out, products on tcgen05
 // kind::f8f6f4 (E4M3 x E4M3, FP32 accumulation).
 //
@@ -239,7 +239,7 @@ __global__ void __launch_bounds__(kF8Threads, 2) f8x3_conv_kernel(const float* _
                                                                int CIN, int COUT, const uint4* __restrict__ img,
                                                                const float* __restrict__ scale,
                                                                const float* __restrict__ bias, float* __restrict__ y,
-                                                               int* err) {
+                                                               int relu_out, int* err) {
     using C = F8Cfg<K, NB, PAIR>;
     extern __shared__ __align__(1024) uint8_t smem[];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -333,6 +333,7 @@ __global__ void __launch_bounds__(kF8Threads, 2) f8x3_conv_kernel(const float* _
                         a = fmaf(a, 1.f / 16.f, d[0][o + e]);
                         const int oc = o0 + 8 * hp + o + e;
                         v[e] = fmaf(a, __ldg(scale + oc), __ldg(bias + oc));
+                        if (relu_out) v[e] = fmaxf(v[e], 0.f);
                     }
                     *reinterpret_cast<float4*>(out + o) = make_float4(v[0], v[1], v[2], v[3]);
                 }
@@ -353,7 +354,7 @@ __global__ void __launch_bounds__(kF8Threads, 2) f8x3_conv_kernel(const float* _
 
 template <int K, int NB, bool PAIR>
 cudaError_t launch_f8x3(const float* x, int relu_in, int H, int W, int cin, int cout, const uint4* img,
-                        const float* scale, const float* bias, float* y, int* err, cudaStream_t st) {
+                        const float* scale, const float* bias, float* y, int relu_out, int* err, cudaStream_t st) {
     using C = F8Cfg<K, NB, PAIR>;
     static int per_sm = 0;  // CTAs resident per SM (per instantiation, set on first use)
     if (per_sm == 0) {
@@ -372,7 +373,7 @@ cudaError_t launch_f8x3(const float* x, int relu_in, int H, int W, int cin, int 
     const long long cap = static_cast<long long>(num_sms()) * per_sm;
     const int grid = static_cast<int>(tiles < cap ? tiles : cap);
     f8x3_conv_kernel<K, NB, PAIR><<<grid, kF8Threads, C::BYTES, st>>>(x, relu_in, H, W, cin, cout, img, scale, bias, y,
-                                                                        err);
+                                                                        relu_out, err);
     return cudaGetLastError();
 }
 
@@ -415,7 +416,7 @@ cudaError_t f8x3_pack(const float* w, int cin, int cout, int k, void* img, cudaS
 }
 
 cudaError_t f8x3_conv(int cin, int cout, int k, const float* x, int relu_in, int H, int W, const void* img,
-                      const float* bias, float* y, int* err, cudaStream_t st) {
+                      const float* bias, float* y, int relu_out, int* err, cudaStream_t st) {
     if (!f8x3_supported(cin, cout, k)) return cudaErrorInvalidValue;
     const uint4* im = static_cast<const uint4*>(img);
     const float* scale =
@@ -423,13 +424,13 @@ cudaError_t f8x3_conv(int cin, int cout, int k, const float* x, int relu_in, int
     const bool nb16 = f8_nb(cout) == 16;
     if (k == 3) {
         if (f8_pair(cin, k))
-            return nb16 ? launch_f8x3<3, 16, true>(x, relu_in, H, W, cin, cout, im, scale, bias, y, err, st)
-                        : launch_f8x3<3, 32, true>(x, relu_in, H, W, cin, cout, im, scale, bias, y, err, st);
-        return nb16 ? launch_f8x3<3, 16, false>(x, relu_in, H, W, cin, cout, im, scale, bias, y, err, st)
-                    : launch_f8x3<3, 32, false>(x, relu_in, H, W, cin, cout, im, scale, bias, y, err, st);
+            return nb16 ? launch_f8x3<3, 16, true>(x, relu_in, H, W, cin, cout, im, scale, bias, y, relu_out, err, st)
+                        : launch_f8x3<3, 32, true>(x, relu_in, H, W, cin, cout, im, scale, bias, y, relu_out, err, st);
+        return nb16 ? launch_f8x3<3, 16, false>(x, relu_in, H, W, cin, cout, im, scale, bias, y, relu_out, err, st)
+                    : launch_f8x3<3, 32, false>(x, relu_in, H, W, cin, cout, im, scale, bias, y, relu_out, err, st);
     }
-    return nb16 ? launch_f8x3<1, 16, false>(x, relu_in, H, W, cin, cout, im, scale, bias, y, err, st)
-                : launch_f8x3<1, 32, false>(x, relu_in, H, W, cin, cout, im, scale, bias, y, err, st);
+    return nb16 ? launch_f8x3<1, 16, false>(x, relu_in, H, W, cin, cout, im, scale, bias, y, relu_out, err, st)
+                : launch_f8x3<1, 32, false>(x, relu_in, H, W, cin, cout, im, scale, bias, y, relu_out, err, st);
 }
 
 }  // namespace tr

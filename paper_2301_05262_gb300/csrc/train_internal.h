@@ -74,7 +74,7 @@ cudaError_t dec_level_fused(int cin, int cout1, const float* lo, const float* sk
                             const float* wt3, const float* b3, const float* w1, const float* b1, int relu_out, float* y,
                             const float* wh, float* vis, cudaStream_t st);
 // Tensor-core layers of the deeper networks' inner levels (deep_tc.cu):
-// y = conv_k(relu?(x)) + b, FP32 NHWC [H][W][C], k = 3 (zero padded) or 1,
+// y = relu?(conv_k(relu?(x)) + b) (relu_out), FP32 NHWC [H][W][C], k = 3 (zero padded) or 1,
 // compensated BF16 operands, FP32 accumulation.  Supported: C_in a multiple of
 // 16 (k = 3) or 64 (k = 1), C_out a multiple of 32.  The weight image (packed
 // from OIHW once per call, deep_tc_image_bytes bytes, 16-byte aligned) feeds
@@ -83,8 +83,8 @@ bool deep_tc_supported(int cin, int cout, int k);
 size_t deep_tc_image_bytes(int cin, int cout, int k);
 cudaError_t deep_tc_pack(const float* w, int cin, int cout, int k, uint4* img, cudaStream_t st);
 cudaError_t deep_tc_conv(int cin, int cout, int k, const float* x, int relu_in, int H, int W, const uint4* img,
-                         const float* bias, float* y, int* err, cudaStream_t st);
-// Three-term FP8 (E4M3) layers (fp8x3.cu): y = conv_k(relu?(x)) + b on FP32
+                         const float* bias, float* y, int relu_out, int* err, cudaStream_t st);
+// Three-term FP8 (E4M3) layers (fp8x3.cu): y = relu?(conv_k(relu?(x)) + b) on FP32
 // NHWC tensors, k = 3 or 1, activations and per-output-channel-scaled weights
 // as three E4M3 terms each (scales 1, 2^-4, 2^-8), products on tcgen05
 // kind::f8f6f4 with FP32 accumulation.  Supported: C_in a multiple of 4, C_out a
@@ -95,7 +95,7 @@ bool f8x3_supported(int cin, int cout, int k);
 size_t f8x3_image_bytes(int cin, int cout, int k);
 cudaError_t f8x3_pack(const float* w, int cin, int cout, int k, void* img, cudaStream_t st);
 cudaError_t f8x3_conv(int cin, int cout, int k, const float* x, int relu_in, int H, int W, const void* img,
-                      const float* bias, float* y, int* err, cudaStream_t st);
+                      const float* bias, float* y, int relu_out, int* err, cudaStream_t st);
 cudaError_t pool_relu(const float* x, int N, int H, int W, int C, float* y, cudaStream_t st);        // avg2x2(relu(x))
 cudaError_t up_add(const float* lo, const float* skip, int N, int H, int W, int C, float* y, cudaStream_t st);
 cudaError_t relu_copy(const float* x, size_t n, float* y, cudaStream_t st);
