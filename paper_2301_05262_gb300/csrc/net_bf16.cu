@@ -1294,13 +1294,17 @@ static const Variant kVarDec1[] = {
     NSM_VARIANT2(2, 4, 8, 2, 32, 32, 16, TPRO_UP_SKIP, TEPI_STORE_PAIR),
     NSM_VARIANT2(2, 8, 8, 2, 32, 32, 16, TPRO_UP_SKIP, TEPI_STORE_PAIR),
     NSM_VARIANT(2, 4, 9, 2, 0, 32, 32, 16, TPRO_UP_SKIP, TEPI_STORE_PAIR),
-    NSM_VARIANT(2, 8, 9, 2, 0, 32, 32, 16, TPRO_UP_SKIP, TEPI_STORE_PAIR)};
+    NSM_VARIANT(2, 8, 9, 2, 0, 32, 32, 16, TPRO_UP_SKIP, TEPI_STORE_PAIR),
+    NSM_VARIANT(2, 4, 12, 2, 0, 32, 32, 16, TPRO_UP_SKIP, TEPI_STORE_PAIR),
+    NSM_VARIANT(2, 8, 12, 2, 0, 32, 32, 16, TPRO_UP_SKIP, TEPI_STORE_PAIR)};
 // level-0 decoder on the coarse grid: the tile is R coarse rows x 128 coarse
 // pixels (2R fine rows x 256 fine pixels), C_mid = 4 parities x 16 channels
 static const Variant kVarDec0[] = {
     NSM_VARIANT2(1, 4, 4, 1, 16, 64, 16, TPRO_PLAIN, TEPI_HEAD_PAR),
     NSM_VARIANT2(2, 4, 4, 1, 16, 64, 16, TPRO_PLAIN, TEPI_HEAD_PAR),
-    NSM_VARIANT2(2, 8, 4, 1, 16, 64, 16, TPRO_PLAIN, TEPI_HEAD_PAR)};
+    NSM_VARIANT2(2, 8, 4, 1, 16, 64, 16, TPRO_PLAIN, TEPI_HEAD_PAR),
+    NSM_VARIANT2(2, 4, 8, 1, 16, 64, 16, TPRO_PLAIN, TEPI_HEAD_PAR),
+    NSM_VARIANT2(2, 8, 8, 1, 16, 64, 16, TPRO_PLAIN, TEPI_HEAD_PAR)};
 
 static const Variant kVarDec1Head4[] = {
     NSM_VARIANT2(2, 4, 8, 2, 32, 32, 16, TPRO_UP_SKIP, TEPI_HEAD4)};
@@ -1323,8 +1327,10 @@ int tc_stage_warps(int stage, int variant, int* producer_warps) {
 }
 
 int tc_default_variant(int stage) {
-    // the fastest plan of the 1080p autotuning runs
-    static const int def[kTcStages] = {2, 8, 6, 4, 5};
+    // the fastest plan of the 1080p autotuning runs: enc0 8 rows with 16 producer
+    // warps, enc1 / bottleneck on TMA rows, dec1 9 producer warps, dec0 8 epilogue
+    // and 8 producer warps
+    static const int def[kTcStages] = {4, 8, 6, 4, 9};
     return def[stage];
 }
 
