@@ -603,76 +603,82 @@ __global__ void pool_fwd_kernel(const float* __restrict__ x, int relu_in, int N,
 }
 
 // gx[n,y,x,c] (+)= 1/4 gy[n,y/2,x/2,c]
-__global__ void pool_adj_kernel(const float* __restrict__ gy, int N, int H, int W, int C, int accumulate,
+__global__ void pool_adj_kernel(const float* __restrict__ gy, int NH, int W, int c4s, const float* __restrict__ add,
                                 float* __restrict__ gx) {
-    const size_t total = static_cast<size_t>(N) * H * W * C;
-    for (size_t i = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; i < total;
-         i += static_cast<size_t>(gridDim.x) * blockDim.x) {
-        const int c = static_cast<int>(i % C);
-        size_t q = i / C;
-        const int x = static_cast<int>(q % W); q /= W;
-        const int y = static_cast<int>(q % H);
-        const int n = static_cast<int>(q / H);
-        const float v = 0.25f * gy[((static_cast<size_t>(n) * (H / 2) + y / 2) * (W / 2) + x / 2) * C + c];
-        gx[i] = accumulate ? gx[i] + v : v;
+    // rows of the fine grid on grid.y (fine row r = n H + y, its coarse row r / 2:
+    // H is even), four channels (one float4) per thread, C / 4 = 2^c4s
+    const int C4 = 1 << c4s, per_row = W << c4s;
+    const float4* g4 = reinterpret_cast<const float4*>(gy);
+    const float4* a4 = reinterpret_cast<const float4*>(add);
+    float4* o4 = reinterpret_cast<float4*>(gx);
+    for (int r = blockIdx.y; r < NH; r += gridDim.y) {
+        const size_t rin = static_cast<size_t>(r >> 1) * ((W >> 1) << c4s);
+        const size_t rout = static_cast<size_t>(r) * per_row;
+        for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < per_row; t += gridDim.x * blockDim.x) {
+            const int x = t >> c4s, c4 = t & (C4 - 1);
+            float4 v = __ldg(g4 + rin + ((x >> 1) << c4s) + c4);
+            v = make_float4(0.25f * v.x, 0.25f * v.y, 0.25f * v.z, 0.25f * v.w);
+            if (a4) {
+                const float4 a = __ldg(a4 + rout + t);
+                v.x += a.x; v.y += a.y; v.z += a.z; v.w += a.w;
+            }
+            o4[rout + t] = v;
+        }
     }
 }
 
 // y[n,y,x,c] = bilinear x2 of lo (H/2 x W/2) (+ skip[n,y,x,c])
-__global__ void up_fwd_kernel(const float* __restrict__ lo, const float* __restrict__ skip, int N, int H, int W, int C,
-                              float* __restrict__ y) {
-    // four channels (one float4) per thread; C % 4 == 0
-    const int Hl = H / 2, Wl = W / 2, C4 = C / 4;
-    const size_t total = static_cast<size_t>(N) * H * W * C4;
+__global__ void up_fwd_kernel(const float* __restrict__ lo, const float* __restrict__ skip, int N, int H, int W,
+                              int c4s, float* __restrict__ y) {
+    // rows of the fine grid on grid.y (r = n H + yy), four channels (one float4)
+    // per thread, C / 4 = 2^c4s
+    const int Hl = H / 2, Wl = W / 2, C4 = 1 << c4s, per_row = W << c4s;
     const float4* lo4 = reinterpret_cast<const float4*>(lo);
-    for (size_t i = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; i < total;
-         i += static_cast<size_t>(gridDim.x) * blockDim.x) {
-        const int c4 = static_cast<int>(i % C4);
-        size_t q = i / C4;
-        const int x = static_cast<int>(q % W); q /= W;
-        const int yy = static_cast<int>(q % H);
-        const int n = static_cast<int>(q / H);
-        float4 v = up_sample4(lo4, n, Hl, Wl, C4, yy, x, c4);
-        if (skip) {
-            const float4 sk = __ldg(reinterpret_cast<const float4*>(skip) + i);
-            v.x += sk.x; v.y += sk.y; v.z += sk.z; v.w += sk.w;
+    for (int r = blockIdx.y; r < N * H; r += gridDim.y) {
+        const int n = r / H, yy = r - n * H;
+        const size_t row = static_cast<size_t>(r) * per_row;
+        for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < per_row; t += gridDim.x * blockDim.x) {
+            const int x = t >> c4s, c4 = t & (C4 - 1);
+            float4 v = up_sample4(lo4, n, Hl, Wl, C4, yy, x, c4);
+            if (skip) {
+                const float4 sk = __ldg(reinterpret_cast<const float4*>(skip) + row + t);
+                v.x += sk.x; v.y += sk.y; v.z += sk.z; v.w += sk.w;
+            }
+            reinterpret_cast<float4*>(y)[row + t] = v;
         }
-        reinterpret_cast<float4*>(y)[i] = v;
     }
 }
 
 // Adjoint of the bilinear x2 upsampling in gather form: each coarse pixel
 // sums the fine-grid cotangents of the (at most 4 x 4) fine pixels whose taps
 // reach it, with those taps' weights.
-__global__ void up_adj_kernel(const float* __restrict__ g, int N, int H, int W, int C, float* __restrict__ glo) {
-    // four channels (one float4) per thread; C % 4 == 0
-    const int Hl = H / 2, Wl = W / 2, C4 = C / 4;
-    const size_t total = static_cast<size_t>(N) * Hl * Wl * C4;
+__global__ void up_adj_kernel(const float* __restrict__ g, int N, int H, int W, int c4s, float* __restrict__ glo) {
+    // coarse rows on grid.y (R = n Hl + Y), four channels (one float4) per
+    // thread, C / 4 = 2^c4s
+    const int Hl = H / 2, Wl = W / 2, C4 = 1 << c4s, per_row = Wl << c4s;
     const float4* g4 = reinterpret_cast<const float4*>(g);
-    for (size_t i = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; i < total;
-         i += static_cast<size_t>(gridDim.x) * blockDim.x) {
-        const int c4 = static_cast<int>(i % C4);
-        size_t q = i / C4;
-        const int X = static_cast<int>(q % Wl); q /= Wl;
-        const int Y = static_cast<int>(q % Hl);
-        const int n = static_cast<int>(q / Hl);
-        float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
-        for (int yy = 2 * Y - 2; yy <= 2 * Y + 3; ++yy) {
-            if (yy < 0 || yy >= H) continue;
-            const BilinTap ty = bilin_tap(yy, Hl);
-            const float wy = (ty.i0 == Y ? ty.w0 : 0.f) + (ty.i1 == Y ? ty.w1 : 0.f);
-            if (wy == 0.f) continue;
-            for (int xx = 2 * X - 2; xx <= 2 * X + 3; ++xx) {
-                if (xx < 0 || xx >= W) continue;
-                const BilinTap tx = bilin_tap(xx, Wl);
-                const float wx = (tx.i0 == X ? tx.w0 : 0.f) + (tx.i1 == X ? tx.w1 : 0.f);
-                if (wx == 0.f) continue;
-                const float wt = wy * wx;
-                const float4 v = __ldg(g4 + ((static_cast<size_t>(n) * H + yy) * W + xx) * C4 + c4);
-                s.x += wt * v.x; s.y += wt * v.y; s.z += wt * v.z; s.w += wt * v.w;
+    for (int R = blockIdx.y; R < N * Hl; R += gridDim.y) {
+        const int n = R / Hl, Y = R - n * Hl;
+        for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < per_row; t += gridDim.x * blockDim.x) {
+            const int X = t >> c4s, c4 = t & (C4 - 1);
+            float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int yy = 2 * Y - 2; yy <= 2 * Y + 3; ++yy) {
+                if (yy < 0 || yy >= H) continue;
+                const BilinTap ty = bilin_tap(yy, Hl);
+                const float wy = (ty.i0 == Y ? ty.w0 : 0.f) + (ty.i1 == Y ? ty.w1 : 0.f);
+                if (wy == 0.f) continue;
+                for (int xx = 2 * X - 2; xx <= 2 * X + 3; ++xx) {
+                    if (xx < 0 || xx >= W) continue;
+                    const BilinTap tx = bilin_tap(xx, Wl);
+                    const float wx = (tx.i0 == X ? tx.w0 : 0.f) + (tx.i1 == X ? tx.w1 : 0.f);
+                    if (wx == 0.f) continue;
+                    const float wt = wy * wx;
+                    const float4 v = __ldg(g4 + ((static_cast<size_t>(n) * H + yy) * W + xx) * C4 + c4);
+                    s.x += wt * v.x; s.y += wt * v.y; s.z += wt * v.z; s.w += wt * v.w;
+                }
             }
+            reinterpret_cast<float4*>(glo)[static_cast<size_t>(R) * per_row + t] = s;
         }
-        reinterpret_cast<float4*>(glo)[i] = s;
     }
 }
 
@@ -680,12 +686,6 @@ __global__ void relu_copy_kernel(const float* __restrict__ x, size_t n, float* _
     for (size_t i = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; i < n;
          i += static_cast<size_t>(gridDim.x) * blockDim.x)
         y[i] = fmaxf(x[i], 0.f);
-}
-
-__global__ void add_kernel(float* __restrict__ y, const float* __restrict__ x, size_t n) {
-    for (size_t i = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; i < n;
-         i += static_cast<size_t>(gridDim.x) * blockDim.x)
-        y[i] += x[i];
 }
 
 // ------------------------------------------------------------------ head, loss
@@ -715,10 +715,17 @@ __global__ void head_bwd_kernel(const float* __restrict__ a1, const float* __res
         const float v = vis[p];
         const float gl = gvis[p] * v * (1.f - v);
 #pragma unroll
-        for (int c = 0; c < 16; ++c) {
-            const float a = a1[p * 16 + c];
-            ga1[p * 16 + c] = (a > 0.f) ? __ldg(wh + c) * gl : 0.f;
-            part[c] = fmaf(gl, fmaxf(a, 0.f), part[c]);
+        for (int c4 = 0; c4 < 4; ++c4) {
+            const float4 a = __ldg(reinterpret_cast<const float4*>(a1 + p * 16) + c4);
+            const float av[4] = {a.x, a.y, a.z, a.w};
+            float gv[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int c = 4 * c4 + e;
+                gv[e] = (av[e] > 0.f) ? __ldg(wh + c) * gl : 0.f;
+                part[c] = fmaf(gl, fmaxf(av[e], 0.f), part[c]);
+            }
+            reinterpret_cast<float4*>(ga1 + p * 16)[c4] = make_float4(gv[0], gv[1], gv[2], gv[3]);
         }
         part[16] += gl;
     }
@@ -802,6 +809,21 @@ __global__ void features_batch_kernel(const GatherParams* __restrict__ gp, int N
         PixelGather o = gather_pixel(g, P, Nn);
         reinterpret_cast<float4*>(feat)[i] = make_float4(o.f[0], o.f[1], o.f[2], o.f[3]);
     }
+}
+
+// grid of the row kernels: rows on y (at most 65,535, grid-stride beyond),
+// about 8 CTAs per SM in all
+static dim3 row_grid(int rows, int per_row) {
+    const int gx = (per_row + 255) / 256;
+    const int want_y = num_sms() * 8 / (gx > 0 ? gx : 1);
+    int gy = rows < want_y ? rows : want_y;
+    gy = gy < 1 ? 1 : (gy > 65535 ? 65535 : gy);
+    return dim3(gx < 1 ? 1 : gx, gy);
+}
+static int log2_c4(int C) {  // C / 4 = 2^result (C a power of two, >= 4)
+    int s = 0;
+    while ((4 << s) < C) ++s;
+    return s;
 }
 
 static int ew_grid(size_t n) {
@@ -930,7 +952,7 @@ cudaError_t backward(const float* th, float* grad, const Buffers& b, int Nb, int
     Level L;
     // ---- level 0 decoder + head: recompute x = up(d1), a3, a1
     L = level(th, grad, DEC0_3, DEC0_1);
-    up_fwd_kernel<<<ew_grid(n * p0 * 16), 256, 0, st>>>(b.d1, nullptr, n, H, W, 16, b.xin);
+    up_fwd_kernel<<<row_grid(n * H, W * 4), 256, 0, st>>>(b.d1, nullptr, n, H, W, log2_c4(16), b.xin);
     if (img) NSM_TRY(conv3_tc(16, 16, b.xin, n, H, W, I(8), L.b3, b.a3, err, st));
     else NSM_TRY((conv_fwd<16, 16, 3>(b.xin, nullptr, 0, n, H, W, L.w3, 0, L.b3, nullptr, b.a3, st)));
     NSM_TRY((conv_fwd<16, 16, 1>(b.a3, nullptr, 1, n, H, W, L.w1, 0, L.b1, nullptr, b.a1, st)));
@@ -947,10 +969,10 @@ cudaError_t backward(const float* th, float* grad, const Buffers& b, int Nb, int
     else NSM_TRY((conv_wgrad<16, 16, 3>(b.xin, 0, b.ga3, nullptr, n, H, W, L.dw3, L.db3, st)));
     if (img) NSM_TRY(conv3_tc(16, 16, b.ga3, n, H, W, I(9), nullptr, b.gx, err, st));
     else NSM_TRY((conv_fwd<16, 16, 3>(b.ga3, nullptr, 0, n, H, W, L.w3, 1, nullptr, nullptr, b.gx, st)));
-    up_adj_kernel<<<ew_grid(n * p1 * 16), 256, 0, st>>>(b.gx, n, H, W, 16, b.glo);  // g d1 [n][H1][W1][16]
+    up_adj_kernel<<<row_grid(n * H1, W1 * 4), 256, 0, st>>>(b.gx, n, H, W, log2_c4(16), b.glo);  // g d1 [n][H1][W1][16]
     // ---- level 1 decoder: recompute x = up(bo) + s1, a3, a1
     L = level(th, grad, DEC1_3, DEC1_1);
-    up_fwd_kernel<<<ew_grid(n * p1 * 32), 256, 0, st>>>(b.bo, b.s1, n, H1, W1, 32, b.xin);
+    up_fwd_kernel<<<row_grid(n * H1, W1 * 8), 256, 0, st>>>(b.bo, b.s1, n, H1, W1, log2_c4(32), b.xin);
     if (img) NSM_TRY(conv3_tc(32, 32, b.xin, n, H1, W1, I(6), L.b3, b.a3, err, st));
     else NSM_TRY((conv_fwd<32, 32, 3, 16>(b.xin, nullptr, 0, n, H1, W1, L.w3, 0, L.b3, nullptr, b.a3, st)));
     NSM_TRY((conv_fwd<32, 16, 1>(b.a3, nullptr, 1, n, H1, W1, L.w1, 0, L.b1, nullptr, b.a1, st)));
@@ -962,7 +984,7 @@ cudaError_t backward(const float* th, float* grad, const Buffers& b, int Nb, int
     else NSM_TRY((conv_wgrad<32, 32, 3>(b.xin, 0, b.ga3, nullptr, n, H1, W1, L.dw3, L.db3, st)));
     if (img) NSM_TRY(conv3_tc(32, 32, b.ga3, n, H1, W1, I(7), nullptr, b.gskip, err, st));  // g x1
     else NSM_TRY((conv_fwd<32, 32, 3, 16>(b.ga3, nullptr, 0, n, H1, W1, L.w3, 1, nullptr, nullptr, b.gskip, st)));
-    up_adj_kernel<<<ew_grid(n * p2 * 32), 256, 0, st>>>(b.gskip, n, H1, W1, 32, b.glo);  // g bo [n][H2][W2][32]
+    up_adj_kernel<<<row_grid(n * H2, W2 * 8), 256, 0, st>>>(b.gskip, n, H1, W1, log2_c4(32), b.glo);  // g bo [n][H2][W2][32]
     // ---- bottleneck: recompute a3 = conv3(p1), a1
     L = level(th, grad, BOTT_3, BOTT_1);
     if (img) NSM_TRY(conv3_tc(32, 64, b.p1, n, H2, W2, I(4), L.b3, b.a3, err, st));
@@ -977,8 +999,7 @@ cudaError_t backward(const float* th, float* grad, const Buffers& b, int Nb, int
     else NSM_TRY((conv_fwd<64, 32, 3, 16>(b.ga3, nullptr, 0, n, H2, W2, L.w3, 1, nullptr, nullptr, b.gx, st)));
     // ---- level 1 encoder: g_h1 = pool_adj(g p1) + g s1 ; recompute a3 = conv3(e0), a1
     L = level(th, grad, ENC1_3, ENC1_1);
-    pool_adj_kernel<<<ew_grid(n * p1 * 32), 256, 0, st>>>(b.gx, n, H1, W1, 32, 0, b.glo);
-    add_kernel<<<ew_grid(n * p1 * 32), 256, 0, st>>>(b.glo, b.gskip, n * p1 * 32);
+    pool_adj_kernel<<<row_grid(n * H1, W1 * 8), 256, 0, st>>>(b.gx, n * H1, W1, log2_c4(32), b.gskip, b.glo);
     if (img) NSM_TRY(conv3_tc(16, 32, b.e0, n, H1, W1, I(2), L.b3, b.a3, err, st));
     else NSM_TRY((conv_fwd<16, 32, 3>(b.e0, nullptr, 0, n, H1, W1, L.w3, 0, L.b3, nullptr, b.a3, st)));
     NSM_TRY((conv_fwd<32, 32, 1>(b.a3, nullptr, 1, n, H1, W1, L.w1, 0, L.b1, nullptr, b.a1, st)));
@@ -991,7 +1012,7 @@ cudaError_t backward(const float* th, float* grad, const Buffers& b, int Nb, int
     else NSM_TRY((conv_fwd<32, 16, 3>(b.ga3, nullptr, 0, n, H1, W1, L.w3, 1, nullptr, nullptr, b.gx, st)));
     // ---- level 0 encoder: g_h1 = pool_adj(g e0); recompute a3 = conv3(feat), a1
     L = level(th, grad, ENC0_3, ENC0_1);
-    pool_adj_kernel<<<ew_grid(n * p0 * 16), 256, 0, st>>>(b.gx, n, H, W, 16, 0, b.gtmp);
+    pool_adj_kernel<<<row_grid(n * H, W * 4), 256, 0, st>>>(b.gx, n * H, W, log2_c4(16), nullptr, b.gtmp);
     if (img) NSM_TRY(conv3_tc(4, 16, b.feat, n, H, W, I(0), L.b3, b.a3, err, st));
     else NSM_TRY((conv_fwd<4, 16, 3>(b.feat, nullptr, 0, n, H, W, L.w3, 0, L.b3, nullptr, b.a3, st)));
     NSM_TRY((conv_fwd<16, 16, 1>(b.a3, nullptr, 1, n, H, W, L.w1, 0, L.b1, nullptr, b.a1, st)));
@@ -1094,7 +1115,8 @@ cudaError_t pool_relu(const float* x, int N, int H, int W, int C, float* y, cuda
 }
 
 cudaError_t up_add(const float* lo, const float* skip, int N, int H, int W, int C, float* y, cudaStream_t st) {
-    up_fwd_kernel<<<ew_grid(static_cast<size_t>(N) * H * W * C), 256, 0, st>>>(lo, skip, N, H, W, C, y);
+    if (C < 4 || (C & (C - 1)) != 0) return cudaErrorInvalidValue;  // a power of two
+    up_fwd_kernel<<<row_grid(N * H, W * (C / 4)), 256, 0, st>>>(lo, skip, N, H, W, log2_c4(C), y);
     return cudaGetLastError();
 }
 
