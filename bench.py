@@ -607,17 +607,24 @@ def extra_s2d(nsm, scenegen, torch, device, ctx, reps, with_error):
 
 def extra_sequence(nsm, scenegen, torch, device, theta, weights, ctx, with_error):
     """The soft temporal sequence (8 frames: the emitter orbits 2 degrees per
-    frame, 4 objects move 0.01 per frame) at 1080p, FP32, BF16 and FP8 forms:
-    per-frame time and error against the FP64 oracle on a band of rows, and the
-    temporal instability E of Eq. 3 (alpha = 3) of each form's 8 outputs."""
+    frame, 4 objects move 0.01 per frame) at 1080p, FP32, BF16, single-term
+    FP8 and three-term FP8 forms: per-frame time and error against the FP64
+    oracle's network forward on a band of rows, every form's (and the FP64
+    network's) error against 1024-sample ray-traced visibility (the FP64 C ray
+    caster) on the same band, and the temporal instability E of Eq. 3
+    (alpha = 3) of each form's 8 outputs."""
+    import dataclasses
     frames = scenegen.temporal_sequence(H, W, HS, WS, N_OBJ, SCENE_SEED + 10)
     y0, y1 = 520, 560
     out = {"workload": "8-frame soft sequence, 1920x1080, 2048^2 map; errors on rows 520-559 of every frame "
-                       "(oracle on rows 488-591: the receptive field is ~20 pixels)", "frames": []}
+                       "(oracle on rows 488-591: the receptive field is ~20 pixels); ray-traced visibility: "
+                       "32 x 32 stratified emitter samples per pixel", "frames": []}
     theta64 = theta.astype(np.float64)
-    forms = ("fp32", "bf16", "fp8")
+    th_dev = torch.from_numpy(theta.astype(np.float32)).to(device)
+    forms = ("fp32", "bf16", "fp8", "fp8_three_term")
     outs = {p: [] for p in forms}
     gbufs = []
+    ws8 = torch.empty((nsm.nsm_infer_deep_workspace_bytes(H, W, 3, nsm.NSM_FP8),), dtype=torch.uint8, device=device)
     for f in frames:
         light = nsm.LightDesc(pos=tuple(f.light_pos), radius=f.light_radius, r_hat=f.r_hat, view_proj=f.view_proj,
                               z_far=f.z_far, bias=f.bias, tan_half_fov=f.tan_half_fov)
@@ -625,24 +632,38 @@ def extra_sequence(nsm, scenegen, torch, device, theta, weights, ctx, with_error
         gbufs.append(t)
         fr = nsm.make_frame(t[0], t[1], t[2], light, f.cam_pos)
         ref = oracle_band(f, theta64, y0, y1) if with_error else None
+        rt = None
+        if with_error:  # 1024-sample ray-traced visibility of the band (FP64 C ray caster, host cores)
+            band = dataclasses.replace(f, H=y1 - y0, pos4=np.ascontiguousarray(f.pos4[y0:y1]),
+                                       nrm4=np.ascontiguousarray(f.nrm4[y0:y1]),
+                                       mask=np.ascontiguousarray(f.mask[y0:y1]))
+            rt = scenegen.soft_visibility(band, spp_side=32, seed=7).astype(np.float64)
         rec = {}
+        if ref is not None:
+            e = np.abs(ref - rt)
+            rec["fp64_network"] = {"vs_ray_traced": {"max_abs": float(e.max()), "mse": float(np.mean(e ** 2))}}
         for pname in forms:
-            prec = nsm.PRECISIONS[pname]
-            ws = torch.empty((nsm.nsm_infer_workspace_bytes(H, W, prec),), dtype=torch.uint8, device=device)
             v = torch.empty((H, W), dtype=torch.float32, device=device)
-            nsm.nsm_infer(ctx, fr, weights, prec, ws, v)
+            if pname == "fp8_three_term":
+                run = lambda: nsm.nsm_infer_deep(ctx, fr, th_dev, 3, ws8, v, precision=nsm.NSM_FP8)
+            else:
+                prec = nsm.PRECISIONS[pname]
+                ws = torch.empty((nsm.nsm_infer_workspace_bytes(H, W, prec),), dtype=torch.uint8, device=device)
+                run = lambda: nsm.nsm_infer(ctx, fr, weights, prec, ws, v)
+            run()
             ev = _events(torch, 2)
             ev[0].record()
-            nsm.nsm_infer(ctx, fr, weights, prec, ws, v)
+            run()
             ev[1].record()
             torch.cuda.synchronize()
             outs[pname].append(v)
-            if pname == "fp32":
-                continue
             r = {"ms": ev[0].elapsed_time(ev[1])}
             if ref is not None:
-                e = np.abs(v[y0:y1].cpu().numpy().astype(np.float64) - ref)
+                vb = v[y0:y1].cpu().numpy().astype(np.float64)
+                e = np.abs(vb - ref)
                 r.update({"max_abs": float(e.max()), "mse": float(np.mean(e ** 2))})
+                e = np.abs(vb - rt)
+                r["vs_ray_traced"] = {"max_abs": float(e.max()), "mse": float(np.mean(e ** 2))}
             rec[pname] = r
         out["frames"].append(rec)
     # Eq. 3 on the device (static camera: reprojection is the identity where
