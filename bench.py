@@ -465,10 +465,30 @@ def extra_fp8_three_term(nsm, torch, device, fr, theta, ctx, ref, reps):
     torch.cuda.synchronize()
     ctx.check()
     ms = sum(ev[2 * k].elapsed_time(ev[2 * k + 1]) for k in range(reps)) / reps
+    vex = v.clone()
+    # the same frame from weights packed once (nsm_infer_deep_packed), which
+    # must give the same bits
+    dw = nsm.DeepWeights(ctx, theta.astype(np.float32), 3, nsm.NSM_FP8)
+    wsp = torch.empty((nsm.nsm_infer_deep_packed_workspace_bytes(H, W, 3, nsm.NSM_FP8),), dtype=torch.uint8,
+                      device=device)
+    for _ in range(3):
+        nsm.nsm_infer_deep_packed(ctx, fr, dw, wsp, v)
+    ev = _events(torch, 2 * reps)
+    for k in range(reps):
+        flush.zero_()
+        ev[2 * k].record()
+        nsm.nsm_infer_deep_packed(ctx, fr, dw, wsp, v)
+        ev[2 * k + 1].record()
+    torch.cuda.synchronize()
+    ctx.check()
+    msp = sum(ev[2 * k].elapsed_time(ev[2 * k + 1]) for k in range(reps)) / reps
+    dw.close()
     out = {"ms_per_frame": ms, "mpix_s": H * W / (ms * 1e-3) / 1e6,
+           "packed_weights": {"ms_per_frame": msp, "mpix_s": H * W / (msp * 1e-3) / 1e6,
+                              "same_bits_as_per_call": bool(torch.equal(v, vex))},
            "form": "three E4M3 terms (scales 1, 2^-4, 2^-8) per activation and per weight (times a per-output-"
                    "channel scale), tcgen05 kind::f8f6f4 with FP32 accumulation, one layer per kernel on FP32 NHWC "
-                   "tensors (weight images packed per call)",
+                   "tensors (weight images packed per call; packed_weights: packed once)",
            "workload": WORKLOAD}
     if ref is not None:
         e = np.abs(v.cpu().numpy().astype(np.float64) - ref)
@@ -734,7 +754,8 @@ def extra_deep(nsm, scenegen, torch, device, reps):
     """Sec. 3.6's deeper networks (3, 5, 7 levels; receptive fields 24, 96,
     384 px) on a 1088x1920 soft frame (both sides multiples of 2^6),
     He-initialised weights: the FP32 form (CUDA cores) and the tensor-core
-    form (BF16), whose visibility is compared with the FP32 form's."""
+    form (BF16), whose visibility is compared with the FP32 form's, each
+    with its weights packed per call and packed once."""
     Hd = 1088
     f = scenegen.soft_frame(Hd, W, HS, WS, N_OBJ, SCENE_SEED + 10)
     light = nsm.LightDesc(pos=tuple(f.light_pos), radius=f.light_radius, r_hat=f.r_hat, view_proj=f.view_proj,
@@ -789,6 +810,27 @@ def extra_deep(nsm, scenegen, torch, device, reps):
             "form": "levels 0, 1 on the compensated-BF16 stage kernels; every 3x3 / 1x1 of levels 2 .. L-1 "
                     "as a tcgen05 implicit GEMM (compensated BF16 operands, FP32 accumulation)"}
         del wsb
+        # the same forms from weights packed once (nsm_infer_deep_packed): the
+        # per-call packing kernels left out of the frame
+        host_theta = theta.cpu().numpy()
+        for prec, key in ((nsm.NSM_FP32, None), (nsm.NSM_BF16, "bf16")):
+            dw = nsm.DeepWeights(ctx, host_theta, L, prec)
+            wsp = torch.empty((nsm.nsm_infer_deep_packed_workspace_bytes(Hd, W, L, prec),), dtype=torch.uint8,
+                              device=device)
+            for _ in range(3):
+                nsm.nsm_infer_deep_packed(ctx, fr, dw, wsp, vis)
+            ev = _events(torch, 2 * reps)
+            for k in range(reps):
+                ev[2 * k].record()
+                nsm.nsm_infer_deep_packed(ctx, fr, dw, wsp, vis)
+                ev[2 * k + 1].record()
+            torch.cuda.synchronize()
+            ctx.check()
+            msp = sum(ev[2 * k].elapsed_time(ev[2 * k + 1]) for k in range(reps)) / reps
+            entry = out[f"levels_{L}"] if key is None else out[f"levels_{L}"][key]
+            entry["packed_weights_ms"] = msp
+            dw.close()
+            del wsp
     ctx.close()
     return out
 

@@ -505,9 +505,10 @@ nsm_status nsm_infer_deep(nsm_ctx* ctx, const nsm_frame* frame, const float* dev
  * NSM_BF16 (levels >= 3; NSM_ERR_UNSUPPORTED for 2): levels 0 and 1, whose
  * shapes are the 3-level network's, on its compensated-BF16 tensor-core stage
  * kernels (gather fused into the level-0 encoder, the level-0 decoder on the
- * coarse grid with the head), their weight images packed per call from this
- * network's vector; every 3x3 and 1x1 layer of levels 2 .. L-1 on a tcgen05
- * implicit GEMM over FP32 NHWC tensors with compensated BF16 operands (hi + lo
+ * coarse grid with the head), their weight images packed from this
+ * network's vector (per call here; once with nsm_deep_weights below); every
+ * 3x3 and 1x1 layer of levels 2 .. L-1 on a tcgen05 implicit GEMM over FP32
+ * NHWC tensors with compensated BF16 operands (hi + lo
  * pairs, FP32 accumulation).  Workspace (device, 256-byte aligned) of
  * nsm_infer_deep_ex_workspace_bytes (0 for an unsupported combination).  A
  * bounded device wait that gives up sets the context's error word
@@ -516,6 +517,38 @@ size_t nsm_infer_deep_ex_workspace_bytes(int H, int W, int levels, nsm_precision
 nsm_status nsm_infer_deep_ex(nsm_ctx* ctx, const nsm_frame* frame, const float* dev_params, int levels,
                              nsm_precision precision, void* workspace, size_t workspace_bytes, float* vis_out,
                              void* stream);
+
+/* Packed weights of an L-level network in one form, made once instead of per
+ * call.  nsm_infer_deep_ex re-lays the weights out in its workspace on every
+ * call (FP32: tap-major transposition; BF16: the stage kernels' images and
+ * the inner levels' tcgen05 images; FP8: the three-term E4M3 images and
+ * per-channel scales); nsm_deep_weights holds a device copy of the canonical
+ * vector and those images, so a serving loop pays neither the packing
+ * kernels nor the images' workspace.
+ *
+ * nsm_deep_weights_create: host_params (host, n floats, n =
+ * nsm_param_count_levels(levels), finite; read before return) copied to the
+ * current device and packed for `precision` (FP32, BF16 with levels >= 3, or
+ * FP8); synchronous; NSM_ERR_SHAPE for a wrong n, NSM_ERR_UNSUPPORTED for a
+ * form the depth lacks, NSM_ERR_CUDA if an allocation fails (nothing is kept).
+ * *out is owned by the caller until nsm_deep_weights_destroy (NULL is a no-op;
+ * frees device memory: no call may be in flight with the weights).
+ * nsm_deep_weights_load_device: replace the weights with dev_params (device,
+ * same n) and re-pack, asynchronous on `stream`; the caller orders it after
+ * calls that still read the old weights.
+ * nsm_infer_deep_packed: nsm_infer_deep_ex from packed weights, bit-identical
+ * to it for the same vector and form; workspace (device, 256-byte aligned) of
+ * nsm_infer_deep_packed_workspace_bytes (0 for an unsupported combination;
+ * the ex workspace less the images), on the device the weights were made on.
+ * Asynchronous; the same error word as nsm_infer_deep_ex. */
+typedef struct nsm_deep_weights nsm_deep_weights;
+nsm_status nsm_deep_weights_create(nsm_ctx* ctx, const float* host_params, size_t n, int levels,
+                                   nsm_precision precision, nsm_deep_weights** out);
+nsm_status nsm_deep_weights_load_device(nsm_deep_weights* w, const float* dev_params, size_t n, void* stream);
+void nsm_deep_weights_destroy(nsm_deep_weights* w);
+size_t nsm_infer_deep_packed_workspace_bytes(int H, int W, int levels, nsm_precision precision);
+nsm_status nsm_infer_deep_packed(nsm_ctx* ctx, const nsm_frame* frame, const nsm_deep_weights* w, void* workspace,
+                                 size_t workspace_bytes, float* vis_out, void* stream);
 
 /* ---------------------------------------------------------------- frame analysis */
 

@@ -617,12 +617,19 @@ def _gen_sigs():
             "nsm_temporal_instability": [I, I, P, P, P, P, P, P, P, F, P, P, P],
             "nsm_infer_deep": [P, ctypes.POINTER(nsm_frame), P, I, P, ctypes.c_size_t, P, P],
             "nsm_infer_deep_ex": [P, ctypes.POINTER(nsm_frame), P, I, I, P, ctypes.c_size_t, P, P],
+            "nsm_deep_weights_create": [P, P, ctypes.c_size_t, I, I, ctypes.POINTER(P)],
+            "nsm_deep_weights_load_device": [P, P, ctypes.c_size_t, P],
+            "nsm_infer_deep_packed": [P, ctypes.POINTER(nsm_frame), P, P, ctypes.c_size_t, P, P],
             "nsm_penumbra_histogram": [I, I, P, P, F, F, I, P, P],
             "nsm_depth_for_penumbra": [P, I, F, P, P],
         }.items():
             fn = getattr(L, name)
             fn.argtypes = args
             fn.restype = I
+        L.nsm_deep_weights_destroy.argtypes = [P]
+        L.nsm_deep_weights_destroy.restype = None
+        L.nsm_infer_deep_packed_workspace_bytes.argtypes = [I, I, I, I]
+        L.nsm_infer_deep_packed_workspace_bytes.restype = ctypes.c_size_t
         _GEN = L
     return _GEN
 
@@ -704,6 +711,47 @@ def nsm_infer_deep(ctx: Context, frame: nsm_frame, dev_params, levels: int, work
         _check(_gen_sigs().nsm_infer_deep_ex(ctx.h, ctypes.byref(frame), _ptr(dev_params), int(levels),
                                              int(precision), _ptr(workspace), nbytes, _ptr(vis_out),
                                              _stream(stream)), "nsm_infer_deep_ex")
+
+
+class DeepWeights:
+    """Packed weights of the L-level network in one form (FP32, BF16 or FP8),
+    made once from a host vector of nsm_param_count_levels(levels) floats."""
+
+    def __init__(self, ctx: Context, params: np.ndarray, levels: int, precision: int = 0):
+        p = np.ascontiguousarray(params, np.float32).reshape(-1)
+        h = ctypes.c_void_p()
+        _check(_gen_sigs().nsm_deep_weights_create(ctx.h, _ptr(p), p.size, int(levels), int(precision),
+                                                   ctypes.byref(h)), "nsm_deep_weights_create")
+        self.h = h
+        self.levels = int(levels)
+        self.precision = int(precision)
+
+    def load_device(self, dev_params, stream=None):
+        _check(_gen_sigs().nsm_deep_weights_load_device(self.h, _ptr(dev_params), int(dev_params.numel()),
+                                                        _stream(stream)), "nsm_deep_weights_load_device")
+
+    def close(self):
+        if self.h:
+            _gen_sigs().nsm_deep_weights_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def nsm_infer_deep_packed_workspace_bytes(H: int, W: int, levels: int, precision: int) -> int:
+    return int(_gen_sigs().nsm_infer_deep_packed_workspace_bytes(H, W, levels, int(precision)))
+
+
+def nsm_infer_deep_packed(ctx: Context, frame: nsm_frame, weights: DeepWeights, workspace, vis_out, stream=None):
+    """Forward of the L-level network from packed weights (nsm_infer_deep_ex's
+    result, without the per-call packing)."""
+    nbytes = int(workspace.numel() * workspace.element_size())
+    _check(_gen_sigs().nsm_infer_deep_packed(ctx.h, ctypes.byref(frame), weights.h, _ptr(workspace), nbytes,
+                                             _ptr(vis_out), _stream(stream)), "nsm_infer_deep_packed")
 
 
 def depth_for_penumbra(hist, bin_px):

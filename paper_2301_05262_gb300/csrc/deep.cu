@@ -64,13 +64,6 @@ static size_t deep_param_count(int L) {
     return t.back().b + 1;
 }
 
-// workspace: gather parameters, features (4), five full-resolution 16-channel
-// FP32 tensors (every level's tensors fit: w_l (H W / 4^l) <= 16 H W), and the
-// weights transposed to [tap][C_in][C_out] at their offsets in the vector
-static size_t deep_ws_floats(int H, int W, int L) {
-    return 64 + static_cast<size_t>(H) * W * (4 + 5 * 16) + deep_param_count(L);
-}
-
 // Layers of the inner levels (2 .. L-1): indices [4, 4L - 6) of deep_layers;
 // the 3-level network's layers map to 0 .. 3 (encoders), 4L - 6 .. 4L - 3
 // (decoders) and 4L - 2 (head).
@@ -84,15 +77,29 @@ static int deep_index_of(Layer l, int L) {
     }
 }
 
-// Bytes the tensor-core form adds after the FP32 form's workspace: the stage
-// kernels' activations, their BF16 weight images and packing table, and the
-// inner levels' weight images.
-static size_t deep_bf16_extra_bytes(int H, int W, int L) {
-    size_t b = activations_bytes(H, W, 4, nullptr, nullptr);
-    b += align_up(bf16_images().total * sizeof(uint16_t), 256);
-    b += align_up(pack_desc_bytes() * NUM_LAYERS, 256);
+// Packed weights of one form, laid out from one 256-byte-aligned base (a
+// workspace region or a nsm_deep_weights allocation): FP32, every layer's
+// weights as [tap][C_in][C_out] at its canonical offset; BF16, the stage
+// kernels' images of levels 0 and 1 (the 3-level packing table with this
+// network's offsets), the table, then the inner levels' tcgen05 images;
+// FP8, every layer's three-term E4M3 image.  The head stays in the FP32
+// vector.
+struct DeepImgs {
+    const float* wt = nullptr;
+    const uint16_t* img16 = nullptr;
+    std::vector<const void*> layer;
+};
+
+static size_t deep_images_bytes(int L, nsm_precision p) {
     const std::vector<DeepLayer> t = deep_layers(L);
-    for (int i = 4; i < 4 * L - 6; ++i) b += align_up(tr::deep_tc_image_bytes(t[i].cin, t[i].cout, t[i].k), 256);
+    if (p == NSM_FP32) return align_up(deep_param_count(L) * sizeof(float), 256);
+    size_t b = 0;
+    if (p == NSM_BF16) {
+        b += align_up(bf16_images().total * sizeof(uint16_t), 256) + align_up(pack_desc_bytes() * NUM_LAYERS, 256);
+        for (int i = 4; i < 4 * L - 6; ++i) b += align_up(tr::deep_tc_image_bytes(t[i].cin, t[i].cout, t[i].k), 256);
+    } else {
+        for (size_t i = 0; i + 1 < t.size(); ++i) b += align_up(tr::f8x3_image_bytes(t[i].cin, t[i].cout, t[i].k), 256);
+    }
     return b;
 }
 
@@ -107,31 +114,17 @@ __global__ void deep_pairs_to_f32_kernel(const uint16_t* __restrict__ in, size_t
     }
 }
 
-// Bytes the three-term FP8 form adds after the FP32 form's workspace: every
-// layer's E4M3 image (the head stays FP32).
-static size_t deep_f8x3_extra_bytes(int L) {
-    const std::vector<DeepLayer> t = deep_layers(L);
-    size_t b = 0;
-    for (size_t i = 0; i + 1 < t.size(); ++i) b += align_up(tr::f8x3_image_bytes(t[i].cin, t[i].cout, t[i].k), 256);
-    return b;
-}
-
-// The L-level network with every convolution in the three-term FP8 form, one
-// layer per kernel on FP32 NHWC tensors (features, a3, a1, h, xin, skip: the
-// FP32 form's workspace regions), as the FP32 form's unfused levels run.
+// The L-level network with every convolution in the three-term FP8 form (packed
+// weights P), one layer per kernel on FP32 NHWC tensors (features, a3, a1, h,
+// xin, skip: the FP32 form's workspace regions), as the FP32 form's unfused
+// levels run.
 static cudaError_t deep_forward_f8x3(nsm_ctx* ctx, const nsm_frame* frame, const float* params, int L,
-                                     GatherParams* dgp, float* feat, float* a3, float* a1, float* h, float* xin,
-                                     float* skip, char* extra, float* vis, cudaStream_t st) {
+                                     const DeepImgs& P, GatherParams* dgp, float* feat, float* a3, float* a1, float* h,
+                                     float* xin, float* skip, float* vis, cudaStream_t st) {
     const int H = frame->H, W = frame->W;
     const std::vector<DeepLayer> Ls = deep_layers(L);
-    std::vector<const void*> img(Ls.size(), nullptr);
+    const std::vector<const void*>& img = P.layer;
     cudaError_t e = cudaSuccess;
-    char* q = extra;
-    for (size_t i = 0; i + 1 < Ls.size() && e == cudaSuccess; ++i) {
-        img[i] = q;
-        e = tr::f8x3_pack(params + Ls[i].w, Ls[i].cin, Ls[i].cout, Ls[i].k, q, st);
-        q += align_up(tr::f8x3_image_bytes(Ls[i].cin, Ls[i].cout, Ls[i].k), 256);
-    }
     const GatherParams g = make_gather(frame);
     if (e == cudaSuccess) e = cudaMemcpyAsync(dgp, &g, sizeof(g), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = tr::features_batch(dgp, 1, H, W, feat, st);
@@ -176,19 +169,31 @@ static cudaError_t deep_forward_f8x3(nsm_ctx* ctx, const nsm_frame* frame, const
     return e;
 }
 
-// The L-level network with levels 0, 1 on the BF16 stage kernels and the inner
-// levels on the tcgen05 layers; fp32 = the FP32 form's workspace regions
-// (a3, a1, h, xin, skip: 16 H W floats each), extra = deep_bf16_extra_bytes.
-static cudaError_t deep_forward_bf16(nsm_ctx* ctx, const nsm_frame* frame, const float* params, int L, float* a3,
-                                     float* a1, float* h, float* xin, float* skip, char* extra, float* vis,
-                                     cudaStream_t st) {
-    const int H = frame->H, W = frame->W;
+// Pack the form's weights from the device vector into base (deep_images_bytes).
+static cudaError_t deep_pack(const float* params, int L, nsm_precision p, char* base, DeepImgs* out, cudaStream_t st) {
     const std::vector<DeepLayer> Ls = deep_layers(L);
-    Activations act{};
-    char* q = extra;
-    q += activations_bytes(H, W, 4, &act, q);
-    BF16Images im = bf16_images();
+    *out = DeepImgs{};
+    out->layer.assign(Ls.size(), nullptr);
+    cudaError_t e = cudaSuccess;
+    if (p == NSM_FP32) {
+        float* wt = reinterpret_cast<float*>(base);
+        out->wt = wt;
+        for (size_t i = 0; i + 1 < Ls.size() && e == cudaSuccess; ++i)  // every layer but the head
+            e = tr::transpose_to_tap_major(params + Ls[i].w, Ls[i].cin, Ls[i].cout, Ls[i].k, wt + Ls[i].w, st);
+        return e;
+    }
+    char* q = base;
+    if (p == NSM_FP8) {
+        for (size_t i = 0; i + 1 < Ls.size() && e == cudaSuccess; ++i) {
+            out->layer[i] = q;
+            e = tr::f8x3_pack(params + Ls[i].w, Ls[i].cin, Ls[i].cout, Ls[i].k, q, st);
+            q += align_up(tr::f8x3_image_bytes(Ls[i].cin, Ls[i].cout, Ls[i].k), 256);
+        }
+        return e;
+    }
+    const BF16Images im = bf16_images();
     uint16_t* img16 = reinterpret_cast<uint16_t*>(q);
+    out->img16 = img16;
     q += align_up(im.total * sizeof(uint16_t), 256);
     void* ddesc = q;
     q += align_up(pack_desc_bytes() * NUM_LAYERS, 256);
@@ -205,15 +210,31 @@ static cudaError_t deep_forward_bf16(nsm_ctx* ctx, const nsm_frame* frame, const
         desc[nd].w_off = Ls[di].w;
         ++nd;
     }
-    cudaError_t e = cudaMemcpyAsync(ddesc, desc, pack_desc_bytes() * nd, cudaMemcpyHostToDevice, st);
+    e = cudaMemcpyAsync(ddesc, desc, pack_desc_bytes() * nd, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = launch_pack_bf16(params, img16, ddesc, nd, st);
-    std::vector<const uint4*> mid(Ls.size(), nullptr);
     for (int i = 4; i < 4 * L - 6 && e == cudaSuccess; ++i) {
-        mid[i] = reinterpret_cast<const uint4*>(q);
+        out->layer[i] = q;
         e = tr::deep_tc_pack(params + Ls[i].w, Ls[i].cin, Ls[i].cout, Ls[i].k, reinterpret_cast<uint4*>(q), st);
         q += align_up(tr::deep_tc_image_bytes(Ls[i].cin, Ls[i].cout, Ls[i].k), 256);
     }
-    if (e != cudaSuccess) return e;
+    return e;
+}
+
+// The L-level network with levels 0, 1 on the BF16 stage kernels and the inner
+// levels on the tcgen05 layers, from packed weights P; a3, a1, h, xin, skip:
+// the FP32 form's workspace regions (16 H W floats each), actb: the stage
+// kernels' activations (activations_bytes).
+static cudaError_t deep_forward_bf16(nsm_ctx* ctx, const nsm_frame* frame, const float* params, int L,
+                                     const DeepImgs& P, float* a3, float* a1, float* h, float* xin, float* skip,
+                                     char* actb, float* vis, cudaStream_t st) {
+    const int H = frame->H, W = frame->W;
+    const std::vector<DeepLayer> Ls = deep_layers(L);
+    Activations act{};
+    activations_bytes(H, W, 4, &act, actb);
+    const BF16Images im = bf16_images();
+    const uint16_t* img16 = P.img16;
+    const std::vector<const void*>& mid = P.layer;
+    cudaError_t e = cudaSuccess;
     auto I = [&](Layer l) { return reinterpret_cast<const uint4*>(img16 + im.img_off[l]); };
     const GatherParams g = make_gather(frame);
     const int head = deep_index_of(HEAD, L);
@@ -246,8 +267,8 @@ static cudaError_t deep_forward_bf16(nsm_ctx* ctx, const nsm_frame* frame, const
     auto wd = [](int l) { return 16 << l; };
     auto conv = [&](int li, const float* x, int relu_in, int Hl, int Wl, float* y, int relu_out = 0) {
         const DeepLayer& d = Ls[li];
-        return tr::deep_tc_conv(d.cin, d.cout, d.k, x, relu_in, Hl, Wl, mid[li], params + d.b, y, relu_out,
-                                ctx->d_err, st);
+        return tr::deep_tc_conv(d.cin, d.cout, d.k, x, relu_in, Hl, Wl, static_cast<const uint4*>(mid[li]),
+                                params + d.b, y, relu_out, ctx->d_err, st);
     };
     const size_t n2 = static_cast<size_t>(H / 4) * (W / 4);
     deep_pairs_to_f32_kernel<32><<<static_cast<int>(std::min<size_t>((n2 * 32 + 255) / 256, 4096)), 256, 0, st>>>(
@@ -284,90 +305,22 @@ static cudaError_t deep_forward_bf16(nsm_ctx* ctx, const nsm_frame* frame, const
     return stage(4, DEC0_3, DEC0_1);
 }
 
-}  // namespace nsm
-
-using namespace nsm;
-
-extern "C" {
-
-size_t nsm_param_count_levels(int levels) {
-    if (levels < 2 || levels > 7) return 0;
-    return deep_param_count(levels);
-}
-
-size_t nsm_infer_deep_workspace_bytes(int H, int W, int levels) {
-    if (H <= 0 || W <= 0 || levels < 2 || levels > 7) return 0;
-    return deep_ws_floats(H, W, levels) * sizeof(float);
-}
-
-size_t nsm_infer_deep_ex_workspace_bytes(int H, int W, int levels, nsm_precision precision) {
-    if (H <= 0 || W <= 0 || levels < 2 || levels > 7) return 0;
-    if (precision == NSM_FP32) return nsm_infer_deep_workspace_bytes(H, W, levels);
-    if (precision == NSM_FP8)
-        return align_up(deep_ws_floats(H, W, levels) * sizeof(float), 256) + deep_f8x3_extra_bytes(levels);
-    if (precision != NSM_BF16 || levels < 3) return 0;
-    return align_up(deep_ws_floats(H, W, levels) * sizeof(float), 256) + deep_bf16_extra_bytes(H, W, levels);
-}
-
-nsm_status nsm_infer_deep(nsm_ctx* ctx, const nsm_frame* frame, const float* dev_params, int levels, void* workspace,
-                          size_t workspace_bytes, float* vis_out, void* stream) {
-    return nsm_infer_deep_ex(ctx, frame, dev_params, levels, NSM_FP32, workspace, workspace_bytes, vis_out, stream);
-}
-
-nsm_status nsm_infer_deep_ex(nsm_ctx* ctx, const nsm_frame* frame, const float* dev_params, int levels,
-                             nsm_precision precision, void* workspace, size_t workspace_bytes, float* vis_out,
-                             void* stream) {
-    if (!ctx) return fail(NSM_ERR_INVALID_ARG, "ctx is NULL");
-    if (levels < 2 || levels > 7) return fail(NSM_ERR_INVALID_ARG, "levels must be 2 .. 7, got %d", levels);
-    if (precision != NSM_FP32 && precision != NSM_BF16 && precision != NSM_FP8)
-        return fail(NSM_ERR_UNSUPPORTED, "the deeper networks run in the FP32, BF16 or three-term FP8 form");
-    if (precision == NSM_BF16 && levels < 3)
-        return fail(NSM_ERR_UNSUPPORTED, "the BF16 form needs 3 or more levels, got %d", levels);
-    nsm_status s = check_frame(frame, false);
-    if (s != NSM_OK) return s;
+// The FP32 form from packed weights P (P.wt): levels 0 and 1 as the training
+// forward's fused kernels, the coarser levels one kernel per layer.
+static cudaError_t deep_forward_fp32(const nsm_frame* frame, const float* params, int levels, const DeepImgs& P,
+                                     GatherParams* dgp, float* feat, float* a3, float* a1, float* h, float* xin,
+                                     float* skip, float* vis_out, cudaStream_t st) {
     const int H = frame->H, W = frame->W;
-    if (static_cast<size_t>(H) * W == 0) return NSM_OK;
-    const int m = 1 << (levels - 1);
-    if (H % m || W % m) return fail(NSM_ERR_SHAPE, "H, W must be multiples of 2^(levels - 1) = %d", m);
-    if ((s = check_dev_ptr(dev_params, "dev_params", 4)) != NSM_OK || (s = check_dev_ptr(vis_out, "vis_out", 4)) != NSM_OK)
-        return s;
-    const size_t need = nsm_infer_deep_ex_workspace_bytes(H, W, levels, precision);
-    if (!workspace || workspace_bytes < need)
-        return fail(NSM_ERR_WORKSPACE, "workspace of %zu bytes given, %zu needed", workspace_bytes, need);
-    if ((s = check_dev_ptr(workspace, "workspace", 256)) != NSM_OK) return s;
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
     const size_t hw = static_cast<size_t>(H) * W;
-    float* base = static_cast<float*>(workspace);
-    GatherParams* dgp = reinterpret_cast<GatherParams*>(base);
-    static_assert(sizeof(GatherParams) <= 64 * sizeof(float), "gather parameters fit the workspace head");
-    float* feat = base + 64;
-    float* a3 = feat + 4 * hw;
-    float* a1 = a3 + 16 * hw;
-    float* h = a1 + 16 * hw;     // a level's input (pooled / bottleneck / decoder output)
-    float* xin = h + 16 * hw;    // decoder input (up-sampled + skip)
-    float* skip = xin + 16 * hw; // encoder outputs of levels 1 .. L-2, one after the other
-    float* wt = base + 64 + hw * (4 + 5 * 16);  // transposed weights
-    if (precision == NSM_FP8) {
-        char* extra = static_cast<char*>(workspace) + align_up(deep_ws_floats(H, W, levels) * sizeof(float), 256);
-        const cudaError_t e =
-            deep_forward_f8x3(ctx, frame, dev_params, levels, dgp, feat, a3, a1, h, xin, skip, extra, vis_out, st);
-        return e == cudaSuccess ? NSM_OK : cuda_fail(e, "deep forward (three-term FP8)");
-    }
-    if (precision == NSM_BF16) {
-        char* extra = static_cast<char*>(workspace) + align_up(deep_ws_floats(H, W, levels) * sizeof(float), 256);
-        const cudaError_t e = deep_forward_bf16(ctx, frame, dev_params, levels, a3, a1, h, xin, skip, extra, vis_out, st);
-        return e == cudaSuccess ? NSM_OK : cuda_fail(e, "deep forward (tensor cores)");
-    }
+    const float* wt = P.wt;
     const GatherParams g = make_gather(frame);
     cudaError_t e = cudaMemcpyAsync(dgp, &g, sizeof(g), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = tr::features_batch(dgp, 1, H, W, feat, st);
     const std::vector<DeepLayer> Ls = deep_layers(levels);
-    for (size_t i = 0; i + 1 < Ls.size() && e == cudaSuccess; ++i)  // every layer but the head
-        e = tr::transpose_to_tap_major(dev_params + Ls[i].w, Ls[i].cin, Ls[i].cout, Ls[i].k, wt + Ls[i].w, st);
     auto wd = [](int l) { return 16 << l; };
     auto conv = [&](int li, const float* x, int relu_in, int Hl, int Wl, float* y) {
         const DeepLayer& d = Ls[li];
-        return tr::conv_layer(d.cin, d.cout, d.k, x, relu_in, 1, Hl, Wl, wt + d.w, dev_params + d.b, y, st);
+        return tr::conv_layer(d.cin, d.cout, d.k, x, relu_in, 1, Hl, Wl, wt + d.w, params + d.b, y, st);
     };
     std::vector<float*> skips(levels, nullptr);
     const float* cur = feat;
@@ -385,8 +338,8 @@ nsm_status nsm_infer_deep_ex(nsm_ctx* ctx, const nsm_frame* frame, const float* 
             skip_off += static_cast<size_t>(Hl) * Wl * wd(l);
         }
         if (tr::enc_level_fusable(d3.cin, d3.cout)) {
-            e = tr::enc_level_fused(d3.cin, d3.cout, cur, 1, Hl, Wl, wt + d3.w, dev_params + d3.b, dev_params + d1.w,
-                                    dev_params + d1.b, skips[l], pooled, st);
+            e = tr::enc_level_fused(d3.cin, d3.cout, cur, 1, Hl, Wl, wt + d3.w, params + d3.b, params + d1.w,
+                                    params + d1.b, skips[l], pooled, st);
         } else {
             e = conv(li, cur, 0, Hl, Wl, a3);
             if (e == cudaSuccess) e = conv(li + 1, a3, 1, Hl, Wl, a1);
@@ -409,8 +362,8 @@ nsm_status nsm_infer_deep_ex(nsm_ctx* ctx, const nsm_frame* frame, const float* 
             // level 0 also applies the head (the layer after its 1x1) and writes only the visibility
             float* out = l >= 1 ? (lo == h ? a1 : h) : nullptr;
             e = tr::dec_level_fused(d3.cin, d1.cout, lo, l >= 1 ? skips[l] : nullptr, 1, Hl, Wl, wt + d3.w,
-                                    dev_params + d3.b, dev_params + d1.w, dev_params + d1.b, l >= 1, out,
-                                    l == 0 ? dev_params + Ls[li + 2].w : nullptr, l == 0 ? vis_out : nullptr, st);
+                                    params + d3.b, params + d1.w, params + d1.b, l >= 1, out,
+                                    l == 0 ? params + Ls[li + 2].w : nullptr, l == 0 ? vis_out : nullptr, st);
             lo = out;
         } else {
             e = tr::up_add(lo, l >= 1 ? skips[l] : nullptr, 1, Hl, Wl, wd(l), xin, st);
@@ -420,8 +373,187 @@ nsm_status nsm_infer_deep_ex(nsm_ctx* ctx, const nsm_frame* frame, const float* 
             lo = l >= 1 ? h : a1;
         }
     }
-    if (e == cudaSuccess && lo) e = tr::head(lo, dev_params + Ls[li].w, hw, vis_out, st);
+    if (e == cudaSuccess && lo) e = tr::head(lo, params + Ls[li].w, hw, vis_out, st);
+    return e;
+}
+
+// Workspace of one call: the gather parameters, the features and five
+// 16 H W-float scratch tensors (every level's tensors fit: w_l (H W / 4^l) <= 16
+// H W), then for the BF16 form the stage kernels' activations.
+static size_t deep_region_bytes(int H, int W) {
+    return align_up((64 + static_cast<size_t>(H) * W * (4 + 5 * 16)) * sizeof(float), 256);
+}
+static size_t deep_act_bytes(int H, int W, nsm_precision p) {
+    return p == NSM_BF16 ? activations_bytes(H, W, 4, nullptr, nullptr) : 0;
+}
+
+// One forward from packed weights P, the workspace laid out as above.
+static cudaError_t deep_run(nsm_ctx* ctx, const nsm_frame* frame, const float* params, int levels, nsm_precision p,
+                            const DeepImgs& P, void* workspace, float* vis_out, cudaStream_t st) {
+    const size_t hw = static_cast<size_t>(frame->H) * frame->W;
+    float* base = static_cast<float*>(workspace);
+    GatherParams* dgp = reinterpret_cast<GatherParams*>(base);
+    static_assert(sizeof(GatherParams) <= 64 * sizeof(float), "gather parameters fit the workspace head");
+    float* feat = base + 64;
+    float* a3 = feat + 4 * hw;
+    float* a1 = a3 + 16 * hw;
+    float* h = a1 + 16 * hw;     // a level's input (pooled / bottleneck / decoder output)
+    float* xin = h + 16 * hw;    // decoder input (up-sampled + skip)
+    float* skip = xin + 16 * hw; // encoder outputs of levels 1 .. L-2, one after the other
+    char* actb = static_cast<char*>(workspace) + deep_region_bytes(frame->H, frame->W);
+    if (p == NSM_FP8)
+        return deep_forward_f8x3(ctx, frame, params, levels, P, dgp, feat, a3, a1, h, xin, skip, vis_out, st);
+    if (p == NSM_BF16) return deep_forward_bf16(ctx, frame, params, levels, P, a3, a1, h, xin, skip, actb, vis_out, st);
+    return deep_forward_fp32(frame, params, levels, P, dgp, feat, a3, a1, h, xin, skip, vis_out, st);
+}
+
+// Shared checks of the deep entry points (frame, levels, form).
+static nsm_status deep_check(nsm_ctx* ctx, const nsm_frame* frame, int levels, nsm_precision precision) {
+    if (!ctx) return fail(NSM_ERR_INVALID_ARG, "ctx is NULL");
+    if (levels < 2 || levels > 7) return fail(NSM_ERR_INVALID_ARG, "levels must be 2 .. 7, got %d", levels);
+    if (precision != NSM_FP32 && precision != NSM_BF16 && precision != NSM_FP8)
+        return fail(NSM_ERR_UNSUPPORTED, "the deeper networks run in the FP32, BF16 or three-term FP8 form");
+    if (precision == NSM_BF16 && levels < 3)
+        return fail(NSM_ERR_UNSUPPORTED, "the BF16 form needs 3 or more levels, got %d", levels);
+    nsm_status s = check_frame(frame, false);
+    if (s != NSM_OK) return s;
+    const int m = 1 << (levels - 1);
+    if (frame->H % m || frame->W % m) return fail(NSM_ERR_SHAPE, "H, W must be multiples of 2^(levels - 1) = %d", m);
+    return NSM_OK;
+}
+
+}  // namespace nsm
+
+// Packed weights of an L-level network in one form (nsm_deep_weights_create).
+struct nsm_deep_weights {
+    int device;
+    int levels;
+    nsm_precision precision;
+    size_t n;
+    float* d_params;   // canonical FP32 vector (biases and the head are read from it)
+    char* d_images;    // deep_images_bytes of the form
+    nsm::DeepImgs imgs;
+};
+
+using namespace nsm;
+
+extern "C" {
+
+size_t nsm_param_count_levels(int levels) {
+    if (levels < 2 || levels > 7) return 0;
+    return deep_param_count(levels);
+}
+
+size_t nsm_infer_deep_workspace_bytes(int H, int W, int levels) {
+    return nsm_infer_deep_ex_workspace_bytes(H, W, levels, NSM_FP32);
+}
+
+size_t nsm_infer_deep_ex_workspace_bytes(int H, int W, int levels, nsm_precision precision) {
+    if (H <= 0 || W <= 0 || levels < 2 || levels > 7) return 0;
+    if (precision != NSM_FP32 && precision != NSM_BF16 && precision != NSM_FP8) return 0;
+    if (precision == NSM_BF16 && levels < 3) return 0;
+    return deep_region_bytes(H, W) + deep_act_bytes(H, W, precision) + deep_images_bytes(levels, precision);
+}
+
+nsm_status nsm_infer_deep(nsm_ctx* ctx, const nsm_frame* frame, const float* dev_params, int levels, void* workspace,
+                          size_t workspace_bytes, float* vis_out, void* stream) {
+    return nsm_infer_deep_ex(ctx, frame, dev_params, levels, NSM_FP32, workspace, workspace_bytes, vis_out, stream);
+}
+
+nsm_status nsm_infer_deep_ex(nsm_ctx* ctx, const nsm_frame* frame, const float* dev_params, int levels,
+                             nsm_precision precision, void* workspace, size_t workspace_bytes, float* vis_out,
+                             void* stream) {
+    nsm_status s = deep_check(ctx, frame, levels, precision);
+    if (s != NSM_OK) return s;
+    const int H = frame->H, W = frame->W;
+    if (static_cast<size_t>(H) * W == 0) return NSM_OK;
+    if ((s = check_dev_ptr(dev_params, "dev_params", 4)) != NSM_OK || (s = check_dev_ptr(vis_out, "vis_out", 4)) != NSM_OK)
+        return s;
+    const size_t need = nsm_infer_deep_ex_workspace_bytes(H, W, levels, precision);
+    if (!workspace || workspace_bytes < need)
+        return fail(NSM_ERR_WORKSPACE, "workspace of %zu bytes given, %zu needed", workspace_bytes, need);
+    if ((s = check_dev_ptr(workspace, "workspace", 256)) != NSM_OK) return s;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    // the weights packed per call after the call's own regions
+    char* images = static_cast<char*>(workspace) + deep_region_bytes(H, W) + deep_act_bytes(H, W, precision);
+    DeepImgs P;
+    cudaError_t e = deep_pack(dev_params, levels, precision, images, &P, st);
+    if (e == cudaSuccess) e = deep_run(ctx, frame, dev_params, levels, precision, P, workspace, vis_out, st);
     return e == cudaSuccess ? NSM_OK : cuda_fail(e, "deep forward");
+}
+
+nsm_status nsm_deep_weights_create(nsm_ctx* ctx, const float* host_params, size_t n, int levels,
+                                   nsm_precision precision, nsm_deep_weights** out) {
+    if (!ctx || !host_params || !out) return fail(NSM_ERR_INVALID_ARG, "ctx, host_params and out must be non-NULL");
+    *out = nullptr;
+    if (levels < 2 || levels > 7) return fail(NSM_ERR_INVALID_ARG, "levels must be 2 .. 7, got %d", levels);
+    if (precision != NSM_FP32 && precision != NSM_BF16 && precision != NSM_FP8)
+        return fail(NSM_ERR_UNSUPPORTED, "the deeper networks run in the FP32, BF16 or three-term FP8 form");
+    if (precision == NSM_BF16 && levels < 3)
+        return fail(NSM_ERR_UNSUPPORTED, "the BF16 form needs 3 or more levels, got %d", levels);
+    if (n != deep_param_count(levels))
+        return fail(NSM_ERR_SHAPE, "parameter vector has %zu floats, expected %zu", n, deep_param_count(levels));
+    if (n > static_cast<size_t>(INT32_MAX) || !finite_all(host_params, static_cast<int>(n)))
+        return fail(NSM_ERR_INVALID_ARG, "parameters must be finite");
+    nsm_deep_weights* w = new nsm_deep_weights{};
+    cudaGetDevice(&w->device);
+    w->levels = levels;
+    w->precision = precision;
+    w->n = n;
+    cudaError_t e = cudaMalloc(&w->d_params, n * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&w->d_images, deep_images_bytes(levels, precision));
+    if (e == cudaSuccess) e = cudaMemcpy(w->d_params, host_params, n * sizeof(float), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = deep_pack(w->d_params, levels, precision, w->d_images, &w->imgs, nullptr);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(nullptr);
+    if (e != cudaSuccess) {
+        nsm_deep_weights_destroy(w);
+        return cuda_fail(e, "deep weights");
+    }
+    *out = w;
+    return NSM_OK;
+}
+
+nsm_status nsm_deep_weights_load_device(nsm_deep_weights* w, const float* dev_params, size_t n, void* stream) {
+    if (!w) return fail(NSM_ERR_INVALID_ARG, "weights are NULL");
+    if (n != w->n) return fail(NSM_ERR_SHAPE, "%zu floats given, the weights hold %zu", n, w->n);
+    nsm_status s = check_dev_ptr(dev_params, "dev_params", 4);
+    if (s != NSM_OK) return s;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaMemcpyAsync(w->d_params, dev_params, n * sizeof(float), cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess) e = deep_pack(w->d_params, w->levels, w->precision, w->d_images, &w->imgs, st);
+    return e == cudaSuccess ? NSM_OK : cuda_fail(e, "deep weights repack");
+}
+
+void nsm_deep_weights_destroy(nsm_deep_weights* w) {
+    if (!w) return;
+    cudaFree(w->d_params);
+    cudaFree(w->d_images);
+    delete w;
+}
+
+size_t nsm_infer_deep_packed_workspace_bytes(int H, int W, int levels, nsm_precision precision) {
+    if (nsm_infer_deep_ex_workspace_bytes(H, W, levels, precision) == 0) return 0;
+    return deep_region_bytes(H, W) + deep_act_bytes(H, W, precision);
+}
+
+nsm_status nsm_infer_deep_packed(nsm_ctx* ctx, const nsm_frame* frame, const nsm_deep_weights* w, void* workspace,
+                                 size_t workspace_bytes, float* vis_out, void* stream) {
+    if (!w) return fail(NSM_ERR_INVALID_ARG, "weights are NULL");
+    nsm_status s = deep_check(ctx, frame, w->levels, w->precision);
+    if (s != NSM_OK) return s;
+    const int H = frame->H, W = frame->W;
+    if (static_cast<size_t>(H) * W == 0) return NSM_OK;
+    int dev = -1;
+    cudaGetDevice(&dev);
+    if (dev != w->device) return fail(NSM_ERR_INVALID_ARG, "weights live on device %d, current device %d", w->device, dev);
+    if ((s = check_dev_ptr(vis_out, "vis_out", 4)) != NSM_OK) return s;
+    const size_t need = nsm_infer_deep_packed_workspace_bytes(H, W, w->levels, w->precision);
+    if (!workspace || workspace_bytes < need)
+        return fail(NSM_ERR_WORKSPACE, "workspace of %zu bytes given, %zu needed", workspace_bytes, need);
+    if ((s = check_dev_ptr(workspace, "workspace", 256)) != NSM_OK) return s;
+    const cudaError_t e = deep_run(ctx, frame, w->d_params, w->levels, w->precision, w->imgs, workspace, vis_out,
+                                   static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? NSM_OK : cuda_fail(e, "deep forward (packed weights)");
 }
 
 }  // extern "C"

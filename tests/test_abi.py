@@ -124,10 +124,38 @@ def test_host_validation_of_the_newer_entry_points(lib):
         assert fp32 == nsm.nsm_infer_deep_workspace_bytes(64, 128, L)
         assert nsm.nsm_infer_deep_workspace_bytes(64, 128, L, nsm.NSM_BF16) > fp32
     assert nsm.nsm_infer_deep_workspace_bytes(64, 128, 2, nsm.NSM_BF16) == 0
-    # the three-term FP8 form: 2 .. 7 levels, the FP32 form's workspace plus the E4M3 images
+    # the three-term FP8 form: 2 .. 7 levels, the FP32 form's tensors plus the
+    # E4M3 images (in place of the FP32 form's weight copy)
     for L in (2, 3, 5, 7):
-        assert nsm.nsm_infer_deep_workspace_bytes(64, 128, L, nsm.NSM_FP8) > nsm.nsm_infer_deep_workspace_bytes(64, 128, L)
+        assert nsm.nsm_infer_deep_workspace_bytes(64, 128, L, nsm.NSM_FP8) > 64 * 128 * 84 * 4
     assert nsm.nsm_infer_deep_workspace_bytes(64, 128, 5, 3) == 0
+
+
+def test_packed_deep_weights_host_checks_and_workspace(lib):
+    """The packed-weights entry points reject NULL handles before any CUDA
+    call; their workspace is the per-call one without the packed images (for
+    FP32: the tap-major copy of the vector, 256-byte aligned)."""
+    typed = nsm._gen_sigs()
+    h = ctypes.c_void_p()
+    assert typed.nsm_deep_weights_create(None, None, 0, 5, nsm.NSM_FP32, ctypes.byref(h)) == 1
+    assert b"ctx" in lib.nsm_last_error()
+    assert typed.nsm_infer_deep_packed(None, None, None, None, 0, None, None) == 1
+    assert b"weights" in lib.nsm_last_error()
+    assert typed.nsm_deep_weights_load_device(None, None, 0, None) == 1
+    typed.nsm_deep_weights_destroy(None)  # a no-op
+    for L in (2, 3, 5, 7):
+        n = N.param_count(L, with_bias=True)
+        ex = nsm.nsm_infer_deep_workspace_bytes(64, 128, L, nsm.NSM_FP32)
+        packed = nsm.nsm_infer_deep_packed_workspace_bytes(64, 128, L, nsm.NSM_FP32)
+        assert ex - packed == (n * 4 + 255) // 256 * 256
+        assert nsm.nsm_infer_deep_packed_workspace_bytes(64, 128, L, nsm.NSM_FP8) == packed
+        assert nsm.nsm_infer_deep_workspace_bytes(64, 128, L, nsm.NSM_FP8) > packed
+        if L >= 3:
+            bf = nsm.nsm_infer_deep_packed_workspace_bytes(64, 128, L, nsm.NSM_BF16)
+            assert packed < bf < nsm.nsm_infer_deep_workspace_bytes(64, 128, L, nsm.NSM_BF16)
+    assert nsm.nsm_infer_deep_packed_workspace_bytes(64, 128, 2, nsm.NSM_BF16) == 0
+    assert nsm.nsm_infer_deep_packed_workspace_bytes(64, 128, 8, nsm.NSM_FP32) == 0
+    assert nsm.nsm_infer_deep_packed_workspace_bytes(64, 128, 5, 3) == 0
 
 
 def test_host_validation_of_the_static_entry_point(lib):

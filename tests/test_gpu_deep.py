@@ -137,3 +137,48 @@ def test_deep_rejects_bad_shapes(ctx):
     assert ei.value.status == 2
     with pytest.raises(nsm.NSMError):
         nsm.nsm_infer_deep(ctx, df.frame, torch.from_numpy(theta).cuda(), 8, ws, torch.empty((40, 64), device="cuda"))
+
+
+@pytest.mark.parametrize("precision,L,H,W", [(0, 2, 68, 132), (0, 5, 128, 192), (1, 3, 96, 136), (1, 5, 256, 656),
+                                             (2, 3, 96, 136), (2, 7, 128, 192)])
+def test_packed_weights_equal_the_per_call_packing(ctx, precision, L, H, W):
+    """nsm_infer_deep_packed from weights packed once gives the same bits as
+    nsm_infer_deep_ex, which packs the same vector per call, in every form
+    (FP32 = 0, BF16 = 1, FP8 three-term = 2), with the smaller workspace;
+    re-packing from a device vector (load_device) follows the new weights."""
+    f = scenegen.soft_frame(H, W, 256, 256, 16, 80 + L)
+    df = DeviceFrame(f)
+    theta = scenegen.he_init_weights(L, N.layer_table(L)).astype(np.float32)
+    ex = _deep(ctx, df, theta, L, precision)
+    w = nsm.DeepWeights(ctx, theta, L, precision)
+    ws = torch.empty((nsm.nsm_infer_deep_packed_workspace_bytes(H, W, L, precision),), dtype=torch.uint8,
+                     device="cuda")
+    vis = torch.empty((H, W), device="cuda")
+    nsm.nsm_infer_deep_packed(ctx, df.frame, w, ws, vis)
+    torch.cuda.synchronize()
+    ctx.check()
+    assert np.array_equal(vis.cpu().numpy().astype(np.float64), ex)
+    theta2 = (theta * np.float32(0.75)).astype(np.float32)
+    w.load_device(torch.from_numpy(theta2).cuda())
+    nsm.nsm_infer_deep_packed(ctx, df.frame, w, ws, vis)
+    torch.cuda.synchronize()
+    ctx.check()
+    assert np.array_equal(vis.cpu().numpy().astype(np.float64), _deep(ctx, df, theta2, L, precision))
+    w.close()
+
+
+def test_packed_weights_reject_bad_arguments(ctx):
+    theta = scenegen.he_init_weights(3, N.layer_table(3)).astype(np.float32)
+    with pytest.raises(nsm.NSMError) as ei:
+        nsm.DeepWeights(ctx, theta[:-1], 3, nsm.NSM_FP32)
+    assert ei.value.status == 2  # NSM_ERR_SHAPE
+    with pytest.raises(nsm.NSMError) as ei:
+        nsm.DeepWeights(ctx, scenegen.he_init_weights(2, N.layer_table(2)).astype(np.float32), 2, nsm.NSM_BF16)
+    assert ei.value.status == 7  # NSM_ERR_UNSUPPORTED
+    w = nsm.DeepWeights(ctx, theta, 3, nsm.NSM_BF16)
+    f = scenegen.hard_frame(64, 64, 64, 64, 4, 2)
+    need = nsm.nsm_infer_deep_packed_workspace_bytes(64, 64, 3, nsm.NSM_BF16)
+    ws = torch.empty((need - 256,), dtype=torch.uint8, device="cuda")
+    with pytest.raises(nsm.NSMError):
+        nsm.nsm_infer_deep_packed(ctx, DeviceFrame(f).frame, w, ws, torch.empty((64, 64), device="cuda"))
+    w.close()
