@@ -16,7 +16,8 @@
 //              a whole level: the input up-sampled while staging (decoders),
 //              3x3, ReLU, the 1x1 in the epilogue, then the rectified
 //              checkpoint, the 2x2 pooling (encoders) or the head (level 0);
-//   conv1x1    1x1 layers without tile staging (one thread per pixel);
+//   conv1x1    1x1 layers: coalesced pixel tiles through shared memory, one
+//              thread per pixel for the products;
 //   conv_wgrad dW += sum_p g~(p) x~(p + tap), db += sum_p g~(p): 8 x 8 register
 //              blocks of outer products per thread, one atomicAdd per weight
 //              per CTA; wgrad1x1 for the 1x1 layers (grid-stride, no staging);
@@ -466,56 +467,103 @@ __global__ void __launch_bounds__(256) wgrad1x1_kernel(const float* __restrict__
         for (int i = tid; i < COUT; i += 256) atomicAdd(db + i, red[CIN * COUT + i]);
 }
 
-// 1x1 layers (no halo, so no tile staging): one thread per pixel, the pixel's
-// input channels in registers, the weights ws[c][o] broadcast from shared
-// memory; same operand semantics as conv_fwd_kernel with K = 1, and the same
-// summation order (bias, then c = 0, 1, ...), so the same values.
+// 1x1 layers (no halo): tiles of kP1 pixels, whose NHWC rows are contiguous in
+// memory, move between HBM and a shared tile with consecutive threads on
+// consecutive float4s (coalesced); the input rectification / mask is applied
+// while loading and the output mask while storing, both in that layout.  In
+// between one thread per pixel reads its row, the weights ws[c][o] broadcast
+// from shared memory; same operand semantics as conv_fwd_kernel with K = 1 and
+// the same summation order (bias, then c = 0, 1, ...), so the same values.
+// Rows are padded to S = max(C_in, C_out) + 4 floats (conflict-free float4
+// row reads); the output rows overwrite the input rows of the same tile.
+constexpr int kP1 = 256;  // pixels per tile = threads per CTA
+
 template <int CIN, int COUT>
-__global__ void __launch_bounds__(256) conv1x1_kernel(const float* __restrict__ x, const float* __restrict__ xm,
+struct Conv1x1Shape {
+    static constexpr int S = (CIN > COUT ? CIN : COUT) + 4;
+    static constexpr size_t SMEM = sizeof(float) * (static_cast<size_t>(kP1) * S + CIN * COUT);
+};
+
+template <int CIN, int COUT>
+__global__ void __launch_bounds__(kP1) conv1x1_kernel(const float* __restrict__ x, const float* __restrict__ xm,
                                                       int relu_in, size_t npx, const float* __restrict__ w, int tf,
                                                       const float* __restrict__ b, const float* __restrict__ ym,
                                                       float* __restrict__ y) {
     static_assert(CIN % 4 == 0 && COUT % 4 == 0, "float4 channels");
-    __shared__ float4 ws4[CIN * COUT / 4];
+    constexpr int S = Conv1x1Shape<CIN, COUT>::S, CI4 = CIN / 4, CO4 = COUT / 4;
+    extern __shared__ float4 smem1[];
+    float* rows = reinterpret_cast<float*>(smem1);             // [kP1][S]
+    float4* ws4 = smem1 + kP1 * S / 4;                          // [CIN][COUT]
     float* ws = reinterpret_cast<float*>(ws4);
-    for (int i = threadIdx.x; i < CIN * COUT; i += blockDim.x) {
+    const int t = threadIdx.x;
+    for (int i = t; i < CIN * COUT; i += kP1) {
         const int c = i / COUT, o = i % COUT;
         ws[i] = tf ? __ldg(w + c * COUT + o) : __ldg(w + o * CIN + c);
     }
-    __syncthreads();
-    for (size_t p = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; p < npx;
-         p += static_cast<size_t>(gridDim.x) * blockDim.x) {
+    const size_t tiles = (npx + kP1 - 1) / kP1;
+    for (size_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+        const size_t p0 = tile * kP1;
+        const int np = static_cast<int>(npx - p0 < static_cast<size_t>(kP1) ? npx - p0 : kP1);
+        // coalesced input rows -> shared tile (rectified / masked)
+        const float4* x4 = reinterpret_cast<const float4*>(x + p0 * CIN);
+        const float4* xm4 = xm ? reinterpret_cast<const float4*>(xm + p0 * CIN) : nullptr;
+#pragma unroll
+        for (int k = 0; k < CI4; ++k) {
+            const int i = t + kP1 * k;  // float4 index within the tile
+            if (i < np * CI4) {
+                float4 v = __ldg(x4 + i);
+                if (relu_in) v = make_float4(fmaxf(v.x, 0.f), fmaxf(v.y, 0.f), fmaxf(v.z, 0.f), fmaxf(v.w, 0.f));
+                if (xm4) {
+                    const float4 m = __ldg(xm4 + i);
+                    v = make_float4(m.x > 0.f ? v.x : 0.f, m.y > 0.f ? v.y : 0.f, m.z > 0.f ? v.z : 0.f,
+                                    m.w > 0.f ? v.w : 0.f);
+                }
+                *reinterpret_cast<float4*>(rows + (i / CI4) * S + 4 * (i % CI4)) = v;
+            }
+        }
+        __syncthreads();
         float xv[CIN];
+        if (t < np) {
 #pragma unroll
-        for (int c4 = 0; c4 < CIN / 4; ++c4) {
-            float4 v = __ldg(reinterpret_cast<const float4*>(x + p * CIN) + c4);
-            if (relu_in) v = make_float4(fmaxf(v.x, 0.f), fmaxf(v.y, 0.f), fmaxf(v.z, 0.f), fmaxf(v.w, 0.f));
-            if (xm) {
-                const float4 m = __ldg(reinterpret_cast<const float4*>(xm + p * CIN) + c4);
-                v = make_float4(m.x > 0.f ? v.x : 0.f, m.y > 0.f ? v.y : 0.f, m.z > 0.f ? v.z : 0.f,
-                                m.w > 0.f ? v.w : 0.f);
+            for (int c4 = 0; c4 < CI4; ++c4) {
+                const float4 v = *reinterpret_cast<const float4*>(rows + t * S + 4 * c4);
+                xv[4 * c4] = v.x; xv[4 * c4 + 1] = v.y; xv[4 * c4 + 2] = v.z; xv[4 * c4 + 3] = v.w;
             }
-            xv[4 * c4] = v.x; xv[4 * c4 + 1] = v.y; xv[4 * c4 + 2] = v.z; xv[4 * c4 + 3] = v.w;
         }
-        float4* dst = reinterpret_cast<float4*>(y + p * COUT);
+        __syncthreads();  // every input row read before the output rows overwrite them
+        if (t < np) {
 #pragma unroll 2
-        for (int o4 = 0; o4 < COUT / 4; ++o4) {
-            float4 s = b ? __ldg(reinterpret_cast<const float4*>(b) + o4) : make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int o4 = 0; o4 < CO4; ++o4) {
+                float4 s = b ? __ldg(reinterpret_cast<const float4*>(b) + o4) : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-            for (int c = 0; c < CIN; ++c) {
-                const float4 wv = ws4[c * (COUT / 4) + o4];
-                s.x = fmaf(xv[c], wv.x, s.x);
-                s.y = fmaf(xv[c], wv.y, s.y);
-                s.z = fmaf(xv[c], wv.z, s.z);
-                s.w = fmaf(xv[c], wv.w, s.w);
+                for (int c = 0; c < CIN; ++c) {
+                    const float4 wv = ws4[c * CO4 + o4];
+                    s.x = fmaf(xv[c], wv.x, s.x);
+                    s.y = fmaf(xv[c], wv.y, s.y);
+                    s.z = fmaf(xv[c], wv.z, s.z);
+                    s.w = fmaf(xv[c], wv.w, s.w);
+                }
+                *reinterpret_cast<float4*>(rows + t * S + 4 * o4) = s;
             }
-            if (ym) {
-                const float4 m = __ldg(reinterpret_cast<const float4*>(ym + p * COUT) + o4);
-                s = make_float4(m.x > 0.f ? s.x : 0.f, m.y > 0.f ? s.y : 0.f, m.z > 0.f ? s.z : 0.f,
-                                m.w > 0.f ? s.w : 0.f);
-            }
-            dst[o4] = s;
         }
+        __syncthreads();
+        // shared tile -> coalesced output rows (masked)
+        float4* y4 = reinterpret_cast<float4*>(y + p0 * COUT);
+        const float4* ym4 = ym ? reinterpret_cast<const float4*>(ym + p0 * COUT) : nullptr;
+#pragma unroll
+        for (int k = 0; k < CO4; ++k) {
+            const int i = t + kP1 * k;
+            if (i < np * CO4) {
+                float4 s = *reinterpret_cast<const float4*>(rows + (i / CO4) * S + 4 * (i % CO4));
+                if (ym4) {
+                    const float4 m = __ldg(ym4 + i);
+                    s = make_float4(m.x > 0.f ? s.x : 0.f, m.y > 0.f ? s.y : 0.f, m.z > 0.f ? s.z : 0.f,
+                                    m.w > 0.f ? s.w : 0.f);
+                }
+                y4[i] = s;
+            }
+        }
+        __syncthreads();  // the tile's rows are free for the next tile
     }
 }
 
@@ -528,7 +576,17 @@ cudaError_t conv_fwd(const float* x, const float* xm, int relu_in, int N, int H,
     if constexpr (K == 1 && CB == CIN && OB == COUT && C1 == 0 && !UPIN && !HEAD && CIN * COUT <= 4096) {
         const size_t npx = static_cast<size_t>(N) * H * W;
         if (npx == 0) return cudaSuccess;
-        conv1x1_kernel<CIN, COUT><<<ew_grid(npx), 256, 0, st>>>(x, xm, relu_in, npx, w, tf, b, ym, y);
+        constexpr size_t smem = Conv1x1Shape<CIN, COUT>::SMEM;
+        auto kern = conv1x1_kernel<CIN, COUT>;
+        static int per_sm = 0;  // resident CTAs per SM, from the shared tile's size
+        if (per_sm == 0) {
+            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+            if (e != cudaSuccess) return e;
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kP1, smem) != cudaSuccess || per_sm < 1)
+                per_sm = 1;
+        }
+        const size_t tiles = (npx + kP1 - 1) / kP1, cap = static_cast<size_t>(num_sms()) * per_sm;
+        kern<<<static_cast<unsigned>(tiles < cap ? tiles : cap), kP1, smem, st>>>(x, xm, relu_in, npx, w, tf, b, ym, y);
         return cudaGetLastError();
     }
     constexpr int P = K / 2, TW = TJ * FwdShape<CB, OB>::PX;
