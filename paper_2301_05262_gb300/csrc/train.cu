@@ -712,27 +712,50 @@ __global__ void up_fwd_kernel(const float* __restrict__ lo, const float* __restr
 // reach it, with those taps' weights.
 __global__ void up_adj_kernel(const float* __restrict__ g, int N, int H, int W, int c4s, float* __restrict__ glo) {
     // coarse rows on grid.y (R = n Hl + Y), four channels (one float4) per
-    // thread, C / 4 = 2^c4s
+    // thread, C / 4 = 2^c4s.  Only fine indices 2X - 1 .. 2X + 2 reach coarse
+    // X (bilin_tap clamps at the borders, where the clamped tap also falls in
+    // that window): their 16 cotangents are loaded together from clamped
+    // (always valid) addresses, and the terms of nonzero weight are summed in
+    // row-major order.
     const int Hl = H / 2, Wl = W / 2, C4 = 1 << c4s, per_row = Wl << c4s;
     const float4* g4 = reinterpret_cast<const float4*>(g);
     for (int R = blockIdx.y; R < N * Hl; R += gridDim.y) {
         const int n = R / Hl, Y = R - n * Hl;
+        float wy[4];
+        int yc[4];
+#pragma unroll
+        for (int d = 0; d < 4; ++d) {
+            const int yy = 2 * Y - 1 + d;
+            yc[d] = yy < 0 ? 0 : (yy >= H ? H - 1 : yy);
+            const BilinTap ty = bilin_tap(yc[d], Hl);
+            wy[d] = (yy < 0 || yy >= H) ? 0.f : (ty.i0 == Y ? ty.w0 : 0.f) + (ty.i1 == Y ? ty.w1 : 0.f);
+        }
         for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < per_row; t += gridDim.x * blockDim.x) {
             const int X = t >> c4s, c4 = t & (C4 - 1);
+            float wx[4];
+            int xc[4];
+#pragma unroll
+            for (int d = 0; d < 4; ++d) {
+                const int xx = 2 * X - 1 + d;
+                xc[d] = xx < 0 ? 0 : (xx >= W ? W - 1 : xx);
+                const BilinTap tx = bilin_tap(xc[d], Wl);
+                wx[d] = (xx < 0 || xx >= W) ? 0.f : (tx.i0 == X ? tx.w0 : 0.f) + (tx.i1 == X ? tx.w1 : 0.f);
+            }
+            float4 v[4][4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    v[i][j] = __ldg(g4 + ((static_cast<size_t>(n) * H + yc[i]) * W + xc[j]) * C4 + c4);
             float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
-            for (int yy = 2 * Y - 2; yy <= 2 * Y + 3; ++yy) {
-                if (yy < 0 || yy >= H) continue;
-                const BilinTap ty = bilin_tap(yy, Hl);
-                const float wy = (ty.i0 == Y ? ty.w0 : 0.f) + (ty.i1 == Y ? ty.w1 : 0.f);
-                if (wy == 0.f) continue;
-                for (int xx = 2 * X - 2; xx <= 2 * X + 3; ++xx) {
-                    if (xx < 0 || xx >= W) continue;
-                    const BilinTap tx = bilin_tap(xx, Wl);
-                    const float wx = (tx.i0 == X ? tx.w0 : 0.f) + (tx.i1 == X ? tx.w1 : 0.f);
-                    if (wx == 0.f) continue;
-                    const float wt = wy * wx;
-                    const float4 v = __ldg(g4 + ((static_cast<size_t>(n) * H + yy) * W + xx) * C4 + c4);
-                    s.x += wt * v.x; s.y += wt * v.y; s.z += wt * v.z; s.w += wt * v.w;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                if (wy[i] == 0.f) continue;
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    if (wx[j] == 0.f) continue;
+                    const float wt = wy[i] * wx[j];
+                    s.x += wt * v[i][j].x; s.y += wt * v[i][j].y; s.z += wt * v[i][j].z; s.w += wt * v[i][j].w;
                 }
             }
             reinterpret_cast<float4*>(glo)[static_cast<size_t>(R) * per_row + t] = s;
