@@ -363,29 +363,35 @@ __global__ void __launch_bounds__(kWgThreads) wgrad_tc_kernel(const float* __res
     if (warp == 0) tmem_dealloc(tbase, C::TMEM_COLS);
 }
 
-// dW[e] += sum over slots s (in order) of part[s][e] for e < nw, db[e - nw] += ... beyond.
-// 32 entries per block (one per lane); the 8 warps take slots w, w + 8, ...
-// and meet in shared memory in warp order.
-__global__ void __launch_bounds__(256) wg_reduce_kernel(const float* __restrict__ part, int slots, int entries, int nw,
-                                                        float* __restrict__ dW, float* __restrict__ db) {
-    __shared__ float red[8][33];
+// dW[e] += sum over slots s of part[s][e] for e < nw, db[e - nw] += ... beyond.
+// 32 entries per block (one per lane); the 32 warps take slots w, w + 32, ...
+// into four accumulators (slot s to accumulator (s / 32) % 4, the tail to the
+// first) and meet in shared memory in warp order: a fixed order, so the same
+// sums every run.
+constexpr int kRedThreads = 1024;
+__global__ void __launch_bounds__(kRedThreads) wg_reduce_kernel(const float* __restrict__ part, int slots, int entries,
+                                                                int nw, float* __restrict__ dW, float* __restrict__ db) {
+    constexpr int NWp = kRedThreads / 32;
+    __shared__ float red[NWp][33];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int e = blockIdx.x * 32 + lane;
-    float a0 = 0.f, a1 = 0.f;
+    float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
     if (e < entries) {
         int s = warp;
-        for (; s + 8 < slots; s += 16) {
+        for (; s + 3 * NWp < slots; s += 4 * NWp) {  // four loads in flight per thread
             a0 += __ldg(part + static_cast<size_t>(s) * entries + e);
-            a1 += __ldg(part + static_cast<size_t>(s + 8) * entries + e);
+            a1 += __ldg(part + static_cast<size_t>(s + NWp) * entries + e);
+            a2 += __ldg(part + static_cast<size_t>(s + 2 * NWp) * entries + e);
+            a3 += __ldg(part + static_cast<size_t>(s + 3 * NWp) * entries + e);
         }
-        if (s < slots) a0 += __ldg(part + static_cast<size_t>(s) * entries + e);
+        for (; s < slots; s += NWp) a0 += __ldg(part + static_cast<size_t>(s) * entries + e);
     }
-    red[warp][lane] = a0 + a1;
+    red[warp][lane] = (a0 + a1) + (a2 + a3);
     __syncthreads();
     if (warp == 0 && e < entries) {
         float v = 0.f;
 #pragma unroll
-        for (int w = 0; w < 8; ++w) v += red[w][lane];
+        for (int w = 0; w < NWp; ++w) v += red[w][lane];
         if (e < nw) dW[e] += v;
         else if (db != nullptr) db[e - nw] += v;
     }
@@ -420,7 +426,7 @@ cudaError_t launch_wgrad(const float* x, int relu_in, const float* g, const floa
                                                                                         part, err);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    wg_reduce_kernel<<<(C::ENTRIES + 31) / 32, 256, 0, st>>>(part, gx, C::ENTRIES, COUT * CIN * K * K, dW, db);
+    wg_reduce_kernel<<<(C::ENTRIES + 31) / 32, kRedThreads, 0, st>>>(part, gx, C::ENTRIES, COUT * CIN * K * K, dW, db);
     return cudaGetLastError();
 }
 
@@ -441,7 +447,7 @@ cudaError_t wgrad_tc(int cin, int cout, int k, const float* x, int relu_in, cons
 
 cudaError_t slot_reduce(const float* part, int slots, int entries, int nw, float* dW, float* db, cudaStream_t st) {
     if (slots < 1 || entries < 1) return cudaSuccess;
-    wg_reduce_kernel<<<(entries + 31) / 32, 256, 0, st>>>(part, slots, entries, nw, dW, db);
+    wg_reduce_kernel<<<(entries + 31) / 32, kRedThreads, 0, st>>>(part, slots, entries, nw, dW, db);
     return cudaGetLastError();
 }
 
