@@ -34,11 +34,14 @@ itself; the tests under tests/test_oracle_*.py):
   penumbra_width -- the r_e = 0 and r_s = 0 closed forms (similar triangles).
   conv2d / avgpool2 / upsample2 -- direct summation loops, torch FP64
       library routines, adjoint dot-product identities.
-  forward / backward -- composition of the pinned operators; backward against
+  forward / backward -- forward against the network written out level by
+      level with direct-summation convolutions, explicit 2 x 2 means and loop
+      bilinear up-sampling (3 and 4 levels, 8 x 8 inputs: a dropped skip, a
+      missing ReLU or pooling before the ReLU each fail it); backward against
       central finite differences; parameter and MAC counts against the
-      paper's printed table values.  With random weights the network output
-      has no printed worked example: parity with respect to trained weights
-      is unpinned beyond the operator level.
+      paper's printed table values.  The paper prints no worked example of
+      the network's output; trained weights are only inputs to these
+      definitions.
   loss_l1 / adam_update / train_step -- closed forms on small vectors and
       finite differences of the loss.
   reproject_fp32 / accept_fp32 / instability_pair / temporal_instability --

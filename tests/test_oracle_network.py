@@ -478,6 +478,51 @@ def test_forward_s2d_matches_direct_summation_network():
     np.testing.assert_allclose(N.forward_s2d(feat, theta), ref, rtol=0, atol=1e-12)
 
 
+@pytest.mark.parametrize("levels", [3, 4])
+def test_forward_matches_direct_summation_network(levels):
+    """forward against the Sec. 3.5 network written out level by level with
+    direct-summation convolutions, explicit 2x2 means and the loop bilinear
+    up-sampling (8 x 8 input: the 4-level bottleneck is 1 x 1): per encoder
+    level 3x3, ReLU, 1x1, ReLU, the rectified output kept as the skip at
+    levels 1 .. L-2, then the mean of each 2 x 2 block; the bottleneck; per
+    decoder level up-sampling (plus the skip), 3x3, ReLU, 1x1, ReLU; the 16 -> 1
+    head and the sigmoid."""
+    rng = np.random.default_rng(40 + levels)
+    n = N.param_count(levels, with_bias=True)
+    theta = rng.normal(0, 0.25, n)
+    feat = rng.normal(0, 1, (4, 8, 8))
+    P = N.unpack(theta, levels)
+    relu = lambda v: np.maximum(v, 0)
+
+    def block(x, key):
+        return relu(_naive_conv(relu(_naive_conv(x, *P[f"{key}_3x3"])), *P[f"{key}_1x1"]))
+
+    def pool(x):
+        C, H, W = x.shape
+        y = np.zeros((C, H // 2, W // 2))
+        for c in range(C):
+            for i in range(H // 2):
+                for j in range(W // 2):
+                    y[c, i, j] = 0.25 * (x[c, 2 * i, 2 * j] + x[c, 2 * i, 2 * j + 1] + x[c, 2 * i + 1, 2 * j] +
+                                         x[c, 2 * i + 1, 2 * j + 1])
+        return y
+
+    h, skips = feat, {}
+    for l in range(levels - 1):
+        h = block(h, f"enc{l}")
+        if l >= 1:
+            skips[l] = h
+        h = pool(h)
+    h = block(h, "bott")
+    for l in range(levels - 2, -1, -1):
+        x = _naive_up(h)
+        if l >= 1:
+            x = x + skips[l]
+        h = block(x, f"dec{l}")
+    ref = 1 / (1 + np.exp(-_naive_conv(h, *P["head"])[0]))
+    np.testing.assert_allclose(N.forward(feat, theta, levels=levels), ref, rtol=0, atol=1e-12)
+
+
 def test_forward_s2d_head_bias_closed_form():
     """Zero weights everywhere but the head biases: every output is the
     sigmoid of b0 plus the detail bias of its square offset."""
