@@ -1034,9 +1034,12 @@ cudaError_t backward(const float* th, float* grad, const Buffers& b, int Nb, int
     // ---- level 0 decoder + head: recompute x = up(d1), a3, a1
     L = level(th, grad, DEC0_3, DEC0_1);
     up_fwd_kernel<<<row_grid(n * H, W * 4), 256, 0, st>>>(b.d1, nullptr, n, H, W, log2_c4(16), b.xin);
-    if (img) NSM_TRY(conv3_tc(16, 16, b.xin, n, H, W, I(8), L.b3, b.a3, err, st));
-    else NSM_TRY((conv_fwd<16, 16, 3>(b.xin, nullptr, 0, n, H, W, L.w3, 0, L.b3, nullptr, b.a3, st)));
-    NSM_TRY((conv_fwd<16, 16, 1>(b.a3, nullptr, 1, n, H, W, L.w1, 0, L.b1, nullptr, b.a1, st)));
+    if (img) {
+        NSM_TRY(conv3_tc(16, 16, b.xin, n, H, W, I(8), L.b3, b.a3, err, st, L.w1, L.b1, 16, b.a1));
+    } else {
+        NSM_TRY((conv_fwd<16, 16, 3>(b.xin, nullptr, 0, n, H, W, L.w3, 0, L.b3, nullptr, b.a3, st)));
+        NSM_TRY((conv_fwd<16, 16, 1>(b.a3, nullptr, 1, n, H, W, L.w1, 0, L.b1, nullptr, b.a1, st)));
+    }
     {
         const int hb = ew_grid(n * p0);
         head_bwd_kernel<<<hb, 256, 0, st>>>(b.a1, b.vis, b.gvis, th + o.w[HEAD], n * p0, b.ga1, grad + o.w[HEAD],
@@ -1054,9 +1057,12 @@ cudaError_t backward(const float* th, float* grad, const Buffers& b, int Nb, int
     // ---- level 1 decoder: recompute x = up(bo) + s1, a3, a1
     L = level(th, grad, DEC1_3, DEC1_1);
     up_fwd_kernel<<<row_grid(n * H1, W1 * 8), 256, 0, st>>>(b.bo, b.s1, n, H1, W1, log2_c4(32), b.xin);
-    if (img) NSM_TRY(conv3_tc(32, 32, b.xin, n, H1, W1, I(6), L.b3, b.a3, err, st));
-    else NSM_TRY((conv_fwd<32, 32, 3, 16>(b.xin, nullptr, 0, n, H1, W1, L.w3, 0, L.b3, nullptr, b.a3, st)));
-    NSM_TRY((conv_fwd<32, 16, 1>(b.a3, nullptr, 1, n, H1, W1, L.w1, 0, L.b1, nullptr, b.a1, st)));
+    if (img) {
+        NSM_TRY(conv3_tc(32, 32, b.xin, n, H1, W1, I(6), L.b3, b.a3, err, st, L.w1, L.b1, 16, b.a1));
+    } else {
+        NSM_TRY((conv_fwd<32, 32, 3, 16>(b.xin, nullptr, 0, n, H1, W1, L.w3, 0, L.b3, nullptr, b.a3, st)));
+        NSM_TRY((conv_fwd<32, 16, 1>(b.a3, nullptr, 1, n, H1, W1, L.w1, 0, L.b1, nullptr, b.a1, st)));
+    }
     // g_a1 = g_d1 (a1 > 0)
     if (img) NSM_TRY(wgrad_tc(32, 16, 1, b.a3, 1, b.glo, b.a1, n, H1, W1, b.wpart, L.dw1, L.db1, err, st));
     else NSM_TRY((conv_wgrad<32, 16, 1>(b.a3, 1, b.glo, b.a1, n, H1, W1, L.dw1, L.db1, st)));
@@ -1068,9 +1074,12 @@ cudaError_t backward(const float* th, float* grad, const Buffers& b, int Nb, int
     up_adj_kernel<<<row_grid(n * H2, W2 * 8), 256, 0, st>>>(b.gskip, n, H1, W1, log2_c4(32), b.glo);  // g bo [n][H2][W2][32]
     // ---- bottleneck: recompute a3 = conv3(p1), a1
     L = level(th, grad, BOTT_3, BOTT_1);
-    if (img) NSM_TRY(conv3_tc(32, 64, b.p1, n, H2, W2, I(4), L.b3, b.a3, err, st));
-    else NSM_TRY((conv_fwd<32, 64, 3, 16>(b.p1, nullptr, 0, n, H2, W2, L.w3, 0, L.b3, nullptr, b.a3, st)));
-    NSM_TRY((conv_fwd<64, 32, 1>(b.a3, nullptr, 1, n, H2, W2, L.w1, 0, L.b1, nullptr, b.a1, st)));
+    if (img) {
+        NSM_TRY(conv3_tc(32, 64, b.p1, n, H2, W2, I(4), L.b3, b.a3, err, st, L.w1, L.b1, 32, b.a1));
+    } else {
+        NSM_TRY((conv_fwd<32, 64, 3, 16>(b.p1, nullptr, 0, n, H2, W2, L.w3, 0, L.b3, nullptr, b.a3, st)));
+        NSM_TRY((conv_fwd<64, 32, 1>(b.a3, nullptr, 1, n, H2, W2, L.w1, 0, L.b1, nullptr, b.a1, st)));
+    }
     if (img) NSM_TRY(wgrad_tc(64, 32, 1, b.a3, 1, b.glo, b.a1, n, H2, W2, b.wpart, L.dw1, L.db1, err, st));
     else NSM_TRY((conv_wgrad<64, 32, 1>(b.a3, 1, b.glo, b.a1, n, H2, W2, L.dw1, L.db1, st)));
     NSM_TRY((conv_fwd<32, 64, 1>(b.glo, b.a1, 0, n, H2, W2, L.w1, 1, nullptr, b.a3, b.ga3, st)));
@@ -1081,9 +1090,12 @@ cudaError_t backward(const float* th, float* grad, const Buffers& b, int Nb, int
     // ---- level 1 encoder: g_h1 = pool_adj(g p1) + g s1 ; recompute a3 = conv3(e0), a1
     L = level(th, grad, ENC1_3, ENC1_1);
     pool_adj_kernel<<<row_grid(n * H1, W1 * 8), 256, 0, st>>>(b.gx, n * H1, W1, log2_c4(32), b.gskip, b.glo);
-    if (img) NSM_TRY(conv3_tc(16, 32, b.e0, n, H1, W1, I(2), L.b3, b.a3, err, st));
-    else NSM_TRY((conv_fwd<16, 32, 3>(b.e0, nullptr, 0, n, H1, W1, L.w3, 0, L.b3, nullptr, b.a3, st)));
-    NSM_TRY((conv_fwd<32, 32, 1>(b.a3, nullptr, 1, n, H1, W1, L.w1, 0, L.b1, nullptr, b.a1, st)));
+    if (img) {
+        NSM_TRY(conv3_tc(16, 32, b.e0, n, H1, W1, I(2), L.b3, b.a3, err, st, L.w1, L.b1, 32, b.a1));
+    } else {
+        NSM_TRY((conv_fwd<16, 32, 3>(b.e0, nullptr, 0, n, H1, W1, L.w3, 0, L.b3, nullptr, b.a3, st)));
+        NSM_TRY((conv_fwd<32, 32, 1>(b.a3, nullptr, 1, n, H1, W1, L.w1, 0, L.b1, nullptr, b.a1, st)));
+    }
     if (img) NSM_TRY(wgrad_tc(32, 32, 1, b.a3, 1, b.glo, b.a1, n, H1, W1, b.wpart, L.dw1, L.db1, err, st));
     else NSM_TRY((conv_wgrad<32, 32, 1>(b.a3, 1, b.glo, b.a1, n, H1, W1, L.dw1, L.db1, st)));
     NSM_TRY((conv_fwd<32, 32, 1>(b.glo, b.a1, 0, n, H1, W1, L.w1, 1, nullptr, b.a3, b.ga3, st)));
@@ -1094,9 +1106,12 @@ cudaError_t backward(const float* th, float* grad, const Buffers& b, int Nb, int
     // ---- level 0 encoder: g_h1 = pool_adj(g e0); recompute a3 = conv3(feat), a1
     L = level(th, grad, ENC0_3, ENC0_1);
     pool_adj_kernel<<<row_grid(n * H, W * 4), 256, 0, st>>>(b.gx, n * H, W, log2_c4(16), nullptr, b.gtmp);
-    if (img) NSM_TRY(conv3_tc(4, 16, b.feat, n, H, W, I(0), L.b3, b.a3, err, st));
-    else NSM_TRY((conv_fwd<4, 16, 3>(b.feat, nullptr, 0, n, H, W, L.w3, 0, L.b3, nullptr, b.a3, st)));
-    NSM_TRY((conv_fwd<16, 16, 1>(b.a3, nullptr, 1, n, H, W, L.w1, 0, L.b1, nullptr, b.a1, st)));
+    if (img) {
+        NSM_TRY(conv3_tc(4, 16, b.feat, n, H, W, I(0), L.b3, b.a3, err, st, L.w1, L.b1, 16, b.a1));
+    } else {
+        NSM_TRY((conv_fwd<4, 16, 3>(b.feat, nullptr, 0, n, H, W, L.w3, 0, L.b3, nullptr, b.a3, st)));
+        NSM_TRY((conv_fwd<16, 16, 1>(b.a3, nullptr, 1, n, H, W, L.w1, 0, L.b1, nullptr, b.a1, st)));
+    }
     if (img) NSM_TRY(wgrad_tc(16, 16, 1, b.a3, 1, b.gtmp, b.a1, n, H, W, b.wpart, L.dw1, L.db1, err, st));
     else NSM_TRY((conv_wgrad<16, 16, 1>(b.a3, 1, b.gtmp, b.a1, n, H, W, L.dw1, L.db1, st)));
     NSM_TRY((conv_fwd<16, 16, 1>(b.gtmp, b.a1, 0, n, H, W, L.w1, 1, nullptr, b.a3, b.ga3, st)));

@@ -40,9 +40,12 @@ Conv3Images conv3_images();
 cudaError_t conv3_pack(const float* theta, uint4* img, cudaStream_t st);
 // y = conv3x3(x) (+ bias), zero padded; (cin, cout) one of the layers' shapes
 // or their transposes (cudaErrorInvalidValue otherwise); err: device error
-// word, set to 7 when a bounded wait gave up.
+// word, set to 7 when a bounded wait gave up.  c1 > 0 (the level's 1x1 after
+// the 3x3, (cin, cout, c1) one of the network's levels): also y1 = b1 + W1
+// relu(y) (W1 OIHW [c1][cout]), in the separate 1x1 layer's summation order.
 cudaError_t conv3_tc(int cin, int cout, const float* x, int N, int H, int W, const uint4* img, const float* bias,
-                     float* y, int* err, cudaStream_t st);
+                     float* y, int* err, cudaStream_t st, const float* w1 = nullptr, const float* b1 = nullptr,
+                     int c1 = 0, float* y1 = nullptr);
 // Tensor-core weight gradients (train_wgrad.cu): dW += sum_p g~[p][o] x~[p + tap][c]
 // (OIHW), db += sum_p g~[p][o], x~ = relu(x) if relu_in, g~ = g (m > 0) if gm;
 // k = 3 (zero padded) or 1.  Compensated BF16 operands, FP32 accumulation in

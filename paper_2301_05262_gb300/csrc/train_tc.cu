@@ -224,10 +224,13 @@ __device__ __forceinline__ void conv3_mma(uint32_t sbase, uint32_t tbase) {
 
 // Accumulators of row r of the tile -> FP32 outputs (hi + lo weight parts
 // summed, bias added); warp w reads TMEM lane quarter w % 4 (pixels
-// 32 (w % 4) .. + 32) of rows r = w / 4, w / 4 + 2, ...
-template <int CIN, int COUT>
+// 32 (w % 4) .. + 32) of rows r = w / 4, w / 4 + 2, ...  C1 > 0: the pixel's
+// 1x1 outputs y1 = b1 + sum_c W1[.][c] relu(y[c]) as well, c ascending (the
+// separate 1x1 layer's order), from w1s [c][o] and b1s in shared memory.
+template <int CIN, int COUT, int C1>
 __device__ __forceinline__ void conv3_epilogue(uint32_t tbase, const float* bias_s, float* __restrict__ y, int n, int H,
-                                               int W, int y0, int x0) {
+                                               int W, int y0, int x0, const float* w1s, const float* b1s,
+                                               float* __restrict__ y1) {
     using C = Conv3Cfg<CIN, COUT>;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, q = warp & 3;
     const int xx = x0 + 32 * q + lane;
@@ -236,21 +239,46 @@ __device__ __forceinline__ void conv3_epilogue(uint32_t tbase, const float* bias
     for (int r = warp >> 2; r < C::R; r += kConv3Threads / 128) {
         const int yy = y0 + r;
         const bool ok = yy < H && xx < W;
-        float* out = y + ((static_cast<size_t>(n) * H + (ok ? yy : 0)) * W + (ok ? xx : 0)) * COUT;
+        const size_t pix = (static_cast<size_t>(n) * H + (ok ? yy : 0)) * W + (ok ? xx : 0);
+        float* out = y + pix * COUT;
         const uint32_t tr = tq + static_cast<uint32_t>(r * C::N);
+        float z[C1 > 0 ? C1 : 1];
+        if constexpr (C1 > 0) {
+#pragma unroll
+            for (int o = 0; o < C1; ++o) z[o] = b1s[o];
+        }
+        // the 1x1's products with channels c0 .. c0 + nc of the 3x3 output
+        auto fuse = [&](const float* v, int c0, int nc) {
+            if constexpr (C1 > 0) {
+#pragma unroll
+                for (int c = 0; c < nc; ++c) {
+                    const float xr = fmaxf(v[c], 0.f);
+                    const float4* w4 = reinterpret_cast<const float4*>(w1s + (c0 + c) * C1);
+#pragma unroll
+                    for (int o = 0; o < C1; o += 4) {
+                        const float4 w = w4[o / 4];
+                        z[o] = fmaf(xr, w.x, z[o]);
+                        z[o + 1] = fmaf(xr, w.y, z[o + 1]);
+                        z[o + 2] = fmaf(xr, w.z, z[o + 2]);
+                        z[o + 3] = fmaf(xr, w.w, z[o + 3]);
+                    }
+                }
+            }
+        };
         if constexpr (C::N <= 32) {
             float v[32];
             if constexpr (C::N == 16) tmem_ld16(tr, *reinterpret_cast<float(*)[16]>(v));
             else tmem_ld32(tr, v);
             tmem_ld_wait();
+            float s[COUT];
+#pragma unroll
+            for (int o = 0; o < COUT; ++o) s[o] = v[o] + v[C::COUTP + o] + bias_s[o];
             if (ok) {
 #pragma unroll
                 for (int o = 0; o < COUT; o += 4)
-                    *reinterpret_cast<float4*>(out + o) =
-                        make_float4(v[o] + v[C::COUTP + o] + bias_s[o], v[o + 1] + v[C::COUTP + o + 1] + bias_s[o + 1],
-                                    v[o + 2] + v[C::COUTP + o + 2] + bias_s[o + 2],
-                                    v[o + 3] + v[C::COUTP + o + 3] + bias_s[o + 3]);
+                    *reinterpret_cast<float4*>(out + o) = make_float4(s[o], s[o + 1], s[o + 2], s[o + 3]);
             }
+            fuse(s, 0, COUT);
         } else {
 #pragma unroll 1
             for (int o0 = 0; o0 < COUT; o0 += 32) {
@@ -258,25 +286,48 @@ __device__ __forceinline__ void conv3_epilogue(uint32_t tbase, const float* bias
                 tmem_ld32(tr + o0, a);
                 tmem_ld32(tr + C::COUTP + o0, b);
                 tmem_ld_wait();
+#pragma unroll
+                for (int o = 0; o < 32; ++o) a[o] = a[o] + b[o] + bias_s[o0 + o];
                 if (ok) {
 #pragma unroll
                     for (int o = 0; o < 32; o += 4)
-                        *reinterpret_cast<float4*>(out + o0 + o) =
-                            make_float4(a[o] + b[o] + bias_s[o0 + o], a[o + 1] + b[o + 1] + bias_s[o0 + o + 1],
-                                        a[o + 2] + b[o + 2] + bias_s[o0 + o + 2],
-                                        a[o + 3] + b[o + 3] + bias_s[o0 + o + 3]);
+                        *reinterpret_cast<float4*>(out + o0 + o) = make_float4(a[o], a[o + 1], a[o + 2], a[o + 3]);
                 }
+                fuse(a, o0, 32);
+            }
+        }
+        if constexpr (C1 > 0) {
+            if (ok) {
+                float* out1 = y1 + pix * C1;
+#pragma unroll
+                for (int o = 0; o < C1; o += 4)
+                    *reinterpret_cast<float4*>(out1 + o) = make_float4(z[o], z[o + 1], z[o + 2], z[o + 3]);
             }
         }
     }
 }
 
-template <int CIN, int COUT>
+// Shared memory of the kernel with a fused 1x1 (C1 > 0): its weights [c][o]
+// and bias after the 3x3 kernel's own regions.
+template <int CIN, int COUT, int C1>
+struct Conv3Fuse {
+    using C = Conv3Cfg<CIN, COUT>;
+    static constexpr uint32_t OFF_W1 = (C::BYTES_USED + 15) / 16 * 16;
+    static constexpr uint32_t USED = OFF_W1 + (C1 > 0 ? static_cast<uint32_t>(COUT * C1 + C1) * 4 : 0);
+    static constexpr uint32_t BYTES = USED < C::BYTES_MIN ? C::BYTES_MIN : USED;
+    static_assert(USED <= 227 * 1024, "shared memory per CTA");
+    static_assert(C1 % 4 == 0 && COUT % 4 == 0, "float4 rows");
+};
+
+template <int CIN, int COUT, int C1>
 __global__ void __launch_bounds__(kConv3Threads) conv3_tc_kernel(const float* __restrict__ x, int NI, int H, int W,
                                                                  const uint4* __restrict__ img,
                                                                  const float* __restrict__ bias, float* __restrict__ y,
-                                                                 int* err) {
+                                                                 int* err, const float* __restrict__ w1,
+                                                                 const float* __restrict__ b1,
+                                                                 float* __restrict__ y1) {
     using C = Conv3Cfg<CIN, COUT>;
+    using F = Conv3Fuse<CIN, COUT, C1>;
     extern __shared__ __align__(128) uint8_t smem[];
     const int tid = threadIdx.x, warp = tid >> 5;
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem + C::OFF_BAR);
@@ -287,6 +338,11 @@ __global__ void __launch_bounds__(kConv3Threads) conv3_tc_kernel(const float* __
     for (int i = tid; i < static_cast<int>(C::B_CHUNKS); i += kConv3Threads)
         st_shared_v4(sbase + C::OFF_B + 16u * i, __ldg(img + i));
     for (int i = tid; i < C::COUTP; i += kConv3Threads) bias_s[i] = (bias != nullptr && i < COUT) ? bias[i] : 0.f;
+    float* w1s = reinterpret_cast<float*>(smem + F::OFF_W1);  // [c][o], then b1
+    if constexpr (C1 > 0) {
+        for (int i = tid; i < COUT * C1; i += kConv3Threads) w1s[i] = __ldg(w1 + (i % C1) * COUT + i / C1);
+        for (int i = tid; i < C1; i += kConv3Threads) w1s[COUT * C1 + i] = b1 != nullptr ? __ldg(b1 + i) : 0.f;
+    }
     if (tid == 0) {
         mbar_init(bar, 1);
         fence_mbar_init();
@@ -336,7 +392,7 @@ __global__ void __launch_bounds__(kConv3Threads) conv3_tc_kernel(const float* __
             atomicExch(err, kConv3ErrCode);
         } else {
             fence_after_sync();
-            conv3_epilogue<CIN, COUT>(tbase, bias_s, y, n, H, W, y0, x0);
+            conv3_epilogue<CIN, COUT, C1>(tbase, bias_s, y, n, H, W, y0, x0, w1s, w1s + COUT * C1, y1);
         }
         // TMEM read out and the operand consumed before the next tile
         fence_before_sync();
@@ -347,39 +403,41 @@ __global__ void __launch_bounds__(kConv3Threads) conv3_tc_kernel(const float* __
 }
 
 // ------------------------------------------------------------------ host side
-template <int CIN, int COUT>
+template <int CIN, int COUT, int C1>
 static cudaError_t launch_conv3(const float* x, int N, int H, int W, const uint4* img, const float* bias, float* y,
-                                int* err, cudaStream_t st) {
+                                int* err, cudaStream_t st, const float* w1, const float* b1, float* y1) {
     using C = Conv3Cfg<CIN, COUT>;
+    using F = Conv3Fuse<CIN, COUT, C1>;
+    auto kern = conv3_tc_kernel<CIN, COUT, C1>;
     static int grid_cap = 0;  // CTAs resident on the device (per instantiation, set on first use)
     if (grid_cap == 0) {
-        cudaError_t e = cudaFuncSetAttribute(conv3_tc_kernel<CIN, COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             static_cast<int>(C::BYTES));
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(F::BYTES));
         if (e != cudaSuccess) return e;
         // all of the unified L1 / shared storage as shared memory: two to four CTAs per SM
-        e = cudaFuncSetAttribute(conv3_tc_kernel<CIN, COUT>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                 cudaSharedmemCarveoutMaxShared);
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
         if (e != cudaSuccess) return e;
         int dev = 0, sms = 0, per_sm = 0;
         if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
         if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-        per_sm = resident_ctas_per_sm(reinterpret_cast<const void*>(conv3_tc_kernel<CIN, COUT>), kConv3Threads,
-                                      C::BYTES);
+        per_sm = resident_ctas_per_sm(reinterpret_cast<const void*>(kern), kConv3Threads, F::BYTES);
         grid_cap = sms * (per_sm < C::TMEM_CAP ? per_sm : C::TMEM_CAP);
     }
     const long long tiles = static_cast<long long>(N) * ((H + C::R - 1) / C::R) * ((W + kTileM - 1) / kTileM);
     if (tiles == 0) return cudaSuccess;
     const int grid = tiles < grid_cap ? static_cast<int>(tiles) : grid_cap;
-    conv3_tc_kernel<CIN, COUT><<<grid, kConv3Threads, C::BYTES, st>>>(x, N, H, W, img, bias, y, err);
+    kern<<<grid, kConv3Threads, F::BYTES, st>>>(x, N, H, W, img, bias, y, err, w1, b1, y1);
     return cudaGetLastError();
 }
 
 cudaError_t conv3_tc(int cin, int cout, const float* x, int N, int H, int W, const uint4* img, const float* bias,
-                     float* y, int* err, cudaStream_t st) {
-#define NSM_CONV3(a, b) \
-    if (cin == a && cout == b) return launch_conv3<a, b>(x, N, H, W, img, bias, y, err, st);
-    NSM_CONV3(4, 16) NSM_CONV3(16, 16) NSM_CONV3(16, 32) NSM_CONV3(32, 16) NSM_CONV3(32, 32) NSM_CONV3(32, 64)
-    NSM_CONV3(64, 32) NSM_CONV3(16, 4)
+                     float* y, int* err, cudaStream_t st, const float* w1, const float* b1, int c1, float* y1) {
+#define NSM_CONV3(a, b, c)                \
+    if (cin == a && cout == b && c1 == c) \
+        return launch_conv3<a, b, c>(x, N, H, W, img, bias, y, err, st, w1, b1, y1);
+    NSM_CONV3(4, 16, 0) NSM_CONV3(16, 16, 0) NSM_CONV3(16, 32, 0) NSM_CONV3(32, 16, 0) NSM_CONV3(32, 32, 0)
+    NSM_CONV3(32, 64, 0) NSM_CONV3(64, 32, 0) NSM_CONV3(16, 4, 0)
+    // the levels' 3x3 + 1x1 pairs (enc0 and dec0, enc1, bottleneck, dec1)
+    NSM_CONV3(4, 16, 16) NSM_CONV3(16, 16, 16) NSM_CONV3(16, 32, 32) NSM_CONV3(32, 64, 32) NSM_CONV3(32, 32, 16)
 #undef NSM_CONV3
     return cudaErrorInvalidValue;
 }
