@@ -534,8 +534,9 @@ nsm_status nsm_infer_deep_ex(nsm_ctx* ctx, const nsm_frame* frame, const float* 
  * *out is owned by the caller until nsm_deep_weights_destroy (NULL is a no-op;
  * frees device memory: no call may be in flight with the weights).
  * nsm_deep_weights_load_device: replace the weights with dev_params (device,
- * same n) and re-pack, asynchronous on `stream`; the caller orders it after
- * calls that still read the old weights.
+ * same n) and re-pack, asynchronous on `stream`, on the device the weights were
+ * made on (NSM_ERR_INVALID_ARG otherwise); the caller orders it after calls
+ * that still read the old weights.
  * nsm_infer_deep_packed: nsm_infer_deep_ex from packed weights, bit-identical
  * to it for the same vector and form; workspace (device, 256-byte aligned) of
  * nsm_infer_deep_packed_workspace_bytes (0 for an unsupported combination;

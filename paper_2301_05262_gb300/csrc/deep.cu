@@ -516,6 +516,9 @@ nsm_status nsm_deep_weights_create(nsm_ctx* ctx, const float* host_params, size_
 nsm_status nsm_deep_weights_load_device(nsm_deep_weights* w, const float* dev_params, size_t n, void* stream) {
     if (!w) return fail(NSM_ERR_INVALID_ARG, "weights are NULL");
     if (n != w->n) return fail(NSM_ERR_SHAPE, "%zu floats given, the weights hold %zu", n, w->n);
+    int dev = -1;
+    cudaGetDevice(&dev);
+    if (dev != w->device) return fail(NSM_ERR_INVALID_ARG, "weights live on device %d, current device %d", w->device, dev);
     nsm_status s = check_dev_ptr(dev_params, "dev_params", 4);
     if (s != NSM_OK) return s;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
