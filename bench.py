@@ -399,7 +399,7 @@ def extra_train(nsm, scenegen, torch, device, theta, reps):
     ctx.check()
     ms_tc = sum(ev3[2 * k].elapsed_time(ev3[2 * k + 1]) for k in range(reps)) / reps
     loss_tc = float(loss.item())
-    # and with the backward's 3x3 convolutions and every weight gradient on the tensor cores
+    # and with the backward's 3x3 convolutions and 3x3 weight gradients on the tensor cores
     state_bf.set_backward_precision(nsm.NSM_BF16)
     for _ in range(3):
         state_bf.step(batch, loss_out=loss)
@@ -433,10 +433,11 @@ def extra_train(nsm, scenegen, torch, device, theta, reps):
                 "ms_per_step": ms_tb, "instances_per_s": B * T / (ms_tb * 1e-3), "loss_last": loss_tb,
                 "achieved_tflops": flop / (ms_tb * 1e-3) / 1e12,
                 "form": "every forward pass on the tcgen05 stage kernels; in the backward the 3x3 recomputations "
-                        "and data gradients as tcgen05 implicit GEMMs and every weight gradient as a tcgen05 "
-                        "pixel-reduction GEMM (compensated BF16 operands, FP32 accumulation in tensor memory, "
-                        "per-CTA slots summed in a fixed order: the same gradient bits every run); 1x1 "
-                        "recomputations and data gradients, pooling / up-sampling adjoints and Adam FP32"},
+                        "(the level's 1x1 in their epilogue) and data gradients as tcgen05 implicit GEMMs and "
+                        "every 3x3 weight gradient as a tcgen05 pixel-reduction GEMM (compensated BF16 operands, "
+                        "FP32 accumulation in tensor memory); 1x1 weight gradients FP32 on CUDA cores; every "
+                        "weight gradient from per-CTA slots summed in a fixed order (the same gradient bits every "
+                        "run); 1x1 data gradients, pooling / up-sampling adjoints and Adam FP32"},
             "algorithmic_gflop": flop / 1e9, "achieved_tflops": tflops,
             "roofline": {"bound": "alu", "peak_tflops": peak, "frac": tflops / peak,
                          "peak_src": "128 FP32 lanes x 2 FLOP x SMs x max SM clock"},

@@ -421,14 +421,15 @@ nsm_status nsm_train_state_set_forward_precision(nsm_train_state* st, nsm_precis
  * every 3x3 and 1x1 layer.  NSM_FP32 (default; FP32 CUDA-core kernels, weight
  * gradients summed with atomics, so their last bits vary from run to run) or
  * NSM_BF16 (tcgen05: implicit GEMMs for the 3x3 convolutions and a GEMM over
- * the pixels for each weight gradient, with compensated BF16 operands:
+ * the pixels for each 3x3 weight gradient, with compensated BF16 operands:
  * activations, gradients and weights as hi + lo BF16 pairs, all four products
  * accumulated in FP32 in tensor memory, ~2^-16 relative per operand; weight
- * images packed on the device at every step; every weight gradient, the
- * head's included, reduced from per-CTA partial sums in a fixed order, so the
+ * images packed on the device at every step; the 1x1 layers' weight gradients,
+ * memory-bound, in FP32 on CUDA cores; every weight gradient, the head's
+ * included, reduced from per-CTA partial sums in a fixed order, so the
  * gradient is the same bits from run to run on one device).  Tensors stay
- * FP32 between the layers; the 1x1 layers' recomputations and data gradients
- * stay FP32.  A bounded device wait that gives up sets the context's error
+ * FP32 between the layers; the 1x1 layers' recomputations (in the 3x3
+ * kernels' epilogues) and data gradients stay FP32.  A bounded device wait that gives up sets the context's error
  * word (nsm_ctx_check: NSM_ERR_TIMEOUT, code 7 or 8).  Other precisions:
  * NSM_ERR_UNSUPPORTED. */
 nsm_status nsm_train_state_set_backward_precision(nsm_train_state* st, nsm_precision precision);

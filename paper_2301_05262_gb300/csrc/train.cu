@@ -1018,10 +1018,11 @@ cudaError_t forward(const float* th, const Buffers& b, int N, int Nb, int H, int
 // Backward of the first Nb views (cotangent b.gvis) into grad (canonical
 // layout, accumulated), recomputing each level from its checkpoint.
 // With gfeat != nullptr also the feature gradient [Nb][H][W][4].  With img
-// != nullptr (the conv3_pack images of th) the 3x3 recomputations and data
-// gradients (conv3_tc) and every weight gradient (wgrad_tc, the head's by
-// per-block slots) run on the tensor cores, reduced in a fixed order, else on
-// the FP32 kernels.
+// != nullptr (the conv3_pack images of th) the 3x3 recomputations (with the
+// level's 1x1 in their epilogue) and data gradients (conv3_tc) and the 3x3
+// weight gradients (wgrad_tc) run on the tensor cores, the 1x1 weight
+// gradients on CUDA cores (wgrad1x1_tiles), every weight gradient (the head's
+// by per-block slots) reduced in a fixed order; else the FP32 kernels.
 cudaError_t backward(const float* th, float* grad, const Buffers& b, int Nb, int H, int W, float* gfeat,
                      cudaStream_t st, const uint4* img, int* err) {
     const Conv3Images im = conv3_images();
@@ -1046,7 +1047,7 @@ cudaError_t backward(const float* th, float* grad, const Buffers& b, int Nb, int
                                             img ? b.wpart : nullptr);
         if (img) NSM_TRY(slot_reduce(b.wpart, hb, 17, 17, grad + o.w[HEAD], nullptr, st));
     }
-    if (img) NSM_TRY(wgrad_tc(16, 16, 1, b.a3, 1, b.ga1, nullptr, n, H, W, b.wpart, L.dw1, L.db1, err, st));
+    if (img) NSM_TRY(wgrad1x1_tiles(16, 16, b.a3, 1, b.ga1, nullptr, n, H, W, b.wpart, L.dw1, L.db1, st));
     else NSM_TRY((conv_wgrad<16, 16, 1>(b.a3, 1, b.ga1, nullptr, n, H, W, L.dw1, L.db1, st)));
     NSM_TRY((conv_fwd<16, 16, 1>(b.ga1, nullptr, 0, n, H, W, L.w1, 1, nullptr, b.a3, b.ga3, st)));
     if (img) NSM_TRY(wgrad_tc(16, 16, 3, b.xin, 0, b.ga3, nullptr, n, H, W, b.wpart, L.dw3, L.db3, err, st));
@@ -1064,7 +1065,7 @@ cudaError_t backward(const float* th, float* grad, const Buffers& b, int Nb, int
         NSM_TRY((conv_fwd<32, 16, 1>(b.a3, nullptr, 1, n, H1, W1, L.w1, 0, L.b1, nullptr, b.a1, st)));
     }
     // g_a1 = g_d1 (a1 > 0)
-    if (img) NSM_TRY(wgrad_tc(32, 16, 1, b.a3, 1, b.glo, b.a1, n, H1, W1, b.wpart, L.dw1, L.db1, err, st));
+    if (img) NSM_TRY(wgrad1x1_tiles(32, 16, b.a3, 1, b.glo, b.a1, n, H1, W1, b.wpart, L.dw1, L.db1, st));
     else NSM_TRY((conv_wgrad<32, 16, 1>(b.a3, 1, b.glo, b.a1, n, H1, W1, L.dw1, L.db1, st)));
     NSM_TRY((conv_fwd<16, 32, 1>(b.glo, b.a1, 0, n, H1, W1, L.w1, 1, nullptr, b.a3, b.ga3, st)));
     if (img) NSM_TRY(wgrad_tc(32, 32, 3, b.xin, 0, b.ga3, nullptr, n, H1, W1, b.wpart, L.dw3, L.db3, err, st));
@@ -1080,7 +1081,7 @@ cudaError_t backward(const float* th, float* grad, const Buffers& b, int Nb, int
         NSM_TRY((conv_fwd<32, 64, 3, 16>(b.p1, nullptr, 0, n, H2, W2, L.w3, 0, L.b3, nullptr, b.a3, st)));
         NSM_TRY((conv_fwd<64, 32, 1>(b.a3, nullptr, 1, n, H2, W2, L.w1, 0, L.b1, nullptr, b.a1, st)));
     }
-    if (img) NSM_TRY(wgrad_tc(64, 32, 1, b.a3, 1, b.glo, b.a1, n, H2, W2, b.wpart, L.dw1, L.db1, err, st));
+    if (img) NSM_TRY(wgrad1x1_tiles(64, 32, b.a3, 1, b.glo, b.a1, n, H2, W2, b.wpart, L.dw1, L.db1, st));
     else NSM_TRY((conv_wgrad<64, 32, 1>(b.a3, 1, b.glo, b.a1, n, H2, W2, L.dw1, L.db1, st)));
     NSM_TRY((conv_fwd<32, 64, 1>(b.glo, b.a1, 0, n, H2, W2, L.w1, 1, nullptr, b.a3, b.ga3, st)));
     if (img) NSM_TRY(wgrad_tc(32, 64, 3, b.p1, 0, b.ga3, nullptr, n, H2, W2, b.wpart, L.dw3, L.db3, err, st));
@@ -1096,7 +1097,7 @@ cudaError_t backward(const float* th, float* grad, const Buffers& b, int Nb, int
         NSM_TRY((conv_fwd<16, 32, 3>(b.e0, nullptr, 0, n, H1, W1, L.w3, 0, L.b3, nullptr, b.a3, st)));
         NSM_TRY((conv_fwd<32, 32, 1>(b.a3, nullptr, 1, n, H1, W1, L.w1, 0, L.b1, nullptr, b.a1, st)));
     }
-    if (img) NSM_TRY(wgrad_tc(32, 32, 1, b.a3, 1, b.glo, b.a1, n, H1, W1, b.wpart, L.dw1, L.db1, err, st));
+    if (img) NSM_TRY(wgrad1x1_tiles(32, 32, b.a3, 1, b.glo, b.a1, n, H1, W1, b.wpart, L.dw1, L.db1, st));
     else NSM_TRY((conv_wgrad<32, 32, 1>(b.a3, 1, b.glo, b.a1, n, H1, W1, L.dw1, L.db1, st)));
     NSM_TRY((conv_fwd<32, 32, 1>(b.glo, b.a1, 0, n, H1, W1, L.w1, 1, nullptr, b.a3, b.ga3, st)));
     if (img) NSM_TRY(wgrad_tc(16, 32, 3, b.e0, 0, b.ga3, nullptr, n, H1, W1, b.wpart, L.dw3, L.db3, err, st));
@@ -1112,7 +1113,7 @@ cudaError_t backward(const float* th, float* grad, const Buffers& b, int Nb, int
         NSM_TRY((conv_fwd<4, 16, 3>(b.feat, nullptr, 0, n, H, W, L.w3, 0, L.b3, nullptr, b.a3, st)));
         NSM_TRY((conv_fwd<16, 16, 1>(b.a3, nullptr, 1, n, H, W, L.w1, 0, L.b1, nullptr, b.a1, st)));
     }
-    if (img) NSM_TRY(wgrad_tc(16, 16, 1, b.a3, 1, b.gtmp, b.a1, n, H, W, b.wpart, L.dw1, L.db1, err, st));
+    if (img) NSM_TRY(wgrad1x1_tiles(16, 16, b.a3, 1, b.gtmp, b.a1, n, H, W, b.wpart, L.dw1, L.db1, st));
     else NSM_TRY((conv_wgrad<16, 16, 1>(b.a3, 1, b.gtmp, b.a1, n, H, W, L.dw1, L.db1, st)));
     NSM_TRY((conv_fwd<16, 16, 1>(b.gtmp, b.a1, 0, n, H, W, L.w1, 1, nullptr, b.a3, b.ga3, st)));
     if (img) NSM_TRY(wgrad_tc(4, 16, 3, b.feat, 0, b.ga3, nullptr, n, H, W, b.wpart, L.dw3, L.db3, err, st));

@@ -55,6 +55,12 @@ cudaError_t conv3_tc(int cin, int cout, const float* x, int N, int H, int W, con
 // bounded wait gave up.
 cudaError_t wgrad_tc(int cin, int cout, int k, const float* x, int relu_in, const float* g, const float* gm, int N,
                      int H, int W, float* part, float* dW, float* db, int* err, cudaStream_t st);
+// 1x1 weight gradients on CUDA cores (train_wgrad.cu): dW += sum_p g~[p][o]
+// x~[p][c] (OIHW), db += sum_p g~[p][o], with x~ and g~ as for wgrad_tc; per-CTA
+// partial sums in part added in a fixed order.  (cin, cout) one of the
+// network's 1x1 layers (cudaErrorInvalidValue otherwise).
+cudaError_t wgrad1x1_tiles(int cin, int cout, const float* x, int relu_in, const float* g, const float* gm, int N,
+                           int H, int W, float* part, float* dW, float* db, cudaStream_t st);
 // dW[e] += sum_s part[s][e] for e < nw, db[e - nw] += ... for nw <= e < entries, s in order.
 cudaError_t slot_reduce(const float* part, int slots, int entries, int nw, float* dW, float* db, cudaStream_t st);
 cudaError_t loss_l1(const float* vis, const float* target, int B, int T, size_t npx, float alpha, float* gvis,

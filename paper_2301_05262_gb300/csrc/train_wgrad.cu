@@ -451,5 +451,141 @@ cudaError_t slot_reduce(const float* part, int slots, int entries, int nw, float
     return cudaGetLastError();
 }
 
+// ------------------------------------------------------------------ 1x1 weight gradients
+// dW[o][c] += sum_p g~[p][o] x~[p][c], db[o] += sum_p g~[p][o] of a 1x1 layer.
+// Two reads per pixel and 16 to 64 channels each: bound by HBM, not a dense
+// contraction, so FP32 on CUDA cores.  CTA b takes the contiguous tiles
+// [T b / G, T (b + 1) / G) of 256 pixels (T tiles, G CTAs); each tile's x~
+// (rectified) and g~ (masked) rows arrive with coalesced float4 loads in a
+// shared tile.  Thread t keeps the 4 x 4 block (o-block, c-block) = t % NB of
+// dW (NB = C_out C_in / 16 blocks) over pixels t / NB, t / NB + NG, ... (NG =
+// 256 / NB pixel groups) of every tile, plus the bias for c-block 0; the
+// groups meet in shared memory in group order and the CTA's sums go to its
+// slot, which slot_reduce adds in slot order: a fixed order throughout.
+constexpr int kW1P = 256;  // pixels per tile = threads per CTA
+
+template <int CIN, int COUT>
+struct W1Shape {
+    static constexpr int CI4 = CIN / 4, CO4 = COUT / 4, NB = CI4 * CO4, NG = kW1P / NB;
+    static constexpr int SX = CIN + 4, SG = COUT + 4;  // padded rows (conflict-free float4 reads)
+    static constexpr int ENTRIES = COUT * CIN + COUT;
+    static constexpr size_t SMEM = sizeof(float) * static_cast<size_t>(kW1P) * (SX + SG);
+    static_assert(CIN % 4 == 0 && COUT % 4 == 0 && kW1P % NB == 0 && NG >= 1, "1x1 weight-gradient shape");
+    static_assert(NG * NB * 20 <= kW1P * (SX + SG), "group sums fit the tile storage");
+};
+
+template <int CIN, int COUT>
+__global__ void __launch_bounds__(kW1P) wgrad1x1_tile_kernel(const float* __restrict__ x, int relu_in,
+                                                             const float* __restrict__ g, const float* __restrict__ gm,
+                                                             size_t npx, float* __restrict__ part) {
+    using S = W1Shape<CIN, COUT>;
+    extern __shared__ float4 w1smem[];
+    float* xs = reinterpret_cast<float*>(w1smem);  // [kW1P][SX]
+    float* gs = xs + kW1P * S::SX;                  // [kW1P][SG]
+    const int t = threadIdx.x, blk = t % S::NB, pg = t / S::NB;
+    const int ob = blk / S::CI4, cb = blk % S::CI4;
+    float acc[4][4] = {};
+    float bacc[4] = {0.f, 0.f, 0.f, 0.f};
+    const long long tiles = static_cast<long long>((npx + kW1P - 1) / kW1P);
+    const long long t0 = tiles * blockIdx.x / gridDim.x, t1 = tiles * (blockIdx.x + 1) / gridDim.x;
+    for (long long tile = t0; tile < t1; ++tile) {
+        const size_t p0 = static_cast<size_t>(tile) * kW1P;
+        const int np = static_cast<int>(npx - p0 < static_cast<size_t>(kW1P) ? npx - p0 : kW1P);
+        const float4* x4 = reinterpret_cast<const float4*>(x + p0 * CIN);
+        const float4* g4 = reinterpret_cast<const float4*>(g + p0 * COUT);
+        const float4* m4 = gm ? reinterpret_cast<const float4*>(gm + p0 * COUT) : nullptr;
+        // rows past the last pixel are zero, so the products need no bound
+#pragma unroll
+        for (int k = 0; k < S::CI4; ++k) {
+            const int i = t + kW1P * k;
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (i < np * S::CI4) {
+                v = __ldg(x4 + i);
+                if (relu_in) v = make_float4(fmaxf(v.x, 0.f), fmaxf(v.y, 0.f), fmaxf(v.z, 0.f), fmaxf(v.w, 0.f));
+            }
+            *reinterpret_cast<float4*>(xs + (i / S::CI4) * S::SX + 4 * (i % S::CI4)) = v;
+        }
+#pragma unroll
+        for (int k = 0; k < S::CO4; ++k) {
+            const int i = t + kW1P * k;
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (i < np * S::CO4) {
+                v = __ldg(g4 + i);
+                if (m4) {
+                    const float4 m = __ldg(m4 + i);
+                    v = make_float4(m.x > 0.f ? v.x : 0.f, m.y > 0.f ? v.y : 0.f, m.z > 0.f ? v.z : 0.f,
+                                    m.w > 0.f ? v.w : 0.f);
+                }
+            }
+            *reinterpret_cast<float4*>(gs + (i / S::CO4) * S::SG + 4 * (i % S::CO4)) = v;
+        }
+        __syncthreads();
+        for (int p = pg; p < np; p += S::NG) {
+            const float4 xv = *reinterpret_cast<const float4*>(xs + p * S::SX + 4 * cb);
+            const float4 gv = *reinterpret_cast<const float4*>(gs + p * S::SG + 4 * ob);
+            const float gq[4] = {gv.x, gv.y, gv.z, gv.w}, xq[4] = {xv.x, xv.y, xv.z, xv.w};
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(gq[i], xq[j], acc[i][j]);
+                bacc[i] += gq[i];
+            }
+        }
+        __syncthreads();  // the tile's rows are free for the next tile
+    }
+    // group sums, in group order, into the CTA's slot
+    float* red = xs;  // [NG][NB][20]
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) red[(pg * S::NB + blk) * 20 + 4 * i + j] = acc[i][j];
+        red[(pg * S::NB + blk) * 20 + 16 + i] = bacc[i];
+    }
+    __syncthreads();
+    float* slot = part + static_cast<size_t>(blockIdx.x) * S::ENTRIES;
+    for (int e = t; e < S::NB * 20; e += kW1P) {
+        const int b2 = e / 20, k = e % 20;
+        float v = 0.f;
+        for (int q = 0; q < S::NG; ++q) v += red[(q * S::NB + b2) * 20 + k];
+        const int o0 = 4 * (b2 / S::CI4), c0 = 4 * (b2 % S::CI4);
+        if (k < 16) slot[(o0 + k / 4) * CIN + c0 + k % 4] = v;
+        else if (c0 == 0) slot[COUT * CIN + o0 + (k - 16)] = v;
+    }
+}
+
+template <int CIN, int COUT>
+static cudaError_t launch_wgrad1x1(const float* x, int relu_in, const float* g, const float* gm, size_t npx,
+                                   float* part, float* dW, float* db, cudaStream_t st) {
+    using S = W1Shape<CIN, COUT>;
+    auto kern = wgrad1x1_tile_kernel<CIN, COUT>;
+    static int per_sm = 0;  // resident CTAs per SM, from the tile storage
+    if (per_sm == 0) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(S::SMEM));
+        if (e != cudaSuccess) return e;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kW1P, S::SMEM) != cudaSuccess || per_sm < 1)
+            per_sm = 1;
+    }
+    const long long tiles = static_cast<long long>((npx + kW1P - 1) / kW1P);
+    long long grid = static_cast<long long>(num_sms()) * per_sm;
+    if (grid > tiles) grid = tiles;
+    if (grid * S::ENTRIES > kWgPartFloats) grid = kWgPartFloats / S::ENTRIES;
+    kern<<<static_cast<unsigned>(grid), kW1P, S::SMEM, st>>>(x, relu_in, g, gm, npx, part);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return slot_reduce(part, static_cast<int>(grid), S::ENTRIES, COUT * CIN, dW, db, st);
+}
+
+cudaError_t wgrad1x1_tiles(int cin, int cout, const float* x, int relu_in, const float* g, const float* gm, int N,
+                           int H, int W, float* part, float* dW, float* db, cudaStream_t st) {
+    const size_t npx = static_cast<size_t>(N) * H * W;
+    if (npx == 0) return cudaSuccess;
+#define NSM_W1(a, b) \
+    if (cin == a && cout == b) return launch_wgrad1x1<a, b>(x, relu_in, g, gm, npx, part, dW, db, st);
+    NSM_W1(16, 16) NSM_W1(32, 16) NSM_W1(32, 32) NSM_W1(64, 32)
+#undef NSM_W1
+    return cudaErrorInvalidValue;
+}
+
+
 }  // namespace tr
 }  // namespace nsm
