@@ -418,8 +418,9 @@ nsm_status nsm_train_state_set_forward_precision(nsm_train_state* st, nsm_precis
 /* Form of the backward's contractions (Sec. 3.3, Eq. 2 adjoint): the
  * recomputed 3x3 pre-activations of every level, the data gradients through
  * them (the transposed, flipped weights) and the weight and bias gradients of
- * every 3x3 and 1x1 layer.  NSM_FP32 (default; FP32 CUDA-core kernels, weight
- * gradients summed with atomics, so their last bits vary from run to run) or
+ * every 3x3 and 1x1 layer.  NSM_FP32 (default; FP32 CUDA-core kernels, the 3x3
+ * weight gradients summed with atomics, so their last bits vary from run to
+ * run) or
  * NSM_BF16 (tcgen05: implicit GEMMs for the 3x3 convolutions and a GEMM over
  * the pixels for each 3x3 weight gradient, with compensated BF16 operands:
  * activations, gradients and weights as hi + lo BF16 pairs, all four products

@@ -18,9 +18,10 @@
 //              checkpoint, the 2x2 pooling (encoders) or the head (level 0);
 //   conv1x1    1x1 layers: coalesced pixel tiles through shared memory, one
 //              thread per pixel for the products;
-//   conv_wgrad dW += sum_p g~(p) x~(p + tap), db += sum_p g~(p): 8 x 8 register
-//              blocks of outer products per thread, one atomicAdd per weight
-//              per CTA; wgrad1x1 for the 1x1 layers (grid-stride, no staging);
+//   conv_wgrad dW += sum_p g~(p) x~(p + tap), db += sum_p g~(p) of the 3x3
+//              layers: 8 x 8 register blocks of outer products per thread, one
+//              atomicAdd per weight per CTA (the 1x1 layers' weight gradients:
+//              wgrad1x1_tiles, fixed order);
 //   pooling, bilinear x2 and their adjoints, head, loss, Adam.
 #include <vector>
 
@@ -399,74 +400,6 @@ __global__ void __launch_bounds__(WNT, 2) conv_wgrad_kernel(const float* __restr
         for (int o = tid; o < COUT; o += WNT) atomicAdd(db + o, dbs[o]);
 }
 
-// 1x1 weight gradients (no halo, so no tile staging): dW[o][c] += sum_p g~[p][o]
-// relu?(x[p][c]), db[o] += sum_p g~[p][o].  Thread t owns the 8 x 8 block
-// t % NB of (output, input) channels and walks the pixels t / NB, + PL, ...
-// of a grid-stride range with 16-byte loads straight from global memory (the
-// NB threads of a pixel share its lines in L1); lanes of a block meet by warp
-// shuffles, warps in shared memory, CTAs by one atomicAdd per weight.
-template <int CIN, int COUT>
-__global__ void __launch_bounds__(256) wgrad1x1_kernel(const float* __restrict__ x, int relu_in,
-                                                       const float* __restrict__ g, const float* __restrict__ gm,
-                                                       size_t npx, float* __restrict__ dW, float* __restrict__ db) {
-    constexpr int BO = 8, BI = 8, BE = BO * BI, OB = COUT / BO, CB = CIN / BI, NB = OB * CB, PL = 256 / NB;
-    static_assert(CIN % BI == 0 && COUT % BO == 0 && 256 % NB == 0 && NB <= 32, "1x1 blocks");
-    __shared__ float red[CIN * COUT + COUT];
-    const int tid = threadIdx.x, b = tid % NB, pl = tid / NB, ob = b / CB, cb = b % CB;
-    for (int i = tid; i < CIN * COUT + COUT; i += 256) red[i] = 0.f;
-    float acc[BE], dacc[BO];
-#pragma unroll
-    for (int e = 0; e < BE; ++e) acc[e] = 0.f;
-#pragma unroll
-    for (int i = 0; i < BO; ++i) dacc[i] = 0.f;
-    for (size_t p = static_cast<size_t>(blockIdx.x) * PL + pl; p < npx; p += static_cast<size_t>(gridDim.x) * PL) {
-        const float4* gp = reinterpret_cast<const float4*>(g + p * COUT + BO * ob);
-        const float4* xp = reinterpret_cast<const float4*>(x + p * CIN + BI * cb);
-        float4 g0 = __ldg(gp), g1 = __ldg(gp + 1), x0 = __ldg(xp), x1 = __ldg(xp + 1);
-        if (gm) {
-            const float4* mp = reinterpret_cast<const float4*>(gm + p * COUT + BO * ob);
-            const float4 m0 = __ldg(mp), m1 = __ldg(mp + 1);
-            g0 = make_float4(m0.x > 0.f ? g0.x : 0.f, m0.y > 0.f ? g0.y : 0.f, m0.z > 0.f ? g0.z : 0.f,
-                             m0.w > 0.f ? g0.w : 0.f);
-            g1 = make_float4(m1.x > 0.f ? g1.x : 0.f, m1.y > 0.f ? g1.y : 0.f, m1.z > 0.f ? g1.z : 0.f,
-                             m1.w > 0.f ? g1.w : 0.f);
-        }
-        const float gv[BO] = {g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, g1.z, g1.w};
-        float xv[BI] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
-        if (relu_in) {
-#pragma unroll
-            for (int j = 0; j < BI; ++j) xv[j] = fmaxf(xv[j], 0.f);
-        }
-#pragma unroll
-        for (int i = 0; i < BO; ++i) {
-            dacc[i] += gv[i];
-#pragma unroll
-            for (int j = 0; j < BI; ++j) acc[BI * i + j] = fmaf(gv[i], xv[j], acc[BI * i + j]);
-        }
-    }
-    // lanes l, l + NB, ... of a warp hold the same block
-#pragma unroll
-    for (int o = NB; o < 32; o <<= 1) {
-#pragma unroll
-        for (int e = 0; e < BE; ++e) acc[e] += __shfl_xor_sync(0xffffffffu, acc[e], o);
-#pragma unroll
-        for (int i = 0; i < BO; ++i) dacc[i] += __shfl_xor_sync(0xffffffffu, dacc[i], o);
-    }
-    __syncthreads();
-    if ((tid & 31) < NB) {
-#pragma unroll
-        for (int e = 0; e < BE; ++e) atomicAdd(red + (BO * ob + e / BI) * CIN + BI * cb + e % BI, acc[e]);
-        if (cb == 0) {
-#pragma unroll
-            for (int i = 0; i < BO; ++i) atomicAdd(red + CIN * COUT + BO * ob + i, dacc[i]);
-        }
-    }
-    __syncthreads();
-    for (int i = tid; i < CIN * COUT; i += 256) atomicAdd(dW + i, red[i]);
-    if (db)
-        for (int i = tid; i < COUT; i += 256) atomicAdd(db + i, red[CIN * COUT + i]);
-}
-
 // 1x1 layers (no halo): tiles of kP1 pixels, whose NHWC rows are contiguous in
 // memory, move between HBM and a shared tile with consecutive threads on
 // consecutive float4s (coalesced); the input rectification / mask is applied
@@ -611,15 +544,6 @@ cudaError_t conv_fwd(const float* x, const float* xm, int relu_in, int N, int H,
 template <int CIN, int COUT, int K>
 cudaError_t conv_wgrad(const float* x, int relu_in, const float* g, const float* gm, int N, int H, int W, float* dW,
                        float* db, cudaStream_t st) {
-    if constexpr (K == 1 && CIN % 8 == 0) {
-        const size_t npx = static_cast<size_t>(N) * H * W;
-        if (npx == 0) return cudaSuccess;
-        const size_t per = 256 / ((COUT / 8) * (CIN / 8));  // pixels per CTA sweep
-        const size_t need = (npx + per - 1) / per, cap = static_cast<size_t>(num_sms()) * 4;
-        wgrad1x1_kernel<CIN, COUT><<<static_cast<int>(need < cap ? need : cap), 256, 0, st>>>(x, relu_in, g, gm, npx,
-                                                                                                dW, db);
-        return cudaGetLastError();
-    }
     constexpr int P = K / 2;
     const size_t smem = sizeof(float) * ((WTH + 2 * P) * (WTW + 2 * P) * CIN + WTH * WTW * COUT + COUT);
     auto kern = conv_wgrad_kernel<CIN, COUT, K>;
@@ -1020,9 +944,10 @@ cudaError_t forward(const float* th, const Buffers& b, int N, int Nb, int H, int
 // With gfeat != nullptr also the feature gradient [Nb][H][W][4].  With img
 // != nullptr (the conv3_pack images of th) the 3x3 recomputations (with the
 // level's 1x1 in their epilogue) and data gradients (conv3_tc) and the 3x3
-// weight gradients (wgrad_tc) run on the tensor cores, the 1x1 weight
-// gradients on CUDA cores (wgrad1x1_tiles), every weight gradient (the head's
-// by per-block slots) reduced in a fixed order; else the FP32 kernels.
+// weight gradients (wgrad_tc) run on the tensor cores, every weight gradient
+// (the head's by per-block slots) reduced in a fixed order; else the FP32
+// kernels.  The 1x1 weight gradients run on CUDA cores in both forms
+// (wgrad1x1_tiles: memory-bound, fixed order).
 cudaError_t backward(const float* th, float* grad, const Buffers& b, int Nb, int H, int W, float* gfeat,
                      cudaStream_t st, const uint4* img, int* err) {
     const Conv3Images im = conv3_images();
@@ -1047,8 +972,7 @@ cudaError_t backward(const float* th, float* grad, const Buffers& b, int Nb, int
                                             img ? b.wpart : nullptr);
         if (img) NSM_TRY(slot_reduce(b.wpart, hb, 17, 17, grad + o.w[HEAD], nullptr, st));
     }
-    if (img) NSM_TRY(wgrad1x1_tiles(16, 16, b.a3, 1, b.ga1, nullptr, n, H, W, b.wpart, L.dw1, L.db1, st));
-    else NSM_TRY((conv_wgrad<16, 16, 1>(b.a3, 1, b.ga1, nullptr, n, H, W, L.dw1, L.db1, st)));
+    NSM_TRY(wgrad1x1_tiles(16, 16, b.a3, 1, b.ga1, nullptr, n, H, W, b.wpart, L.dw1, L.db1, st));  // FP32, both forms
     NSM_TRY((conv_fwd<16, 16, 1>(b.ga1, nullptr, 0, n, H, W, L.w1, 1, nullptr, b.a3, b.ga3, st)));
     if (img) NSM_TRY(wgrad_tc(16, 16, 3, b.xin, 0, b.ga3, nullptr, n, H, W, b.wpart, L.dw3, L.db3, err, st));
     else NSM_TRY((conv_wgrad<16, 16, 3>(b.xin, 0, b.ga3, nullptr, n, H, W, L.dw3, L.db3, st)));
@@ -1065,8 +989,7 @@ cudaError_t backward(const float* th, float* grad, const Buffers& b, int Nb, int
         NSM_TRY((conv_fwd<32, 16, 1>(b.a3, nullptr, 1, n, H1, W1, L.w1, 0, L.b1, nullptr, b.a1, st)));
     }
     // g_a1 = g_d1 (a1 > 0)
-    if (img) NSM_TRY(wgrad1x1_tiles(32, 16, b.a3, 1, b.glo, b.a1, n, H1, W1, b.wpart, L.dw1, L.db1, st));
-    else NSM_TRY((conv_wgrad<32, 16, 1>(b.a3, 1, b.glo, b.a1, n, H1, W1, L.dw1, L.db1, st)));
+    NSM_TRY(wgrad1x1_tiles(32, 16, b.a3, 1, b.glo, b.a1, n, H1, W1, b.wpart, L.dw1, L.db1, st));  // FP32, both forms
     NSM_TRY((conv_fwd<16, 32, 1>(b.glo, b.a1, 0, n, H1, W1, L.w1, 1, nullptr, b.a3, b.ga3, st)));
     if (img) NSM_TRY(wgrad_tc(32, 32, 3, b.xin, 0, b.ga3, nullptr, n, H1, W1, b.wpart, L.dw3, L.db3, err, st));
     else NSM_TRY((conv_wgrad<32, 32, 3>(b.xin, 0, b.ga3, nullptr, n, H1, W1, L.dw3, L.db3, st)));
@@ -1081,8 +1004,7 @@ cudaError_t backward(const float* th, float* grad, const Buffers& b, int Nb, int
         NSM_TRY((conv_fwd<32, 64, 3, 16>(b.p1, nullptr, 0, n, H2, W2, L.w3, 0, L.b3, nullptr, b.a3, st)));
         NSM_TRY((conv_fwd<64, 32, 1>(b.a3, nullptr, 1, n, H2, W2, L.w1, 0, L.b1, nullptr, b.a1, st)));
     }
-    if (img) NSM_TRY(wgrad1x1_tiles(64, 32, b.a3, 1, b.glo, b.a1, n, H2, W2, b.wpart, L.dw1, L.db1, st));
-    else NSM_TRY((conv_wgrad<64, 32, 1>(b.a3, 1, b.glo, b.a1, n, H2, W2, L.dw1, L.db1, st)));
+    NSM_TRY(wgrad1x1_tiles(64, 32, b.a3, 1, b.glo, b.a1, n, H2, W2, b.wpart, L.dw1, L.db1, st));  // FP32, both forms
     NSM_TRY((conv_fwd<32, 64, 1>(b.glo, b.a1, 0, n, H2, W2, L.w1, 1, nullptr, b.a3, b.ga3, st)));
     if (img) NSM_TRY(wgrad_tc(32, 64, 3, b.p1, 0, b.ga3, nullptr, n, H2, W2, b.wpart, L.dw3, L.db3, err, st));
     else NSM_TRY((conv_wgrad<32, 64, 3>(b.p1, 0, b.ga3, nullptr, n, H2, W2, L.dw3, L.db3, st)));
@@ -1097,8 +1019,7 @@ cudaError_t backward(const float* th, float* grad, const Buffers& b, int Nb, int
         NSM_TRY((conv_fwd<16, 32, 3>(b.e0, nullptr, 0, n, H1, W1, L.w3, 0, L.b3, nullptr, b.a3, st)));
         NSM_TRY((conv_fwd<32, 32, 1>(b.a3, nullptr, 1, n, H1, W1, L.w1, 0, L.b1, nullptr, b.a1, st)));
     }
-    if (img) NSM_TRY(wgrad1x1_tiles(32, 32, b.a3, 1, b.glo, b.a1, n, H1, W1, b.wpart, L.dw1, L.db1, st));
-    else NSM_TRY((conv_wgrad<32, 32, 1>(b.a3, 1, b.glo, b.a1, n, H1, W1, L.dw1, L.db1, st)));
+    NSM_TRY(wgrad1x1_tiles(32, 32, b.a3, 1, b.glo, b.a1, n, H1, W1, b.wpart, L.dw1, L.db1, st));  // FP32, both forms
     NSM_TRY((conv_fwd<32, 32, 1>(b.glo, b.a1, 0, n, H1, W1, L.w1, 1, nullptr, b.a3, b.ga3, st)));
     if (img) NSM_TRY(wgrad_tc(16, 32, 3, b.e0, 0, b.ga3, nullptr, n, H1, W1, b.wpart, L.dw3, L.db3, err, st));
     else NSM_TRY((conv_wgrad<16, 32, 3>(b.e0, 0, b.ga3, nullptr, n, H1, W1, L.dw3, L.db3, st)));
@@ -1113,8 +1034,7 @@ cudaError_t backward(const float* th, float* grad, const Buffers& b, int Nb, int
         NSM_TRY((conv_fwd<4, 16, 3>(b.feat, nullptr, 0, n, H, W, L.w3, 0, L.b3, nullptr, b.a3, st)));
         NSM_TRY((conv_fwd<16, 16, 1>(b.a3, nullptr, 1, n, H, W, L.w1, 0, L.b1, nullptr, b.a1, st)));
     }
-    if (img) NSM_TRY(wgrad1x1_tiles(16, 16, b.a3, 1, b.gtmp, b.a1, n, H, W, b.wpart, L.dw1, L.db1, st));
-    else NSM_TRY((conv_wgrad<16, 16, 1>(b.a3, 1, b.gtmp, b.a1, n, H, W, L.dw1, L.db1, st)));
+    NSM_TRY(wgrad1x1_tiles(16, 16, b.a3, 1, b.gtmp, b.a1, n, H, W, b.wpart, L.dw1, L.db1, st));  // FP32, both forms
     NSM_TRY((conv_fwd<16, 16, 1>(b.gtmp, b.a1, 0, n, H, W, L.w1, 1, nullptr, b.a3, b.ga3, st)));
     if (img) NSM_TRY(wgrad_tc(4, 16, 3, b.feat, 0, b.ga3, nullptr, n, H, W, b.wpart, L.dw3, L.db3, err, st));
     else NSM_TRY((conv_wgrad<4, 16, 3>(b.feat, 0, b.ga3, nullptr, n, H, W, L.dw3, L.db3, st)));
